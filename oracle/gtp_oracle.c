@@ -1,0 +1,346 @@
+/*
+ * FP64 reference oracle for gate-level time-based power analysis.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is a plain, slow, single-threaded CPU
+ * statement of what the GPU engine computes.  Only the test suite, the smoke
+ * check and the benchmark's CPU baseline call it; the GPU engine never does.
+ * It shares no code with the engine.
+ *
+ * What it computes (paper section / equation in brackets):
+ *   * An event is (value, timestamp) on one pin of one gate; the gate state is
+ *     the vector of all pin values, changed by each event [Sec. 2.1].
+ *   * Events of a gate are processed in time order; all events sharing one
+ *     timestamp form a group.  Lookups for every event of the group use the
+ *     state held before the group; the state is updated after the whole group
+ *     [Algorithm 1, the timestamp loop].
+ *   * Internal energy of an input-pin event: the state-dependent NLDM table
+ *     selected by (cell, pin, edge, side-input bits of the pre-group state),
+ *     interpolated bilinearly at (input slew, output load), times the cell's
+ *     energy scale [Sec. 2.2; Sec. 4.1 state-indexed lookup].
+ *   * Switching energy of an output-pin event: 0.5*C*Vdd^2 per output toggle
+ *     [Eq. switching energy, read as half of c*v^2 per toggle].
+ *   * Leakage: the state-dependent leakage power holds between events; the
+ *     energy of an interval is P*dt [Eq. leakage energy], and each interval
+ *     is split over the time bins it overlaps in proportion to the overlap
+ *     [Sec. 2.4.2, waveform accumulation].
+ *   * Dynamic energy goes to the bin containing the event time.
+ * Units: ps, fF, V, fJ, nW.  E[fJ] = P[nW] * dt[ps] * 1e-6; 0.5*C[fF]*V^2 = fJ.
+ *
+ * Parity status: the walk and the adjoint are pinned by closed forms, a
+ * per-picosecond brute-force simulator, library interpolation and invariants
+ * (tests/test_oracle_*.py).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_OK 0
+#define OR_EINVAL (-1)
+#define OR_EORDER (-2)
+#define OR_ERANGE (-3)
+#define OR_ENOTOGGLE (-4)
+
+typedef struct {
+  int32_t n_cells;
+  const int32_t* n_in;      /* [n_cells] input pins; output pin index = n_in */
+  double vdd;               /* V */
+  int32_t n_slew;
+  const float* slew_axis;   /* [n_slew] ps, increasing */
+  int32_t n_load;
+  const float* load_axis;   /* [n_load] fF, increasing */
+  const float* e_int;       /* flat tables, fJ */
+  const float* p_leak;      /* flat leakage, nW */
+  const double* escale;     /* [n_cells] */
+  const double* lscale;     /* [n_cells] */
+} oracle_lib;
+
+typedef struct {
+  int64_t n_gates;
+  const int32_t* cell;      /* [n_gates] */
+  const double* load_ff;    /* [n_gates] */
+  const float* slew_ps;     /* [n_gates][slew_stride][2] */
+  int32_t slew_stride;
+} oracle_net;
+
+typedef struct {
+  int64_t window_ps;
+  const int64_t* offsets;   /* [n_gates + 1] */
+  const uint32_t* records;  /* [n_events][2] = {t_ps, meta} */
+  const uint8_t* init_state;/* [n_gates] */
+} oracle_trace;
+
+/* ---------------------------------------------------------------- lookup */
+
+/* Segment of an interpolation axis: the lower knot index i with
+ * axis[i] <= x < axis[i+1], clamped to [0, n-2] so that points outside the
+ * axis extrapolate linearly from the edge segment. */
+static int32_t segment_of(const float* axis, int32_t n, double x) {
+  int32_t i = 0;
+  while (i < n - 2 && x >= (double)axis[i + 1]) ++i;
+  return i;
+}
+
+/* Bilinear interpolation of one n_slew x n_load table (slew-major). */
+double oracle_bilinear(int32_t n_slew, const float* slew_axis, int32_t n_load, const float* load_axis,
+                       const float* table, double slew, double load) {
+  int32_t i = segment_of(slew_axis, n_slew, slew);
+  int32_t j = segment_of(load_axis, n_load, load);
+  double fs = (slew - slew_axis[i]) / ((double)slew_axis[i + 1] - slew_axis[i]);
+  double fl = (load - load_axis[j]) / ((double)load_axis[j + 1] - load_axis[j]);
+  double t00 = table[i * n_load + j], t01 = table[i * n_load + j + 1];
+  double t10 = table[(i + 1) * n_load + j], t11 = table[(i + 1) * n_load + j + 1];
+  return (1.0 - fs) * (1.0 - fl) * t00 + (1.0 - fs) * fl * t01 + fs * (1.0 - fl) * t10 + fs * fl * t11;
+}
+
+/* Partial derivative of the bilinear interpolant with respect to the load,
+ * on the located load segment (right derivative at a knot). */
+double oracle_bilinear_dload(int32_t n_slew, const float* slew_axis, int32_t n_load, const float* load_axis,
+                             const float* table, double slew, double load) {
+  int32_t i = segment_of(slew_axis, n_slew, slew);
+  int32_t j = segment_of(load_axis, n_load, load);
+  double fs = (slew - slew_axis[i]) / ((double)slew_axis[i + 1] - slew_axis[i]);
+  double w = (double)load_axis[j + 1] - load_axis[j];
+  double t00 = table[i * n_load + j], t01 = table[i * n_load + j + 1];
+  double t10 = table[(i + 1) * n_load + j], t11 = table[(i + 1) * n_load + j + 1];
+  return ((1.0 - fs) * (t01 - t00) + fs * (t11 - t10)) / w;
+}
+
+/* Side-input state: the input-pin bits of S other than `pin`, compacted in
+ * pin order (state-indexed lookup, Sec. 4.1). */
+static uint32_t side_bits(uint32_t S, int32_t pin, int32_t n_in) {
+  uint32_t side = 0;
+  int32_t pos = 0;
+  for (int32_t p = 0; p < n_in; ++p) {
+    if (p == pin) continue;
+    side |= ((S >> p) & 1u) << pos;
+    ++pos;
+  }
+  return side;
+}
+
+/* Start of cell c's tables (in tables) and of its leakage entries. */
+static void cell_bases(const oracle_lib* L, int64_t* tab_base, int64_t* leak_base) {
+  int64_t t = 0, l = 0;
+  for (int32_t c = 0; c < L->n_cells; ++c) {
+    tab_base[c] = t;
+    leak_base[c] = l;
+    t += (int64_t)L->n_in[c] * 2 * (1ll << (L->n_in[c] - 1));
+    l += 1ll << (L->n_in[c] + 1);
+  }
+}
+
+static const float* table_for(const oracle_lib* L, const int64_t* tab_base, int32_t c, int32_t pin,
+                              int32_t edge, uint32_t side) {
+  int64_t n_side = 1ll << (L->n_in[c] - 1);
+  int64_t idx = tab_base[c] + ((int64_t)(pin * 2 + edge) * n_side + side);
+  return L->e_int + idx * (int64_t)L->n_slew * L->n_load;
+}
+
+/* ---------------------------------------------------------------- binning */
+
+typedef struct {
+  int64_t bin_ps;
+  int64_t n_bins;
+  double* out;              /* all bins, or the sampled bins */
+  int64_t n_sample;         /* 0 = all bins */
+  const int64_t* sample;    /* sorted bin indices */
+} binner;
+
+static int64_t first_sample_at_or_after(const binner* B, int64_t b) {
+  int64_t lo = 0, hi = B->n_sample;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) / 2;
+    if (B->sample[mid] < b) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+static void bin_add(const binner* B, int64_t t, double e) {
+  if (!B->out) return;
+  int64_t b = t / B->bin_ps;
+  if (B->n_sample == 0) { B->out[b] += e; return; }
+  int64_t k = first_sample_at_or_after(B, b);
+  if (k < B->n_sample && B->sample[k] == b) B->out[k] += e;
+}
+
+/* Leakage of power P (nW) over [a, b) ps, split over the overlapped bins. */
+static void bin_add_interval(const binner* B, double P, int64_t a, int64_t b) {
+  if (!B->out || b <= a) return;
+  int64_t k0 = a / B->bin_ps, k1 = (b - 1) / B->bin_ps;
+  if (B->n_sample == 0) {
+    for (int64_t k = k0; k <= k1; ++k) {
+      int64_t lo = a > k * B->bin_ps ? a : k * B->bin_ps;
+      int64_t hi = b < (k + 1) * B->bin_ps ? b : (k + 1) * B->bin_ps;
+      B->out[k] += P * (double)(hi - lo) * 1e-6;
+    }
+    return;
+  }
+  for (int64_t s = first_sample_at_or_after(B, k0); s < B->n_sample && B->sample[s] <= k1; ++s) {
+    int64_t k = B->sample[s];
+    int64_t lo = a > k * B->bin_ps ? a : k * B->bin_ps;
+    int64_t hi = b < (k + 1) * B->bin_ps ? b : (k + 1) * B->bin_ps;
+    B->out[s] += P * (double)(hi - lo) * 1e-6;
+  }
+}
+
+/* ---------------------------------------------------------------- the walk */
+
+/*
+ * Walk every selected gate.  gates == NULL selects all; otherwise gates[i]
+ * (i < n_sel) names gate indices and the per-gate outputs are written at
+ * position i.  bins: all n_bins bins (sample == NULL) or the n_sample sorted
+ * bins in `sample`; NULL skips the waveform.  Per-gate outputs may be NULL.
+ * On a malformed trace returns a negative code and the offending record
+ * index in *bad_record.
+ */
+int oracle_walk(const oracle_lib* L, const oracle_net* N, const oracle_trace* T, int64_t bin_ps,
+                int64_t n_sel, const int64_t* gates,
+                double* bins, int64_t n_sample, const int64_t* sample,
+                double* e_leak, double* e_int, double* e_sw, int64_t* n_events, uint8_t* final_state,
+                int64_t* bad_record) {
+  if (bin_ps <= 0 || T->window_ps <= 0 || T->window_ps % bin_ps != 0) return OR_EINVAL;
+  int64_t* tab_base = (int64_t*)malloc(sizeof(int64_t) * (size_t)L->n_cells);
+  int64_t* leak_base = (int64_t*)malloc(sizeof(int64_t) * (size_t)L->n_cells);
+  cell_bases(L, tab_base, leak_base);
+  binner B = {bin_ps, T->window_ps / bin_ps, bins, n_sample, sample};
+  int64_t count = gates ? n_sel : N->n_gates;
+  int rc = OR_OK;
+  double half_v2 = 0.5 * L->vdd * L->vdd;
+  for (int64_t gi = 0; gi < count && rc == OR_OK; ++gi) {
+    int64_t g = gates ? gates[gi] : gi;
+    int32_t c = N->cell[g];
+    int32_t n_in = L->n_in[c];
+    int32_t n_pins = n_in + 1;
+    double C = N->load_ff[g];
+    double ls = L->lscale[c], es = L->escale[c];
+    const float* leak = L->p_leak + leak_base[c];
+    uint32_t S = T->init_state[g];
+    int64_t t_prev = 0;
+    double El = 0.0, Ei = 0.0, Es = 0.0;
+    int64_t a = T->offsets[g], b = T->offsets[g + 1];
+    int64_t i = a;
+    while (i < b) {
+      int64_t t = (int32_t)T->records[2 * i];
+      int64_t j = i;
+      while (j < b && (int32_t)T->records[2 * j] == t) ++j;
+      if (t < 0 || t >= T->window_ps) { rc = OR_ERANGE; *bad_record = i; break; }
+      if (t < t_prev) { rc = OR_EORDER; *bad_record = i; break; }
+      /* leakage held since the previous group, at the pre-group state */
+      double P = (double)leak[S] * ls;
+      El += P * (double)(t - t_prev) * 1e-6;
+      bin_add_interval(&B, P, t_prev, t);
+      /* dynamic energy of each event in the group, at the pre-group state */
+      uint32_t S_next = S;
+      for (int64_t e = i; e < j; ++e) {
+        uint32_t meta = T->records[2 * e + 1];
+        int32_t pin = (int32_t)(meta & 0xFu);
+        int32_t value = (int32_t)((meta >> 4) & 1u);
+        if ((meta >> 5) != 0 || pin >= n_pins) { rc = OR_ERANGE; *bad_record = e; break; }
+        if ((int32_t)((S_next >> pin) & 1u) == value) { rc = OR_ENOTOGGLE; *bad_record = e; break; }
+        S_next ^= 1u << pin;
+        double E;
+        if (pin < n_in) {
+          const float* tab = table_for(L, tab_base, c, pin, value, side_bits(S, pin, n_in));
+          double slew = N->slew_ps[((int64_t)g * N->slew_stride + pin) * 2 + value];
+          E = es * oracle_bilinear(L->n_slew, L->slew_axis, L->n_load, L->load_axis, tab, slew, C);
+          Ei += E;
+        } else {
+          E = half_v2 * C;
+          Es += E;
+        }
+        bin_add(&B, t, E);
+      }
+      if (rc != OR_OK) break;
+      S = S_next;
+      t_prev = t;
+      i = j;
+    }
+    if (rc != OR_OK) break;
+    double P = (double)leak[S] * ls;
+    El += P * (double)(T->window_ps - t_prev) * 1e-6;
+    bin_add_interval(&B, P, t_prev, T->window_ps);
+    if (e_leak) e_leak[gi] = El;
+    if (e_int) e_int[gi] = Ei;
+    if (e_sw) e_sw[gi] = Es;
+    if (n_events) n_events[gi] = b - a;
+    if (final_state) final_state[gi] = (uint8_t)S;
+  }
+  free(tab_base);
+  free(leak_base);
+  return rc;
+}
+
+/* ---------------------------------------------------------------- adjoint */
+
+/*
+ * Gradient of a loss L(P) of the power waveform P_b = E_b * 1e-3 / bin_ps
+ * (W), given dLdP[b], with respect to each gate's load C (dC), each cell's
+ * energy scale (d_escale) and leakage scale (d_lscale).  FP64, by the chain
+ * rule through the same definition as oracle_walk:
+ *   dE_int/dC = escale * d(bilinear)/d(load)   (located load segment)
+ *   dE_sw/dC  = 0.5 * Vdd^2
+ *   dE_int/d escale = bilinear value;  leakage energy is linear in lscale.
+ */
+int oracle_adjoint(const oracle_lib* L, const oracle_net* N, const oracle_trace* T, int64_t bin_ps,
+                   const double* dLdP, double* dC, double* d_escale, double* d_lscale) {
+  if (bin_ps <= 0 || T->window_ps <= 0 || T->window_ps % bin_ps != 0) return OR_EINVAL;
+  int64_t* tab_base = (int64_t*)malloc(sizeof(int64_t) * (size_t)L->n_cells);
+  int64_t* leak_base = (int64_t*)malloc(sizeof(int64_t) * (size_t)L->n_cells);
+  cell_bases(L, tab_base, leak_base);
+  double per_fj = 1e-3 / (double)bin_ps;     /* dP_b / dE_b */
+  double half_v2 = 0.5 * L->vdd * L->vdd;
+  for (int32_t c = 0; c < L->n_cells; ++c) { d_escale[c] = 0.0; d_lscale[c] = 0.0; }
+  for (int64_t g = 0; g < N->n_gates; ++g) {
+    int32_t c = N->cell[g];
+    int32_t n_in = L->n_in[c];
+    double C = N->load_ff[g];
+    double es = L->escale[c];
+    const float* leak = L->p_leak + leak_base[c];
+    uint32_t S = T->init_state[g];
+    int64_t t_prev = 0;
+    double gC = 0.0;
+    int64_t a = T->offsets[g], b = T->offsets[g + 1];
+    int64_t i = a;
+    for (;;) {
+      int64_t t = (i < b) ? (int32_t)T->records[2 * i] : T->window_ps;
+      /* leakage interval [t_prev, t) at state S: dL/dlscale += P0 * sum_b dL/dE_b * overlap */
+      double P0 = leak[S];
+      if (t > t_prev) {
+        int64_t k0 = t_prev / bin_ps, k1 = (t - 1) / bin_ps;
+        for (int64_t k = k0; k <= k1; ++k) {
+          int64_t lo = t_prev > k * bin_ps ? t_prev : k * bin_ps;
+          int64_t hi = t < (k + 1) * bin_ps ? t : (k + 1) * bin_ps;
+          d_lscale[c] += P0 * (double)(hi - lo) * 1e-6 * dLdP[k] * per_fj;
+        }
+      }
+      if (i >= b) break;
+      int64_t j = i;
+      while (j < b && (int32_t)T->records[2 * j] == t) ++j;
+      double gb = dLdP[t / bin_ps] * per_fj;
+      uint32_t S_next = S;
+      for (int64_t e = i; e < j; ++e) {
+        uint32_t meta = T->records[2 * e + 1];
+        int32_t pin = (int32_t)(meta & 0xFu);
+        int32_t value = (int32_t)((meta >> 4) & 1u);
+        S_next ^= 1u << pin;
+        if (pin < n_in) {
+          const float* tab = table_for(L, tab_base, c, pin, value, side_bits(S, pin, n_in));
+          double slew = N->slew_ps[((int64_t)g * N->slew_stride + pin) * 2 + value];
+          double B0 = oracle_bilinear(L->n_slew, L->slew_axis, L->n_load, L->load_axis, tab, slew, C);
+          double dB = oracle_bilinear_dload(L->n_slew, L->slew_axis, L->n_load, L->load_axis, tab, slew, C);
+          gC += gb * es * dB;
+          d_escale[c] += gb * B0;
+        } else {
+          gC += gb * half_v2;
+        }
+      }
+      S = S_next;
+      t_prev = t;
+      i = j;
+    }
+    dC[g] = gC;
+  }
+  free(tab_base);
+  free(leak_base);
+  return OR_OK;
+}
