@@ -1,0 +1,369 @@
+"""Benchmark of the GB300 power-walk engine.
+
+One step = one pass of the whole hot path over one stimulus window with its
+inputs resident in HBM: gtp_load_events (device records used in place, CSR
+check), gtp_run_power (gate pass, segment seeds, fused walk, FP64 merge into
+the waveform) and gtp_gate_energy (per-gate results to device buffers).
+
+Default workload: 1M gates, 200M events (1.6 GB of 8-byte records), Zipf 1.2
+per-gate counts capped at 1e5, 10 us window, 10 ps bins (1M bins).  The
+records (1.6 GB) are larger than L2 (129 MB), so no L2 flush is needed
+between steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload instead.
+
+Multi-GPU (torchrun): every rank runs its own stimulus window (seeded per
+rank) on its own GPU, with no collective on the data path (weak scaling);
+the only collectives are the barrier and the max-over-ranks of the timings.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "events/sec and % of HBM roofline; batched and adjoint vs plain kernel"
+UNIT = "events/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--config", default="large")
+    p.add_argument("--e2e-steps", type=int, default=10)
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-clocks", action="store_true")
+    return p.parse_args()
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl"
+        try:
+            import torch
+            if not torch.cuda.is_available():
+                backend = "gloo"
+            else:
+                torch.cuda.set_device(local)
+        except Exception:
+            backend = "gloo"
+        dist.init_process_group(backend)
+        pg = dist
+    return ws, rank, local, pg
+
+
+def max_over_ranks(pg, x: float) -> float:
+    if pg is None:
+        return x
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device()) if torch.cuda.is_available() else torch.device("cpu")
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def workload_desc(cfg, n_bins):
+    cap = f", cap {cfg.cap:g}" if cfg.cap else ""
+    return (f"{cfg.name}: {cfg.n_gates:,} gates, {cfg.n_events:,} events, Zipf {cfg.zipf_s}{cap}, "
+            f"{cfg.window_ps / 1e6:g} us window, {cfg.bin_ps} ps bins ({n_bins:,} bins)")
+
+
+def algorithmic_bytes(n_events, n_gates_active, n_gates, n_bins):
+    """Bytes the walk must move: 8 per record read; per gate with events the
+    cell id, load, 6 slews, CSR offset and initial state read (41 B) and three
+    FP64 energies plus the final state written (25 B); 8 per bin (the
+    {energy, leakage step} accumulator pair)."""
+    return 8 * n_events + 66 * n_gates_active + 8 * n_bins
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self, gpu_index: int, enabled: bool):
+        self.enabled = enabled
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        if not self.enabled:
+            return self
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.enabled or self.path is None:
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), float(parts[2]), parts[3:]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for n, v in zip(names, r[3][1:]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def oracle_sample(lib, net, counts, cfg, seed_ev, budget_s, rng_seed=0):
+    """Time the FP64 oracle on randomly chosen gates of the workload (their
+    events regenerated on the host) until ``budget_s`` seconds of CPU work."""
+    import oracle
+    import synth
+
+    rng = np.random.default_rng(rng_seed)
+    order = rng.permutation(cfg.n_gates)
+    trace = synth.make_trace(net, counts, cfg.window_ps, seed_ev, cfg.tie_p, materialise=False)
+    done_ev, done_g, spent = 0, 0, 0.0
+    pos = 0
+    chunk = 16
+    while spent < budget_s and pos < len(order):
+        gates = np.sort(order[pos:pos + chunk])
+        pos += chunk
+        off, rec = synth.gate_records(net, trace, gates)
+        sub_net = synth.Netlist(net.cell[gates], net.load_ff[gates], np.ascontiguousarray(net.slew_ps[gates]),
+                                net.n_pins[gates], net.level[gates], net.fanin[gates])
+        sub_tr = synth.Trace(cfg.window_ps, off, rec, trace.init_state[gates], trace.seed, trace.tie24)
+        t0 = time.perf_counter()
+        oracle.walk(lib, sub_net, sub_tr, cfg.bin_ps)
+        spent += time.perf_counter() - t0
+        done_ev += int(off[-1])
+        done_g += len(gates)
+    return done_ev, done_g, spent
+
+
+def run_reference(args, cfg_name):
+    import synth
+    ws, rank, local, pg = dist_init()
+    if rank != 0:
+        return
+    cfg = synth.CONFIGS[cfg_name]
+    lib = synth.make_library(cfg.seed_lib)
+    net = synth.make_netlist(lib, cfg.n_gates, cfg.seed_net)
+    counts = synth.zipf_counts(cfg.n_gates, cfg.n_events, cfg.zipf_s, cfg.cap, cfg.seed_ev)
+    n_bins = cfg.window_ps // cfg.bin_ps
+    total = args.steps + args.warmup
+    per_step = max(0.05, min(args.cpu_seconds, 150.0 / max(total, 1)))
+    ev_tot, g_tot, t_tot = 0, 0, 0.0
+    for i in range(total):
+        ev, g, t = oracle_sample(lib, net, counts, cfg, cfg.seed_ev, per_step, rng_seed=i)
+        if i >= args.warmup:
+            ev_tot, g_tot, t_tot = ev_tot + ev, g_tot + g, t_tot + t
+    value = ev_tot / t_tot if t_tot > 0 else 0.0
+    sample = (f"FP64 oracle, single thread, on {g_tot:,} randomly chosen gates ({ev_tot:,} events, all "
+              f"{n_bins:,} bins) over {args.steps} steps of ~{per_step:.2f} s")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / max(args.steps, 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": workload_desc(cfg, n_bins), "gates": cfg.n_gates, "events": cfg.n_events,
+                      "bins": n_bins},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ our engine
+def run_ours(args, cfg_name):
+    import torch
+
+    import synth
+    from paper_2609_05960_gb300 import Engine, gtpower
+
+    ws, rank, local, pg = dist_init()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    cfg = synth.CONFIGS[cfg_name]
+    seed_ev = cfg.seed_ev + 1000 * rank
+    lib = synth.make_library(cfg.seed_lib)
+    net = synth.make_netlist(lib, cfg.n_gates, cfg.seed_net)
+    counts = synth.zipf_counts(cfg.n_gates, cfg.n_events, cfg.zipf_s, cfg.cap, seed_ev)
+    trace, rec = synth.make_trace_gpu(net, counts, cfg.window_ps, seed_ev, cfg.tie_p, device=dev)
+    n_ev = trace.n_events
+    n_bins = cfg.window_ps // cfg.bin_ps
+    G = cfg.n_gates
+    n_active = int((counts > 0).sum())
+
+    eng = Engine(local)
+    eng.load_library(lib)
+    eng.load_netlist(net)
+    ctx = eng.ctx
+    off_d = torch.from_numpy(trace.offsets).to(dev)
+    init_d = torch.from_numpy(trace.init_state).to(dev)
+    wave = torch.empty(n_bins, dtype=torch.float64, device=dev)
+    g_leak = torch.empty(G, dtype=torch.float64, device=dev)
+    g_int = torch.empty_like(g_leak)
+    g_sw = torch.empty_like(g_leak)
+    g_cnt = torch.empty(G, dtype=torch.int64, device=dev)
+    g_fin = torch.empty(G, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        gtpower.gtp_load_events(ctx, 0, cfg.window_ps, off_d, rec, init_d, borrow=True)
+        gtpower.gtp_run_power(ctx, 0, cfg.bin_ps, wave)
+        gtpower.gtp_gate_energy(ctx, 0, g_leak, g_int, g_sw, g_cnt, g_fin)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    eng.set_param("timing", 1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local, not args.no_clocks) as clk:
+        barrier(pg)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(pg)
+    ms = e0.elapsed_time(e1)
+    clocks = clk.summary()
+    n_timed = max(eng.get_param("n_timed"), 1)
+    walk_s = eng.get_param("t_walk_ns") * 1e-9 / n_timed
+    seeds_s = eng.get_param("t_seeds_ns") * 1e-9 / n_timed
+    merge_s = eng.get_param("t_merge_ns") * 1e-9 / n_timed
+    gate_s = eng.get_param("t_gate_pass_ns") * 1e-9 / n_timed
+    launches = eng.get_param("launches")
+    eng.set_param("timing", 0)
+    ms_max = max_over_ranks(pg, ms)
+    value = ws * args.steps * n_ev / (ms_max * 1e-3)
+
+    import json as _json
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = _json.load(open(pk_path))
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    alg = algorithmic_bytes(n_ev, n_active, G, n_bins)
+    achieved = alg / walk_s / 1e9 if walk_s > 0 else 0.0
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        rec_h = torch.empty((n_ev, 2), dtype=torch.int32, pin_memory=True)
+        rec_h.copy_(rec)
+        off_h = trace.offsets
+        init_h = trace.init_state
+        wave_h = torch.empty(n_bins, dtype=torch.float64, pin_memory=True)
+        outs_h = [torch.empty(G, dtype=torch.float64, pin_memory=True) for _ in range(3)]
+        cnt_h = torch.empty(G, dtype=torch.int64, pin_memory=True)
+        fin_h = torch.empty(G, dtype=torch.uint8, pin_memory=True)
+
+        def e2e_step():
+            gtpower.gtp_load_events(ctx, 1, cfg.window_ps, off_h, rec_h, init_h)
+            gtpower.gtp_run_power(ctx, 1, cfg.bin_ps, wave_h)
+            gtpower.gtp_gate_energy(ctx, 1, outs_h[0], outs_h[1], outs_h[2], cnt_h, fin_h)
+
+        e2e_step()
+        torch.cuda.synchronize(dev)
+        barrier(pg)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        t_e2e = max_over_ranks(pg, time.perf_counter() - t0)
+        h2d = rec_h.numel() * 4 + off_h.nbytes + init_h.nbytes
+        d2h = n_bins * 8 + G * (8 * 3 + 8 + 1)
+        e2e = {"value": ws * args.e2e_steps * n_ev / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * t_e2e / args.e2e_steps}
+        del rec_h
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        ev, g, t = oracle_sample(lib, net, counts, cfg, seed_ev, args.cpu_seconds)
+        cpu = {"value": ev / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"FP64 oracle, single thread, on {g:,} randomly chosen gates of this workload "
+                         f"({ev:,} events, all {n_bins:,} bins), {t:.1f} s"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_desc(cfg, n_bins), "gates": G, "events": n_ev, "bins": n_bins,
+                       "records_bytes": 8 * n_ev, "l2_flush": "none: inputs (records) larger than L2",
+                       "kernel": "segmented warp walk", "records_per_thread": eng.get_param("records_per_thread"),
+                       "block_threads": eng.get_param("block_threads")},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_segwalk",
+                         "algorithmic_bytes": alg, "walk_ms": walk_s * 1e3, "peak_source": peak_src},
+            "phases_ms": {"gate_pass": gate_s * 1e3, "seeds": seeds_s * 1e3, "walk": walk_s * 1e3,
+                          "merge": merge_s * 1e3},
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        print(json.dumps(out), flush=True)
+    eng.close()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args, args.config)
+    else:
+        run_ours(args, args.config)
+
+
+if __name__ == "__main__":
+    main()

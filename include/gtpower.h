@@ -1,0 +1,210 @@
+/*
+ * gtpower.h - C ABI of the GB300 engine for gate-level time-based power
+ * analysis (event-driven power walk of arxiv 2609.05960, "GPU-Accelerated
+ * Gate-Level Time-Based Power Analysis via Event-Density-Aware Partitioning
+ * and Kernel Fusion").
+ *
+ * The engine walks each gate's time-ordered events, tracks the gate state,
+ * looks up state-dependent internal energy (bilinear NLDM interpolation),
+ * adds output switching energy and state-dependent leakage between events,
+ * and accumulates everything into a per-time-bin power waveform and per-gate
+ * energies.
+ *
+ * Conventions for every entry point:
+ *   - Return value: GTP_OK (0) or a negative GTP_E* code; gtp_last_error()
+ *     returns a message for the last failure on that context.  No C++
+ *     exception crosses this boundary.
+ *   - Units: time in ps (int32 timestamps), load in fF, slew in ps, supply in
+ *     V, energy in fJ, leakage power in nW, waveform power in W.
+ *   - Ownership: input arrays are copied unless GTP_BORROW is given; the
+ *     caller may free them on return.  Outputs go into caller buffers on the
+ *     host (GTP_HOST) or the device (GTP_DEVICE) as flagged.
+ *   - Streams: all device work is enqueued on the context's stream.  Calls
+ *     that return results or validation status synchronise that stream.
+ *   - A context is bound to one device and is not thread-safe.
+ */
+#ifndef GTPOWER_H
+#define GTPOWER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define GTP_OK 0
+#define GTP_EINVAL (-1)     /* bad argument (NULL, size, flag, call order) */
+#define GTP_EORDER (-2)     /* timestamps decrease within a gate */
+#define GTP_ERANGE (-3)     /* t outside [0, window_ps), pin >= pins of the cell,
+                               reserved meta bits set, window_ps % bin_ps != 0,
+                               or a size beyond an engine limit */
+#define GTP_ENOTOGGLE (-4)  /* an event sets a pin to the value it already has */
+#define GTP_ENOMEM (-5)     /* device or host allocation failed */
+#define GTP_ECUDA (-6)      /* a CUDA runtime call failed */
+#define GTP_ETIMEOUT (-7)   /* a bounded device wait expired */
+#define GTP_EDEVICE (-8)    /* a kernel reported an internal inconsistency */
+
+/* ---- memory-space flags ---------------------------------------------- */
+#define GTP_HOST 0          /* pointer is host memory */
+#define GTP_DEVICE 1        /* pointer is device memory of the context's device */
+#define GTP_BORROW 2        /* gtp_load_events only, with GTP_DEVICE: use the
+                               caller's event buffer in place (no copy); it must
+                               stay valid and unchanged while the window is used
+                               and be 16-byte aligned */
+
+/* Limits of this engine: at most 7 input pins per cell (8 pins, so the gate
+ * state fits in one byte), at most 16 points per interpolation axis, and
+ * library tables that fit in one SM's shared memory (GTP_MAX_TABLE_BYTES). */
+#define GTP_MAX_PINS 8
+#define GTP_MAX_AXIS 16
+#define GTP_MAX_TABLE_BYTES (160 * 1024)
+
+/* One event record, 8 bytes.  An event is a (value, timestamp) pair on one
+ * pin: the pin switches to `value` at t_ps (Sec. 2.1).
+ *   t_ps: timestamp in ps, 0 <= t_ps < window_ps
+ *   meta: bits [0,4) gate-local pin (inputs 0..n_in-1, output = n_in),
+ *         bit 4 the new value, bits [5,32) reserved and must be 0. */
+typedef struct gtp_event {
+  int32_t t_ps;
+  uint32_t meta;
+} gtp_event;
+
+typedef struct gtp_ctx gtp_ctx;
+
+/* Create a context on CUDA device `device`, enqueueing on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * context, or NULL on failure. */
+int gtp_create(gtp_ctx** out, int device, void* cuda_stream);
+
+/* Free every device buffer the context owns, then the context. */
+void gtp_destroy(gtp_ctx* ctx);
+
+/* Change the stream later calls enqueue on. */
+int gtp_set_stream(gtp_ctx* ctx, void* cuda_stream);
+
+/* Message describing the last failure on ctx ("" if none).  Valid until the
+ * next call on ctx. */
+const char* gtp_last_error(const gtp_ctx* ctx);
+
+/*
+ * Load the cell library (host arrays).  Internal power is state dependent
+ * (Sec. 2.2): each (cell, input pin, edge, side-input state) has its own
+ * NLDM table, and the state is binary-encoded into a table index in pin
+ * order (state-indexed lookup, Sec. 4.1).
+ *   n_in[c]      input pins of cell c (1..7); the output pin is pin n_in[c]
+ *   vdd          supply voltage (V)
+ *   slew_axis    n_slew increasing input-slew knots (ps)
+ *   load_axis    n_load increasing output-load knots (fF)
+ *   e_int        n_e_int floats: cell-major; cell c holds n_in[c] pins x 2
+ *                edges (0 fall, 1 rise) x 2^(n_in[c]-1) side states (the
+ *                other input pins' bits, compacted in pin order) x
+ *                n_slew x n_load (slew-major) internal energies in fJ
+ *   p_leak       n_p_leak floats: cell-major; cell c holds 2^(n_in[c]+1)
+ *                leakage powers in nW indexed by the full pin state
+ *                (bit p = value of pin p, output included)
+ * Errors: GTP_EINVAL on inconsistent sizes, GTP_ERANGE beyond the limits.
+ * Loading a library invalidates loaded netlists and windows.
+ */
+int gtp_load_library(gtp_ctx* ctx, int32_t n_cells, const int32_t* n_in, float vdd,
+                     int32_t n_slew, const float* slew_axis, int32_t n_load, const float* load_axis,
+                     const float* e_int, int64_t n_e_int, const float* p_leak, int64_t n_p_leak);
+
+/*
+ * Per-cell multipliers on internal energy and on leakage power (host arrays
+ * of n_cells; NULL leaves that scale at 1).  They are the parameters the
+ * adjoint differentiates.
+ */
+int gtp_set_scales(gtp_ctx* ctx, const float* escale, const float* lscale);
+
+/*
+ * Load the netlist: per gate its cell, output load C (fF; the total load of
+ * the switching-energy equation, Sec. 2.4.1) and input slews (ps) per
+ * (input pin, edge), as static timing provides them (Sec. 2.3).
+ *   cell      [n_gates] int32 in [0, n_cells)
+ *   load_ff   [n_gates] float
+ *   slew_ps   [n_gates][slew_stride][2] float, slew_stride >= max n_in
+ * flags: GTP_HOST or GTP_DEVICE for all three arrays.  Connectivity is not
+ * needed by the walk.  Invalidates loaded windows.
+ */
+int gtp_load_netlist(gtp_ctx* ctx, int64_t n_gates, const int32_t* cell, const float* load_ff,
+                     const float* slew_ps, int32_t slew_stride, int flags);
+
+/* Replace every gate's output load (fF) without reloading the netlist
+ * (e.g. inside an optimisation loop driven by the adjoint). */
+int gtp_set_load(gtp_ctx* ctx, const float* load_ff, int flags);
+
+/*
+ * Load one stimulus window's events as slot `window` (0 <= window < 1024;
+ * reloading a slot replaces it).
+ *   window_ps     length of the analysis window, > 0, < 2^31
+ *   n_events      number of records (may be 0)
+ *   gate_offsets  [n_gates+1] int64 CSR offsets: gate g's records are
+ *                 events[gate_offsets[g] .. gate_offsets[g+1]), time-ordered
+ *                 (ties allowed: events sharing a timestamp form one group)
+ *   events        [n_events] records
+ *   init_state    [n_gates] state of every gate at t = 0 (bit p = pin p)
+ * flags: GTP_HOST, GTP_DEVICE, or GTP_DEVICE|GTP_BORROW (events only).
+ * The CSR structure is checked here (GTP_EINVAL); timestamps, pins and
+ * toggles are checked by the walk and reported by gtp_run_power.
+ */
+int gtp_load_events(gtp_ctx* ctx, int32_t window, int64_t window_ps, int64_t n_events,
+                    const int64_t* gate_offsets, const gtp_event* events, const uint8_t* init_state,
+                    int flags);
+
+/*
+ * Run the power walk of one window with bins of bin_ps ps
+ * (n_bins = window_ps / bin_ps; window_ps % bin_ps must be 0).
+ * Writes waveform_w[n_bins] (FP64, W): the mean power of each bin, i.e. the
+ * energy of all events in the bin (dynamic energy goes to the bin holding the
+ * event time; a time on a bin boundary belongs to the later bin) plus the
+ * leakage energy overlapping the bin, divided by bin_ps.  Per-gate results are
+ * kept for gtp_gate_energy.  Synchronous; returns GTP_EORDER / GTP_ERANGE /
+ * GTP_ENOTOGGLE if the trace is malformed (results are then undefined).
+ * waveform_w may be NULL to compute per-gate results only.
+ * flags: GTP_HOST or GTP_DEVICE for waveform_w.
+ */
+int gtp_run_power(gtp_ctx* ctx, int32_t window, int32_t bin_ps, double* waveform_w, int flags);
+
+/*
+ * Per-gate results of the last gtp_run_power / batched run of `window`:
+ * leakage, internal and switching energy (fJ, FP64), event count and the
+ * state after the last event.  Any pointer may be NULL.
+ * flags: GTP_HOST or GTP_DEVICE for all outputs.
+ */
+int gtp_gate_energy(gtp_ctx* ctx, int32_t window, double* e_leak, double* e_int, double* e_sw,
+                    int64_t* n_events, uint8_t* final_state, int flags);
+
+/*
+ * Run n_windows loaded windows over the same netlist in one persistent
+ * launch (windows[i] names the slot; waveforms[i] receives window i's
+ * waveform, same layout as gtp_run_power).  flags: GTP_HOST or GTP_DEVICE
+ * for the waveform buffers (the pointer array itself is host memory).
+ */
+int gtp_run_power_batched(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_t bin_ps,
+                          double* const* waveforms, int flags);
+
+/*
+ * Adjoint of gtp_run_power for one window: given dL_dP[n_bins] (device,
+ * FP32, the gradient of a scalar loss with respect to each bin's power in W),
+ * write the gradients with respect to every gate's load (dC[n_gates]) and
+ * every cell's energy and leakage scale (d_escale[n_cells],
+ * d_lscale[n_cells]), all FP32 device buffers; any output may be NULL.
+ * The internal-energy derivative in the load is the slope of the located
+ * load segment of the bilinear table (right derivative on a knot);
+ * d(0.5*C*Vdd^2)/dC = 0.5*Vdd^2.
+ */
+int gtp_run_power_backward(gtp_ctx* ctx, int32_t window, int32_t bin_ps, const float* dL_dP, float* dC,
+                           float* d_escale, float* d_lscale);
+
+/* Engine tuning knobs (see the engine documentation); value < 0 restores
+ * the default.  Keys: "records_per_thread", "block_threads", "ctas_per_sm",
+ * "kernel" (0 = segmented warp walk, 1 = one thread per gate). */
+int gtp_set_param(gtp_ctx* ctx, const char* key, int64_t value);
+int64_t gtp_get_param(const gtp_ctx* ctx, const char* key);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GTPOWER_H */

@@ -1,0 +1,287 @@
+"""Python binding of the C ABI in ``include/gtpower.h`` (ctypes).
+
+Argument marshalling only: every step of the power walk runs in the CUDA
+library ``libgtpower.so``.  Functions carry the C names; ``Engine`` bundles
+them for convenience.  PyTorch provides device memory and streams.  If the
+library is missing the binding raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgtpower.so")
+
+GTP_OK, GTP_EINVAL, GTP_EORDER, GTP_ERANGE, GTP_ENOTOGGLE = 0, -1, -2, -3, -4
+GTP_ENOMEM, GTP_ECUDA, GTP_ETIMEOUT, GTP_EDEVICE = -5, -6, -7, -8
+GTP_HOST, GTP_DEVICE, GTP_BORROW = 0, 1, 2
+
+CODE_NAMES = {GTP_EINVAL: "EINVAL", GTP_EORDER: "EORDER", GTP_ERANGE: "ERANGE", GTP_ENOTOGGLE: "ENOTOGGLE",
+              GTP_ENOMEM: "ENOMEM", GTP_ECUDA: "ECUDA", GTP_ETIMEOUT: "ETIMEOUT", GTP_EDEVICE: "EDEVICE"}
+
+# every entry point the header declares
+ABI_SYMBOLS = ["gtp_create", "gtp_destroy", "gtp_set_stream", "gtp_last_error", "gtp_load_library",
+               "gtp_set_scales", "gtp_load_netlist", "gtp_set_load", "gtp_load_events", "gtp_run_power",
+               "gtp_gate_energy", "gtp_run_power_batched", "gtp_run_power_backward", "gtp_set_param",
+               "gtp_get_param"]
+
+
+class GtpError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{CODE_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libgtpower.so and declare the ABI signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() (no CPU fallback exists)")
+    L = ctypes.CDLL(path)
+    P, I32, I64, F = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+    sig = {
+        "gtp_create": ([ctypes.POINTER(P), ctypes.c_int, P], ctypes.c_int),
+        "gtp_destroy": ([P], None),
+        "gtp_set_stream": ([P, P], ctypes.c_int),
+        "gtp_last_error": ([P], ctypes.c_char_p),
+        "gtp_load_library": ([P, I32, P, F, I32, P, I32, P, P, I64, P, I64], ctypes.c_int),
+        "gtp_set_scales": ([P, P, P], ctypes.c_int),
+        "gtp_load_netlist": ([P, I64, P, P, P, I32, ctypes.c_int], ctypes.c_int),
+        "gtp_set_load": ([P, P, ctypes.c_int], ctypes.c_int),
+        "gtp_load_events": ([P, I32, I64, I64, P, P, P, ctypes.c_int], ctypes.c_int),
+        "gtp_run_power": ([P, I32, I32, P, ctypes.c_int], ctypes.c_int),
+        "gtp_gate_energy": ([P, I32, P, P, P, P, P, ctypes.c_int], ctypes.c_int),
+        "gtp_run_power_batched": ([P, I32, P, I32, P, ctypes.c_int], ctypes.c_int),
+        "gtp_run_power_backward": ([P, I32, I32, P, P, P, P], ctypes.c_int),
+        "gtp_set_param": ([P, ctypes.c_char_p, I64], ctypes.c_int),
+        "gtp_get_param": ([P, ctypes.c_char_p], I64),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+# ------------------------------------------------------------------ marshalling helpers
+def _ptr_flags(a, dtype):
+    """(pointer, flags, keepalive) for a numpy array or torch tensor."""
+    if a is None:
+        return None, GTP_HOST, None
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            want = {np.float32: torch.float32, np.float64: torch.float64, np.int32: torch.int32,
+                    np.int64: torch.int64, np.uint8: torch.uint8, np.uint32: torch.int32}[dtype]
+            if a.dtype != want or not a.is_contiguous():
+                raise TypeError(f"tensor must be contiguous {want}, got {a.dtype}")
+            return a.data_ptr(), (GTP_DEVICE if a.is_cuda else GTP_HOST), a
+    except ImportError:
+        pass
+    arr = np.ascontiguousarray(np.asarray(a), dtype=dtype)
+    return arr.ctypes.data, GTP_HOST, arr
+
+
+def _check(ctx, rc: int):
+    if rc != GTP_OK:
+        msg = gtp_last_error(ctx) if ctx else ""
+        raise GtpError(rc, msg)
+
+
+# ------------------------------------------------------------------ ABI-named functions
+def gtp_create(device: int = 0, stream: Optional[int] = None):
+    h = ctypes.c_void_p()
+    rc = load().gtp_create(ctypes.byref(h), int(device), stream)
+    if rc != GTP_OK:
+        raise GtpError(rc, f"gtp_create failed on device {device}")
+    return h
+
+
+def gtp_destroy(ctx) -> None:
+    load().gtp_destroy(ctx)
+
+
+def gtp_set_stream(ctx, stream: Optional[int]) -> None:
+    _check(ctx, load().gtp_set_stream(ctx, stream))
+
+
+def gtp_last_error(ctx) -> str:
+    r = load().gtp_last_error(ctx)
+    return r.decode() if r else ""
+
+
+def gtp_load_library(ctx, n_in, vdd, slew_axis, load_axis, e_int, p_leak) -> None:
+    ni = np.ascontiguousarray(n_in, np.int32)
+    sa = np.ascontiguousarray(slew_axis, np.float32)
+    la = np.ascontiguousarray(load_axis, np.float32)
+    ei = np.ascontiguousarray(e_int, np.float32)
+    pl = np.ascontiguousarray(p_leak, np.float32)
+    _check(ctx, load().gtp_load_library(ctx, len(ni), ni.ctypes.data, float(vdd), len(sa), sa.ctypes.data, len(la),
+                                        la.ctypes.data, ei.ctypes.data, ei.size, pl.ctypes.data, pl.size))
+
+
+def gtp_set_scales(ctx, escale=None, lscale=None) -> None:
+    e = None if escale is None else np.ascontiguousarray(escale, np.float32)
+    l = None if lscale is None else np.ascontiguousarray(lscale, np.float32)
+    _check(ctx, load().gtp_set_scales(ctx, None if e is None else e.ctypes.data, None if l is None else l.ctypes.data))
+
+
+def gtp_load_netlist(ctx, cell, load_ff, slew_ps) -> None:
+    pc, fc, kc = _ptr_flags(cell, np.int32)
+    pl, fl, kl = _ptr_flags(load_ff, np.float32)
+    ps, fs, ks = _ptr_flags(slew_ps, np.float32)
+    if not (fc == fl == fs):
+        raise ValueError("netlist arrays must all be host or all be device")
+    n = len(cell)
+    stride = int(slew_ps.shape[1]) if len(slew_ps.shape) == 3 else int(np.asarray(slew_ps).size // (2 * n))
+    _check(ctx, load().gtp_load_netlist(ctx, n, pc, pl, ps, stride, fc))
+
+
+def gtp_set_load(ctx, load_ff) -> None:
+    p, f, k = _ptr_flags(load_ff, np.float32)
+    _check(ctx, load().gtp_set_load(ctx, p, f))
+
+
+def gtp_load_events(ctx, window: int, window_ps: int, gate_offsets, events, init_state, borrow: bool = False) -> None:
+    po, fo, ko = _ptr_flags(gate_offsets, np.int64)
+    pe, fe, ke = _ptr_flags(events, np.uint32)
+    pi, fi, ki = _ptr_flags(init_state, np.uint8)
+    if not (fo == fe == fi):
+        raise ValueError("event arrays must all be host or all be device")
+    n_events = int(events.shape[0]) if events is not None else 0
+    flags = fo | (GTP_BORROW if borrow else 0)
+    _check(ctx, load().gtp_load_events(ctx, int(window), int(window_ps), n_events, po, pe, pi, flags))
+
+
+def gtp_run_power(ctx, window: int, bin_ps: int, waveform=None) -> None:
+    p, f, k = _ptr_flags(waveform, np.float64)
+    _check(ctx, load().gtp_run_power(ctx, int(window), int(bin_ps), p, f))
+
+
+def gtp_gate_energy(ctx, window: int, e_leak=None, e_int=None, e_sw=None, n_events=None, final_state=None) -> None:
+    args = [_ptr_flags(e_leak, np.float64), _ptr_flags(e_int, np.float64), _ptr_flags(e_sw, np.float64),
+            _ptr_flags(n_events, np.int64), _ptr_flags(final_state, np.uint8)]
+    flags = {a[1] for a in args if a[0] is not None}
+    if len(flags) > 1:
+        raise ValueError("outputs must all be host or all be device")
+    f = flags.pop() if flags else GTP_HOST
+    _check(ctx, load().gtp_gate_energy(ctx, int(window), *[a[0] for a in args], f))
+
+
+def gtp_run_power_batched(ctx, windows: Sequence[int], bin_ps: int, waveforms: Sequence) -> None:
+    w = np.ascontiguousarray(windows, np.int32)
+    ptrs = [_ptr_flags(x, np.float64) for x in waveforms]
+    flags = {p[1] for p in ptrs if p[0] is not None}
+    if len(flags) > 1:
+        raise ValueError("waveforms must all be host or all be device")
+    f = flags.pop() if flags else GTP_HOST
+    arr = (ctypes.c_void_p * len(ptrs))(*[p[0] for p in ptrs])
+    _check(ctx, load().gtp_run_power_batched(ctx, len(w), w.ctypes.data, int(bin_ps), ctypes.cast(arr, ctypes.c_void_p), f))
+
+
+def gtp_run_power_backward(ctx, window: int, bin_ps: int, dL_dP, dC=None, d_escale=None, d_lscale=None) -> None:
+    ptr = lambda t: None if t is None else t.data_ptr()  # device tensors
+    _check(ctx, load().gtp_run_power_backward(ctx, int(window), int(bin_ps), ptr(dL_dP), ptr(dC), ptr(d_escale),
+                                              ptr(d_lscale)))
+
+
+def gtp_set_param(ctx, key: str, value: int) -> None:
+    _check(ctx, load().gtp_set_param(ctx, key.encode(), int(value)))
+
+
+def gtp_get_param(ctx, key: str) -> int:
+    return int(load().gtp_get_param(ctx, key.encode()))
+
+
+# ------------------------------------------------------------------ convenience object
+class Engine:
+    """One context on one GPU, enqueueing on torch's current stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self.device = torch.device("cuda", device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        self.ctx = gtp_create(device, stream.cuda_stream)
+        self.n_gates = 0
+        self.n_cells = 0
+        self.windows: Dict[int, dict] = {}
+
+    def close(self):
+        if self.ctx:
+            gtp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_library(self, lib) -> None:
+        gtp_load_library(self.ctx, lib.n_in, lib.vdd, lib.slew_axis, lib.load_axis, lib.e_int, lib.p_leak)
+        self.n_cells = len(lib.n_in)
+
+    def set_scales(self, escale=None, lscale=None) -> None:
+        gtp_set_scales(self.ctx, escale, lscale)
+
+    def load_netlist(self, net) -> None:
+        gtp_load_netlist(self.ctx, net.cell, net.load_ff, net.slew_ps)
+        self.n_gates = len(net.cell)
+
+    def set_load(self, load_ff) -> None:
+        gtp_set_load(self.ctx, load_ff)
+
+    def load_events(self, window: int, trace=None, *, window_ps=None, offsets=None, records=None, init_state=None,
+                    borrow: bool = False) -> None:
+        if trace is not None:
+            window_ps, offsets, records, init_state = trace.window_ps, trace.offsets, trace.records, trace.init_state
+        gtp_load_events(self.ctx, window, window_ps, offsets, records, init_state, borrow=borrow)
+        self.windows[window] = dict(window_ps=int(window_ps))
+
+    def run_power(self, window: int, bin_ps: int, out=None):
+        """Waveform in W as a float64 CUDA tensor of window_ps / bin_ps bins."""
+        import torch
+        nb = self.windows[window]["window_ps"] // bin_ps
+        if out is None:
+            out = torch.empty(nb, dtype=torch.float64, device=self.device)
+        gtp_run_power(self.ctx, window, bin_ps, out)
+        return out
+
+    def gate_energy(self, window: int, device: bool = True):
+        import torch
+        G = self.n_gates
+        if device:
+            kw = dict(device=self.device)
+            r = dict(e_leak=torch.empty(G, dtype=torch.float64, **kw), e_int=torch.empty(G, dtype=torch.float64, **kw),
+                     e_sw=torch.empty(G, dtype=torch.float64, **kw), n_events=torch.empty(G, dtype=torch.int64, **kw),
+                     final_state=torch.empty(G, dtype=torch.uint8, **kw))
+        else:
+            r = dict(e_leak=np.empty(G), e_int=np.empty(G), e_sw=np.empty(G), n_events=np.empty(G, np.int64),
+                     final_state=np.empty(G, np.uint8))
+        gtp_gate_energy(self.ctx, window, r["e_leak"], r["e_int"], r["e_sw"], r["n_events"], r["final_state"])
+        return r
+
+    def run_power_batched(self, windows: Sequence[int], bin_ps: int):
+        import torch
+        outs = [torch.empty(self.windows[w]["window_ps"] // bin_ps, dtype=torch.float64, device=self.device)
+                for w in windows]
+        gtp_run_power_batched(self.ctx, windows, bin_ps, outs)
+        return outs
+
+    def set_param(self, key: str, value: int) -> None:
+        gtp_set_param(self.ctx, key, value)
+
+    def get_param(self, key: str) -> int:
+        return gtp_get_param(self.ctx, key)

@@ -1,0 +1,248 @@
+"""GPU engine vs the FP64 oracle, element by element, through the C ABI.
+
+Bar (spec accuracy): per-gate event counts and final states bit-exact;
+every waveform bin within 1e-5 relative of the oracle; per-gate energies
+within 1e-5 relative (absolute floor 1e-9 fJ for exact zeros)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from cases import and2_worked, netlist_from, single_cell_library, small_random, trace_from
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+KERNELS = [
+    dict(kernel=1),
+    dict(kernel=0, records_per_thread=4, block_threads=256),
+    dict(kernel=0, records_per_thread=8, block_threads=256),
+    dict(kernel=0, records_per_thread=16, block_threads=128),
+]
+KID = ["per_gate", "seg_k4", "seg_k8", "seg_k16"]
+
+
+@pytest.fixture(scope="module")
+def engine():
+    from paper_2609_05960_gb300 import Engine
+    e = Engine(0)
+    yield e
+    e.close()
+
+
+def run(engine, lib, net, tr, bin_ps, params=None, escale=None, lscale=None, window=0):
+    engine.load_library(lib)
+    engine.load_netlist(net)
+    for k in ("kernel", "records_per_thread", "block_threads", "ctas_per_sm"):
+        engine.set_param(k, -1)
+    for k, v in (params or {}).items():
+        engine.set_param(k, v)
+    if escale is not None or lscale is not None:
+        engine.set_scales(escale, lscale)
+    engine.load_events(window, tr)
+    w = engine.run_power(window, bin_ps).cpu().numpy()
+    ge = engine.gate_energy(window, device=False)
+    return w, ge
+
+
+def assert_matches(w, ge, ref, bin_ps, tol=TOL):
+    want = oracle.waveform_w(ref["bins"], bin_ps)
+    assert w.shape == want.shape
+    rel = np.abs(w - want) / np.abs(want)
+    assert rel.max() <= tol, f"bin {rel.argmax()}: got {w[rel.argmax()]}, want {want[rel.argmax()]}, rel {rel.max()}"
+    np.testing.assert_array_equal(ge["n_events"], ref["n_events"])
+    np.testing.assert_array_equal(ge["final_state"], ref["final_state"])
+    for k in ("e_leak", "e_int", "e_sw"):
+        err = np.abs(ge[k] - ref[k])
+        bad = err > tol * np.abs(ref[k]) + 1e-9
+        assert not bad.any(), f"{k}: gate {np.argmax(bad)} got {ge[k][np.argmax(bad)]} want {ref[k][np.argmax(bad)]}"
+
+
+@pytest.mark.parametrize("params", KERNELS, ids=KID)
+def test_hand_worked_example(engine, params):
+    fx, lib, net, tr = and2_worked()
+    w, ge = run(engine, lib, net, tr, fx["bin_ps"], params)
+    np.testing.assert_allclose(w, np.array(fx["expected"]["bins_fj"]) * 1e-3 / fx["bin_ps"], rtol=TOL)
+    assert ge["final_state"][0] == fx["expected"]["final_state"]
+    assert ge["n_events"][0] == fx["expected"]["n_events"]
+
+
+@pytest.mark.parametrize("params", KERNELS, ids=KID)
+def test_tiny_workload_matches_oracle(engine, params):
+    """2,000 gates, 200k events, Zipf 1.1, 1 us window, 100 ps bins."""
+    lib, net, tr = synth.make_inputs(synth.CONFIGS["tiny"])
+    w, ge = run(engine, lib, net, tr, 100, params)
+    assert_matches(w, ge, oracle.walk(lib, net, tr, 100), 100)
+
+
+@pytest.mark.parametrize("params", KERNELS, ids=KID)
+@pytest.mark.parametrize("tie_p", [0.05, 0.5, 0.95])
+def test_timestamp_ties(engine, params, tie_p):
+    lib, net, tr = small_random(n_gates=60, n_events=40_000, window_ps=400_000, seed=71, tie_p=tie_p)
+    w, ge = run(engine, lib, net, tr, 50, params)
+    assert_matches(w, ge, oracle.walk(lib, net, tr, 50), 50)
+
+
+@pytest.mark.parametrize("params", KERNELS, ids=KID)
+def test_one_dense_gate_across_many_segments(engine, params):
+    lib = synth.make_library(1)
+    net = synth.make_netlist(lib, 3, seed=5)
+    net.cell[:] = [3, 0, 11]  # NAND3, INV, MUX2
+    net.n_pins[:] = (lib.n_in[net.cell] + 1).astype(np.uint8)
+    tr = synth.make_trace(net, np.array([3, 70_001, 5]), 2_000_000, seed=9, tie_p=0.02)
+    w, ge = run(engine, lib, net, tr, 1000, params)
+    assert_matches(w, ge, oracle.walk(lib, net, tr, 1000), 1000)
+
+
+@pytest.mark.parametrize("params", KERNELS, ids=KID)
+@pytest.mark.parametrize("n_events", [0, 1, 255, 256, 257, 4097])
+def test_ragged_sizes_and_empty_gates(engine, params, n_events):
+    lib = synth.make_library(1)
+    net = synth.make_netlist(lib, 50, seed=13)
+    counts = np.zeros(50, np.int64)
+    if n_events:
+        counts[[3, 4, 17, 49]] = synth.zipf_counts(4, n_events, 1.0, None, 3)
+    tr = synth.make_trace(net, counts, 100_000, seed=21)
+    w, ge = run(engine, lib, net, tr, 100, params)
+    assert_matches(w, ge, oracle.walk(lib, net, tr, 100), 100)
+
+
+@pytest.mark.parametrize("params", KERNELS, ids=KID)
+@pytest.mark.parametrize("bin_ps", [1, 7, 3000])
+def test_bin_sizes_and_window_edges(engine, params, bin_ps):
+    lib, net, tr = small_random(n_gates=40, n_events=5_000, window_ps=21_000, seed=31, tie_p=0.05)
+    rec = tr.records
+    for g in range(0, 40, 5):  # events at t = 0 and t = T - 1
+        a, b = tr.offsets[g], tr.offsets[g + 1]
+        if b - a >= 2:
+            rec[a, 0] = 0
+            rec[b - 1, 0] = tr.window_ps - 1
+    w, ge = run(engine, lib, net, tr, bin_ps, params)
+    assert_matches(w, ge, oracle.walk(lib, net, tr, bin_ps), bin_ps)
+
+
+@pytest.mark.parametrize("params", KERNELS, ids=KID)
+def test_scales_and_extrapolated_lookups(engine, params):
+    lib, net, tr = small_random(n_gates=200, n_events=30_000, window_ps=300_000, seed=41, tie_p=0.01)
+    net.slew_ps[::3, :, 0] = 2.0
+    net.slew_ps[1::3, :, 1] = 700.0
+    net.load_ff[::4] = 0.1
+    net.load_ff[1::4] = 40.0
+    rng = np.random.default_rng(0)
+    es = rng.uniform(0.3, 3.0, lib.n_cells).astype(np.float32)
+    ls = rng.uniform(0.3, 3.0, lib.n_cells).astype(np.float32)
+    w, ge = run(engine, lib, net, tr, 100, params, escale=es, lscale=ls)
+    ref = oracle.walk(lib, net, tr, 100, escale=es.astype(np.float64), lscale=ls.astype(np.float64))
+    assert_matches(w, ge, ref, 100)
+
+
+@pytest.mark.parametrize("params", KERNELS[1:], ids=KID[1:])
+def test_seed_fixup_for_idle_pin(engine, params):
+    """Pin 2 of a NAND3 stays idle for most of a 30k-event gate, so the
+    bounded backward seed scan cannot resolve it and the fix-up pass runs."""
+    lib = synth.make_library(1)
+    net = netlist_from(lib, [3, 0], [2.0, 1.0])
+    S = 0b0101
+    ev = []
+    rng = np.random.default_rng(3)
+    for k in range(30_000):
+        pin = int(rng.integers(0, 2)) if k != 29_000 else 2
+        if k % 7 == 0 and k != 29_000:
+            pin = 3
+        v = 1 - ((S >> pin) & 1)
+        S ^= 1 << pin
+        ev.append((k * 10 + (5 if k % 11 else 0), pin, v))
+    ev2 = [(100, 0, 1), (200, 1, 0)]
+    tr = trace_from([ev, ev2], [0b0101, 0b10], 400_000)
+    w, ge = run(engine, lib, net, tr, 100, params)
+    assert_matches(w, ge, oracle.walk(lib, net, tr, 100), 100)
+
+
+@pytest.mark.parametrize("params", KERNELS, ids=KID)
+@pytest.mark.parametrize("events,code", [
+    ([(100, 0, 1), (50, 1, 1)], -2),
+    ([(100, 0, 1), (5000, 1, 1)], -3),
+    ([(100, 3, 1)], -3),
+    ([(100, 0, 0)], -4),
+    ([(100, 0, 1), (100, 0, 1)], -4),
+])
+def test_malformed_traces_are_rejected(engine, params, events, code):
+    from paper_2609_05960_gb300 import GtpError
+    lib = single_cell_library(2, lambda *a: 1.0, lambda s: 1.0)
+    net = netlist_from(lib, [0, 0], [1.0, 1.0])
+    tr = trace_from([[(10, 1, 1)], events], [0, 0], 1000)
+    with pytest.raises(GtpError) as ei:
+        run(engine, lib, net, tr, 100, params)
+    assert ei.value.code == code
+    with pytest.raises(oracle.OracleError) as eo:
+        oracle.walk(lib, net, tr, 100)
+    assert eo.value.code == code
+
+
+def test_bad_bin_size_rejected(engine):
+    from paper_2609_05960_gb300 import GtpError
+    lib, net, tr = small_random(n_gates=5, n_events=100, window_ps=1000, seed=2)
+    engine.load_library(lib)
+    engine.load_netlist(net)
+    engine.load_events(0, tr)
+    with pytest.raises(GtpError) as ei:
+        engine.run_power(0, 300)
+    assert ei.value.code == -3
+
+
+def test_gpu_generator_matches_host_generator():
+    import torch
+    cfg = synth.scaled(synth.CONFIGS["tiny"], 500, 150_000, tie_p=0.2)
+    lib, net, tr = synth.make_inputs(cfg)
+    counts = np.diff(tr.offsets)
+    tr2, rec = synth.make_trace_gpu(net, counts, cfg.window_ps, cfg.seed_ev, cfg.tie_p, chunk=100)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(rec.cpu().numpy().view(np.uint32), tr.records)
+    np.testing.assert_array_equal(tr2.init_state, tr.init_state)
+
+
+@pytest.mark.parametrize("borrow", [False, True])
+def test_device_resident_events(engine, borrow):
+    import torch
+    lib, net, tr = small_random(n_gates=100, n_events=20_001, window_ps=200_000, seed=51, tie_p=0.02)
+    engine.load_library(lib)
+    engine.load_netlist(net)
+    for k in ("kernel", "records_per_thread", "block_threads", "ctas_per_sm"):
+        engine.set_param(k, -1)
+    dev = engine.device
+    off = torch.from_numpy(tr.offsets).to(dev)
+    rec = torch.from_numpy(tr.records.view(np.int32)).to(dev)
+    init = torch.from_numpy(tr.init_state).to(dev)
+    engine.load_events(3, window_ps=tr.window_ps, offsets=off, records=rec, init_state=init, borrow=borrow)
+    w = engine.run_power(3, 100).cpu().numpy()
+    ge = engine.gate_energy(3, device=True)
+    ge = {k: v.cpu().numpy() for k, v in ge.items()}
+    assert_matches(w, ge, oracle.walk(lib, net, tr, 100), 100)
+
+
+def test_host_waveform_output_and_repeat_runs(engine):
+    from paper_2609_05960_gb300 import gtpower
+    lib, net, tr = small_random(n_gates=100, n_events=20_000, window_ps=200_000, seed=52)
+    engine.load_library(lib)
+    engine.load_netlist(net)
+    engine.load_events(0, tr)
+    host = np.zeros(2000)
+    gtpower.gtp_run_power(engine.ctx, 0, 100, host)
+    dev = engine.run_power(0, 100).cpu().numpy()
+    ref = oracle.waveform_w(oracle.walk(lib, net, tr, 100)["bins"], 100)
+    for w in (host, dev):
+        assert (np.abs(w - ref) / ref).max() <= TOL
+
+
+def test_bin_and_gate_totals_agree(engine):
+    """Sum over bins of energy equals the sum over gates of their energies."""
+    cfg = synth.scaled(synth.CONFIGS["large"], 20_000, 2_000_000)
+    cfg = synth.dataclasses.replace(cfg, window_ps=1_000_000, bin_ps=10)
+    lib, net, tr = synth.make_inputs(cfg)
+    w, ge = run(engine, lib, net, tr, 10)
+    e_bins = (w * 10 * 1e3).sum()
+    e_gates = ge["e_leak"].sum() + ge["e_int"].sum() + ge["e_sw"].sum()
+    assert e_bins == pytest.approx(e_gates, rel=1e-6)
+    w2, _ = run(engine, lib, net, tr, 20)
+    np.testing.assert_allclose(w.reshape(-1, 2).mean(1), w2, rtol=TOL)
