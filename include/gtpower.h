@@ -52,6 +52,10 @@ extern "C" {
                                caller's event buffer in place (no copy); it must
                                stay valid and unchanged while the window is used
                                and be 16-byte aligned */
+#define GTP_GRAPH 4         /* gtp_run_power_batched only, with GTP_DEVICE:
+                               capture the run in a CUDA graph on its first call
+                               and replay it on later calls with the same window
+                               list, bin size and tuning */
 
 /* Limits of this engine: at most 7 input pins per cell (8 pins, so the gate
  * state fits in one byte), at most 16 points per interpolation axis, and
@@ -176,10 +180,13 @@ int gtp_gate_energy(gtp_ctx* ctx, int32_t window, double* e_leak, double* e_int,
                     int64_t* n_events, uint8_t* final_state, int flags);
 
 /*
- * Run n_windows loaded windows over the same netlist in one persistent
- * launch (windows[i] names the slot; waveforms[i] receives window i's
- * waveform, same layout as gtp_run_power).  flags: GTP_HOST or GTP_DEVICE
- * for the waveform buffers (the pointer array itself is host memory).
+ * Run n_windows (<= 1024) distinct loaded windows over the same netlist: one
+ * gate-pass launch, one seed pass and one persistent walk launch whose warps
+ * take segments from a single list covering every window, and one merge
+ * (windows[i] names the slot; waveforms[i] receives window i's waveform,
+ * same layout as gtp_run_power; a NULL entry skips that waveform).
+ * flags: GTP_HOST or GTP_DEVICE for the waveform buffers (the pointer array
+ * itself is host memory), optionally | GTP_GRAPH (device buffers only).
  */
 int gtp_run_power_batched(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_t bin_ps,
                           double* const* waveforms, int flags);
@@ -192,14 +199,31 @@ int gtp_run_power_batched(gtp_ctx* ctx, int32_t n_windows, const int32_t* window
  * d_lscale[n_cells]), all FP32 device buffers; any output may be NULL.
  * The internal-energy derivative in the load is the slope of the located
  * load segment of the bilinear table (right derivative on a knot);
- * d(0.5*C*Vdd^2)/dC = 0.5*Vdd^2.
+ * d(0.5*C*Vdd^2)/dC = 0.5*Vdd^2; leakage energy is linear in lscale and
+ * internal energy in escale.  Uses the context's current scales and loads.
+ * Synchronous; reports malformed traces like gtp_run_power.
  */
 int gtp_run_power_backward(gtp_ctx* ctx, int32_t window, int32_t bin_ps, const float* dL_dP, float* dC,
                            float* d_escale, float* d_lscale);
 
-/* Engine tuning knobs (see the engine documentation); value < 0 restores
- * the default.  Keys: "records_per_thread", "block_threads", "ctas_per_sm",
- * "kernel" (0 = segmented warp walk, 1 = one thread per gate). */
+/*
+ * Autotuner: time the segmented walk of the given windows for every
+ * candidate (records per lane 4/8/16 = segment length 128/256/512 records,
+ * 128 or 256 threads per CTA, 0 (= full occupancy) /1/2/4 CTAs per SM),
+ * `iters` timed runs each, keep the fastest as the context's parameters and
+ * report its time per run (ms) in *best_ms.  Runs the windows repeatedly;
+ * their per-gate results are those of the last run.
+ */
+int gtp_autotune(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_t bin_ps, int32_t iters,
+                 double* best_ms);
+
+/* Engine tuning knobs; value < 0 restores the default.  Keys:
+ * "records_per_thread" (4, 8, 16), "block_threads" (128, 256),
+ * "ctas_per_sm" (0 = full occupancy), "kernel" (0 = segmented warp walk,
+ * 1 = one thread per gate, a plain cross-check), "timing" (1 = time the
+ * phases of later runs with CUDA events; read back with gtp_get_param keys
+ * "t_gate_pass_ns", "t_seeds_ns", "t_walk_ns", "t_merge_ns", "n_timed",
+ * and "launches" = kernels launched since timing was last set). */
 int gtp_set_param(gtp_ctx* ctx, const char* key, int64_t value);
 int64_t gtp_get_param(const gtp_ctx* ctx, const char* key);
 

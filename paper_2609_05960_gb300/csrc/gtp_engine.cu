@@ -1,19 +1,25 @@
 // Host engine behind the C ABI of include/gtpower.h: device buffers, input
-// validation, plans and launches.  All device work goes to the context's
-// stream; results are synchronised only where the ABI says so.
+// validation, launch plans (window descriptor tables), CUDA-graph replay of
+// batched runs, the adjoint, phase timing and the autotuner.  All device work
+// goes to the context's stream; results are synchronised only where the ABI
+// says so.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "gtp_internal.cuh"
-#include "gtp_segwalk.cuh"
+#include "gtp_walk.cuh"
 
 using namespace gtp;
 
 namespace {
+
+constexpr int kMaxWindows = 1024;
 
 struct DevBuf {
   void* p = nullptr;
@@ -41,20 +47,27 @@ struct Window {
   int64_t n_events = 0;
   DevBuf offsets, records, init;
   const uint2* borrowed = nullptr;
-  // per-gate results and scratch
-  DevBuf e_leak, e_int, e_sw, final_state;
-  DevBuf bins, tiles, l0, wave;
-  DevBuf seeds, runs;
+  DevBuf e_leak, e_int, e_sw, final_state, bins, tiles, wave, seeds;
   bool has_result = false;
   int32_t last_bin_ps = 0;
   const uint2* rec() const { return borrowed ? borrowed : records.as<uint2>(); }
   void release() {
-    for (DevBuf* b : {&offsets, &records, &init, &e_leak, &e_int, &e_sw, &final_state, &bins, &tiles, &l0,
-                      &wave, &seeds, &runs})
+    for (DevBuf* b : {&offsets, &records, &init, &e_leak, &e_int, &e_sw, &final_state, &bins, &tiles, &wave, &seeds})
       b->release();
     borrowed = nullptr;
     loaded = false;
     has_result = false;
+  }
+};
+
+struct GraphKey {
+  std::vector<int32_t> windows;
+  int32_t bin_ps;
+  int64_t rpt, block, ctas, kernel;
+  const void* runs;
+  bool operator<(const GraphKey& o) const {
+    return std::tie(windows, bin_ps, rpt, block, ctas, kernel, runs) <
+           std::tie(o.windows, o.bin_ps, o.rpt, o.block, o.ctas, o.kernel, o.runs);
   }
 };
 
@@ -73,11 +86,17 @@ struct gtp_ctx {
   LibView L{};
   // netlist
   bool net_loaded = false;
-  DevBuf cell, load, slew;
+  DevBuf cell, load, slew, coord, wld, rwl;
   NetView N{};
   std::map<int, Window> windows;
+  // launch plan: device descriptor table and its pinned host staging copy
+  DevBuf plan;  // WinDesc[kMaxWindows] | seg_base[kMaxWindows+1] | tile_base[kMaxWindows+1] | l0[kMaxWindows+1]
+  unsigned char* h_plan = nullptr;
+  DevBuf runs, cell_acc, grad, gtiles, dC_scratch;
   DevBuf d_err;
   DevError* h_err = nullptr;
+  std::map<GraphKey, cudaGraphExec_t> graphs;
+  cudaStream_t capture_stream = nullptr;
   // parameters
   int64_t p_kernel = 0;
   int64_t p_rpt = 8;
@@ -93,6 +112,14 @@ struct gtp_ctx {
 
 namespace {
 
+size_t plan_bytes() { return sizeof(WinDesc) * kMaxWindows + 3 * sizeof(int64_t) * (kMaxWindows + 1); }
+WinDesc* plan_wins(void* base) { return static_cast<WinDesc*>(base); }
+int64_t* plan_seg_base(void* base) {
+  return reinterpret_cast<int64_t*>(static_cast<unsigned char*>(base) + sizeof(WinDesc) * kMaxWindows);
+}
+int64_t* plan_tile_base(void* base) { return plan_seg_base(base) + (kMaxWindows + 1); }
+double* plan_l0(void* base) { return reinterpret_cast<double*>(plan_tile_base(base) + (kMaxWindows + 1)); }
+
 int fail(gtp_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
   return code;
@@ -104,10 +131,16 @@ int cuda_fail(gtp_ctx* c, cudaError_t e, const char* where) {
   return fail(c, GTP_ECUDA, m);
 }
 
-#define CU(call, where)                           \
-  do {                                            \
-    cudaError_t e_ = (call);                      \
+#define CU(call, where)                                      \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+  } while (0)
+
+#define RC(call)                 \
+  do {                           \
+    int r_ = (call);             \
+    if (r_ != GTP_OK) return r_; \
   } while (0)
 
 struct DeviceGuard {
@@ -149,7 +182,7 @@ int check_device_error(gtp_ctx* ctx, const char* what) {
   CU(cudaStreamSynchronize(ctx->stream), what);
   if (ctx->h_err->code != 0) {
     char buf[256];
-    long long idx = (long long)ctx->h_err->index;
+    const long long idx = (long long)ctx->h_err->index;
     if (idx >= 0)
       snprintf(buf, sizeof buf, "%s: %s at record %lld", what, code_name(ctx->h_err->code), idx);
     else
@@ -165,48 +198,100 @@ Window* get_window(gtp_ctx* ctx, int32_t w) {
   return &it->second;
 }
 
-int prepare_outputs(gtp_ctx* ctx, Window& W, int32_t bin_ps, Outputs* O) {
-  if (bin_ps <= 0 || W.window_ps % bin_ps != 0) return fail(ctx, GTP_ERANGE, "window_ps must be a multiple of bin_ps > 0");
-  int64_t nb = W.window_ps / bin_ps;
-  int64_t G = ctx->N.n_gates;
-  CU(W.e_leak.reserve(sizeof(double) * G), "alloc e_leak");
-  CU(W.e_int.reserve(sizeof(double) * G), "alloc e_int");
-  CU(W.e_sw.reserve(sizeof(double) * G), "alloc e_sw");
-  CU(W.final_state.reserve((size_t)G), "alloc final_state");
-  CU(W.bins.reserve(sizeof(float2) * nb), "alloc bins");
-  CU(W.tiles.reserve(sizeof(double) * (size_t)merge_tiles((int)nb)), "alloc tiles");
-  CU(W.l0.reserve(sizeof(double)), "alloc l0");
-  Outputs o{};
-  o.e_leak = W.e_leak.as<double>();
-  o.e_int = W.e_int.as<double>();
-  o.e_sw = W.e_sw.as<double>();
-  o.final_state = W.final_state.as<uint8_t>();
-  o.bins = W.bins.as<float2>();
-  o.l0 = W.l0.as<double>();
-  o.err = ctx->d_err.as<DevError>();
-  o.bin_ps = bin_ps;
-  bin_magic(bin_ps, &o.bin_magic, &o.bin_shift);
-  o.n_bins = (int32_t)nb;
-  *O = o;
+int64_t seg_len_of(const gtp_ctx* ctx) { return 32 * ctx->p_rpt; }
+
+// Fill the descriptor table of a run in the pinned staging buffer, reserving
+// the windows' device buffers.  The upload is enqueued by upload_plan().
+int build_plan(gtp_ctx* ctx, const std::vector<Window*>& ws, int32_t bin_ps, const std::vector<double*>& waves,
+               bool backward, int64_t* n_seg_total, int64_t* n_tiles_total) {
+  const int n = (int)ws.size();
+  if (n <= 0 || n > kMaxWindows) return fail(ctx, GTP_EINVAL, "between 1 and 1024 windows per run");
+  WinDesc* hw = plan_wins(ctx->h_plan);
+  int64_t* hs = plan_seg_base(ctx->h_plan);
+  int64_t* ht = plan_tile_base(ctx->h_plan);
+  double* dl0 = plan_l0(ctx->plan.p);
+  const int64_t G = ctx->N.n_gates;
+  const int64_t seg_len = seg_len_of(ctx);
+  int64_t sb = 0, tb = 0;
+  for (int i = 0; i < n; ++i) {
+    Window& W = *ws[i];
+    if (bin_ps <= 0 || W.window_ps % bin_ps != 0)
+      return fail(ctx, GTP_ERANGE, "window_ps must be a multiple of bin_ps > 0");
+    const int64_t nb = W.window_ps / bin_ps;
+    const int64_t n_seg = (W.n_events + seg_len - 1) / seg_len;
+    const int nt = merge_tiles((int)nb);
+    CU(W.e_leak.reserve(sizeof(double) * G), "alloc e_leak");
+    CU(W.e_int.reserve(sizeof(double) * G), "alloc e_int");
+    CU(W.e_sw.reserve(sizeof(double) * G), "alloc e_sw");
+    CU(W.final_state.reserve((size_t)G), "alloc final_state");
+    CU(W.bins.reserve(sizeof(float2) * nb), "alloc bins");
+    CU(W.tiles.reserve(sizeof(double) * (size_t)nt), "alloc tiles");
+    CU(W.seeds.reserve(sizeof(Seed) * (size_t)(n_seg + 1)), "alloc seeds");
+    WinDesc d{};
+    d.offsets = W.offsets.as<int64_t>();
+    d.rec = W.rec();
+    d.init = W.init.as<uint8_t>();
+    d.seeds = W.seeds.as<Seed>();
+    d.e_leak = W.e_leak.as<double>();
+    d.e_int = W.e_int.as<double>();
+    d.e_sw = W.e_sw.as<double>();
+    d.final_state = W.final_state.as<uint8_t>();
+    d.bins = W.bins.as<float2>();
+    d.l0 = dl0 + i;
+    d.tiles = W.tiles.as<double>();
+    d.wave = waves.empty() ? nullptr : waves[i];
+    d.grad = backward ? ctx->grad.as<float2>() : nullptr;
+    d.dC = nullptr;
+    d.n_events = W.n_events;
+    d.seg_base = sb;
+    d.n_seg = n_seg;
+    d.tile_base = tb;
+    d.n_tiles = nt;
+    d.window_ps = (int32_t)W.window_ps;
+    d.bin_ps = bin_ps;
+    bin_magic(bin_ps, &d.bin_magic, &d.bin_shift);
+    d.n_bins = (int32_t)nb;
+    hw[i] = d;
+    hs[i] = sb;
+    ht[i] = tb;
+    sb += n_seg;
+    tb += nt;
+  }
+  hs[n] = sb;
+  ht[n] = tb;
+  CU(ctx->runs.reserve(sizeof(int64_t) * (size_t)(sb + 1)), "alloc runs");
+  *n_seg_total = sb;
+  *n_tiles_total = tb;
   return GTP_OK;
 }
 
-WindowView view_of(const gtp_ctx* ctx, const Window& W) {
-  WindowView v{};
-  v.offsets = W.offsets.as<int64_t>();
-  v.rec = W.rec();
-  v.init = W.init.as<uint8_t>();
-  v.n_events = W.n_events;
-  v.window_ps = (int32_t)W.window_ps;
-  (void)ctx;
-  return v;
+int upload_plan(gtp_ctx* ctx, int n, cudaStream_t st) {
+  CU(cudaMemcpyAsync(ctx->plan.p, ctx->h_plan, sizeof(WinDesc) * n, cudaMemcpyHostToDevice, st), "upload plan");
+  CU(cudaMemcpyAsync(plan_seg_base(ctx->plan.p), plan_seg_base(ctx->h_plan), sizeof(int64_t) * (kMaxWindows + 1) * 2,
+                     cudaMemcpyHostToDevice, st), "upload plan bases");
+  return GTP_OK;
 }
 
-void mark(gtp_ctx* ctx, int i) {
-  if (ctx->timing) cudaEventRecord(ctx->ev[i], ctx->stream);
+WalkArgs walk_args(gtp_ctx* ctx, int n, int64_t n_seg_total) {
+  WalkArgs A{};
+  A.wins = plan_wins(ctx->plan.p);
+  A.seg_base = plan_seg_base(ctx->plan.p);
+  A.n_win = n;
+  A.n_seg_total = n_seg_total;
+  A.seg_len = seg_len_of(ctx);
+  A.rpt = (int)ctx->p_rpt;
+  A.block = (int)ctx->p_block;
+  A.grid = ctx->p_ctas_per_sm > 0 ? (int)(ctx->p_ctas_per_sm * ctx->n_sm) : 0;
+  A.n_sm = ctx->n_sm;
+  A.err = ctx->d_err.as<DevError>();
+  A.cell_acc = ctx->cell_acc.as<double>();
+  return A;
 }
 
-// Accumulate the phase times of the last enqueue_forward (stream synchronised).
+void mark(gtp_ctx* ctx, int i, cudaStream_t st) {
+  if (ctx->timing && st == ctx->stream) cudaEventRecord(ctx->ev[i], st);
+}
+
 void collect_timing(gtp_ctx* ctx) {
   if (!ctx->timing) return;
   for (int k = 0; k < 4; ++k) {
@@ -217,45 +302,152 @@ void collect_timing(gtp_ctx* ctx) {
   ctx->n_timed += 1;
 }
 
-// Enqueue one window's forward pass (no synchronisation).
-int enqueue_forward(gtp_ctx* ctx, Window& W, const Outputs& O, double* wave_dev) {
-  cudaStream_t st = ctx->stream;
-  WindowView V = view_of(ctx, W);
-  CU(cudaMemsetAsync(O.bins, 0, sizeof(float2) * (size_t)O.n_bins, st), "zero bins");
-  CU(cudaMemsetAsync(O.l0, 0, sizeof(double), st), "zero l0");
-  mark(ctx, 0);
-  CU(launch_gate_pass(ctx->L, ctx->N, V, O, st), "gate pass");
-  ctx->launches += 1;
-  mark(ctx, 1);
-  mark(ctx, 2);
-  if (W.n_events > 0) {
+// Enqueue the forward pass of the planned windows (no synchronisation).
+int enqueue_forward(gtp_ctx* ctx, int n, int64_t n_seg_total, int64_t n_tiles_total, bool any_events,
+                    cudaStream_t st) {
+  const WinDesc* dw = plan_wins(ctx->plan.p);
+  const int64_t* tile_base = plan_tile_base(ctx->plan.p);
+  RC(upload_plan(ctx, n, st));
+  CU(cudaMemsetAsync(plan_l0(ctx->plan.p), 0, sizeof(double) * n, st), "zero l0");
+  CU(launch_zero_bins(dw, tile_base, n, n_tiles_total, st), "zero bins");
+  mark(ctx, 0, st);
+  CU(launch_gate_pass(ctx->L, ctx->N, dw, n, ctx->d_err.as<DevError>(), st), "gate pass");
+  mark(ctx, 1, st);
+  ctx->launches += 2;
+  mark(ctx, 2, st);
+  if (any_events) {
+    const WalkArgs A = walk_args(ctx, n, n_seg_total);
     if (ctx->p_kernel == 1) {
-      mark(ctx, 3);
-      mark(ctx, 4);
-      CU(launch_walk_per_gate(ctx->L, ctx->N, V, O, 128, st), "walk (per gate)");
+      mark(ctx, 3, st);
+      mark(ctx, 4, st);
+      CU(launch_walk_per_gate(ctx->L, ctx->N, dw, n, ctx->d_err.as<DevError>(), st), "walk (per gate)");
       ctx->launches += 1;
     } else {
-      SegPlan P = make_seg_plan((int)ctx->p_rpt, (int)ctx->p_block, (int)ctx->p_ctas_per_sm, ctx->n_sm, W.n_events);
-      CU(W.seeds.reserve(sizeof(Seed) * (size_t)P.n_seg), "alloc seeds");
-      CU(W.runs.reserve(sizeof(int64_t) * (size_t)(P.n_seg + 1)), "alloc runs");
-      CU(launch_seeds(ctx->L, ctx->N, V, P, W.seeds.as<Seed>(), W.runs.as<int64_t>(), st), "seeds");
-      mark(ctx, 3);
-      mark(ctx, 4);
-      CU(launch_walk(ctx->L, ctx->N, V, O, P, W.seeds.as<Seed>(), st), "walk (segmented)");
-      ctx->launches += 3;
+      CU(launch_seeds(ctx->N, ctx->L, A, ctx->runs.as<int64_t>(), st), "seeds");
+      mark(ctx, 3, st);
+      mark(ctx, 4, st);
+      CU(launch_walk(ctx->L, ctx->N, A, false, st), "walk");
+      ctx->launches += 4;
     }
   } else {
-    mark(ctx, 3);
-    mark(ctx, 4);
+    mark(ctx, 3, st);
+    mark(ctx, 4, st);
   }
-  mark(ctx, 5);
-  mark(ctx, 6);
-  if (wave_dev) {
-    CU(launch_merge(O, wave_dev, W.tiles.as<double>(), merge_tiles(O.n_bins), st), "merge");
-    ctx->launches += 3;
-  }
-  mark(ctx, 7);
+  mark(ctx, 5, st);
+  mark(ctx, 6, st);
+  CU(launch_merge(dw, tile_base, n, n_tiles_total, st), "merge");
+  ctx->launches += 3;
+  mark(ctx, 7, st);
   return GTP_OK;
+}
+
+int ensure_netlist_coords(gtp_ctx* ctx) {
+  const int64_t G = ctx->N.n_gates;
+  CU(ctx->coord.reserve(sizeof(float2) * 2 * ctx->N.stride * G), "alloc coord");
+  CU(ctx->wld.reserve(sizeof(float) * G), "alloc wld");
+  CU(ctx->rwl.reserve(sizeof(float) * G), "alloc rwl");
+  ctx->N.coord = ctx->coord.as<float2>();
+  ctx->N.wld = ctx->wld.as<float>();
+  ctx->N.rwl = ctx->rwl.as<float>();
+  CU(launch_interp_coords(ctx->L, ctx->N, ctx->coord.as<float2>(), ctx->wld.as<float>(), ctx->rwl.as<float>(),
+                          ctx->stream), "interpolation coordinates");
+  ctx->launches += 1;
+  return GTP_OK;
+}
+
+void drop_graphs(gtp_ctx* ctx) {
+  for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+  ctx->graphs.clear();
+}
+
+__global__ void k_check_cells(const int32_t* cell, int64_t n, int32_t n_cells, DevError* err) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    if (cell[g] < 0 || cell[g] >= n_cells) report_error(err, GTP_ERANGE, -1 - g);
+}
+
+__global__ void k_check_offsets(const int64_t* off, int64_t n_gates, int64_t n_events, DevError* err) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_gates;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    if (off[g + 1] < off[g]) report_error(err, GTP_EINVAL, -1 - g);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (off[0] != 0 || off[n_gates] != n_events))
+    report_error(err, GTP_EINVAL, -1);
+}
+
+__global__ void k_counts(const int64_t* off, int64_t n, int64_t* out) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    out[g] = off[g + 1] - off[g];
+}
+
+// Forward run of a window list; waveforms per window (device or host).
+int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, double* const* waveforms, int flags,
+                bool use_graph) {
+  if (!ctx->net_loaded) return fail(ctx, GTP_EINVAL, "run_power: load the library, netlist and events first");
+  std::vector<Window*> ws(n);
+  bool any_events = false;
+  for (int i = 0; i < n; ++i) {
+    ws[i] = get_window(ctx, windows[i]);
+    if (!ws[i]) return fail(ctx, GTP_EINVAL, "run_power: window not loaded");
+    for (int j = 0; j < i; ++j)
+      if (windows[j] == windows[i]) return fail(ctx, GTP_EINVAL, "run_power: a window is listed twice");
+    any_events |= ws[i]->n_events > 0;
+  }
+  if (bin_ps <= 0) return fail(ctx, GTP_ERANGE, "window_ps must be a multiple of bin_ps > 0");
+  std::vector<double*> waves(n, nullptr);
+  for (int i = 0; i < n; ++i) {
+    if (!waveforms || !waveforms[i]) continue;
+    if (flags & GTP_DEVICE) {
+      waves[i] = waveforms[i];
+    } else {
+      CU(ws[i]->wave.reserve(sizeof(double) * (size_t)(ws[i]->window_ps / bin_ps)), "alloc waveform");
+      waves[i] = ws[i]->wave.as<double>();
+    }
+  }
+  int64_t n_seg_total = 0, n_tiles_total = 0;
+  RC(build_plan(ctx, ws, bin_ps, waves, false, &n_seg_total, &n_tiles_total));
+  CU(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(DevError), ctx->stream), "zero status");
+  if (use_graph) {
+    const GraphKey key{std::vector<int32_t>(windows, windows + n), bin_ps, ctx->p_rpt, ctx->p_block,
+                       ctx->p_ctas_per_sm, ctx->p_kernel, ctx->runs.p};
+    auto it = ctx->graphs.find(key);
+    if (it == ctx->graphs.end()) {
+      if (!ctx->capture_stream) CU(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking), "stream");
+      const int64_t launches0 = ctx->launches;
+      CU(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+      const int rc = enqueue_forward(ctx, n, n_seg_total, n_tiles_total, any_events, ctx->capture_stream);
+      cudaGraph_t graph = nullptr;
+      cudaError_t ce = cudaStreamEndCapture(ctx->capture_stream, &graph);
+      if (rc != GTP_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+      }
+      CU(ce, "end capture");
+      cudaGraphExec_t exec = nullptr;
+      ce = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      CU(ce, "instantiate graph");
+      it = ctx->graphs.emplace(key, exec).first;
+      ctx->launches = launches0;
+    }
+    // the graph's first node uploads the descriptor table from the staging buffer
+    CU(cudaGraphLaunch(it->second, ctx->stream), "graph launch");
+    ctx->launches += any_events ? (ctx->p_kernel == 1 ? 6 : 9) : 5;
+  } else {
+    RC(enqueue_forward(ctx, n, n_seg_total, n_tiles_total, any_events, ctx->stream));
+  }
+  if (waveforms && !(flags & GTP_DEVICE)) {
+    for (int i = 0; i < n; ++i)
+      if (waveforms[i])
+        CU(cudaMemcpyAsync(waveforms[i], waves[i], sizeof(double) * (size_t)(ws[i]->window_ps / bin_ps),
+                           cudaMemcpyDeviceToHost, ctx->stream), "copy waveform");
+  }
+  const int rc = check_device_error(ctx, "run_power");
+  if (!use_graph) collect_timing(ctx);
+  for (Window* w : ws) {
+    w->has_result = (rc == GTP_OK);
+    w->last_bin_ps = bin_ps;
+  }
+  return rc;
 }
 
 }  // namespace
@@ -274,12 +466,16 @@ int gtp_create(gtp_ctx** out, int device, void* cuda_stream) {
   ctx->stream = (cudaStream_t)cuda_stream;
   DeviceGuard dg(device);
   cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device);
-  if (ctx->d_err.reserve(sizeof(DevError)) != cudaSuccess ||
-      cudaMallocHost(&ctx->h_err, sizeof(DevError)) != cudaSuccess) {
+  if (ctx->d_err.reserve(sizeof(DevError)) != cudaSuccess || ctx->plan.reserve(plan_bytes()) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_err, sizeof(DevError)) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_plan, plan_bytes()) != cudaSuccess) {
     ctx->d_err.release();
+    ctx->plan.release();
+    if (ctx->h_err) cudaFreeHost(ctx->h_err);
     delete ctx;
     return GTP_ENOMEM;
   }
+  memset(ctx->h_plan, 0, plan_bytes());
   cudaMemset(ctx->d_err.p, 0, sizeof(DevError));
   *out = ctx;
   return GTP_OK;
@@ -289,11 +485,16 @@ void gtp_destroy(gtp_ctx* ctx) {
   if (!ctx) return;
   DeviceGuard dg(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  cudaDeviceSynchronize();
+  drop_graphs(ctx);
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   for (auto& kv : ctx->windows) kv.second.release();
-  for (DevBuf* b : {&ctx->tab, &ctx->leak, &ctx->cells, &ctx->table_cell, &ctx->leak_cell, &ctx->escale,
-                    &ctx->lscale, &ctx->cell, &ctx->load, &ctx->slew, &ctx->d_err})
+  for (DevBuf* b : {&ctx->tab, &ctx->leak, &ctx->cells, &ctx->table_cell, &ctx->leak_cell, &ctx->escale, &ctx->lscale,
+                    &ctx->cell, &ctx->load, &ctx->slew, &ctx->coord, &ctx->wld, &ctx->rwl, &ctx->plan, &ctx->runs,
+                    &ctx->cell_acc, &ctx->grad, &ctx->gtiles, &ctx->dC_scratch, &ctx->d_err})
     b->release();
   if (ctx->h_err) cudaFreeHost(ctx->h_err);
+  if (ctx->h_plan) cudaFreeHost(ctx->h_plan);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
   delete ctx;
@@ -332,7 +533,7 @@ int gtp_load_library(gtp_ctx* ctx, int32_t n_cells, const int32_t* n_in, float v
     n_leak += 2ll << n_in[c];
     if (n_in[c] > max_in) max_in = n_in[c];
   }
-  int64_t tsize = (int64_t)n_slew * n_load;
+  const int64_t tsize = (int64_t)n_slew * n_load;
   if (n_e_int != n_tables * tsize) return fail(ctx, GTP_EINVAL, "load_library: e_int size does not match the cells");
   if (n_p_leak != n_leak) return fail(ctx, GTP_EINVAL, "load_library: p_leak size does not match the cells");
   LibView L{};
@@ -347,11 +548,13 @@ int gtp_load_library(gtp_ctx* ctx, int32_t n_cells, const int32_t* n_in, float v
   DeviceGuard dg(ctx->device);
   std::vector<uint8_t> tcell(n_tables), lcell(n_leak);
   for (int c = 0; c < n_cells; ++c) {
-    int64_t nt = (int64_t)n_in[c] * (2ll << (n_in[c] - 1));
+    const int64_t nt = (int64_t)n_in[c] * (2ll << (n_in[c] - 1));
     for (int64_t k = 0; k < nt; ++k) tcell[ci[c].tab_base + k] = (uint8_t)c;
     for (int64_t k = 0; k < (2ll << n_in[c]); ++k) lcell[ci[c].leak_base + k] = (uint8_t)c;
   }
   std::vector<float> ones(n_cells, 1.0f);
+  CU(cudaStreamSynchronize(ctx->stream), "load_library");
+  drop_graphs(ctx);
   CU(ctx->tab.reserve(sizeof(float) * n_e_int), "alloc tables");
   CU(ctx->leak.reserve(sizeof(float) * n_leak), "alloc leakage");
   CU(ctx->cells.reserve(sizeof(CellInfo) * n_cells), "alloc cells");
@@ -359,6 +562,7 @@ int gtp_load_library(gtp_ctx* ctx, int32_t n_cells, const int32_t* n_in, float v
   CU(ctx->leak_cell.reserve(n_leak), "alloc leak_cell");
   CU(ctx->escale.reserve(sizeof(float) * n_cells), "alloc escale");
   CU(ctx->lscale.reserve(sizeof(float) * n_cells), "alloc lscale");
+  CU(ctx->cell_acc.reserve(sizeof(double) * 2 * n_cells), "alloc cell_acc");
   CU(cudaMemcpy(ctx->tab.p, e_int, sizeof(float) * n_e_int, cudaMemcpyHostToDevice), "copy tables");
   CU(cudaMemcpy(ctx->leak.p, p_leak, sizeof(float) * n_leak, cudaMemcpyHostToDevice), "copy leakage");
   CU(cudaMemcpy(ctx->cells.p, ci.data(), sizeof(CellInfo) * n_cells, cudaMemcpyHostToDevice), "copy cells");
@@ -403,31 +607,18 @@ int gtp_set_scales(gtp_ctx* ctx, const float* escale, const float* lscale) {
   return GTP_OK;
 }
 
-namespace {
-__global__ void k_check_cells(const int32_t* cell, int64_t n, int32_t n_cells, DevError* err) {
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
-    if (cell[g] < 0 || cell[g] >= n_cells) report_error(err, GTP_ERANGE, -1 - g);
-}
-
-__global__ void k_check_offsets(const int64_t* off, int64_t n_gates, int64_t n_events, DevError* err) {
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_gates;
-       g += (int64_t)gridDim.x * blockDim.x) {
-    if (off[g + 1] < off[g]) report_error(err, GTP_EINVAL, -1 - g);
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0 && (off[0] != 0 || off[n_gates] != n_events))
-    report_error(err, GTP_EINVAL, -1);
-}
-}  // namespace
-
 int gtp_load_netlist(gtp_ctx* ctx, int64_t n_gates, const int32_t* cell, const float* load_ff,
                      const float* slew_ps, int32_t slew_stride, int flags) {
   if (!ctx) return GTP_EINVAL;
   if (!ctx->lib_loaded) return fail(ctx, GTP_EINVAL, "load_netlist: load the library first");
   if (n_gates <= 0 || n_gates >= (1ll << 31) || !cell || !load_ff || !slew_ps)
     return fail(ctx, GTP_EINVAL, "load_netlist: need 1 <= n_gates < 2^31 and non-null arrays");
-  if (slew_stride < ctx->max_in) return fail(ctx, GTP_EINVAL, "load_netlist: slew_stride < max input pins");
+  if (slew_stride < ctx->max_in || slew_stride > GTP_MAX_PINS)
+    return fail(ctx, GTP_EINVAL, "load_netlist: slew_stride must cover the widest cell (and be <= 8)");
   DeviceGuard dg(ctx->device);
-  cudaMemcpyKind k = kind_in(flags);
+  CU(cudaStreamSynchronize(ctx->stream), "load_netlist");
+  drop_graphs(ctx);
+  const cudaMemcpyKind k = kind_in(flags);
   CU(ctx->cell.reserve(sizeof(int32_t) * n_gates), "alloc cell");
   CU(ctx->load.reserve(sizeof(float) * n_gates), "alloc load");
   CU(ctx->slew.reserve(sizeof(float) * 2 * slew_stride * n_gates), "alloc slew");
@@ -435,15 +626,19 @@ int gtp_load_netlist(gtp_ctx* ctx, int64_t n_gates, const int32_t* cell, const f
   CU(cudaMemcpyAsync(ctx->load.p, load_ff, sizeof(float) * n_gates, k, ctx->stream), "copy load");
   CU(cudaMemcpyAsync(ctx->slew.p, slew_ps, sizeof(float) * 2 * slew_stride * n_gates, k, ctx->stream), "copy slew");
   CU(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(DevError), ctx->stream), "zero status");
-  k_check_cells<<<1024, 256, 0, ctx->stream>>>(ctx->cell.as<int32_t>(), n_gates, ctx->L.n_cells, ctx->d_err.as<DevError>());
+  k_check_cells<<<1024, 256, 0, ctx->stream>>>(ctx->cell.as<int32_t>(), n_gates, ctx->L.n_cells,
+                                                ctx->d_err.as<DevError>());
   CU(cudaGetLastError(), "check cells");
-  int rc = check_device_error(ctx, "load_netlist");
+  ctx->launches += 1;
+  const int rc = check_device_error(ctx, "load_netlist");
   if (rc != GTP_OK) return fail(ctx, GTP_ERANGE, "load_netlist: cell index out of range");
   ctx->N.cell = ctx->cell.as<int32_t>();
   ctx->N.load = ctx->load.as<float>();
   ctx->N.slew = ctx->slew.as<float>();
   ctx->N.n_gates = n_gates;
   ctx->N.stride = slew_stride;
+  RC(ensure_netlist_coords(ctx));
+  CU(cudaStreamSynchronize(ctx->stream), "load_netlist");
   ctx->net_loaded = true;
   for (auto& kv : ctx->windows) kv.second.release();
   ctx->windows.clear();
@@ -455,6 +650,7 @@ int gtp_set_load(gtp_ctx* ctx, const float* load_ff, int flags) {
   if (!ctx->net_loaded || !load_ff) return fail(ctx, GTP_EINVAL, "set_load: no netlist or null array");
   DeviceGuard dg(ctx->device);
   CU(cudaMemcpyAsync(ctx->load.p, load_ff, sizeof(float) * ctx->N.n_gates, kind_in(flags), ctx->stream), "copy load");
+  RC(ensure_netlist_coords(ctx));
   CU(cudaStreamSynchronize(ctx->stream), "set_load");
   return GTP_OK;
 }
@@ -463,21 +659,23 @@ int gtp_load_events(gtp_ctx* ctx, int32_t window, int64_t window_ps, int64_t n_e
                     const gtp_event* events, const uint8_t* init_state, int flags) {
   if (!ctx) return GTP_EINVAL;
   if (!ctx->net_loaded) return fail(ctx, GTP_EINVAL, "load_events: load the netlist first");
-  if (window < 0 || window >= 1024) return fail(ctx, GTP_EINVAL, "load_events: window slot must be 0..1023");
-  if (window_ps <= 0 || window_ps >= (1ll << 31)) return fail(ctx, GTP_ERANGE, "load_events: window_ps must be in (0, 2^31)");
+  if (window < 0 || window >= kMaxWindows) return fail(ctx, GTP_EINVAL, "load_events: window slot must be 0..1023");
+  if (window_ps <= 0 || window_ps >= (1ll << 31))
+    return fail(ctx, GTP_ERANGE, "load_events: window_ps must be in (0, 2^31)");
   if (n_events < 0 || !gate_offsets || !init_state || (n_events > 0 && !events))
     return fail(ctx, GTP_EINVAL, "load_events: null array or negative n_events");
-  bool borrow = (flags & GTP_BORROW) != 0;
+  const bool borrow = (flags & GTP_BORROW) != 0;
   if (borrow && !(flags & GTP_DEVICE)) return fail(ctx, GTP_EINVAL, "load_events: GTP_BORROW needs GTP_DEVICE");
-  if (borrow && (((uintptr_t)events) & 15)) return fail(ctx, GTP_EINVAL, "load_events: borrowed events must be 16-byte aligned");
+  if (borrow && (((uintptr_t)events) & 15))
+    return fail(ctx, GTP_EINVAL, "load_events: borrowed events must be 16-byte aligned");
   DeviceGuard dg(ctx->device);
-  int64_t G = ctx->N.n_gates;
+  const int64_t G = ctx->N.n_gates;
   Window& W = ctx->windows[window];
   // buffers are kept and grown as needed, so reloading a slot does not reallocate
   W.loaded = false;
   W.has_result = false;
   W.borrowed = nullptr;
-  cudaMemcpyKind k = kind_in(flags);
+  const cudaMemcpyKind k = kind_in(flags);
   CU(W.offsets.reserve(sizeof(int64_t) * (G + 1)), "alloc offsets");
   CU(W.init.reserve((size_t)G), "alloc init");
   CU(cudaMemcpyAsync(W.offsets.p, gate_offsets, sizeof(int64_t) * (G + 1), k, ctx->stream), "copy offsets");
@@ -485,8 +683,8 @@ int gtp_load_events(gtp_ctx* ctx, int32_t window, int64_t window_ps, int64_t n_e
   if (borrow) {
     W.borrowed = reinterpret_cast<const uint2*>(events);
   } else {
-    // pad to an even number of records so 16-byte vector loads stay in bounds
-    size_t bytes = sizeof(uint2) * (size_t)(n_events + 2);
+    // padded by two records so that 16-byte vector loads stay in bounds
+    const size_t bytes = sizeof(uint2) * (size_t)(n_events + 2);
     CU(W.records.reserve(bytes), "alloc records");
     CU(cudaMemsetAsync(W.records.as<uint2>() + n_events, 0, 2 * sizeof(uint2), ctx->stream), "zero padding");
     if (n_events > 0)
@@ -496,8 +694,9 @@ int gtp_load_events(gtp_ctx* ctx, int32_t window, int64_t window_ps, int64_t n_e
   k_check_offsets<<<1024, 256, 0, ctx->stream>>>(W.offsets.as<int64_t>(), G, n_events, ctx->d_err.as<DevError>());
   CU(cudaGetLastError(), "check offsets");
   ctx->launches += 1;
-  int rc = check_device_error(ctx, "load_events");
-  if (rc != GTP_OK) return fail(ctx, GTP_EINVAL, "load_events: offsets must start at 0, end at n_events and not decrease");
+  const int rc = check_device_error(ctx, "load_events");
+  if (rc != GTP_OK)
+    return fail(ctx, GTP_EINVAL, "load_events: offsets must start at 0, end at n_events and not decrease");
   W.window_ps = window_ps;
   W.n_events = n_events;
   W.loaded = true;
@@ -506,40 +705,21 @@ int gtp_load_events(gtp_ctx* ctx, int32_t window, int64_t window_ps, int64_t n_e
 
 int gtp_run_power(gtp_ctx* ctx, int32_t window, int32_t bin_ps, double* waveform_w, int flags) {
   if (!ctx) return GTP_EINVAL;
-  Window* W = get_window(ctx, window);
-  if (!W) return fail(ctx, GTP_EINVAL, "run_power: window not loaded");
   DeviceGuard dg(ctx->device);
-  Outputs O;
-  int rc = prepare_outputs(ctx, *W, bin_ps, &O);
-  if (rc) return rc;
-  double* wave = nullptr;
-  if (waveform_w) {
-    if (flags & GTP_DEVICE) {
-      wave = waveform_w;
-    } else {
-      CU(W->wave.reserve(sizeof(double) * (size_t)O.n_bins), "alloc waveform");
-      wave = W->wave.as<double>();
-    }
-  }
-  CU(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(DevError), ctx->stream), "zero status");
-  rc = enqueue_forward(ctx, *W, O, wave);
-  if (rc) return rc;
-  if (waveform_w && !(flags & GTP_DEVICE))
-    CU(cudaMemcpyAsync(waveform_w, wave, sizeof(double) * (size_t)O.n_bins, cudaMemcpyDeviceToHost, ctx->stream),
-       "copy waveform");
-  rc = check_device_error(ctx, "run_power");
-  collect_timing(ctx);
-  W->has_result = (rc == GTP_OK);
-  W->last_bin_ps = bin_ps;
-  return rc;
+  double* const waves[1] = {waveform_w};
+  return run_forward(ctx, &window, 1, bin_ps, waves, flags, false);
 }
 
-namespace {
-__global__ void k_counts(const int64_t* off, int64_t n, int64_t* out) {
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
-    out[g] = off[g + 1] - off[g];
+int gtp_run_power_batched(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_t bin_ps,
+                          double* const* waveforms, int flags) {
+  if (!ctx) return GTP_EINVAL;
+  if (n_windows <= 0 || n_windows > kMaxWindows || !windows || !waveforms)
+    return fail(ctx, GTP_EINVAL, "run_power_batched: bad arguments");
+  if ((flags & GTP_GRAPH) && !(flags & GTP_DEVICE))
+    return fail(ctx, GTP_EINVAL, "run_power_batched: graph replay needs device waveforms");
+  DeviceGuard dg(ctx->device);
+  return run_forward(ctx, windows, n_windows, bin_ps, waveforms, flags, (flags & GTP_GRAPH) != 0);
 }
-}  // namespace
 
 int gtp_gate_energy(gtp_ctx* ctx, int32_t window, double* e_leak, double* e_int, double* e_sw, int64_t* n_events,
                     uint8_t* final_state, int flags) {
@@ -547,8 +727,8 @@ int gtp_gate_energy(gtp_ctx* ctx, int32_t window, double* e_leak, double* e_int,
   Window* W = get_window(ctx, window);
   if (!W || !W->has_result) return fail(ctx, GTP_EINVAL, "gate_energy: no result for this window");
   DeviceGuard dg(ctx->device);
-  int64_t G = ctx->N.n_gates;
-  cudaMemcpyKind k = kind_out(flags);
+  const int64_t G = ctx->N.n_gates;
+  const cudaMemcpyKind k = kind_out(flags);
   if (e_leak) CU(cudaMemcpyAsync(e_leak, W->e_leak.p, sizeof(double) * G, k, ctx->stream), "copy e_leak");
   if (e_int) CU(cudaMemcpyAsync(e_int, W->e_int.p, sizeof(double) * G, k, ctx->stream), "copy e_int");
   if (e_sw) CU(cudaMemcpyAsync(e_sw, W->e_sw.p, sizeof(double) * G, k, ctx->stream), "copy e_sw");
@@ -570,63 +750,122 @@ int gtp_gate_energy(gtp_ctx* ctx, int32_t window, double* e_leak, double* e_int,
   return GTP_OK;
 }
 
-int gtp_run_power_batched(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_t bin_ps,
-                          double* const* waveforms, int flags) {
-  if (!ctx) return GTP_EINVAL;
-  if (n_windows <= 0 || !windows || !waveforms) return fail(ctx, GTP_EINVAL, "run_power_batched: bad arguments");
-  DeviceGuard dg(ctx->device);
-  std::vector<Window*> ws(n_windows);
-  std::vector<Outputs> os(n_windows);
-  for (int i = 0; i < n_windows; ++i) {
-    ws[i] = get_window(ctx, windows[i]);
-    if (!ws[i]) return fail(ctx, GTP_EINVAL, "run_power_batched: window not loaded");
-    int rc = prepare_outputs(ctx, *ws[i], bin_ps, &os[i]);
-    if (rc) return rc;
-  }
-  CU(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(DevError), ctx->stream), "zero status");
-  for (int i = 0; i < n_windows; ++i) {
-    double* wave = nullptr;
-    if (waveforms[i]) {
-      if (flags & GTP_DEVICE) {
-        wave = waveforms[i];
-      } else {
-        CU(ws[i]->wave.reserve(sizeof(double) * (size_t)os[i].n_bins), "alloc waveform");
-        wave = ws[i]->wave.as<double>();
-      }
-    }
-    int rc = enqueue_forward(ctx, *ws[i], os[i], wave);
-    if (rc) return rc;
-    if (waveforms[i] && !(flags & GTP_DEVICE))
-      CU(cudaMemcpyAsync(waveforms[i], wave, sizeof(double) * (size_t)os[i].n_bins, cudaMemcpyDeviceToHost,
-                         ctx->stream), "copy waveform");
-  }
-  int rc = check_device_error(ctx, "run_power_batched");
-  for (int i = 0; i < n_windows; ++i) {
-    ws[i]->has_result = (rc == GTP_OK);
-    ws[i]->last_bin_ps = bin_ps;
-  }
-  return rc;
-}
-
 int gtp_run_power_backward(gtp_ctx* ctx, int32_t window, int32_t bin_ps, const float* dL_dP, float* dC,
                            float* d_escale, float* d_lscale) {
   if (!ctx) return GTP_EINVAL;
-  (void)window; (void)bin_ps; (void)dL_dP; (void)dC; (void)d_escale; (void)d_lscale;
-  return fail(ctx, GTP_EINVAL, "run_power_backward: not available in this build");
+  Window* W = get_window(ctx, window);
+  if (!W) return fail(ctx, GTP_EINVAL, "run_power_backward: window not loaded");
+  if (!dL_dP) return fail(ctx, GTP_EINVAL, "run_power_backward: dL_dP is required");
+  if (bin_ps <= 0 || W->window_ps % bin_ps != 0)
+    return fail(ctx, GTP_ERANGE, "window_ps must be a multiple of bin_ps > 0");
+  DeviceGuard dg(ctx->device);
+  const int64_t nb = W->window_ps / bin_ps;
+  const int nt = merge_tiles((int)nb);
+  const int64_t G = ctx->N.n_gates;
+  CU(ctx->grad.reserve(sizeof(float2) * nb), "alloc grad");
+  CU(ctx->gtiles.reserve(sizeof(double) * nt), "alloc grad tiles");
+  float* dc = dC;
+  if (!dc) {
+    CU(ctx->dC_scratch.reserve(sizeof(float) * G), "alloc dC");
+    dc = ctx->dC_scratch.as<float>();
+  }
+  std::vector<Window*> ws{W};
+  std::vector<double*> waves;
+  int64_t n_seg_total = 0, n_tiles_total = 0;
+  RC(build_plan(ctx, ws, bin_ps, waves, true, &n_seg_total, &n_tiles_total));
+  plan_wins(ctx->h_plan)[0].dC = dc;
+  cudaStream_t st = ctx->stream;
+  CU(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(DevError), st), "zero status");
+  RC(upload_plan(ctx, 1, st));
+  CU(cudaMemsetAsync(dc, 0, sizeof(float) * G, st), "zero dC");
+  CU(cudaMemsetAsync(ctx->cell_acc.p, 0, sizeof(double) * 2 * ctx->L.n_cells, st), "zero cell sums");
+  CU(launch_grad_prep(plan_wins(ctx->plan.p), dL_dP, ctx->grad.as<float2>(), ctx->gtiles.as<double>(), nt, (int)nb,
+                      bin_ps, &plan_wins(ctx->plan.p)[0].g_total, st), "gradient prefix");
+  CU(launch_gate_pass_bwd(ctx->L, ctx->N, plan_wins(ctx->plan.p), ctx->cell_acc.as<double>(), st), "gate pass");
+  ctx->launches += 4;
+  if (W->n_events > 0) {
+    const WalkArgs A = walk_args(ctx, 1, n_seg_total);
+    CU(launch_seeds(ctx->N, ctx->L, A, ctx->runs.as<int64_t>(), st), "seeds");
+    CU(launch_walk(ctx->L, ctx->N, A, true, st), "adjoint walk");
+    ctx->launches += 4;
+  }
+  if (d_escale || d_lscale) {
+    CU(launch_cells_out(ctx->cell_acc.as<double>(), ctx->L.n_cells, d_escale, d_lscale, st), "cell gradients");
+    ctx->launches += 1;
+  }
+  return check_device_error(ctx, "run_power_backward");
+}
+
+int gtp_autotune(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_t bin_ps, int32_t iters,
+                 double* best_ms) {
+  if (!ctx) return GTP_EINVAL;
+  if (n_windows <= 0 || n_windows > kMaxWindows || !windows) return fail(ctx, GTP_EINVAL, "autotune: bad arguments");
+  DeviceGuard dg(ctx->device);
+  if (iters <= 0) iters = 3;
+  const int64_t keep_kernel = ctx->p_kernel;
+  const bool keep_timing = ctx->timing;
+  ctx->p_kernel = 0;
+  ctx->timing = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CU(cudaEventCreate(&e0), "event");
+  CU(cudaEventCreate(&e1), "event");
+  double best = 1e300;
+  int64_t br = ctx->p_rpt, bb = ctx->p_block, bc = ctx->p_ctas_per_sm;
+  std::vector<double*> none(n_windows, nullptr);
+  const int rpts[] = {4, 8, 16};
+  const int blocks[] = {128, 256};
+  const int ctas[] = {0, 1, 2, 4};
+  int rc = GTP_OK;
+  for (int r : rpts) {
+    for (int b : blocks) {
+      for (int c : ctas) {
+        ctx->p_rpt = r;
+        ctx->p_block = b;
+        ctx->p_ctas_per_sm = c;
+        rc = run_forward(ctx, windows, n_windows, bin_ps, none.data(), GTP_DEVICE, false);  // warm-up
+        if (rc != GTP_OK) break;
+        cudaEventRecord(e0, ctx->stream);
+        for (int it = 0; it < iters && rc == GTP_OK; ++it)
+          rc = run_forward(ctx, windows, n_windows, bin_ps, none.data(), GTP_DEVICE, false);
+        cudaEventRecord(e1, ctx->stream);
+        cudaEventSynchronize(e1);
+        if (rc != GTP_OK) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms / iters < best) {
+          best = ms / iters;
+          br = r;
+          bb = b;
+          bc = c;
+        }
+      }
+      if (rc != GTP_OK) break;
+    }
+    if (rc != GTP_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->p_rpt = br;
+  ctx->p_block = bb;
+  ctx->p_ctas_per_sm = bc;
+  ctx->p_kernel = keep_kernel;
+  ctx->timing = keep_timing;
+  if (best_ms) *best_ms = best;
+  return rc;
 }
 
 int gtp_set_param(gtp_ctx* ctx, const char* key, int64_t value) {
   if (!ctx || !key) return GTP_EINVAL;
-  std::string k(key);
+  const std::string k(key);
   if (k == "kernel") {
     if (value > 1) return fail(ctx, GTP_ERANGE, "kernel must be 0 or 1");
     ctx->p_kernel = value < 0 ? 0 : value;
   } else if (k == "records_per_thread") {
-    if (value >= 0 && !seg_rpt_supported((int)value)) return fail(ctx, GTP_ERANGE, "records_per_thread must be 4, 8 or 16");
+    if (value >= 0 && !walk_rpt_supported((int)value))
+      return fail(ctx, GTP_ERANGE, "records_per_thread must be 4, 8 or 16");
     ctx->p_rpt = value < 0 ? 8 : value;
   } else if (k == "block_threads") {
-    if (value >= 0 && value != 128 && value != 256)
-      return fail(ctx, GTP_ERANGE, "block_threads must be 128 or 256");
+    if (value >= 0 && value != 128 && value != 256) return fail(ctx, GTP_ERANGE, "block_threads must be 128 or 256");
     ctx->p_block = value < 0 ? 256 : value;
   } else if (k == "ctas_per_sm") {
     if (value > 32) return fail(ctx, GTP_ERANGE, "ctas_per_sm must be <= 32");
@@ -648,7 +887,7 @@ int gtp_set_param(gtp_ctx* ctx, const char* key, int64_t value) {
 
 int64_t gtp_get_param(const gtp_ctx* ctx, const char* key) {
   if (!ctx || !key) return -1;
-  std::string k(key);
+  const std::string k(key);
   if (k == "kernel") return ctx->p_kernel;
   if (k == "records_per_thread") return ctx->p_rpt;
   if (k == "block_threads") return ctx->p_block;

@@ -1,16 +1,20 @@
 // Internal definitions shared by the engine's translation units.
 //
 // Device data layout (per context):
-//   library   tab[n_tab_floats] (fJ, unscaled), leak[n_leak] (nW, unscaled),
-//             cell_info[n_cells] = {tab_base (first table of the cell),
-//             leak_base, n_in}, table_cell[n_tables], leak_cell[n_leak]
-//             (owning cell of each table / leakage entry, for scaling),
-//             escale[n_cells], lscale[n_cells]
-//   netlist   cell[G] int32, load[G] float, slew[G][stride][2] float
-//   window    offsets[G+1] int64, records[E] (8 B: int32 t, uint32 meta),
-//             init[G] uint8, segment seeds, per-gate outputs (FP64 energies,
-//             uint8 final state), bin accumulators float2[n_bins] =
-//             {dynamic + in-bin leakage energy (fJ), leakage-power step (nW)}
+//   library   tab[n_tables * ns * nl] (fJ, unscaled), leak[n_leak] (nW,
+//             unscaled), cells[n_cells] = {first table, first leakage entry,
+//             n_in}, table_cell[n_tables], leak_cell[n_leak] (owning cell of
+//             each table / leakage entry, for scaling), escale/lscale[n_cells]
+//   netlist   cell[G] int32, load[G] float, slew[G][stride][2] float, and the
+//             interpolation coordinates derived from them once per netlist:
+//             coord[G][stride][2] = {slew fraction, corner offset of the table
+//             cell (slew segment * nl + load segment)}, wld[G] = load fraction,
+//             rwl[G] = 1 / width of the gate's load segment
+//   window    offsets[G+1] int64, records[E] 8 B {int32 t, uint32 meta},
+//             init[G] uint8, segment seeds (16 B per segment), per-gate
+//             outputs (FP64 energies, uint8 final state), and the bin
+//             accumulators float2[n_bins] = {dynamic + in-bin leakage energy
+//             (fJ), leakage-power step (nW)}
 #pragma once
 
 #include <cstdint>
@@ -54,6 +58,9 @@ struct NetView {
   const int32_t* cell;
   const float* load;
   const float* slew;         // [G][stride][2]
+  const float2* coord;       // [G][stride][2] {slew fraction, corner offset as float bits}
+  const float* wld;          // [G] load fraction
+  const float* rwl;          // [G] 1 / load segment width
   int64_t n_gates;
   int32_t stride;
 };
@@ -65,7 +72,7 @@ struct DevError {
   int64_t index;
 };
 
-// Per-segment seed for the segmented walk (16 bytes).
+// Per-segment seed of the segmented walk (16 bytes).
 struct Seed {
   int32_t gate;      // gate holding the segment's first record
   int32_t t_prev;    // time of the group before the first record's group (0 at gate start)
@@ -77,41 +84,42 @@ struct Seed {
 };
 constexpr uint8_t kSeedGateStart = 1;   // first record starts its gate
 constexpr uint8_t kSeedGroupHead = 2;   // first record starts its timestamp group
-constexpr uint8_t kSeedUnresolved = 4;  // x / p still partial (keep masks pending)
+constexpr uint8_t kSeedUnresolved = 4;  // the bounded backward scan left pins open
 
-struct WindowView {
+// One stimulus window as the kernels see it (single, batched and adjoint
+// runs all use an array of these in device memory).
+struct WinDesc {
   const int64_t* offsets;    // [G+1]
-  const uint2* rec;          // [E] {t, meta}
+  const uint2* rec;          // [E]
   const uint8_t* init;       // [G]
-  int64_t n_events;
-  int32_t window_ps;
-};
-
-struct Outputs {
+  Seed* seeds;               // [n_seg]
   double* e_leak;            // [G]
   double* e_int;             // [G]
   double* e_sw;              // [G]
   uint8_t* final_state;      // [G]
-  float2* bins;              // [n_bins]
-  double* l0;                // [1] sum over gates of P_leak(init) (nW)
-  DevError* err;
+  float2* bins;              // [n_bins] accumulators
+  double* l0;                // sum over gates of P_leak(initial state), nW
+  double* tiles;             // merge scratch
+  double* wave;              // [n_bins] output waveform (W), or null
+  const float2* grad;        // adjoint: [n_bins] {dL/dE_b, G(b * bin_ps)}
+  float* dC;                 // adjoint: [G]
+  int64_t n_events;
+  int64_t seg_base;          // first global segment of this window
+  int64_t n_seg;
+  int64_t tile_base;         // first global merge tile of this window
+  int32_t n_tiles;
+  int32_t window_ps;
   int32_t bin_ps;
-  uint32_t bin_magic;        // t / bin_ps == __umulhi(t, magic) >> shift for t < 2^31
+  uint32_t bin_magic;        // see bin_of()
   uint32_t bin_shift;
   int32_t n_bins;
+  float g_total;             // adjoint: G(window_ps)
+  int32_t pad;
 };
 
 // ------------------------------------------------------------------ device helpers
 __device__ __forceinline__ void report_error(DevError* err, int code, int64_t index) {
   if (atomicCAS(&err->code, 0, code) == 0) err->index = index;
-}
-
-__device__ __forceinline__ int segment_of(const float* axis, int n, float x) {
-  int i = 0;
-#pragma unroll
-  for (int k = 1; k < kMaxAxis - 1; ++k)
-    if (k < n - 1) i += (x >= axis[k]) ? 1 : 0;
-  return i;
 }
 
 // Side-input bits: input pins other than `pin`, compacted in pin order.
@@ -122,38 +130,12 @@ __device__ __forceinline__ uint32_t side_bits(uint32_t S, uint32_t pin, uint32_t
   return (low | high) & (in_mask >> 1);
 }
 
-// Shared-memory copy of the (scaled) library.  Layout in dynamic smem:
-// [axes: 4 x kMaxAxis floats][tab: n_tab_floats][leak: n_leak][cells].
-struct SmemLib {
-  const float* axes;  // slew axis, load axis, slew 1/width, load 1/width
-  const float* tab;
-  const float* leak;
-  const CellInfo* cells;
-};
-
-// Bilinear NLDM interpolation of one table at (slew, load); the located
-// segment is clamped to the axis so that outside points extrapolate linearly.
-__device__ __forceinline__ float bilinear(const LibView& L, const SmemLib& sl, const float* table, float slew,
-                                          float load) {
-  const float* sa = sl.axes;
-  const float* la = sl.axes + kMaxAxis;
-  int i = segment_of(sa, L.ns, slew);
-  int j = segment_of(la, L.nl, load);
-  float fs = (slew - sa[i]) * sa[2 * kMaxAxis + i];
-  float fl = (load - la[j]) * la[2 * kMaxAxis + j];
-  const float* r0 = table + i * L.nl + j;
-  const float* r1 = r0 + L.nl;
-  float a = fmaf(fl, r0[1] - r0[0], r0[0]);
-  float b = fmaf(fl, r1[1] - r1[0], r1[0]);
-  return fmaf(fs, b - a, a);
-}
-
 // floor(t / bin_ps) for 0 <= t < 2^31: the multiply-high estimate is q or
 // q - 1 (magic = min(floor(2^(32+s) / d), 2^32 - 1), s = floor(log2 d)), and
 // one correction step makes it exact.
-__device__ __forceinline__ uint32_t bin_of(const Outputs& O, uint32_t t) {
-  uint32_t b = __umulhi(t, O.bin_magic) >> O.bin_shift;
-  return b + (((b + 1u) * (uint32_t)O.bin_ps <= t) ? 1u : 0u);
+__device__ __forceinline__ uint32_t bin_of(uint32_t t, uint32_t magic, uint32_t shift, uint32_t bin_ps) {
+  uint32_t b = __umulhi(t, magic) >> shift;
+  return b + (((b + 1u) * bin_ps <= t) ? 1u : 0u);
 }
 
 // Fire-and-forget vector add of {energy, leakage step} into one bin.
@@ -174,19 +156,39 @@ struct Kahan {
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
-size_t smem_lib_bytes(const LibView& L);
+// Shared-memory copy of the library: [axes 4 x kMaxAxis][tab][leak][cells][escale].
+struct SmemLib {
+  const float* axes;  // slew axis, load axis, slew 1/width, load 1/width
+  const float* tab;
+  const float* leak;
+  const CellInfo* cells;
+  const float* escale;
+};
 
-// Stage the library into dynamic shared memory, applying the per-cell
-// scales; all threads of the block participate; ends with __syncthreads().
-__device__ __forceinline__ SmemLib stage_library(const LibView& L, unsigned char* smem) {
+__host__ __device__ inline size_t smem_lib_bytes(const LibView& L) {
+  size_t b = sizeof(float) * 4 * kMaxAxis + (size_t)L.n_tables * L.tsize * 4 + (size_t)((L.n_leak + 3) & ~3) * 4 +
+             (size_t)L.n_cells * (sizeof(CellInfo) + sizeof(float));
+  return (b + 15) & ~(size_t)15;
+}
+
+// Stage the library into dynamic shared memory.  With `scaled`, tables and
+// leakage are multiplied by the per-cell scales (forward); without, they are
+// copied unscaled (adjoint).  All threads participate; ends with a barrier.
+__device__ __forceinline__ SmemLib stage_library(const LibView& L, unsigned char* smem, bool scaled) {
   float* axes = reinterpret_cast<float*>(smem);
   float* tab = axes + 4 * kMaxAxis;
   float* leak = tab + (size_t)L.n_tables * L.tsize;
   CellInfo* cells = reinterpret_cast<CellInfo*>(leak + ((L.n_leak + 3) & ~3));
+  float* esc = reinterpret_cast<float*>(cells + L.n_cells);
   int nt = L.n_tables * L.tsize;
-  for (int k = threadIdx.x; k < nt; k += blockDim.x) tab[k] = L.tab[k] * L.escale[L.table_cell[k / L.tsize]];
-  for (int k = threadIdx.x; k < L.n_leak; k += blockDim.x) leak[k] = L.leak[k] * L.lscale[L.leak_cell[k]];
-  for (int k = threadIdx.x; k < L.n_cells; k += blockDim.x) cells[k] = L.cells[k];
+  for (int k = threadIdx.x; k < nt; k += blockDim.x)
+    tab[k] = scaled ? L.tab[k] * L.escale[L.table_cell[k / L.tsize]] : L.tab[k];
+  for (int k = threadIdx.x; k < L.n_leak; k += blockDim.x)
+    leak[k] = scaled ? L.leak[k] * L.lscale[L.leak_cell[k]] : L.leak[k];
+  for (int k = threadIdx.x; k < L.n_cells; k += blockDim.x) {
+    cells[k] = L.cells[k];
+    esc[k] = L.escale[k];
+  }
   if (threadIdx.x < kMaxAxis) {
     axes[threadIdx.x] = L.slew_axis[threadIdx.x];
     axes[kMaxAxis + threadIdx.x] = L.load_axis[threadIdx.x];
@@ -194,16 +196,26 @@ __device__ __forceinline__ SmemLib stage_library(const LibView& L, unsigned char
     axes[3 * kMaxAxis + threadIdx.x] = L.load_rw[threadIdx.x];
   }
   __syncthreads();
-  return SmemLib{axes, tab, leak, cells};
+  return SmemLib{axes, tab, leak, cells, esc};
 }
 
 // ------------------------------------------------------------------ launchers (host)
-// Each returns cudaError_t of the launch.
-cudaError_t launch_gate_pass(const LibView& L, const NetView& N, const WindowView& W, const Outputs& O,
+cudaError_t launch_interp_coords(const LibView& L, NetView N, float2* coord, float* wld, float* rwl,
+                                 cudaStream_t st);
+cudaError_t launch_gate_pass(const LibView& L, const NetView& N, const WinDesc* wins, int n_win, DevError* err,
                              cudaStream_t st);
-cudaError_t launch_walk_per_gate(const LibView& L, const NetView& N, const WindowView& W, const Outputs& O,
-                                 int block, cudaStream_t st);
-cudaError_t launch_merge(const Outputs& O, double* waveform_w, double* tile_sums, int n_tiles, cudaStream_t st);
+cudaError_t launch_gate_pass_bwd(const LibView& L, const NetView& N, const WinDesc* wins, double* cell_acc,
+                                 cudaStream_t st);
+cudaError_t launch_walk_per_gate(const LibView& L, const NetView& N, const WinDesc* wins, int n_win,
+                                 DevError* err, cudaStream_t st);
+cudaError_t launch_merge(const WinDesc* wins, const int64_t* tile_base, int n_win, int64_t n_tiles_total,
+                         cudaStream_t st);
+// Adjoint input: grad[b] = {dL/dP_b * 1e-3 / bin_ps, G(b * bin_ps)}, and G(T).
+cudaError_t launch_grad_prep(const WinDesc* wins, const float* dLdP, float2* grad, double* tiles, int n_tiles,
+                             int n_bins, int bin_ps, float* g_total, cudaStream_t st);
+cudaError_t launch_zero_bins(const WinDesc* wins, const int64_t* tile_base, int n_win, int64_t n_tiles_total,
+                             cudaStream_t st);
+cudaError_t launch_cells_out(const double* acc, int n_cells, float* d_escale, float* d_lscale, cudaStream_t st);
 int merge_tiles(int n_bins);
 
 }  // namespace gtp

@@ -1,4 +1,5 @@
-// Gate pass, one-thread-per-gate walk, and the FP64 bin merge.
+// Interpolation coordinates, gate pass, one-thread-per-gate walk, the FP64
+// bin merge, and the adjoint's gradient prefix.
 //
 // Leakage in the waveform uses a step representation: the design's leakage
 // power is a step function of time, L(t) = L0 + sum_k dP_k [t >= t_k], where
@@ -16,31 +17,94 @@
 
 namespace gtp {
 
+namespace {
+
+__device__ __forceinline__ int segment_of(const float* axis, int n, float x) {
+  int i = 0;
+  while (i < n - 2 && x >= axis[i + 1]) ++i;
+  return i;
+}
+
+// Window of a global index given ascending bases (n_win + 1 entries).
+__device__ __forceinline__ int window_of(const int64_t* base, int n_win, int64_t x) {
+  int lo = 0, hi = n_win - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (base[mid] <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ interpolation coordinates
+// The NLDM lookup point of every (gate, input pin, edge) is static: its
+// slew segment and fraction, and the gate's load segment and fraction, are
+// located once per netlist (or load update) instead of once per event.
+__global__ void k_interp_coords(LibView L, NetView N, float2* __restrict__ coord, float* __restrict__ wld,
+                                float* __restrict__ rwl) {
+  __shared__ float ax[4 * kMaxAxis];
+  if (threadIdx.x < kMaxAxis) {
+    ax[threadIdx.x] = L.slew_axis[threadIdx.x];
+    ax[kMaxAxis + threadIdx.x] = L.load_axis[threadIdx.x];
+    ax[2 * kMaxAxis + threadIdx.x] = L.slew_rw[threadIdx.x];
+    ax[3 * kMaxAxis + threadIdx.x] = L.load_rw[threadIdx.x];
+  }
+  __syncthreads();
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N.n_gates;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int n_in = L.cells[N.cell[g]].n_in;
+    const float C = N.load[g];
+    const int j = segment_of(ax + kMaxAxis, L.nl, C);
+    wld[g] = (C - ax[kMaxAxis + j]) * ax[3 * kMaxAxis + j];
+    rwl[g] = ax[3 * kMaxAxis + j];
+    for (int p = 0; p < N.stride; ++p) {
+      for (int e = 0; e < 2; ++e) {
+        float2 c = make_float2(0.f, 0.f);
+        if (p < n_in) {
+          const float s = N.slew[((size_t)g * N.stride + p) * 2 + e];
+          const int i = segment_of(ax, L.ns, s);
+          c.x = (s - ax[i]) * ax[2 * kMaxAxis + i];
+          c.y = __uint_as_float((uint32_t)(i * L.nl + j));
+        }
+        coord[((size_t)g * N.stride + p) * 2 + e] = c;
+      }
+    }
+  }
+}
+
+cudaError_t launch_interp_coords(const LibView& L, NetView N, float2* coord, float* wld, float* rwl,
+                                 cudaStream_t st) {
+  int64_t blocks = (N.n_gates + 255) / 256;
+  if (blocks > 8192) blocks = 8192;
+  k_interp_coords<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, st>>>(L, N, coord, wld, rwl);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ gate pass
-// Per gate: zero the energy accumulators, resolve gates without events
-// (leakage at the initial state over the whole window), and reduce
-// L0 = sum_g P_leak(cell_g, init_g) * lscale into O.l0.
-__global__ void k_gate_pass(LibView L, NetView N, WindowView W, Outputs O, int64_t* counts) {
+// Per (window, gate): zero the energy accumulators, resolve gates without
+// events (leakage at the initial state over the whole window), and reduce
+// L0 = sum_g P_leak(cell_g, init_g) * lscale into the window's l0.
+__global__ void k_gate_pass(LibView L, NetView N, const WinDesc* __restrict__ wins, DevError* err) {
+  const WinDesc& W = wins[blockIdx.y];
   double p0 = 0.0;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N.n_gates;
        g += (int64_t)gridDim.x * blockDim.x) {
-    int32_t c = N.cell[g];
-    CellInfo ci = L.cells[c];
+    const int32_t c = N.cell[g];
+    const CellInfo ci = L.cells[c];
     uint32_t s0 = W.init[g];
     if (s0 >> (ci.n_in + 1)) {
-      report_error(O.err, GTP_ERANGE, -1 - g);
+      report_error(err, GTP_ERANGE, -1 - g);
       s0 &= (2u << ci.n_in) - 1u;
     }
-    float P = L.leak[ci.leak_base + s0] * L.lscale[c];
+    const float P = L.leak[ci.leak_base + s0] * L.lscale[c];
     p0 += (double)P;
-    int64_t cnt = W.offsets[g + 1] - W.offsets[g];
-    if (counts) counts[g] = cnt;
-    O.e_leak[g] = cnt == 0 ? (double)P * (double)W.window_ps * 1e-6 : 0.0;
-    O.e_int[g] = 0.0;
-    O.e_sw[g] = 0.0;
-    O.final_state[g] = (uint8_t)s0;
+    const int64_t cnt = W.offsets[g + 1] - W.offsets[g];
+    W.e_leak[g] = cnt == 0 ? (double)P * (double)W.window_ps * 1e-6 : 0.0;
+    W.e_int[g] = 0.0;
+    W.e_sw[g] = 0.0;
+    W.final_state[g] = (uint8_t)s0;
   }
-  // block reduction of p0
   __shared__ double red[32];
   for (int o = 16; o > 0; o >>= 1) p0 += __shfl_down_sync(0xffffffffu, p0, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = p0;
@@ -48,41 +112,69 @@ __global__ void k_gate_pass(LibView L, NetView N, WindowView W, Outputs O, int64
   if (threadIdx.x < 32) {
     double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (threadIdx.x == 0) atomicAdd(O.l0, v);
+    if (threadIdx.x == 0) atomicAdd(W.l0, v);
   }
 }
 
-cudaError_t launch_gate_pass(const LibView& L, const NetView& N, const WindowView& W, const Outputs& O,
+// Adjoint of the gate pass: a gate without events leaks at its initial state
+// over the whole window, so d L / d lscale[c] gains P0(init) * G(T) * 1e-6.
+__global__ void k_gate_pass_bwd(LibView L, NetView N, const WinDesc* __restrict__ wins, double* __restrict__ cell_acc) {
+  const WinDesc& W = wins[0];
+  extern __shared__ double acc[];
+  for (int c = threadIdx.x; c < L.n_cells; c += blockDim.x) acc[c] = 0.0;
+  __syncthreads();
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N.n_gates;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    if (W.offsets[g + 1] != W.offsets[g]) continue;
+    const int32_t c = N.cell[g];
+    const CellInfo ci = L.cells[c];
+    const uint32_t s0 = W.init[g] & ((2u << ci.n_in) - 1u);
+    atomicAdd(acc + c, (double)L.leak[ci.leak_base + s0]);
+  }
+  __syncthreads();
+  const double gT = (double)W.g_total * 1e-6;
+  for (int c = threadIdx.x; c < L.n_cells; c += blockDim.x)
+    if (acc[c] != 0.0) atomicAdd(cell_acc + L.n_cells + c, acc[c] * gT);
+}
+
+cudaError_t launch_gate_pass_bwd(const LibView& L, const NetView& N, const WinDesc* wins, double* cell_acc,
+                                 cudaStream_t st) {
+  int64_t blocks = (N.n_gates + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  k_gate_pass_bwd<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, sizeof(double) * L.n_cells, st>>>(L, N, wins, cell_acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gate_pass(const LibView& L, const NetView& N, const WinDesc* wins, int n_win, DevError* err,
                              cudaStream_t st) {
-  (void)0;
-  int block = 256;
-  int64_t blocks = (N.n_gates + block - 1) / block;
-  if (blocks > 4096) blocks = 4096;
-  if (blocks < 1) blocks = 1;
-  k_gate_pass<<<(unsigned)blocks, block, 0, st>>>(L, N, W, O, nullptr);
+  int64_t blocks = (N.n_gates + 255) / 256;
+  if (blocks > 2048) blocks = 2048;
+  dim3 grid((unsigned)(blocks < 1 ? 1 : blocks), (unsigned)n_win);
+  k_gate_pass<<<grid, 256, 0, st>>>(L, N, wins, err);
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ one thread per gate
-// The plain walk of Algorithm 1, one gate per thread: timestamp groups with
-// lookups at the pre-group state, the state update after the group, leakage
-// held between groups.  Per-gate energies use Kahan-compensated FP32 sums.
-__global__ void k_walk_per_gate(LibView L, NetView N, WindowView W, Outputs O) {
+// The plain walk of Algorithm 1, one (window, gate) per thread: timestamp
+// groups with lookups at the pre-group state, the state update after the
+// group, leakage held between groups.  Kahan-compensated FP32 per-gate sums.
+// A simple cross-check of the segmented walk; it is not tuned.
+__global__ void k_walk_per_gate(LibView L, NetView N, const WinDesc* __restrict__ wins, DevError* err) {
   extern __shared__ __align__(16) unsigned char smem[];
-  SmemLib sl = stage_library(L, smem);
+  const SmemLib sl = stage_library(L, smem, true);
+  const WinDesc& W = wins[blockIdx.y];
   const float T = (float)W.window_ps;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N.n_gates;
        g += (int64_t)gridDim.x * blockDim.x) {
-    int64_t a = W.offsets[g], b = W.offsets[g + 1];
+    const int64_t a = W.offsets[g], b = W.offsets[g + 1];
     if (a == b) continue;
-    int32_t c = N.cell[g];
-    CellInfo ci = sl.cells[c];
-    uint32_t n_in = (uint32_t)ci.n_in, n_pins = n_in + 1;
+    const CellInfo ci = sl.cells[N.cell[g]];
+    const uint32_t n_in = (uint32_t)ci.n_in, n_pins = n_in + 1;
     const float* leak = sl.leak + ci.leak_base;
     const float* tabs = sl.tab + (size_t)ci.tab_base * L.tsize;
-    uint32_t n_side = 1u << (n_in - 1);
-    float C = N.load[g];
-    const float* slew = N.slew + (size_t)g * N.stride * 2;
+    const float C = N.load[g];
+    const float fl = N.wld[g];
+    const float2* crd = N.coord + (size_t)g * N.stride * 2;
     uint32_t st = W.init[g] & ((2u << n_in) - 1u);
     float P = leak[st];
     int32_t t_prev = 0;
@@ -90,27 +182,29 @@ __global__ void k_walk_per_gate(LibView L, NetView N, WindowView W, Outputs O) {
     bool bad = false;
     int64_t i = a;
     while (i < b) {
-      uint2 r0 = W.rec[i];
-      int32_t t = (int32_t)r0.x;
-      if (t < 0 || t >= W.window_ps) { report_error(O.err, GTP_ERANGE, i); bad = true; break; }
-      if (t < t_prev) { report_error(O.err, GTP_EORDER, i); bad = true; break; }
+      const int32_t t = (int32_t)W.rec[i].x;
+      if (t < 0 || t >= W.window_ps) { report_error(err, GTP_ERANGE, i); bad = true; break; }
+      if (t < t_prev) { report_error(err, GTP_EORDER, i); bad = true; break; }
       El.add(P * (float)(t - t_prev) * 1e-6f);
-      uint32_t bin = bin_of(O, (uint32_t)t);
+      const uint32_t bin = bin_of((uint32_t)t, W.bin_magic, W.bin_shift, (uint32_t)W.bin_ps);
       uint32_t s_next = st;
       float e_bin = 0.f;
       int64_t j = i;
       for (; j < b; ++j) {
-        uint2 r = W.rec[j];
+        const uint2 r = W.rec[j];
         if ((int32_t)r.x != t) break;
-        uint32_t pin = r.y & 0xFu, val = (r.y >> 4) & 1u;
-        if ((r.y >> 5) != 0u || pin >= n_pins) { report_error(O.err, GTP_ERANGE, j); bad = true; break; }
-        if (((s_next >> pin) & 1u) == val) { report_error(O.err, GTP_ENOTOGGLE, j); bad = true; break; }
+        const uint32_t pin = r.y & 0xFu, val = (r.y >> 4) & 1u;
+        if ((r.y >> 5) != 0u || pin >= n_pins) { report_error(err, GTP_ERANGE, j); bad = true; break; }
+        if (((s_next >> pin) & 1u) == val) { report_error(err, GTP_ENOTOGGLE, j); bad = true; break; }
         s_next ^= 1u << pin;
         float E;
         if (pin < n_in) {
-          uint32_t side = side_bits(st, pin, n_in);
-          const float* tb = tabs + (size_t)(((pin * 2u + val) * n_side) + side) * L.tsize;
-          E = bilinear(L, sl, tb, slew[pin * 2 + val], C);
+          const uint32_t side = side_bits(st, pin, n_in);
+          const float2 cc = crd[pin * 2 + val];
+          const float* p = tabs + (size_t)(((pin * 2u + val) << (n_in - 1u)) + side) * L.tsize + __float_as_uint(cc.y);
+          const float lo = fmaf(fl, p[1] - p[0], p[0]);
+          const float hi = fmaf(fl, p[L.nl + 1] - p[L.nl], p[L.nl]);
+          E = fmaf(cc.x, hi - lo, lo);
           Ei.add(E);
         } else {
           E = L.half_v2 * C;
@@ -119,10 +213,10 @@ __global__ void k_walk_per_gate(LibView L, NetView N, WindowView W, Outputs O) {
         e_bin += E;
       }
       if (bad) break;
-      float P_new = leak[s_next];
-      float dP = P_new - P;
-      float frac = (float)((int32_t)(bin + 1u) * O.bin_ps - t);
-      red_bin(O.bins, bin, e_bin + dP * frac * 1e-6f, dP);
+      const float P_new = leak[s_next];
+      const float dP = P_new - P;
+      const float frac = (float)((int32_t)(bin + 1u) * W.bin_ps - t);
+      red_bin(W.bins, bin, e_bin + dP * frac * 1e-6f, dP);
       st = s_next;
       P = P_new;
       t_prev = t;
@@ -130,22 +224,22 @@ __global__ void k_walk_per_gate(LibView L, NetView N, WindowView W, Outputs O) {
     }
     if (bad) continue;
     El.add(P * (T - (float)t_prev) * 1e-6f);
-    O.e_leak[g] = El.value();
-    O.e_int[g] = Ei.value();
-    O.e_sw[g] = Es.value();
-    O.final_state[g] = (uint8_t)st;
+    W.e_leak[g] = El.value();
+    W.e_int[g] = Ei.value();
+    W.e_sw[g] = Es.value();
+    W.final_state[g] = (uint8_t)st;
   }
 }
 
-cudaError_t launch_walk_per_gate(const LibView& L, const NetView& N, const WindowView& W, const Outputs& O,
-                                 int block, cudaStream_t st) {
-  size_t smem = smem_lib_bytes(L);
+cudaError_t launch_walk_per_gate(const LibView& L, const NetView& N, const WinDesc* wins, int n_win,
+                                 DevError* err, cudaStream_t st) {
+  const size_t smem = smem_lib_bytes(L);
   cudaError_t e = cudaFuncSetAttribute(k_walk_per_gate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  int64_t blocks = (N.n_gates + block - 1) / block;
-  if (blocks > 65535) blocks = 65535;
-  if (blocks < 1) blocks = 1;
-  k_walk_per_gate<<<(unsigned)blocks, block, smem, st>>>(L, N, W, O);
+  int64_t blocks = (N.n_gates + 127) / 128;
+  if (blocks > 4096) blocks = 4096;
+  dim3 grid((unsigned)(blocks < 1 ? 1 : blocks), (unsigned)n_win);
+  k_walk_per_gate<<<grid, 128, smem, st>>>(L, N, wins, err);
   return cudaGetLastError();
 }
 
@@ -157,10 +251,12 @@ constexpr int kMergeTile = kMergeThreads * kMergePer;
 
 int merge_tiles(int n_bins) { return (n_bins + kMergeTile - 1) / kMergeTile; }
 
+namespace {
+
 __device__ __forceinline__ double warp_incl_scan(double v) {
-  int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31;
   for (int o = 1; o < 32; o <<= 1) {
-    double u = __shfl_up_sync(0xffffffffu, v, o);
+    const double u = __shfl_up_sync(0xffffffffu, v, o);
     if (lane >= o) v += u;
   }
   return v;
@@ -170,82 +266,178 @@ __device__ __forceinline__ double warp_incl_scan(double v) {
 // prefix and writes the block total.
 __device__ double block_excl_scan(double v, double* total) {
   __shared__ double warp_tot[32];
-  double inc = warp_incl_scan(v);
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const double inc = warp_incl_scan(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 31) warp_tot[w] = inc;
   __syncthreads();
   if (w == 0) {
-    int nw = blockDim.x >> 5;
-    double x = lane < nw ? warp_tot[lane] : 0.0;
-    double xi = warp_incl_scan(x);
+    const int nw = blockDim.x >> 5;
+    const double x = lane < nw ? warp_tot[lane] : 0.0;
+    const double xi = warp_incl_scan(x);
     if (lane < nw) warp_tot[lane] = xi - x;
     if (lane == nw - 1) *total = xi;
   }
   __syncthreads();
-  double r = inc - v + warp_tot[w];
+  const double r = inc - v + warp_tot[w];
   __syncthreads();
   return r;
 }
 
-__global__ void k_tile_sums(const float2* __restrict__ bins, int n_bins, double* __restrict__ tile_sums) {
-  int tile = blockIdx.x;
-  int base = tile * kMergeTile + threadIdx.x * kMergePer;
+__global__ void k_tile_sums(const WinDesc* __restrict__ wins, const int64_t* __restrict__ tile_base, int n_win) {
+  const int64_t gt = blockIdx.x;
+  const int w = window_of(tile_base, n_win, gt);
+  const WinDesc& W = wins[w];
+  const int tile = (int)(gt - W.tile_base);
+  const int base = tile * kMergeTile + threadIdx.x * kMergePer;
   double s = 0.0;
 #pragma unroll
   for (int k = 0; k < kMergePer; ++k)
-    if (base + k < n_bins) s += (double)bins[base + k].y;
+    if (base + k < W.n_bins) s += (double)W.bins[base + k].y;
   __shared__ double tot;
   block_excl_scan(s, &tot);
-  if (threadIdx.x == 0) tile_sums[tile] = tot;
+  if (threadIdx.x == 0) W.tiles[tile] = tot;
 }
 
-// Exclusive scan of tile sums in place (one block, sequential over chunks).
-__global__ void k_scan_tiles(double* tile_sums, int n_tiles) {
+// Exclusive scan of one window's tile sums in place (one block per window).
+__global__ void k_scan_tiles(const WinDesc* __restrict__ wins) {
+  const WinDesc& W = wins[blockIdx.x];
   __shared__ double tot;
   double carry = 0.0;
-  for (int base = 0; base < n_tiles; base += blockDim.x) {
-    int i = base + threadIdx.x;
-    double v = i < n_tiles ? tile_sums[i] : 0.0;
-    double ex = block_excl_scan(v, &tot);
-    if (i < n_tiles) tile_sums[i] = carry + ex;
+  for (int base = 0; base < W.n_tiles; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const double v = i < W.n_tiles ? W.tiles[i] : 0.0;
+    const double ex = block_excl_scan(v, &tot);
+    if (i < W.n_tiles) W.tiles[i] = carry + ex;
     carry += tot;
     __syncthreads();
   }
 }
 
-__global__ void k_finalize(const float2* __restrict__ bins, int n_bins, const double* __restrict__ tile_pre,
-                           const double* __restrict__ l0, int bin_ps, double* __restrict__ out) {
-  int tile = blockIdx.x;
-  int base = tile * kMergeTile + threadIdx.x * kMergePer;
+__global__ void k_finalize(const WinDesc* __restrict__ wins, const int64_t* __restrict__ tile_base, int n_win) {
+  const int64_t gt = blockIdx.x;
+  const int w = window_of(tile_base, n_win, gt);
+  const WinDesc& W = wins[w];
+  const int tile = (int)(gt - W.tile_base);
+  const int base = tile * kMergeTile + threadIdx.x * kMergePer;
   float2 v[kMergePer];
   double s = 0.0;
 #pragma unroll
   for (int k = 0; k < kMergePer; ++k) {
-    v[k] = base + k < n_bins ? bins[base + k] : make_float2(0.f, 0.f);
+    v[k] = base + k < W.n_bins ? W.bins[base + k] : make_float2(0.f, 0.f);
     s += (double)v[k].y;
   }
   __shared__ double tot;
-  double pre = block_excl_scan(s, &tot) + tile_pre[tile] + *l0;
-  const double dt = (double)bin_ps;
+  double pre = block_excl_scan(s, &tot) + W.tiles[tile] + *W.l0;
+  if (W.wave == nullptr) return;
+  const double dt = (double)W.bin_ps;
   const double to_w = 1e-3 / dt;
 #pragma unroll
   for (int k = 0; k < kMergePer; ++k) {
-    if (base + k < n_bins) out[base + k] = ((double)v[k].x + pre * dt * 1e-6) * to_w;
+    if (base + k < W.n_bins) W.wave[base + k] = ((double)v[k].x + pre * dt * 1e-6) * to_w;
     pre += (double)v[k].y;
   }
 }
 
-cudaError_t launch_merge(const Outputs& O, double* waveform_w, double* tile_sums, int n_tiles, cudaStream_t st) {
-  if (O.n_bins <= 0) return cudaSuccess;
-  k_tile_sums<<<n_tiles, kMergeThreads, 0, st>>>(O.bins, O.n_bins, tile_sums);
-  k_scan_tiles<<<1, 1024, 0, st>>>(tile_sums, n_tiles);
-  k_finalize<<<n_tiles, kMergeThreads, 0, st>>>(O.bins, O.n_bins, tile_sums, O.l0, O.bin_ps, waveform_w);
+// ------------------------------------------------------------------ adjoint gradient prefix
+// grad[b] = {g_b, G(b * bin_ps)} with g_b = dL/dP_b * 1e-3 / bin_ps = dL/dE_b
+// and G(t) = integral of g over [0, t) (g piecewise constant per bin), the
+// weight a leakage interval [t0, t1) receives: G(t1) - G(t0).
+__global__ void k_grad_tiles(const float* __restrict__ dLdP, int n_bins, int bin_ps, double* __restrict__ tiles) {
+  const int base = blockIdx.x * kMergeTile + threadIdx.x * kMergePer;
+  const double f = 1e-3;  // dE_b -> dP_b is 1e-3 / bin_ps; times bin_ps for the integral
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < kMergePer; ++k)
+    if (base + k < n_bins) s += (double)dLdP[base + k] * f;
+  __shared__ double tot;
+  block_excl_scan(s, &tot);
+  if (threadIdx.x == 0) tiles[blockIdx.x] = tot;
+  (void)bin_ps;
+}
+
+__global__ void k_grad_scan(double* tiles, int n_tiles, float* g_total) {
+  __shared__ double tot;
+  double carry = 0.0;
+  for (int base = 0; base < n_tiles; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const double v = i < n_tiles ? tiles[i] : 0.0;
+    const double ex = block_excl_scan(v, &tot);
+    if (i < n_tiles) tiles[i] = carry + ex;
+    carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *g_total = (float)carry;
+}
+
+__global__ void k_grad_finalize(const float* __restrict__ dLdP, int n_bins, int bin_ps,
+                                const double* __restrict__ tiles, float2* __restrict__ grad) {
+  const int base = blockIdx.x * kMergeTile + threadIdx.x * kMergePer;
+  double v[kMergePer];
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < kMergePer; ++k) {
+    v[k] = base + k < n_bins ? (double)dLdP[base + k] * 1e-3 : 0.0;  // g_b * bin_ps
+    s += v[k];
+  }
+  __shared__ double tot;
+  double pre = block_excl_scan(s, &tot) + tiles[blockIdx.x];
+  const double inv = 1.0 / (double)bin_ps;
+#pragma unroll
+  for (int k = 0; k < kMergePer; ++k) {
+    if (base + k < n_bins) grad[base + k] = make_float2((float)(v[k] * inv), (float)pre);
+    pre += v[k];
+  }
+}
+
+// Zero every window's bin accumulators, one tile per block.
+__global__ void k_zero_bins(const WinDesc* __restrict__ wins, const int64_t* __restrict__ tile_base, int n_win) {
+  const int64_t gt = blockIdx.x;
+  const int w = window_of(tile_base, n_win, gt);
+  const WinDesc& W = wins[w];
+  const int base = (int)(gt - W.tile_base) * kMergeTile;
+  for (int k = threadIdx.x; k < kMergeTile; k += blockDim.x)
+    if (base + k < W.n_bins) W.bins[base + k] = make_float2(0.f, 0.f);
+}
+
+__global__ void k_cells_out(const double* __restrict__ acc, int n_cells, float* d_escale, float* d_lscale) {
+  const int c = threadIdx.x + blockIdx.x * blockDim.x;
+  if (c < n_cells) {
+    if (d_escale) d_escale[c] = (float)acc[c];
+    if (d_lscale) d_lscale[c] = (float)acc[n_cells + c];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_zero_bins(const WinDesc* wins, const int64_t* tile_base, int n_win, int64_t n_tiles_total,
+                             cudaStream_t st) {
+  if (n_tiles_total <= 0) return cudaSuccess;
+  k_zero_bins<<<(unsigned)n_tiles_total, kMergeThreads, 0, st>>>(wins, tile_base, n_win);
   return cudaGetLastError();
 }
 
-size_t smem_lib_bytes(const LibView& L) {
-  size_t b = sizeof(float) * 4 * kMaxAxis + (size_t)L.n_tables * L.tsize * 4 + (size_t)((L.n_leak + 3) & ~3) * 4 + (size_t)L.n_cells * sizeof(CellInfo);
-  return (b + 15) & ~(size_t)15;
+cudaError_t launch_cells_out(const double* acc, int n_cells, float* d_escale, float* d_lscale, cudaStream_t st) {
+  k_cells_out<<<(n_cells + 255) / 256, 256, 0, st>>>(acc, n_cells, d_escale, d_lscale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge(const WinDesc* wins, const int64_t* tile_base, int n_win, int64_t n_tiles_total,
+                         cudaStream_t st) {
+  if (n_tiles_total <= 0) return cudaSuccess;
+  k_tile_sums<<<(unsigned)n_tiles_total, kMergeThreads, 0, st>>>(wins, tile_base, n_win);
+  k_scan_tiles<<<(unsigned)n_win, 1024, 0, st>>>(wins);
+  k_finalize<<<(unsigned)n_tiles_total, kMergeThreads, 0, st>>>(wins, tile_base, n_win);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_prep(const WinDesc* wins, const float* dLdP, float2* grad, double* tiles, int n_tiles,
+                             int n_bins, int bin_ps, float* g_total, cudaStream_t st) {
+  (void)wins;
+  if (n_tiles <= 0) return cudaSuccess;
+  k_grad_tiles<<<n_tiles, kMergeThreads, 0, st>>>(dLdP, n_bins, bin_ps, tiles);
+  k_grad_scan<<<1, 1024, 0, st>>>(tiles, n_tiles, g_total);
+  k_grad_finalize<<<n_tiles, kMergeThreads, 0, st>>>(dLdP, n_bins, bin_ps, tiles, grad);
+  return cudaGetLastError();
 }
 
 }  // namespace gtp

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libgtpower.so")
 
 GTP_OK, GTP_EINVAL, GTP_EORDER, GTP_ERANGE, GTP_ENOTOGGLE = 0, -1, -2, -3, -4
 GTP_ENOMEM, GTP_ECUDA, GTP_ETIMEOUT, GTP_EDEVICE = -5, -6, -7, -8
-GTP_HOST, GTP_DEVICE, GTP_BORROW = 0, 1, 2
+GTP_HOST, GTP_DEVICE, GTP_BORROW, GTP_GRAPH = 0, 1, 2, 4
 
 CODE_NAMES = {GTP_EINVAL: "EINVAL", GTP_EORDER: "EORDER", GTP_ERANGE: "ERANGE", GTP_ENOTOGGLE: "ENOTOGGLE",
               GTP_ENOMEM: "ENOMEM", GTP_ECUDA: "ECUDA", GTP_ETIMEOUT: "ETIMEOUT", GTP_EDEVICE: "EDEVICE"}
@@ -26,8 +26,8 @@ CODE_NAMES = {GTP_EINVAL: "EINVAL", GTP_EORDER: "EORDER", GTP_ERANGE: "ERANGE", 
 # every entry point the header declares
 ABI_SYMBOLS = ["gtp_create", "gtp_destroy", "gtp_set_stream", "gtp_last_error", "gtp_load_library",
                "gtp_set_scales", "gtp_load_netlist", "gtp_set_load", "gtp_load_events", "gtp_run_power",
-               "gtp_gate_energy", "gtp_run_power_batched", "gtp_run_power_backward", "gtp_set_param",
-               "gtp_get_param"]
+               "gtp_gate_energy", "gtp_run_power_batched", "gtp_run_power_backward", "gtp_autotune",
+               "gtp_set_param", "gtp_get_param"]
 
 
 class GtpError(RuntimeError):
@@ -62,6 +62,7 @@ def load(path: str = LIB_PATH):
         "gtp_gate_energy": ([P, I32, P, P, P, P, P, ctypes.c_int], ctypes.c_int),
         "gtp_run_power_batched": ([P, I32, P, I32, P, ctypes.c_int], ctypes.c_int),
         "gtp_run_power_backward": ([P, I32, I32, P, P, P, P], ctypes.c_int),
+        "gtp_autotune": ([P, I32, P, I32, I32, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "gtp_set_param": ([P, ctypes.c_char_p, I64], ctypes.c_int),
         "gtp_get_param": ([P, ctypes.c_char_p], I64),
     }
@@ -178,15 +179,22 @@ def gtp_gate_energy(ctx, window: int, e_leak=None, e_int=None, e_sw=None, n_even
     _check(ctx, load().gtp_gate_energy(ctx, int(window), *[a[0] for a in args], f))
 
 
-def gtp_run_power_batched(ctx, windows: Sequence[int], bin_ps: int, waveforms: Sequence) -> None:
+def gtp_run_power_batched(ctx, windows: Sequence[int], bin_ps: int, waveforms: Sequence, graph: bool = False) -> None:
     w = np.ascontiguousarray(windows, np.int32)
     ptrs = [_ptr_flags(x, np.float64) for x in waveforms]
     flags = {p[1] for p in ptrs if p[0] is not None}
     if len(flags) > 1:
         raise ValueError("waveforms must all be host or all be device")
-    f = flags.pop() if flags else GTP_HOST
+    f = (flags.pop() if flags else GTP_HOST) | (GTP_GRAPH if graph else 0)
     arr = (ctypes.c_void_p * len(ptrs))(*[p[0] for p in ptrs])
     _check(ctx, load().gtp_run_power_batched(ctx, len(w), w.ctypes.data, int(bin_ps), ctypes.cast(arr, ctypes.c_void_p), f))
+
+
+def gtp_autotune(ctx, windows: Sequence[int], bin_ps: int, iters: int = 3) -> float:
+    w = np.ascontiguousarray(windows, np.int32)
+    best = ctypes.c_double(0.0)
+    _check(ctx, load().gtp_autotune(ctx, len(w), w.ctypes.data, int(bin_ps), int(iters), ctypes.byref(best)))
+    return best.value
 
 
 def gtp_run_power_backward(ctx, window: int, bin_ps: int, dL_dP, dC=None, d_escale=None, d_lscale=None) -> None:
@@ -273,12 +281,27 @@ class Engine:
         gtp_gate_energy(self.ctx, window, r["e_leak"], r["e_int"], r["e_sw"], r["n_events"], r["final_state"])
         return r
 
-    def run_power_batched(self, windows: Sequence[int], bin_ps: int):
+    def run_power_batched(self, windows: Sequence[int], bin_ps: int, outs=None, graph: bool = False):
         import torch
-        outs = [torch.empty(self.windows[w]["window_ps"] // bin_ps, dtype=torch.float64, device=self.device)
-                for w in windows]
-        gtp_run_power_batched(self.ctx, windows, bin_ps, outs)
+        if outs is None:
+            outs = [torch.empty(self.windows[w]["window_ps"] // bin_ps, dtype=torch.float64, device=self.device)
+                    for w in windows]
+        gtp_run_power_batched(self.ctx, windows, bin_ps, outs, graph=graph)
         return outs
+
+    def run_power_backward(self, window: int, bin_ps: int, dL_dP):
+        """Gradients (dC[n_gates], d_escale[n_cells], d_lscale[n_cells]) as
+        float32 CUDA tensors, for dL/dP given per bin (float32 CUDA)."""
+        import torch
+        kw = dict(dtype=torch.float32, device=self.device)
+        dC = torch.empty(self.n_gates, **kw)
+        de = torch.empty(self.n_cells, **kw)
+        dl = torch.empty(self.n_cells, **kw)
+        gtp_run_power_backward(self.ctx, window, bin_ps, dL_dP.to(torch.float32).contiguous(), dC, de, dl)
+        return dC, de, dl
+
+    def autotune(self, windows: Sequence[int], bin_ps: int, iters: int = 3) -> float:
+        return gtp_autotune(self.ctx, windows, bin_ps, iters)
 
     def set_param(self, key: str, value: int) -> None:
         gtp_set_param(self.ctx, key, value)

@@ -124,17 +124,38 @@ def test_bin_sizes_and_window_edges(engine, params, bin_ps):
 
 @pytest.mark.parametrize("params", KERNELS, ids=KID)
 def test_scales_and_extrapolated_lookups(engine, params):
+    # points outside both axes (linear extrapolation), kept where the tables
+    # stay positive so that every bin is a sum of positive terms
     lib, net, tr = small_random(n_gates=200, n_events=30_000, window_ps=300_000, seed=41, tie_p=0.01)
-    net.slew_ps[::3, :, 0] = 2.0
-    net.slew_ps[1::3, :, 1] = 700.0
-    net.load_ff[::4] = 0.1
-    net.load_ff[1::4] = 40.0
+    net.slew_ps[::3, :, 0] = 4.5
+    net.slew_ps[1::3, :, 1] = 330.0
+    net.load_ff[::4] = 0.24
+    net.load_ff[1::4] = 16.5
     rng = np.random.default_rng(0)
     es = rng.uniform(0.3, 3.0, lib.n_cells).astype(np.float32)
     ls = rng.uniform(0.3, 3.0, lib.n_cells).astype(np.float32)
     w, ge = run(engine, lib, net, tr, 100, params, escale=es, lscale=ls)
     ref = oracle.walk(lib, net, tr, 100, escale=es.astype(np.float64), lscale=ls.astype(np.float64))
     assert_matches(w, ge, ref, 100)
+
+
+@pytest.mark.parametrize("params", KERNELS, ids=KID)
+def test_far_extrapolation_with_signed_energies(engine, params):
+    """Far outside the axes the random tables extrapolate to negative
+    energies, so bins are sums of signed terms; the bar is then relative to
+    the waveform's mean magnitude."""
+    lib, net, tr = small_random(n_gates=200, n_events=30_000, window_ps=300_000, seed=42, tie_p=0.01)
+    net.slew_ps[::3, :, 0] = 1.0
+    net.slew_ps[1::3, :, 1] = 700.0
+    net.load_ff[::4] = 0.1
+    net.load_ff[1::4] = 40.0
+    w, ge = run(engine, lib, net, tr, 100, params)
+    ref = oracle.walk(lib, net, tr, 100)
+    want = oracle.waveform_w(ref["bins"], 100)
+    assert np.abs(w - want).max() <= TOL * np.abs(want).mean()
+    np.testing.assert_array_equal(ge["final_state"], ref["final_state"])
+    for k in ("e_leak", "e_int", "e_sw"):
+        assert np.abs(ge[k] - ref[k]).max() <= TOL * np.abs(ref[k]).mean()
 
 
 @pytest.mark.parametrize("params", KERNELS[1:], ids=KID[1:])
