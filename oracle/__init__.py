@@ -69,7 +69,7 @@ def _lib():
         lib.oracle_walk.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int64, P, P, ctypes.c_int64, P,
                                     P, P, P, P, P, P]
         lib.oracle_adjoint.restype = ctypes.c_int
-        lib.oracle_adjoint.argtypes = [P, P, P, ctypes.c_int64, P, P, P, P]
+        lib.oracle_adjoint.argtypes = [P, P, P, ctypes.c_int64, P, ctypes.c_int64, P, P, P, P]
         lib.oracle_bilinear.restype = ctypes.c_double
         lib.oracle_bilinear.argtypes = [ctypes.c_int32, P, ctypes.c_int32, P, P, ctypes.c_double,
                                         ctypes.c_double]
@@ -155,15 +155,21 @@ def walk(lib, net, trace, bin_ps: int, escale=None, lscale=None, load_ff=None, g
     return out
 
 
-def adjoint(lib, net, trace, bin_ps: int, dLdP, escale=None, lscale=None, load_ff=None):
+def adjoint(lib, net, trace, bin_ps: int, dLdP, escale=None, lscale=None, load_ff=None, gates=None):
     """FP64 gradient of L(P) given dL/dP per bin (P in W); returns
-    (dC[n_gates], d_escale[n_cells], d_lscale[n_cells])."""
+    (dC, d_escale[n_cells], d_lscale[n_cells]).  With ``gates`` only those
+    gates are walked (dC follows their order; the cell gradients then hold
+    only their contributions)."""
     L, N, T, keep = _structs(lib, net, trace, escale, lscale, load_ff)
     g = _c(dLdP, np.float64)
-    dC = np.zeros(len(net.cell), np.float64)
+    if gates is not None:
+        gates = _c(gates, np.int64)
+    n_sel = len(gates) if gates is not None else len(net.cell)
+    dC = np.zeros(n_sel, np.float64)
     de = np.zeros(len(lib.n_in), np.float64)
     dl = np.zeros(len(lib.n_in), np.float64)
     rc = _lib().oracle_adjoint(ctypes.byref(L), ctypes.byref(N), ctypes.byref(T), int(bin_ps), g.ctypes.data,
+                               n_sel, gates.ctypes.data if gates is not None else None,
                                dC.ctypes.data, de.ctypes.data, dl.ctypes.data)
     del keep
     if rc != OK:

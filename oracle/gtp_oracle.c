@@ -276,13 +276,16 @@ int oracle_walk(const oracle_lib* L, const oracle_net* N, const oracle_trace* T,
  * Gradient of a loss L(P) of the power waveform P_b = E_b * 1e-3 / bin_ps
  * (W), given dLdP[b], with respect to each gate's load C (dC), each cell's
  * energy scale (d_escale) and leakage scale (d_lscale).  FP64, by the chain
- * rule through the same definition as oracle_walk:
+ * rule through the same definition as oracle_walk.  With `gates`, only the
+ * listed gates are walked: dC[i] belongs to gates[i] and the cell gradients
+ * hold those gates' contributions only.
  *   dE_int/dC = escale * d(bilinear)/d(load)   (located load segment)
  *   dE_sw/dC  = 0.5 * Vdd^2
  *   dE_int/d escale = bilinear value;  leakage energy is linear in lscale.
  */
 int oracle_adjoint(const oracle_lib* L, const oracle_net* N, const oracle_trace* T, int64_t bin_ps,
-                   const double* dLdP, double* dC, double* d_escale, double* d_lscale) {
+                   const double* dLdP, int64_t n_sel, const int64_t* gates,
+                   double* dC, double* d_escale, double* d_lscale) {
   if (bin_ps <= 0 || T->window_ps <= 0 || T->window_ps % bin_ps != 0) return OR_EINVAL;
   int64_t* tab_base = (int64_t*)malloc(sizeof(int64_t) * (size_t)L->n_cells);
   int64_t* leak_base = (int64_t*)malloc(sizeof(int64_t) * (size_t)L->n_cells);
@@ -290,7 +293,9 @@ int oracle_adjoint(const oracle_lib* L, const oracle_net* N, const oracle_trace*
   double per_fj = 1e-3 / (double)bin_ps;     /* dP_b / dE_b */
   double half_v2 = 0.5 * L->vdd * L->vdd;
   for (int32_t c = 0; c < L->n_cells; ++c) { d_escale[c] = 0.0; d_lscale[c] = 0.0; }
-  for (int64_t g = 0; g < N->n_gates; ++g) {
+  int64_t count = gates ? n_sel : N->n_gates;
+  for (int64_t gi = 0; gi < count; ++gi) {
+    int64_t g = gates ? gates[gi] : gi;
     int32_t c = N->cell[g];
     int32_t n_in = L->n_in[c];
     double C = N->load_ff[g];
@@ -338,7 +343,7 @@ int oracle_adjoint(const oracle_lib* L, const oracle_net* N, const oracle_trace*
       t_prev = t;
       i = j;
     }
-    dC[g] = gC;
+    dC[gi] = gC;
   }
   free(tab_base);
   free(leak_base);

@@ -22,15 +22,16 @@ class _PowerWaveform(torch.autograd.Function):
                           lscale.detach().to(torch.float32).cpu().numpy())
         wave = engine.run_power(window, bin_ps)
         ctx.engine, ctx.window, ctx.bin_ps = engine, window, bin_ps
-        ctx.dtypes = (load_ff.dtype, escale.dtype, lscale.dtype)
+        ctx.like = (torch.empty(0, dtype=load_ff.dtype, device=load_ff.device),
+                    torch.empty(0, dtype=escale.dtype, device=escale.device),
+                    torch.empty(0, dtype=lscale.dtype, device=lscale.device))
         return wave
 
     @staticmethod
     def backward(ctx, grad_wave):
         dC, de, dl = ctx.engine.run_power_backward(ctx.window, ctx.bin_ps, grad_wave.to(torch.float32))
-        t_load, t_e, t_l = ctx.dtypes
-        return (dC.to(t_load), de.to(device=grad_wave.device, dtype=t_e), dl.to(device=grad_wave.device, dtype=t_l),
-                None, None, None)
+        lc, le, ll = ctx.like
+        return dC.to(lc), de.to(le), dl.to(ll), None, None, None
 
 
 def power_waveform(engine: Engine, window: int, bin_ps: int, load_ff: torch.Tensor, escale: torch.Tensor,

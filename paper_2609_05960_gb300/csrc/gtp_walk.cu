@@ -52,15 +52,6 @@ namespace {
 constexpr uint32_t kFull = 0xffffffffu;
 constexpr int kSeedScanSegments = 4;  // backward seed scan bound, in segments
 
-__device__ __forceinline__ int64_t gate_of(const int64_t* __restrict__ off, int64_t lo, int64_t hi, int64_t i) {
-  // largest g in [lo, hi] with off[g] <= i (requires off[lo] <= i)
-  while (lo < hi) {
-    const int64_t mid = (lo + hi + 1) >> 1;
-    if (off[mid] <= i) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
 __device__ __forceinline__ int window_of(const int64_t* base, int n_win, int64_t x) {
   int lo = 0, hi = n_win - 1;
   while (lo < hi) {
@@ -216,6 +207,8 @@ __global__ void __launch_bounds__(256) k_walk(LibView L, NetView N, const WinDes
   const int wib = threadIdx.x >> 5;
   uint2* stage = reinterpret_cast<uint2*>(sp) + (size_t)wib * SEG;
   sp += (size_t)n_wib * SEG * sizeof(uint2);
+  int* gid = reinterpret_cast<int*>(sp) + (size_t)wib * SEG;  // gate starting at each record, or -1
+  sp += (size_t)n_wib * SEG * sizeof(int);
   float* wacc = nullptr;     // adjoint: per warp 2*n_cells FP32 (escale, lscale)
   double* wacc64 = nullptr;  // adjoint: per warp 2*n_cells FP64
   const int nc2 = 2 * L.n_cells;
@@ -272,9 +265,44 @@ __global__ void __launch_bounds__(256) k_walk(LibView L, NetView N, const WinDes
     __syncwarp();
 
     const Seed sd = Wp->seeds[s];
-    const int64_t g_hi = (s + 1 < n_seg) ? (int64_t)Wp->seeds[s + 1].gate : G - 1;
-    const int64_t g0 = active ? gate_of(off, sd.gate, g_hi, i0) : g_hi;
-    const int64_t gstart0 = off[g0], gend0 = off[g0 + 1];
+    const bool has_next = s + 1 < n_seg;
+    const int64_t g_lo = sd.gate;
+    int64_t g_hi = G - 1;
+    bool next_is_gs = false;
+    if (has_next) {
+      const Seed sn = Wp->seeds[s + 1];
+      g_hi = sn.gate;
+      next_is_gs = (sn.flags & kSeedGateStart) != 0;
+    }
+    // first record after the segment, for the last lane's group-tail test
+    uint32_t t_next_seg = 0u;
+    if (lane == 31 && s0 + SEG < n_ev) t_next_seg = rec[s0 + SEG].x;
+
+    // ---- gate starts inside the segment, from one coalesced pass over its
+    // CSR offsets: gid[k][lane] = the gate whose first record is (lane, k)
+#pragma unroll
+    for (int k = 0; k < K; ++k) gid[k * 32 + lane] = -1;
+    __syncwarp();
+    for (int64_t j = g_lo + lane; j <= g_hi; j += 32) {
+      const int64_t b = off[j];
+      if (b >= s0 && b < s0 + SEG && b < n_ev) {
+        const int r = (int)(b - s0);
+        atomicMax(&gid[(r % K) * 32 + r / K], (int)j);  // empty gates share a start: the last one owns it
+      }
+    }
+    __syncwarp();
+    // gate of each lane's first record: the last gate start before it
+    int lmax = -1;
+#pragma unroll
+    for (int k = 0; k < K; ++k) lmax = max(lmax, gid[k * 32 + lane]);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(kFull, lmax, o);
+      if (lane >= o) lmax = max(lmax, u);
+    }
+    int g_before = __shfl_up_sync(kFull, lmax, 1);
+    if (lane == 0) g_before = -1;
+    const int64_t g0 = max((int64_t)g_before, g_lo);
     uint32_t t_before;
     if (lane > 0) t_before = stage[(K - 1) * 32 + lane - 1].x;
     else t_before = (sd.flags & kSeedGroupHead) ? (uint32_t)sd.t_prev : stage[0].x;
@@ -283,25 +311,18 @@ __global__ void __launch_bounds__(256) k_walk(LibView L, NetView N, const WinDes
     uint32_t gs_mask = 0u, gh_mask = 0u;
     uint32_t xk = 0xFFu, xs = 0u, pk = 0xFFu, ps = 0u, pm = 0u;
     {
-      int64_t gg = g0, a = gstart0, b = gend0;
       uint32_t tp = t_before;
 #pragma unroll 1
       for (int k = 0; k < K; ++k) {
         const int64_t i = i0 + k;
         if (i >= n_ev) break;
         const uint2 r = stage[k * 32 + lane];
-        if (i >= b) {
-          do {
-            ++gg;
-            a = b;
-            b = off[gg + 1];
-          } while (i >= b);
-        }
-        const bool is_gs = (i == a);
+        const int gm = gid[k * 32 + lane];
+        const bool is_gs = gm >= 0;
         const bool is_gh = is_gs || r.x != tp;
         if (is_gs) {
           xk = 0u;
-          xs = init[gg];
+          xs = init[gm];
         }
         if (is_gh) {
           pk = xk;
@@ -349,7 +370,6 @@ __global__ void __launch_bounds__(256) k_walk(LibView L, NetView N, const WinDes
     }
     const uint32_t x_in = ((uint32_t)sd.x & (ea & 0xFFu)) | ((ea >> 8) & 0xFFu);
     const uint32_t p_in = eb ? (((uint32_t)sd.x & ((ea >> 16) & 0xFFu)) | (ea >> 24)) : (uint32_t)sd.p;
-    const uint32_t next_gh = __shfl_down_sync(kFull, gh_mask & 1u, 1);
 
     // ---- pass 2: replay with energies (forward) or gradients (adjoint)
     float v0 = 0.f, v1 = 0.f, v2 = 0.f;  // forward: e_leak, e_int, e_sw; adjoint: dC, d_escale, d_lscale
@@ -359,7 +379,7 @@ __global__ void __launch_bounds__(256) k_walk(LibView L, NetView N, const WinDes
     uint32_t st = x_in, spre = p_in;
     uint32_t pb = 0xFFFFFFFFu;
     float pe = 0.f, pdp = 0.f;
-    int64_t gg = g0, b = gend0;
+    int64_t gg = g0;
     int64_t loaded = -1;
     int cell = 0;
     uint32_t n_in = 1u, pmask = 0u;
@@ -385,10 +405,7 @@ __global__ void __launch_bounds__(256) k_walk(LibView L, NetView N, const WinDes
       const bool is_gs = (gs_mask >> k) & 1u;
       const bool is_gh = (gh_mask >> k) & 1u;
       if (is_gs) {
-        while (i >= b) {
-          ++gg;
-          b = off[gg + 1];
-        }
+        gg = gid[k * 32 + lane];
         st = init[gg];
         v0 = v1 = v2 = 0.f;
         run_here = true;
@@ -474,12 +491,21 @@ __global__ void __launch_bounds__(256) k_walk(LibView L, NetView N, const WinDes
       }
       if (pin <= n_in) st = (st & ~(1u << pin)) | (val << pin);
       st &= pmask;
+      // last record of its gate / of its timestamp group (all from shared memory)
+      bool gate_end, tail;
+      if (i + 1 >= n_ev) {
+        gate_end = tail = true;
+      } else if (k + 1 < K) {
+        gate_end = gid[(k + 1) * 32 + lane] >= 0;
+        tail = gate_end || stage[(k + 1) * 32 + lane].x != t;
+      } else if (lane < 31) {
+        gate_end = gid[lane + 1] >= 0;
+        tail = gate_end || stage[lane + 1].x != t;
+      } else {
+        gate_end = next_is_gs;
+        tail = gate_end || t_next_seg != t;
+      }
       if (!BWD) {
-        bool tail;
-        if (i + 1 >= n_ev || i + 1 >= b) tail = true;
-        else if (k + 1 < K) tail = (gh_mask >> (k + 1)) & 1u;
-        else if (lane < 31) tail = next_gh != 0u;
-        else tail = rec[i + 1].x != t;
         if (ok) {
           float add = 0.f, dp = 0.f;
           if (tail) {
@@ -496,7 +522,7 @@ __global__ void __launch_bounds__(256) k_walk(LibView L, NetView N, const WinDes
           pdp += dp;
         }
       }
-      last_closed = (i + 1 == b);
+      last_closed = gate_end;
       if (last_closed) {
         if (BWD) {
           v2 += leak[st] * (Wp->g_total - Gt) * 1e-6f;
@@ -605,7 +631,7 @@ __global__ void __launch_bounds__(256) k_walk(LibView L, NetView N, const WinDes
 template <int K, bool BWD>
 size_t walk_smem(const LibView& L, int block, int n_win) {
   size_t b = smem_lib_bytes(L) + (((size_t)(n_win + 1) * 8 + 15) & ~(size_t)15) +
-             (size_t)(block / 32) * 32 * K * sizeof(uint2);
+             (size_t)(block / 32) * 32 * K * (sizeof(uint2) + sizeof(int));
   if (BWD) b += (size_t)(block / 32) * 2 * L.n_cells * (sizeof(double) + sizeof(float));
   return b;
 }

@@ -1,0 +1,235 @@
+"""Full-size workloads on the GPU, in the launch configuration the benchmark
+times.  The oracle checks sampled outputs one by one (per-gate results of
+random, hot and empty gates; sampled waveform bins where the host can hold
+the trace), and invariants that hold at any size are checked on everything:
+sum over bins = sum over gates, and merging pairs of fine bins = coarse bins.
+
+Workloads (synthetic, seeded; see synth.CONFIGS):
+  large    1M gates, 200M events, Zipf 1.2 cap 1e5, 10 us, 10 ps bins
+  adjoint  500k gates, 100M events, 5 us, 10 ps bins
+  batched  200k gates, 64 windows of 1k-100k bins and 1M-20M events
+  stress   10M gates, 2B events (16 GB), Zipf 1.5 cap 1e7, 100 us, 10 ps bins
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def engine():
+    from paper_2609_05960_gb300 import Engine
+    e = Engine(0)
+    yield e
+    e.close()
+
+
+def _gpu_trace(engine, net, cfg, counts, seed=None):
+    import torch
+    tr, rec = synth.make_trace_gpu(net, counts, cfg.window_ps, cfg.seed_ev if seed is None else seed, cfg.tie_p,
+                                   device=engine.device)
+    off = torch.from_numpy(tr.offsets).to(engine.device)
+    init = torch.from_numpy(tr.init_state).to(engine.device)
+    return tr, rec, off, init
+
+
+def _sample_gates(counts, n_random=1500, n_hot=16, seed=0):
+    rng = np.random.default_rng(seed)
+    hot = np.argsort(-counts, kind="stable")[:n_hot]
+    empty = np.flatnonzero(counts == 0)[:8]
+    rnd = rng.choice(len(counts), size=min(n_random, len(counts)), replace=False)
+    return np.unique(np.concatenate([hot, empty, rnd]))
+
+
+def _oracle_gates(lib, net, tr, gates, bin_ps):
+    off, rec = synth.gate_records(net, tr, gates)
+    sub_net = synth.Netlist(net.cell[gates], net.load_ff[gates], np.ascontiguousarray(net.slew_ps[gates]),
+                            net.n_pins[gates], net.level[gates], net.fanin[gates])
+    sub_tr = synth.Trace(tr.window_ps, off, rec, tr.init_state[gates], tr.seed, tr.tie24)
+    return sub_net, sub_tr, oracle.walk(lib, sub_net, sub_tr, bin_ps, waveform=False)
+
+
+def _check_gates(ge, ref, gates):
+    got = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v)[gates] for k, v in ge.items()}
+    np.testing.assert_array_equal(got["n_events"], ref["n_events"])
+    np.testing.assert_array_equal(got["final_state"], ref["final_state"])
+    for k in ("e_leak", "e_int", "e_sw"):
+        err = np.abs(got[k] - ref[k])
+        bad = err > TOL * np.abs(ref[k]) + 1e-9
+        assert not bad.any(), f"{k}: gate {gates[np.argmax(bad)]} got {got[k][np.argmax(bad)]} want {ref[k][np.argmax(bad)]}"
+
+
+def _totals_agree(wave, ge, bin_ps):
+    e_bins = float((wave.double() * (bin_ps * 1e3)).sum())
+    e_gates = float(ge["e_leak"].sum() + ge["e_int"].sum() + ge["e_sw"].sum())
+    assert e_bins == pytest.approx(e_gates, rel=1e-6)
+
+
+def _defaults(engine):
+    for k in ("kernel", "records_per_thread", "block_threads", "ctas_per_sm"):
+        engine.set_param(k, -1)
+
+
+def test_large_full_size(engine):
+    cfg = synth.CONFIGS["large"]
+    lib = synth.make_library(cfg.seed_lib)
+    net = synth.make_netlist(lib, cfg.n_gates, cfg.seed_net)
+    counts = synth.zipf_counts(cfg.n_gates, cfg.n_events, cfg.zipf_s, cfg.cap, cfg.seed_ev)
+    engine.load_library(lib)
+    engine.load_netlist(net)
+    _defaults(engine)
+    tr, rec, off, init = _gpu_trace(engine, net, cfg, counts)
+    engine.load_events(0, window_ps=cfg.window_ps, offsets=off, records=rec, init_state=init, borrow=True)
+    wave = engine.run_power(0, cfg.bin_ps)
+    ge = engine.gate_energy(0, device=True)
+    gates = _sample_gates(counts)
+    _, _, ref = _oracle_gates(lib, net, tr, gates, cfg.bin_ps)
+    _check_gates(ge, ref, gates)
+    _totals_agree(wave, ge, cfg.bin_ps)
+    # sampled bins against the oracle over the whole trace (host copy of the records)
+    host = synth.make_trace(net, counts, cfg.window_ps, cfg.seed_ev, cfg.tie_p)
+    assert np.array_equal(host.records[:1000], rec[:1000].cpu().numpy().view(np.uint32))
+    sample = np.unique(np.concatenate([[0, 1, cfg.window_ps // cfg.bin_ps - 1],
+                                       np.random.default_rng(1).integers(0, cfg.window_ps // cfg.bin_ps, 40)]))
+    rb = oracle.walk(lib, net, host, cfg.bin_ps, sample_bins=sample)
+    want = oracle.waveform_w(rb["bins"], cfg.bin_ps)
+    got = wave.cpu().numpy()[sample]
+    assert (np.abs(got - want) / want).max() <= TOL
+    del host
+    # coarse bins = merged fine bins
+    wave2 = engine.run_power(0, 2 * cfg.bin_ps)
+    np.testing.assert_allclose(wave.view(-1, 2).mean(1).cpu().numpy(), wave2.cpu().numpy(), rtol=TOL)
+
+
+def test_adjoint_full_size(engine):
+    import torch
+    from paper_2609_05960_gb300 import peak_loss
+    cfg = synth.CONFIGS["adjoint"]
+    lib = synth.make_library(cfg.seed_lib)
+    net = synth.make_netlist(lib, cfg.n_gates, cfg.seed_net)
+    counts = synth.zipf_counts(cfg.n_gates, cfg.n_events, cfg.zipf_s, cfg.cap, cfg.seed_ev)
+    engine.load_library(lib)
+    engine.load_netlist(net)
+    _defaults(engine)
+    tr, rec, off, init = _gpu_trace(engine, net, cfg, counts)
+    engine.load_events(0, window_ps=cfg.window_ps, offsets=off, records=rec, init_state=init, borrow=True)
+    P = engine.run_power(0, cfg.bin_ps).clone().requires_grad_(True)
+    peak_loss(P).backward()
+    g = P.grad.to(torch.float32)
+    dC, de, dl = engine.run_power_backward(0, cfg.bin_ps, g)
+    # per-gate load gradients of sampled gates against the FP64 oracle adjoint
+    gates = _sample_gates(counts, n_random=600, n_hot=8)
+    sub_net, sub_tr, _ = _oracle_gates(lib, net, tr, gates, cfg.bin_ps)
+    rC, _, _ = oracle.adjoint(lib, sub_net, sub_tr, cfg.bin_ps, g.cpu().numpy().astype(np.float64))
+    got = dC.cpu().numpy()[gates]
+    scale = np.abs(rC).max()
+    assert np.all(np.abs(got - rC) <= 1e-4 * np.abs(rC) + 1e-5 * scale)
+    # cell-scale gradients: the waveform is linear in each scale, so for the
+    # linear functional w.P with w = dL/dP, dL/ds_c = w.(P(s = e_c) - P(s = 0))
+    w = g.double()
+    z = np.zeros(lib.n_cells, np.float32)
+    engine.set_scales(z, z)
+    base = float((engine.run_power(0, cfg.bin_ps) * w).sum())
+    for c in range(lib.n_cells):
+        e = z.copy()
+        e[c] = 1.0
+        engine.set_scales(e, z)
+        ge_ = float((engine.run_power(0, cfg.bin_ps) * w).sum()) - base
+        engine.set_scales(z, e)
+        gl_ = float((engine.run_power(0, cfg.bin_ps) * w).sum()) - base
+        assert float(de[c]) == pytest.approx(ge_, rel=1e-4)
+        assert float(dl[c]) == pytest.approx(gl_, rel=1e-4)
+    engine.set_scales(None, None)
+
+
+def test_batched_full_size(engine):
+    import torch
+    lib = synth.make_library(1)
+    net = synth.make_netlist(lib, synth.BATCHED_GATES, 2)
+    wins = synth.batched_windows()
+    engine.load_library(lib)
+    engine.load_netlist(net)
+    _defaults(engine)
+    keep = []
+    traces = []
+    for w, spec in enumerate(wins):
+        cfg = synth.Config(f"w{w}", synth.BATCHED_GATES, spec["n_events"], 1.2, 100_000, spec["window_ps"], 10,
+                           seed_ev=spec["seed"])
+        counts = synth.zipf_counts(cfg.n_gates, cfg.n_events, 1.2, 100_000, cfg.seed_ev)
+        tr, rec, off, init = _gpu_trace(engine, net, cfg, counts)
+        engine.load_events(w, window_ps=cfg.window_ps, offsets=off, records=rec, init_state=init, borrow=True)
+        keep.append((rec, off, init))
+        traces.append((cfg, counts, tr))
+    ids = list(range(len(wins)))
+    outs = [torch.empty(s["window_ps"] // 10, dtype=torch.float64, device=engine.device) for s in wins]
+    engine.run_power_batched(ids, 10, outs=outs, graph=True)
+    engine.run_power_batched(ids, 10, outs=outs, graph=True)  # graph replay
+    for w in ids:
+        ge = engine.gate_energy(w, device=True)
+        _totals_agree(outs[w], ge, 10)
+        if w % 8 == 0:
+            cfg, counts, tr = traces[w]
+            gates = _sample_gates(counts, n_random=200, n_hot=4, seed=w)
+            _, _, ref = _oracle_gates(lib, net, tr, gates, 10)
+            _check_gates(ge, ref, gates)
+    # the smallest window in full against the oracle
+    w = int(np.argmin([s["n_events"] for s in wins]))
+    cfg, counts, _ = traces[w]
+    host = synth.make_trace(net, counts, cfg.window_ps, cfg.seed_ev)
+    want = oracle.waveform_w(oracle.walk(lib, net, host, 10)["bins"], 10)
+    got = outs[w].cpu().numpy()
+    assert (np.abs(got - want) / want).max() <= TOL
+
+
+def test_stress_full_size(engine):
+    import torch
+    cfg = synth.CONFIGS["stress"]
+    lib = synth.make_library(cfg.seed_lib)
+    net = synth.make_netlist(lib, cfg.n_gates, cfg.seed_net)
+    counts = synth.zipf_counts(cfg.n_gates, cfg.n_events, cfg.zipf_s, cfg.cap, cfg.seed_ev)
+    engine.load_library(lib)
+    engine.load_netlist(net)
+    _defaults(engine)
+    tr, rec, off, init = _gpu_trace(engine, net, cfg, counts)
+    engine.load_events(0, window_ps=cfg.window_ps, offsets=off, records=rec, init_state=init, borrow=True)
+    wave = engine.run_power(0, cfg.bin_ps)
+    ge = engine.gate_energy(0, device=True)
+    gates = _sample_gates(counts, n_random=400, n_hot=4)
+    _, _, ref = _oracle_gates(lib, net, tr, gates, cfg.bin_ps)
+    _check_gates(ge, ref, gates)
+    _totals_agree(wave, ge, cfg.bin_ps)
+    # adjoint form on the same window: sampled load gradients
+    g = torch.linspace(1.0, 2.0, wave.numel(), device=engine.device, dtype=torch.float32)
+    dC, de, dl = engine.run_power_backward(0, cfg.bin_ps, g)
+    few = gates[:40]
+    sub_net, sub_tr, _ = _oracle_gates(lib, net, tr, few, cfg.bin_ps)
+    rC, _, _ = oracle.adjoint(lib, sub_net, sub_tr, cfg.bin_ps, g.cpu().numpy().astype(np.float64))
+    got = dC.cpu().numpy()[few]
+    assert np.all(np.abs(got - rC) <= 1e-4 * np.abs(rC) + 1e-5 * np.abs(rC).max())
+    del rec, off, init, wave
+    torch.cuda.empty_cache()
+    # batched form: 4 windows of 500M events
+    keep = []
+    traces = []
+    for w in range(4):
+        c4 = dataclasses.replace(cfg, n_events=cfg.n_events // 4, seed_ev=cfg.seed_ev + 10 * (w + 1))
+        cnt = synth.zipf_counts(c4.n_gates, c4.n_events, c4.zipf_s, c4.cap, c4.seed_ev)
+        t4, r4, o4, i4 = _gpu_trace(engine, net, c4, cnt)
+        engine.load_events(w, window_ps=c4.window_ps, offsets=o4, records=r4, init_state=i4, borrow=True)
+        keep.append((r4, o4, i4))
+        traces.append((cnt, t4))
+    outs = engine.run_power_batched([0, 1, 2, 3], cfg.bin_ps)
+    for w in range(4):
+        ge = engine.gate_energy(w, device=True)
+        _totals_agree(outs[w], ge, cfg.bin_ps)
+        cnt, t4 = traces[w]
+        gs = _sample_gates(cnt, n_random=100, n_hot=2, seed=w)
+        _, _, ref = _oracle_gates(lib, net, t4, gs, cfg.bin_ps)
+        _check_gates(ge, ref, gs)
