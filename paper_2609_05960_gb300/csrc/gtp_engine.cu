@@ -86,7 +86,7 @@ struct gtp_ctx {
   LibView L{};
   // netlist
   bool net_loaded = false;
-  DevBuf cell, load, slew, coord, wld, rwl;
+  DevBuf cell, load, slew, desc;
   NetView N{};
   std::map<int, Window> windows;
   // launch plan: device descriptor table and its pinned host staging copy
@@ -343,14 +343,10 @@ int enqueue_forward(gtp_ctx* ctx, int n, int64_t n_seg_total, int64_t n_tiles_to
 
 int ensure_netlist_coords(gtp_ctx* ctx) {
   const int64_t G = ctx->N.n_gates;
-  CU(ctx->coord.reserve(sizeof(float2) * 2 * ctx->N.stride * G), "alloc coord");
-  CU(ctx->wld.reserve(sizeof(float) * G), "alloc wld");
-  CU(ctx->rwl.reserve(sizeof(float) * G), "alloc rwl");
-  ctx->N.coord = ctx->coord.as<float2>();
-  ctx->N.wld = ctx->wld.as<float>();
-  ctx->N.rwl = ctx->rwl.as<float>();
-  CU(launch_interp_coords(ctx->L, ctx->N, ctx->coord.as<float2>(), ctx->wld.as<float>(), ctx->rwl.as<float>(),
-                          ctx->stream), "interpolation coordinates");
+  ctx->N.dstride = 2 * (ctx->N.stride + 1);
+  CU(ctx->desc.reserve(sizeof(uint4) * ctx->N.dstride * G), "alloc event descriptors");
+  ctx->N.desc = ctx->desc.as<uint4>();
+  CU(launch_event_desc(ctx->L, ctx->N, ctx->desc.as<uint4>(), ctx->stream), "event descriptors");
   ctx->launches += 1;
   return GTP_OK;
 }
@@ -490,7 +486,7 @@ void gtp_destroy(gtp_ctx* ctx) {
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   for (auto& kv : ctx->windows) kv.second.release();
   for (DevBuf* b : {&ctx->tab, &ctx->leak, &ctx->cells, &ctx->table_cell, &ctx->leak_cell, &ctx->escale, &ctx->lscale,
-                    &ctx->cell, &ctx->load, &ctx->slew, &ctx->coord, &ctx->wld, &ctx->rwl, &ctx->plan, &ctx->runs,
+                    &ctx->cell, &ctx->load, &ctx->slew, &ctx->desc, &ctx->plan, &ctx->runs,
                     &ctx->cell_acc, &ctx->grad, &ctx->gtiles, &ctx->dC_scratch, &ctx->d_err})
     b->release();
   if (ctx->h_err) cudaFreeHost(ctx->h_err);
@@ -543,7 +539,7 @@ int gtp_load_library(gtp_ctx* ctx, int32_t n_cells, const int32_t* n_in, float v
   L.ns = n_slew;
   L.nl = n_load;
   L.tsize = (int32_t)tsize;
-  if (smem_lib_bytes(L) > GTP_MAX_TABLE_BYTES)
+  if (smem_lib_bytes(L) > GTP_MAX_TABLE_BYTES || n_tables * tsize > 65535)
     return fail(ctx, GTP_ERANGE, "load_library: tables exceed the shared-memory budget");
   DeviceGuard dg(ctx->device);
   std::vector<uint8_t> tcell(n_tables), lcell(n_leak);

@@ -6,10 +6,8 @@
 //             n_in}, table_cell[n_tables], leak_cell[n_leak] (owning cell of
 //             each table / leakage entry, for scaling), escale/lscale[n_cells]
 //   netlist   cell[G] int32, load[G] float, slew[G][stride][2] float, and the
-//             interpolation coordinates derived from them once per netlist:
-//             coord[G][stride][2] = {slew fraction, corner offset of the table
-//             cell (slew segment * nl + load segment)}, wld[G] = load fraction,
-//             rwl[G] = 1 / width of the gate's load segment
+//             event descriptors derived from them once per netlist:
+//             desc[G][2*(stride+1)] (16 B each, see NetView)
 //   window    offsets[G+1] int64, records[E] 8 B {int32 t, uint32 meta},
 //             init[G] uint8, segment seeds (16 B per segment), per-gate
 //             outputs (FP64 energies, uint8 final state), and the bin
@@ -54,15 +52,21 @@ struct LibView {
   float load_rw[kMaxAxis];
 };
 
+// Event descriptor of one (gate, pin, edge), 16 bytes, built once per
+// netlist / load update (k_event_desc):
+//   input pin:  x = slew fraction, y = load fraction, w = 1 / load-segment width
+//   output pin: w = 0.5 * C * Vdd^2 (the switching energy)
+//   z = table element offset without the side bits (bits 0-15; for the
+//       output pin the cell's first table) | cell << 16 | output << 24 |
+//       load segment << 25
 struct NetView {
   const int32_t* cell;
   const float* load;
   const float* slew;         // [G][stride][2]
-  const float2* coord;       // [G][stride][2] {slew fraction, corner offset as float bits}
-  const float* wld;          // [G] load fraction
-  const float* rwl;          // [G] 1 / load segment width
+  const uint4* desc;         // [G][dstride] event descriptors
   int64_t n_gates;
-  int32_t stride;
+  int32_t stride;            // slew stride (input pins per gate)
+  int32_t dstride;           // descriptors per gate = 2 * (stride + 1)
 };
 
 // First failure seen by a kernel: code and record index.
@@ -200,8 +204,7 @@ __device__ __forceinline__ SmemLib stage_library(const LibView& L, unsigned char
 }
 
 // ------------------------------------------------------------------ launchers (host)
-cudaError_t launch_interp_coords(const LibView& L, NetView N, float2* coord, float* wld, float* rwl,
-                                 cudaStream_t st);
+cudaError_t launch_event_desc(const LibView& L, NetView N, uint4* desc, cudaStream_t st);
 cudaError_t launch_gate_pass(const LibView& L, const NetView& N, const WinDesc* wins, int n_win, DevError* err,
                              cudaStream_t st);
 cudaError_t launch_gate_pass_bwd(const LibView& L, const NetView& N, const WinDesc* wins, double* cell_acc,

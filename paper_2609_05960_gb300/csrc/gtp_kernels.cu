@@ -37,12 +37,12 @@ __device__ __forceinline__ int window_of(const int64_t* base, int n_win, int64_t
 
 }  // namespace
 
-// ------------------------------------------------------------------ interpolation coordinates
-// The NLDM lookup point of every (gate, input pin, edge) is static: its
-// slew segment and fraction, and the gate's load segment and fraction, are
-// located once per netlist (or load update) instead of once per event.
-__global__ void k_interp_coords(LibView L, NetView N, float2* __restrict__ coord, float* __restrict__ wld,
-                                float* __restrict__ rwl) {
+// ------------------------------------------------------------------ event descriptors
+// The NLDM lookup point of every (gate, input pin, edge) is static: its slew
+// segment and fraction and the gate's load segment and fraction are located
+// once per netlist (or load update), together with the table element and the
+// switching energy, instead of once per event.
+__global__ void k_event_desc(LibView L, NetView N, uint4* __restrict__ desc) {
   __shared__ float ax[4 * kMaxAxis];
   if (threadIdx.x < kMaxAxis) {
     ax[threadIdx.x] = L.slew_axis[threadIdx.x];
@@ -53,31 +53,37 @@ __global__ void k_interp_coords(LibView L, NetView N, float2* __restrict__ coord
   __syncthreads();
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N.n_gates;
        g += (int64_t)gridDim.x * blockDim.x) {
-    const int n_in = L.cells[N.cell[g]].n_in;
+    const int32_t c = N.cell[g];
+    const CellInfo ci = L.cells[c];
+    const int n_in = ci.n_in;
     const float C = N.load[g];
     const int j = segment_of(ax + kMaxAxis, L.nl, C);
-    wld[g] = (C - ax[kMaxAxis + j]) * ax[3 * kMaxAxis + j];
-    rwl[g] = ax[3 * kMaxAxis + j];
-    for (int p = 0; p < N.stride; ++p) {
+    const float fl = (C - ax[kMaxAxis + j]) * ax[3 * kMaxAxis + j];
+    const uint32_t hi_bits = ((uint32_t)c << 16) | ((uint32_t)j << 25);
+    for (int p = 0; p <= N.stride; ++p) {
       for (int e = 0; e < 2; ++e) {
-        float2 c = make_float2(0.f, 0.f);
+        uint4 d;
         if (p < n_in) {
           const float s = N.slew[((size_t)g * N.stride + p) * 2 + e];
           const int i = segment_of(ax, L.ns, s);
-          c.x = (s - ax[i]) * ax[2 * kMaxAxis + i];
-          c.y = __uint_as_float((uint32_t)(i * L.nl + j));
+          const uint32_t tab = (uint32_t)(ci.tab_base + ((p * 2 + e) << (n_in - 1))) * (uint32_t)L.tsize +
+                               (uint32_t)(i * L.nl + j);
+          d = make_uint4(__float_as_uint((s - ax[i]) * ax[2 * kMaxAxis + i]), __float_as_uint(fl),
+                         tab | hi_bits, __float_as_uint(ax[3 * kMaxAxis + j]));
+        } else {  // output pin (and any pin past it): switching energy
+          d = make_uint4(0u, 0u, ((uint32_t)ci.tab_base * (uint32_t)L.tsize) | hi_bits | (1u << 24),
+                         __float_as_uint(L.half_v2 * C));
         }
-        coord[((size_t)g * N.stride + p) * 2 + e] = c;
+        desc[(size_t)g * N.dstride + p * 2 + e] = d;
       }
     }
   }
 }
 
-cudaError_t launch_interp_coords(const LibView& L, NetView N, float2* coord, float* wld, float* rwl,
-                                 cudaStream_t st) {
+cudaError_t launch_event_desc(const LibView& L, NetView N, uint4* desc, cudaStream_t st) {
   int64_t blocks = (N.n_gates + 255) / 256;
   if (blocks > 8192) blocks = 8192;
-  k_interp_coords<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, st>>>(L, N, coord, wld, rwl);
+  k_event_desc<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, st>>>(L, N, desc);
   return cudaGetLastError();
 }
 
@@ -171,10 +177,7 @@ __global__ void k_walk_per_gate(LibView L, NetView N, const WinDesc* __restrict_
     const CellInfo ci = sl.cells[N.cell[g]];
     const uint32_t n_in = (uint32_t)ci.n_in, n_pins = n_in + 1;
     const float* leak = sl.leak + ci.leak_base;
-    const float* tabs = sl.tab + (size_t)ci.tab_base * L.tsize;
-    const float C = N.load[g];
-    const float fl = N.wld[g];
-    const float2* crd = N.coord + (size_t)g * N.stride * 2;
+    const uint4* dsc = N.desc + (size_t)g * N.dstride;
     uint32_t st = W.init[g] & ((2u << n_in) - 1u);
     float P = leak[st];
     int32_t t_prev = 0;
@@ -198,16 +201,17 @@ __global__ void k_walk_per_gate(LibView L, NetView N, const WinDesc* __restrict_
         if (((s_next >> pin) & 1u) == val) { report_error(err, GTP_ENOTOGGLE, j); bad = true; break; }
         s_next ^= 1u << pin;
         float E;
+        const uint4 d = dsc[pin * 2 + val];
         if (pin < n_in) {
           const uint32_t side = side_bits(st, pin, n_in);
-          const float2 cc = crd[pin * 2 + val];
-          const float* p = tabs + (size_t)(((pin * 2u + val) << (n_in - 1u)) + side) * L.tsize + __float_as_uint(cc.y);
+          const float* p = sl.tab + (d.z & 0xFFFFu) + side * (uint32_t)L.tsize;
+          const float fl = __uint_as_float(d.y);
           const float lo = fmaf(fl, p[1] - p[0], p[0]);
           const float hi = fmaf(fl, p[L.nl + 1] - p[L.nl], p[L.nl]);
-          E = fmaf(cc.x, hi - lo, lo);
+          E = fmaf(__uint_as_float(d.x), hi - lo, lo);
           Ei.add(E);
         } else {
-          E = L.half_v2 * C;
+          E = __uint_as_float(d.w);
           Es.add(E);
         }
         e_bin += E;

@@ -205,9 +205,12 @@ __global__ void __launch_bounds__(256) k_walk(LibView L, NetView N, const WinDes
   for (int k = threadIdx.x; k <= n_win; k += blockDim.x) sbase[k] = seg_base_g[k];
   const int n_wib = blockDim.x >> 5;
   const int wib = threadIdx.x >> 5;
-  uint2* stage = reinterpret_cast<uint2*>(sp) + (size_t)wib * SEG;
+  // per-warp staging, all [k][lane]: event descriptors, records, gate ids
+  uint4* dsc_s = reinterpret_cast<uint4*>(sp) + (size_t)wib * SEG;
+  sp += (size_t)n_wib * SEG * sizeof(uint4);
+  uint2* rec_s = reinterpret_cast<uint2*>(sp) + (size_t)wib * SEG;
   sp += (size_t)n_wib * SEG * sizeof(uint2);
-  int* gid = reinterpret_cast<int*>(sp) + (size_t)wib * SEG;  // gate starting at each record, or -1
+  int* gid_s = reinterpret_cast<int*>(sp) + (size_t)wib * SEG;
   sp += (size_t)n_wib * SEG * sizeof(int);
   float* wacc = nullptr;     // adjoint: per warp 2*n_cells FP32 (escale, lscale)
   double* wacc64 = nullptr;  // adjoint: per warp 2*n_cells FP64
@@ -229,6 +232,8 @@ __global__ void __launch_bounds__(256) k_walk(LibView L, NetView N, const WinDes
   const int64_t G = N.n_gates;
   const int tsize = L.tsize;
   const int nl = L.nl;
+  const int dstride = N.dstride;
+  const uint4* __restrict__ desc = N.desc;
 
   for (int64_t sgl = warp; sgl < n_seg_total; sgl += n_warps) {
     const int w = window_of(sbase, n_win, sgl);
@@ -242,28 +247,26 @@ __global__ void __launch_bounds__(256) k_walk(LibView L, NetView N, const WinDes
     const int32_t T = Wp->window_ps;
     const uint32_t bin_ps = (uint32_t)Wp->bin_ps, magic = Wp->bin_magic, shift = Wp->bin_shift;
     const int64_t s0 = s * SEG;
-    const int64_t i0 = s0 + (int64_t)lane * K;
-    const bool active = i0 < n_ev;
+    const int n_rem = (int)min((int64_t)SEG, n_ev - s0);  // records in this segment
+    const int j0 = lane * K;                                // first segment-local record of the lane
+    const bool active = j0 < n_rem;
 
-    // ---- stage the segment in shared memory, transposed: [k][lane]
+    // ---- stage the segment's records, transposed [k][lane], with 16-byte loads
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < K / 2; ++j) {
       const int r = 2 * (j * 32 + lane);
-      const int64_t gi = s0 + r;
       uint2 a = make_uint2(0u, 0u), b = make_uint2(0u, 0u);
-      if (gi + 1 < n_ev) {
-        const uint4 v = __ldcs(reinterpret_cast<const uint4*>(rec + gi));
+      if (r + 1 < n_rem) {
+        const uint4 v = __ldcs(reinterpret_cast<const uint4*>(rec + s0 + r));
         a = make_uint2(v.x, v.y);
         b = make_uint2(v.z, v.w);
-      } else if (gi < n_ev) {
-        a = rec[gi];
+      } else if (r < n_rem) {
+        a = rec[s0 + r];
       }
-      stage[(r % K) * 32 + r / K] = a;
-      stage[((r + 1) % K) * 32 + (r + 1) / K] = b;
+      rec_s[(r % K) * 32 + r / K] = a;
+      rec_s[((r + 1) % K) * 32 + (r + 1) / K] = b;
     }
-    __syncwarp();
-
     const Seed sd = Wp->seeds[s];
     const bool has_next = s + 1 < n_seg;
     const int64_t g_lo = sd.gate;
@@ -274,27 +277,25 @@ __global__ void __launch_bounds__(256) k_walk(LibView L, NetView N, const WinDes
       g_hi = sn.gate;
       next_is_gs = (sn.flags & kSeedGateStart) != 0;
     }
-    // first record after the segment, for the last lane's group-tail test
-    uint32_t t_next_seg = 0u;
-    if (lane == 31 && s0 + SEG < n_ev) t_next_seg = rec[s0 + SEG].x;
+    uint32_t t_next_seg = 0u;  // first record after the segment, for the last lane's group-tail test
+    if (lane == 31 && n_rem == SEG && s0 + SEG < n_ev) t_next_seg = rec[s0 + SEG].x;
 
     // ---- gate starts inside the segment, from one coalesced pass over its
     // CSR offsets: gid[k][lane] = the gate whose first record is (lane, k)
 #pragma unroll
-    for (int k = 0; k < K; ++k) gid[k * 32 + lane] = -1;
+    for (int k = 0; k < K; ++k) gid_s[k * 32 + lane] = -1;
     __syncwarp();
-    for (int64_t j = g_lo + lane; j <= g_hi; j += 32) {
-      const int64_t b = off[j];
-      if (b >= s0 && b < s0 + SEG && b < n_ev) {
+    for (int64_t jg = g_lo + lane; jg <= g_hi; jg += 32) {
+      const int64_t b = off[jg];
+      if (b >= s0 && b < s0 + n_rem) {
         const int r = (int)(b - s0);
-        atomicMax(&gid[(r % K) * 32 + r / K], (int)j);  // empty gates share a start: the last one owns it
+        atomicMax(&gid_s[(r % K) * 32 + r / K], (int)jg);  // empty gates share a start: the last one owns it
       }
     }
     __syncwarp();
-    // gate of each lane's first record: the last gate start before it
     int lmax = -1;
 #pragma unroll
-    for (int k = 0; k < K; ++k) lmax = max(lmax, gid[k * 32 + lane]);
+    for (int k = 0; k < K; ++k) lmax = max(lmax, gid_s[k * 32 + lane]);
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int u = __shfl_up_sync(kFull, lmax, o);
@@ -302,28 +303,30 @@ __global__ void __launch_bounds__(256) k_walk(LibView L, NetView N, const WinDes
     }
     int g_before = __shfl_up_sync(kFull, lmax, 1);
     if (lane == 0) g_before = -1;
-    const int64_t g0 = max((int64_t)g_before, g_lo);
+    const int g0 = (int)max((int64_t)g_before, g_lo);
     uint32_t t_before;
-    if (lane > 0) t_before = stage[(K - 1) * 32 + lane - 1].x;
-    else t_before = (sd.flags & kSeedGroupHead) ? (uint32_t)sd.t_prev : stage[0].x;
+    if (lane > 0) t_before = rec_s[(K - 1) * 32 + lane - 1].x;
+    else t_before = (sd.flags & kSeedGroupHead) ? (uint32_t)sd.t_prev : rec_s[0].x;
 
-    // ---- pass 1: gate-start / group-head flags and the lane's state maps
+    // ---- pass 1: flags, per-record gate ids, the lane's state maps
     uint32_t gs_mask = 0u, gh_mask = 0u;
     uint32_t xk = 0xFFu, xs = 0u, pk = 0xFFu, ps = 0u, pm = 0u;
     {
       uint32_t tp = t_before;
+      int gg = g0;
 #pragma unroll 1
       for (int k = 0; k < K; ++k) {
-        const int64_t i = i0 + k;
-        if (i >= n_ev) break;
-        const uint2 r = stage[k * 32 + lane];
-        const int gm = gid[k * 32 + lane];
+        if (j0 + k >= n_rem) break;
+        const uint2 r = rec_s[k * 32 + lane];
+        const int gm = gid_s[k * 32 + lane];
         const bool is_gs = gm >= 0;
         const bool is_gh = is_gs || r.x != tp;
         if (is_gs) {
+          gg = gm;
           xk = 0u;
           xs = init[gm];
         }
+        gid_s[k * 32 + lane] = gg;
         if (is_gh) {
           pk = xk;
           ps = xs;
@@ -335,6 +338,18 @@ __global__ void __launch_bounds__(256) k_walk(LibView L, NetView N, const WinDes
         gs_mask |= (is_gs ? 1u : 0u) << k;
         gh_mask |= (is_gh ? 1u : 0u) << k;
         tp = r.x;
+      }
+    }
+
+    __syncwarp();  // pass 2 reads the next lane's gate ids
+
+    // ---- gather every record's event descriptor in one burst of independent loads
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (j0 + k < n_rem) {
+        const uint2 r = rec_s[k * 32 + lane];
+        const uint32_t pin = min(r.y & 0xFu, (uint32_t)(dstride / 2 - 1));
+        dsc_s[k * 32 + lane] = __ldg(desc + (size_t)gid_s[k * 32 + lane] * dstride + pin * 2u + ((r.y >> 4) & 1u));
       }
     }
 
@@ -375,23 +390,17 @@ __global__ void __launch_bounds__(256) k_walk(LibView L, NetView N, const WinDes
     float v0 = 0.f, v1 = 0.f, v2 = 0.f;  // forward: e_leak, e_int, e_sw; adjoint: dC, d_escale, d_lscale
     bool run_here = false, last_closed = false, has_head = false;
     float h0 = 0.f, h1 = 0.f, h2 = 0.f;
-    int64_t head_gate = 0;
+    int head_gate = 0;
     uint32_t st = x_in, spre = p_in;
     uint32_t pb = 0xFFFFFFFFu;
     float pe = 0.f, pdp = 0.f;
-    int64_t gg = g0;
-    int64_t loaded = -1;
-    int cell = 0;
-    uint32_t n_in = 1u, pmask = 0u;
-    const float* leak = sl.leak;
-    const float* tabs = sl.tab;
-    const float2* crd = N.coord;
-    float C = 0.f, fl = 0.f, rwl = 0.f, es = 1.f;
+    int gg = g0;
+    uint32_t cell = 0u;
     float Gcur = 0.f;  // adjoint: G(time of the current group)
     if (BWD && active && !(gs_mask & 1u)) {
       const uint32_t tb = t_before;
-      const uint32_t bb = bin_of(tb, magic, shift, bin_ps);
       if ((int32_t)tb >= 0 && (int32_t)tb < T) {
+        const uint32_t bb = bin_of(tb, magic, shift, bin_ps);
         const float2 gv = Wp->grad[bb];
         Gcur = gv.y + gv.x * (float)(tb - bb * bin_ps);
       }
@@ -399,51 +408,33 @@ __global__ void __launch_bounds__(256) k_walk(LibView L, NetView N, const WinDes
     uint32_t tp = t_before;
 #pragma unroll 1
     for (int k = 0; k < K; ++k) {
-      const int64_t i = i0 + k;
-      if (i >= n_ev) break;
-      const uint2 r = stage[k * 32 + lane];
+      const int jl = j0 + k;
+      if (jl >= n_rem) break;
+      const uint2 r = rec_s[k * 32 + lane];
+      const uint4 d = dsc_s[k * 32 + lane];
       const bool is_gs = (gs_mask >> k) & 1u;
       const bool is_gh = (gh_mask >> k) & 1u;
       if (is_gs) {
-        gg = gid[k * 32 + lane];
+        gg = gid_s[k * 32 + lane];
         st = init[gg];
         v0 = v1 = v2 = 0.f;
         run_here = true;
         Gcur = 0.f;
       }
-      if (gg != loaded) {
-        loaded = gg;
-        cell = N.cell[gg];
-        const CellInfo ci = sl.cells[cell];
-        n_in = (uint32_t)ci.n_in;
-        pmask = (2u << n_in) - 1u;
-        leak = sl.leak + ci.leak_base;
-        tabs = sl.tab + (size_t)ci.tab_base * tsize;
-        crd = N.coord + (size_t)gg * N.stride * 2;
-        C = N.load[gg];
-        fl = N.wld[gg];
-        if (BWD) {
-          rwl = N.rwl[gg];
-          es = sl.escale[cell];
-        }
-      }
+      cell = (d.z >> 16) & 0xFFu;
+      const CellInfo ci = sl.cells[cell];
+      const uint32_t n_in = (uint32_t)ci.n_in;
+      const uint32_t pmask = (2u << n_in) - 1u;
+      const float* leak = sl.leak + ci.leak_base;
       const uint32_t t = r.x, meta = r.y;
       const uint32_t pin = meta & 0xFu, val = (meta >> 4) & 1u;
-      bool ok = true;
-      if ((int32_t)t < 0 || (int32_t)t >= T) {
-        report_error(err, GTP_ERANGE, i);
-        ok = false;
-      } else if (!is_gs && (int32_t)t < (int32_t)tp) {
-        report_error(err, GTP_EORDER, i);
-        ok = false;
-      }
-      if ((meta >> 5) != 0u || pin > n_in) {
-        report_error(err, GTP_ERANGE, i);
-        ok = false;
-      } else if (((st >> pin) & 1u) == val) {
-        report_error(err, GTP_ENOTOGGLE, i);
-        ok = false;
-      }
+      const bool t_bad = (int32_t)t < 0 || (int32_t)t >= T;
+      const bool o_bad = !is_gs && (int32_t)t < (int32_t)tp;
+      const bool p_bad = (meta >> 5) != 0u || pin > n_in;
+      const bool g_bad = !p_bad && ((st >> pin) & 1u) == val;
+      const bool ok = !(t_bad || o_bad || p_bad || g_bad);
+      if (!ok)
+        report_error(err, t_bad ? GTP_ERANGE : (o_bad ? GTP_EORDER : (p_bad ? GTP_ERANGE : GTP_ENOTOGGLE)), s0 + jl);
       const uint32_t bn = ok ? bin_of(t, magic, shift, bin_ps) : 0u;
       float gE = 0.f, Gt = 0.f;
       if (BWD && ok) {
@@ -462,68 +453,64 @@ __global__ void __launch_bounds__(256) k_walk(LibView L, NetView N, const WinDes
           }
         }
       }
+      // internal energy: the descriptor holds the table element of this (gate, pin, edge)
+      // without the side bits; output events point at a valid table and take d.w instead
+      const bool is_out = (d.z >> 24) & 1u;
+      const uint32_t side = side_bits(spre & pmask, min(pin, n_in), n_in);
+      const float* p = sl.tab + (d.z & 0xFFFFu) + side * (uint32_t)tsize;
+      const float a0 = p[0], a1 = p[1], b0 = p[nl], b1 = p[nl + 1];
+      const float da = a1 - a0, db = b1 - b0;
+      const float lo = fmaf(__uint_as_float(d.y), da, a0);
+      const float hi = fmaf(__uint_as_float(d.y), db, b0);
+      const float e_in = fmaf(__uint_as_float(d.x), hi - lo, lo);
       float e = 0.f;
-      if (ok) {
-        if (pin < n_in) {
-          const uint32_t side = side_bits(spre & pmask, pin, n_in);
-          const float2 cc = crd[pin * 2u + val];
-          const float* p = tabs + (size_t)(((pin * 2u + val) << (n_in - 1u)) + side) * tsize + __float_as_uint(cc.y);
-          const float a0 = p[0], a1 = p[1], b0 = p[nl], b1 = p[nl + 1];
-          const float da = a1 - a0, db = b1 - b0;
-          const float lo = fmaf(fl, da, a0);
-          const float hi = fmaf(fl, db, b0);
-          e = fmaf(cc.x, hi - lo, lo);
-          if (BWD) {
-            const float dB = fmaf(cc.x, db - da, da) * rwl;
-            v0 += gE * es * dB;
-            v1 += gE * e;
-          } else {
-            v1 += e;
-          }
-        } else {
-          if (BWD) {
+      if (BWD) {
+        if (ok) {
+          if (is_out) {
             v0 += gE * L.half_v2;
           } else {
-            e = L.half_v2 * C;
-            v2 += e;
+            const float dB = fmaf(__uint_as_float(d.x), db - da, da) * __uint_as_float(d.w);
+            v0 += gE * sl.escale[cell] * dB;
+            v1 += gE * e_in;
           }
         }
+      } else if (ok) {
+        e = is_out ? __uint_as_float(d.w) : e_in;
+        if (is_out) v2 += e; else v1 += e;
       }
       if (pin <= n_in) st = (st & ~(1u << pin)) | (val << pin);
       st &= pmask;
-      // last record of its gate / of its timestamp group (all from shared memory)
+      // last record of its gate / of its timestamp group (from shared memory)
       bool gate_end, tail;
-      if (i + 1 >= n_ev) {
+      if (s0 + jl + 1 >= n_ev) {  // last record of the window
         gate_end = tail = true;
-      } else if (k + 1 < K) {
-        gate_end = gid[(k + 1) * 32 + lane] >= 0;
-        tail = gate_end || stage[(k + 1) * 32 + lane].x != t;
-      } else if (lane < 31) {
-        gate_end = gid[lane + 1] >= 0;
-        tail = gate_end || stage[lane + 1].x != t;
-      } else {
+      } else if (jl + 1 >= n_rem) {  // last record of the segment
         gate_end = next_is_gs;
         tail = gate_end || t_next_seg != t;
+      } else if (k + 1 < K) {
+        gate_end = ((gs_mask >> (k + 1)) & 1u) != 0u;
+        tail = gate_end || rec_s[(k + 1) * 32 + lane].x != t;
+      } else {  // the next record is the next lane's first
+        gate_end = gid_s[lane + 1] != gg;
+        tail = gate_end || rec_s[lane + 1].x != t;
       }
-      if (!BWD) {
-        if (ok) {
-          float add = 0.f, dp = 0.f;
-          if (tail) {
-            dp = leak[st] - leak[spre & pmask];
-            add = dp * (float)((int32_t)((bn + 1u) * bin_ps) - (int32_t)t) * 1e-6f;
-          }
-          if (bn != pb) {
-            if (pb != 0xFFFFFFFFu) red_bin(Wp->bins, pb, pe, pdp);
-            pb = bn;
-            pe = 0.f;
-            pdp = 0.f;
-          }
-          pe += e + add;
-          pdp += dp;
+      if (!BWD && ok) {
+        float add = 0.f, dp = 0.f;
+        if (tail) {
+          dp = leak[st] - leak[spre & pmask];
+          add = dp * (float)((int32_t)((bn + 1u) * bin_ps) - (int32_t)t) * 1e-6f;
         }
+        if (bn != pb) {
+          if (pb != 0xFFFFFFFFu) red_bin(Wp->bins, pb, pe, pdp);
+          pb = bn;
+          pe = 0.f;
+          pdp = 0.f;
+        }
+        pe += e + add;
+        pdp += dp;
       }
       last_closed = gate_end;
-      if (last_closed) {
+      if (gate_end) {
         if (BWD) {
           v2 += leak[st] * (Wp->g_total - Gt) * 1e-6f;
           atomicAdd(wacc + cell, v1);
@@ -631,7 +618,7 @@ __global__ void __launch_bounds__(256) k_walk(LibView L, NetView N, const WinDes
 template <int K, bool BWD>
 size_t walk_smem(const LibView& L, int block, int n_win) {
   size_t b = smem_lib_bytes(L) + (((size_t)(n_win + 1) * 8 + 15) & ~(size_t)15) +
-             (size_t)(block / 32) * 32 * K * (sizeof(uint2) + sizeof(int));
+             (size_t)(block / 32) * 32 * K * (sizeof(uint4) + sizeof(uint2) + sizeof(int));
   if (BWD) b += (size_t)(block / 32) * 2 * L.n_cells * (sizeof(double) + sizeof(float));
   return b;
 }
