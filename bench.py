@@ -49,6 +49,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
+    p.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
     return p.parse_args()
 
 
@@ -334,6 +335,11 @@ def run_ours(args, cfg_name):
                "sample": f"FP64 oracle, single thread, on {g:,} randomly chosen gates of this workload "
                          f"({ev:,} events, all {n_bins:,} bins), {t:.1f} s"}
 
+    extras = {}
+    if rank == 0 and not args.no_extras and cfg_name == "large":
+        extras["batched"] = measure_batched(eng, dev, max(3, min(args.steps // 10, 10)))
+        extras["adjoint"] = measure_adjoint(eng, dev, max(3, min(args.steps // 10, 10)))
+
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -353,8 +359,97 @@ def run_ours(args, cfg_name):
             "gpu_launches": int(launches),
             "clocks": clocks,
         }
+        out.update(extras)
         print(json.dumps(out), flush=True)
     eng.close()
+
+
+# ------------------------------------------------------------------ batched and adjoint forms
+def _events_per_s(fn, steps, dev):
+    import torch
+    fn()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1) / steps  # ms
+
+
+def measure_batched(eng, dev, steps):
+    """64 windows of uneven length over a 200k-gate netlist: autotuned plan,
+    one persistent launch per run, replayed from a CUDA graph, against the
+    same windows run one at a time through gtp_run_power."""
+    import torch
+
+    import synth
+    from paper_2609_05960_gb300 import gtpower
+
+    lib = synth.make_library(1)
+    net = synth.make_netlist(lib, synth.BATCHED_GATES, 2)
+    eng.load_library(lib)
+    eng.load_netlist(net)
+    wins = synth.batched_windows()
+    keep, total = [], 0
+    for w, spec in enumerate(wins):
+        counts = synth.zipf_counts(synth.BATCHED_GATES, spec["n_events"], 1.2, 100_000, spec["seed"])
+        tr, rec = synth.make_trace_gpu(net, counts, spec["window_ps"], spec["seed"], device=dev)
+        off = torch.from_numpy(tr.offsets).to(dev)
+        init = torch.from_numpy(tr.init_state).to(dev)
+        eng.load_events(w, window_ps=spec["window_ps"], offsets=off, records=rec, init_state=init, borrow=True)
+        keep.append((rec, off, init))
+        total += tr.n_events
+    ids = list(range(len(wins)))
+    tuned_ms = eng.autotune(ids, 10, iters=2)
+    plan = {k: eng.get_param(k) for k in ("records_per_thread", "block_threads", "ctas_per_sm")}
+    outs = [torch.empty(s["window_ps"] // 10, dtype=torch.float64, device=dev) for s in wins]
+    ms_b = _events_per_s(lambda: gtpower.gtp_run_power_batched(eng.ctx, ids, 10, outs, graph=True), steps, dev)
+    ref = [o.clone() for o in outs]
+    ms_p = _events_per_s(lambda: [gtpower.gtp_run_power(eng.ctx, w, 10, outs[w]) for w in ids], steps, dev)
+    diff = max(float(((o - r).abs() / r.abs()).max()) for o, r in zip(outs, ref))
+    del keep
+    return {"workload": f"{len(wins)} windows over {synth.BATCHED_GATES:,} gates, {total:,} events, "
+                        f"1k-100k bins of 10 ps", "events": total, "ms_per_run": ms_b,
+            "value": total / (ms_b * 1e-3), "unit": UNIT, "plain_ms_per_run": ms_p,
+            "plain_value": total / (ms_p * 1e-3), "speedup_vs_plain": ms_p / ms_b,
+            "max_rel_diff_vs_plain": diff, "autotuned_plan": plan, "autotune_best_ms": tuned_ms,
+            "graph": True}
+
+
+def measure_adjoint(eng, dev, steps):
+    """500k gates, 100M events, 5 us, 10 ps bins: the adjoint walk (gradients
+    of sum P^2 + tau*LSE(P/tau)) against the forward walk on the same window."""
+    import torch
+
+    import synth
+    from paper_2609_05960_gb300 import gtpower, peak_loss
+
+    cfg = synth.CONFIGS["adjoint"]
+    lib = synth.make_library(cfg.seed_lib)
+    net = synth.make_netlist(lib, cfg.n_gates, cfg.seed_net)
+    eng.load_library(lib)
+    eng.load_netlist(net)
+    counts = synth.zipf_counts(cfg.n_gates, cfg.n_events, cfg.zipf_s, cfg.cap, cfg.seed_ev)
+    tr, rec = synth.make_trace_gpu(net, counts, cfg.window_ps, cfg.seed_ev, device=dev)
+    off = torch.from_numpy(tr.offsets).to(dev)
+    init = torch.from_numpy(tr.init_state).to(dev)
+    eng.load_events(0, window_ps=cfg.window_ps, offsets=off, records=rec, init_state=init, borrow=True)
+    nb = cfg.window_ps // cfg.bin_ps
+    wave = torch.empty(nb, dtype=torch.float64, device=dev)
+    gtpower.gtp_run_power(eng.ctx, 0, cfg.bin_ps, wave)
+    P = wave.clone().requires_grad_(True)
+    peak_loss(P).backward()
+    g = P.grad.to(torch.float32).contiguous()
+    kw = dict(dtype=torch.float32, device=dev)
+    dC, de, dl = torch.empty(cfg.n_gates, **kw), torch.empty(lib.n_cells, **kw), torch.empty(lib.n_cells, **kw)
+    ms_f = _events_per_s(lambda: gtpower.gtp_run_power(eng.ctx, 0, cfg.bin_ps, wave), steps, dev)
+    ms_b = _events_per_s(lambda: gtpower.gtp_run_power_backward(eng.ctx, 0, cfg.bin_ps, g, dC, de, dl), steps, dev)
+    n = tr.n_events
+    return {"workload": workload_desc(cfg, nb), "events": n, "ms_per_backward": ms_b, "value": n / (ms_b * 1e-3),
+            "unit": UNIT, "forward_ms": ms_f, "forward_value": n / (ms_f * 1e-3), "backward_over_forward": ms_b / ms_f,
+            "loss": "sum P^2 + tau*logsumexp(P/tau), P in mW, tau = 0.01*mean(P)"}
 
 
 def main():

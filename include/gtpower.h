@@ -219,7 +219,8 @@ int gtp_autotune(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_
 
 /* Engine tuning knobs; value < 0 restores the default.  Keys:
  * "records_per_thread" (4, 8, 16), "block_threads" (128, 256),
- * "ctas_per_sm" (0 = full occupancy), "kernel" (0 = segmented warp walk,
+ * "ctas_per_sm" (0 = full occupancy), "dense_min" (gates with more events are cut into segments; 1..4096),
+ * "kernel" (0 = density-split walk,
  * 1 = one thread per gate, a plain cross-check), "timing" (1 = time the
  * phases of later runs with CUDA events; read back with gtp_get_param keys
  * "t_gate_pass_ns", "t_seeds_ns", "t_walk_ns", "t_merge_ns", "n_timed",

@@ -47,12 +47,12 @@ struct Window {
   int64_t n_events = 0;
   DevBuf offsets, records, init;
   const uint2* borrowed = nullptr;
-  DevBuf e_leak, e_int, e_sw, final_state, bins, tiles, wave, seeds;
+  DevBuf e_leak, e_int, e_sw, final_state, bins, tiles, wave;
   bool has_result = false;
   int32_t last_bin_ps = 0;
   const uint2* rec() const { return borrowed ? borrowed : records.as<uint2>(); }
   void release() {
-    for (DevBuf* b : {&offsets, &records, &init, &e_leak, &e_int, &e_sw, &final_state, &bins, &tiles, &wave, &seeds})
+    for (DevBuf* b : {&offsets, &records, &init, &e_leak, &e_int, &e_sw, &final_state, &bins, &tiles, &wave})
       b->release();
     borrowed = nullptr;
     loaded = false;
@@ -63,11 +63,10 @@ struct Window {
 struct GraphKey {
   std::vector<int32_t> windows;
   int32_t bin_ps;
-  int64_t rpt, block, ctas, kernel;
-  const void* runs;
+  int64_t rpt, block, ctas, kernel, dmin, plan_gen;
   bool operator<(const GraphKey& o) const {
-    return std::tie(windows, bin_ps, rpt, block, ctas, kernel, runs) <
-           std::tie(o.windows, o.bin_ps, o.rpt, o.block, o.ctas, o.kernel, o.runs);
+    return std::tie(windows, bin_ps, rpt, block, ctas, kernel, dmin, plan_gen) <
+           std::tie(o.windows, o.bin_ps, o.rpt, o.block, o.ctas, o.kernel, o.dmin, o.plan_gen);
   }
 };
 
@@ -90,9 +89,13 @@ struct gtp_ctx {
   NetView N{};
   std::map<int, Window> windows;
   // launch plan: device descriptor table and its pinned host staging copy
-  DevBuf plan;  // WinDesc[kMaxWindows] | seg_base[kMaxWindows+1] | tile_base[kMaxWindows+1] | l0[kMaxWindows+1]
+  DevBuf plan;  // WinDesc[kMaxWindows] | tile_base[kMaxWindows+1] | l0[kMaxWindows+1]
   unsigned char* h_plan = nullptr;
-  DevBuf runs, cell_acc, grad, gtiles, dC_scratch;
+  // device-side work plan: dense segments, their seeds, sorted sparse gates, counters
+  DevBuf dtask, dseed, slist, counters, pruns;
+  int64_t dcap = 0, scap = 0;
+  int64_t plan_gen = 0;  // bumped whenever a plan buffer moves (captured graphs hold its pointers)
+  DevBuf cell_acc, grad, gtiles, dC_scratch;
   DevBuf d_err;
   DevError* h_err = nullptr;
   std::map<GraphKey, cudaGraphExec_t> graphs;
@@ -102,6 +105,7 @@ struct gtp_ctx {
   int64_t p_rpt = 8;
   int64_t p_block = 256;
   int64_t p_ctas_per_sm = 0;
+  int64_t p_dense_min = 256;
   // phase timing (CUDA events on the context stream) and launch counting
   bool timing = false;
   cudaEvent_t ev[8] = {};
@@ -112,12 +116,11 @@ struct gtp_ctx {
 
 namespace {
 
-size_t plan_bytes() { return sizeof(WinDesc) * kMaxWindows + 3 * sizeof(int64_t) * (kMaxWindows + 1); }
+size_t plan_bytes() { return sizeof(WinDesc) * kMaxWindows + 2 * sizeof(int64_t) * (kMaxWindows + 1); }
 WinDesc* plan_wins(void* base) { return static_cast<WinDesc*>(base); }
-int64_t* plan_seg_base(void* base) {
+int64_t* plan_tile_base(void* base) {
   return reinterpret_cast<int64_t*>(static_cast<unsigned char*>(base) + sizeof(WinDesc) * kMaxWindows);
 }
-int64_t* plan_tile_base(void* base) { return plan_seg_base(base) + (kMaxWindows + 1); }
 double* plan_l0(void* base) { return reinterpret_cast<double*>(plan_tile_base(base) + (kMaxWindows + 1)); }
 
 int fail(gtp_ctx* c, int code, const std::string& msg) {
@@ -207,7 +210,6 @@ int build_plan(gtp_ctx* ctx, const std::vector<Window*>& ws, int32_t bin_ps, con
   const int n = (int)ws.size();
   if (n <= 0 || n > kMaxWindows) return fail(ctx, GTP_EINVAL, "between 1 and 1024 windows per run");
   WinDesc* hw = plan_wins(ctx->h_plan);
-  int64_t* hs = plan_seg_base(ctx->h_plan);
   int64_t* ht = plan_tile_base(ctx->h_plan);
   double* dl0 = plan_l0(ctx->plan.p);
   const int64_t G = ctx->N.n_gates;
@@ -218,7 +220,7 @@ int build_plan(gtp_ctx* ctx, const std::vector<Window*>& ws, int32_t bin_ps, con
     if (bin_ps <= 0 || W.window_ps % bin_ps != 0)
       return fail(ctx, GTP_ERANGE, "window_ps must be a multiple of bin_ps > 0");
     const int64_t nb = W.window_ps / bin_ps;
-    const int64_t n_seg = (W.n_events + seg_len - 1) / seg_len;
+    const int64_t n_seg = W.n_events / seg_len + G + 1;  // bound on the dense segments of this window
     const int nt = merge_tiles((int)nb);
     CU(W.e_leak.reserve(sizeof(double) * G), "alloc e_leak");
     CU(W.e_int.reserve(sizeof(double) * G), "alloc e_int");
@@ -226,12 +228,10 @@ int build_plan(gtp_ctx* ctx, const std::vector<Window*>& ws, int32_t bin_ps, con
     CU(W.final_state.reserve((size_t)G), "alloc final_state");
     CU(W.bins.reserve(sizeof(float2) * nb), "alloc bins");
     CU(W.tiles.reserve(sizeof(double) * (size_t)nt), "alloc tiles");
-    CU(W.seeds.reserve(sizeof(Seed) * (size_t)(n_seg + 1)), "alloc seeds");
     WinDesc d{};
     d.offsets = W.offsets.as<int64_t>();
     d.rec = W.rec();
     d.init = W.init.as<uint8_t>();
-    d.seeds = W.seeds.as<Seed>();
     d.e_leak = W.e_leak.as<double>();
     d.e_int = W.e_int.as<double>();
     d.e_sw = W.e_sw.as<double>();
@@ -243,8 +243,6 @@ int build_plan(gtp_ctx* ctx, const std::vector<Window*>& ws, int32_t bin_ps, con
     d.grad = backward ? ctx->grad.as<float2>() : nullptr;
     d.dC = nullptr;
     d.n_events = W.n_events;
-    d.seg_base = sb;
-    d.n_seg = n_seg;
     d.tile_base = tb;
     d.n_tiles = nt;
     d.window_ps = (int32_t)W.window_ps;
@@ -252,14 +250,27 @@ int build_plan(gtp_ctx* ctx, const std::vector<Window*>& ws, int32_t bin_ps, con
     bin_magic(bin_ps, &d.bin_magic, &d.bin_shift);
     d.n_bins = (int32_t)nb;
     hw[i] = d;
-    hs[i] = sb;
     ht[i] = tb;
     sb += n_seg;
     tb += nt;
   }
-  hs[n] = sb;
   ht[n] = tb;
-  CU(ctx->runs.reserve(sizeof(int64_t) * (size_t)(sb + 1)), "alloc runs");
+  if (sb > ctx->dcap) {
+    CU(ctx->dtask.reserve(sizeof(int4) * (size_t)sb), "alloc dense tasks");
+    CU(ctx->dseed.reserve(sizeof(Seed) * (size_t)sb), "alloc seeds");
+    CU(ctx->pruns.reserve(sizeof(int64_t) * (size_t)sb), "alloc seed fix-up list");
+    ctx->dcap = sb;
+    ++ctx->plan_gen;
+  }
+  if ((int64_t)n * G > ctx->scap) {
+    CU(ctx->slist.reserve(sizeof(int2) * (size_t)n * G), "alloc sparse list");
+    ctx->scap = (int64_t)n * G;
+    ++ctx->plan_gen;
+  }
+  if (!ctx->counters.p) {
+    CU(ctx->counters.reserve(sizeof(unsigned long long) * plan_counter_slots(4096)), "alloc plan counters");
+    ++ctx->plan_gen;
+  }
   *n_seg_total = sb;
   *n_tiles_total = tb;
   return GTP_OK;
@@ -267,24 +278,30 @@ int build_plan(gtp_ctx* ctx, const std::vector<Window*>& ws, int32_t bin_ps, con
 
 int upload_plan(gtp_ctx* ctx, int n, cudaStream_t st) {
   CU(cudaMemcpyAsync(ctx->plan.p, ctx->h_plan, sizeof(WinDesc) * n, cudaMemcpyHostToDevice, st), "upload plan");
-  CU(cudaMemcpyAsync(plan_seg_base(ctx->plan.p), plan_seg_base(ctx->h_plan), sizeof(int64_t) * (kMaxWindows + 1) * 2,
+  CU(cudaMemcpyAsync(plan_tile_base(ctx->plan.p), plan_tile_base(ctx->h_plan), sizeof(int64_t) * (kMaxWindows + 1),
                      cudaMemcpyHostToDevice, st), "upload plan bases");
   return GTP_OK;
 }
 
-WalkArgs walk_args(gtp_ctx* ctx, int n, int64_t n_seg_total) {
+WalkArgs walk_args(gtp_ctx* ctx, int n) {
   WalkArgs A{};
   A.wins = plan_wins(ctx->plan.p);
-  A.seg_base = plan_seg_base(ctx->plan.p);
   A.n_win = n;
-  A.n_seg_total = n_seg_total;
-  A.seg_len = seg_len_of(ctx);
   A.rpt = (int)ctx->p_rpt;
+  A.dense_min = (int)ctx->p_dense_min;
   A.block = (int)ctx->p_block;
   A.grid = ctx->p_ctas_per_sm > 0 ? (int)(ctx->p_ctas_per_sm * ctx->n_sm) : 0;
   A.n_sm = ctx->n_sm;
   A.err = ctx->d_err.as<DevError>();
   A.cell_acc = ctx->cell_acc.as<double>();
+  A.plan.dtask = ctx->dtask.as<int4>();
+  A.plan.dseed = ctx->dseed.as<Seed>();
+  A.plan.slist = ctx->slist.as<int2>();
+  A.plan.counters = ctx->counters.as<unsigned long long>();
+  A.plan.runs = ctx->pruns.as<int64_t>();
+  A.plan.dcap = ctx->dcap;
+  A.plan.scap = ctx->scap;
+  A.n_gates = ctx->N.n_gates;
   return A;
 }
 
@@ -316,18 +333,18 @@ int enqueue_forward(gtp_ctx* ctx, int n, int64_t n_seg_total, int64_t n_tiles_to
   ctx->launches += 2;
   mark(ctx, 2, st);
   if (any_events) {
-    const WalkArgs A = walk_args(ctx, n, n_seg_total);
+    const WalkArgs A = walk_args(ctx, n);
     if (ctx->p_kernel == 1) {
       mark(ctx, 3, st);
       mark(ctx, 4, st);
       CU(launch_walk_per_gate(ctx->L, ctx->N, dw, n, ctx->d_err.as<DevError>(), st), "walk (per gate)");
       ctx->launches += 1;
     } else {
-      CU(launch_seeds(ctx->N, ctx->L, A, ctx->runs.as<int64_t>(), st), "seeds");
+      CU(launch_plan(ctx->N, ctx->L, A, st), "plan");
       mark(ctx, 3, st);
       mark(ctx, 4, st);
       CU(launch_walk(ctx->L, ctx->N, A, false, st), "walk");
-      ctx->launches += 4;
+      ctx->launches += 7;
     }
   } else {
     mark(ctx, 3, st);
@@ -404,7 +421,7 @@ int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, dou
   CU(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(DevError), ctx->stream), "zero status");
   if (use_graph) {
     const GraphKey key{std::vector<int32_t>(windows, windows + n), bin_ps, ctx->p_rpt, ctx->p_block,
-                       ctx->p_ctas_per_sm, ctx->p_kernel, ctx->runs.p};
+                       ctx->p_ctas_per_sm, ctx->p_kernel, ctx->p_dense_min, ctx->plan_gen};
     auto it = ctx->graphs.find(key);
     if (it == ctx->graphs.end()) {
       if (!ctx->capture_stream) CU(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking), "stream");
@@ -427,7 +444,7 @@ int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, dou
     }
     // the graph's first node uploads the descriptor table from the staging buffer
     CU(cudaGraphLaunch(it->second, ctx->stream), "graph launch");
-    ctx->launches += any_events ? (ctx->p_kernel == 1 ? 6 : 9) : 5;
+    ctx->launches += any_events ? (ctx->p_kernel == 1 ? 6 : 12) : 5;
   } else {
     RC(enqueue_forward(ctx, n, n_seg_total, n_tiles_total, any_events, ctx->stream));
   }
@@ -486,7 +503,8 @@ void gtp_destroy(gtp_ctx* ctx) {
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   for (auto& kv : ctx->windows) kv.second.release();
   for (DevBuf* b : {&ctx->tab, &ctx->leak, &ctx->cells, &ctx->table_cell, &ctx->leak_cell, &ctx->escale, &ctx->lscale,
-                    &ctx->cell, &ctx->load, &ctx->slew, &ctx->desc, &ctx->plan, &ctx->runs,
+                    &ctx->cell, &ctx->load, &ctx->slew, &ctx->desc, &ctx->plan, &ctx->dtask, &ctx->dseed, &ctx->slist,
+                    &ctx->counters, &ctx->pruns,
                     &ctx->cell_acc, &ctx->grad, &ctx->gtiles, &ctx->dC_scratch, &ctx->d_err})
     b->release();
   if (ctx->h_err) cudaFreeHost(ctx->h_err);
@@ -780,10 +798,10 @@ int gtp_run_power_backward(gtp_ctx* ctx, int32_t window, int32_t bin_ps, const f
   CU(launch_gate_pass_bwd(ctx->L, ctx->N, plan_wins(ctx->plan.p), ctx->cell_acc.as<double>(), st), "gate pass");
   ctx->launches += 4;
   if (W->n_events > 0) {
-    const WalkArgs A = walk_args(ctx, 1, n_seg_total);
-    CU(launch_seeds(ctx->N, ctx->L, A, ctx->runs.as<int64_t>(), st), "seeds");
+    const WalkArgs A = walk_args(ctx, 1);
+    CU(launch_plan(ctx->N, ctx->L, A, st), "plan");
     CU(launch_walk(ctx->L, ctx->N, A, true, st), "adjoint walk");
-    ctx->launches += 4;
+    ctx->launches += 7;
   }
   if (d_escale || d_lscale) {
     CU(launch_cells_out(ctx->cell_acc.as<double>(), ctx->L.n_cells, d_escale, d_lscale, st), "cell gradients");
@@ -806,18 +824,19 @@ int gtp_autotune(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_
   CU(cudaEventCreate(&e0), "event");
   CU(cudaEventCreate(&e1), "event");
   double best = 1e300;
-  int64_t br = ctx->p_rpt, bb = ctx->p_block, bc = ctx->p_ctas_per_sm;
+  int64_t br = ctx->p_rpt, bb = ctx->p_block, bc = ctx->p_dense_min;
   std::vector<double*> none(n_windows, nullptr);
   const int rpts[] = {4, 8, 16};
   const int blocks[] = {128, 256};
-  const int ctas[] = {0, 1, 2, 4};
+  const int dmins[] = {64, 256, 1024};
   int rc = GTP_OK;
+  ctx->p_ctas_per_sm = 0;
   for (int r : rpts) {
     for (int b : blocks) {
-      for (int c : ctas) {
+      for (int c : dmins) {
         ctx->p_rpt = r;
         ctx->p_block = b;
-        ctx->p_ctas_per_sm = c;
+        ctx->p_dense_min = c;
         rc = run_forward(ctx, windows, n_windows, bin_ps, none.data(), GTP_DEVICE, false);  // warm-up
         if (rc != GTP_OK) break;
         cudaEventRecord(e0, ctx->stream);
@@ -843,7 +862,7 @@ int gtp_autotune(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_
   cudaEventDestroy(e1);
   ctx->p_rpt = br;
   ctx->p_block = bb;
-  ctx->p_ctas_per_sm = bc;
+  ctx->p_dense_min = bc;
   ctx->p_kernel = keep_kernel;
   ctx->timing = keep_timing;
   if (best_ms) *best_ms = best;
@@ -866,6 +885,9 @@ int gtp_set_param(gtp_ctx* ctx, const char* key, int64_t value) {
   } else if (k == "ctas_per_sm") {
     if (value > 32) return fail(ctx, GTP_ERANGE, "ctas_per_sm must be <= 32");
     ctx->p_ctas_per_sm = value < 0 ? 0 : value;
+  } else if (k == "dense_min") {
+    if (value == 0 || value > 4096) return fail(ctx, GTP_ERANGE, "dense_min must be 1..4096");
+    ctx->p_dense_min = value < 0 ? 256 : value;
   } else if (k == "timing") {
     // 1: time the phases of every following run with CUDA events; any value resets the totals
     DeviceGuard dg(ctx->device);
@@ -888,6 +910,7 @@ int64_t gtp_get_param(const gtp_ctx* ctx, const char* key) {
   if (k == "records_per_thread") return ctx->p_rpt;
   if (k == "block_threads") return ctx->p_block;
   if (k == "ctas_per_sm") return ctx->p_ctas_per_sm;
+  if (k == "dense_min") return ctx->p_dense_min;
   if (k == "n_sm") return ctx->n_sm;
   if (k == "timing") return ctx->timing ? 1 : 0;
   if (k == "t_gate_pass_ns") return ctx->t_ns[0];

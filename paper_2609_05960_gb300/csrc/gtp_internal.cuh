@@ -9,8 +9,8 @@
 //             event descriptors derived from them once per netlist:
 //             desc[G][2*(stride+1)] (16 B each, see NetView)
 //   window    offsets[G+1] int64, records[E] 8 B {int32 t, uint32 meta},
-//             init[G] uint8, segment seeds (16 B per segment), per-gate
-//             outputs (FP64 energies, uint8 final state), and the bin
+//             init[G] uint8, per-gate outputs (FP64 energies, uint8 final
+//             state), and the bin
 //             accumulators float2[n_bins] = {dynamic + in-bin leakage energy
 //             (fJ), leakage-power step (nW)}
 #pragma once
@@ -76,7 +76,7 @@ struct DevError {
   int64_t index;
 };
 
-// Per-segment seed of the segmented walk (16 bytes).
+// Seed of one dense segment (16 bytes).
 struct Seed {
   int32_t gate;      // gate holding the segment's first record
   int32_t t_prev;    // time of the group before the first record's group (0 at gate start)
@@ -96,7 +96,6 @@ struct WinDesc {
   const int64_t* offsets;    // [G+1]
   const uint2* rec;          // [E]
   const uint8_t* init;       // [G]
-  Seed* seeds;               // [n_seg]
   double* e_leak;            // [G]
   double* e_int;             // [G]
   double* e_sw;              // [G]
@@ -108,8 +107,6 @@ struct WinDesc {
   const float2* grad;        // adjoint: [n_bins] {dL/dE_b, G(b * bin_ps)}
   float* dC;                 // adjoint: [G]
   int64_t n_events;
-  int64_t seg_base;          // first global segment of this window
-  int64_t n_seg;
   int64_t tile_base;         // first global merge tile of this window
   int32_t n_tiles;
   int32_t window_ps;
