@@ -228,6 +228,60 @@ int gtp_autotune(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_
 int gtp_set_param(gtp_ctx* ctx, const char* key, int64_t value);
 int64_t gtp_get_param(const gtp_ctx* ctx, const char* key);
 
+/* Largest window (in bins) gtp_run_power_noalloc accepts. */
+#define GTP_NOALLOC_MAX_BINS (1 << 19)
+
+/*
+ * gtp_run_power_noalloc - one window's power walk that allocates nothing.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc, such as code inside another framework's device
+ * memory pool (which owns every device byte), a host callback, or a caller
+ * that must not pay cudaMalloc/cudaFree's implicit synchronisation between
+ * its own launches.  It needs no context: inputs and outputs are the
+ * caller's, and the walk's scratch (bin accumulators, merge tile sums, L0,
+ * error word, cell map) lives in one fixed file-scope device array of about
+ * 4.2 MB (header 8 KB, tile sums 2 KB, GTP_NOALLOC_MAX_BINS x 8 bytes of bin
+ * accumulators), which every GPU that loads this library holds until the
+ * process exits.
+ *
+ * Runs on the calling thread's current device, enqueues on cuda_stream (a
+ * cudaStream_t of that device; NULL = the legacy default stream) and
+ * synchronises it before returning.  The first call on a device looks up the
+ * scratch array's device address (cudaGetSymbolAddress) and keeps it for
+ * later calls; make that first call outside any stream capture.  Calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Every call on a device shares the one scratch array and starts by clearing
+ * what must begin at zero (bins, L0, error word).  Calls whose GPU work
+ * overlaps (other host threads, other streams) race on the scratch and give
+ * undefined results: serialise them.
+ *
+ * Arguments, with the meaning, layout and units of gtp_load_library,
+ * gtp_load_netlist, gtp_load_events and gtp_run_power:
+ *   host memory:   n_in[n_cells] (n_cells <= 256), slew_axis[n_slew],
+ *                  load_axis[n_load]
+ *   device memory: e_int[n_e_int], p_leak[n_p_leak], cell[n_gates],
+ *                  load_ff[n_gates], slew_ps[n_gates][slew_stride][2],
+ *                  gate_offsets[n_gates+1], events[n_events] (8-byte
+ *                  aligned), init_state[n_gates]; outputs waveform_w[n_bins]
+ *                  (W), e_leak/e_int_out/e_sw[n_gates] (fJ, FP64) and
+ *                  final_state[n_gates], each of which may be NULL.
+ * Per-cell energy and leakage scales are 1.  n_bins = window_ps / bin_ps.
+ * Errors: GTP_ERANGE for n_bins > GTP_NOALLOC_MAX_BINS or the limits of
+ * gtp_load_library (checked before any work is enqueued), GTP_EINVAL for bad
+ * sizes or pointers and for a malformed CSR or cell index (found by the
+ * kernel), GTP_EORDER / GTP_ERANGE / GTP_ENOTOGGLE for a malformed trace as
+ * in gtp_run_power (outputs are then undefined), GTP_ECUDA if a CUDA call
+ * fails.  There is no message string.
+ */
+int gtp_run_power_noalloc(void* cuda_stream, int32_t n_cells, const int32_t* n_in, float vdd, int32_t n_slew,
+                          const float* slew_axis, int32_t n_load, const float* load_axis, const float* e_int,
+                          int64_t n_e_int, const float* p_leak, int64_t n_p_leak, int64_t n_gates,
+                          const int32_t* cell, const float* load_ff, const float* slew_ps, int32_t slew_stride,
+                          int64_t window_ps, int64_t n_events, const int64_t* gate_offsets,
+                          const gtp_event* events, const uint8_t* init_state, int32_t bin_ps, double* waveform_w,
+                          double* e_leak, double* e_int_out, double* e_sw, uint8_t* final_state);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libgtpower.so")
 GTP_OK, GTP_EINVAL, GTP_EORDER, GTP_ERANGE, GTP_ENOTOGGLE = 0, -1, -2, -3, -4
 GTP_ENOMEM, GTP_ECUDA, GTP_ETIMEOUT, GTP_EDEVICE = -5, -6, -7, -8
 GTP_HOST, GTP_DEVICE, GTP_BORROW, GTP_GRAPH = 0, 1, 2, 4
+GTP_NOALLOC_MAX_BINS = 1 << 19
 
 CODE_NAMES = {GTP_EINVAL: "EINVAL", GTP_EORDER: "EORDER", GTP_ERANGE: "ERANGE", GTP_ENOTOGGLE: "ENOTOGGLE",
               GTP_ENOMEM: "ENOMEM", GTP_ECUDA: "ECUDA", GTP_ETIMEOUT: "ETIMEOUT", GTP_EDEVICE: "EDEVICE"}
@@ -27,7 +28,7 @@ CODE_NAMES = {GTP_EINVAL: "EINVAL", GTP_EORDER: "EORDER", GTP_ERANGE: "ERANGE", 
 ABI_SYMBOLS = ["gtp_create", "gtp_destroy", "gtp_set_stream", "gtp_last_error", "gtp_load_library",
                "gtp_set_scales", "gtp_load_netlist", "gtp_set_load", "gtp_load_events", "gtp_run_power",
                "gtp_gate_energy", "gtp_run_power_batched", "gtp_run_power_backward", "gtp_autotune",
-               "gtp_set_param", "gtp_get_param"]
+               "gtp_set_param", "gtp_get_param", "gtp_run_power_noalloc"]
 
 
 class GtpError(RuntimeError):
@@ -65,6 +66,8 @@ def load(path: str = LIB_PATH):
         "gtp_autotune": ([P, I32, P, I32, I32, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "gtp_set_param": ([P, ctypes.c_char_p, I64], ctypes.c_int),
         "gtp_get_param": ([P, ctypes.c_char_p], I64),
+        "gtp_run_power_noalloc": ([P, I32, P, F, I32, P, I32, P, P, I64, P, I64, I64, P, P, P, I32, I64, I64, P, P, P,
+                                   I32, P, P, P, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -209,6 +212,38 @@ def gtp_set_param(ctx, key: str, value: int) -> None:
 
 def gtp_get_param(ctx, key: str) -> int:
     return int(load().gtp_get_param(ctx, key.encode()))
+
+
+def gtp_run_power_noalloc(n_in, vdd, slew_axis, load_axis, e_int, p_leak, cell, load_ff, slew_ps, window_ps: int,
+                          gate_offsets, events, init_state, bin_ps: int, waveform=None, e_leak=None, e_int_out=None,
+                          e_sw=None, final_state=None, stream: Optional[int] = None) -> None:
+    """The allocation-free single-window walk.  n_in and the axes are host
+    arrays; every other array is a contiguous CUDA tensor on the current
+    device (slew_ps shaped [G, stride, 2], events [E, 2] int32); outputs may
+    be None.  Raises GtpError with the returned code."""
+    import torch
+    ni = np.ascontiguousarray(n_in, np.int32)
+    sa = np.ascontiguousarray(slew_axis, np.float32)
+    la = np.ascontiguousarray(load_axis, np.float32)
+    want = [(e_int, torch.float32), (p_leak, torch.float32), (cell, torch.int32), (load_ff, torch.float32),
+            (slew_ps, torch.float32), (gate_offsets, torch.int64), (events, torch.int32), (init_state, torch.uint8),
+            (waveform, torch.float64), (e_leak, torch.float64), (e_int_out, torch.float64), (e_sw, torch.float64),
+            (final_state, torch.uint8)]
+    for t, dt in want:
+        if t is not None and (not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dt
+                              or not t.is_contiguous()):
+            raise TypeError(f"gtp_run_power_noalloc: expected a contiguous CUDA {dt} tensor")
+    ptr = lambda t: None if t is None else t.data_ptr()
+    G = int(cell.numel())
+    rc = load().gtp_run_power_noalloc(stream, len(ni), ni.ctypes.data, float(vdd), len(sa), sa.ctypes.data, len(la),
+                                      la.ctypes.data, ptr(e_int), int(e_int.numel()), ptr(p_leak),
+                                      int(p_leak.numel()), G, ptr(cell), ptr(load_ff), ptr(slew_ps),
+                                      int(slew_ps.shape[1]) if slew_ps.dim() == 3 else int(slew_ps.numel() // (2 * G)),
+                                      int(window_ps), int(events.shape[0]), ptr(gate_offsets), ptr(events),
+                                      ptr(init_state), int(bin_ps), ptr(waveform), ptr(e_leak), ptr(e_int_out),
+                                      ptr(e_sw), ptr(final_state))
+    if rc != GTP_OK:
+        raise GtpError(rc, "gtp_run_power_noalloc failed")
 
 
 # ------------------------------------------------------------------ convenience object
