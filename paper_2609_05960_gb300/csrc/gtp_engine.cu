@@ -92,8 +92,8 @@ struct gtp_ctx {
   DevBuf plan;  // WinDesc[kMaxWindows] | tile_base[kMaxWindows+1] | l0[kMaxWindows+1]
   unsigned char* h_plan = nullptr;
   // device-side work plan: dense segments, their seeds, sorted sparse gates, counters
-  DevBuf dtask, dseed, slist, counters, pruns;
-  int64_t dcap = 0, scap = 0;
+  DevBuf glist, counters;
+  int64_t gcap = 0;
   int64_t plan_gen = 0;  // bumped whenever a plan buffer moves (captured graphs hold its pointers)
   DevBuf cell_acc, grad, gtiles, dC_scratch;
   DevBuf d_err;
@@ -220,7 +220,7 @@ int build_plan(gtp_ctx* ctx, const std::vector<Window*>& ws, int32_t bin_ps, con
     if (bin_ps <= 0 || W.window_ps % bin_ps != 0)
       return fail(ctx, GTP_ERANGE, "window_ps must be a multiple of bin_ps > 0");
     const int64_t nb = W.window_ps / bin_ps;
-    const int64_t n_seg = W.n_events / seg_len + G + 1;  // bound on the dense segments of this window
+    const int64_t n_seg = W.n_events / seg_len + G + 1;  // bound on the dense segments of this window (reported)
     const int nt = merge_tiles((int)nb);
     CU(W.e_leak.reserve(sizeof(double) * G), "alloc e_leak");
     CU(W.e_int.reserve(sizeof(double) * G), "alloc e_int");
@@ -255,16 +255,9 @@ int build_plan(gtp_ctx* ctx, const std::vector<Window*>& ws, int32_t bin_ps, con
     tb += nt;
   }
   ht[n] = tb;
-  if (sb > ctx->dcap) {
-    CU(ctx->dtask.reserve(sizeof(int4) * (size_t)sb), "alloc dense tasks");
-    CU(ctx->dseed.reserve(sizeof(Seed) * (size_t)sb), "alloc seeds");
-    CU(ctx->pruns.reserve(sizeof(int64_t) * (size_t)sb), "alloc seed fix-up list");
-    ctx->dcap = sb;
-    ++ctx->plan_gen;
-  }
-  if ((int64_t)n * G > ctx->scap) {
-    CU(ctx->slist.reserve(sizeof(int2) * (size_t)n * G), "alloc sparse list");
-    ctx->scap = (int64_t)n * G;
+  if ((int64_t)n * G > ctx->gcap) {
+    CU(ctx->glist.reserve(sizeof(int2) * (size_t)n * G), "alloc work list");
+    ctx->gcap = (int64_t)n * G;
     ++ctx->plan_gen;
   }
   if (!ctx->counters.p) {
@@ -294,13 +287,9 @@ WalkArgs walk_args(gtp_ctx* ctx, int n) {
   A.n_sm = ctx->n_sm;
   A.err = ctx->d_err.as<DevError>();
   A.cell_acc = ctx->cell_acc.as<double>();
-  A.plan.dtask = ctx->dtask.as<int4>();
-  A.plan.dseed = ctx->dseed.as<Seed>();
-  A.plan.slist = ctx->slist.as<int2>();
+  A.plan.glist = ctx->glist.as<int2>();
   A.plan.counters = ctx->counters.as<unsigned long long>();
-  A.plan.runs = ctx->pruns.as<int64_t>();
-  A.plan.dcap = ctx->dcap;
-  A.plan.scap = ctx->scap;
+  A.plan.gcap = ctx->gcap;
   A.n_gates = ctx->N.n_gates;
   return A;
 }
@@ -344,7 +333,7 @@ int enqueue_forward(gtp_ctx* ctx, int n, int64_t n_seg_total, int64_t n_tiles_to
       mark(ctx, 3, st);
       mark(ctx, 4, st);
       CU(launch_walk(ctx->L, ctx->N, A, false, st), "walk");
-      ctx->launches += 7;
+      ctx->launches += 5;
     }
   } else {
     mark(ctx, 3, st);
@@ -444,7 +433,7 @@ int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, dou
     }
     // the graph's first node uploads the descriptor table from the staging buffer
     CU(cudaGraphLaunch(it->second, ctx->stream), "graph launch");
-    ctx->launches += any_events ? (ctx->p_kernel == 1 ? 6 : 12) : 5;
+    ctx->launches += any_events ? (ctx->p_kernel == 1 ? 6 : 10) : 5;
   } else {
     RC(enqueue_forward(ctx, n, n_seg_total, n_tiles_total, any_events, ctx->stream));
   }
@@ -503,8 +492,8 @@ void gtp_destroy(gtp_ctx* ctx) {
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   for (auto& kv : ctx->windows) kv.second.release();
   for (DevBuf* b : {&ctx->tab, &ctx->leak, &ctx->cells, &ctx->table_cell, &ctx->leak_cell, &ctx->escale, &ctx->lscale,
-                    &ctx->cell, &ctx->load, &ctx->slew, &ctx->desc, &ctx->plan, &ctx->dtask, &ctx->dseed, &ctx->slist,
-                    &ctx->counters, &ctx->pruns,
+                    &ctx->cell, &ctx->load, &ctx->slew, &ctx->desc, &ctx->plan, &ctx->glist,
+                    &ctx->counters,
                     &ctx->cell_acc, &ctx->grad, &ctx->gtiles, &ctx->dC_scratch, &ctx->d_err})
     b->release();
   if (ctx->h_err) cudaFreeHost(ctx->h_err);
@@ -801,7 +790,7 @@ int gtp_run_power_backward(gtp_ctx* ctx, int32_t window, int32_t bin_ps, const f
     const WalkArgs A = walk_args(ctx, 1);
     CU(launch_plan(ctx->N, ctx->L, A, st), "plan");
     CU(launch_walk(ctx->L, ctx->N, A, true, st), "adjoint walk");
-    ctx->launches += 7;
+    ctx->launches += 5;
   }
   if (d_escale || d_lscale) {
     CU(launch_cells_out(ctx->cell_acc.as<double>(), ctx->L.n_cells, d_escale, d_lscale, st), "cell gradients");

@@ -76,20 +76,6 @@ struct DevError {
   int64_t index;
 };
 
-// Seed of one dense segment (16 bytes).
-struct Seed {
-  int32_t gate;      // gate holding the segment's first record
-  int32_t t_prev;    // time of the group before the first record's group (0 at gate start)
-  uint8_t x;         // state just before the first record
-  uint8_t p;         // state before the first record's timestamp group
-  uint8_t flags;     // kSeed* bits
-  uint8_t pad0;
-  int32_t pad1;
-};
-constexpr uint8_t kSeedGateStart = 1;   // first record starts its gate
-constexpr uint8_t kSeedGroupHead = 2;   // first record starts its timestamp group
-constexpr uint8_t kSeedUnresolved = 4;  // the bounded backward scan left pins open
-
 // One stimulus window as the kernels see it (single, batched and adjoint
 // runs all use an array of these in device memory).
 struct WinDesc {

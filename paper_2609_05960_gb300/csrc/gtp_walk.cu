@@ -1,42 +1,40 @@
 // The fused power walk (forward) and its adjoint, over one or many windows.
 //
 // Gates are split by event density (the paper's event-density-aware
-// partitioning, Sec. 4.2, re-cast for one GB300):
+// partitioning, Sec. 4.2, re-cast for one GB300), and every gate is owned by
+// exactly one warp or one CTA, so no walk waits on another CTA:
 //   * sparse gates (at most `dense_min` events) are packed one per lane: a
-//     warp takes 32 gates with equal event counts (a counting sort by count
-//     builds that order on the device) and each lane walks its gate's events
-//     sequentially, so a gate start and end are just the loop bounds;
-//   * dense gates are cut into time segments of 32*K events, one warp per
-//     segment and K consecutive events per lane; every segment lies inside
-//     one gate.
+//     warp takes 32 gates with equal event counts and each lane walks its
+//     gate's events sequentially;
+//   * medium gates (up to 8 segments of 32*K events) belong to one warp,
+//     which walks their segments in order, K consecutive events per lane;
+//   * big gates belong to one CTA of 8 warps, which walks them in chunks of
+//     8 consecutive segments, one per warp.
+// A counting sort on the device orders the work list big gates first
+// (largest first), then medium, then sparse, so persistent CTAs that take
+// work from a shared counter finish together.
 //
-// State tracking in a dense segment.  Every event sets one pin to a value, so
-// a run of events acts on the gate state as an affine bit map
-// S -> (S & keep) | set.  Maps compose associatively: each lane folds its K
-// events into a map, a warp shuffle scan composes the lane maps, and the
-// segment's incoming state comes from its seed.  Lookups use the state before
-// the event's timestamp group (Algorithm 1), so the scan carries a second map:
-// the state before the lane's last group.
+// State tracking inside a segment.  Every valid event toggles its pin, so a
+// run of events acts on the gate state by XOR; Algorithm 1 looks energies up
+// at the state before the event's timestamp group, so a run is summarised by
+// a transfer word (see xcompose): the XOR of its toggles, whether it holds a
+// group head, and the XOR of its toggles before its last head.  Transfers
+// compose associatively: each lane folds its K events, a warp shuffle scan
+// composes the lanes, and the state entering a segment is the composition of
+// the gate's earlier segments (carried by the warp, or exchanged through
+// shared memory across the 8 warps of a chunk).  An event that does not
+// toggle is reported (GTP_ENOTOGGLE).
 //
-// Seeds.  A dense segment's seed is the state just before its first event,
-// read from the events just before it: scanning backwards, the last event of
-// each pin fixes that pin's bit; pins without an event since the gate start
-// keep their initial bit.  A bounded scan that leaves a pin open (a pin idle
-// for a long stretch of a very long gate) hands the segment to a sequential
-// fix-up that walks forward from the previous segment's seed, chain by chain,
-// so the total fix-up cost stays linear.
-//
-// Energies (Sec. 2.2, Algorithm 1): each event's 16-byte descriptor (see
-// NetView) holds its table element (without the side bits) and its
-// interpolation weights; the internal energy is the bilinear value of the
-// state-indexed table selected by the side bits of the pre-group state; an
-// output event carries 0.5*C*Vdd^2.  Tables live in shared memory.
+// Energies (Sec. 2.2, Algorithm 1): for cells with at most kTabMaxIn inputs
+// the owning warp tabulates the gate's energy per (pin, edge, input state)
+// once per gate (bilinear NLDM value of the state-indexed table for an input
+// pin, 0.5*C*Vdd^2 for the output pin), so an event's energy is one
+// shared-memory load; wider cells interpolate per event.
 //
 // Forward outputs: one vector reduction {energy, leakage step} per distinct
 // bin of a lane's consecutive events (leakage step representation, see
-// gtp_kernels.cu); per-gate sums in FP32 per lane, then FP64 (a plain store
-// for a sparse gate, one warp reduction and FP64 atomic add per dense
-// segment).
+// gtp_kernels.cu); per-gate sums in FP32 per lane and segment, FP64 across
+// segments, one plain store per gate.
 //
 // Adjoint: the same walks gather g_b = dL/dE_b of each event's bin instead of
 // scattering energy, and accumulate dL/dC per gate and dL/d(escale),
@@ -50,188 +48,78 @@ namespace gtp {
 namespace {
 
 constexpr uint32_t kFull = 0xffffffffu;
-constexpr int kSeedScanSegments = 4;  // backward seed scan bound, in segments
-constexpr int KS = 8;                 // events staged per lane and chunk in the sparse walk
+constexpr int KS = 8;          // events staged per lane and chunk in the sparse walk
+constexpr int kWarps = 8;      // warps of a dense CTA (a big gate's chunk is kWarps segments)
+constexpr int kBigBuckets = 32;
+constexpr int kSparseBase = kBigBuckets + kWarps;
 
 // ------------------------------------------------------------------ plan
-// Per (window, gate): dense gates get consecutive slots in the segment list;
-// sparse gates are counted per event count.  Block-aggregated atomics.
-__global__ void k_plan_classify(const WinDesc* __restrict__ wins, int64_t G, int64_t seg_len, int dmin, PlanBufs P) {
-  extern __shared__ unsigned int sh[];  // [0, dmin]: sparse counts; [dmin+1]: dense slots; [dmin+2]: dense base
-  const WinDesc& W = wins[blockIdx.y];
-  unsigned long long* hist = P.counters + 3;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < G; base += (int64_t)gridDim.x * blockDim.x) {
-    for (int b = threadIdx.x; b <= dmin + 2; b += blockDim.x) sh[b] = 0u;
-    __syncthreads();
-    const int64_t g = base + threadIdx.x;
-    const int64_t c = g < G ? W.offsets[g + 1] - W.offsets[g] : 0;
-    unsigned int nseg = 0u, local = 0u;
-    if (c > dmin) {
-      nseg = (unsigned int)((c + seg_len - 1) / seg_len);
-      local = atomicAdd(&sh[dmin + 1], nseg);
-    } else if (c > 0) {
-      atomicAdd(&sh[c], 1u);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0 && sh[dmin + 1])
-      sh[dmin + 2] = (unsigned int)atomicAdd(P.counters, (unsigned long long)sh[dmin + 1]);
-    for (int b = 1 + threadIdx.x; b <= dmin; b += blockDim.x)
-      if (sh[b]) atomicAdd(hist + b, (unsigned long long)sh[b]);
-    __syncthreads();
-    if (nseg) {
-      const int64_t slot = (int64_t)sh[dmin + 2] + local;
-      for (unsigned int k = 0; k < nseg; ++k) P.dtask[slot + k] = make_int4((int)blockIdx.y, (int)g, (int)k, 0);
-    }
-    __syncthreads();
-  }
+// Work-list bucket of a gate with c > 0 events (lower buckets first):
+//   big    (c > kWarps * seg_len):        0..31 by decreasing floor(log2 c)
+//   medium (dense_min < c, <= 8 segments): 32..39 by decreasing segment count
+//   sparse (c <= dense_min):              40..40+dense_min-1 by decreasing c
+__device__ __forceinline__ int work_bucket(int64_t c, int dmin, int64_t seg_len) {
+  if (c <= dmin) return kSparseBase + dmin - (int)c;
+  if (c > kWarps * seg_len) return kBigBuckets - 1 - min(kBigBuckets - 1, 63 - __clzll((unsigned long long)c));
+  return kSparseBase - (int)((c + seg_len - 1) / seg_len);
 }
 
-// Bucket starts for the sparse list, largest event count first.
+__host__ __device__ constexpr int n_buckets(int dmin) { return kSparseBase + dmin; }
+
+// Per (window, gate): histogram of work buckets (block-aggregated).
+__global__ void k_plan_classify(const WinDesc* __restrict__ wins, int64_t G, int64_t seg_len, int dmin, PlanBufs P) {
+  extern __shared__ unsigned int sh[];
+  const int nb = n_buckets(dmin);
+  const WinDesc& W = wins[blockIdx.y];
+  unsigned long long* hist = P.counters + 4;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) sh[b] = 0u;
+  __syncthreads();
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < G; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = W.offsets[g + 1] - W.offsets[g];
+    if (c > 0) atomicAdd(&sh[work_bucket(c, dmin, seg_len)], 1u);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < nb; b += blockDim.x)
+    if (sh[b]) atomicAdd(hist + b, (unsigned long long)sh[b]);
+}
+
+// Bucket starts (exclusive scan in bucket order) and the three list sizes.
 __global__ void k_plan_scan(int dmin, PlanBufs P) {
   if (threadIdx.x != 0) return;
-  unsigned long long* hist = P.counters + 3;
-  unsigned long long* cursor = hist + dmin + 1;
-  unsigned long long acc = 0;
-  for (int c = dmin; c >= 1; --c) {
-    cursor[c] = acc;
-    acc += hist[c];
+  const int nb = n_buckets(dmin);
+  unsigned long long* hist = P.counters + 4;
+  unsigned long long* cursor = hist + nb;
+  unsigned long long acc = 0, part[3] = {0, 0, 0};
+  for (int b = 0; b < nb; ++b) {
+    cursor[b] = acc;
+    acc += hist[b];
+    part[b < kBigBuckets ? 0 : (b < kSparseBase ? 1 : 2)] += hist[b];
   }
-  P.counters[1] = acc;
+  P.counters[0] = part[0];
+  P.counters[1] = part[1];
+  P.counters[2] = part[2];
 }
 
-__global__ void k_plan_scatter(const WinDesc* __restrict__ wins, int64_t G, int dmin, PlanBufs P) {
-  extern __shared__ unsigned int sh[];  // [0, dmin]: local counts; [dmin+1, 2*dmin+1]: block bases
+__global__ void k_plan_scatter(const WinDesc* __restrict__ wins, int64_t G, int64_t seg_len, int dmin, PlanBufs P) {
+  extern __shared__ unsigned long long sbase[];  // [0, nb): block bases; then [0, nb) local counts (32-bit)
+  const int nb = n_buckets(dmin);
+  unsigned int* sh = reinterpret_cast<unsigned int*>(sbase + nb);
   const WinDesc& W = wins[blockIdx.y];
-  unsigned long long* cursor = P.counters + 3 + dmin + 1;
-  unsigned int* sbase = sh + dmin + 1;
+  unsigned long long* cursor = P.counters + 4 + nb;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < G; base += (int64_t)gridDim.x * blockDim.x) {
-    for (int b = threadIdx.x; b <= dmin; b += blockDim.x) sh[b] = 0u;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) sh[b] = 0u;
     __syncthreads();
     const int64_t g = base + threadIdx.x;
     const int64_t c = g < G ? W.offsets[g + 1] - W.offsets[g] : 0;
+    const int b = c > 0 ? work_bucket(c, dmin, seg_len) : -1;
     unsigned int local = 0u;
-    const bool sparse = c > 0 && c <= dmin;
-    if (sparse) local = atomicAdd(&sh[c], 1u);
+    if (b >= 0) local = atomicAdd(&sh[b], 1u);
     __syncthreads();
-    for (int b = 1 + threadIdx.x; b <= dmin; b += blockDim.x)
-      if (sh[b]) sbase[b] = (unsigned int)atomicAdd(cursor + b, (unsigned long long)sh[b]);
+    for (int k = threadIdx.x; k < nb; k += blockDim.x)
+      if (sh[k]) sbase[k] = atomicAdd(cursor + k, (unsigned long long)sh[k]);
     __syncthreads();
-    if (sparse) P.slist[(int64_t)sbase[c] + local] = make_int2((int)blockIdx.y, (int)g);
+    if (b >= 0) P.glist[(int64_t)sbase[b] + local] = make_int2((int)blockIdx.y, (int)g);
     __syncthreads();
-  }
-}
-
-// One thread per dense segment: the state just before its first event (x),
-// the state before that event's timestamp group (p), and the time of the
-// group before it.
-__global__ void k_dseed(LibView L, NetView N, const WinDesc* __restrict__ wins, int64_t seg_len, PlanBufs P) {
-  const int64_t n_task = (int64_t)P.counters[0];
-  const int64_t limit = seg_len * kSeedScanSegments;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_task; t += (int64_t)gridDim.x * blockDim.x) {
-    const int4 dt = P.dtask[t];
-    const WinDesc& W = wins[dt.x];
-    const int64_t g = dt.y;
-    const int64_t gs = W.offsets[g];
-    const int64_t s0 = gs + (int64_t)dt.z * seg_len;
-    const uint32_t init = W.init[g];
-    const uint32_t full = (2u << L.cells[N.cell[g]].n_in) - 1u;
-    Seed sd;
-    sd.gate = (int32_t)g;
-    sd.pad0 = 0;
-    sd.pad1 = 0;
-    if (dt.z == 0) {
-      sd.t_prev = 0;
-      sd.x = (uint8_t)(init & full);
-      sd.p = (uint8_t)(init & full);
-      sd.flags = kSeedGateStart | kSeedGroupHead;
-      P.dseed[t] = sd;
-      continue;
-    }
-    const uint2* rec = W.rec;
-    const uint32_t t0 = rec[s0].x;
-    int64_t h = s0;
-    while (h > gs && s0 - h < limit && rec[h - 1].x == t0) --h;
-    const bool head_found = h == gs || rec[h - 1].x != t0;
-    uint32_t xres = 0, xval = 0, pres = 0, pval = 0;
-    int64_t j = s0 - 1;
-    if (head_found) {
-      while (j >= gs && ((xres & pres) & full) != full && s0 - 1 - j < limit) {
-        const uint32_t meta = rec[j].y;
-        const uint32_t bit = (1u << (meta & 0xFu)) & 0xFFu;
-        const uint32_t v = (meta & 0x10u) ? bit : 0u;
-        if (!(xres & bit)) {
-          xres |= bit;
-          xval |= v;
-        }
-        if (j < h && !(pres & bit)) {
-          pres |= bit;
-          pval |= v;
-        }
-        --j;
-      }
-      if (j < gs) {  // reached the gate start: untouched pins keep their initial value
-        xval |= init & ~xres;
-        pval |= init & ~pres;
-        xres = pres = full;
-      }
-    }
-    const bool unresolved = !head_found || (xres & full) != full || (pres & full) != full;
-    sd.t_prev = (head_found && h > gs) ? (int32_t)rec[h - 1].x : 0;
-    sd.x = (uint8_t)(xval & full);
-    sd.p = (uint8_t)(pval & full);
-    sd.flags = (uint8_t)((head_found && h == s0 ? kSeedGroupHead : 0) | (unresolved ? kSeedUnresolved : 0));
-    P.dseed[t] = sd;
-    if (unresolved) {
-      const int64_t k = (int64_t)atomicAdd(P.counters + 2, 1ull);
-      P.runs[k] = t;
-    }
-  }
-}
-
-// Resolve seeds left partial by k_dseed: the head of each chain of
-// unresolved segments of a gate walks forward from the previous segment's
-// resolved seed (segments of one gate have consecutive slots).  The
-// unresolved flag stays set, since other threads read it to find chain heads.
-__global__ void k_dseed_fix(const WinDesc* __restrict__ wins, int64_t seg_len, PlanBufs P) {
-  const int64_t n = (int64_t)P.counters[2];
-  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t t = P.runs[u];
-    if (P.dseed[t - 1].flags & kSeedUnresolved) continue;  // not the head of its chain (t - 1: same gate)
-    const int4 dt = P.dtask[t];
-    const WinDesc& W = wins[dt.x];
-    const int64_t g = dt.y;
-    const int64_t gs = W.offsets[g], ge = W.offsets[g + 1];
-    const Seed an = P.dseed[t - 1];
-    const int64_t a = gs + (int64_t)(dt.z - 1) * seg_len;
-    uint32_t X = an.x, Pg = an.p;
-    int32_t tp = an.t_prev;
-    int32_t tcur = (int32_t)W.rec[a].x;
-    int64_t tk = t;
-    for (int64_t i = a; i < ge; ++i) {
-      const int32_t ti = (int32_t)W.rec[i].x;
-      const bool head = ti != tcur;
-      if (i > a && (i - gs) % seg_len == 0) {
-        if (!(P.dseed[tk].flags & kSeedUnresolved)) break;
-        Seed r;
-        r.gate = (int32_t)g;
-        r.x = (uint8_t)X;
-        r.p = (uint8_t)(head ? X : Pg);
-        r.t_prev = head ? tcur : tp;
-        r.flags = (uint8_t)((head ? kSeedGroupHead : 0) | kSeedUnresolved);
-        r.pad0 = 0;
-        r.pad1 = 0;
-        P.dseed[tk] = r;
-        ++tk;
-      }
-      if (head) {
-        tp = tcur;
-        tcur = ti;
-        Pg = X;
-      }
-      const uint32_t meta = W.rec[i].y;
-      const uint32_t bit = (1u << (meta & 0xFu)) & 0xFFu;
-      X = (X & ~bit) | ((meta & 0x10u) ? bit : 0u);
-    }
   }
 }
 
@@ -265,231 +153,499 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// ------------------------------------------------------------------ dense segments
-template <int K, bool BWD>
-__global__ void __launch_bounds__(256) k_dense(LibView L, NetView N, const WinDesc* __restrict__ wins, PlanBufs P,
-                                               DevError* err, double* __restrict__ cell_acc) {
+// ------------------------------------------------------------------ dense gates
+// Transfer word of a run of events:
+//   bits 0-7   X: XOR of the run's toggled pin bits
+//   bits 8-15  Y: XOR of the toggles before the run's last group head
+//   bit 16     H: the run holds a group head (Y is 0 without one)
+//   bit 17     A: absolute: X is the state after the run and Y the state
+//              before its last group (the state entering the run is folded in)
+// Applying a transfer to (state S, pre-group state P) gives
+// (S ^ X, H ? S ^ Y : P); xcompose(a, b) is "a, then b".
+constexpr uint32_t kXH = 1u << 16;
+constexpr uint32_t kXAbs = 1u << 17;
+constexpr int kTabMaxIn = 4;                                     // wider cells interpolate per event
+constexpr int kTabEntries = (kTabMaxIn + 1) << (kTabMaxIn + 1);  // (pin, edge, input state) energies
+constexpr int kLeakEntries = 2 << kTabMaxIn;
+
+__device__ __forceinline__ uint32_t xcompose(uint32_t a, uint32_t b) {
+  if (b & kXAbs) return b;
+  if (b & kXH) return (b ^ ((a & 0xFFu) * 0x101u)) | (a & kXAbs);
+  return a ^ b;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Swizzled position (in records) of record k of lane `row` in a warp's
+// staging buffer: 16-byte chunks of a lane's row are XOR-permuted so that
+// both the transposing 8-byte copies and the lanes' 16-byte reads are free of
+// bank conflicts.
+template <int K>
+__device__ __forceinline__ int stage_pos(int row, int k) {
+  constexpr int kShift = K == 16 ? 0 : (K == 8 ? 1 : 2);
+  const int sw = (row >> kShift) & (K / 2 - 1);
+  return row * K + ((((k >> 1) ^ sw) << 1) | (k & 1));
+}
+
+// Per-warp shared memory of the dense walk.
+struct DenseSmem {
+  uint2* rec;      // [2][32 * K] staged records (double buffer)
+  float* etab;     // [kTabEntries] energy per (pin, edge, input state); adjoint: unscaled
+  float* dtab;     // adjoint: [kTabEntries] escale * dE/dC
+  float* leak;     // [kLeakEntries] leakage per state (forward: scaled)
+  double* wacc;    // adjoint: [2 * n_cells] per-warp cell sums
+};
+
+// One gate as its owning warp sees it.
+struct DGate {
+  const WinDesc* W;
+  const uint2* rec;
+  int64_t g, ga, n;          // gate, first record, events
+  const uint4* dsc;          // the gate's event descriptors
+  const float* gleak;        // the cell's leakage entries (unscaled)
+  uint32_t cell, n_in, pmask, inmask, init;
+  float esc, lsc;            // energy scale; leakage scale (1 in the adjoint)
+  uint32_t T, bin_ps, magic, shift;
+};
+
+template <bool BWD>
+__device__ __forceinline__ DGate dense_gate(const LibView& L, const NetView& N, const WinDesc* __restrict__ wins,
+                                            int2 wg) {
+  DGate d;
+  d.W = wins + wg.x;
+  d.rec = d.W->rec;
+  d.g = wg.y;
+  d.ga = d.W->offsets[d.g];
+  d.n = d.W->offsets[d.g + 1] - d.ga;
+  d.cell = (uint32_t)N.cell[d.g];
+  const CellInfo ci = L.cells[d.cell];
+  d.n_in = (uint32_t)ci.n_in;
+  d.pmask = (2u << d.n_in) - 1u;
+  d.inmask = (1u << d.n_in) - 1u;
+  d.init = (uint32_t)d.W->init[d.g] & d.pmask;
+  d.esc = L.escale[d.cell];
+  d.lsc = BWD ? 1.f : L.lscale[d.cell];
+  d.dsc = N.desc + (size_t)d.g * N.dstride;
+  d.gleak = L.leak + ci.leak_base;
+  d.T = (uint32_t)d.W->window_ps;
+  d.bin_ps = (uint32_t)d.W->bin_ps;
+  d.magic = d.W->bin_magic;
+  d.shift = d.W->bin_shift;
+  return d;
+}
+
+// The gate's energy table and leakage row in the warp's shared memory.
+template <bool BWD>
+__device__ __forceinline__ void build_tables(const LibView& L, const DGate& d, const DenseSmem& sm, int lane) {
+  const int ne = (int)((d.n_in + 1u) << (d.n_in + 1u));
+  for (int e = lane; e < ne; e += 32) {
+    const uint32_t pv = (uint32_t)e >> d.n_in, s = (uint32_t)e & d.inmask;
+    const uint32_t pin = pv >> 1;
+    const uint4 q = __ldg(d.dsc + pv);
+    float E, dE;
+    if (pin < d.n_in) {
+      const float* p = L.tab + (q.z & 0xFFFFu) + side_bits(s, pin, d.n_in) * (uint32_t)L.tsize;
+      const float a0 = __ldg(p), a1 = __ldg(p + 1), b0 = __ldg(p + L.nl), b1 = __ldg(p + L.nl + 1);
+      const float fl = __uint_as_float(q.y), fs = __uint_as_float(q.x);
+      const float lo = fmaf(fl, a1 - a0, a0), hi = fmaf(fl, b1 - b0, b0);
+      const float eu = fmaf(fs, hi - lo, lo);
+      E = BWD ? eu : eu * d.esc;
+      dE = d.esc * (fmaf(fs, (b1 - b0) - (a1 - a0), a1 - a0) * __uint_as_float(q.w));
+    } else {
+      E = BWD ? 0.f : __uint_as_float(q.w);
+      dE = L.half_v2;
+    }
+    sm.etab[e] = E;
+    if (BWD) sm.dtab[e] = dE;
+  }
+  for (int s = lane; s < (int)(2u << d.n_in); s += 32) sm.leak[s] = __ldg(d.gleak + s) * d.lsc;
+}
+
+// Start the copy of segment `s` of the gate into staging buffer `buf`
+// (one commit group, possibly empty).
+template <int K>
+__device__ __forceinline__ void issue_segment(const DGate& d, int64_t s, uint2* buf, int lane) {
   constexpr int SEG = 32 * K;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const SmemLib sl = stage_library(L, smem, !BWD);
-  unsigned char* sp = smem + smem_lib_bytes(L);
-  const int n_wib = blockDim.x >> 5;
-  const int wib = threadIdx.x >> 5;
-  const int lane = threadIdx.x & 31;
-  const int dstride = N.dstride;
-  uint4* dblk = reinterpret_cast<uint4*>(sp) + (size_t)wib * dstride;  // the gate's event descriptors
-  sp += (size_t)n_wib * dstride * sizeof(uint4);
-  uint2* rec_s = reinterpret_cast<uint2*>(sp) + (size_t)wib * SEG;     // [k][lane]
-  sp += (size_t)n_wib * SEG * sizeof(uint2);
-  double* wacc = reinterpret_cast<double*>(sp) + (size_t)wib * 2 * L.n_cells;  // adjoint: per-warp cell sums
-  if (BWD)
-    for (int c = lane; c < 2 * L.n_cells; c += 32) wacc[c] = 0.0;
-  __syncthreads();
-
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t n_task = (int64_t)P.counters[0];
-  const int tsize = L.tsize, nl = L.nl;
-  const uint32_t dmax = (uint32_t)(dstride / 2 - 1);
-
-  for (int64_t tk = warp; tk < n_task; tk += n_warps) {
-    const int4 dt = P.dtask[tk];
-    const WinDesc* Wp = wins + dt.x;
-    const int64_t g = dt.y;
-    const int64_t* __restrict__ off = Wp->offsets;
-    const uint2* __restrict__ rec = Wp->rec;
-    const int64_t ga = off[g], ge = off[g + 1];
-    const int64_t s0 = ga + (int64_t)dt.z * SEG;
-    const int n_rem = (int)min((int64_t)SEG, ge - s0);
-    const bool last_seg = s0 + n_rem == ge;
-    const bool first_seg = dt.z == 0;
-    const int32_t T = Wp->window_ps;
-    const uint32_t bin_ps = (uint32_t)Wp->bin_ps, magic = Wp->bin_magic, shift = Wp->bin_shift;
-    const int j0 = lane * K;
-    const bool active = j0 < n_rem;
-
-    __syncwarp();
+  if (s * SEG < d.n) {
+    const int64_t s0 = d.ga + s * SEG;
+    const int n_rem = (int)min((int64_t)SEG, d.n - s * SEG);
 #pragma unroll
     for (int m = 0; m < K; ++m) {
       const int r = m * 32 + lane;
-      if (r < n_rem) rec_s[(r % K) * 32 + r / K] = __ldcs(rec + s0 + r);
+      if (r < n_rem) cp_async8(smem_addr(buf + stage_pos<K>(r / K, r % K)), d.rec + s0 + r);
     }
-    if (lane < dstride) dblk[lane] = __ldg(N.desc + (size_t)g * dstride + lane);
-    const Seed sd = P.dseed[tk];
-    uint32_t t_next = 0u;  // first event after the segment, for the group-tail test
-    if (lane == 31 && !last_seg) t_next = rec[s0 + n_rem].x;
-    const uint32_t cell = (uint32_t)N.cell[g];
-    const CellInfo ci = sl.cells[cell];
-    const uint32_t n_in = (uint32_t)ci.n_in;
-    const uint32_t pmask = (2u << n_in) - 1u;
-    const float* leak = sl.leak + ci.leak_base;
-    __syncwarp();
-    uint32_t t_before;
-    if (lane > 0) t_before = rec_s[(K - 1) * 32 + lane - 1].x;
-    else t_before = (sd.flags & kSeedGroupHead) ? (uint32_t)sd.t_prev : rec_s[0].x;
+  }
+  cp_async_commit();
+}
 
-    // ---- pass 1: group heads, range checks, the lane's state maps
-    uint32_t gh_mask = 0u;
-    uint32_t xk = 0xFFu, xs = 0u, pk = 0xFFu, ps = 0u, pm = 0u;
-    {
-      uint32_t tp = t_before;
-#pragma unroll 1
-      for (int k = 0; k < K; ++k) {
-        const int j = j0 + k;
-        if (j >= n_rem) break;
-        const uint2 r = rec_s[k * 32 + lane];
-        const bool gate_first = first_seg && j == 0;
-        const bool is_gh = gate_first || r.x != tp;
-        const bool t_bad = r.x >= (uint32_t)T;
-        const bool o_bad = !gate_first && (int32_t)r.x < (int32_t)tp;
-        const bool p_bad = (r.y >> 5) != 0u || (r.y & 0xFu) > n_in;
-        if (t_bad || o_bad || p_bad) report_error(err, bad_code(t_bad, o_bad, p_bad), s0 + j);
-        if (is_gh) {
-          pk = xk;
-          ps = xs;
-          pm = 1u;
-        }
-        const uint32_t bit = (1u << (r.y & 0xFu)) & 0xFFu;
-        xk &= ~bit;
-        xs = (xs & ~bit) | ((r.y & 0x10u) ? bit : 0u);
-        gh_mask |= (is_gh ? 1u : 0u) << k;
-        tp = r.x;
-      }
-    }
+// Record k of this lane from the staging buffer (t, meta).
+template <int K>
+__device__ __forceinline__ uint2 stage_rec(const uint2* buf, int lane, int k) {
+  return buf[stage_pos<K>(lane, k)];
+}
 
-    // ---- warp scan of lane maps: (X map, P map, P mode)
-    uint32_t wa = (xk & 0xFFu) | ((xs & 0xFFu) << 8) | ((pk & 0xFFu) << 16) | ((ps & 0xFFu) << 24);
-    uint32_t wb = pm;
+// One staged segment with its first pass done.
+struct Seg {
+  int64_t s0;
+  int n_rem, nk;             // events in the segment; this lane's events
+  uint32_t t_before;         // time of the event before the lane's first (0 at the gate start)
+  uint32_t t_after;          // time of the event after the lane's last (~0 at the gate end)
+  bool fh, last_seg;         // the lane's first event starts the gate; the segment ends it
+  uint32_t ex;               // transfer of the segment's events before this lane
+  uint32_t bad_r, bad_o;     // per-record check bits
+};
+
+// Pass 1 of segment s of the gate, staged in `buf` (its copy must have
+// landed): the lane's transfer, the warp scan of transfers and the record
+// checks.  Returns the segment's transfer (identity past the gate's end).
+template <int K>
+__device__ __forceinline__ uint32_t seg_front(const DGate& d, int64_t s, const uint2* buf, Seg& q, int lane) {
+  constexpr int SEG = 32 * K;
+  q.s0 = d.ga + s * SEG;
+  q.n_rem = (int)max((int64_t)0, min((int64_t)SEG, d.n - s * SEG));
+  const int j0 = lane * K;
+  q.nk = max(0, min(K, q.n_rem - j0));
+  q.last_seg = s * SEG + SEG >= d.n;
+  q.fh = s == 0 && lane == 0;
+  q.bad_r = 0u;
+  q.bad_o = 0u;
+  q.ex = 0u;
+  if (q.n_rem == 0) return 0u;
+  uint32_t t_edge = 0u;
+  if (lane == 0 && s > 0) t_edge = d.rec[q.s0 - 1].x;
+  if (lane == 31) t_edge = q.last_seg ? 0xFFFFFFFFu : d.rec[q.s0 + q.n_rem].x;
+  const uint32_t seg_after = __shfl_sync(kFull, t_edge, 31);
+  const uint32_t t_prev_lane = stage_rec<K>(buf, max(lane - 1, 0), K - 1).x;  // garbage where unused
+  const uint32_t t_next_lane = stage_rec<K>(buf, min(lane + 1, 31), 0).x;
+  q.t_before = lane == 0 ? t_edge : t_prev_lane;
+  q.t_after = j0 + K < q.n_rem ? t_next_lane : seg_after;
+
+  uint32_t X = 0u, Y = 0u, H = 0u;
+  uint32_t tp = q.t_before;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t oa = __shfl_up_sync(kFull, wa, o);
-      const uint32_t ob = __shfl_up_sync(kFull, wb, o);
-      if (lane >= o) {
-        const uint32_t Axk = oa & 0xFFu, Axs = (oa >> 8) & 0xFFu, Apk = (oa >> 16) & 0xFFu, Aps = oa >> 24;
-        const uint32_t Bxk = wa & 0xFFu, Bxs = (wa >> 8) & 0xFFu, Bpk = (wa >> 16) & 0xFFu, Bps = wa >> 24;
-        const uint32_t nxk = Axk & Bxk, nxs = (Axs & Bxk) | Bxs;
-        uint32_t npk, nps, npm;
-        if (wb) {
-          npk = Axk & Bpk;
-          nps = (Axs & Bpk) | Bps;
-          npm = 1u;
-        } else {
-          npk = Apk;
-          nps = Aps;
-          npm = ob;
-        }
-        wa = nxk | (nxs << 8) | (npk << 16) | (nps << 24);
-        wb = npm;
+  for (int k = 0; k < K; ++k) {
+    if (k < q.nk) {
+      const uint2 r = stage_rec<K>(buf, lane, k);
+      const uint32_t t = r.x, m = r.y;
+      const bool head = t != tp || (k == 0 && q.fh);
+      if (head) {
+        Y = X;
+        H = kXH;
       }
-    }
-    uint32_t ea = __shfl_up_sync(kFull, wa, 1), eb = __shfl_up_sync(kFull, wb, 1);
-    if (lane == 0) {
-      ea = 0xFFu;
-      eb = 0u;
-    }
-    uint32_t st = (((uint32_t)sd.x & (ea & 0xFFu)) | ((ea >> 8) & 0xFFu)) & pmask;
-    uint32_t spre = (eb ? (((uint32_t)sd.x & ((ea >> 16) & 0xFFu)) | (ea >> 24)) : (uint32_t)sd.p) & pmask;
-
-    // ---- pass 2: replay
-    float v0 = 0.f, v1 = 0.f, v2 = 0.f;  // forward: e_leak, e_int, e_sw; adjoint: dC, d_escale, d_lscale
-    uint32_t pb = 0xFFFFFFFFu;
-    float pe = 0.f, pdp = 0.f;
-    float Gcur = 0.f;  // adjoint: G(time of the current group)
-    if (BWD && active && !(first_seg && lane == 0)) {
-      const uint32_t tb = t_before;
-      if (tb < (uint32_t)T) {
-        const uint32_t bb = bin_of(tb, magic, shift, bin_ps);
-        const float2 gv = Wp->grad[bb];
-        Gcur = gv.y + gv.x * (float)(tb - bb * bin_ps);
-      }
-    }
-    uint32_t tp = t_before;
-#pragma unroll 1
-    for (int k = 0; k < K; ++k) {
-      const int j = j0 + k;
-      if (j >= n_rem) break;
-      const uint2 r = rec_s[k * 32 + lane];
-      const uint32_t t = r.x, pin = r.y & 0xFu, val = (r.y >> 4) & 1u;
-      const bool is_gh = (gh_mask >> k) & 1u;
-      if (is_gh) spre = st;
-      if (((st >> pin) & 1u) == val && pin <= n_in) report_error(err, GTP_ENOTOGGLE, s0 + j);
-      const bool ok = t < (uint32_t)T;
-      const uint32_t bn = ok ? bin_of(t, magic, shift, bin_ps) : 0u;
-      const uint4 d = dblk[min(pin, dmax) * 2u + val];
-      const bool is_out = (d.z >> 24) & 1u;
-      const EventOut eo = table_energy(sl, d, spre, pin, n_in, tsize, nl);
-      if (pin <= n_in) st = ((st & ~(1u << pin)) | (val << pin)) & pmask;
-      const bool seg_last = j + 1 == n_rem;
-      const bool gate_end = seg_last && last_seg;
-      bool tail;
-      if (seg_last) tail = gate_end || t_next != t;
-      else if (k + 1 < K) tail = rec_s[(k + 1) * 32 + lane].x != t;
-      else tail = rec_s[lane + 1].x != t;
-      if (BWD) {
-        float gE = 0.f, Gt = 0.f;
-        if (ok) {
-          const float2 gv = Wp->grad[bn];
-          gE = gv.x;
-          Gt = gv.y + gv.x * (float)(t - bn * bin_ps);
-        }
-        if (is_gh) {
-          v2 += leak[spre] * (Gt - Gcur) * 1e-6f;
-          Gcur = Gt;
-        }
-        if (is_out) {
-          v0 += gE * L.half_v2;
-        } else {
-          v0 += gE * sl.escale[cell] * (fmaf(__uint_as_float(d.x), eo.db - eo.da, eo.da) * __uint_as_float(d.w));
-          v1 += gE * eo.e_in;
-        }
-        if (gate_end) v2 += leak[st] * (Wp->g_total - Gt) * 1e-6f;
-      } else {
-        if (is_gh) v0 += leak[spre] * (float)((int32_t)t - (int32_t)tp) * 1e-6f;
-        const float e = is_out ? __uint_as_float(d.w) : eo.e_in;
-        if (is_out) v2 += e; else v1 += e;
-        float dp = 0.f, add = 0.f;
-        if (tail) {
-          dp = leak[st] - leak[spre];
-          add = dp * (float)((int32_t)((bn + 1u) * bin_ps) - (int32_t)t) * 1e-6f;
-        }
-        if (ok) {
-          if (bn != pb) {
-            if (pb != 0xFFFFFFFFu) red_bin(Wp->bins, pb, pe, pdp);
-            pb = bn;
-            pe = 0.f;
-            pdp = 0.f;
-          }
-          pe += e + add;
-          pdp += dp;
-        }
-        if (gate_end) {
-          v0 += leak[st] * (float)(T - (int32_t)t) * 1e-6f;
-          Wp->final_state[g] = (uint8_t)st;
-        }
-      }
+      X ^= (1u << (m & 0xFu)) & 0xFFu;
+      q.bad_r |= (uint32_t)(t >= d.T || (m & ~0x10u) > d.n_in) << k;
+      q.bad_o |= (uint32_t)((int32_t)t < (int32_t)tp && !(k == 0 && q.fh)) << k;
       tp = t;
     }
-    if (!BWD && pb != 0xFFFFFFFFu) red_bin(Wp->bins, pb, pe, pdp);
-    // ---- per-gate sums: one warp reduction and one atomic add per segment
-    v0 = warp_sum(v0);
-    v1 = warp_sum(v1);
-    v2 = warp_sum(v2);
-    if (lane == 0) {
+  }
+  uint32_t w = X | (Y << 8) | H;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t a = __shfl_up_sync(kFull, w, o);
+    if (lane >= o) w = xcompose(a, w);
+  }
+  q.ex = __shfl_up_sync(kFull, w, 1);
+  if (lane == 0) q.ex = 0u;
+  return __shfl_sync(kFull, w, 31);
+}
+
+// Per-lane sums of one segment (forward: leakage nW*ps, internal fJ,
+// switching fJ; adjoint: dC, d_escale, d_lscale * 1e6).
+struct SegSums {
+  float v0, v1, v2;
+};
+
+// Pass 2 of a staged segment whose incoming state is the absolute transfer
+// seg_in.
+template <int K, bool BWD, bool TAB>
+__device__ __forceinline__ SegSums seg_back(const LibView& L, const DGate& d, const DenseSmem& sm, const uint2* buf,
+                                            const Seg& q, uint32_t seg_in, DevError* err, int lane) {
+  SegSums out{0.f, 0.f, 0.f};
+  if (q.n_rem == 0) return out;
+  const bool any_r = __any_sync(kFull, q.bad_r != 0u);
+  if (any_r || __any_sync(kFull, q.bad_o != 0u)) {
+    const uint32_t bb = q.bad_r | q.bad_o;
+    if (bb) {
+      const int k = __ffs(bb) - 1;
+      report_error(err, ((q.bad_r >> k) & 1u) ? GTP_ERANGE : GTP_EORDER, q.s0 + lane * K + k);
+    }
+    if (any_r) return out;  // an event outside the window: skip the replay
+  }
+  const uint32_t li = xcompose(seg_in, q.ex);
+  uint32_t st = li & d.pmask;            // state before the lane's first event
+  uint32_t spre = (li >> 8) & d.pmask;   // state before the group in progress
+  float Pcur, Pg;                        // leakage after the last group; before the current one
+  if (TAB) {
+    Pcur = sm.leak[st];
+    Pg = sm.leak[spre];
+  } else {
+    Pcur = __ldg(d.gleak + st) * d.lsc;
+    Pg = __ldg(d.gleak + spre) * d.lsc;
+  }
+  float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+  float Gcur = 0.f;
+  if (BWD && q.t_before < d.T && !q.fh) {
+    const uint32_t bb = bin_of(q.t_before, d.magic, d.shift, d.bin_ps);
+    const float2 gv = d.W->grad[bb];
+    Gcur = gv.y + gv.x * (float)(q.t_before - bb * d.bin_ps);
+  }
+  uint32_t pb = 0xFFFFFFFFu;
+  float pe = 0.f, pdp = 0.f;
+  uint32_t bad_t = 0u;
+  uint32_t tp = q.t_before;
+  uint2 r = stage_rec<K>(buf, lane, 0);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (k < q.nk) {
+      const uint32_t t = r.x, m = r.y;
+      if (k + 1 < K) r = stage_rec<K>(buf, lane, k + 1);
+      const uint32_t tn = k + 1 < q.nk ? r.x : q.t_after;
+      const uint32_t pin = m & 0xFu, val = (m >> 4) & 1u;
+      const bool head = t != tp || (k == 0 && q.fh);
+      const uint32_t bn = bin_of(t, d.magic, d.shift, d.bin_ps);
+      float Gt = 0.f, gE = 0.f;
       if (BWD) {
-        atomicAdd(Wp->dC + g, v0);
-        wacc[cell] += (double)v1;
-        wacc[L.n_cells + cell] += (double)v2;
+        const float2 gv = d.W->grad[bn];
+        gE = gv.x;
+        Gt = gv.y + gv.x * (float)(t - bn * d.bin_ps);
+      }
+      if (head) {
+        if (BWD) {
+          v2 += Pcur * (Gt - Gcur);
+          Gcur = Gt;
+        } else {
+          v0 += Pcur * (float)(int32_t)(t - tp);
+        }
+        spre = st;
+        Pg = Pcur;
+      }
+      bad_t |= (uint32_t)(((st >> pin) & 1u) == val) << k;
+      st = (st ^ (1u << pin)) & d.pmask;
+      const bool is_out = pin >= d.n_in;
+      float E, dE = 0.f;
+      if (TAB) {
+        const uint32_t idx = ((min(pin, d.n_in) * 2u + val) << d.n_in) | (spre & d.inmask);
+        E = sm.etab[idx];
+        if (BWD) dE = sm.dtab[idx];
       } else {
-        atomicAdd(Wp->e_leak + g, (double)v0);
-        atomicAdd(Wp->e_int + g, (double)v1);
-        atomicAdd(Wp->e_sw + g, (double)v2);
+        const uint4 dq = __ldg(d.dsc + min(pin, d.n_in) * 2u + val);
+        if (is_out) {
+          E = BWD ? 0.f : __uint_as_float(dq.w);
+          dE = L.half_v2;
+        } else {
+          const float* p = L.tab + (dq.z & 0xFFFFu) + side_bits(spre, pin, d.n_in) * (uint32_t)L.tsize;
+          const float a0 = __ldg(p), a1 = __ldg(p + 1), b0 = __ldg(p + L.nl), b1 = __ldg(p + L.nl + 1);
+          const float fl = __uint_as_float(dq.y), fs = __uint_as_float(dq.x);
+          const float lo = fmaf(fl, a1 - a0, a0), hi = fmaf(fl, b1 - b0, b0);
+          const float eu = fmaf(fs, hi - lo, lo);
+          E = BWD ? eu : eu * d.esc;
+          dE = d.esc * (fmaf(fs, (b1 - b0) - (a1 - a0), a1 - a0) * __uint_as_float(dq.w));
+        }
+      }
+      const bool tail = tn != t;
+      float Pn = Pcur;
+      if (tail) Pn = TAB ? sm.leak[st] : __ldg(d.gleak + st) * d.lsc;
+      if (BWD) {
+        v0 += gE * dE;
+        v1 += gE * E;
+      } else {
+        if (is_out) v2 += E; else v1 += E;
+        float dp = 0.f, add = 0.f;
+        if (tail) {
+          dp = Pn - Pg;
+          add = dp * (float)(int32_t)((bn + 1u) * d.bin_ps - t) * 1e-6f;
+        }
+        if (bn != pb) {
+          if (pb != 0xFFFFFFFFu) red_bin(d.W->bins, pb, pe, pdp);
+          pb = bn;
+          pe = 0.f;
+          pdp = 0.f;
+        }
+        pe += E + add;
+        pdp += dp;
+      }
+      Pcur = Pn;
+      tp = t;
+    }
+  }
+  if (!BWD && pb != 0xFFFFFFFFu) red_bin(d.W->bins, pb, pe, pdp);
+  if (bad_t) report_error(err, GTP_ENOTOGGLE, q.s0 + lane * K + (__ffs(bad_t) - 1));
+  // gate end: leakage to the window end and the final state
+  if (q.last_seg && q.nk > 0 && lane * K + q.nk == q.n_rem) {
+    if (BWD) {
+      v2 += Pcur * (d.W->g_total - Gcur);
+    } else {
+      v0 += Pcur * (float)(int32_t)(d.T - tp);
+      d.W->final_state[d.g] = (uint8_t)st;
+    }
+  }
+  out.v0 = v0;
+  out.v1 = v1;
+  out.v2 = v2;
+  return out;
+}
+
+// Warp-level FP64 accumulation of per-lane segment sums (valid in lane 0).
+struct GateAcc {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  __device__ __forceinline__ void add(const SegSums& s) {
+    const float v0 = warp_sum(s.v0), v1 = warp_sum(s.v1), v2 = warp_sum(s.v2);
+    a0 += (double)v0;
+    a1 += (double)v1;
+    a2 += (double)v2;
+  }
+};
+
+// Per-gate results from the gate's totals.
+template <bool BWD>
+__device__ __forceinline__ void store_gate(const LibView& L, const DGate& d, const DenseSmem& sm, double a0,
+                                           double a1, double a2) {
+  if (BWD) {
+    d.W->dC[d.g] = (float)a0;
+    sm.wacc[d.cell] += a1;
+    sm.wacc[L.n_cells + d.cell] += a2 * 1e-6;
+  } else {
+    d.W->e_leak[d.g] = a0 * 1e-6;
+    d.W->e_int[d.g] = a1;
+    d.W->e_sw[d.g] = a2;
+  }
+}
+
+// A medium gate, walked by one warp segment by segment.
+template <int K, bool BWD, bool TAB>
+__device__ __forceinline__ void medium_gate(const LibView& L, const DGate& d, const DenseSmem& sm, DevError* err,
+                                            int lane) {
+  constexpr int SEG = 32 * K;
+  const int64_t nseg = (d.n + SEG - 1) / SEG;
+  __syncwarp();
+  issue_segment<K>(d, 0, sm.rec, lane);
+  if (TAB) build_tables<BWD>(L, d, sm, lane);
+  uint32_t carry = kXAbs | kXH | d.init | (d.init << 8);
+  GateAcc acc;
+  Seg q;
+  for (int64_t s = 0; s < nseg; ++s) {
+    const uint2* cur = sm.rec + (s & 1) * SEG;
+    issue_segment<K>(d, s + 1, sm.rec + ((s + 1) & 1) * SEG, lane);
+    cp_async_wait_1();
+    __syncwarp();
+    const uint32_t tx = seg_front<K>(d, s, cur, q, lane);
+    acc.add(seg_back<K, BWD, TAB>(L, d, sm, cur, q, carry, err, lane));
+    carry = xcompose(carry, tx);
+    __syncwarp();
+  }
+  if (lane == 0) store_gate<BWD>(L, d, sm, acc.a0, acc.a1, acc.a2);
+}
+
+// A big gate, walked by the CTA's 8 warps in chunks of 8 consecutive
+// segments; the state entering each segment is the carry into the chunk
+// composed with the transfers of the chunk's earlier segments.
+template <int K, bool BWD, bool TAB>
+__device__ __forceinline__ void big_gate(const LibView& L, const DGate& d, const DenseSmem& sm, DevError* err,
+                                         uint32_t (*xfer)[kWarps], double (*red)[3], int wib, int lane) {
+  constexpr int SEG = 32 * K;
+  const int64_t nchunk = (d.n + (int64_t)kWarps * SEG - 1) / ((int64_t)kWarps * SEG);
+  __syncwarp();
+  issue_segment<K>(d, wib, sm.rec, lane);
+  if (TAB) build_tables<BWD>(L, d, sm, lane);
+  uint32_t carry = kXAbs | kXH | d.init | (d.init << 8);
+  GateAcc acc;
+  Seg q;
+  for (int64_t c = 0; c < nchunk; ++c) {
+    const int64_t s = c * kWarps + wib;
+    const uint2* cur = sm.rec + (c & 1) * SEG;
+    issue_segment<K>(d, s + kWarps, sm.rec + ((c + 1) & 1) * SEG, lane);
+    cp_async_wait_1();
+    __syncwarp();
+    const uint32_t tx = seg_front<K>(d, s, cur, q, lane);
+    if (lane == 0) xfer[c & 1][wib] = tx;
+    __syncthreads();
+    uint32_t seg_in = carry;
+#pragma unroll
+    for (int v = 0; v < kWarps; ++v) {
+      const uint32_t x = xfer[c & 1][v];
+      if (v == wib) seg_in = carry;
+      carry = xcompose(carry, x);
+    }
+    acc.add(seg_back<K, BWD, TAB>(L, d, sm, cur, q, seg_in, err, lane));
+    __syncwarp();
+  }
+  if (lane == 0) {
+    red[wib][0] = acc.a0;
+    red[wib][1] = acc.a1;
+    red[wib][2] = acc.a2;
+  }
+  __syncthreads();
+  if (wib == 0 && lane == 0) {
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int v = 0; v < kWarps; ++v) {
+      a0 += red[v][0];
+      a1 += red[v][1];
+      a2 += red[v][2];
+    }
+    store_gate<BWD>(L, d, sm, a0, a1, a2);
+  }
+}
+
+// Persistent CTAs of 8 warps take work from the shared counter: one big gate
+// per item, or 8 medium gates (one per warp).
+template <int K, bool BWD>
+__global__ void __launch_bounds__(256, 3) k_dense(LibView L, NetView N, const WinDesc* __restrict__ wins, PlanBufs P,
+                                               DevError* err, double* __restrict__ cell_acc) {
+  constexpr int SEG = 32 * K;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t xfer[2][kWarps];
+  __shared__ double red[kWarps][3];
+  __shared__ unsigned long long s_item;
+  const int wib = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  unsigned char* sp = smem;
+  DenseSmem sm;
+  sm.rec = reinterpret_cast<uint2*>(sp) + (size_t)wib * 2 * SEG;
+  sp += (size_t)kWarps * 2 * SEG * sizeof(uint2);
+  sm.etab = reinterpret_cast<float*>(sp) + (size_t)wib * kTabEntries;
+  sp += (size_t)kWarps * kTabEntries * sizeof(float);
+  sm.dtab = reinterpret_cast<float*>(sp) + (size_t)wib * kTabEntries;
+  if (BWD) sp += (size_t)kWarps * kTabEntries * sizeof(float);
+  sm.leak = reinterpret_cast<float*>(sp) + (size_t)wib * kLeakEntries;
+  sp += (size_t)kWarps * kLeakEntries * sizeof(float);
+  sm.wacc = reinterpret_cast<double*>(sp) + (size_t)wib * 2 * L.n_cells;
+  if (BWD)
+    for (int c = lane; c < 2 * L.n_cells; c += 32) sm.wacc[c] = 0.0;
+
+  const int64_t n_big = (int64_t)P.counters[0];
+  const int64_t n_med = (int64_t)P.counters[1];
+  const int64_t n_items = n_big + (n_med + kWarps - 1) / kWarps;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(P.counters + 3, 1ull);
+    __syncthreads();
+    const int64_t item = (int64_t)s_item;
+    if (item >= n_items) break;
+    if (item < n_big) {
+      const DGate d = dense_gate<BWD>(L, N, wins, P.glist[item]);
+      if (d.n_in <= (uint32_t)kTabMaxIn) big_gate<K, BWD, true>(L, d, sm, err, xfer, red, wib, lane);
+      else big_gate<K, BWD, false>(L, d, sm, err, xfer, red, wib, lane);
+    } else {
+      const int64_t i = (item - n_big) * kWarps + wib;
+      if (i < n_med) {
+        const DGate d = dense_gate<BWD>(L, N, wins, P.glist[n_big + i]);
+        if (d.n_in <= (uint32_t)kTabMaxIn) medium_gate<K, BWD, true>(L, d, sm, err, lane);
+        else medium_gate<K, BWD, false>(L, d, sm, err, lane);
       }
     }
   }
   if (BWD) {
     __syncwarp();
     for (int c = lane; c < 2 * L.n_cells; c += 32)
-      if (wacc[c] != 0.0) atomicAdd(cell_acc + c, wacc[c]);
+      if (sm.wacc[c] != 0.0) atomicAdd(cell_acc + c, sm.wacc[c]);
   }
 }
 
@@ -520,7 +676,8 @@ __global__ void __launch_bounds__(256) k_sparse(LibView L, NetView N, const WinD
 
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t n_sparse = (int64_t)P.counters[1];
+  const int64_t n_sparse = (int64_t)P.counters[2];
+  const int2* __restrict__ slist = P.glist + (P.counters[0] + P.counters[1]);
   const int64_t n_task = (n_sparse + 31) / 32;
   const int tsize = L.tsize, nl = L.nl;
   const uint32_t dmax = (uint32_t)(dstride / 2 - 1);
@@ -528,7 +685,7 @@ __global__ void __launch_bounds__(256) k_sparse(LibView L, NetView N, const WinD
   for (int64_t tk = warp; tk < n_task; tk += n_warps) {
     const int64_t idx = tk * 32 + lane;
     const bool valid = idx < n_sparse;
-    const int2 wg = valid ? P.slist[idx] : make_int2(0, 0);
+    const int2 wg = valid ? slist[idx] : make_int2(0, 0);
     const WinDesc* Wp = wins + wg.x;
     const int64_t g = wg.y;
     const uint2* rec = Wp->rec;
@@ -663,10 +820,10 @@ __global__ void __launch_bounds__(256) k_sparse(LibView L, NetView N, const WinD
 }
 
 // ------------------------------------------------------------------ launchers
-size_t dense_smem(const LibView& L, const NetView& N, int K, int block, bool bwd) {
-  const size_t w = (size_t)(block / 32);
-  size_t b = smem_lib_bytes(L) + w * N.dstride * sizeof(uint4) + w * 32 * K * sizeof(uint2);
-  if (bwd) b += w * 2 * L.n_cells * sizeof(double);
+size_t dense_smem(const LibView& L, int K, bool bwd) {
+  const size_t w = (size_t)kWarps;
+  size_t b = w * (2 * 32 * K * sizeof(uint2) + kTabEntries * sizeof(float) + kLeakEntries * sizeof(float));
+  if (bwd) b += w * (kTabEntries * sizeof(float) + 2 * L.n_cells * sizeof(double));
   return b;
 }
 
@@ -678,29 +835,31 @@ size_t sparse_smem(const LibView& L, const NetView& N, int block, bool bwd) {
 }
 
 template <class Kern>
-cudaError_t launch_persistent(Kern kern, size_t smem, const WalkArgs& A, const LibView& L, const NetView& N,
-                              cudaStream_t st) {
+cudaError_t launch_persistent(Kern kern, size_t smem, int block, const WalkArgs& A, const LibView& L,
+                              const NetView& N, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int grid = A.grid;
   if (grid <= 0) {
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, A.block, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem);
     if (e != cudaSuccess) return e;
     grid = (per_sm > 0 ? per_sm : 1) * A.n_sm;
   }
-  kern<<<grid, A.block, smem, st>>>(L, N, A.wins, A.plan, A.err, A.cell_acc);
+  kern<<<grid, block, smem, st>>>(L, N, A.wins, A.plan, A.err, A.cell_acc);
   return cudaGetLastError();
 }
 
 template <int K, bool BWD>
 cudaError_t launch_dense_k(const LibView& L, const NetView& N, const WalkArgs& A, cudaStream_t st) {
-  return launch_persistent(k_dense<K, BWD>, dense_smem(L, N, K, A.block, BWD), A, L, N, st);
+  return launch_persistent(k_dense<K, BWD>, dense_smem(L, K, BWD), 32 * kWarps, A, L, N, st);
 }
 
 }  // namespace
 
 bool walk_rpt_supported(int rpt) { return rpt == 4 || rpt == 8 || rpt == 16; }
+
+int plan_counter_slots(int dense_min) { return 4 + 2 * n_buckets(dense_min); }
 
 cudaError_t launch_plan(const NetView& N, const LibView& L, const WalkArgs& A, cudaStream_t st) {
   const int64_t seg_len = 32ll * A.rpt;
@@ -711,15 +870,15 @@ cudaError_t launch_plan(const NetView& N, const LibView& L, const WalkArgs& A, c
   if (blocks > 1024) blocks = 1024;
   if (blocks < 1) blocks = 1;
   const dim3 grid((unsigned)blocks, (unsigned)A.n_win);
-  k_plan_classify<<<grid, 256, sizeof(unsigned int) * (dmin + 3), st>>>(A.wins, A.n_gates, seg_len, dmin, A.plan);
+  const size_t nb = (size_t)n_buckets(dmin);
+  k_plan_classify<<<grid, 256, sizeof(unsigned int) * nb, st>>>(A.wins, A.n_gates, seg_len, dmin, A.plan);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_plan_scan<<<1, 32, 0, st>>>(dmin, A.plan);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_plan_scatter<<<grid, 256, sizeof(unsigned int) * 2 * (dmin + 1), st>>>(A.wins, A.n_gates, dmin, A.plan);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_dseed<<<(unsigned)(4 * A.n_sm), 128, 0, st>>>(L, N, A.wins, seg_len, A.plan);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_dseed_fix<<<64, 128, 0, st>>>(A.wins, seg_len, A.plan);
+  const size_t scatter_smem = nb * (sizeof(unsigned long long) + sizeof(unsigned int));
+  e = cudaFuncSetAttribute(k_plan_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scatter_smem);
+  if (e != cudaSuccess) return e;
+  k_plan_scatter<<<grid, 256, scatter_smem, st>>>(A.wins, A.n_gates, seg_len, dmin, A.plan);
   return cudaGetLastError();
 }
 
@@ -732,7 +891,7 @@ cudaError_t launch_walk(const LibView& L, const NetView& N, const WalkArgs& A, b
       default: e = launch_dense_k<8, true>(L, N, A, st); break;
     }
     if (e != cudaSuccess) return e;
-    return launch_persistent(k_sparse<true>, sparse_smem(L, N, A.block, true), A, L, N, st);
+    return launch_persistent(k_sparse<true>, sparse_smem(L, N, A.block, true), A.block, A, L, N, st);
   }
   switch (A.rpt) {
     case 4: e = launch_dense_k<4, false>(L, N, A, st); break;
@@ -740,7 +899,7 @@ cudaError_t launch_walk(const LibView& L, const NetView& N, const WalkArgs& A, b
     default: e = launch_dense_k<8, false>(L, N, A, st); break;
   }
   if (e != cudaSuccess) return e;
-  return launch_persistent(k_sparse<false>, sparse_smem(L, N, A.block, false), A, L, N, st);
+  return launch_persistent(k_sparse<false>, sparse_smem(L, N, A.block, false), A.block, A, L, N, st);
 }
 
 }  // namespace gtp
