@@ -50,6 +50,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
+    p.add_argument("--events", type=int, default=0,
+                   help="scale the configuration to this many events (same gates and distribution; "
+                        "for profiling a smaller case)")
     return p.parse_args()
 
 
@@ -88,6 +91,15 @@ def max_over_ranks(pg, x: float) -> float:
 def barrier(pg):
     if pg is not None:
         pg.barrier()
+
+
+def config_of(args, cfg_name):
+    import dataclasses
+    import synth
+    cfg = synth.CONFIGS[cfg_name]
+    if args.events:
+        cfg = dataclasses.replace(cfg, n_events=int(args.events), name=f"{cfg.name} ({args.events:,} events)")
+    return cfg
 
 
 def workload_desc(cfg, n_bins):
@@ -195,7 +207,7 @@ def run_reference(args, cfg_name):
     ws, rank, local, pg = dist_init()
     if rank != 0:
         return
-    cfg = synth.CONFIGS[cfg_name]
+    cfg = config_of(args, cfg_name)
     lib = synth.make_library(cfg.seed_lib)
     net = synth.make_netlist(lib, cfg.n_gates, cfg.seed_net)
     counts = synth.zipf_counts(cfg.n_gates, cfg.n_events, cfg.zipf_s, cfg.cap, cfg.seed_ev)
@@ -230,7 +242,7 @@ def run_ours(args, cfg_name):
     ws, rank, local, pg = dist_init()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    cfg = synth.CONFIGS[cfg_name]
+    cfg = config_of(args, cfg_name)
     seed_ev = cfg.seed_ev + 1000 * rank
     lib = synth.make_library(cfg.seed_lib)
     net = synth.make_netlist(lib, cfg.n_gates, cfg.seed_net)
@@ -336,7 +348,7 @@ def run_ours(args, cfg_name):
                          f"({ev:,} events, all {n_bins:,} bins), {t:.1f} s"}
 
     extras = {}
-    if rank == 0 and not args.no_extras and cfg_name == "large":
+    if rank == 0 and not args.no_extras and cfg_name == "large" and not args.events:
         extras["batched"] = measure_batched(eng, dev, max(3, min(args.steps // 10, 10)))
         extras["adjoint"] = measure_adjoint(eng, dev, max(3, min(args.steps // 10, 10)))
 
