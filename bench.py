@@ -359,11 +359,11 @@ def run_ours(args, cfg_name):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_desc(cfg, n_bins), "gates": G, "events": n_ev, "bins": n_bins,
                        "records_bytes": 8 * n_ev, "l2_flush": "none: inputs (records) larger than L2",
-                       "kernel": "density-split walk (dense gates in per-gate segments, sparse gates one per lane)",
+                       "kernel": "density-split walk (dense gates in per-gate segments, sparse gates one per thread), one launch",
                        "records_per_thread": eng.get_param("records_per_thread"),
-                       "block_threads": eng.get_param("block_threads"), "dense_min": eng.get_param("dense_min")},
+                       "dense_min": eng.get_param("dense_min")},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "k_dense+k_sparse",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_walk",
                          "algorithmic_bytes": alg, "walk_ms": walk_s * 1e3, "peak_source": peak_src},
             "phases_ms": {"gate_pass": gate_s * 1e3, "seeds": seeds_s * 1e3, "walk": walk_s * 1e3,
                           "merge": merge_s * 1e3},
@@ -416,7 +416,7 @@ def measure_batched(eng, dev, steps):
         total += tr.n_events
     ids = list(range(len(wins)))
     tuned_ms = eng.autotune(ids, 10, iters=2)
-    plan = {k: eng.get_param(k) for k in ("records_per_thread", "block_threads", "ctas_per_sm", "dense_min")}
+    plan = {k: eng.get_param(k) for k in ("records_per_thread", "ctas_per_sm", "dense_min")}
     outs = [torch.empty(s["window_ps"] // 10, dtype=torch.float64, device=dev) for s in wins]
     ms_b = _events_per_s(lambda: gtpower.gtp_run_power_batched(eng.ctx, ids, 10, outs, graph=True), steps, dev)
     ref = [o.clone() for o in outs]

@@ -208,17 +208,16 @@ int gtp_run_power_backward(gtp_ctx* ctx, int32_t window, int32_t bin_ps, const f
 
 /*
  * Autotuner: time the walk of the given windows for every candidate
- * (records per lane 4/8/16 = segment length 128/256/512 events, 128 or 256
- * threads per CTA of the sparse walk, dense_min 64/256/1024), `iters` timed
- * runs each, keep the fastest as the context's parameters and report its
- * time per run (ms) in *best_ms.  Runs the windows repeatedly; their
- * per-gate results are those of the last run.
+ * (records per lane 4/8/16 = segment length 128/256/512 events, dense_min
+ * 64/256/1024), `iters` timed runs each, keep the fastest as the context's
+ * parameters and report its time per run (ms) in *best_ms.  Runs the windows
+ * repeatedly; their per-gate results are those of the last run.
  */
 int gtp_autotune(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_t bin_ps, int32_t iters,
                  double* best_ms);
 
 /* Engine tuning knobs; value < 0 restores the default.  Keys:
- * "records_per_thread" (4, 8, 16), "block_threads" (128, 256; the sparse walk),
+ * "records_per_thread" (4, 8, 16; events per lane of a dense segment),
  * "ctas_per_sm" (0 = full occupancy), "dense_min" (gates with more events are cut into segments; 1..4096),
  * "kernel" (0 = density-split walk,
  * 1 = one thread per gate, a plain cross-check), "timing" (1 = time the

@@ -63,10 +63,10 @@ struct Window {
 struct GraphKey {
   std::vector<int32_t> windows;
   int32_t bin_ps;
-  int64_t rpt, block, ctas, kernel, dmin, plan_gen;
+  int64_t rpt, ctas, kernel, dmin, plan_gen;
   bool operator<(const GraphKey& o) const {
-    return std::tie(windows, bin_ps, rpt, block, ctas, kernel, dmin, plan_gen) <
-           std::tie(o.windows, o.bin_ps, o.rpt, o.block, o.ctas, o.kernel, o.dmin, o.plan_gen);
+    return std::tie(windows, bin_ps, rpt, ctas, kernel, dmin, plan_gen) <
+           std::tie(o.windows, o.bin_ps, o.rpt, o.ctas, o.kernel, o.dmin, o.plan_gen);
   }
 };
 
@@ -87,6 +87,9 @@ struct gtp_ctx {
   bool net_loaded = false;
   DevBuf cell, load, slew, desc;
   NetView N{};
+  // per-gate energy tables (forward: scaled; adjoint: unscaled + load derivative), rebuilt when stale
+  DevBuf gtab, gtab_bwd;
+  bool gtab_ok = false, gtab_bwd_ok = false;
   std::map<int, Window> windows;
   // launch plan: device descriptor table and its pinned host staging copy
   DevBuf plan;  // WinDesc[kMaxWindows] | tile_base[kMaxWindows+1] | l0[kMaxWindows+1]
@@ -103,7 +106,6 @@ struct gtp_ctx {
   // parameters
   int64_t p_kernel = 0;
   int64_t p_rpt = 8;
-  int64_t p_block = 256;
   int64_t p_ctas_per_sm = 0;
   int64_t p_dense_min = 256;
   // phase timing (CUDA events on the context stream) and launch counting
@@ -282,11 +284,12 @@ WalkArgs walk_args(gtp_ctx* ctx, int n) {
   A.n_win = n;
   A.rpt = (int)ctx->p_rpt;
   A.dense_min = (int)ctx->p_dense_min;
-  A.block = (int)ctx->p_block;
   A.grid = ctx->p_ctas_per_sm > 0 ? (int)(ctx->p_ctas_per_sm * ctx->n_sm) : 0;
   A.n_sm = ctx->n_sm;
   A.err = ctx->d_err.as<DevError>();
   A.cell_acc = ctx->cell_acc.as<double>();
+  A.gtab = ctx->gtab.as<float>();
+  A.gtab_bwd = ctx->gtab_bwd.as<float>();
   A.plan.glist = ctx->glist.as<int2>();
   A.plan.counters = ctx->counters.as<unsigned long long>();
   A.plan.gcap = ctx->gcap;
@@ -333,7 +336,7 @@ int enqueue_forward(gtp_ctx* ctx, int n, int64_t n_seg_total, int64_t n_tiles_to
       mark(ctx, 3, st);
       mark(ctx, 4, st);
       CU(launch_walk(ctx->L, ctx->N, A, false, st), "walk");
-      ctx->launches += 5;
+      ctx->launches += 4;
     }
   } else {
     mark(ctx, 3, st);
@@ -354,6 +357,28 @@ int ensure_netlist_coords(gtp_ctx* ctx) {
   ctx->N.desc = ctx->desc.as<uint4>();
   CU(launch_event_desc(ctx->L, ctx->N, ctx->desc.as<uint4>(), ctx->stream), "event descriptors");
   ctx->launches += 1;
+  ctx->gtab_ok = false;
+  ctx->gtab_bwd_ok = false;
+  return GTP_OK;
+}
+
+// Per-gate energy tables for the walk (forward: scaled energies; adjoint:
+// unscaled energies and load derivatives), rebuilt after a netlist, load,
+// scale or library change.
+int ensure_gate_tables(gtp_ctx* ctx, bool backward) {
+  const int64_t G = ctx->N.n_gates;
+  if (!ctx->gtab_ok) {
+    CU(ctx->gtab.reserve(sizeof(float) * kGateTab * (size_t)G), "alloc gate tables");
+    CU(launch_gate_tables(ctx->L, ctx->N, ctx->gtab.as<float>(), nullptr, ctx->stream), "gate tables");
+    ctx->launches += 1;
+    ctx->gtab_ok = true;
+  }
+  if (backward && !ctx->gtab_bwd_ok) {
+    CU(ctx->gtab_bwd.reserve(sizeof(float) * 2 * kGateTab * (size_t)G), "alloc adjoint gate tables");
+    CU(launch_gate_tables(ctx->L, ctx->N, nullptr, ctx->gtab_bwd.as<float>(), ctx->stream), "adjoint gate tables");
+    ctx->launches += 1;
+    ctx->gtab_bwd_ok = true;
+  }
   return GTP_OK;
 }
 
@@ -406,10 +431,11 @@ int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, dou
     }
   }
   int64_t n_seg_total = 0, n_tiles_total = 0;
+  RC(ensure_gate_tables(ctx, false));
   RC(build_plan(ctx, ws, bin_ps, waves, false, &n_seg_total, &n_tiles_total));
   CU(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(DevError), ctx->stream), "zero status");
   if (use_graph) {
-    const GraphKey key{std::vector<int32_t>(windows, windows + n), bin_ps, ctx->p_rpt, ctx->p_block,
+    const GraphKey key{std::vector<int32_t>(windows, windows + n), bin_ps, ctx->p_rpt,
                        ctx->p_ctas_per_sm, ctx->p_kernel, ctx->p_dense_min, ctx->plan_gen};
     auto it = ctx->graphs.find(key);
     if (it == ctx->graphs.end()) {
@@ -433,7 +459,7 @@ int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, dou
     }
     // the graph's first node uploads the descriptor table from the staging buffer
     CU(cudaGraphLaunch(it->second, ctx->stream), "graph launch");
-    ctx->launches += any_events ? (ctx->p_kernel == 1 ? 6 : 10) : 5;
+    ctx->launches += any_events ? (ctx->p_kernel == 1 ? 6 : 9) : 5;
   } else {
     RC(enqueue_forward(ctx, n, n_seg_total, n_tiles_total, any_events, ctx->stream));
   }
@@ -492,7 +518,7 @@ void gtp_destroy(gtp_ctx* ctx) {
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   for (auto& kv : ctx->windows) kv.second.release();
   for (DevBuf* b : {&ctx->tab, &ctx->leak, &ctx->cells, &ctx->table_cell, &ctx->leak_cell, &ctx->escale, &ctx->lscale,
-                    &ctx->cell, &ctx->load, &ctx->slew, &ctx->desc, &ctx->plan, &ctx->glist,
+                    &ctx->cell, &ctx->load, &ctx->slew, &ctx->desc, &ctx->plan, &ctx->glist, &ctx->gtab, &ctx->gtab_bwd,
                     &ctx->counters,
                     &ctx->cell_acc, &ctx->grad, &ctx->gtiles, &ctx->dC_scratch, &ctx->d_err})
     b->release();
@@ -591,6 +617,8 @@ int gtp_load_library(gtp_ctx* ctx, int32_t n_cells, const int32_t* n_in, float v
   ctx->n_in.assign(n_in, n_in + n_cells);
   ctx->max_in = max_in;
   ctx->lib_loaded = true;
+  ctx->gtab_ok = false;
+  ctx->gtab_bwd_ok = false;
   ctx->net_loaded = false;
   for (auto& kv : ctx->windows) kv.second.release();
   ctx->windows.clear();
@@ -607,6 +635,7 @@ int gtp_set_scales(gtp_ctx* ctx, const float* escale, const float* lscale) {
   CU(cudaMemcpyAsync(ctx->lscale.p, lscale ? lscale : ones.data(), sizeof(float) * ctx->L.n_cells,
                      cudaMemcpyHostToDevice, ctx->stream), "copy lscale");
   CU(cudaStreamSynchronize(ctx->stream), "set_scales");
+  ctx->gtab_ok = false;
   return GTP_OK;
 }
 
@@ -775,6 +804,7 @@ int gtp_run_power_backward(gtp_ctx* ctx, int32_t window, int32_t bin_ps, const f
   std::vector<Window*> ws{W};
   std::vector<double*> waves;
   int64_t n_seg_total = 0, n_tiles_total = 0;
+  RC(ensure_gate_tables(ctx, true));
   RC(build_plan(ctx, ws, bin_ps, waves, true, &n_seg_total, &n_tiles_total));
   plan_wins(ctx->h_plan)[0].dC = dc;
   cudaStream_t st = ctx->stream;
@@ -790,7 +820,7 @@ int gtp_run_power_backward(gtp_ctx* ctx, int32_t window, int32_t bin_ps, const f
     const WalkArgs A = walk_args(ctx, 1);
     CU(launch_plan(ctx->N, ctx->L, A, st), "plan");
     CU(launch_walk(ctx->L, ctx->N, A, true, st), "adjoint walk");
-    ctx->launches += 5;
+    ctx->launches += 4;
   }
   if (d_escale || d_lscale) {
     CU(launch_cells_out(ctx->cell_acc.as<double>(), ctx->L.n_cells, d_escale, d_lscale, st), "cell gradients");
@@ -813,18 +843,16 @@ int gtp_autotune(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_
   CU(cudaEventCreate(&e0), "event");
   CU(cudaEventCreate(&e1), "event");
   double best = 1e300;
-  int64_t br = ctx->p_rpt, bb = ctx->p_block, bc = ctx->p_dense_min;
+  int64_t br = ctx->p_rpt, bc = ctx->p_dense_min;
   std::vector<double*> none(n_windows, nullptr);
   const int rpts[] = {4, 8, 16};
-  const int blocks[] = {128, 256};
   const int dmins[] = {64, 256, 1024};
   int rc = GTP_OK;
   ctx->p_ctas_per_sm = 0;
   for (int r : rpts) {
-    for (int b : blocks) {
+    {
       for (int c : dmins) {
         ctx->p_rpt = r;
-        ctx->p_block = b;
         ctx->p_dense_min = c;
         rc = run_forward(ctx, windows, n_windows, bin_ps, none.data(), GTP_DEVICE, false);  // warm-up
         if (rc != GTP_OK) break;
@@ -839,7 +867,6 @@ int gtp_autotune(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_
         if (ms / iters < best) {
           best = ms / iters;
           br = r;
-          bb = b;
           bc = c;
         }
       }
@@ -850,7 +877,6 @@ int gtp_autotune(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   ctx->p_rpt = br;
-  ctx->p_block = bb;
   ctx->p_dense_min = bc;
   ctx->p_kernel = keep_kernel;
   ctx->timing = keep_timing;
@@ -868,9 +894,6 @@ int gtp_set_param(gtp_ctx* ctx, const char* key, int64_t value) {
     if (value >= 0 && !walk_rpt_supported((int)value))
       return fail(ctx, GTP_ERANGE, "records_per_thread must be 4, 8 or 16");
     ctx->p_rpt = value < 0 ? 8 : value;
-  } else if (k == "block_threads") {
-    if (value >= 0 && value != 128 && value != 256) return fail(ctx, GTP_ERANGE, "block_threads must be 128 or 256");
-    ctx->p_block = value < 0 ? 256 : value;
   } else if (k == "ctas_per_sm") {
     if (value > 32) return fail(ctx, GTP_ERANGE, "ctas_per_sm must be <= 32");
     ctx->p_ctas_per_sm = value < 0 ? 0 : value;
@@ -897,7 +920,6 @@ int64_t gtp_get_param(const gtp_ctx* ctx, const char* key) {
   const std::string k(key);
   if (k == "kernel") return ctx->p_kernel;
   if (k == "records_per_thread") return ctx->p_rpt;
-  if (k == "block_threads") return ctx->p_block;
   if (k == "ctas_per_sm") return ctx->p_ctas_per_sm;
   if (k == "dense_min") return ctx->p_dense_min;
   if (k == "n_sm") return ctx->n_sm;

@@ -13,7 +13,7 @@
 // in between.
 #include <cstdio>
 
-#include "gtp_internal.cuh"
+#include "gtp_walk.cuh"
 
 namespace gtp {
 
@@ -78,6 +78,61 @@ __global__ void k_event_desc(LibView L, NetView N, uint4* __restrict__ desc) {
       }
     }
   }
+}
+
+// ------------------------------------------------------------------ per-gate energy tables
+// For each gate whose cell has at most kGateTabMaxIn inputs, the energy of
+// every (input pin, edge, side state) lookup at the gate's slews and load,
+// i.e. the bilinear NLDM value of Sec. 2.3 on the state-indexed table of
+// Sec. 4.1, and the switching energy of its output (Eq. switching).  Entry
+// (pin << n_in) | s, with s the input-pin state before the event: the pin's
+// own bit in s is its old value (so the edge is its complement) and the other
+// bits are the side state; the output pin is pin n_in.  Forward table:
+// energies times escale, output slots 0.5 * C * Vdd^2.  Adjoint table:
+// unscaled energies (output slots 0), then their load derivatives (the slope
+// of the located load segment; output slots 0.5 * Vdd^2).
+__global__ void k_gate_tables(LibView L, NetView N, float* __restrict__ gtab, float* __restrict__ gbwd) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N.n_gates;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = N.cell[g];
+    const CellInfo ci = L.cells[c];
+    const uint32_t n_in = (uint32_t)ci.n_in;
+    if (n_in > (uint32_t)kGateTabMaxIn) continue;
+    const uint4* dsc = N.desc + (size_t)g * N.dstride;
+    const float esc = L.escale[c];
+    const float e_sw = __uint_as_float(dsc[2u * n_in].w);
+    const uint32_t inmask = (1u << n_in) - 1u;
+    for (uint32_t e = 0; e < ((n_in + 1u) << n_in); ++e) {
+      const uint32_t pin = e >> n_in, s = e & inmask;
+      float eu, ed;
+      if (pin < n_in) {
+        const uint32_t val = ((s >> pin) & 1u) ^ 1u;  // the pin's own bit is its value before the edge
+        const uint4 d = dsc[pin * 2u + val];
+        const float* p = L.tab + (d.z & 0xFFFFu) + side_bits(s, pin, n_in) * (uint32_t)L.tsize;
+        const float a0 = p[0], a1 = p[1], b0 = p[L.nl], b1 = p[L.nl + 1];
+        const float fl = __uint_as_float(d.y), fs = __uint_as_float(d.x);
+        const float lo = fmaf(fl, a1 - a0, a0), hi = fmaf(fl, b1 - b0, b0);
+        eu = fmaf(fs, hi - lo, lo);
+        ed = fmaf(fs, (b1 - b0) - (a1 - a0), a1 - a0) * __uint_as_float(d.w);
+        if (gtab) gtab[(size_t)g * kGateTab + e] = eu * esc;
+      } else {
+        eu = 0.f;
+        ed = L.half_v2;
+        if (gtab) gtab[(size_t)g * kGateTab + e] = e_sw;
+      }
+      if (gbwd) {
+        gbwd[(size_t)g * 2 * kGateTab + e] = eu;
+        gbwd[(size_t)g * 2 * kGateTab + kGateTab + e] = ed;
+      }
+    }
+  }
+}
+
+cudaError_t launch_gate_tables(const LibView& L, const NetView& N, float* gtab, float* gtab_bwd, cudaStream_t st) {
+  int64_t blocks = (N.n_gates + 255) / 256;
+  if (blocks > 8192) blocks = 8192;
+  k_gate_tables<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, st>>>(L, N, gtab, gtab_bwd);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_event_desc(const LibView& L, NetView N, uint4* desc, cudaStream_t st) {

@@ -48,8 +48,7 @@ namespace gtp {
 namespace {
 
 constexpr uint32_t kFull = 0xffffffffu;
-constexpr int KS = 8;          // events staged per lane and chunk in the sparse walk
-constexpr int kWarps = 8;      // warps of a dense CTA (a big gate's chunk is kWarps segments)
+constexpr int kWarps = kWalkThreads / 32;  // warps of a walk CTA (a big gate's chunk is kWarps segments)
 constexpr int kBigBuckets = 32;
 constexpr int kSparseBase = kBigBuckets + kWarps;
 
@@ -124,29 +123,6 @@ __global__ void k_plan_scatter(const WinDesc* __restrict__ wins, int64_t G, int6
 }
 
 // ------------------------------------------------------------------ shared per-event math
-struct EventOut {
-  float e_in;  // internal energy from the table (meaningful for input events)
-  float da, db;
-};
-
-__device__ __forceinline__ EventOut table_energy(const SmemLib& sl, const uint4& d, uint32_t spre, uint32_t pin,
-                                                 uint32_t n_in, int tsize, int nl) {
-  const uint32_t side = side_bits(spre, min(pin, n_in), n_in);
-  const float* p = sl.tab + (d.z & 0xFFFFu) + side * (uint32_t)tsize;
-  const float a0 = p[0], a1 = p[1], b0 = p[nl], b1 = p[nl + 1];
-  EventOut o;
-  o.da = a1 - a0;
-  o.db = b1 - b0;
-  const float lo = fmaf(__uint_as_float(d.y), o.da, a0);
-  const float hi = fmaf(__uint_as_float(d.y), o.db, b0);
-  o.e_in = fmaf(__uint_as_float(d.x), hi - lo, lo);
-  return o;
-}
-
-__device__ __forceinline__ int bad_code(bool t_bad, bool o_bad, bool p_bad) {
-  return t_bad ? GTP_ERANGE : (o_bad ? GTP_EORDER : (p_bad ? GTP_ERANGE : GTP_ENOTOGGLE));
-}
-
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
@@ -594,11 +570,259 @@ __device__ __forceinline__ void big_gate(const LibView& L, const DGate& d, const
   }
 }
 
-// Persistent CTAs of 8 warps take work from the shared counter: one big gate
-// per item, or 8 medium gates (one per warp).
+// ------------------------------------------------------------------ sparse gates, one per thread
+constexpr int kChunk = 4;             // records a thread stages per copy round (two rounds in flight)
+constexpr uint32_t kNoTime = 0xFFFFFFFFu;  // past every valid timestamp
+
+
+// Copy records [u, u + kChunk) of a gate (base rec_g, n records) into this
+// thread's staging column; those at or past n are zero-filled without
+// reading.  One commit group.
+__device__ __forceinline__ void stage_chunk(const uint2* __restrict__ rec_g, uint32_t u, uint32_t n, uint2* col) {
+#pragma unroll
+  for (int k = 0; k < kChunk; ++k) {
+    const bool v = u + k < n;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_addr(col + k * kWalkThreads)),
+                 "l"(v ? rec_g + u + k : rec_g), "r"(v ? 8 : 0)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Per-thread sums, FP32 over a few chunks, then folded into FP64.
+struct Sums {
+  float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+  double d0 = 0.0, d1 = 0.0, d2 = 0.0;
+  __device__ __forceinline__ void fold() {
+    d0 += (double)f0;
+    d1 += (double)f1;
+    d2 += (double)f2;
+    f0 = f1 = f2 = 0.f;
+  }
+};
+
+__device__ __forceinline__ int bad_event_code(uint32_t t, uint32_t m, uint32_t T, uint32_t n_in, bool order_bad) {
+  if (t >= T || (m & ~0x10u) > n_in) return GTP_ERANGE;
+  return order_bad ? GTP_EORDER : GTP_ENOTOGGLE;
+}
+
+// Per-thread walk of a gate's events from local index u0 while their time is
+// below t_stop (n = the gate's event count, rec_g its first record), for the
+// sparse gates (one gate per thread).  `tabl` is this thread's column of the
+// CTA's staged gate tables (stride kWalkThreads), `col` its staging column
+// (2 x kChunk records, stride kWalkThreads), `sleak` the CTA's leakage table
+// (forward: scaled).  Forward: each distinct bin of consecutive events gets
+// one reduction {energy, leakage step} into L2 (TILE: into a shared-memory
+// tile instead, local bin = bin - bin_lo).
+struct WalkOut {
+  double v0, v1, v2;  // forward: leakage (nW*ps), internal, switching; adjoint: dC, d_escale, d_lscale * 1e6
+  uint32_t end;       // local index of the first event not walked
+};
+
+template <bool BWD, bool TILE>
+__device__ __forceinline__ WalkOut walk_events(const LibView& L, const NetView& N, const WinDesc& W,
+                                               const float* tabl, uint2* col, const float* sleak, DevError* err,
+                                               int64_t g, const uint2* __restrict__ rec_g, uint32_t u0, uint32_t n,
+                                               uint32_t t_stop, uint32_t st, uint32_t tp, float2* sbin,
+                                               uint32_t bin_lo) {
+  const uint32_t cell = (uint32_t)N.cell[g];
+  const CellInfo ci = L.cells[cell];
+  const uint32_t n_in = (uint32_t)ci.n_in;
+  const uint32_t pmask = (2u << n_in) - 1u, inmask = (1u << n_in) - 1u;
+  const float* leak = sleak + ci.leak_base;
+  const float esc = L.escale[cell];
+  const bool tab = n_in <= (uint32_t)kGateTabMaxIn;
+  const uint4* __restrict__ dsc = N.desc + (size_t)g * N.dstride;
+  const uint32_t T = (uint32_t)W.window_ps, bin_ps = (uint32_t)W.bin_ps, magic = W.bin_magic,
+                 shift = W.bin_shift;
+
+  st &= pmask;
+  float Pcur = leak[st];  // leakage after the last group
+  float Pg = Pcur;        // leakage before the current group
+  uint32_t spre = st;     // state before the current group
+  Sums acc;
+  float Gcur = 0.f;
+  if (BWD && tp > 0u && tp < T) {
+    const uint32_t bb = bin_of(tp, magic, shift, bin_ps);
+    const float2 gv = W.grad[bb];
+    Gcur = gv.y + gv.x * (float)(tp - bb * bin_ps);
+  }
+  uint32_t pb = kNoTime;
+  float pe = 0.f, pdp = 0.f;
+  bool live = true, bad = false, first = true;
+  uint32_t u = u0;  // first event of the current chunk
+  uint32_t end = n;
+  stage_chunk(rec_g, u, n, col);
+  stage_chunk(rec_g, u + kChunk, n, col + kChunk * kWalkThreads);
+  uint32_t ta_cur = u + kChunk < n ? __ldg(&rec_g[u + kChunk].x) : kNoTime;  // event after each staged chunk
+  uint32_t ta_nxt = u + 2 * kChunk < n ? __ldg(&rec_g[u + 2 * kChunk].x) : kNoTime;
+  int b = 0, n_chunks = 0;
+  while (live) {
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    const uint2* buf = col + b * kChunk * kWalkThreads;
+    uint32_t rt[kChunk], rm[kChunk];
+#pragma unroll
+    for (int k = 0; k < kChunk; ++k) {
+      const uint2 r = buf[k * kWalkThreads];
+      rt[k] = u + k < n ? r.x : kNoTime;
+      rm[k] = r.y;
+    }
+#pragma unroll
+    for (int k = 0; k < kChunk; ++k) {
+      if (!live) continue;
+      const uint32_t t = rt[k], m = rm[k];
+      if (t >= t_stop) {  // the tile's (or, at kNoTime, the gate's) end
+        live = false;
+        end = u + k;
+        continue;
+      }
+      const uint32_t t_next = k + 1 < kChunk ? rt[k + 1] : ta_cur;
+      const uint32_t pin = m & 0xFu, val = (m >> 4) & 1u;
+      const bool order_bad = (int32_t)t < (int32_t)tp;
+      if (t >= T || (m & ~0x10u) > n_in || order_bad || ((st >> pin) & 1u) == val) {
+        report_error(err, bad_event_code(t, m, T, n_in, order_bad), (rec_g - W.rec) + u + k);
+        live = false;
+        bad = true;
+        end = u + k;
+        continue;
+      }
+      const bool head = first || t != tp;
+      first = false;
+      const uint32_t bn = bin_of(t, magic, shift, bin_ps);
+      float gE = 0.f, Gt = 0.f;
+      if (BWD) {
+        const float2 gv = W.grad[bn];
+        gE = gv.x;
+        Gt = gv.y + gv.x * (float)(t - bn * bin_ps);
+        if (head) acc.f2 += Pcur * (Gt - Gcur);
+        Gcur = head ? Gt : Gcur;
+      } else {
+        if (head) acc.f0 += Pcur * (float)(int32_t)(t - tp);
+      }
+      Pg = head ? Pcur : Pg;
+      spre = head ? st : spre;
+      const uint32_t bitp = 1u << pin;
+      st ^= bitp;
+      const bool is_out = pin == n_in;
+      float E, dE = 0.f;
+      if (tab) {
+        // entry (pin, input state with the pin's own bit = its value before the edge)
+        const uint32_t own = (val - 1u) & bitp & inmask;
+        const uint32_t idx = (pin << n_in) | (spre & inmask & ~bitp) | own;
+        E = tabl[idx * kWalkThreads];
+        if (BWD) dE = tabl[(kGateTab + idx) * kWalkThreads] * (is_out ? 1.f : esc);
+      } else if (is_out) {
+        E = BWD ? 0.f : __uint_as_float(__ldg(dsc + 2u * n_in).w);
+        dE = L.half_v2;
+      } else {
+        const uint4 d = __ldg(dsc + pin * 2u + val);
+        const float* p = L.tab + (d.z & 0xFFFFu) + side_bits(spre, pin, n_in) * (uint32_t)L.tsize;
+        const float a0 = __ldg(p), a1 = __ldg(p + 1), b0 = __ldg(p + L.nl), b1 = __ldg(p + L.nl + 1);
+        const float fl = __uint_as_float(d.y), fs = __uint_as_float(d.x);
+        const float lo = fmaf(fl, a1 - a0, a0), hi = fmaf(fl, b1 - b0, b0);
+        const float eu = fmaf(fs, hi - lo, lo);
+        E = BWD ? eu : eu * esc;
+        dE = esc * (fmaf(fs, (b1 - b0) - (a1 - a0), a1 - a0) * __uint_as_float(d.w));
+      }
+      const bool tail = t_next != t;
+      const float Pn = leak[st];
+      if (BWD) {
+        acc.f0 += gE * dE;
+        acc.f1 += gE * E;
+      } else {
+        if (is_out) acc.f2 += E; else acc.f1 += E;
+        const float dp = tail ? Pn - Pg : 0.f;
+        const float add = dp * (float)(int32_t)((bn + 1u) * bin_ps - t) * 1e-6f;
+        if (bn != pb) {
+          if (pb != kNoTime) {
+            if (TILE) {
+              atomicAdd(&sbin[pb - bin_lo].x, pe);
+              atomicAdd(&sbin[pb - bin_lo].y, pdp);
+            } else {
+              red_bin(W.bins, pb, pe, pdp);
+            }
+          }
+          pb = bn;
+          pe = 0.f;
+          pdp = 0.f;
+        }
+        pe += E + add;
+        pdp += dp;
+      }
+      Pcur = tail ? Pn : Pcur;
+      tp = t;
+    }
+    if (!live) break;
+    // refill the chunk just walked with the one two chunks ahead
+    stage_chunk(rec_g, u + 2 * kChunk, n, col + b * kChunk * kWalkThreads);
+    ta_cur = ta_nxt;
+    ta_nxt = u + 3 * kChunk < n ? __ldg(&rec_g[u + 3 * kChunk].x) : kNoTime;
+    u += kChunk;
+    b ^= 1;
+    if (++n_chunks == 16) {
+      acc.fold();
+      n_chunks = 0;
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  if (!BWD && pb != kNoTime) {
+    if (TILE) {
+      atomicAdd(&sbin[pb - bin_lo].x, pe);
+      atomicAdd(&sbin[pb - bin_lo].y, pdp);
+    } else {
+      red_bin(W.bins, pb, pe, pdp);
+    }
+  }
+  // the gate's end: leakage to the window end, and the final state
+  if (!bad && end == n) {
+    if (BWD) {
+      acc.f2 += Pcur * (W.g_total - Gcur);
+    } else {
+      acc.f0 += Pcur * (float)(int32_t)(T - tp);
+      W.final_state[g] = (uint8_t)st;
+    }
+  }
+  acc.fold();
+  return WalkOut{acc.d0, acc.d1, acc.d2, end};
+}
+
+// This thread's gate table into its column of the CTA's staged tables.
+template <bool BWD>
+__device__ __forceinline__ void stage_gate_table(const float* __restrict__ gt, int64_t g, float* stab) {
+  constexpr int kN = BWD ? 2 * kGateTab : kGateTab;
+  const float4* src = reinterpret_cast<const float4*>(gt + (size_t)g * kN);
+#pragma unroll
+  for (int q = 0; q < kN / 4; ++q) {
+    const float4 v = __ldg(src + q);
+    stab[(4 * q + 0) * kWalkThreads] = v.x;
+    stab[(4 * q + 1) * kWalkThreads] = v.y;
+    stab[(4 * q + 2) * kWalkThreads] = v.z;
+    stab[(4 * q + 3) * kWalkThreads] = v.w;
+  }
+}
+
+// Shared memory of a walk CTA: a union of the dense items' per-warp areas
+// (staged records, energy table, leakage row) and the sparse items' area
+// (per-thread gate tables, per-thread staged records, the leakage table),
+// then, for the adjoint, the per-warp cell sums.
+__host__ __device__ inline size_t dense_area(int K, bool bwd) {
+  return (size_t)kWarps * (2 * 32 * K * sizeof(uint2) + (bwd ? 2 : 1) * kTabEntries * sizeof(float) +
+                           kLeakEntries * sizeof(float));
+}
+__host__ __device__ inline size_t sparse_area(int n_leak, bool bwd) {
+  return (size_t)(bwd ? 2 : 1) * kGateTab * kWalkThreads * sizeof(float) +
+         (size_t)2 * kChunk * kWalkThreads * sizeof(uint2) + (((size_t)n_leak * sizeof(float) + 15) & ~(size_t)15);
+}
+__host__ __device__ inline size_t union_area(int K, int n_leak, bool bwd) {
+  const size_t d = dense_area(K, bwd), sp = sparse_area(n_leak, bwd);
+  return d > sp ? d : sp;
+}
+
+// Persistent CTAs of 8 warps take work items from the shared counter: one big
+// gate per item (all 8 warps), 8 medium gates per item (one per warp), then
+// 256 sparse gates per item (one per thread).
 template <int K, bool BWD>
-__global__ void __launch_bounds__(256, 3) k_dense(LibView L, NetView N, const WinDesc* __restrict__ wins, PlanBufs P,
-                                               DevError* err, double* __restrict__ cell_acc) {
+__global__ void __launch_bounds__(kWalkThreads, 3) k_walk(LibView L, NetView N, WalkArgs A) {
   constexpr int SEG = 32 * K;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t xfer[2][kWarps];
@@ -606,6 +830,10 @@ __global__ void __launch_bounds__(256, 3) k_dense(LibView L, NetView N, const Wi
   __shared__ unsigned long long s_item;
   const int wib = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  const PlanBufs& P = A.plan;
+  const WinDesc* __restrict__ wins = A.wins;
+  DevError* err = A.err;
+  // dense view of the union area
   unsigned char* sp = smem;
   DenseSmem sm;
   sm.rec = reinterpret_cast<uint2*>(sp) + (size_t)wib * 2 * SEG;
@@ -615,14 +843,21 @@ __global__ void __launch_bounds__(256, 3) k_dense(LibView L, NetView N, const Wi
   sm.dtab = reinterpret_cast<float*>(sp) + (size_t)wib * kTabEntries;
   if (BWD) sp += (size_t)kWarps * kTabEntries * sizeof(float);
   sm.leak = reinterpret_cast<float*>(sp) + (size_t)wib * kLeakEntries;
-  sp += (size_t)kWarps * kLeakEntries * sizeof(float);
-  sm.wacc = reinterpret_cast<double*>(sp) + (size_t)wib * 2 * L.n_cells;
+  // sparse view of the union area
+  float* stab = reinterpret_cast<float*>(smem);
+  uint2* sstg = reinterpret_cast<uint2*>(stab + (BWD ? 2 : 1) * kGateTab * kWalkThreads);
+  float* sleak = reinterpret_cast<float*>(sstg + 2 * kChunk * kWalkThreads);
+  // adjoint cell sums, after the union
+  sm.wacc = reinterpret_cast<double*>(smem + union_area(K, L.n_leak, BWD)) + (size_t)wib * 2 * L.n_cells;
   if (BWD)
     for (int c = lane; c < 2 * L.n_cells; c += 32) sm.wacc[c] = 0.0;
 
   const int64_t n_big = (int64_t)P.counters[0];
   const int64_t n_med = (int64_t)P.counters[1];
-  const int64_t n_items = n_big + (n_med + kWarps - 1) / kWarps;
+  const int64_t n_sparse = (int64_t)P.counters[2];
+  const int64_t n_dense_items = n_big + (n_med + kWarps - 1) / kWarps;
+  const int64_t n_items = n_dense_items + (n_sparse + kWalkThreads - 1) / kWalkThreads;
+  const float* gt = BWD ? A.gtab_bwd : A.gtab;
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_item = atomicAdd(P.counters + 3, 1ull);
@@ -633,226 +868,64 @@ __global__ void __launch_bounds__(256, 3) k_dense(LibView L, NetView N, const Wi
       const DGate d = dense_gate<BWD>(L, N, wins, P.glist[item]);
       if (d.n_in <= (uint32_t)kTabMaxIn) big_gate<K, BWD, true>(L, d, sm, err, xfer, red, wib, lane);
       else big_gate<K, BWD, false>(L, d, sm, err, xfer, red, wib, lane);
-    } else {
+    } else if (item < n_dense_items) {
       const int64_t i = (item - n_big) * kWarps + wib;
       if (i < n_med) {
         const DGate d = dense_gate<BWD>(L, N, wins, P.glist[n_big + i]);
         if (d.n_in <= (uint32_t)kTabMaxIn) medium_gate<K, BWD, true>(L, d, sm, err, lane);
         else medium_gate<K, BWD, false>(L, d, sm, err, lane);
       }
-    }
-  }
-  if (BWD) {
-    __syncwarp();
-    for (int c = lane; c < 2 * L.n_cells; c += 32)
-      if (sm.wacc[c] != 0.0) atomicAdd(cell_acc + c, sm.wacc[c]);
-  }
-}
-
-// ------------------------------------------------------------------ sparse gates, one per lane
-template <bool BWD>
-__global__ void __launch_bounds__(256) k_sparse(LibView L, NetView N, const WinDesc* __restrict__ wins, PlanBufs P,
-                                                DevError* err, double* __restrict__ cell_acc) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const SmemLib sl = stage_library(L, smem, !BWD);
-  unsigned char* sp = smem + smem_lib_bytes(L);
-  const int n_wib = blockDim.x >> 5;
-  const int wib = threadIdx.x >> 5;
-  const int lane = threadIdx.x & 31;
-  const int dstride = N.dstride;
-  uint4* dblk = reinterpret_cast<uint4*>(sp) + (size_t)wib * dstride * 32;  // [entry][lane]
-  sp += (size_t)n_wib * dstride * 32 * sizeof(uint4);
-  uint2* stage = reinterpret_cast<uint2*>(sp) + (size_t)wib * KS * 32;      // [k][lane]
-  sp += (size_t)n_wib * KS * 32 * sizeof(uint2);
-  double* wacc64 = reinterpret_cast<double*>(sp) + (size_t)wib * 2 * L.n_cells;  // adjoint: per-warp cell sums
-  sp += (size_t)n_wib * 2 * L.n_cells * sizeof(double);
-  float* wacc = reinterpret_cast<float*>(sp) + (size_t)wib * 2 * L.n_cells;
-  if (BWD)
-    for (int c = lane; c < 2 * L.n_cells; c += 32) {
-      wacc[c] = 0.f;
-      wacc64[c] = 0.0;
-    }
-  __syncthreads();
-
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t n_sparse = (int64_t)P.counters[2];
-  const int2* __restrict__ slist = P.glist + (P.counters[0] + P.counters[1]);
-  const int64_t n_task = (n_sparse + 31) / 32;
-  const int tsize = L.tsize, nl = L.nl;
-  const uint32_t dmax = (uint32_t)(dstride / 2 - 1);
-
-  for (int64_t tk = warp; tk < n_task; tk += n_warps) {
-    const int64_t idx = tk * 32 + lane;
-    const bool valid = idx < n_sparse;
-    const int2 wg = valid ? slist[idx] : make_int2(0, 0);
-    const WinDesc* Wp = wins + wg.x;
-    const int64_t g = wg.y;
-    const uint2* rec = Wp->rec;
-    const int64_t a = valid ? Wp->offsets[g] : 0;
-    const int n = valid ? (int)(Wp->offsets[g + 1] - a) : 0;
-    const uint32_t cell = valid ? (uint32_t)N.cell[g] : 0u;
-    const CellInfo ci = sl.cells[cell];
-    const uint32_t n_in = (uint32_t)ci.n_in;
-    const uint32_t pmask = (2u << n_in) - 1u;
-    const float* leak = sl.leak + ci.leak_base;
-    const int32_t T = Wp->window_ps;
-    const uint32_t bin_ps = (uint32_t)Wp->bin_ps, magic = Wp->bin_magic, shift = Wp->bin_shift;
-    __syncwarp();
-    for (int e = 0; e < dstride; ++e)
-      dblk[e * 32 + lane] = valid ? __ldg(N.desc + (size_t)g * dstride + e) : make_uint4(0u, 0u, 0u, 0u);
-    uint32_t st = valid ? (uint32_t)Wp->init[g] & pmask : 0u;
-    uint32_t spre = st;
-    uint32_t tp = 0u;
-    int n_max = n;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) n_max = max(n_max, __shfl_xor_sync(kFull, n_max, o));
-    float v0 = 0.f, v1 = 0.f, v2 = 0.f;
-    float Gcur = 0.f, Gt = 0.f;
-    uint32_t pb = 0xFFFFFFFFu;
-    float pe = 0.f, pdp = 0.f;
-    const uint64_t rec_addr = reinterpret_cast<uint64_t>(rec + a);
-    for (int c0 = 0; c0 < n_max; c0 += KS) {
-      // stage KS events of each of the 32 gates: 8 lanes copy one gate's 64-byte run
-      __syncwarp();
-#pragma unroll
-      for (int m = 0; m < KS; ++m) {
-        const int q = m * 32 + lane;
-        const int gi = q / KS, kk = q % KS;
-        const uint64_t ra = __shfl_sync(kFull, rec_addr, gi);
-        const int ngi = __shfl_sync(kFull, n, gi);
-        uint2 rr = make_uint2(0u, 0u);
-        if (c0 + kk < ngi) rr = __ldcs(reinterpret_cast<const uint2*>(ra) + c0 + kk);
-        stage[kk * 32 + gi] = rr;
-      }
-      uint32_t t_look = 0u;  // first event of the next chunk
-      if (c0 + KS < n) t_look = rec[a + c0 + KS].x;
-      __syncwarp();
-#pragma unroll 1
-      for (int kk = 0; kk < KS; ++kk) {
-        const int j = c0 + kk;
-        if (j >= n) break;
-        const uint2 r = stage[kk * 32 + lane];
-        const uint32_t t = r.x, pin = r.y & 0xFu, val = (r.y >> 4) & 1u;
-        const bool is_gh = j == 0 || t != tp;
-        const bool t_bad = t >= (uint32_t)T;
-        const bool o_bad = j > 0 && (int32_t)t < (int32_t)tp;
-        const bool p_bad = (r.y >> 5) != 0u || pin > n_in;
-        const bool g_bad = !p_bad && ((st >> pin) & 1u) == val;
-        if (t_bad || o_bad || p_bad || g_bad) report_error(err, bad_code(t_bad, o_bad, p_bad), a + j);
-        const bool ok = !t_bad;
-        if (is_gh) spre = st;
-        const uint32_t bn = ok ? bin_of(t, magic, shift, bin_ps) : 0u;
-        const uint4 d = dblk[(min(pin, dmax) * 2u + val) * 32 + lane];
-        const bool is_out = (d.z >> 24) & 1u;
-        const EventOut eo = table_energy(sl, d, spre, pin, n_in, tsize, nl);
-        if (pin <= n_in) st = ((st & ~(1u << pin)) | (val << pin)) & pmask;
-        const bool gate_end = j + 1 == n;
-        const uint32_t t_nx = kk + 1 < KS ? stage[(kk + 1) * 32 + lane].x : t_look;
-        const bool tail = gate_end || t_nx != t;
+    } else {
+      // ---- 256 sparse gates, one per thread
+      for (int k = threadIdx.x; k < L.n_leak; k += kWalkThreads)
+        sleak[k] = BWD ? L.leak[k] : L.leak[k] * L.lscale[L.leak_cell[k]];
+      __syncthreads();
+      const int64_t i = (item - n_dense_items) * kWalkThreads + threadIdx.x;
+      if (i < n_sparse) {
+        const int2 wg = P.glist[n_big + n_med + i];
+        const WinDesc& W = wins[wg.x];
+        const int64_t g = wg.y;
+        const int64_t ga = W.offsets[g], ge = W.offsets[g + 1];
+        float* my_tab = stab + threadIdx.x;
+        if (L.cells[N.cell[g]].n_in <= kGateTabMaxIn) stage_gate_table<BWD>(gt, g, my_tab);
+        const WalkOut o = walk_events<BWD, false>(L, N, W, my_tab, sstg + threadIdx.x, sleak, err, g, W.rec + ga, 0u,
+                                                  (uint32_t)(ge - ga), kNoTime, (uint32_t)W.init[g], 0u, nullptr,
+                                                  0u);
         if (BWD) {
-          float gE = 0.f;
-          Gt = 0.f;
-          if (ok) {
-            const float2 gv = Wp->grad[bn];
-            gE = gv.x;
-            Gt = gv.y + gv.x * (float)(t - bn * bin_ps);
-          }
-          if (is_gh) {
-            v2 += leak[spre] * (Gt - Gcur) * 1e-6f;
-            Gcur = Gt;
-          }
-          if (is_out) {
-            v0 += gE * L.half_v2;
-          } else {
-            v0 += gE * sl.escale[cell] * (fmaf(__uint_as_float(d.x), eo.db - eo.da, eo.da) * __uint_as_float(d.w));
-            v1 += gE * eo.e_in;
-          }
-          if (gate_end) v2 += leak[st] * (Wp->g_total - Gt) * 1e-6f;
+          W.dC[g] = (float)o.v0;
+          const uint32_t cell = (uint32_t)N.cell[g];
+          atomicAdd(sm.wacc + cell, o.v1);
+          atomicAdd(sm.wacc + L.n_cells + cell, o.v2 * 1e-6);
         } else {
-          if (is_gh) v0 += leak[spre] * (float)((int32_t)t - (int32_t)tp) * 1e-6f;
-          const float e = is_out ? __uint_as_float(d.w) : eo.e_in;
-          if (is_out) v2 += e; else v1 += e;
-          float dp = 0.f, add = 0.f;
-          if (tail) {
-            dp = leak[st] - leak[spre];
-            add = dp * (float)((int32_t)((bn + 1u) * bin_ps) - (int32_t)t) * 1e-6f;
-          }
-          if (ok) {
-            if (bn != pb) {
-              if (pb != 0xFFFFFFFFu) red_bin(Wp->bins, pb, pe, pdp);
-              pb = bn;
-              pe = 0.f;
-              pdp = 0.f;
-            }
-            pe += e + add;
-            pdp += dp;
-          }
-          if (gate_end) v0 += leak[st] * (float)(T - (int32_t)t) * 1e-6f;
+          W.e_leak[g] = o.v0 * 1e-6;
+          W.e_int[g] = o.v1;
+          W.e_sw[g] = o.v2;
         }
-        tp = t;
       }
-    }
-    if (BWD) {
-      if (valid) {
-        Wp->dC[g] = v0;
-        atomicAdd(wacc + cell, v1);
-        atomicAdd(wacc + L.n_cells + cell, v2);
-      }
-      __syncwarp();
-      for (int c = lane; c < 2 * L.n_cells; c += 32) {
-        wacc64[c] += (double)wacc[c];
-        wacc[c] = 0.f;
-      }
-    } else if (valid) {
-      if (pb != 0xFFFFFFFFu) red_bin(Wp->bins, pb, pe, pdp);
-      Wp->e_leak[g] = (double)v0;
-      Wp->e_int[g] = (double)v1;
-      Wp->e_sw[g] = (double)v2;
-      Wp->final_state[g] = (uint8_t)st;
     }
   }
   if (BWD) {
     __syncwarp();
     for (int c = lane; c < 2 * L.n_cells; c += 32)
-      if (wacc64[c] != 0.0) atomicAdd(cell_acc + c, wacc64[c]);
+      if (sm.wacc[c] != 0.0) atomicAdd(A.cell_acc + c, sm.wacc[c]);
   }
 }
 
 // ------------------------------------------------------------------ launchers
-size_t dense_smem(const LibView& L, int K, bool bwd) {
-  const size_t w = (size_t)kWarps;
-  size_t b = w * (2 * 32 * K * sizeof(uint2) + kTabEntries * sizeof(float) + kLeakEntries * sizeof(float));
-  if (bwd) b += w * (kTabEntries * sizeof(float) + 2 * L.n_cells * sizeof(double));
-  return b;
-}
-
-size_t sparse_smem(const LibView& L, const NetView& N, int block, bool bwd) {
-  const size_t w = (size_t)(block / 32);
-  size_t b = smem_lib_bytes(L) + w * N.dstride * 32 * sizeof(uint4) + w * KS * 32 * sizeof(uint2);
-  if (bwd) b += w * 2 * L.n_cells * (sizeof(float) + sizeof(double));
-  return b;
-}
-
-template <class Kern>
-cudaError_t launch_persistent(Kern kern, size_t smem, int block, const WalkArgs& A, const LibView& L,
-                              const NetView& N, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int K, bool BWD>
+cudaError_t launch_walk_k(const LibView& L, const NetView& N, const WalkArgs& A, cudaStream_t st) {
+  const size_t smem = union_area(K, L.n_leak, BWD) + (BWD ? (size_t)kWarps * 2 * L.n_cells * sizeof(double) : 0);
+  cudaError_t e = cudaFuncSetAttribute(k_walk<K, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int grid = A.grid;
   if (grid <= 0) {
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<K, BWD>, kWalkThreads, smem);
     if (e != cudaSuccess) return e;
     grid = (per_sm > 0 ? per_sm : 1) * A.n_sm;
   }
-  kern<<<grid, block, smem, st>>>(L, N, A.wins, A.plan, A.err, A.cell_acc);
+  k_walk<K, BWD><<<grid, kWalkThreads, smem, st>>>(L, N, A);
   return cudaGetLastError();
-}
-
-template <int K, bool BWD>
-cudaError_t launch_dense_k(const LibView& L, const NetView& N, const WalkArgs& A, cudaStream_t st) {
-  return launch_persistent(k_dense<K, BWD>, dense_smem(L, K, BWD), 32 * kWarps, A, L, N, st);
 }
 
 }  // namespace
@@ -883,23 +956,18 @@ cudaError_t launch_plan(const NetView& N, const LibView& L, const WalkArgs& A, c
 }
 
 cudaError_t launch_walk(const LibView& L, const NetView& N, const WalkArgs& A, bool backward, cudaStream_t st) {
-  cudaError_t e;
   if (backward) {
     switch (A.rpt) {
-      case 4: e = launch_dense_k<4, true>(L, N, A, st); break;
-      case 16: e = launch_dense_k<16, true>(L, N, A, st); break;
-      default: e = launch_dense_k<8, true>(L, N, A, st); break;
+      case 4: return launch_walk_k<4, true>(L, N, A, st);
+      case 16: return launch_walk_k<16, true>(L, N, A, st);
+      default: return launch_walk_k<8, true>(L, N, A, st);
     }
-    if (e != cudaSuccess) return e;
-    return launch_persistent(k_sparse<true>, sparse_smem(L, N, A.block, true), A.block, A, L, N, st);
   }
   switch (A.rpt) {
-    case 4: e = launch_dense_k<4, false>(L, N, A, st); break;
-    case 16: e = launch_dense_k<16, false>(L, N, A, st); break;
-    default: e = launch_dense_k<8, false>(L, N, A, st); break;
+    case 4: return launch_walk_k<4, false>(L, N, A, st);
+    case 16: return launch_walk_k<16, false>(L, N, A, st);
+    default: return launch_walk_k<8, false>(L, N, A, st);
   }
-  if (e != cudaSuccess) return e;
-  return launch_persistent(k_sparse<false>, sparse_smem(L, N, A.block, false), A.block, A, L, N, st);
 }
 
 }  // namespace gtp

@@ -5,6 +5,19 @@
 
 namespace gtp {
 
+constexpr int kWalkThreads = 256;  // threads of a walk CTA
+
+// Per-gate energy tables (built by launch_gate_tables): for a gate whose cell
+// has at most kGateTabMaxIn inputs, entry (pin << n_in) | s holds the
+// energy of an event on `pin` when the input-pin state before it is s (the
+// pin's own bit being its old value): the internal energy (fJ, bilinear NLDM
+// value times escale) for an input pin, 0.5 * C * Vdd^2 for the output pin
+// (pin n_in).  The adjoint table holds the unscaled energies in
+// [0, kGateTab) (output slots 0) and their load derivatives in
+// [kGateTab, 2 * kGateTab) (output slots 0.5 * Vdd^2).
+constexpr int kGateTab = 32;
+constexpr int kGateTabMaxIn = 3;
+
 // Device-side plan scratch of one run (all windows of the run).
 struct PlanBufs {
   int2* glist;                  // gates with events {window, gate}: big, then medium, then sparse
@@ -22,11 +35,12 @@ struct WalkArgs {
   int n_win;
   int rpt;                  // records per lane of a dense segment: 4, 8 or 16
   int dense_min;            // gates with more events than this are cut into segments
-  int block;                // threads per CTA of the sparse walk: 128 or 256 (the dense walk uses 256)
   int grid;                 // persistent CTAs (0 = one wave at full occupancy)
   int n_sm;
   DevError* err;
   double* cell_acc;         // adjoint: [2 * n_cells] FP64 sums (d_escale, d_lscale)
+  const float* gtab;        // forward gate tables [G][kGateTab]
+  const float* gtab_bwd;    // adjoint gate tables [G][2 * kGateTab] (adjoint runs only)
   PlanBufs plan;
   int64_t n_gates;
 };
@@ -36,5 +50,6 @@ bool walk_rpt_supported(int rpt);
 // gates, sparse gates (no host synchronisation).
 cudaError_t launch_plan(const NetView& N, const LibView& L, const WalkArgs& A, cudaStream_t st);
 cudaError_t launch_walk(const LibView& L, const NetView& N, const WalkArgs& A, bool backward, cudaStream_t st);
+cudaError_t launch_gate_tables(const LibView& L, const NetView& N, float* gtab, float* gtab_bwd, cudaStream_t st);
 
 }  // namespace gtp

@@ -16,9 +16,9 @@ TOL = 1e-5
 
 KERNELS = [
     dict(kernel=1),
-    dict(kernel=0, records_per_thread=4, block_threads=256),
-    dict(kernel=0, records_per_thread=8, block_threads=256),
-    dict(kernel=0, records_per_thread=16, block_threads=128),
+    dict(kernel=0, records_per_thread=4, dense_min=16),
+    dict(kernel=0, records_per_thread=8),
+    dict(kernel=0, records_per_thread=16, dense_min=64),
 ]
 KID = ["per_gate", "seg_k4", "seg_k8", "seg_k16"]
 
@@ -34,7 +34,7 @@ def engine():
 def run(engine, lib, net, tr, bin_ps, params=None, escale=None, lscale=None, window=0):
     engine.load_library(lib)
     engine.load_netlist(net)
-    for k in ("kernel", "records_per_thread", "block_threads", "ctas_per_sm"):
+    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm"):
         engine.set_param(k, -1)
     for k, v in (params or {}).items():
         engine.set_param(k, v)
@@ -229,7 +229,7 @@ def test_device_resident_events(engine, borrow):
     lib, net, tr = small_random(n_gates=100, n_events=20_001, window_ps=200_000, seed=51, tie_p=0.02)
     engine.load_library(lib)
     engine.load_netlist(net)
-    for k in ("kernel", "records_per_thread", "block_threads", "ctas_per_sm"):
+    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm"):
         engine.set_param(k, -1)
     dev = engine.device
     off = torch.from_numpy(tr.offsets).to(dev)
