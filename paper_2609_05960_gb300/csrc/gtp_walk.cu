@@ -856,14 +856,21 @@ __global__ void __launch_bounds__(kWalkThreads, 3) k_walk(LibView L, NetView N, 
   const int64_t n_med = (int64_t)P.counters[1];
   const int64_t n_sparse = (int64_t)P.counters[2];
   const int64_t n_dense_items = n_big + (n_med + kWarps - 1) / kWarps;
-  const int64_t n_items = n_dense_items + (n_sparse + kWalkThreads - 1) / kWalkThreads;
+  const int64_t n_sparse_items = (n_sparse + kWalkThreads - 1) / kWalkThreads;
+  const int64_t n_items = n_dense_items + n_sparse_items;
   const float* gt = BWD ? A.gtab_bwd : A.gtab;
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_item = atomicAdd(P.counters + 3, 1ull);
     __syncthreads();
-    const int64_t item = (int64_t)s_item;
-    if (item >= n_items) break;
+    const int64_t pos = (int64_t)s_item;
+    if (pos >= n_items) break;
+    // Dense and sparse items are handed out evenly interleaved (each list
+    // keeps its order), so L2-reduction-bound dense work and latency-bound
+    // sparse work share the SMs for the whole launch.
+    const int64_t dense_before = pos * n_dense_items / n_items;
+    const bool is_dense = (pos + 1) * n_dense_items / n_items > dense_before;
+    const int64_t item = is_dense ? dense_before : n_dense_items + (pos - dense_before);
     if (item < n_big) {
       const DGate d = dense_gate<BWD>(L, N, wins, P.glist[item]);
       if (d.n_in <= (uint32_t)kTabMaxIn) big_gate<K, BWD, true>(L, d, sm, err, xfer, red, wib, lane);
