@@ -222,7 +222,7 @@ int gtp_autotune(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_
  * "kernel" (0 = density-split walk,
  * 1 = one thread per gate, a plain cross-check), "timing" (1 = time the
  * phases of later runs with CUDA events; read back with gtp_get_param keys
- * "t_gate_pass_ns", "t_seeds_ns", "t_walk_ns", "t_merge_ns", "n_timed",
+ * "t_gate_pass_ns", "t_plan_ns", "t_walk_ns", "t_merge_ns", "n_timed",
  * and "launches" = kernels launched since timing was last set). */
 int gtp_set_param(gtp_ctx* ctx, const char* key, int64_t value);
 int64_t gtp_get_param(const gtp_ctx* ctx, const char* key);

@@ -111,7 +111,7 @@ struct gtp_ctx {
   // phase timing (CUDA events on the context stream) and launch counting
   bool timing = false;
   cudaEvent_t ev[8] = {};
-  int64_t t_ns[4] = {0, 0, 0, 0};  // gate pass, seeds, walk, merge
+  int64_t t_ns[4] = {0, 0, 0, 0};  // gate pass, plan, walk, merge
   int64_t n_timed = 0;
   int64_t launches = 0;
 };
@@ -925,7 +925,7 @@ int64_t gtp_get_param(const gtp_ctx* ctx, const char* key) {
   if (k == "n_sm") return ctx->n_sm;
   if (k == "timing") return ctx->timing ? 1 : 0;
   if (k == "t_gate_pass_ns") return ctx->t_ns[0];
-  if (k == "t_seeds_ns") return ctx->t_ns[1];
+  if (k == "t_plan_ns") return ctx->t_ns[1];
   if (k == "t_walk_ns") return ctx->t_ns[2];
   if (k == "t_merge_ns") return ctx->t_ns[3];
   if (k == "n_timed") return ctx->n_timed;
