@@ -52,10 +52,11 @@ extern "C" {
                                caller's event buffer in place (no copy); it must
                                stay valid and unchanged while the window is used
                                and be 16-byte aligned */
-#define GTP_GRAPH 4         /* gtp_run_power_batched only, with GTP_DEVICE:
-                               capture the run in a CUDA graph on its first call
-                               and replay it on later calls with the same window
-                               list, bin size and tuning */
+#define GTP_GRAPH 4         /* gtp_run_power and gtp_run_power_batched, with
+                               GTP_DEVICE: capture the run in a CUDA graph on
+                               its first call and replay it on later calls with
+                               the same window list, bin size, window sizes,
+                               tuning and phase-timing setting */
 
 /* Limits of this engine: at most 7 input pins per cell (8 pins, so the gate
  * state fits in one byte), at most 16 points per interpolation axis, and
@@ -166,7 +167,8 @@ int gtp_load_events(gtp_ctx* ctx, int32_t window, int64_t window_ps, int64_t n_e
  * kept for gtp_gate_energy.  Synchronous; returns GTP_EORDER / GTP_ERANGE /
  * GTP_ENOTOGGLE if the trace is malformed (results are then undefined).
  * waveform_w may be NULL to compute per-gate results only.
- * flags: GTP_HOST or GTP_DEVICE for waveform_w.
+ * flags: GTP_HOST or GTP_DEVICE for waveform_w, optionally | GTP_GRAPH
+ * (device waveform only).
  */
 int gtp_run_power(gtp_ctx* ctx, int32_t window, int32_t bin_ps, double* waveform_w, int flags);
 
@@ -222,8 +224,10 @@ int gtp_autotune(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_
  * "kernel" (0 = density-split walk,
  * 1 = one thread per gate, a plain cross-check), "timing" (1 = time the
  * phases of later runs with CUDA events; read back with gtp_get_param keys
- * "t_gate_pass_ns", "t_plan_ns", "t_walk_ns", "t_merge_ns", "n_timed",
- * and "launches" = kernels launched since timing was last set). */
+ * "t_gate_pass_ns" (the preparation launch: bins cleared, gate pass and
+ * work-list histogram), "t_plan_ns" (work-list scatter), "t_walk_ns",
+ * "t_merge_ns", "n_timed", and "launches" = kernels launched since timing
+ * was last set). */
 int gtp_set_param(gtp_ctx* ctx, const char* key, int64_t value);
 int64_t gtp_get_param(const gtp_ctx* ctx, const char* key);
 

@@ -64,9 +64,13 @@ struct GraphKey {
   std::vector<int32_t> windows;
   int32_t bin_ps;
   int64_t rpt, ctas, kernel, dmin, plan_gen;
+  int64_t n_tiles;  // launch sizes baked into the graph
+  bool any_events;  // whether the walk was captured
+  bool timing;      // whether phase events were captured
   bool operator<(const GraphKey& o) const {
-    return std::tie(windows, bin_ps, rpt, ctas, kernel, dmin, plan_gen) <
-           std::tie(o.windows, o.bin_ps, o.rpt, o.ctas, o.kernel, o.dmin, o.plan_gen);
+    return std::tie(windows, bin_ps, rpt, ctas, kernel, dmin, plan_gen, n_tiles, any_events, timing) <
+           std::tie(o.windows, o.bin_ps, o.rpt, o.ctas, o.kernel, o.dmin, o.plan_gen, o.n_tiles, o.any_events,
+                    o.timing);
   }
 };
 
@@ -297,8 +301,13 @@ WalkArgs walk_args(gtp_ctx* ctx, int n) {
   return A;
 }
 
+// Phase boundary i (0..7); on a capturing stream the record becomes an
+// event-record node of the graph and is re-recorded at every replay.
 void mark(gtp_ctx* ctx, int i, cudaStream_t st) {
-  if (ctx->timing && st == ctx->stream) cudaEventRecord(ctx->ev[i], st);
+  if (!ctx->timing) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cs);
+  cudaEventRecordWithFlags(ctx->ev[i], st, cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u);
 }
 
 void collect_timing(gtp_ctx* ctx) {
@@ -318,25 +327,25 @@ int enqueue_forward(gtp_ctx* ctx, int n, int64_t n_seg_total, int64_t n_tiles_to
   const int64_t* tile_base = plan_tile_base(ctx->plan.p);
   RC(upload_plan(ctx, n, st));
   CU(cudaMemsetAsync(plan_l0(ctx->plan.p), 0, sizeof(double) * n, st), "zero l0");
-  CU(launch_zero_bins(dw, tile_base, n, n_tiles_total, st), "zero bins");
+  const WalkArgs A = walk_args(ctx, n);
+  const bool fused = any_events && ctx->p_kernel != 1;
   mark(ctx, 0, st);
-  CU(launch_gate_pass(ctx->L, ctx->N, dw, n, ctx->d_err.as<DevError>(), st), "gate pass");
+  CU(launch_prepare(ctx->L, ctx->N, A, fused, st), "prepare");
   mark(ctx, 1, st);
-  ctx->launches += 2;
+  ctx->launches += 1;
   mark(ctx, 2, st);
   if (any_events) {
-    const WalkArgs A = walk_args(ctx, n);
-    if (ctx->p_kernel == 1) {
+    if (!fused) {
       mark(ctx, 3, st);
       mark(ctx, 4, st);
       CU(launch_walk_per_gate(ctx->L, ctx->N, dw, n, ctx->d_err.as<DevError>(), st), "walk (per gate)");
       ctx->launches += 1;
     } else {
-      CU(launch_plan(ctx->N, ctx->L, A, st), "plan");
+      CU(launch_plan_scatter(ctx->N, A, st), "plan");
       mark(ctx, 3, st);
       mark(ctx, 4, st);
       CU(launch_walk(ctx->L, ctx->N, A, false, st), "walk");
-      ctx->launches += 4;
+      ctx->launches += 2;
     }
   } else {
     mark(ctx, 3, st);
@@ -436,7 +445,8 @@ int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, dou
   CU(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(DevError), ctx->stream), "zero status");
   if (use_graph) {
     const GraphKey key{std::vector<int32_t>(windows, windows + n), bin_ps, ctx->p_rpt,
-                       ctx->p_ctas_per_sm, ctx->p_kernel, ctx->p_dense_min, ctx->plan_gen};
+                       ctx->p_ctas_per_sm, ctx->p_kernel, ctx->p_dense_min, ctx->plan_gen,
+                       n_tiles_total, any_events, ctx->timing};
     auto it = ctx->graphs.find(key);
     if (it == ctx->graphs.end()) {
       if (!ctx->capture_stream) CU(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking), "stream");
@@ -459,7 +469,7 @@ int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, dou
     }
     // the graph's first node uploads the descriptor table from the staging buffer
     CU(cudaGraphLaunch(it->second, ctx->stream), "graph launch");
-    ctx->launches += any_events ? (ctx->p_kernel == 1 ? 6 : 9) : 5;
+    ctx->launches += any_events ? (ctx->p_kernel == 1 ? 5 : 6) : 4;
   } else {
     RC(enqueue_forward(ctx, n, n_seg_total, n_tiles_total, any_events, ctx->stream));
   }
@@ -470,7 +480,7 @@ int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, dou
                            cudaMemcpyDeviceToHost, ctx->stream), "copy waveform");
   }
   const int rc = check_device_error(ctx, "run_power");
-  if (!use_graph) collect_timing(ctx);
+  collect_timing(ctx);
   for (Window* w : ws) {
     w->has_result = (rc == GTP_OK);
     w->last_bin_ps = bin_ps;
@@ -737,9 +747,11 @@ int gtp_load_events(gtp_ctx* ctx, int32_t window, int64_t window_ps, int64_t n_e
 
 int gtp_run_power(gtp_ctx* ctx, int32_t window, int32_t bin_ps, double* waveform_w, int flags) {
   if (!ctx) return GTP_EINVAL;
+  if ((flags & GTP_GRAPH) && !(flags & GTP_DEVICE))
+    return fail(ctx, GTP_EINVAL, "run_power: graph replay needs a device waveform");
   DeviceGuard dg(ctx->device);
   double* const waves[1] = {waveform_w};
-  return run_forward(ctx, &window, 1, bin_ps, waves, flags, false);
+  return run_forward(ctx, &window, 1, bin_ps, waves, flags, (flags & GTP_GRAPH) != 0);
 }
 
 int gtp_run_power_batched(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_t bin_ps,

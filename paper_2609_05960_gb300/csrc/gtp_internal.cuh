@@ -188,8 +188,6 @@ __device__ __forceinline__ SmemLib stage_library(const LibView& L, unsigned char
 
 // ------------------------------------------------------------------ launchers (host)
 cudaError_t launch_event_desc(const LibView& L, NetView N, uint4* desc, cudaStream_t st);
-cudaError_t launch_gate_pass(const LibView& L, const NetView& N, const WinDesc* wins, int n_win, DevError* err,
-                             cudaStream_t st);
 cudaError_t launch_gate_pass_bwd(const LibView& L, const NetView& N, const WinDesc* wins, double* cell_acc,
                                  cudaStream_t st);
 cudaError_t launch_walk_per_gate(const LibView& L, const NetView& N, const WinDesc* wins, int n_win,
@@ -199,8 +197,6 @@ cudaError_t launch_merge(const WinDesc* wins, const int64_t* tile_base, int n_wi
 // Adjoint input: grad[b] = {dL/dP_b * 1e-3 / bin_ps, G(b * bin_ps)}, and G(T).
 cudaError_t launch_grad_prep(const WinDesc* wins, const float* dLdP, float2* grad, double* tiles, int n_tiles,
                              int n_bins, int bin_ps, float* g_total, cudaStream_t st);
-cudaError_t launch_zero_bins(const WinDesc* wins, const int64_t* tile_base, int n_win, int64_t n_tiles_total,
-                             cudaStream_t st);
 cudaError_t launch_cells_out(const double* acc, int n_cells, float* d_escale, float* d_lscale, cudaStream_t st);
 int merge_tiles(int n_bins);
 

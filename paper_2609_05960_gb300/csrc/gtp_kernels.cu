@@ -142,41 +142,7 @@ cudaError_t launch_event_desc(const LibView& L, NetView N, uint4* desc, cudaStre
   return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ gate pass
-// Per (window, gate): zero the energy accumulators, resolve gates without
-// events (leakage at the initial state over the whole window), and reduce
-// L0 = sum_g P_leak(cell_g, init_g) * lscale into the window's l0.
-__global__ void k_gate_pass(LibView L, NetView N, const WinDesc* __restrict__ wins, DevError* err) {
-  const WinDesc& W = wins[blockIdx.y];
-  double p0 = 0.0;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N.n_gates;
-       g += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t c = N.cell[g];
-    const CellInfo ci = L.cells[c];
-    uint32_t s0 = W.init[g];
-    if (s0 >> (ci.n_in + 1)) {
-      report_error(err, GTP_ERANGE, -1 - g);
-      s0 &= (2u << ci.n_in) - 1u;
-    }
-    const float P = L.leak[ci.leak_base + s0] * L.lscale[c];
-    p0 += (double)P;
-    const int64_t cnt = W.offsets[g + 1] - W.offsets[g];
-    W.e_leak[g] = cnt == 0 ? (double)P * (double)W.window_ps * 1e-6 : 0.0;
-    W.e_int[g] = 0.0;
-    W.e_sw[g] = 0.0;
-    W.final_state[g] = (uint8_t)s0;
-  }
-  __shared__ double red[32];
-  for (int o = 16; o > 0; o >>= 1) p0 += __shfl_down_sync(0xffffffffu, p0, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = p0;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (threadIdx.x == 0) atomicAdd(W.l0, v);
-  }
-}
-
+// ------------------------------------------------------------------ gate pass (adjoint)
 // Adjoint of the gate pass: a gate without events leaks at its initial state
 // over the whole window, so d L / d lscale[c] gains P0(init) * G(T) * 1e-6.
 __global__ void k_gate_pass_bwd(LibView L, NetView N, const WinDesc* __restrict__ wins, double* __restrict__ cell_acc) {
@@ -203,15 +169,6 @@ cudaError_t launch_gate_pass_bwd(const LibView& L, const NetView& N, const WinDe
   int64_t blocks = (N.n_gates + 255) / 256;
   if (blocks > 1024) blocks = 1024;
   k_gate_pass_bwd<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, sizeof(double) * L.n_cells, st>>>(L, N, wins, cell_acc);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_gate_pass(const LibView& L, const NetView& N, const WinDesc* wins, int n_win, DevError* err,
-                             cudaStream_t st) {
-  int64_t blocks = (N.n_gates + 255) / 256;
-  if (blocks > 2048) blocks = 2048;
-  dim3 grid((unsigned)(blocks < 1 ? 1 : blocks), (unsigned)n_win);
-  k_gate_pass<<<grid, 256, 0, st>>>(L, N, wins, err);
   return cudaGetLastError();
 }
 
@@ -342,18 +299,36 @@ __device__ double block_excl_scan(double v, double* total) {
   return r;
 }
 
+// Block-wide sum of one double per thread (valid in thread 0).
+__device__ double block_sum(double v) {
+  __shared__ double warp_tot[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) warp_tot[w] = v;
+  __syncthreads();
+  v = 0.0;
+  if (w == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+
+// Leakage-step sum of each merge tile.  A thread adds its kMergePer steps in
+// FP32 (a handful of terms of the same bins' FP32 accumulators) and the block
+// sums the threads' partials in FP64, so the long prefix is FP64 throughout.
 __global__ void k_tile_sums(const WinDesc* __restrict__ wins, const int64_t* __restrict__ tile_base, int n_win) {
   const int64_t gt = blockIdx.x;
   const int w = window_of(tile_base, n_win, gt);
   const WinDesc& W = wins[w];
   const int tile = (int)(gt - W.tile_base);
+  if (tile >= W.n_tiles) return;
   const int base = tile * kMergeTile + threadIdx.x * kMergePer;
-  double s = 0.0;
+  float s = 0.f;
 #pragma unroll
   for (int k = 0; k < kMergePer; ++k)
-    if (base + k < W.n_bins) s += (double)W.bins[base + k].y;
-  __shared__ double tot;
-  block_excl_scan(s, &tot);
+    if (base + k < W.n_bins) s += W.bins[base + k].y;
+  const double tot = block_sum((double)s);
   if (threadIdx.x == 0) W.tiles[tile] = tot;
 }
 
@@ -372,28 +347,35 @@ __global__ void k_scan_tiles(const WinDesc* __restrict__ wins) {
   }
 }
 
+// Waveform of each merge tile: the leakage power entering a thread's first
+// bin is the FP64 prefix (L0, the earlier tiles, the block's earlier
+// threads); the thread's own bins add, in FP32, their energy and the steps
+// of its earlier bins (a few terms) to that FP64 base.
 __global__ void k_finalize(const WinDesc* __restrict__ wins, const int64_t* __restrict__ tile_base, int n_win) {
   const int64_t gt = blockIdx.x;
   const int w = window_of(tile_base, n_win, gt);
   const WinDesc& W = wins[w];
   const int tile = (int)(gt - W.tile_base);
+  if (tile >= W.n_tiles) return;
   const int base = tile * kMergeTile + threadIdx.x * kMergePer;
   float2 v[kMergePer];
-  double s = 0.0;
+  float s = 0.f;
 #pragma unroll
   for (int k = 0; k < kMergePer; ++k) {
     v[k] = base + k < W.n_bins ? W.bins[base + k] : make_float2(0.f, 0.f);
-    s += (double)v[k].y;
+    s += v[k].y;
   }
   __shared__ double tot;
-  double pre = block_excl_scan(s, &tot) + W.tiles[tile] + *W.l0;
+  const double pre = block_excl_scan((double)s, &tot) + W.tiles[tile] + *W.l0;
   if (W.wave == nullptr) return;
-  const double dt = (double)W.bin_ps;
-  const double to_w = 1e-3 / dt;
+  // W per bin: E (fJ) * 1e-3 / bin_ps + P (nW) * 1e-9
+  const float to_w = (float)(1e-3 / (double)W.bin_ps);
+  const double p0 = pre * 1e-9;
+  float dp = 0.f;
 #pragma unroll
   for (int k = 0; k < kMergePer; ++k) {
-    if (base + k < W.n_bins) W.wave[base + k] = ((double)v[k].x + pre * dt * 1e-6) * to_w;
-    pre += (double)v[k].y;
+    if (base + k < W.n_bins) W.wave[base + k] = (double)fmaf(v[k].x, to_w, dp * 1e-9f) + p0;
+    dp += v[k].y;
   }
 }
 
@@ -449,15 +431,6 @@ __global__ void k_grad_finalize(const float* __restrict__ dLdP, int n_bins, int 
 }
 
 // Zero every window's bin accumulators, one tile per block.
-__global__ void k_zero_bins(const WinDesc* __restrict__ wins, const int64_t* __restrict__ tile_base, int n_win) {
-  const int64_t gt = blockIdx.x;
-  const int w = window_of(tile_base, n_win, gt);
-  const WinDesc& W = wins[w];
-  const int base = (int)(gt - W.tile_base) * kMergeTile;
-  for (int k = threadIdx.x; k < kMergeTile; k += blockDim.x)
-    if (base + k < W.n_bins) W.bins[base + k] = make_float2(0.f, 0.f);
-}
-
 __global__ void k_cells_out(const double* __restrict__ acc, int n_cells, float* d_escale, float* d_lscale) {
   const int c = threadIdx.x + blockIdx.x * blockDim.x;
   if (c < n_cells) {
@@ -467,13 +440,6 @@ __global__ void k_cells_out(const double* __restrict__ acc, int n_cells, float* 
 }
 
 }  // namespace
-
-cudaError_t launch_zero_bins(const WinDesc* wins, const int64_t* tile_base, int n_win, int64_t n_tiles_total,
-                             cudaStream_t st) {
-  if (n_tiles_total <= 0) return cudaSuccess;
-  k_zero_bins<<<(unsigned)n_tiles_total, kMergeThreads, 0, st>>>(wins, tile_base, n_win);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_cells_out(const double* acc, int n_cells, float* d_escale, float* d_lscale, cudaStream_t st) {
   k_cells_out<<<(n_cells + 255) / 256, 256, 0, st>>>(acc, n_cells, d_escale, d_lscale);

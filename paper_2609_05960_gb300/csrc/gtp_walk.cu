@@ -65,38 +65,145 @@ __device__ __forceinline__ int work_bucket(int64_t c, int dmin, int64_t seg_len)
 
 __host__ __device__ constexpr int n_buckets(int dmin) { return kSparseBase + dmin; }
 
-// Per (window, gate): histogram of work buckets (block-aggregated).
-__global__ void k_plan_classify(const WinDesc* __restrict__ wins, int64_t G, int64_t seg_len, int dmin, PlanBufs P) {
-  extern __shared__ unsigned int sh[];
-  const int nb = n_buckets(dmin);
-  const WinDesc& W = wins[blockIdx.y];
-  unsigned long long* hist = P.counters + 4;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) sh[b] = 0u;
+// Plan counters: [0] big, [1] medium, [2] sparse gates; [3] the walk's work
+// counter; [4] blocks of the preparation pass that have finished; then the
+// work-list histogram [nb] and the bucket cursors [nb].
+constexpr int kCntDone = 4;
+constexpr int kCntHist = 5;
+
+// Block-wide exclusive scan of one value per thread (blockDim.x a multiple of
+// 32); returns the thread's exclusive prefix and writes the block total.
+__device__ unsigned long long block_excl_scan_u64(unsigned long long v, unsigned long long* total) {
+  __shared__ unsigned long long warp_tot[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned long long inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
+  }
+  if (lane == 31) warp_tot[w] = inc;
   __syncthreads();
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < G; g += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = W.offsets[g + 1] - W.offsets[g];
-    if (c > 0) atomicAdd(&sh[work_bucket(c, dmin, seg_len)], 1u);
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    const unsigned long long x = lane < nw ? warp_tot[lane] : 0ull;
+    unsigned long long xi = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long u = __shfl_up_sync(0xffffffffu, xi, o);
+      if (lane >= o) xi += u;
+    }
+    if (lane < nw) warp_tot[lane] = xi - x;
+    if (lane == nw - 1) *total = xi;
   }
   __syncthreads();
-  for (int b = threadIdx.x; b < nb; b += blockDim.x)
-    if (sh[b]) atomicAdd(hist + b, (unsigned long long)sh[b]);
+  const unsigned long long r = inc - v + warp_tot[w];
+  __syncthreads();
+  return r;
 }
 
-// Bucket starts (exclusive scan in bucket order) and the three list sizes.
-__global__ void k_plan_scan(int dmin, PlanBufs P) {
-  if (threadIdx.x != 0) return;
-  const int nb = n_buckets(dmin);
-  unsigned long long* hist = P.counters + 4;
-  unsigned long long* cursor = hist + nb;
-  unsigned long long acc = 0, part[3] = {0, 0, 0};
-  for (int b = 0; b < nb; ++b) {
-    cursor[b] = acc;
-    acc += hist[b];
-    part[b < kBigBuckets ? 0 : (b < kSparseBase ? 1 : 2)] += hist[b];
+// Bucket starts (exclusive scan of the histogram in bucket order) and the
+// three list sizes; run by one whole block once every histogram update has
+// landed.
+__device__ void plan_bucket_starts(int nb, PlanBufs P) {
+  const unsigned long long* hist = P.counters + kCntHist;
+  unsigned long long* cursor = P.counters + kCntHist + nb;
+  __shared__ unsigned long long starts[2], tot;
+  const int per = (nb + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int b0 = min(nb, (int)threadIdx.x * per), b1 = min(nb, b0 + per);
+  unsigned long long sum = 0ull;
+  for (int b = b0; b < b1; ++b) sum += __ldcg(hist + b);
+  unsigned long long pre = block_excl_scan_u64(sum, &tot);
+  for (int b = b0; b < b1; ++b) {
+    if (b == kBigBuckets) starts[0] = pre;
+    if (b == kSparseBase) starts[1] = pre;
+    cursor[b] = pre;
+    pre += __ldcg(hist + b);
   }
-  P.counters[0] = part[0];
-  P.counters[1] = part[1];
-  P.counters[2] = part[2];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    P.counters[0] = starts[0];
+    P.counters[1] = starts[1] - starts[0];
+    P.counters[2] = tot - starts[1];
+  }
+}
+
+// One pass over (window, gate), launched on a grid of (blocks, windows):
+//   GATE  clear the window's bins and do the gate pass: L0 = sum over gates
+//         of P_leak(cell, initial state) * lscale into the window's l0, and a
+//         gate without events leaks at its initial state over the whole
+//         window (with PLAN the walk writes the results of the other gates;
+//         without it every gate's results are initialised here);
+//   PLAN  histogram of work buckets (block-aggregated); the block that
+//         finishes last turns it into bucket starts.
+template <bool GATE, bool PLAN>
+__global__ void __launch_bounds__(256) k_prepare(LibView L, NetView N, const WinDesc* __restrict__ wins,
+                                                 DevError* err, int64_t seg_len, int dmin, PlanBufs P) {
+  extern __shared__ unsigned int sh[];  // PLAN: [nb] bucket counts of this block
+  __shared__ double red[32];
+  __shared__ bool s_last;
+  const int nb = n_buckets(dmin);
+  const WinDesc& W = wins[blockIdx.y];
+  const int64_t G = N.n_gates;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (PLAN) {
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) sh[b] = 0u;
+    __syncthreads();
+  }
+  if (GATE) {  // bins are 8-byte pairs in a 256-byte aligned buffer: two per 16-byte store
+    float4* b4 = reinterpret_cast<float4*>(W.bins);
+    const int64_t n4 = (int64_t)W.n_bins >> 1;
+    for (int64_t i = tid; i < n4; i += stride) b4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (tid == 0 && (W.n_bins & 1)) W.bins[W.n_bins - 1] = make_float2(0.f, 0.f);
+  }
+  double p0 = 0.0;
+  for (int64_t g = tid; g < G; g += stride) {
+    const int64_t c = W.offsets[g + 1] - W.offsets[g];
+    if (GATE) {
+      const int32_t cell = N.cell[g];
+      const CellInfo ci = L.cells[cell];
+      uint32_t s0 = W.init[g];
+      if (s0 >> (ci.n_in + 1)) {
+        report_error(err, GTP_ERANGE, -1 - g);
+        s0 &= (2u << ci.n_in) - 1u;
+      }
+      const float Pl = L.leak[ci.leak_base + s0] * L.lscale[cell];
+      p0 += (double)Pl;
+      if (!PLAN || c == 0) {
+        W.e_leak[g] = c == 0 ? (double)Pl * (double)W.window_ps * 1e-6 : 0.0;
+        W.e_int[g] = 0.0;
+        W.e_sw[g] = 0.0;
+        W.final_state[g] = (uint8_t)s0;
+      }
+    }
+    if (PLAN && c > 0) atomicAdd(&sh[work_bucket(c, dmin, seg_len)], 1u);
+  }
+  if (GATE) {
+    for (int o = 16; o > 0; o >>= 1) p0 += __shfl_down_sync(0xffffffffu, p0, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = p0;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (threadIdx.x == 0) atomicAdd(W.l0, v);
+    }
+  }
+  if (PLAN) {
+    __syncthreads();
+    unsigned long long* hist = P.counters + kCntHist;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+      if (sh[b]) atomicAdd(hist + b, (unsigned long long)sh[b]);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0)
+      s_last = atomicAdd(P.counters + kCntDone, 1ull) == (unsigned long long)gridDim.x * gridDim.y - 1ull;
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      plan_bucket_starts(nb, P);
+    }
+  }
 }
 
 __global__ void k_plan_scatter(const WinDesc* __restrict__ wins, int64_t G, int64_t seg_len, int dmin, PlanBufs P) {
@@ -104,7 +211,7 @@ __global__ void k_plan_scatter(const WinDesc* __restrict__ wins, int64_t G, int6
   const int nb = n_buckets(dmin);
   unsigned int* sh = reinterpret_cast<unsigned int*>(sbase + nb);
   const WinDesc& W = wins[blockIdx.y];
-  unsigned long long* cursor = P.counters + 4 + nb;
+  unsigned long long* cursor = P.counters + kCntHist + nb;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < G; base += (int64_t)gridDim.x * blockDim.x) {
     for (int b = threadIdx.x; b < nb; b += blockDim.x) sh[b] = 0u;
     __syncthreads();
@@ -141,7 +248,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 constexpr uint32_t kXH = 1u << 16;
 constexpr uint32_t kXAbs = 1u << 17;
 constexpr int kTabMaxIn = 4;                                     // wider cells interpolate per event
-constexpr int kTabEntries = (kTabMaxIn + 1) << (kTabMaxIn + 1);  // (pin, edge, input state) energies
+constexpr int kTabEntries = 32 << kTabMaxIn;  // energies by (record meta bits 0-4, input state)
 constexpr int kLeakEntries = 2 << kTabMaxIn;
 
 __device__ __forceinline__ uint32_t xcompose(uint32_t a, uint32_t b) {
@@ -174,9 +281,10 @@ __device__ __forceinline__ int stage_pos(int row, int k) {
 // Per-warp shared memory of the dense walk.
 struct DenseSmem {
   uint2* rec;      // [2][32 * K] staged records (double buffer)
-  float* etab;     // [kTabEntries] energy per (pin, edge, input state); adjoint: unscaled
+  float* etab;     // [kTabEntries] energy at ((val << 4 | pin) << n_in) | input state; adjoint: unscaled
   float* dtab;     // adjoint: [kTabEntries] escale * dE/dC
   float* leak;     // [kLeakEntries] leakage per state (forward: scaled)
+  uint2* halo;     // [2][2] per staging buffer: the records just before and just after the segment
   double* wacc;    // adjoint: [2 * n_cells] per-warp cell sums
 };
 
@@ -239,33 +347,48 @@ __device__ __forceinline__ void build_tables(const LibView& L, const DGate& d, c
       E = BWD ? 0.f : __uint_as_float(q.w);
       dE = L.half_v2;
     }
-    sm.etab[e] = E;
-    if (BWD) sm.dtab[e] = dE;
+    // indexed by the record's low meta bits (pin, value after the edge) and the input state
+    const uint32_t at = ((((pv & 1u) << 4) | pin) << d.n_in) | s;
+    sm.etab[at] = E;
+    if (BWD) sm.dtab[at] = dE;
   }
   for (int s = lane; s < (int)(2u << d.n_in); s += 32) sm.leak[s] = __ldg(d.gleak + s) * d.lsc;
 }
 
-// Start the copy of segment `s` of the gate into staging buffer `buf`
-// (one commit group, possibly empty).
+// Word offset of record 0 of lane `row` in a staging buffer: record k of
+// that row sits at row_base ^ k (the identity stage_pos(row, k) ==
+// stage_pos(row, 0) ^ k holds because the swizzle only permutes aligned
+// pairs within the row).
 template <int K>
-__device__ __forceinline__ void issue_segment(const DGate& d, int64_t s, uint2* buf, int lane) {
+__device__ __forceinline__ uint32_t row_base(int row) {
+  constexpr int kShift = K == 16 ? 0 : (K == 8 ? 1 : 2);
+  return (uint32_t)(row * K) ^ ((((uint32_t)row >> kShift) & (uint32_t)(K / 2 - 1)) << 1);
+}
+
+// Start the copy of segment `s` of the gate into staging buffer `buf`, with
+// its neighbouring records (the gate's record before the segment, if any, and
+// the one after it, if any) into `halo` (one commit group, possibly empty).
+// Lane l copies records m * 32 + l; their swizzled positions are
+// 32 * m + (c0 ^ (((2 * m) & (K/2 - 1)) << 1)) with c0 = stage_pos(l / K, l % K).
+template <int K>
+__device__ __forceinline__ void issue_segment(const DGate& d, int64_t s, uint2* buf, uint2* halo, int lane) {
   constexpr int SEG = 32 * K;
+  constexpr uint32_t M = K / 2 - 1;
   if (s * SEG < d.n) {
     const int64_t s0 = d.ga + s * SEG;
     const int n_rem = (int)min((int64_t)SEG, d.n - s * SEG);
+    const uint32_t sb = smem_addr(buf);
+    const uint32_t c0 = 8u * (row_base<K>(lane / K) ^ (uint32_t)(lane % K));  // bytes
+    const uint2* src = d.rec + s0 + lane;
 #pragma unroll
     for (int m = 0; m < K; ++m) {
-      const int r = m * 32 + lane;
-      if (r < n_rem) cp_async8(smem_addr(buf + stage_pos<K>(r / K, r % K)), d.rec + s0 + r);
+      const uint32_t cm = 8u * ((((uint32_t)(2 * m)) & M) << 1);
+      if (m * 32 + lane < n_rem) cp_async8(sb + 256u * m + (c0 ^ cm), src + m * 32);
     }
+    if (lane == 0 && s > 0) cp_async8(smem_addr(halo), d.rec + s0 - 1);
+    if (lane == 31 && s * SEG + SEG < d.n) cp_async8(smem_addr(halo + 1), d.rec + s0 + SEG);
   }
   cp_async_commit();
-}
-
-// Record k of this lane from the staging buffer (t, meta).
-template <int K>
-__device__ __forceinline__ uint2 stage_rec(const uint2* buf, int lane, int k) {
-  return buf[stage_pos<K>(lane, k)];
 }
 
 // One staged segment with its first pass done.
@@ -275,53 +398,61 @@ struct Seg {
   uint32_t t_before;         // time of the event before the lane's first (0 at the gate start)
   uint32_t t_after;          // time of the event after the lane's last (~0 at the gate end)
   bool fh, last_seg;         // the lane's first event starts the gate; the segment ends it
+  bool bad;                  // one of the lane's records may fail a check (seg_check_bits decides)
   uint32_t ex;               // transfer of the segment's events before this lane
-  uint32_t bad_r, bad_o;     // per-record check bits
 };
 
-// Pass 1 of segment s of the gate, staged in `buf` (its copy must have
-// landed): the lane's transfer, the warp scan of transfers and the record
-// checks.  Returns the segment's transfer (identity past the gate's end).
-template <int K>
-__device__ __forceinline__ uint32_t seg_front(const DGate& d, int64_t s, const uint2* buf, Seg& q, int lane) {
+// Pass 1 of segment s of the gate, staged in `buf` with its neighbours in
+// `halo` (the copy must have landed): the lane's transfer, the warp scan of
+// transfers, and a cheap screen of the records (the largest time and pin,
+// the smallest step between times).  Returns the segment's transfer
+// (identity past the gate's end).  FULL: the segment holds 32 * K events.
+template <int K, bool FULL>
+__device__ __forceinline__ uint32_t seg_front(const DGate& d, int64_t s, const uint2* buf, const uint2* halo, Seg& q,
+                                              int lane) {
   constexpr int SEG = 32 * K;
   q.s0 = d.ga + s * SEG;
-  q.n_rem = (int)max((int64_t)0, min((int64_t)SEG, d.n - s * SEG));
+  q.n_rem = FULL ? SEG : (int)max((int64_t)0, min((int64_t)SEG, d.n - s * SEG));
   const int j0 = lane * K;
-  q.nk = max(0, min(K, q.n_rem - j0));
+  q.nk = FULL ? K : max(0, min(K, q.n_rem - j0));
   q.last_seg = s * SEG + SEG >= d.n;
   q.fh = s == 0 && lane == 0;
-  q.bad_r = 0u;
-  q.bad_o = 0u;
+  q.bad = false;
   q.ex = 0u;
-  if (q.n_rem == 0) return 0u;
-  uint32_t t_edge = 0u;
-  if (lane == 0 && s > 0) t_edge = d.rec[q.s0 - 1].x;
-  if (lane == 31) t_edge = q.last_seg ? 0xFFFFFFFFu : d.rec[q.s0 + q.n_rem].x;
-  const uint32_t seg_after = __shfl_sync(kFull, t_edge, 31);
-  const uint32_t t_prev_lane = stage_rec<K>(buf, max(lane - 1, 0), K - 1).x;  // garbage where unused
-  const uint32_t t_next_lane = stage_rec<K>(buf, min(lane + 1, 31), 0).x;
-  q.t_before = lane == 0 ? t_edge : t_prev_lane;
-  q.t_after = j0 + K < q.n_rem ? t_next_lane : seg_after;
+  if (!FULL && q.n_rem == 0) return 0u;
+  const uint32_t seg_before = s > 0 ? halo[0].x : 0u;
+  const uint32_t seg_after = q.last_seg ? 0xFFFFFFFFu : halo[1].x;
+  const uint32_t t_prev_lane = buf[row_base<K>(max(lane - 1, 0)) ^ (uint32_t)(K - 1)].x;  // garbage where unused
+  const uint32_t t_next_lane = buf[row_base<K>(min(lane + 1, 31))].x;
+  q.t_before = lane == 0 ? seg_before : t_prev_lane;
+  q.t_after = (FULL ? lane < 31 : j0 + K < q.n_rem) ? t_next_lane : seg_after;
 
-  uint32_t X = 0u, Y = 0u, H = 0u;
+  const uint32_t rb = row_base<K>(lane);
+  const uint4* b4 = reinterpret_cast<const uint4*>(buf);
+  uint32_t X = 0u, Y = 0u, H = 0u, tmax = 0u, mmax = 0u;
+  int32_t step_min = 0;
   uint32_t tp = q.t_before;
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    if (k < q.nk) {
-      const uint2 r = stage_rec<K>(buf, lane, k);
-      const uint32_t t = r.x, m = r.y;
-      const bool head = t != tp || (k == 0 && q.fh);
-      if (head) {
-        Y = X;
-        H = kXH;
+  for (int k = 0; k < K; k += 2) {
+    const uint4 v = b4[(rb ^ (uint32_t)k) >> 1];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (FULL || k + h < q.nk) {
+        const uint32_t t = h ? v.z : v.x, m = h ? v.w : v.y;
+        const bool head = t != tp || (k + h == 0 && q.fh);
+        Y = head ? X : Y;
+        H = head ? kXH : H;
+        X ^= (1u << (m & 0xFu)) & 0xFFu;
+        tmax = max(tmax, t);
+        mmax = max(mmax, m & ~0x10u);
+        step_min = min(step_min, (int32_t)(t - tp));
+        tp = t;
       }
-      X ^= (1u << (m & 0xFu)) & 0xFFu;
-      q.bad_r |= (uint32_t)(t >= d.T || (m & ~0x10u) > d.n_in) << k;
-      q.bad_o |= (uint32_t)((int32_t)t < (int32_t)tp && !(k == 0 && q.fh)) << k;
-      tp = t;
     }
   }
+  // any time at or past the window end or past 2^31, any pin or reserved bit
+  // out of range, or any decrease (exactly: see seg_check_bits)
+  q.bad = tmax >= d.T || mmax > d.n_in || step_min < 0;
   uint32_t w = X | (Y << 8) | H;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -333,6 +464,59 @@ __device__ __forceinline__ uint32_t seg_front(const DGate& d, int64_t s, const u
   return __shfl_sync(kFull, w, 31);
 }
 
+// The per-record check bits of a lane whose screen failed: bit k of bad_r
+// for a record outside the window or with a bad pin or reserved bit, of
+// bad_o for a time below its predecessor's (signed, as the walk compares).
+template <int K>
+__device__ __noinline__ void seg_check_bits(const DGate& d, const uint2* buf, const Seg& q, int lane, uint32_t& bad_r,
+                                            uint32_t& bad_o) {
+  const uint32_t rb = row_base<K>(lane);
+  uint32_t tp = q.t_before;
+  bad_r = 0u;
+  bad_o = 0u;
+  for (int k = 0; k < q.nk; ++k) {
+    const uint2 r = buf[rb ^ (uint32_t)k];
+    const uint32_t t = r.x, m = r.y;
+    bad_r |= (uint32_t)(t >= d.T || (m & ~0x10u) > d.n_in) << k;
+    bad_o |= (uint32_t)((int32_t)t < (int32_t)tp && !(k == 0 && q.fh)) << k;
+    tp = t;
+  }
+}
+
+// First record of the lane whose event does not toggle its pin, replaying
+// the lane's states from st (-1 if none).
+template <int K>
+__device__ __noinline__ int seg_first_no_toggle(const DGate& d, const uint2* buf, const Seg& q, int lane,
+                                                uint32_t st) {
+  const uint32_t rb = row_base<K>(lane);
+  for (int k = 0; k < q.nk; ++k) {
+    const uint32_t m = buf[rb ^ (uint32_t)k].y;
+    const uint32_t pin = m & 0xFu, val = (m >> 4) & 1u;
+    if (((st >> pin) & 1u) == val) return k;
+    st = (st ^ (1u << pin)) & d.pmask;
+  }
+  return -1;
+}
+
+// Fire-and-forget {energy, leakage step} reduction into bin b when p holds
+// (predicated, no branch).
+__device__ __forceinline__ void red_bin_if(bool p, float2* bins, uint32_t b, float e, float dp) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %3, 0;\n\t@q red.global.add.v2.f32 [%0], {%1, %2};\n\t}" ::"l"(bins + b),
+      "f"(e), "f"(dp), "r"((uint32_t)p)
+      : "memory");
+}
+
+// Bin of t (as bin_of) and the end of that bin in ps.
+__device__ __forceinline__ uint32_t bin_end_of(uint32_t t, const DGate& d, uint32_t& end) {
+  uint32_t b = __umulhi(t, d.magic) >> d.shift;
+  end = (b + 1u) * d.bin_ps;
+  const bool up = end <= t;
+  b += up ? 1u : 0u;
+  end += up ? d.bin_ps : 0u;
+  return b;
+}
+
 // Per-lane sums of one segment (forward: leakage nW*ps, internal fJ,
 // switching fJ; adjoint: dC, d_escale, d_lscale * 1e6).
 struct SegSums {
@@ -340,20 +524,21 @@ struct SegSums {
 };
 
 // Pass 2 of a staged segment whose incoming state is the absolute transfer
-// seg_in.
-template <int K, bool BWD, bool TAB>
+// seg_in.  FULL: the segment holds 32 * K events.
+template <int K, bool BWD, bool TAB, bool FULL>
 __device__ __forceinline__ SegSums seg_back(const LibView& L, const DGate& d, const DenseSmem& sm, const uint2* buf,
                                             const Seg& q, uint32_t seg_in, DevError* err, int lane) {
   SegSums out{0.f, 0.f, 0.f};
-  if (q.n_rem == 0) return out;
-  const bool any_r = __any_sync(kFull, q.bad_r != 0u);
-  if (any_r || __any_sync(kFull, q.bad_o != 0u)) {
-    const uint32_t bb = q.bad_r | q.bad_o;
+  if (!FULL && q.n_rem == 0) return out;
+  if (__any_sync(kFull, q.bad)) {
+    uint32_t bad_r = 0u, bad_o = 0u;
+    if (q.bad) seg_check_bits<K>(d, buf, q, lane, bad_r, bad_o);
+    const uint32_t bb = bad_r | bad_o;
     if (bb) {
       const int k = __ffs(bb) - 1;
-      report_error(err, ((q.bad_r >> k) & 1u) ? GTP_ERANGE : GTP_EORDER, q.s0 + lane * K + k);
+      report_error(err, ((bad_r >> k) & 1u) ? GTP_ERANGE : GTP_EORDER, q.s0 + lane * K + k);
     }
-    if (any_r) return out;  // an event outside the window: skip the replay
+    if (__any_sync(kFull, bad_r != 0u)) return out;  // an event outside the window: skip the replay
   }
   const uint32_t li = xcompose(seg_in, q.ex);
   uint32_t st = li & d.pmask;            // state before the lane's first event
@@ -373,87 +558,85 @@ __device__ __forceinline__ SegSums seg_back(const LibView& L, const DGate& d, co
     const float2 gv = d.W->grad[bb];
     Gcur = gv.y + gv.x * (float)(q.t_before - bb * d.bin_ps);
   }
-  uint32_t pb = 0xFFFFFFFFu;
+  const uint32_t rb = row_base<K>(lane);
+  uint2 r = buf[rb];                       // the lane's next record
+  uint32_t pb = bin_of(r.x, d.magic, d.shift, d.bin_ps);  // pending bin (garbage for a lane without events)
   float pe = 0.f, pdp = 0.f;
-  uint32_t bad_t = 0u;
+  uint32_t tog = 1u;                       // bit 0 clears on an event that does not toggle its pin
   uint32_t tp = q.t_before;
-  uint2 r = stage_rec<K>(buf, lane, 0);
+  auto event = [&](int k, uint32_t t, uint32_t m, uint32_t tn) {
+    if (!FULL && k >= q.nk) return;
+    const uint32_t pin = m & 0xFu, val = (m >> 4) & 1u;
+    const bool head = t != tp || (k == 0 && q.fh);
+    uint32_t bend;
+    const uint32_t bn = bin_end_of(t, d, bend);
+    float Gt = 0.f, gE = 0.f;
+    if (BWD) {
+      const float2 gv = d.W->grad[bn];
+      gE = gv.x;
+      Gt = gv.y + gv.x * (float)(t - (bend - d.bin_ps));
+      v2 = head ? fmaf(Pcur, Gt - Gcur, v2) : v2;
+      Gcur = head ? Gt : Gcur;
+    } else {
+      v0 = head ? fmaf(Pcur, (float)(int32_t)(t - tp), v0) : v0;
+    }
+    spre = head ? st : spre;
+    Pg = head ? Pcur : Pg;
+    tog &= (st >> pin) ^ val;
+    st = (st ^ (1u << pin)) & d.pmask;
+    const bool is_out = pin >= d.n_in;
+    float E, dE = 0.f;
+    if (TAB) {
+      const uint32_t idx = ((m & 0x1Fu) << d.n_in) | (spre & d.inmask);
+      E = sm.etab[idx];
+      if (BWD) dE = sm.dtab[idx];
+    } else {
+      const uint4 dq = __ldg(d.dsc + min(pin, d.n_in) * 2u + val);
+      if (is_out) {
+        E = BWD ? 0.f : __uint_as_float(dq.w);
+        dE = L.half_v2;
+      } else {
+        const float* p = L.tab + (dq.z & 0xFFFFu) + side_bits(spre, pin, d.n_in) * (uint32_t)L.tsize;
+        const float a0 = __ldg(p), a1 = __ldg(p + 1), b0 = __ldg(p + L.nl), b1 = __ldg(p + L.nl + 1);
+        const float fl = __uint_as_float(dq.y), fs = __uint_as_float(dq.x);
+        const float lo = fmaf(fl, a1 - a0, a0), hi = fmaf(fl, b1 - b0, b0);
+        const float eu = fmaf(fs, hi - lo, lo);
+        E = BWD ? eu : eu * d.esc;
+        dE = d.esc * (fmaf(fs, (b1 - b0) - (a1 - a0), a1 - a0) * __uint_as_float(dq.w));
+      }
+    }
+    const bool tail = tn != t;
+    float Pn = Pcur;
+    if (tail) Pn = TAB ? sm.leak[st] : __ldg(d.gleak + st) * d.lsc;
+    if (BWD) {
+      v0 = fmaf(gE, dE, v0);
+      v1 = fmaf(gE, E, v1);
+    } else {
+      const float Eo = is_out ? E : 0.f;
+      v2 += Eo;
+      v1 += E - Eo;
+      const float dp = tail ? Pn - Pg : 0.f;
+      const float add = dp * (float)(int32_t)(bend - t) * 1e-6f;
+      const bool nb = bn != pb;
+      red_bin_if(nb, d.W->bins, pb, pe, pdp);
+      pe = (nb ? 0.f : pe) + (E + add);
+      pdp = (nb ? 0.f : pdp) + dp;
+      pb = bn;
+    }
+    Pcur = Pn;
+    tp = t;
+  };
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    if (k < q.nk) {
-      const uint32_t t = r.x, m = r.y;
-      if (k + 1 < K) r = stage_rec<K>(buf, lane, k + 1);
-      const uint32_t tn = k + 1 < q.nk ? r.x : q.t_after;
-      const uint32_t pin = m & 0xFu, val = (m >> 4) & 1u;
-      const bool head = t != tp || (k == 0 && q.fh);
-      const uint32_t bn = bin_of(t, d.magic, d.shift, d.bin_ps);
-      float Gt = 0.f, gE = 0.f;
-      if (BWD) {
-        const float2 gv = d.W->grad[bn];
-        gE = gv.x;
-        Gt = gv.y + gv.x * (float)(t - bn * d.bin_ps);
-      }
-      if (head) {
-        if (BWD) {
-          v2 += Pcur * (Gt - Gcur);
-          Gcur = Gt;
-        } else {
-          v0 += Pcur * (float)(int32_t)(t - tp);
-        }
-        spre = st;
-        Pg = Pcur;
-      }
-      bad_t |= (uint32_t)(((st >> pin) & 1u) == val) << k;
-      st = (st ^ (1u << pin)) & d.pmask;
-      const bool is_out = pin >= d.n_in;
-      float E, dE = 0.f;
-      if (TAB) {
-        const uint32_t idx = ((min(pin, d.n_in) * 2u + val) << d.n_in) | (spre & d.inmask);
-        E = sm.etab[idx];
-        if (BWD) dE = sm.dtab[idx];
-      } else {
-        const uint4 dq = __ldg(d.dsc + min(pin, d.n_in) * 2u + val);
-        if (is_out) {
-          E = BWD ? 0.f : __uint_as_float(dq.w);
-          dE = L.half_v2;
-        } else {
-          const float* p = L.tab + (dq.z & 0xFFFFu) + side_bits(spre, pin, d.n_in) * (uint32_t)L.tsize;
-          const float a0 = __ldg(p), a1 = __ldg(p + 1), b0 = __ldg(p + L.nl), b1 = __ldg(p + L.nl + 1);
-          const float fl = __uint_as_float(dq.y), fs = __uint_as_float(dq.x);
-          const float lo = fmaf(fl, a1 - a0, a0), hi = fmaf(fl, b1 - b0, b0);
-          const float eu = fmaf(fs, hi - lo, lo);
-          E = BWD ? eu : eu * d.esc;
-          dE = d.esc * (fmaf(fs, (b1 - b0) - (a1 - a0), a1 - a0) * __uint_as_float(dq.w));
-        }
-      }
-      const bool tail = tn != t;
-      float Pn = Pcur;
-      if (tail) Pn = TAB ? sm.leak[st] : __ldg(d.gleak + st) * d.lsc;
-      if (BWD) {
-        v0 += gE * dE;
-        v1 += gE * E;
-      } else {
-        if (is_out) v2 += E; else v1 += E;
-        float dp = 0.f, add = 0.f;
-        if (tail) {
-          dp = Pn - Pg;
-          add = dp * (float)(int32_t)((bn + 1u) * d.bin_ps - t) * 1e-6f;
-        }
-        if (bn != pb) {
-          if (pb != 0xFFFFFFFFu) red_bin(d.W->bins, pb, pe, pdp);
-          pb = bn;
-          pe = 0.f;
-          pdp = 0.f;
-        }
-        pe += E + add;
-        pdp += dp;
-      }
-      Pcur = Pn;
-      tp = t;
-    }
+    const uint32_t t = r.x, m = r.y;
+    if (k + 1 < K) r = buf[rb ^ (uint32_t)(k + 1)];
+    event(k, t, m, (k + 1 < K && (FULL || k + 1 < q.nk)) ? r.x : q.t_after);
   }
-  if (!BWD && pb != 0xFFFFFFFFu) red_bin(d.W->bins, pb, pe, pdp);
-  if (bad_t) report_error(err, GTP_ENOTOGGLE, q.s0 + lane * K + (__ffs(bad_t) - 1));
+  if (!BWD && (FULL || q.nk > 0)) red_bin(d.W->bins, pb, pe, pdp);
+  if (!(tog & 1u)) {
+    const int k = seg_first_no_toggle<K>(d, buf, q, lane, li & d.pmask);
+    report_error(err, GTP_ENOTOGGLE, q.s0 + lane * K + (k < 0 ? 0 : k));
+  }
   // gate end: leakage to the window end and the final state
   if (q.last_seg && q.nk > 0 && lane * K + q.nk == q.n_rem) {
     if (BWD) {
@@ -469,14 +652,29 @@ __device__ __forceinline__ SegSums seg_back(const LibView& L, const DGate& d, co
   return out;
 }
 
-// Warp-level FP64 accumulation of per-lane segment sums (valid in lane 0).
+// Per-gate sums of a warp: each lane adds its segment sums in FP32 for up to
+// F segments (at most 64 events a lane), then the warp folds them into FP64
+// (valid in lane 0 after flush()).  GB300 issues FP64 at a small fraction of
+// the FP32 rate, so the FP64 work is kept to one fold per F segments.
+template <int K>
 struct GateAcc {
+  static constexpr int F = 64 / K;
   double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-  __device__ __forceinline__ void add(const SegSums& s) {
-    const float v0 = warp_sum(s.v0), v1 = warp_sum(s.v1), v2 = warp_sum(s.v2);
+  float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+  int n = 0;
+  __device__ __forceinline__ void flush() {
+    const float v0 = warp_sum(f0), v1 = warp_sum(f1), v2 = warp_sum(f2);
     a0 += (double)v0;
     a1 += (double)v1;
     a2 += (double)v2;
+    f0 = f1 = f2 = 0.f;
+    n = 0;
+  }
+  __device__ __forceinline__ void add(const SegSums& s) {
+    f0 += s.v0;
+    f1 += s.v1;
+    f2 += s.v2;
+    if (++n == F) flush();
   }
 };
 
@@ -502,21 +700,29 @@ __device__ __forceinline__ void medium_gate(const LibView& L, const DGate& d, co
   constexpr int SEG = 32 * K;
   const int64_t nseg = (d.n + SEG - 1) / SEG;
   __syncwarp();
-  issue_segment<K>(d, 0, sm.rec, lane);
+  issue_segment<K>(d, 0, sm.rec, sm.halo, lane);
   if (TAB) build_tables<BWD>(L, d, sm, lane);
   uint32_t carry = kXAbs | kXH | d.init | (d.init << 8);
-  GateAcc acc;
+  GateAcc<K> acc;
   Seg q;
   for (int64_t s = 0; s < nseg; ++s) {
     const uint2* cur = sm.rec + (s & 1) * SEG;
-    issue_segment<K>(d, s + 1, sm.rec + ((s + 1) & 1) * SEG, lane);
+    issue_segment<K>(d, s + 1, sm.rec + ((s + 1) & 1) * SEG, sm.halo + ((s + 1) & 1) * 2, lane);
     cp_async_wait_1();
     __syncwarp();
-    const uint32_t tx = seg_front<K>(d, s, cur, q, lane);
-    acc.add(seg_back<K, BWD, TAB>(L, d, sm, cur, q, carry, err, lane));
+    const uint2* halo = sm.halo + (s & 1) * 2;
+    uint32_t tx;
+    if ((s + 1) * SEG <= d.n) {
+      tx = seg_front<K, true>(d, s, cur, halo, q, lane);
+      acc.add(seg_back<K, BWD, TAB, true>(L, d, sm, cur, q, carry, err, lane));
+    } else {
+      tx = seg_front<K, false>(d, s, cur, halo, q, lane);
+      acc.add(seg_back<K, BWD, TAB, false>(L, d, sm, cur, q, carry, err, lane));
+    }
     carry = xcompose(carry, tx);
     __syncwarp();
   }
+  acc.flush();
   if (lane == 0) store_gate<BWD>(L, d, sm, acc.a0, acc.a1, acc.a2);
 }
 
@@ -529,18 +735,20 @@ __device__ __forceinline__ void big_gate(const LibView& L, const DGate& d, const
   constexpr int SEG = 32 * K;
   const int64_t nchunk = (d.n + (int64_t)kWarps * SEG - 1) / ((int64_t)kWarps * SEG);
   __syncwarp();
-  issue_segment<K>(d, wib, sm.rec, lane);
+  issue_segment<K>(d, wib, sm.rec, sm.halo, lane);
   if (TAB) build_tables<BWD>(L, d, sm, lane);
   uint32_t carry = kXAbs | kXH | d.init | (d.init << 8);
-  GateAcc acc;
+  GateAcc<K> acc;
   Seg q;
   for (int64_t c = 0; c < nchunk; ++c) {
     const int64_t s = c * kWarps + wib;
     const uint2* cur = sm.rec + (c & 1) * SEG;
-    issue_segment<K>(d, s + kWarps, sm.rec + ((c + 1) & 1) * SEG, lane);
+    issue_segment<K>(d, s + kWarps, sm.rec + ((c + 1) & 1) * SEG, sm.halo + ((c + 1) & 1) * 2, lane);
     cp_async_wait_1();
     __syncwarp();
-    const uint32_t tx = seg_front<K>(d, s, cur, q, lane);
+    const uint2* halo = sm.halo + (c & 1) * 2;
+    const bool full = (s + 1) * SEG <= d.n;
+    const uint32_t tx = full ? seg_front<K, true>(d, s, cur, halo, q, lane) : seg_front<K, false>(d, s, cur, halo, q, lane);
     if (lane == 0) xfer[c & 1][wib] = tx;
     __syncthreads();
     uint32_t seg_in = carry;
@@ -550,9 +758,11 @@ __device__ __forceinline__ void big_gate(const LibView& L, const DGate& d, const
       if (v == wib) seg_in = carry;
       carry = xcompose(carry, x);
     }
-    acc.add(seg_back<K, BWD, TAB>(L, d, sm, cur, q, seg_in, err, lane));
+    acc.add(full ? seg_back<K, BWD, TAB, true>(L, d, sm, cur, q, seg_in, err, lane)
+                 : seg_back<K, BWD, TAB, false>(L, d, sm, cur, q, seg_in, err, lane));
     __syncwarp();
   }
+  acc.flush();
   if (lane == 0) {
     red[wib][0] = acc.a0;
     red[wib][1] = acc.a1;
@@ -571,25 +781,26 @@ __device__ __forceinline__ void big_gate(const LibView& L, const DGate& d, const
 }
 
 // ------------------------------------------------------------------ sparse gates, one per thread
-constexpr int kChunk = 4;             // records a thread stages per copy round (two rounds in flight)
+constexpr int kChunk = 4;                  // events a thread walks per staged round
+constexpr int kStage = kChunk + 1;         // records staged per round: its events and the one after them
+constexpr int kRounds = 2;                 // rounds in flight (a power of two)
 constexpr uint32_t kNoTime = 0xFFFFFFFFu;  // past every valid timestamp
 
-
-// Copy records [u, u + kChunk) of a gate (base rec_g, n records) into this
-// thread's staging column; those at or past n are zero-filled without
-// reading.  One commit group.
-__device__ __forceinline__ void stage_chunk(const uint2* __restrict__ rec_g, uint32_t u, uint32_t n, uint2* col) {
+// Copy records [u, u + kStage) of a gate (base rec_g, n records) into one
+// staging slot of this thread's column (stride kWalkThreads); records at or
+// past n are zero-filled without reading.  One commit group.
+__device__ __forceinline__ void stage_round(const uint2* __restrict__ rec_g, uint32_t u, uint32_t n, uint2* slot) {
 #pragma unroll
-  for (int k = 0; k < kChunk; ++k) {
+  for (int k = 0; k < kStage; ++k) {
     const bool v = u + k < n;
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_addr(col + k * kWalkThreads)),
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_addr(slot + k * kWalkThreads)),
                  "l"(v ? rec_g + u + k : rec_g), "r"(v ? 8 : 0)
                  : "memory");
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// Per-thread sums, FP32 over a few chunks, then folded into FP64.
+// Per-thread sums, FP32 over a few rounds, then folded into FP64.
 struct Sums {
   float f0 = 0.f, f1 = 0.f, f2 = 0.f;
   double d0 = 0.0, d1 = 0.0, d2 = 0.0;
@@ -606,25 +817,24 @@ __device__ __forceinline__ int bad_event_code(uint32_t t, uint32_t m, uint32_t T
   return order_bad ? GTP_EORDER : GTP_ENOTOGGLE;
 }
 
-// Per-thread walk of a gate's events from local index u0 while their time is
-// below t_stop (n = the gate's event count, rec_g its first record), for the
-// sparse gates (one gate per thread).  `tabl` is this thread's column of the
-// CTA's staged gate tables (stride kWalkThreads), `col` its staging column
-// (2 x kChunk records, stride kWalkThreads), `sleak` the CTA's leakage table
-// (forward: scaled).  Forward: each distinct bin of consecutive events gets
-// one reduction {energy, leakage step} into L2 (TILE: into a shared-memory
-// tile instead, local bin = bin - bin_lo).
 struct WalkOut {
   double v0, v1, v2;  // forward: leakage (nW*ps), internal, switching; adjoint: dC, d_escale, d_lscale * 1e6
-  uint32_t end;       // local index of the first event not walked
 };
 
-template <bool BWD, bool TILE>
-__device__ __forceinline__ WalkOut walk_events(const LibView& L, const NetView& N, const WinDesc& W,
-                                               const float* tabl, uint2* col, const float* sleak, DevError* err,
-                                               int64_t g, const uint2* __restrict__ rec_g, uint32_t u0, uint32_t n,
-                                               uint32_t t_stop, uint32_t st, uint32_t tp, float2* sbin,
-                                               uint32_t bin_lo) {
+// Walk of one sparse gate by one thread (Algorithm 1 in event order): n > 0
+// events from rec_g, initial state st.  `tabl` is this thread's column of the
+// CTA's staged gate tables (stride kWalkThreads), `col` its staging column
+// (kRounds slots of kStage records, stride kWalkThreads), `sleak` the CTA's
+// leakage table (forward: scaled).  The records are staged kRounds rounds
+// ahead, each round with the record after it so that the last event of a
+// round sees the next timestamp without another load.  Forward: each distinct
+// bin of consecutive events gets one reduction {energy, leakage step} into L2.
+template <bool BWD>
+__device__ __forceinline__ WalkOut walk_gate(const LibView& L, const NetView& N, const WinDesc& W, const float* tabl,
+                                             uint2* col, const float* sleak, DevError* err, int64_t g,
+                                             const uint2* __restrict__ rec_g, uint32_t n, uint32_t st) {
+#pragma unroll
+  for (int r = 0; r < kRounds; ++r) stage_round(rec_g, (uint32_t)(r * kChunk), n, col + r * kStage * kWalkThreads);
   const uint32_t cell = (uint32_t)N.cell[g];
   const CellInfo ci = L.cells[cell];
   const uint32_t n_in = (uint32_t)ci.n_in;
@@ -641,49 +851,38 @@ __device__ __forceinline__ WalkOut walk_events(const LibView& L, const NetView& 
   float Pg = Pcur;        // leakage before the current group
   uint32_t spre = st;     // state before the current group
   Sums acc;
-  float Gcur = 0.f;
-  if (BWD && tp > 0u && tp < T) {
-    const uint32_t bb = bin_of(tp, magic, shift, bin_ps);
-    const float2 gv = W.grad[bb];
-    Gcur = gv.y + gv.x * (float)(tp - bb * bin_ps);
-  }
+  float Gcur = 0.f;       // adjoint: G at the last group (G(0) = 0)
+  uint32_t tp = 0u;
   uint32_t pb = kNoTime;
   float pe = 0.f, pdp = 0.f;
   bool live = true, bad = false, first = true;
-  uint32_t u = u0;  // first event of the current chunk
-  uint32_t end = n;
-  stage_chunk(rec_g, u, n, col);
-  stage_chunk(rec_g, u + kChunk, n, col + kChunk * kWalkThreads);
-  uint32_t ta_cur = u + kChunk < n ? __ldg(&rec_g[u + kChunk].x) : kNoTime;  // event after each staged chunk
-  uint32_t ta_nxt = u + 2 * kChunk < n ? __ldg(&rec_g[u + 2 * kChunk].x) : kNoTime;
-  int b = 0, n_chunks = 0;
+  uint32_t u = 0u;  // first event of the current round
+  int slot = 0, n_done = 0;
   while (live) {
-    asm volatile("cp.async.wait_group 1;" ::: "memory");
-    const uint2* buf = col + b * kChunk * kWalkThreads;
-    uint32_t rt[kChunk], rm[kChunk];
+    asm volatile("cp.async.wait_group %0;" ::"n"(kRounds - 1) : "memory");
+    uint2* buf = col + slot * kStage * kWalkThreads;
+    uint32_t rt[kStage], rm[kChunk];
 #pragma unroll
-    for (int k = 0; k < kChunk; ++k) {
+    for (int k = 0; k < kStage; ++k) {
       const uint2 r = buf[k * kWalkThreads];
       rt[k] = u + k < n ? r.x : kNoTime;
-      rm[k] = r.y;
+      if (k < kChunk) rm[k] = r.y;
     }
 #pragma unroll
     for (int k = 0; k < kChunk; ++k) {
       if (!live) continue;
-      const uint32_t t = rt[k], m = rm[k];
-      if (t >= t_stop) {  // the tile's (or, at kNoTime, the gate's) end
+      if (u + k >= n) {  // the gate's end
         live = false;
-        end = u + k;
         continue;
       }
-      const uint32_t t_next = k + 1 < kChunk ? rt[k + 1] : ta_cur;
+      const uint32_t t = rt[k], m = rm[k];
+      const uint32_t t_next = rt[k + 1];
       const uint32_t pin = m & 0xFu, val = (m >> 4) & 1u;
       const bool order_bad = (int32_t)t < (int32_t)tp;
       if (t >= T || (m & ~0x10u) > n_in || order_bad || ((st >> pin) & 1u) == val) {
         report_error(err, bad_event_code(t, m, T, n_in, order_bad), (rec_g - W.rec) + u + k);
         live = false;
         bad = true;
-        end = u + k;
         continue;
       }
       const bool head = first || t != tp;
@@ -734,14 +933,7 @@ __device__ __forceinline__ WalkOut walk_events(const LibView& L, const NetView& 
         const float dp = tail ? Pn - Pg : 0.f;
         const float add = dp * (float)(int32_t)((bn + 1u) * bin_ps - t) * 1e-6f;
         if (bn != pb) {
-          if (pb != kNoTime) {
-            if (TILE) {
-              atomicAdd(&sbin[pb - bin_lo].x, pe);
-              atomicAdd(&sbin[pb - bin_lo].y, pdp);
-            } else {
-              red_bin(W.bins, pb, pe, pdp);
-            }
-          }
+          if (pb != kNoTime) red_bin(W.bins, pb, pe, pdp);
           pb = bn;
           pe = 0.f;
           pdp = 0.f;
@@ -753,28 +945,19 @@ __device__ __forceinline__ WalkOut walk_events(const LibView& L, const NetView& 
       tp = t;
     }
     if (!live) break;
-    // refill the chunk just walked with the one two chunks ahead
-    stage_chunk(rec_g, u + 2 * kChunk, n, col + b * kChunk * kWalkThreads);
-    ta_cur = ta_nxt;
-    ta_nxt = u + 3 * kChunk < n ? __ldg(&rec_g[u + 3 * kChunk].x) : kNoTime;
+    // refill the slot just walked with the round kRounds ahead
+    stage_round(rec_g, u + kRounds * kChunk, n, buf);
     u += kChunk;
-    b ^= 1;
-    if (++n_chunks == 16) {
+    slot = (slot + 1) & (kRounds - 1);
+    if (++n_done == 16) {
       acc.fold();
-      n_chunks = 0;
+      n_done = 0;
     }
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");
-  if (!BWD && pb != kNoTime) {
-    if (TILE) {
-      atomicAdd(&sbin[pb - bin_lo].x, pe);
-      atomicAdd(&sbin[pb - bin_lo].y, pdp);
-    } else {
-      red_bin(W.bins, pb, pe, pdp);
-    }
-  }
+  if (!BWD && pb != kNoTime) red_bin(W.bins, pb, pe, pdp);
   // the gate's end: leakage to the window end, and the final state
-  if (!bad && end == n) {
+  if (!bad) {
     if (BWD) {
       acc.f2 += Pcur * (W.g_total - Gcur);
     } else {
@@ -783,7 +966,7 @@ __device__ __forceinline__ WalkOut walk_events(const LibView& L, const NetView& 
     }
   }
   acc.fold();
-  return WalkOut{acc.d0, acc.d1, acc.d2, end};
+  return WalkOut{acc.d0, acc.d1, acc.d2};
 }
 
 // This thread's gate table into its column of the CTA's staged tables.
@@ -802,16 +985,16 @@ __device__ __forceinline__ void stage_gate_table(const float* __restrict__ gt, i
 }
 
 // Shared memory of a walk CTA: a union of the dense items' per-warp areas
-// (staged records, energy table, leakage row) and the sparse items' area
+// (staged records and their neighbours, energy table, leakage row) and the sparse items' area
 // (per-thread gate tables, per-thread staged records, the leakage table),
 // then, for the adjoint, the per-warp cell sums.
 __host__ __device__ inline size_t dense_area(int K, bool bwd) {
   return (size_t)kWarps * (2 * 32 * K * sizeof(uint2) + (bwd ? 2 : 1) * kTabEntries * sizeof(float) +
-                           kLeakEntries * sizeof(float));
+                           kLeakEntries * sizeof(float) + 4 * sizeof(uint2));
 }
 __host__ __device__ inline size_t sparse_area(int n_leak, bool bwd) {
   return (size_t)(bwd ? 2 : 1) * kGateTab * kWalkThreads * sizeof(float) +
-         (size_t)2 * kChunk * kWalkThreads * sizeof(uint2) + (((size_t)n_leak * sizeof(float) + 15) & ~(size_t)15);
+         (size_t)kRounds * kStage * kWalkThreads * sizeof(uint2) + (((size_t)n_leak * sizeof(float) + 15) & ~(size_t)15);
 }
 __host__ __device__ inline size_t union_area(int K, int n_leak, bool bwd) {
   const size_t d = dense_area(K, bwd), sp = sparse_area(n_leak, bwd);
@@ -820,9 +1003,11 @@ __host__ __device__ inline size_t union_area(int K, int n_leak, bool bwd) {
 
 // Persistent CTAs of 8 warps take work items from the shared counter: one big
 // gate per item (all 8 warps), 8 medium gates per item (one per warp), then
-// 256 sparse gates per item (one per thread).
+// 256 sparse gates per item (one per thread).  The forward walk fits three
+// CTAs per SM (80 registers); the adjoint's larger tables allow two, so it
+// is given the registers of two.
 template <int K, bool BWD>
-__global__ void __launch_bounds__(kWalkThreads, 3) k_walk(LibView L, NetView N, WalkArgs A) {
+__global__ void __launch_bounds__(kWalkThreads, BWD ? 2 : 3) k_walk(LibView L, NetView N, WalkArgs A) {
   constexpr int SEG = 32 * K;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t xfer[2][kWarps];
@@ -843,10 +1028,12 @@ __global__ void __launch_bounds__(kWalkThreads, 3) k_walk(LibView L, NetView N, 
   sm.dtab = reinterpret_cast<float*>(sp) + (size_t)wib * kTabEntries;
   if (BWD) sp += (size_t)kWarps * kTabEntries * sizeof(float);
   sm.leak = reinterpret_cast<float*>(sp) + (size_t)wib * kLeakEntries;
+  sp += (size_t)kWarps * kLeakEntries * sizeof(float);
+  sm.halo = reinterpret_cast<uint2*>(sp) + (size_t)wib * 4;
   // sparse view of the union area
   float* stab = reinterpret_cast<float*>(smem);
   uint2* sstg = reinterpret_cast<uint2*>(stab + (BWD ? 2 : 1) * kGateTab * kWalkThreads);
-  float* sleak = reinterpret_cast<float*>(sstg + 2 * kChunk * kWalkThreads);
+  float* sleak = reinterpret_cast<float*>(sstg + kRounds * kStage * kWalkThreads);
   // adjoint cell sums, after the union
   sm.wacc = reinterpret_cast<double*>(smem + union_area(K, L.n_leak, BWD)) + (size_t)wib * 2 * L.n_cells;
   if (BWD)
@@ -895,9 +1082,8 @@ __global__ void __launch_bounds__(kWalkThreads, 3) k_walk(LibView L, NetView N, 
         const int64_t ga = W.offsets[g], ge = W.offsets[g + 1];
         float* my_tab = stab + threadIdx.x;
         if (L.cells[N.cell[g]].n_in <= kGateTabMaxIn) stage_gate_table<BWD>(gt, g, my_tab);
-        const WalkOut o = walk_events<BWD, false>(L, N, W, my_tab, sstg + threadIdx.x, sleak, err, g, W.rec + ga, 0u,
-                                                  (uint32_t)(ge - ga), kNoTime, (uint32_t)W.init[g], 0u, nullptr,
-                                                  0u);
+        const WalkOut o = walk_gate<BWD>(L, N, W, my_tab, sstg + threadIdx.x, sleak, err, g, W.rec + ga,
+                                         (uint32_t)(ge - ga), (uint32_t)W.init[g]);
         if (BWD) {
           W.dC[g] = (float)o.v0;
           const uint32_t cell = (uint32_t)N.cell[g];
@@ -939,27 +1125,50 @@ cudaError_t launch_walk_k(const LibView& L, const NetView& N, const WalkArgs& A,
 
 bool walk_rpt_supported(int rpt) { return rpt == 4 || rpt == 8 || rpt == 16; }
 
-int plan_counter_slots(int dense_min) { return 4 + 2 * n_buckets(dense_min); }
+int plan_counter_slots(int dense_min) { return kCntHist + 2 * n_buckets(dense_min); }
 
-cudaError_t launch_plan(const NetView& N, const LibView& L, const WalkArgs& A, cudaStream_t st) {
-  const int64_t seg_len = 32ll * A.rpt;
-  const int dmin = A.dense_min;
-  cudaError_t e = cudaMemsetAsync(A.plan.counters, 0, sizeof(unsigned long long) * plan_counter_slots(dmin), st);
-  if (e != cudaSuccess) return e;
+namespace {
+
+dim3 prepare_grid(const WalkArgs& A) {
   int64_t blocks = (A.n_gates + 255) / 256;
   if (blocks > 1024) blocks = 1024;
   if (blocks < 1) blocks = 1;
-  const dim3 grid((unsigned)blocks, (unsigned)A.n_win);
-  const size_t nb = (size_t)n_buckets(dmin);
-  k_plan_classify<<<grid, 256, sizeof(unsigned int) * nb, st>>>(A.wins, A.n_gates, seg_len, dmin, A.plan);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_plan_scan<<<1, 32, 0, st>>>(dmin, A.plan);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const size_t scatter_smem = nb * (sizeof(unsigned long long) + sizeof(unsigned int));
-  e = cudaFuncSetAttribute(k_plan_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scatter_smem);
+  return dim3((unsigned)blocks, (unsigned)A.n_win);
+}
+
+template <bool GATE>
+cudaError_t launch_prepare_plan(const LibView& L, const NetView& N, const WalkArgs& A, cudaStream_t st) {
+  const int dmin = A.dense_min;
+  cudaError_t e = cudaMemsetAsync(A.plan.counters, 0, sizeof(unsigned long long) * plan_counter_slots(dmin), st);
   if (e != cudaSuccess) return e;
-  k_plan_scatter<<<grid, 256, scatter_smem, st>>>(A.wins, A.n_gates, seg_len, dmin, A.plan);
+  k_prepare<GATE, true><<<prepare_grid(A), 256, sizeof(unsigned int) * (size_t)n_buckets(dmin), st>>>(
+      L, N, A.wins, A.err, 32ll * A.rpt, dmin, A.plan);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_prepare(const LibView& L, const NetView& N, const WalkArgs& A, bool plan, cudaStream_t st) {
+  if (plan) return launch_prepare_plan<true>(L, N, A, st);
+  k_prepare<true, false><<<prepare_grid(A), 256, 0, st>>>(L, N, A.wins, A.err, 32ll * A.rpt, A.dense_min, A.plan);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plan_scatter(const NetView& N, const WalkArgs& A, cudaStream_t st) {
+  (void)N;
+  const int dmin = A.dense_min;
+  const size_t nb = (size_t)n_buckets(dmin);
+  const size_t scatter_smem = nb * (sizeof(unsigned long long) + sizeof(unsigned int));
+  cudaError_t e = cudaFuncSetAttribute(k_plan_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scatter_smem);
+  if (e != cudaSuccess) return e;
+  k_plan_scatter<<<prepare_grid(A), 256, scatter_smem, st>>>(A.wins, A.n_gates, 32ll * A.rpt, dmin, A.plan);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plan(const NetView& N, const LibView& L, const WalkArgs& A, cudaStream_t st) {
+  cudaError_t e = launch_prepare_plan<false>(L, N, A, st);
+  if (e != cudaSuccess) return e;
+  return launch_plan_scatter(N, A, st);
 }
 
 cudaError_t launch_walk(const LibView& L, const NetView& N, const WalkArgs& A, bool backward, cudaStream_t st) {

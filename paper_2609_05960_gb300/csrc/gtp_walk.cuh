@@ -25,9 +25,10 @@ struct PlanBufs {
   int64_t gcap;                 // capacity of glist (windows x gates)
 };
 
-// counters[0] = big gates, [1] = medium gates, [2] = sparse gates, [3] = dense
-// work items handed out so far (the walk's work counter), then the work-list
-// histogram and its bucket cursors.
+// counters[0] = big gates, [1] = medium gates, [2] = sparse gates, [3] = work
+// items handed out so far (the walk's work counter), [4] = blocks of the
+// preparation pass that finished, then the work-list histogram and its bucket
+// cursors.
 int plan_counter_slots(int dense_min);
 
 struct WalkArgs {
@@ -46,8 +47,16 @@ struct WalkArgs {
 };
 
 bool walk_rpt_supported(int rpt);
-// Classify gates and build the work list: big gates (largest first), medium
-// gates, sparse gates (no host synchronisation).
+// Forward preparation in one launch over (window, gate): clear the windows'
+// bins, the gate pass (L0 into each window's l0; results of gates without
+// events), and with `plan` the work-list histogram and bucket starts.
+cudaError_t launch_prepare(const LibView& L, const NetView& N, const WalkArgs& A, bool plan, cudaStream_t st);
+// Scatter of the (window, gate) pairs with events into the work list: big
+// gates (largest first), medium gates, sparse gates.  Follows launch_prepare
+// with plan, or launch_plan's histogram.
+cudaError_t launch_plan_scatter(const NetView& N, const WalkArgs& A, cudaStream_t st);
+// The whole work list without the gate pass (the adjoint): histogram, bucket
+// starts and scatter (no host synchronisation).
 cudaError_t launch_plan(const NetView& N, const LibView& L, const WalkArgs& A, cudaStream_t st);
 cudaError_t launch_walk(const LibView& L, const NetView& N, const WalkArgs& A, bool backward, cudaStream_t st);
 cudaError_t launch_gate_tables(const LibView& L, const NetView& N, float* gtab, float* gtab_bwd, cudaStream_t st);

@@ -167,9 +167,9 @@ def gtp_load_events(ctx, window: int, window_ps: int, gate_offsets, events, init
     _check(ctx, load().gtp_load_events(ctx, int(window), int(window_ps), n_events, po, pe, pi, flags))
 
 
-def gtp_run_power(ctx, window: int, bin_ps: int, waveform=None) -> None:
+def gtp_run_power(ctx, window: int, bin_ps: int, waveform=None, graph: bool = False) -> None:
     p, f, k = _ptr_flags(waveform, np.float64)
-    _check(ctx, load().gtp_run_power(ctx, int(window), int(bin_ps), p, f))
+    _check(ctx, load().gtp_run_power(ctx, int(window), int(bin_ps), p, f | (GTP_GRAPH if graph else 0)))
 
 
 def gtp_gate_energy(ctx, window: int, e_leak=None, e_int=None, e_sw=None, n_events=None, final_state=None) -> None:
@@ -293,13 +293,14 @@ class Engine:
         gtp_load_events(self.ctx, window, window_ps, offsets, records, init_state, borrow=borrow)
         self.windows[window] = dict(window_ps=int(window_ps))
 
-    def run_power(self, window: int, bin_ps: int, out=None):
-        """Waveform in W as a float64 CUDA tensor of window_ps / bin_ps bins."""
+    def run_power(self, window: int, bin_ps: int, out=None, graph: bool = False):
+        """Waveform in W as a float64 CUDA tensor of window_ps / bin_ps bins
+        (graph: capture the run in a CUDA graph once and replay it)."""
         import torch
         nb = self.windows[window]["window_ps"] // bin_ps
         if out is None:
             out = torch.empty(nb, dtype=torch.float64, device=self.device)
-        gtp_run_power(self.ctx, window, bin_ps, out)
+        gtp_run_power(self.ctx, window, bin_ps, out, graph=graph)
         return out
 
     def gate_energy(self, window: int, device: bool = True):

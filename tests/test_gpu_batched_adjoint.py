@@ -184,3 +184,35 @@ def test_autotune_picks_a_valid_plan(engine):
     w = engine.run_power(0, 100).cpu().numpy()
     ref = oracle.waveform_w(oracle.walk(lib, net, tr, 100)["bins"], 100)
     assert (np.abs(w - ref) / ref).max() <= TOL
+
+
+def test_single_window_graph_follows_reloads_and_times_phases(engine):
+    """A captured single-window run is replayed only while the launch sizes
+    it holds still apply: reloading the window with another length or with no
+    events gives a new graph, and every run matches the oracle.  Phase timing
+    recorded inside the graph accumulates once per replay."""
+    lib = synth.make_library(1)
+    net = synth.make_netlist(lib, 300, seed=12)
+    engine.load_library(lib)
+    engine.load_netlist(net)
+    _reset(engine)
+    specs = [(2500, 30_000), (2500, 30_000), (7000, 50_000), (400, 0), (7000, 20_000)]
+    for i, (n_bins, n_ev) in enumerate(specs):
+        counts = synth.zipf_counts(net.n_gates, n_ev, 1.2, None, 300 + i) if n_ev else np.zeros(net.n_gates, np.int64)
+        tr = synth.make_trace(net, counts, n_bins * 20, 300 + i, tie_p=0.05)
+        engine.load_events(0, tr)
+        ref = oracle.waveform_w(oracle.walk(lib, net, tr, 20)["bins"], 20)
+        for _ in range(2):
+            got = engine.run_power(0, 20, graph=True).cpu().numpy()
+            assert got.shape == ref.shape
+            assert (np.abs(got - ref) / ref).max() <= TOL, (i, n_bins, n_ev)
+    engine.set_param("timing", 1)
+    for _ in range(3):
+        engine.run_power(0, 20, graph=True)
+    assert engine.get_param("n_timed") == 3
+    assert engine.get_param("t_walk_ns") > 0 and engine.get_param("t_merge_ns") > 0
+    engine.set_param("timing", 1)  # and on the stream, without a graph
+    got = engine.run_power(0, 20).cpu().numpy()
+    assert (np.abs(got - ref) / ref).max() <= TOL
+    assert engine.get_param("n_timed") == 1 and engine.get_param("t_walk_ns") > 0
+    engine.set_param("timing", 0)
