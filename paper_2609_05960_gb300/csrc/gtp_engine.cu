@@ -104,6 +104,7 @@ struct gtp_ctx {
   int64_t plan_gen = 0;  // bumped whenever a plan buffer moves (captured graphs hold its pointers)
   DevBuf cell_acc, grad, gtiles, dC_scratch;
   DevBuf d_err;
+  DevBuf first_bad;  // trace check result (see launch_validate)
   DevError* h_err = nullptr;
   std::map<GraphKey, cudaGraphExec_t> graphs;
   cudaStream_t capture_stream = nullptr;
@@ -199,6 +200,36 @@ int check_device_error(gtp_ctx* ctx, const char* what) {
     return fail(ctx, ctx->h_err->code, buf);
   }
   return GTP_OK;
+}
+
+// Status of a walk over the n_win planned windows (window slots ids[]).  The
+// walk flags a malformed trace without classifying it exactly; the exact
+// first bad record (smallest window, then record) is found by the trace
+// check before the error is reported, so the code and index match the
+// oracle's and do not depend on thread timing.
+int check_walk_error(gtp_ctx* ctx, int n_win, const int32_t* ids, const char* what) {
+  CU(cudaMemcpyAsync(ctx->h_err, ctx->d_err.p, sizeof(DevError), cudaMemcpyDeviceToHost, ctx->stream), "read status");
+  CU(cudaStreamSynchronize(ctx->stream), what);
+  if (ctx->h_err->code == 0) return GTP_OK;
+  if (ctx->h_err->index < 0 || n_win <= 0) return check_device_error(ctx, what);
+  CU(ctx->first_bad.reserve(sizeof(unsigned long long)), "alloc trace check");
+  CU(launch_validate(ctx->L, ctx->N, plan_wins(ctx->plan.p), n_win, ctx->first_bad.as<unsigned long long>(),
+                     ctx->stream), "trace check");
+  unsigned long long key = ~0ull;
+  CU(cudaMemcpyAsync(&key, ctx->first_bad.p, sizeof key, cudaMemcpyDeviceToHost, ctx->stream), "read trace check");
+  CU(cudaStreamSynchronize(ctx->stream), what);
+  if (key == ~0ull) return check_device_error(ctx, what);
+  const int code = -(int)(key & 7ull);
+  const long long rec = (long long)((key >> 3) & ((1ull << 40) - 1ull));
+  const int w = (int)(key >> 43);
+  char buf[256];
+  if (n_win > 1)
+    snprintf(buf, sizeof buf, "%s: %s at record %lld of window %d", what, code_name(code), rec, ids[w]);
+  else
+    snprintf(buf, sizeof buf, "%s: %s at record %lld", what, code_name(code), rec);
+  ctx->h_err->code = code;
+  ctx->h_err->index = rec;
+  return fail(ctx, code, buf);
 }
 
 Window* get_window(gtp_ctx* ctx, int32_t w) {
@@ -479,7 +510,7 @@ int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, dou
         CU(cudaMemcpyAsync(waveforms[i], waves[i], sizeof(double) * (size_t)(ws[i]->window_ps / bin_ps),
                            cudaMemcpyDeviceToHost, ctx->stream), "copy waveform");
   }
-  const int rc = check_device_error(ctx, "run_power");
+  const int rc = check_walk_error(ctx, n, windows, "run_power");
   collect_timing(ctx);
   for (Window* w : ws) {
     w->has_result = (rc == GTP_OK);
@@ -529,7 +560,7 @@ void gtp_destroy(gtp_ctx* ctx) {
   for (auto& kv : ctx->windows) kv.second.release();
   for (DevBuf* b : {&ctx->tab, &ctx->leak, &ctx->cells, &ctx->table_cell, &ctx->leak_cell, &ctx->escale, &ctx->lscale,
                     &ctx->cell, &ctx->load, &ctx->slew, &ctx->desc, &ctx->plan, &ctx->glist, &ctx->gtab, &ctx->gtab_bwd,
-                    &ctx->counters,
+                    &ctx->counters, &ctx->first_bad,
                     &ctx->cell_acc, &ctx->grad, &ctx->gtiles, &ctx->dC_scratch, &ctx->d_err})
     b->release();
   if (ctx->h_err) cudaFreeHost(ctx->h_err);
@@ -838,7 +869,7 @@ int gtp_run_power_backward(gtp_ctx* ctx, int32_t window, int32_t bin_ps, const f
     CU(launch_cells_out(ctx->cell_acc.as<double>(), ctx->L.n_cells, d_escale, d_lscale, st), "cell gradients");
     ctx->launches += 1;
   }
-  return check_device_error(ctx, "run_power_backward");
+  return check_walk_error(ctx, W->n_events > 0 ? 1 : 0, &window, "run_power_backward");
 }
 
 int gtp_autotune(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_t bin_ps, int32_t iters,

@@ -198,6 +198,10 @@ cudaError_t launch_merge(const WinDesc* wins, const int64_t* tile_base, int n_wi
 cudaError_t launch_grad_prep(const WinDesc* wins, const float* dLdP, float2* grad, double* tiles, int n_tiles,
                              int n_bins, int bin_ps, float* g_total, cudaStream_t st);
 cudaError_t launch_cells_out(const double* acc, int n_cells, float* d_escale, float* d_lscale, cudaStream_t st);
+// Exact first malformed record of the given windows (see k_validate): *first
+// = ((window << 40 | record) << 3) | -code, or ~0 if every record is valid.
+cudaError_t launch_validate(const LibView& L, const NetView& N, const WinDesc* wins, int n_win,
+                            unsigned long long* first, cudaStream_t st);
 int merge_tiles(int n_bins);
 
 }  // namespace gtp

@@ -441,6 +441,55 @@ __global__ void k_cells_out(const double* __restrict__ acc, int n_cells, float* 
 
 }  // namespace
 
+// ------------------------------------------------------------------ exact trace check
+// Run after a walk flagged a malformed trace.  Per (window, gate), the
+// events in record order against the input rules of Algorithm 1, in the
+// order the oracle applies them: the time in [0, T), not below the previous
+// event's, no reserved meta bits and a pin of the cell, and an event that
+// toggles its pin.  The smallest failing (window, record) wins, so the
+// reported error does not depend on the order in which threads ran:
+// key = ((window << 40 | record) << 3) | -code.
+__global__ void k_validate(LibView L, NetView N, const WinDesc* __restrict__ wins, unsigned long long* first) {
+  const WinDesc& W = wins[blockIdx.y];
+  const int32_t T = W.window_ps;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N.n_gates;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = W.offsets[g], b = W.offsets[g + 1];
+    if (a == b) continue;
+    const uint32_t n_pins = (uint32_t)L.cells[N.cell[g]].n_in + 1u;
+    uint32_t S = (uint32_t)W.init[g] & ((1u << n_pins) - 1u);
+    int32_t tp = 0;
+    for (int64_t i = a; i < b; ++i) {
+      const uint2 r = W.rec[i];
+      const int32_t t = (int32_t)r.x;
+      const uint32_t pin = r.y & 0xFu, val = (r.y >> 4) & 1u;
+      int code = 0;
+      if (t < 0 || t >= T) code = GTP_ERANGE;
+      else if (t < tp) code = GTP_EORDER;
+      else if ((r.y >> 5) != 0u || pin >= n_pins) code = GTP_ERANGE;
+      else if (((S >> pin) & 1u) == val) code = GTP_ENOTOGGLE;
+      if (code != 0) {
+        const unsigned long long key =
+            ((((unsigned long long)blockIdx.y << 40) | (unsigned long long)i) << 3) | (unsigned long long)(-code);
+        atomicMin(first, key);
+        break;
+      }
+      S ^= 1u << pin;
+      tp = t;
+    }
+  }
+}
+
+cudaError_t launch_validate(const LibView& L, const NetView& N, const WinDesc* wins, int n_win,
+                            unsigned long long* first, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(first, 0xFF, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  int64_t blocks = (N.n_gates + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  k_validate<<<dim3((unsigned)(blocks < 1 ? 1 : blocks), (unsigned)n_win), 256, 0, st>>>(L, N, wins, first);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cells_out(const double* acc, int n_cells, float* d_escale, float* d_lscale, cudaStream_t st) {
   k_cells_out<<<(n_cells + 255) / 256, 256, 0, st>>>(acc, n_cells, d_escale, d_lscale);
   return cudaGetLastError();

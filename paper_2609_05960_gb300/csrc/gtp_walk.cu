@@ -248,7 +248,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 constexpr uint32_t kXH = 1u << 16;
 constexpr uint32_t kXAbs = 1u << 17;
 constexpr int kTabMaxIn = 4;                                     // wider cells interpolate per event
-constexpr int kTabEntries = 32 << kTabMaxIn;  // energies by (record meta bits 0-4, input state)
+constexpr int kTabEntries = (kTabMaxIn + 1) << (kTabMaxIn + 1);  // energies by (pin, edge, input state)
 constexpr int kLeakEntries = 2 << kTabMaxIn;
 
 __device__ __forceinline__ uint32_t xcompose(uint32_t a, uint32_t b) {
@@ -281,7 +281,7 @@ __device__ __forceinline__ int stage_pos(int row, int k) {
 // Per-warp shared memory of the dense walk.
 struct DenseSmem {
   uint2* rec;      // [2][32 * K] staged records (double buffer)
-  float* etab;     // [kTabEntries] energy at ((val << 4 | pin) << n_in) | input state; adjoint: unscaled
+  float* etab;     // [kTabEntries] energy at ((pin * 2 + val) << n_in) | input state; adjoint: unscaled
   float* dtab;     // adjoint: [kTabEntries] escale * dE/dC
   float* leak;     // [kLeakEntries] leakage per state (forward: scaled)
   uint2* halo;     // [2][2] per staging buffer: the records just before and just after the segment
@@ -347,10 +347,8 @@ __device__ __forceinline__ void build_tables(const LibView& L, const DGate& d, c
       E = BWD ? 0.f : __uint_as_float(q.w);
       dE = L.half_v2;
     }
-    // indexed by the record's low meta bits (pin, value after the edge) and the input state
-    const uint32_t at = ((((pv & 1u) << 4) | pin) << d.n_in) | s;
-    sm.etab[at] = E;
-    if (BWD) sm.dtab[at] = dE;
+    sm.etab[e] = E;
+    if (BWD) sm.dtab[e] = dE;
   }
   for (int s = lane; s < (int)(2u << d.n_in); s += 32) sm.leak[s] = __ldg(d.gleak + s) * d.lsc;
 }
@@ -398,7 +396,7 @@ struct Seg {
   uint32_t t_before;         // time of the event before the lane's first (0 at the gate start)
   uint32_t t_after;          // time of the event after the lane's last (~0 at the gate end)
   bool fh, last_seg;         // the lane's first event starts the gate; the segment ends it
-  bool bad;                  // one of the lane's records may fail a check (seg_check_bits decides)
+  bool bad;                  // one of the lane's records fails a check (located by the host's trace check)
   uint32_t ex;               // transfer of the segment's events before this lane
 };
 
@@ -464,40 +462,6 @@ __device__ __forceinline__ uint32_t seg_front(const DGate& d, int64_t s, const u
   return __shfl_sync(kFull, w, 31);
 }
 
-// The per-record check bits of a lane whose screen failed: bit k of bad_r
-// for a record outside the window or with a bad pin or reserved bit, of
-// bad_o for a time below its predecessor's (signed, as the walk compares).
-template <int K>
-__device__ __noinline__ void seg_check_bits(const DGate& d, const uint2* buf, const Seg& q, int lane, uint32_t& bad_r,
-                                            uint32_t& bad_o) {
-  const uint32_t rb = row_base<K>(lane);
-  uint32_t tp = q.t_before;
-  bad_r = 0u;
-  bad_o = 0u;
-  for (int k = 0; k < q.nk; ++k) {
-    const uint2 r = buf[rb ^ (uint32_t)k];
-    const uint32_t t = r.x, m = r.y;
-    bad_r |= (uint32_t)(t >= d.T || (m & ~0x10u) > d.n_in) << k;
-    bad_o |= (uint32_t)((int32_t)t < (int32_t)tp && !(k == 0 && q.fh)) << k;
-    tp = t;
-  }
-}
-
-// First record of the lane whose event does not toggle its pin, replaying
-// the lane's states from st (-1 if none).
-template <int K>
-__device__ __noinline__ int seg_first_no_toggle(const DGate& d, const uint2* buf, const Seg& q, int lane,
-                                                uint32_t st) {
-  const uint32_t rb = row_base<K>(lane);
-  for (int k = 0; k < q.nk; ++k) {
-    const uint32_t m = buf[rb ^ (uint32_t)k].y;
-    const uint32_t pin = m & 0xFu, val = (m >> 4) & 1u;
-    if (((st >> pin) & 1u) == val) return k;
-    st = (st ^ (1u << pin)) & d.pmask;
-  }
-  return -1;
-}
-
 // Fire-and-forget {energy, leakage step} reduction into bin b when p holds
 // (predicated, no branch).
 __device__ __forceinline__ void red_bin_if(bool p, float2* bins, uint32_t b, float e, float dp) {
@@ -530,15 +494,12 @@ __device__ __forceinline__ SegSums seg_back(const LibView& L, const DGate& d, co
                                             const Seg& q, uint32_t seg_in, DevError* err, int lane) {
   SegSums out{0.f, 0.f, 0.f};
   if (!FULL && q.n_rem == 0) return out;
+  // A record out of range or out of order: flag the trace (the host then
+  // locates the first bad record exactly) and skip the replay, whose bins
+  // and table entries would not be safe to index.
   if (__any_sync(kFull, q.bad)) {
-    uint32_t bad_r = 0u, bad_o = 0u;
-    if (q.bad) seg_check_bits<K>(d, buf, q, lane, bad_r, bad_o);
-    const uint32_t bb = bad_r | bad_o;
-    if (bb) {
-      const int k = __ffs(bb) - 1;
-      report_error(err, ((bad_r >> k) & 1u) ? GTP_ERANGE : GTP_EORDER, q.s0 + lane * K + k);
-    }
-    if (__any_sync(kFull, bad_r != 0u)) return out;  // an event outside the window: skip the replay
+    if (q.bad) report_error(err, GTP_ERANGE, q.s0 + lane * K);
+    return out;
   }
   const uint32_t li = xcompose(seg_in, q.ex);
   uint32_t st = li & d.pmask;            // state before the lane's first event
@@ -587,7 +548,7 @@ __device__ __forceinline__ SegSums seg_back(const LibView& L, const DGate& d, co
     const bool is_out = pin >= d.n_in;
     float E, dE = 0.f;
     if (TAB) {
-      const uint32_t idx = ((m & 0x1Fu) << d.n_in) | (spre & d.inmask);
+      const uint32_t idx = ((pin * 2u + val) << d.n_in) | (spre & d.inmask);
       E = sm.etab[idx];
       if (BWD) dE = sm.dtab[idx];
     } else {
@@ -633,10 +594,7 @@ __device__ __forceinline__ SegSums seg_back(const LibView& L, const DGate& d, co
     event(k, t, m, (k + 1 < K && (FULL || k + 1 < q.nk)) ? r.x : q.t_after);
   }
   if (!BWD && (FULL || q.nk > 0)) red_bin(d.W->bins, pb, pe, pdp);
-  if (!(tog & 1u)) {
-    const int k = seg_first_no_toggle<K>(d, buf, q, lane, li & d.pmask);
-    report_error(err, GTP_ENOTOGGLE, q.s0 + lane * K + (k < 0 ? 0 : k));
-  }
+  if (!(tog & 1u)) report_error(err, GTP_ENOTOGGLE, q.s0 + lane * K);  // located exactly by the host
   // gate end: leakage to the window end and the final state
   if (q.last_seg && q.nk > 0 && lane * K + q.nk == q.n_rem) {
     if (BWD) {

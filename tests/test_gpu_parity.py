@@ -201,6 +201,55 @@ def test_malformed_traces_are_rejected(engine, params, events, code):
     assert eo.value.code == code
 
 
+def _toggling_events(n, n_pins, seed, t0=100, step=7):
+    """n valid events (each toggles its pin) with increasing times."""
+    rng = np.random.default_rng(seed)
+    S, ev, t = 0, [], t0
+    for _ in range(n):
+        pin = int(rng.integers(0, n_pins))
+        v = 1 - ((S >> pin) & 1)
+        S ^= 1 << pin
+        ev.append((t, pin, v))
+        t += int(rng.integers(0, step))  # ties allowed
+    return ev
+
+
+@pytest.mark.parametrize("params", KERNELS, ids=KID)
+@pytest.mark.parametrize("kind,code", [("order", -2), ("time", -3), ("pin", -3), ("toggle", -4)])
+@pytest.mark.parametrize("pos", [0, 131, 2200])
+def test_malformed_dense_gate_reports_first_bad_record(engine, params, kind, code, pos):
+    """A 3000-event gate (big or medium, depending on the segment length)
+    with one bad record, and a later bad record in another gate: the error is
+    the first bad record, with the oracle's code, whichever kernel ran."""
+    from paper_2609_05960_gb300 import GtpError
+    lib = single_cell_library(2, lambda *a: 1.0, lambda s: 1.0 + s)
+    net = netlist_from(lib, [0, 0, 0], [1.0, 1.0, 1.0])
+    T = 40_000
+    g0 = _toggling_events(40, 3, 1)
+    g1 = _toggling_events(3000, 3, 2)
+    g2 = _toggling_events(50, 3, 3)
+    t, pin, v = g1[pos]
+    if kind == "order":
+        g1[pos] = (g1[pos - 1][0] - 1 if pos else -1, pin, v)
+        if pos == 0:
+            code = -3  # a negative time is out of range before it is out of order
+    elif kind == "time":
+        g1[pos] = (T + 5, pin, v)
+    elif kind == "pin":
+        g1[pos] = (t, 3, v)
+    else:
+        g1[pos] = (t, pin, 1 - v)
+    g2[10] = (g2[10][0], 3, 0)  # a later pin error in another gate
+    tr = trace_from([g0, g1, g2], [0, 0, 0], T)
+    with pytest.raises(GtpError) as ei:
+        run(engine, lib, net, tr, 100, params)
+    assert ei.value.code == code
+    assert f"at record {40 + pos}" in str(ei.value)
+    with pytest.raises(oracle.OracleError) as eo:
+        oracle.walk(lib, net, tr, 100)
+    assert eo.value.code == code and eo.value.record == 40 + pos
+
+
 def test_bad_bin_size_rejected(engine):
     from paper_2609_05960_gb300 import GtpError
     lib, net, tr = small_random(n_gates=5, n_events=100, window_ps=1000, seed=2)
