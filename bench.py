@@ -55,6 +55,9 @@ def parse():
     p.add_argument("--events", type=int, default=0,
                    help="scale the configuration to this many events (same gates and distribution; "
                         "for profiling a smaller case)")
+    p.add_argument("--sweep", default="", choices=["", "contention"],
+                   help="contention: uniform high activity (1, 2, 4, 8 events per gate per 1k bins) "
+                        "instead of the default run; one JSON line per density")
     return p.parse_args()
 
 
@@ -469,8 +472,62 @@ def measure_adjoint(eng, dev, steps):
             "loss": "sum P^2 + tau*logsumexp(P/tau), P in mW, tau = 0.01*mean(P)"}
 
 
+def run_contention_sweep(args):
+    """Bin-update contention: every gate equally active, 1, 2, 4 and 8 events
+    per gate per 1k bins, over 250k gates and 1M bins of 10 ps (up to 2B
+    events, 2,000 events per bin).  Each density runs with the autotuned
+    plan; one JSON line each, timed like the main bench (CUDA events around
+    graph-replayed gtp_run_power calls, phase timing for the walk)."""
+    import torch
+
+    import synth
+    from paper_2609_05960_gb300 import Engine, gtpower
+
+    dev = torch.device("cuda", 0)
+    G, window_ps, bin_ps = 250_000, 10_000_000, 10
+    n_bins = window_ps // bin_ps
+    lib = synth.make_library(1)
+    net = synth.make_netlist(lib, G, 2)
+    eng = Engine(0)
+    eng.load_library(lib)
+    eng.load_netlist(net)
+    wave = torch.empty(n_bins, dtype=torch.float64, device=dev)
+    for k in (1, 2, 4, 8):
+        counts = np.full(G, k * n_bins // 1000, np.int64)
+        tr, rec = synth.make_trace_gpu(net, counts, window_ps, 40 + k, device=dev)
+        off = torch.from_numpy(tr.offsets).to(dev)
+        init = torch.from_numpy(tr.init_state).to(dev)
+        eng.load_events(0, window_ps=window_ps, offsets=off, records=rec, init_state=init, borrow=True)
+        for key in ("records_per_thread", "ctas_per_sm", "dense_min"):
+            eng.set_param(key, -1)
+        best = gtpower.gtp_autotune(eng.ctx, [0], bin_ps, 3)
+        run = lambda: gtpower.gtp_run_power(eng.ctx, 0, bin_ps, wave, graph=True)
+        for _ in range(max(args.warmup, 3)):
+            run()
+        torch.cuda.synchronize(dev)
+        eng.set_param("timing", 1)
+        steps = max(3, min(args.steps, 20))
+        ms = _events_per_s(run, steps, dev)
+        n_t = max(eng.get_param("n_timed"), 1)
+        walk_ms = eng.get_param("t_walk_ns") * 1e-6 / n_t
+        eng.set_param("timing", 0)
+        n = int(tr.n_events)
+        print(json.dumps({
+            "sweep": "contention", "events_per_gate_per_1k_bins": k, "gates": G, "bins": n_bins,
+            "events": n, "events_per_bin": n / n_bins, "ms_per_run": ms, "value": n / (ms * 1e-3), "unit": UNIT,
+            "walk_ms": walk_ms, "walk_events_per_s": n / (walk_ms * 1e-3),
+            "autotuned_plan": {key: eng.get_param(key) for key in ("records_per_thread", "dense_min")},
+            "autotune_best_ms": best, "data": "synthetic"}), flush=True)
+        del rec, off, init
+        torch.cuda.empty_cache()
+    eng.close()
+
+
 def main():
     args = parse()
+    if args.sweep == "contention":
+        run_contention_sweep(args)
+        return
     if args.impl == "reference":
         run_reference(args, args.config)
     else:
