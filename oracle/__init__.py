@@ -51,6 +51,10 @@ class _Net(ctypes.Structure):
                 ("slew_ps", ctypes.c_void_p), ("slew_stride", ctypes.c_int32)]
 
 
+class _Glitch(ctypes.Structure):
+    _fields_ = [("clock_ps", ctypes.c_int64), ("out_slew_ps", ctypes.c_void_p)]
+
+
 class _Trace(ctypes.Structure):
     _fields_ = [("window_ps", ctypes.c_int64), ("offsets", ctypes.c_void_p), ("records", ctypes.c_void_p),
                 ("init_state", ctypes.c_void_p)]
@@ -67,9 +71,9 @@ def _lib():
         P = ctypes.c_void_p
         lib.oracle_walk.restype = ctypes.c_int
         lib.oracle_walk.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int64, P, P, ctypes.c_int64, P,
-                                    P, P, P, P, P, P]
+                                    P, P, P, P, P, P, P, P]
         lib.oracle_adjoint.restype = ctypes.c_int
-        lib.oracle_adjoint.argtypes = [P, P, P, ctypes.c_int64, P, ctypes.c_int64, P, P, P, P]
+        lib.oracle_adjoint.argtypes = [P, P, P, ctypes.c_int64, P, ctypes.c_int64, P, P, P, P, P]
         lib.oracle_bilinear.restype = ctypes.c_double
         lib.oracle_bilinear.argtypes = [ctypes.c_int32, P, ctypes.c_int32, P, P, ctypes.c_double,
                                         ctypes.c_double]
@@ -111,14 +115,27 @@ def _structs(lib, net, trace, escale, lscale, load_ff):
     return L, N, T, keep
 
 
+def _glitch(glitch, keep):
+    """(clock_ps, out_slew[n_gates][2] {fall, rise} ps) -> _Glitch, or None."""
+    if glitch is None:
+        return None
+    clock_ps, out_slew = glitch
+    a = _c(out_slew, np.float32)
+    keep.append(a)
+    return _Glitch(int(clock_ps), a.ctypes.data)
+
+
 def walk(lib, net, trace, bin_ps: int, escale=None, lscale=None, load_ff=None, gates=None,
-         sample_bins=None, waveform: bool = True):
+         sample_bins=None, waveform: bool = True, glitch=None):
     """Run the FP64 walk.  Returns a dict with ``bins`` (fJ per bin; the
     sampled bins only if ``sample_bins`` is given), ``e_leak``, ``e_int``,
-    ``e_sw`` (fJ per gate), ``n_events`` and ``final_state``.  With ``gates``
-    the per-gate outputs follow that order (and ``bins`` only receive those
-    gates' contributions)."""
+    ``e_sw``, ``e_gl`` (fJ per gate), ``n_events`` and ``final_state``.  With
+    ``gates`` the per-gate outputs follow that order (and ``bins`` only
+    receive those gates' contributions).  ``glitch`` = (clock_ps, out_slew
+    [n_gates][2] {fall, rise} ps) turns on glitch detection; e_gl is 0
+    without it."""
     L, N, T, keep = _structs(lib, net, trace, escale, lscale, load_ff)
+    GL = _glitch(glitch, keep)
     n_bins = int(trace.window_ps) // int(bin_ps) if bin_ps > 0 else 0
     if gates is not None:
         gates = _c(gates, np.int64)
@@ -133,7 +150,7 @@ def walk(lib, net, trace, bin_ps: int, escale=None, lscale=None, load_ff=None, g
         bins = np.zeros(len(sample_bins), np.float64)
     else:
         bins = np.zeros(max(n_bins, 0), np.float64)
-    out = {k: np.zeros(n_sel, np.float64) for k in ("e_leak", "e_int", "e_sw")}
+    out = {k: np.zeros(n_sel, np.float64) for k in ("e_leak", "e_int", "e_sw", "e_gl")}
     out["n_events"] = np.zeros(n_sel, np.int64)
     out["final_state"] = np.zeros(n_sel, np.uint8)
     bad = ctypes.c_int64(-1)
@@ -145,7 +162,8 @@ def walk(lib, net, trace, bin_ps: int, escale=None, lscale=None, load_ff=None, g
         len(sample_bins) if sample_bins is not None else 0,
         sample_bins.ctypes.data if sample_bins is not None else nullp,
         out["e_leak"].ctypes.data, out["e_int"].ctypes.data, out["e_sw"].ctypes.data,
-        out["n_events"].ctypes.data, out["final_state"].ctypes.data, ctypes.byref(bad))
+        out["n_events"].ctypes.data, out["final_state"].ctypes.data, ctypes.byref(bad),
+        ctypes.byref(GL) if GL is not None else nullp, out["e_gl"].ctypes.data)
     del keep
     if rc == EINVAL:
         raise ValueError("invalid bin size / window")
@@ -155,12 +173,13 @@ def walk(lib, net, trace, bin_ps: int, escale=None, lscale=None, load_ff=None, g
     return out
 
 
-def adjoint(lib, net, trace, bin_ps: int, dLdP, escale=None, lscale=None, load_ff=None, gates=None):
+def adjoint(lib, net, trace, bin_ps: int, dLdP, escale=None, lscale=None, load_ff=None, gates=None, glitch=None):
     """FP64 gradient of L(P) given dL/dP per bin (P in W); returns
     (dC, d_escale[n_cells], d_lscale[n_cells]).  With ``gates`` only those
     gates are walked (dC follows their order; the cell gradients then hold
-    only their contributions)."""
+    only their contributions).  ``glitch`` as for walk()."""
     L, N, T, keep = _structs(lib, net, trace, escale, lscale, load_ff)
+    GL = _glitch(glitch, keep)
     g = _c(dLdP, np.float64)
     if gates is not None:
         gates = _c(gates, np.int64)
@@ -170,7 +189,8 @@ def adjoint(lib, net, trace, bin_ps: int, dLdP, escale=None, lscale=None, load_f
     dl = np.zeros(len(lib.n_in), np.float64)
     rc = _lib().oracle_adjoint(ctypes.byref(L), ctypes.byref(N), ctypes.byref(T), int(bin_ps), g.ctypes.data,
                                n_sel, gates.ctypes.data if gates is not None else None,
-                               dC.ctypes.data, de.ctypes.data, dl.ctypes.data)
+                               dC.ctypes.data, de.ctypes.data, dl.ctypes.data,
+                               ctypes.byref(GL) if GL is not None else None)
     del keep
     if rc != OK:
         raise ValueError(f"oracle_adjoint failed: {rc}")

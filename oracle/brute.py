@@ -9,6 +9,10 @@ update, as in Algorithm 1's timestamp loop), and charges one picosecond of
 leakage at the state holding during that picosecond.  Table interpolation is
 delegated to ``scipy.interpolate.RegularGridInterpolator`` (linear, with
 linear extrapolation outside the axes), not to the oracle's own routine.
+Glitch detection, when asked for, follows the paper's counting formulation
+(Sec. 2.4.1, Algorithm 1): per pin, a counter of events in the current clock
+cycle, reset when a new cycle starts; an event that brings its pin's counter
+above one is a glitch, scaled by Eq. (glitch scaling ratio).
 
 Only for windows of a few thousand ps and a handful of gates.
 """
@@ -40,8 +44,10 @@ def _tables(lib):
     return tabs, leaks
 
 
-def simulate(lib, net, trace, bin_ps: int, escale=None, lscale=None, load_ff=None):
-    """Returns dict(bins[fJ], e_leak, e_int, e_sw, n_events, final_state)."""
+def simulate(lib, net, trace, bin_ps: int, escale=None, lscale=None, load_ff=None, glitch=None):
+    """Returns dict(bins[fJ], e_leak, e_int, e_sw, e_gl, n_events,
+    final_state).  glitch = (clock_ps, out_slew[n_gates][2] {fall, rise})."""
+    clock, out_slew = glitch if glitch is not None else (0, None)
     T = int(trace.window_ps)
     n_bins = T // bin_ps
     n_gates = len(net.cell)
@@ -52,7 +58,7 @@ def simulate(lib, net, trace, bin_ps: int, escale=None, lscale=None, load_ff=Non
     tabs, leaks = _tables(lib)
     vdd = float(lib.vdd)
     bins = np.zeros(n_bins)
-    out = dict(e_leak=np.zeros(n_gates), e_int=np.zeros(n_gates), e_sw=np.zeros(n_gates),
+    out = dict(e_leak=np.zeros(n_gates), e_int=np.zeros(n_gates), e_sw=np.zeros(n_gates), e_gl=np.zeros(n_gates),
                n_events=np.zeros(n_gates, np.int64), final_state=np.zeros(n_gates, np.uint8))
     for g in range(n_gates):
         c = int(net.cell[g])
@@ -66,16 +72,36 @@ def simulate(lib, net, trace, bin_ps: int, escale=None, lscale=None, load_ff=Non
             t = int(np.int32(trace.records[k, 0]))
             meta = int(trace.records[k, 1])
             at.setdefault(t, []).append((meta & 0xF, (meta >> 4) & 1))
+        count = [0] * n_pins   # events of each pin in the current clock cycle
+        last = [0] * n_pins    # each pin's previous event time
+        cycle = -1
         for tau in range(T):
+            if clock and tau // clock != cycle:
+                cycle = tau // clock
+                count = [0] * n_pins
             for pin, value in at.get(tau, []):
                 if pin < n_in:
                     others = [bits[p] for p in range(n_in) if p != pin]
                     side = sum(v << k for k, v in enumerate(others))
                     slew = float(net.slew_ps[g, pin, value])
                     E = escale[c] * float(tabs[(c, pin, value, side)]([[slew, C]])[0])
-                    out["e_int"][g] += E
+                    rise_fall = float(net.slew_ps[g, pin, 0]) + float(net.slew_ps[g, pin, 1])
                 else:
                     E = 0.5 * C * vdd * vdd
+                    rise_fall = float(out_slew[g][0]) + float(out_slew[g][1]) if clock else 0.0
+                is_glitch = False
+                if clock:
+                    count[pin] += 1
+                    if count[pin] > 1:
+                        width = tau - last[pin]
+                        E *= 1.0 if rise_fall <= 0 else min(1.0, (2.0 * width / rise_fall) ** 2)
+                        is_glitch = True
+                    last[pin] = tau
+                if is_glitch:
+                    out["e_gl"][g] += E
+                elif pin < n_in:
+                    out["e_int"][g] += E
+                else:
                     out["e_sw"][g] += E
                 bins[tau // bin_ps] += E
             for pin, value in at.get(tau, []):

@@ -24,11 +24,22 @@
  *     is split over the time bins it overlaps in proportion to the overlap
  *     [Sec. 2.4.2, waveform accumulation].
  *   * Dynamic energy goes to the bin containing the event time.
+ *   * Glitches (optional, with a clock period T_clk): an event on a pin that
+ *     already had an event earlier in the same clock cycle floor(t / T_clk)
+ *     is a glitch event [Sec. 2.4.1, clock-cycle glitch detection;
+ *     Algorithm 1, GlitchDetectUpdate].  Its dynamic energy is scaled by
+ *     r_gl = min(1, (2 * pulse_width / (rSlew + fSlew))^2) [Eq. glitch
+ *     scaling ratio], with pulse_width the time since that pin's previous
+ *     event and rSlew, fSlew the pin's rise and fall transition times; the
+ *     scaled energy is glitch energy (not internal or switching energy) and
+ *     goes to the event's bin.
  * Units: ps, fF, V, fJ, nW.  E[fJ] = P[nW] * dt[ps] * 1e-6; 0.5*C[fF]*V^2 = fJ.
  *
  * Parity status: the walk and the adjoint are pinned by closed forms, a
  * per-picosecond brute-force simulator, library interpolation and invariants
- * (tests/test_oracle_*.py).
+ * (tests/test_oracle_*.py); glitch detection by a hand-worked trace, closed
+ * forms, the brute-force simulator's per-cycle pin counters and central
+ * differences (tests/test_oracle_glitch.py).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -61,6 +72,11 @@ typedef struct {
   const float* slew_ps;     /* [n_gates][slew_stride][2] */
   int32_t slew_stride;
 } oracle_net;
+
+typedef struct {
+  int64_t clock_ps;         /* > 0: clock period for glitch detection */
+  const float* out_slew_ps; /* [n_gates][2] output-pin {fall, rise} transition times */
+} oracle_glitch;
 
 typedef struct {
   int64_t window_ps;
@@ -193,11 +209,21 @@ static void bin_add_interval(const binner* B, double P, int64_t a, int64_t b) {
  * On a malformed trace returns a negative code and the offending record
  * index in *bad_record.
  */
+/* Glitch scaling ratio of an event pulse_width ps after the previous event on
+ * its pin, for rise + fall transition time sum_slew ps [Eq. glitch scaling
+ * ratio]; a pin without transition time (sum <= 0) swings fully: ratio 1. */
+static double glitch_ratio(double pulse_width, double sum_slew) {
+  if (sum_slew <= 0.0) return 1.0;
+  double x = 2.0 * pulse_width / sum_slew;
+  double r = x * x;
+  return r < 1.0 ? r : 1.0;
+}
+
 int oracle_walk(const oracle_lib* L, const oracle_net* N, const oracle_trace* T, int64_t bin_ps,
                 int64_t n_sel, const int64_t* gates,
                 double* bins, int64_t n_sample, const int64_t* sample,
                 double* e_leak, double* e_int, double* e_sw, int64_t* n_events, uint8_t* final_state,
-                int64_t* bad_record) {
+                int64_t* bad_record, const oracle_glitch* GL, double* e_gl) {
   if (bin_ps <= 0 || T->window_ps <= 0 || T->window_ps % bin_ps != 0) return OR_EINVAL;
   int64_t* tab_base = (int64_t*)malloc(sizeof(int64_t) * (size_t)L->n_cells);
   int64_t* leak_base = (int64_t*)malloc(sizeof(int64_t) * (size_t)L->n_cells);
@@ -216,7 +242,9 @@ int oracle_walk(const oracle_lib* L, const oracle_net* N, const oracle_trace* T,
     const float* leak = L->p_leak + leak_base[c];
     uint32_t S = T->init_state[g];
     int64_t t_prev = 0;
-    double El = 0.0, Ei = 0.0, Es = 0.0;
+    double El = 0.0, Ei = 0.0, Es = 0.0, Eg = 0.0;
+    int64_t last_t[16];  /* each pin's previous event time, -1 before its first */
+    for (int p = 0; p < 16; ++p) last_t[p] = -1;
     int64_t a = T->offsets[g], b = T->offsets[g + 1];
     int64_t i = a;
     while (i < b) {
@@ -238,16 +266,25 @@ int oracle_walk(const oracle_lib* L, const oracle_net* N, const oracle_trace* T,
         if ((meta >> 5) != 0 || pin >= n_pins) { rc = OR_ERANGE; *bad_record = e; break; }
         if ((int32_t)((S_next >> pin) & 1u) == value) { rc = OR_ENOTOGGLE; *bad_record = e; break; }
         S_next ^= 1u << pin;
-        double E;
+        double E, sum_slew;
         if (pin < n_in) {
           const float* tab = table_for(L, tab_base, c, pin, value, side_bits(S, pin, n_in));
-          double slew = N->slew_ps[((int64_t)g * N->slew_stride + pin) * 2 + value];
-          E = es * oracle_bilinear(L->n_slew, L->slew_axis, L->n_load, L->load_axis, tab, slew, C);
-          Ei += E;
+          const float* sl = N->slew_ps + ((int64_t)g * N->slew_stride + pin) * 2;
+          E = es * oracle_bilinear(L->n_slew, L->slew_axis, L->n_load, L->load_axis, tab, sl[value], C);
+          sum_slew = (double)sl[0] + (double)sl[1];
         } else {
           E = half_v2 * C;
+          sum_slew = GL ? (double)GL->out_slew_ps[2 * g] + (double)GL->out_slew_ps[2 * g + 1] : 0.0;
+        }
+        if (GL && GL->clock_ps > 0 && last_t[pin] >= 0 && last_t[pin] / GL->clock_ps == t / GL->clock_ps) {
+          E *= glitch_ratio((double)(t - last_t[pin]), sum_slew);
+          Eg += E;
+        } else if (pin < n_in) {
+          Ei += E;
+        } else {
           Es += E;
         }
+        last_t[pin] = t;
         bin_add(&B, t, E);
       }
       if (rc != OR_OK) break;
@@ -262,6 +299,7 @@ int oracle_walk(const oracle_lib* L, const oracle_net* N, const oracle_trace* T,
     if (e_leak) e_leak[gi] = El;
     if (e_int) e_int[gi] = Ei;
     if (e_sw) e_sw[gi] = Es;
+    if (e_gl) e_gl[gi] = Eg;
     if (n_events) n_events[gi] = b - a;
     if (final_state) final_state[gi] = (uint8_t)S;
   }
@@ -282,10 +320,12 @@ int oracle_walk(const oracle_lib* L, const oracle_net* N, const oracle_trace* T,
  *   dE_int/dC = escale * d(bilinear)/d(load)   (located load segment)
  *   dE_sw/dC  = 0.5 * Vdd^2
  *   dE_int/d escale = bilinear value;  leakage energy is linear in lscale.
+ * With glitch detection (GL), a glitch event's derivatives carry its ratio
+ * r_gl, which depends on times and transition times only.
  */
 int oracle_adjoint(const oracle_lib* L, const oracle_net* N, const oracle_trace* T, int64_t bin_ps,
                    const double* dLdP, int64_t n_sel, const int64_t* gates,
-                   double* dC, double* d_escale, double* d_lscale) {
+                   double* dC, double* d_escale, double* d_lscale, const oracle_glitch* GL) {
   if (bin_ps <= 0 || T->window_ps <= 0 || T->window_ps % bin_ps != 0) return OR_EINVAL;
   int64_t* tab_base = (int64_t*)malloc(sizeof(int64_t) * (size_t)L->n_cells);
   int64_t* leak_base = (int64_t*)malloc(sizeof(int64_t) * (size_t)L->n_cells);
@@ -304,6 +344,8 @@ int oracle_adjoint(const oracle_lib* L, const oracle_net* N, const oracle_trace*
     uint32_t S = T->init_state[g];
     int64_t t_prev = 0;
     double gC = 0.0;
+    int64_t last_t[16];
+    for (int p = 0; p < 16; ++p) last_t[p] = -1;
     int64_t a = T->offsets[g], b = T->offsets[g + 1];
     int64_t i = a;
     for (;;) {
@@ -328,15 +370,23 @@ int oracle_adjoint(const oracle_lib* L, const oracle_net* N, const oracle_trace*
         int32_t pin = (int32_t)(meta & 0xFu);
         int32_t value = (int32_t)((meta >> 4) & 1u);
         S_next ^= 1u << pin;
+        double r = 1.0;
+        if (GL && GL->clock_ps > 0 && last_t[pin] >= 0 && last_t[pin] / GL->clock_ps == t / GL->clock_ps) {
+          double sum_slew = pin < n_in ? (double)N->slew_ps[((int64_t)g * N->slew_stride + pin) * 2] +
+                                             (double)N->slew_ps[((int64_t)g * N->slew_stride + pin) * 2 + 1]
+                                       : (double)GL->out_slew_ps[2 * g] + (double)GL->out_slew_ps[2 * g + 1];
+          r = glitch_ratio((double)(t - last_t[pin]), sum_slew);
+        }
+        last_t[pin] = t;
         if (pin < n_in) {
           const float* tab = table_for(L, tab_base, c, pin, value, side_bits(S, pin, n_in));
           double slew = N->slew_ps[((int64_t)g * N->slew_stride + pin) * 2 + value];
           double B0 = oracle_bilinear(L->n_slew, L->slew_axis, L->n_load, L->load_axis, tab, slew, C);
           double dB = oracle_bilinear_dload(L->n_slew, L->slew_axis, L->n_load, L->load_axis, tab, slew, C);
-          gC += gb * es * dB;
-          d_escale[c] += gb * B0;
+          gC += gb * r * es * dB;
+          d_escale[c] += gb * r * B0;
         } else {
-          gC += gb * half_v2;
+          gC += gb * r * half_v2;
         }
       }
       S = S_next;
