@@ -140,6 +140,30 @@ int gtp_load_netlist(gtp_ctx* ctx, int64_t n_gates, const int32_t* cell, const f
 int gtp_set_load(gtp_ctx* ctx, const float* load_ff, int flags);
 
 /*
+ * Clock-cycle glitch detection [Sec. 2.4.1, Eq. glitch scaling ratio,
+ * Algorithm 1 GlitchDetectUpdate] for the following runs (forward, batched
+ * and adjoint).  With clock_ps > 0, an event on a pin that already had an
+ * event earlier in the same clock cycle floor(t / clock_ps) (t in window
+ * time, so windows start on cycle boundaries) is a glitch event: its dynamic
+ * energy is scaled by r = min(1, (2 w / (rise + fall))^2), w the time since
+ * that pin's previous event and rise, fall the pin's transition times (input
+ * pins: the netlist's slews; the output pin: out_slew_ps), and it counts as
+ * glitch energy (gtp_gate_glitch) instead of internal or switching energy.
+ * The waveform receives the scaled energy.  clock_ps = 0 turns detection off
+ * (the default; also after gtp_load_netlist).
+ *   out_slew_ps [n_gates][2] float {fall, rise} ps, copied; may be NULL when
+ *               clock_ps == 0.  flags: GTP_HOST or GTP_DEVICE.
+ * Errors: GTP_EINVAL without a netlist or with a NULL array, GTP_ERANGE for
+ * clock_ps outside [0, 2^31).  gtp_run_power_noalloc does not detect
+ * glitches.
+ */
+int gtp_set_glitch(gtp_ctx* ctx, int64_t clock_ps, const float* out_slew_ps, int flags);
+
+/* Per-gate glitch energy (fJ, FP64) of the last run of `window`: zeros if
+ * that run did not detect glitches.  flags: GTP_HOST or GTP_DEVICE. */
+int gtp_gate_glitch(gtp_ctx* ctx, int32_t window, double* e_gl, int flags);
+
+/*
  * Load one stimulus window's events as slot `window` (0 <= window < 1024;
  * reloading a slot replaces it).
  *   window_ps     length of the analysis window, > 0, < 2^31

@@ -47,12 +47,13 @@ struct Window {
   int64_t n_events = 0;
   DevBuf offsets, records, init;
   const uint2* borrowed = nullptr;
-  DevBuf e_leak, e_int, e_sw, final_state, bins, tiles, wave;
+  DevBuf e_leak, e_int, e_sw, e_gl, final_state, bins, tiles, wave;
   bool has_result = false;
+  bool glitch_result = false;  // the last run detected glitches (e_gl holds them)
   int32_t last_bin_ps = 0;
   const uint2* rec() const { return borrowed ? borrowed : records.as<uint2>(); }
   void release() {
-    for (DevBuf* b : {&offsets, &records, &init, &e_leak, &e_int, &e_sw, &final_state, &bins, &tiles, &wave})
+    for (DevBuf* b : {&offsets, &records, &init, &e_leak, &e_int, &e_sw, &e_gl, &final_state, &bins, &tiles, &wave})
       b->release();
     borrowed = nullptr;
     loaded = false;
@@ -105,6 +106,7 @@ struct gtp_ctx {
   DevBuf cell_acc, grad, gtiles, dC_scratch;
   DevBuf d_err;
   DevBuf first_bad;  // trace check result (see launch_validate)
+  DevBuf out_slew;   // glitch detection: [n_gates][2] output {fall, rise} transition times
   DevError* h_err = nullptr;
   std::map<GraphKey, cudaGraphExec_t> graphs;
   cudaStream_t capture_stream = nullptr;
@@ -262,6 +264,7 @@ int build_plan(gtp_ctx* ctx, const std::vector<Window*>& ws, int32_t bin_ps, con
     CU(W.e_leak.reserve(sizeof(double) * G), "alloc e_leak");
     CU(W.e_int.reserve(sizeof(double) * G), "alloc e_int");
     CU(W.e_sw.reserve(sizeof(double) * G), "alloc e_sw");
+    if (ctx->N.clock_ps > 0) CU(W.e_gl.reserve(sizeof(double) * G), "alloc e_gl");
     CU(W.final_state.reserve((size_t)G), "alloc final_state");
     CU(W.bins.reserve(sizeof(float2) * nb), "alloc bins");
     CU(W.tiles.reserve(sizeof(double) * (size_t)nt), "alloc tiles");
@@ -272,6 +275,7 @@ int build_plan(gtp_ctx* ctx, const std::vector<Window*>& ws, int32_t bin_ps, con
     d.e_leak = W.e_leak.as<double>();
     d.e_int = W.e_int.as<double>();
     d.e_sw = W.e_sw.as<double>();
+    d.e_gl = ctx->N.clock_ps > 0 ? W.e_gl.as<double>() : nullptr;
     d.final_state = W.final_state.as<uint8_t>();
     d.bins = W.bins.as<float2>();
     d.l0 = dl0 + i;
@@ -514,6 +518,7 @@ int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, dou
   collect_timing(ctx);
   for (Window* w : ws) {
     w->has_result = (rc == GTP_OK);
+    w->glitch_result = ctx->N.clock_ps > 0;
     w->last_bin_ps = bin_ps;
   }
   return rc;
@@ -560,7 +565,7 @@ void gtp_destroy(gtp_ctx* ctx) {
   for (auto& kv : ctx->windows) kv.second.release();
   for (DevBuf* b : {&ctx->tab, &ctx->leak, &ctx->cells, &ctx->table_cell, &ctx->leak_cell, &ctx->escale, &ctx->lscale,
                     &ctx->cell, &ctx->load, &ctx->slew, &ctx->desc, &ctx->plan, &ctx->glist, &ctx->gtab, &ctx->gtab_bwd,
-                    &ctx->counters, &ctx->first_bad,
+                    &ctx->counters, &ctx->first_bad, &ctx->out_slew,
                     &ctx->cell_acc, &ctx->grad, &ctx->gtiles, &ctx->dC_scratch, &ctx->d_err})
     b->release();
   if (ctx->h_err) cudaFreeHost(ctx->h_err);
@@ -710,11 +715,55 @@ int gtp_load_netlist(gtp_ctx* ctx, int64_t n_gates, const int32_t* cell, const f
   ctx->N.slew = ctx->slew.as<float>();
   ctx->N.n_gates = n_gates;
   ctx->N.stride = slew_stride;
+  ctx->N.clock_ps = 0;  // glitch detection is set per netlist
+  ctx->N.out_slew = nullptr;
   RC(ensure_netlist_coords(ctx));
   CU(cudaStreamSynchronize(ctx->stream), "load_netlist");
   ctx->net_loaded = true;
   for (auto& kv : ctx->windows) kv.second.release();
   ctx->windows.clear();
+  return GTP_OK;
+}
+
+int gtp_set_glitch(gtp_ctx* ctx, int64_t clock_ps, const float* out_slew_ps, int flags) {
+  if (!ctx) return GTP_EINVAL;
+  if (!ctx->net_loaded) return fail(ctx, GTP_EINVAL, "set_glitch: load the netlist first");
+  if (clock_ps < 0 || clock_ps >= (1ll << 31)) return fail(ctx, GTP_ERANGE, "set_glitch: clock_ps must be in [0, 2^31)");
+  if (clock_ps > 0 && !out_slew_ps) return fail(ctx, GTP_EINVAL, "set_glitch: out_slew_ps is null");
+  DeviceGuard dg(ctx->device);
+  CU(cudaStreamSynchronize(ctx->stream), "set_glitch");
+  drop_graphs(ctx);
+  if (clock_ps == 0) {
+    ctx->N.clock_ps = 0;
+    ctx->N.out_slew = nullptr;
+    return GTP_OK;
+  }
+  const int64_t G = ctx->N.n_gates;
+  CU(ctx->out_slew.reserve(sizeof(float) * 2 * (size_t)G), "alloc out_slew");
+  CU(cudaMemcpyAsync(ctx->out_slew.p, out_slew_ps, sizeof(float) * 2 * (size_t)G, kind_in(flags), ctx->stream),
+     "copy out_slew");
+  CU(cudaStreamSynchronize(ctx->stream), "set_glitch");
+  ctx->N.out_slew = ctx->out_slew.as<float>();
+  ctx->N.clock_ps = (int32_t)clock_ps;
+  bin_magic((int32_t)clock_ps, &ctx->N.clock_magic, &ctx->N.clock_shift);
+  return GTP_OK;
+}
+
+int gtp_gate_glitch(gtp_ctx* ctx, int32_t window, double* e_gl, int flags) {
+  if (!ctx) return GTP_EINVAL;
+  Window* W = get_window(ctx, window);
+  if (!W || !W->has_result) return fail(ctx, GTP_EINVAL, "gate_glitch: no result for this window");
+  if (!e_gl) return fail(ctx, GTP_EINVAL, "gate_glitch: null output");
+  DeviceGuard dg(ctx->device);
+  const size_t bytes = sizeof(double) * (size_t)ctx->N.n_gates;
+  if (W->glitch_result) {
+    CU(cudaMemcpyAsync(e_gl, W->e_gl.p, bytes, kind_out(flags), ctx->stream), "copy e_gl");
+  } else if (flags & GTP_DEVICE) {
+    CU(cudaMemsetAsync(e_gl, 0, bytes, ctx->stream), "zero e_gl");
+  } else {
+    memset(e_gl, 0, bytes);
+  }
+  CU(cudaStreamSynchronize(ctx->stream), "gate_glitch");
   return GTP_OK;
 }
 

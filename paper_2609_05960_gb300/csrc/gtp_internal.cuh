@@ -67,6 +67,12 @@ struct NetView {
   int64_t n_gates;
   int32_t stride;            // slew stride (input pins per gate)
   int32_t dstride;           // descriptors per gate = 2 * (stride + 1)
+  // glitch detection (Sec. 2.4.1): clock period in ps (0: off), its
+  // division constants (see bin_of), and the output pins' {fall, rise}
+  // transition times [G][2]
+  int32_t clock_ps;
+  uint32_t clock_magic, clock_shift;
+  const float* out_slew;
 };
 
 // First failure seen by a kernel: code and record index.
@@ -85,6 +91,7 @@ struct WinDesc {
   double* e_leak;            // [G]
   double* e_int;             // [G]
   double* e_sw;              // [G]
+  double* e_gl;              // [G] glitch energy, or null without glitch detection
   uint8_t* final_state;      // [G]
   float2* bins;              // [n_bins] accumulators
   double* l0;                // sum over gates of P_leak(initial state), nW
@@ -123,6 +130,21 @@ __device__ __forceinline__ uint32_t side_bits(uint32_t S, uint32_t pin, uint32_t
 __device__ __forceinline__ uint32_t bin_of(uint32_t t, uint32_t magic, uint32_t shift, uint32_t bin_ps) {
   uint32_t b = __umulhi(t, magic) >> shift;
   return b + (((b + 1u) * bin_ps <= t) ? 1u : 0u);
+}
+
+// Glitch scaling ratio (Eq. glitch scaling ratio) of an event `width` ps
+// after the previous event on its pin, for the pin's rise + fall transition
+// time sum: min(1, (2 * width / sum)^2); a pin without transition time
+// (sum <= 0) swings fully.
+__device__ __forceinline__ float glitch_ratio(uint32_t width, float sum) {
+  if (!(sum > 0.f)) return 1.f;
+  const float x = 2.f * (float)width / sum;
+  return fminf(1.f, x * x);
+}
+
+// Start of the clock cycle holding t (glitch detection).
+__device__ __forceinline__ uint32_t cycle_start(uint32_t t, int32_t clock_ps, uint32_t magic, uint32_t shift) {
+  return bin_of(t, magic, shift, (uint32_t)clock_ps) * (uint32_t)clock_ps;
 }
 
 // Fire-and-forget vector add of {energy, leakage step} into one bin.

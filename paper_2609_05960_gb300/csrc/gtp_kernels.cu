@@ -176,7 +176,8 @@ cudaError_t launch_gate_pass_bwd(const LibView& L, const NetView& N, const WinDe
 // The plain walk of Algorithm 1, one (window, gate) per thread: timestamp
 // groups with lookups at the pre-group state, the state update after the
 // group, leakage held between groups.  Kahan-compensated FP32 per-gate sums.
-// A simple cross-check of the segmented walk; it is not tuned.
+// With a clock, glitch detection as in the fused walk.  A simple
+// cross-check of the segmented walk; it is not tuned.
 __global__ void k_walk_per_gate(LibView L, NetView N, const WinDesc* __restrict__ wins, DevError* err) {
   extern __shared__ __align__(16) unsigned char smem[];
   const SmemLib sl = stage_library(L, smem, true);
@@ -193,7 +194,9 @@ __global__ void k_walk_per_gate(LibView L, NetView N, const WinDesc* __restrict_
     uint32_t st = W.init[g] & ((2u << n_in) - 1u);
     float P = leak[st];
     int32_t t_prev = 0;
-    Kahan El, Ei, Es;
+    Kahan El, Ei, Es, Eg;
+    uint32_t last[8];  // glitch detection: each pin's previous event time
+    for (int p = 0; p < 8; ++p) last[p] = 0xFFFFFFFFu;
     bool bad = false;
     int64_t i = a;
     while (i < b) {
@@ -221,11 +224,22 @@ __global__ void k_walk_per_gate(LibView L, NetView N, const WinDesc* __restrict_
           const float lo = fmaf(fl, p[1] - p[0], p[0]);
           const float hi = fmaf(fl, p[L.nl + 1] - p[L.nl], p[L.nl]);
           E = fmaf(__uint_as_float(d.x), hi - lo, lo);
-          Ei.add(E);
         } else {
           E = __uint_as_float(d.w);
-          Es.add(E);
         }
+        bool glitch = false;
+        if (N.clock_ps > 0) {  // Sec. 2.4.1: an earlier event on this pin in the same clock cycle
+          const uint32_t tp = last[pin];
+          last[pin] = (uint32_t)t;
+          if (tp != 0xFFFFFFFFu && tp >= cycle_start((uint32_t)t, N.clock_ps, N.clock_magic, N.clock_shift)) {
+            const float* sw = pin < n_in ? N.slew + ((size_t)g * N.stride + pin) * 2 : N.out_slew + 2 * g;
+            E *= glitch_ratio((uint32_t)t - tp, sw[0] + sw[1]);
+            glitch = true;
+          }
+        }
+        if (glitch) Eg.add(E);
+        else if (pin < n_in) Ei.add(E);
+        else Es.add(E);
         e_bin += E;
       }
       if (bad) break;
@@ -243,6 +257,7 @@ __global__ void k_walk_per_gate(LibView L, NetView N, const WinDesc* __restrict_
     W.e_leak[g] = El.value();
     W.e_int[g] = Ei.value();
     W.e_sw[g] = Es.value();
+    if (W.e_gl) W.e_gl[g] = Eg.value();
     W.final_state[g] = (uint8_t)st;
   }
 }

@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(256) k_prepare(LibView L, NetView N, const Win
         W.e_leak[g] = c == 0 ? (double)Pl * (double)W.window_ps * 1e-6 : 0.0;
         W.e_int[g] = 0.0;
         W.e_sw[g] = 0.0;
+        if (W.e_gl) W.e_gl[g] = 0.0;
         W.final_state[g] = (uint8_t)s0;
       }
     }
@@ -239,18 +240,8 @@ cudaError_t launch_plan(const NetView& N, const LibView& L, const WalkArgs& A, c
 }
 
 cudaError_t launch_walk(const LibView& L, const NetView& N, const WalkArgs& A, bool backward, cudaStream_t st) {
-  if (backward) {
-    switch (A.rpt) {
-      case 4: return launch_walk_k<4, true>(L, N, A, st);
-      case 16: return launch_walk_k<16, true>(L, N, A, st);
-      default: return launch_walk_k<8, true>(L, N, A, st);
-    }
-  }
-  switch (A.rpt) {
-    case 4: return launch_walk_k<4, false>(L, N, A, st);
-    case 16: return launch_walk_k<16, false>(L, N, A, st);
-    default: return launch_walk_k<8, false>(L, N, A, st);
-  }
+  if (N.clock_ps > 0) return launch_walk_glitch(L, N, A, backward, st);
+  return launch_walk_gl<false>(L, N, A, backward, st);
 }
 
 }  // namespace gtp

@@ -59,6 +59,8 @@ cudaError_t launch_plan_scatter(const NetView& N, const WalkArgs& A, cudaStream_
 // starts and scatter (no host synchronisation).
 cudaError_t launch_plan(const NetView& N, const LibView& L, const WalkArgs& A, cudaStream_t st);
 cudaError_t launch_walk(const LibView& L, const NetView& N, const WalkArgs& A, bool backward, cudaStream_t st);
+// The walk with glitch detection (N.clock_ps > 0), in its own translation unit.
+cudaError_t launch_walk_glitch(const LibView& L, const NetView& N, const WalkArgs& A, bool backward, cudaStream_t st);
 cudaError_t launch_gate_tables(const LibView& L, const NetView& N, float* gtab, float* gtab_bwd, cudaStream_t st);
 
 }  // namespace gtp

@@ -108,6 +108,7 @@ struct DenseSmem {
   float* dtab;     // adjoint: [kTabEntries] escale * dE/dC
   float* leak;     // [kLeakEntries] leakage per state (forward: scaled)
   uint2* halo;     // [2][2] per staging buffer: the records just before and just after the segment
+  float* gsum;     // glitch detection: [8] rise + fall transition time of each pin
   double* wacc;    // adjoint: [2 * n_cells] per-warp cell sums
 };
 
@@ -121,9 +122,15 @@ struct DGate {
   uint32_t cell, n_in, pmask, inmask, init;
   float esc, lsc;            // energy scale; leakage scale (1 in the adjoint)
   uint32_t T, bin_ps, magic, shift;
+  // glitch detection: clock and its division constants, the gate's input
+  // slews [stride][2] and output {fall, rise} transition times
+  int32_t clk;
+  uint32_t cmagic, cshift;
+  const float* islew;
+  const float* oslew;
 };
 
-template <bool BWD>
+template <bool BWD, bool GL>
 __device__ __forceinline__ DGate dense_gate(const LibView& L, const NetView& N, const WinDesc* __restrict__ wins,
                                             int2 wg) {
   DGate d;
@@ -146,12 +153,26 @@ __device__ __forceinline__ DGate dense_gate(const LibView& L, const NetView& N, 
   d.bin_ps = (uint32_t)d.W->bin_ps;
   d.magic = d.W->bin_magic;
   d.shift = d.W->bin_shift;
+  if (GL) {
+    d.clk = N.clock_ps;
+    d.cmagic = N.clock_magic;
+    d.cshift = N.clock_shift;
+    d.islew = N.slew + (size_t)d.g * N.stride * 2;
+    d.oslew = N.out_slew + 2 * d.g;
+  }
   return d;
 }
 
-// The gate's energy table and leakage row in the warp's shared memory.
-template <bool BWD>
+// The gate's energy table and leakage row in the warp's shared memory (TAB:
+// cells of at most kTabMaxIn inputs) and, for glitch detection, each pin's
+// rise + fall transition time (any cell: at most 8 pins).
+template <bool BWD, bool TAB, bool GL>
 __device__ __forceinline__ void build_tables(const LibView& L, const DGate& d, const DenseSmem& sm, int lane) {
+  if (GL && lane <= (int)d.n_in) {
+    const float* sl = lane < (int)d.n_in ? d.islew + 2 * lane : d.oslew;
+    sm.gsum[lane] = __ldg(sl) + __ldg(sl + 1);
+  }
+  if (!TAB) return;
   const int ne = (int)((d.n_in + 1u) << (d.n_in + 1u));
   for (int e = lane; e < ne; e += 32) {
     const uint32_t pv = (uint32_t)e >> d.n_in, s = (uint32_t)e & d.inmask;
@@ -305,17 +326,43 @@ __device__ __forceinline__ uint32_t bin_end_of(uint32_t t, const DGate& d, uint3
 }
 
 // Per-lane sums of one segment (forward: leakage nW*ps, internal fJ,
-// switching fJ; adjoint: dC, d_escale, d_lscale * 1e6).
+// switching fJ, glitch fJ; adjoint: dC, d_escale, d_lscale * 1e6, unused).
 struct SegSums {
-  float v0, v1, v2;
+  float v0, v1, v2, v3;
 };
+
+// Time of the previous event on `pin` if it lies at or after c0 (the start
+// of the event's clock cycle): scan back from segment position j - 1
+// through the staged segment, then through the gate's earlier records in
+// memory.  Returns false if there is none in the cycle.
+template <int K>
+__device__ __forceinline__ bool prev_in_cycle(const DGate& d, const uint2* buf, int64_t s0, int j, uint32_t pin,
+                                              uint32_t c0, uint32_t& t_prev) {
+  for (int jj = j - 1; jj >= 0; --jj) {
+    const uint2 r = buf[row_base<K>(jj / K) ^ (uint32_t)(jj % K)];
+    if (r.x < c0) return false;
+    if ((r.y & 0xFu) == pin) {
+      t_prev = r.x;
+      return true;
+    }
+  }
+  for (int64_t i = s0 - 1; i >= d.ga; --i) {
+    const uint2 r = __ldg(d.rec + i);
+    if (r.x < c0) return false;
+    if ((r.y & 0xFu) == pin) {
+      t_prev = r.x;
+      return true;
+    }
+  }
+  return false;
+}
 
 // Pass 2 of a staged segment whose incoming state is the absolute transfer
 // seg_in.  FULL: the segment holds 32 * K events.
-template <int K, bool BWD, bool TAB, bool FULL>
+template <int K, bool BWD, bool TAB, bool FULL, bool GL>
 __device__ __forceinline__ SegSums seg_back(const LibView& L, const DGate& d, const DenseSmem& sm, const uint2* buf,
                                             const Seg& q, uint32_t seg_in, DevError* err, int lane) {
-  SegSums out{0.f, 0.f, 0.f};
+  SegSums out{0.f, 0.f, 0.f, 0.f};
   if (!FULL && q.n_rem == 0) return out;
   // A record out of range or out of order: flag the trace (the host then
   // locates the first bad record exactly) and skip the replay, whose bins
@@ -335,7 +382,7 @@ __device__ __forceinline__ SegSums seg_back(const LibView& L, const DGate& d, co
     Pcur = __ldg(d.gleak + st) * d.lsc;
     Pg = __ldg(d.gleak + spre) * d.lsc;
   }
-  float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+  float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
   float Gcur = 0.f;
   if (BWD && q.t_before < d.T && !q.fh) {
     const uint32_t bb = bin_of(q.t_before, d.magic, d.shift, d.bin_ps);
@@ -389,6 +436,16 @@ __device__ __forceinline__ SegSums seg_back(const LibView& L, const DGate& d, co
         dE = d.esc * (fmaf(fs, (b1 - b0) - (a1 - a0), a1 - a0) * __uint_as_float(dq.w));
       }
     }
+    bool glitch = false;
+    if (GL) {  // Sec. 2.4.1: an earlier event on this pin in the same clock cycle
+      uint32_t t_prev;
+      if (prev_in_cycle<K>(d, buf, q.s0, lane * K + k, pin, cycle_start(t, d.clk, d.cmagic, d.cshift), t_prev)) {
+        const float r = glitch_ratio(t - t_prev, sm.gsum[pin]);
+        E *= r;
+        dE *= r;
+        glitch = true;
+      }
+    }
     const bool tail = tn != t;
     float Pn = Pcur;
     if (tail) Pn = TAB ? sm.leak[st] : __ldg(d.gleak + st) * d.lsc;
@@ -396,9 +453,12 @@ __device__ __forceinline__ SegSums seg_back(const LibView& L, const DGate& d, co
       v0 = fmaf(gE, dE, v0);
       v1 = fmaf(gE, E, v1);
     } else {
-      const float Eo = is_out ? E : 0.f;
+      const float Eg = GL && glitch ? E : 0.f;
+      const float Er = E - Eg;
+      const float Eo = is_out ? Er : 0.f;
       v2 += Eo;
-      v1 += E - Eo;
+      v1 += Er - Eo;
+      if (GL) v3 += Eg;
       const float dp = tail ? Pn - Pg : 0.f;
       const float add = dp * (float)(int32_t)(bend - t) * 1e-6f;
       const bool nb = bn != pb;
@@ -430,6 +490,7 @@ __device__ __forceinline__ SegSums seg_back(const LibView& L, const DGate& d, co
   out.v0 = v0;
   out.v1 = v1;
   out.v2 = v2;
+  out.v3 = v3;
   return out;
 }
 
@@ -440,29 +501,31 @@ __device__ __forceinline__ SegSums seg_back(const LibView& L, const DGate& d, co
 template <int K>
 struct GateAcc {
   static constexpr int F = 64 / K;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-  float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
   int n = 0;
-  __device__ __forceinline__ void flush() {
+  __device__ __forceinline__ void flush(bool gl) {
     const float v0 = warp_sum(f0), v1 = warp_sum(f1), v2 = warp_sum(f2);
     a0 += (double)v0;
     a1 += (double)v1;
     a2 += (double)v2;
-    f0 = f1 = f2 = 0.f;
+    if (gl) a3 += (double)warp_sum(f3);
+    f0 = f1 = f2 = f3 = 0.f;
     n = 0;
   }
-  __device__ __forceinline__ void add(const SegSums& s) {
+  __device__ __forceinline__ void add(const SegSums& s, bool gl) {
     f0 += s.v0;
     f1 += s.v1;
     f2 += s.v2;
-    if (++n == F) flush();
+    f3 += s.v3;
+    if (++n == F) flush(gl);
   }
 };
 
 // Per-gate results from the gate's totals.
-template <bool BWD>
+template <bool BWD, bool GL>
 __device__ __forceinline__ void store_gate(const LibView& L, const DGate& d, const DenseSmem& sm, double a0,
-                                           double a1, double a2) {
+                                           double a1, double a2, double a3) {
   if (BWD) {
     d.W->dC[d.g] = (float)a0;
     sm.wacc[d.cell] += a1;
@@ -471,18 +534,19 @@ __device__ __forceinline__ void store_gate(const LibView& L, const DGate& d, con
     d.W->e_leak[d.g] = a0 * 1e-6;
     d.W->e_int[d.g] = a1;
     d.W->e_sw[d.g] = a2;
+    if (GL) d.W->e_gl[d.g] = a3;
   }
 }
 
 // A medium gate, walked by one warp segment by segment.
-template <int K, bool BWD, bool TAB>
+template <int K, bool BWD, bool TAB, bool GL>
 __device__ __forceinline__ void medium_gate(const LibView& L, const DGate& d, const DenseSmem& sm, DevError* err,
                                             int lane) {
   constexpr int SEG = 32 * K;
   const int64_t nseg = (d.n + SEG - 1) / SEG;
   __syncwarp();
   issue_segment<K>(d, 0, sm.rec, sm.halo, lane);
-  if (TAB) build_tables<BWD>(L, d, sm, lane);
+  if (TAB || GL) build_tables<BWD, TAB, GL>(L, d, sm, lane);
   uint32_t carry = kXAbs | kXH | d.init | (d.init << 8);
   GateAcc<K> acc;
   Seg q;
@@ -495,29 +559,29 @@ __device__ __forceinline__ void medium_gate(const LibView& L, const DGate& d, co
     uint32_t tx;
     if ((s + 1) * SEG <= d.n) {
       tx = seg_front<K, true>(d, s, cur, halo, q, lane);
-      acc.add(seg_back<K, BWD, TAB, true>(L, d, sm, cur, q, carry, err, lane));
+      acc.add(seg_back<K, BWD, TAB, true, GL>(L, d, sm, cur, q, carry, err, lane), GL);
     } else {
       tx = seg_front<K, false>(d, s, cur, halo, q, lane);
-      acc.add(seg_back<K, BWD, TAB, false>(L, d, sm, cur, q, carry, err, lane));
+      acc.add(seg_back<K, BWD, TAB, false, GL>(L, d, sm, cur, q, carry, err, lane), GL);
     }
     carry = xcompose(carry, tx);
     __syncwarp();
   }
-  acc.flush();
-  if (lane == 0) store_gate<BWD>(L, d, sm, acc.a0, acc.a1, acc.a2);
+  acc.flush(GL);
+  if (lane == 0) store_gate<BWD, GL>(L, d, sm, acc.a0, acc.a1, acc.a2, acc.a3);
 }
 
 // A big gate, walked by the CTA's 8 warps in chunks of 8 consecutive
 // segments; the state entering each segment is the carry into the chunk
 // composed with the transfers of the chunk's earlier segments.
-template <int K, bool BWD, bool TAB>
+template <int K, bool BWD, bool TAB, bool GL>
 __device__ __forceinline__ void big_gate(const LibView& L, const DGate& d, const DenseSmem& sm, DevError* err,
-                                         uint32_t (*xfer)[kWarps], double (*red)[3], int wib, int lane) {
+                                         uint32_t (*xfer)[kWarps], double (*red)[4], int wib, int lane) {
   constexpr int SEG = 32 * K;
   const int64_t nchunk = (d.n + (int64_t)kWarps * SEG - 1) / ((int64_t)kWarps * SEG);
   __syncwarp();
   issue_segment<K>(d, wib, sm.rec, sm.halo, lane);
-  if (TAB) build_tables<BWD>(L, d, sm, lane);
+  if (TAB || GL) build_tables<BWD, TAB, GL>(L, d, sm, lane);
   uint32_t carry = kXAbs | kXH | d.init | (d.init << 8);
   GateAcc<K> acc;
   Seg q;
@@ -539,25 +603,27 @@ __device__ __forceinline__ void big_gate(const LibView& L, const DGate& d, const
       if (v == wib) seg_in = carry;
       carry = xcompose(carry, x);
     }
-    acc.add(full ? seg_back<K, BWD, TAB, true>(L, d, sm, cur, q, seg_in, err, lane)
-                 : seg_back<K, BWD, TAB, false>(L, d, sm, cur, q, seg_in, err, lane));
+    acc.add(full ? seg_back<K, BWD, TAB, true, GL>(L, d, sm, cur, q, seg_in, err, lane)
+                 : seg_back<K, BWD, TAB, false, GL>(L, d, sm, cur, q, seg_in, err, lane), GL);
     __syncwarp();
   }
-  acc.flush();
+  acc.flush(GL);
   if (lane == 0) {
     red[wib][0] = acc.a0;
     red[wib][1] = acc.a1;
     red[wib][2] = acc.a2;
+    red[wib][3] = acc.a3;
   }
   __syncthreads();
   if (wib == 0 && lane == 0) {
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     for (int v = 0; v < kWarps; ++v) {
       a0 += red[v][0];
       a1 += red[v][1];
       a2 += red[v][2];
+      a3 += red[v][3];
     }
-    store_gate<BWD>(L, d, sm, a0, a1, a2);
+    store_gate<BWD, GL>(L, d, sm, a0, a1, a2, a3);
   }
 }
 
@@ -583,13 +649,14 @@ __device__ __forceinline__ void stage_round(const uint2* __restrict__ rec_g, uin
 
 // Per-thread sums, FP32 over a few rounds, then folded into FP64.
 struct Sums {
-  float f0 = 0.f, f1 = 0.f, f2 = 0.f;
-  double d0 = 0.0, d1 = 0.0, d2 = 0.0;
-  __device__ __forceinline__ void fold() {
+  float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
+  double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+  __device__ __forceinline__ void fold(bool gl) {
     d0 += (double)f0;
     d1 += (double)f1;
     d2 += (double)f2;
-    f0 = f1 = f2 = 0.f;
+    if (gl) d3 += (double)f3;
+    f0 = f1 = f2 = f3 = 0.f;
   }
 };
 
@@ -600,6 +667,7 @@ __device__ __forceinline__ int bad_event_code(uint32_t t, uint32_t m, uint32_t T
 
 struct WalkOut {
   double v0, v1, v2;  // forward: leakage (nW*ps), internal, switching; adjoint: dC, d_escale, d_lscale * 1e6
+  double v3;          // forward with glitch detection: glitch energy
 };
 
 // Walk of one sparse gate by one thread (Algorithm 1 in event order): n > 0
@@ -610,10 +678,14 @@ struct WalkOut {
 // ahead, each round with the record after it so that the last event of a
 // round sees the next timestamp without another load.  Forward: each distinct
 // bin of consecutive events gets one reduction {energy, leakage step} into L2.
-template <bool BWD>
+//
+// Glitch detection (GL): `last` is this thread's column (stride
+// kWalkThreads) of each pin's previous event time.
+template <bool BWD, bool GL>
 __device__ __forceinline__ WalkOut walk_gate(const LibView& L, const NetView& N, const WinDesc& W, const float* tabl,
                                              uint2* col, const float* sleak, DevError* err, int64_t g,
-                                             const uint2* __restrict__ rec_g, uint32_t n, uint32_t st) {
+                                             const uint2* __restrict__ rec_g, uint32_t n, uint32_t st,
+                                             uint32_t* last) {
 #pragma unroll
   for (int r = 0; r < kRounds; ++r) stage_round(rec_g, (uint32_t)(r * kChunk), n, col + r * kStage * kWalkThreads);
   const uint32_t cell = (uint32_t)N.cell[g];
@@ -632,6 +704,8 @@ __device__ __forceinline__ WalkOut walk_gate(const LibView& L, const NetView& N,
   float Pg = Pcur;        // leakage before the current group
   uint32_t spre = st;     // state before the current group
   Sums acc;
+  if (GL)
+    for (uint32_t p = 0; p <= n_in; ++p) last[p * kWalkThreads] = kNoTime;
   float Gcur = 0.f;       // adjoint: G at the last group (G(0) = 0)
   uint32_t tp = 0u;
   uint32_t pb = kNoTime;
@@ -704,13 +778,25 @@ __device__ __forceinline__ WalkOut walk_gate(const LibView& L, const NetView& N,
         E = BWD ? eu : eu * esc;
         dE = esc * (fmaf(fs, (b1 - b0) - (a1 - a0), a1 - a0) * __uint_as_float(d.w));
       }
+      bool glitch = false;
+      if (GL) {  // Sec. 2.4.1: an earlier event on this pin in the same clock cycle
+        const uint32_t t_prev = last[pin * kWalkThreads];
+        last[pin * kWalkThreads] = t;
+        if (t_prev != kNoTime && t_prev >= cycle_start(t, N.clock_ps, N.clock_magic, N.clock_shift)) {
+          const float* sl = pin < n_in ? N.slew + ((size_t)g * N.stride + pin) * 2 : N.out_slew + 2 * g;
+          const float r = glitch_ratio(t - t_prev, __ldg(sl) + __ldg(sl + 1));
+          E *= r;
+          dE *= r;
+          glitch = true;
+        }
+      }
       const bool tail = t_next != t;
       const float Pn = leak[st];
       if (BWD) {
         acc.f0 += gE * dE;
         acc.f1 += gE * E;
       } else {
-        if (is_out) acc.f2 += E; else acc.f1 += E;
+        if (GL && glitch) acc.f3 += E; else if (is_out) acc.f2 += E; else acc.f1 += E;
         const float dp = tail ? Pn - Pg : 0.f;
         const float add = dp * (float)(int32_t)((bn + 1u) * bin_ps - t) * 1e-6f;
         if (bn != pb) {
@@ -731,7 +817,7 @@ __device__ __forceinline__ WalkOut walk_gate(const LibView& L, const NetView& N,
     u += kChunk;
     slot = (slot + 1) & (kRounds - 1);
     if (++n_done == 16) {
-      acc.fold();
+      acc.fold(GL);
       n_done = 0;
     }
   }
@@ -746,8 +832,8 @@ __device__ __forceinline__ WalkOut walk_gate(const LibView& L, const NetView& N,
       W.final_state[g] = (uint8_t)st;
     }
   }
-  acc.fold();
-  return WalkOut{acc.d0, acc.d1, acc.d2};
+  acc.fold(GL);
+  return WalkOut{acc.d0, acc.d1, acc.d2, acc.d3};
 }
 
 // This thread's gate table into its column of the CTA's staged tables.
@@ -769,16 +855,19 @@ __device__ __forceinline__ void stage_gate_table(const float* __restrict__ gt, i
 // (staged records and their neighbours, energy table, leakage row) and the sparse items' area
 // (per-thread gate tables, per-thread staged records, the leakage table),
 // then, for the adjoint, the per-warp cell sums.
-__host__ __device__ inline size_t dense_area(int K, bool bwd) {
+// With glitch detection the dense area adds each warp's per-pin transition
+// times and the sparse area each thread's per-pin previous event times.
+__host__ __device__ inline size_t dense_area(int K, bool bwd, bool gl) {
   return (size_t)kWarps * (2 * 32 * K * sizeof(uint2) + (bwd ? 2 : 1) * kTabEntries * sizeof(float) +
-                           kLeakEntries * sizeof(float) + 4 * sizeof(uint2));
+                           kLeakEntries * sizeof(float) + 4 * sizeof(uint2) + (gl ? 8 * sizeof(float) : 0));
 }
-__host__ __device__ inline size_t sparse_area(int n_leak, bool bwd) {
+__host__ __device__ inline size_t sparse_area(int n_leak, bool bwd, bool gl) {
   return (size_t)(bwd ? 2 : 1) * kGateTab * kWalkThreads * sizeof(float) +
-         (size_t)kRounds * kStage * kWalkThreads * sizeof(uint2) + (((size_t)n_leak * sizeof(float) + 15) & ~(size_t)15);
+         (size_t)kRounds * kStage * kWalkThreads * sizeof(uint2) + (gl ? (size_t)8 * kWalkThreads * sizeof(uint32_t) : 0) +
+         (((size_t)n_leak * sizeof(float) + 15) & ~(size_t)15);
 }
-__host__ __device__ inline size_t union_area(int K, int n_leak, bool bwd) {
-  const size_t d = dense_area(K, bwd), sp = sparse_area(n_leak, bwd);
+__host__ __device__ inline size_t union_area(int K, int n_leak, bool bwd, bool gl) {
+  const size_t d = dense_area(K, bwd, gl), sp = sparse_area(n_leak, bwd, gl);
   return d > sp ? d : sp;
 }
 
@@ -787,12 +876,12 @@ __host__ __device__ inline size_t union_area(int K, int n_leak, bool bwd) {
 // 256 sparse gates per item (one per thread).  The forward walk fits three
 // CTAs per SM (80 registers); the adjoint's larger tables allow two, so it
 // is given the registers of two.
-template <int K, bool BWD>
+template <int K, bool BWD, bool GL>
 __global__ void __launch_bounds__(kWalkThreads, BWD ? 2 : 3) k_walk(LibView L, NetView N, WalkArgs A) {
   constexpr int SEG = 32 * K;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t xfer[2][kWarps];
-  __shared__ double red[kWarps][3];
+  __shared__ double red[kWarps][4];
   __shared__ unsigned long long s_item;
   const int wib = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -811,12 +900,15 @@ __global__ void __launch_bounds__(kWalkThreads, BWD ? 2 : 3) k_walk(LibView L, N
   sm.leak = reinterpret_cast<float*>(sp) + (size_t)wib * kLeakEntries;
   sp += (size_t)kWarps * kLeakEntries * sizeof(float);
   sm.halo = reinterpret_cast<uint2*>(sp) + (size_t)wib * 4;
+  sp += (size_t)kWarps * 4 * sizeof(uint2);
+  sm.gsum = reinterpret_cast<float*>(sp) + (size_t)wib * 8;
   // sparse view of the union area
   float* stab = reinterpret_cast<float*>(smem);
   uint2* sstg = reinterpret_cast<uint2*>(stab + (BWD ? 2 : 1) * kGateTab * kWalkThreads);
-  float* sleak = reinterpret_cast<float*>(sstg + kRounds * kStage * kWalkThreads);
+  uint32_t* slast = reinterpret_cast<uint32_t*>(sstg + kRounds * kStage * kWalkThreads);
+  float* sleak = reinterpret_cast<float*>(slast + (GL ? 8 * kWalkThreads : 0));
   // adjoint cell sums, after the union
-  sm.wacc = reinterpret_cast<double*>(smem + union_area(K, L.n_leak, BWD)) + (size_t)wib * 2 * L.n_cells;
+  sm.wacc = reinterpret_cast<double*>(smem + union_area(K, L.n_leak, BWD, GL)) + (size_t)wib * 2 * L.n_cells;
   if (BWD)
     for (int c = lane; c < 2 * L.n_cells; c += 32) sm.wacc[c] = 0.0;
 
@@ -840,15 +932,15 @@ __global__ void __launch_bounds__(kWalkThreads, BWD ? 2 : 3) k_walk(LibView L, N
     const bool is_dense = (pos + 1) * n_dense_items / n_items > dense_before;
     const int64_t item = is_dense ? dense_before : n_dense_items + (pos - dense_before);
     if (item < n_big) {
-      const DGate d = dense_gate<BWD>(L, N, wins, P.glist[item]);
-      if (d.n_in <= (uint32_t)kTabMaxIn) big_gate<K, BWD, true>(L, d, sm, err, xfer, red, wib, lane);
-      else big_gate<K, BWD, false>(L, d, sm, err, xfer, red, wib, lane);
+      const DGate d = dense_gate<BWD, GL>(L, N, wins, P.glist[item]);
+      if (d.n_in <= (uint32_t)kTabMaxIn) big_gate<K, BWD, true, GL>(L, d, sm, err, xfer, red, wib, lane);
+      else big_gate<K, BWD, false, GL>(L, d, sm, err, xfer, red, wib, lane);
     } else if (item < n_dense_items) {
       const int64_t i = (item - n_big) * kWarps + wib;
       if (i < n_med) {
-        const DGate d = dense_gate<BWD>(L, N, wins, P.glist[n_big + i]);
-        if (d.n_in <= (uint32_t)kTabMaxIn) medium_gate<K, BWD, true>(L, d, sm, err, lane);
-        else medium_gate<K, BWD, false>(L, d, sm, err, lane);
+        const DGate d = dense_gate<BWD, GL>(L, N, wins, P.glist[n_big + i]);
+        if (d.n_in <= (uint32_t)kTabMaxIn) medium_gate<K, BWD, true, GL>(L, d, sm, err, lane);
+        else medium_gate<K, BWD, false, GL>(L, d, sm, err, lane);
       }
     } else {
       // ---- 256 sparse gates, one per thread
@@ -863,8 +955,8 @@ __global__ void __launch_bounds__(kWalkThreads, BWD ? 2 : 3) k_walk(LibView L, N
         const int64_t ga = W.offsets[g], ge = W.offsets[g + 1];
         float* my_tab = stab + threadIdx.x;
         if (L.cells[N.cell[g]].n_in <= kGateTabMaxIn) stage_gate_table<BWD>(gt, g, my_tab);
-        const WalkOut o = walk_gate<BWD>(L, N, W, my_tab, sstg + threadIdx.x, sleak, err, g, W.rec + ga,
-                                         (uint32_t)(ge - ga), (uint32_t)W.init[g]);
+        const WalkOut o = walk_gate<BWD, GL>(L, N, W, my_tab, sstg + threadIdx.x, sleak, err, g, W.rec + ga,
+                                             (uint32_t)(ge - ga), (uint32_t)W.init[g], slast + threadIdx.x);
         if (BWD) {
           W.dC[g] = (float)o.v0;
           const uint32_t cell = (uint32_t)N.cell[g];
@@ -874,6 +966,7 @@ __global__ void __launch_bounds__(kWalkThreads, BWD ? 2 : 3) k_walk(LibView L, N
           W.e_leak[g] = o.v0 * 1e-6;
           W.e_int[g] = o.v1;
           W.e_sw[g] = o.v2;
+          if (GL) W.e_gl[g] = o.v3;
         }
       }
     }
@@ -886,20 +979,38 @@ __global__ void __launch_bounds__(kWalkThreads, BWD ? 2 : 3) k_walk(LibView L, N
 }
 
 // ------------------------------------------------------------------ launchers
-template <int K, bool BWD>
+template <int K, bool BWD, bool GL>
 cudaError_t launch_walk_k(const LibView& L, const NetView& N, const WalkArgs& A, cudaStream_t st) {
-  const size_t smem = union_area(K, L.n_leak, BWD) + (BWD ? (size_t)kWarps * 2 * L.n_cells * sizeof(double) : 0);
-  cudaError_t e = cudaFuncSetAttribute(k_walk<K, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem =
+      union_area(K, L.n_leak, BWD, GL) + (BWD ? (size_t)kWarps * 2 * L.n_cells * sizeof(double) : 0);
+  cudaError_t e = cudaFuncSetAttribute(k_walk<K, BWD, GL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int grid = A.grid;
   if (grid <= 0) {
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<K, BWD>, kWalkThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<K, BWD, GL>, kWalkThreads, smem);
     if (e != cudaSuccess) return e;
     grid = (per_sm > 0 ? per_sm : 1) * A.n_sm;
   }
-  k_walk<K, BWD><<<grid, kWalkThreads, smem, st>>>(L, N, A);
+  k_walk<K, BWD, GL><<<grid, kWalkThreads, smem, st>>>(L, N, A);
   return cudaGetLastError();
+}
+
+// The walk of one glitch setting: GL = whether glitch detection is on.
+template <bool GL>
+cudaError_t launch_walk_gl(const LibView& L, const NetView& N, const WalkArgs& A, bool backward, cudaStream_t st) {
+  if (backward) {
+    switch (A.rpt) {
+      case 4: return launch_walk_k<4, true, GL>(L, N, A, st);
+      case 16: return launch_walk_k<16, true, GL>(L, N, A, st);
+      default: return launch_walk_k<8, true, GL>(L, N, A, st);
+    }
+  }
+  switch (A.rpt) {
+    case 4: return launch_walk_k<4, false, GL>(L, N, A, st);
+    case 16: return launch_walk_k<16, false, GL>(L, N, A, st);
+    default: return launch_walk_k<8, false, GL>(L, N, A, st);
+  }
 }
 
 }  // namespace

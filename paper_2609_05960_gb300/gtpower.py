@@ -28,7 +28,7 @@ CODE_NAMES = {GTP_EINVAL: "EINVAL", GTP_EORDER: "EORDER", GTP_ERANGE: "ERANGE", 
 ABI_SYMBOLS = ["gtp_create", "gtp_destroy", "gtp_set_stream", "gtp_last_error", "gtp_load_library",
                "gtp_set_scales", "gtp_load_netlist", "gtp_set_load", "gtp_load_events", "gtp_run_power",
                "gtp_gate_energy", "gtp_run_power_batched", "gtp_run_power_backward", "gtp_autotune",
-               "gtp_set_param", "gtp_get_param", "gtp_run_power_noalloc"]
+               "gtp_set_param", "gtp_get_param", "gtp_run_power_noalloc", "gtp_set_glitch", "gtp_gate_glitch"]
 
 
 class GtpError(RuntimeError):
@@ -58,6 +58,8 @@ def load(path: str = LIB_PATH):
         "gtp_set_scales": ([P, P, P], ctypes.c_int),
         "gtp_load_netlist": ([P, I64, P, P, P, I32, ctypes.c_int], ctypes.c_int),
         "gtp_set_load": ([P, P, ctypes.c_int], ctypes.c_int),
+        "gtp_set_glitch": ([P, I64, P, ctypes.c_int], ctypes.c_int),
+        "gtp_gate_glitch": ([P, I32, P, ctypes.c_int], ctypes.c_int),
         "gtp_load_events": ([P, I32, I64, I64, P, P, P, ctypes.c_int], ctypes.c_int),
         "gtp_run_power": ([P, I32, I32, P, ctypes.c_int], ctypes.c_int),
         "gtp_gate_energy": ([P, I32, P, P, P, P, P, ctypes.c_int], ctypes.c_int),
@@ -154,6 +156,18 @@ def gtp_load_netlist(ctx, cell, load_ff, slew_ps) -> None:
 def gtp_set_load(ctx, load_ff) -> None:
     p, f, k = _ptr_flags(load_ff, np.float32)
     _check(ctx, load().gtp_set_load(ctx, p, f))
+
+
+def gtp_set_glitch(ctx, clock_ps: int, out_slew=None) -> None:
+    """Glitch detection with a clock of clock_ps (0: off); out_slew[n_gates][2]
+    {fall, rise} output transition times in ps (float32)."""
+    p, f, k = _ptr_flags(out_slew, np.float32)
+    _check(ctx, load().gtp_set_glitch(ctx, int(clock_ps), p, f))
+
+
+def gtp_gate_glitch(ctx, window: int, e_gl) -> None:
+    p, f, k = _ptr_flags(e_gl, np.float64)
+    _check(ctx, load().gtp_gate_glitch(ctx, int(window), p, f))
 
 
 def gtp_load_events(ctx, window: int, window_ps: int, gate_offsets, events, init_state, borrow: bool = False) -> None:
@@ -285,6 +299,17 @@ class Engine:
 
     def set_load(self, load_ff) -> None:
         gtp_set_load(self.ctx, load_ff)
+
+    def set_glitch(self, clock_ps: int, out_slew=None) -> None:
+        gtp_set_glitch(self.ctx, clock_ps, out_slew)
+
+    def gate_glitch(self, window: int, device: bool = True):
+        """Per-gate glitch energy (fJ, float64) of the window's last run."""
+        import torch
+        out = (torch.empty(self.n_gates, dtype=torch.float64, device=self.device) if device
+               else np.empty(self.n_gates))
+        gtp_gate_glitch(self.ctx, window, out)
+        return out
 
     def load_events(self, window: int, trace=None, *, window_ps=None, offsets=None, records=None, init_state=None,
                     borrow: bool = False) -> None:
