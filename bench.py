@@ -354,6 +354,7 @@ def run_ours(args, cfg_name):
 
     extras = {}
     if rank == 0 and not args.no_extras and cfg_name == "large" and not args.events:
+        extras["glitch"] = measure_glitch(eng, dev, cfg, wave, walk_s * 1e3, n_ev, max(3, min(args.steps // 10, 10)))
         extras["batched"] = measure_batched(eng, dev, max(3, min(args.steps // 10, 10)))
         extras["adjoint"] = measure_adjoint(eng, dev, max(3, min(args.steps // 10, 10)))
 
@@ -436,6 +437,38 @@ def measure_batched(eng, dev, steps):
             "plain_value": total / (ms_p * 1e-3), "speedup_vs_plain": ms_p / ms_b,
             "max_rel_diff_vs_plain": diff, "autotuned_plan": plan, "autotune_best_ms": tuned_ms,
             "graph": True}
+
+
+def measure_glitch(eng, dev, cfg, wave, walk_plain_ms, n_ev, steps):
+    """The same window (still loaded in slot 0) with clock-cycle glitch
+    detection at a 1 GHz clock (output transition times 10-200 ps, seeded):
+    run time, walk time against the plain walk, and the glitch share of the
+    dynamic energy."""
+    import torch
+
+    from paper_2609_05960_gb300 import gtpower
+
+    clock_ps = 1000
+    rng = np.random.default_rng(7)
+    out_slew = rng.uniform(10.0, 200.0, (eng.n_gates, 2)).astype(np.float32)
+    eng.set_glitch(clock_ps, out_slew)
+    run = lambda: gtpower.gtp_run_power(eng.ctx, 0, cfg.bin_ps, wave, graph=True)
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize(dev)
+    eng.set_param("timing", 1)
+    ms = _events_per_s(run, steps, dev)
+    n_t = max(eng.get_param("n_timed"), 1)
+    walk_ms = eng.get_param("t_walk_ns") * 1e-6 / n_t
+    eng.set_param("timing", 0)
+    ge = eng.gate_energy(0)
+    e_gl = eng.gate_glitch(0)
+    dyn = float(ge["e_int"].sum() + ge["e_sw"].sum() + e_gl.sum())
+    eng.set_glitch(0)
+    return {"clock_ps": clock_ps, "ms_per_run": ms, "value": n_ev / (ms * 1e-3), "unit": UNIT, "walk_ms": walk_ms,
+            "walk_over_plain": walk_ms / walk_plain_ms,
+            "glitch_share_of_dynamic_energy": float(e_gl.sum()) / dyn if dyn > 0 else 0.0,
+            "out_slew": "uniform 10-200 ps per gate and edge, seed 7"}
 
 
 def measure_adjoint(eng, dev, steps):

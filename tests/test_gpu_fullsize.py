@@ -108,6 +108,41 @@ def test_large_full_size(engine):
     np.testing.assert_allclose(wave.view(-1, 2).mean(1).cpu().numpy(), wave2.cpu().numpy(), rtol=TOL)
 
 
+def test_large_full_size_with_glitches(engine):
+    """Large with clock-cycle glitch detection at a 1 GHz clock: sampled
+    gates (including the hot ones, with ~10 events per cycle) against the
+    oracle, and the totals over bins and gates, glitch energy included."""
+    cfg = synth.CONFIGS["large"]
+    lib = synth.make_library(cfg.seed_lib)
+    net = synth.make_netlist(lib, cfg.n_gates, cfg.seed_net)
+    counts = synth.zipf_counts(cfg.n_gates, cfg.n_events, cfg.zipf_s, cfg.cap, cfg.seed_ev)
+    out_slew = np.random.default_rng(7).uniform(10.0, 200.0, (cfg.n_gates, 2)).astype(np.float32)
+    engine.load_library(lib)
+    engine.load_netlist(net)
+    _defaults(engine)
+    engine.set_glitch(1000, out_slew)
+    tr, rec, off, init = _gpu_trace(engine, net, cfg, counts)
+    engine.load_events(0, window_ps=cfg.window_ps, offsets=off, records=rec, init_state=init, borrow=True)
+    wave = engine.run_power(0, cfg.bin_ps)
+    ge = engine.gate_energy(0, device=True)
+    e_gl = engine.gate_glitch(0, device=True)
+    gates = _sample_gates(counts)
+    goff, grec = synth.gate_records(net, tr, gates)
+    sub_net = synth.Netlist(net.cell[gates], net.load_ff[gates], np.ascontiguousarray(net.slew_ps[gates]),
+                            net.n_pins[gates], net.level[gates], net.fanin[gates])
+    sub_tr = synth.Trace(tr.window_ps, goff, grec, tr.init_state[gates], tr.seed, tr.tie24)
+    ref = oracle.walk(lib, sub_net, sub_tr, cfg.bin_ps, waveform=False, glitch=(1000, out_slew[gates]))
+    assert ref["e_gl"].sum() > 0
+    _check_gates(ge, ref, gates)
+    got = e_gl.cpu().numpy()[gates]
+    bad = np.abs(got - ref["e_gl"]) > TOL * np.abs(ref["e_gl"]) + 1e-9
+    assert not bad.any(), f"e_gl: gate {gates[np.argmax(bad)]}"
+    e_bins = float((wave.double() * (cfg.bin_ps * 1e3)).sum())
+    e_gates = float(ge["e_leak"].sum() + ge["e_int"].sum() + ge["e_sw"].sum() + e_gl.sum())
+    assert e_bins == pytest.approx(e_gates, rel=1e-6)
+    engine.set_glitch(0)
+
+
 def test_adjoint_full_size(engine):
     import torch
     from paper_2609_05960_gb300 import peak_loss
