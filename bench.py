@@ -327,8 +327,8 @@ def run_ours(args, cfg_name):
         fin_h = torch.empty(G, dtype=torch.uint8, pin_memory=True)
 
         def e2e_step():
-            gtpower.gtp_load_events(ctx, 1, cfg.window_ps, off_h, rec_h, init_h)
-            gtpower.gtp_run_power(ctx, 1, cfg.bin_ps, wave_h)
+            # records streamed from pinned host memory in 8 chunks, copies overlapping the walk
+            gtpower.gtp_run_power_streamed(ctx, 1, cfg.window_ps, off_h, rec_h, init_h, cfg.bin_ps, wave_h, 8)
             gtpower.gtp_gate_energy(ctx, 1, outs_h[0], outs_h[1], outs_h[2], cnt_h, fin_h)
 
         e2e_step()

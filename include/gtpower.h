@@ -197,6 +197,27 @@ int gtp_load_events(gtp_ctx* ctx, int32_t window, int64_t window_ps, int64_t n_e
 int gtp_run_power(gtp_ctx* ctx, int32_t window, int32_t bin_ps, double* waveform_w, int flags);
 
 /*
+ * One window run straight from host memory, in chunks [Sec. 5, event
+ * chunking with the packing and copy of the next chunk overlapping the
+ * kernel]: the window's records are copied to the GPU in n_chunks gate-range
+ * chunks of about n_events / n_chunks records, through two device buffers of
+ * the largest chunk's size, and the walk of each chunk overlaps the copy of
+ * the next.  A trace larger than the device memory runs this way.  Results
+ * equal gtp_load_events + gtp_run_power on the same inputs; the per-gate
+ * results are kept for gtp_gate_energy / gtp_gate_glitch, but the records
+ * are not: the window must be loaded again for any other run.
+ *   gate_offsets [n_gates+1], events [n_events] and init_state [n_gates]
+ *   are host memory (events pinned for the copies to overlap), as for
+ *   gtp_load_events; waveform_w [n_bins] as for gtp_run_power.
+ *   n_chunks: 1..1024.  flags: GTP_HOST or GTP_DEVICE for waveform_w.
+ * Synchronous.  Errors as gtp_load_events and gtp_run_power (offsets are
+ * checked on the host before any copy).
+ */
+int gtp_run_power_streamed(gtp_ctx* ctx, int32_t window, int64_t window_ps, int64_t n_events,
+                           const int64_t* gate_offsets, const gtp_event* events, const uint8_t* init_state,
+                           int32_t bin_ps, double* waveform_w, int32_t n_chunks, int flags);
+
+/*
  * Per-gate results of the last gtp_run_power / batched run of `window`:
  * leakage, internal and switching energy (fJ, FP64), event count and the
  * state after the last event.  Any pointer may be NULL.

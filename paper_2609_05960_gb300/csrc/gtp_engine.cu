@@ -50,6 +50,7 @@ struct Window {
   DevBuf e_leak, e_int, e_sw, e_gl, final_state, bins, tiles, wave;
   bool has_result = false;
   bool glitch_result = false;  // the last run detected glitches (e_gl holds them)
+  bool streamed = false;       // filled by a streamed run: results only, no resident records
   int32_t last_bin_ps = 0;
   const uint2* rec() const { return borrowed ? borrowed : records.as<uint2>(); }
   void release() {
@@ -107,6 +108,10 @@ struct gtp_ctx {
   DevBuf d_err;
   DevBuf first_bad;  // trace check result (see launch_validate)
   DevBuf out_slew;   // glitch detection: [n_gates][2] output {fall, rise} transition times
+  // streamed runs: two chunk buffers, a copy stream and its events
+  DevBuf chunk_buf[2];
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_copied[2] = {}, ev_walked[2] = {};
   DevError* h_err = nullptr;
   std::map<GraphKey, cudaGraphExec_t> graphs;
   cudaStream_t capture_stream = nullptr;
@@ -285,6 +290,9 @@ int build_plan(gtp_ctx* ctx, const std::vector<Window*>& ws, int32_t bin_ps, con
     d.dC = nullptr;
     d.n_events = W.n_events;
     d.tile_base = tb;
+    d.g0 = 0;
+    d.g1 = G;
+    d.keep_bins = 0;
     d.n_tiles = nt;
     d.window_ps = (int32_t)W.window_ps;
     d.bin_ps = bin_ps;
@@ -458,7 +466,7 @@ int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, dou
   bool any_events = false;
   for (int i = 0; i < n; ++i) {
     ws[i] = get_window(ctx, windows[i]);
-    if (!ws[i]) return fail(ctx, GTP_EINVAL, "run_power: window not loaded");
+    if (!ws[i] || ws[i]->streamed) return fail(ctx, GTP_EINVAL, "run_power: window not loaded");
     for (int j = 0; j < i; ++j)
       if (windows[j] == windows[i]) return fail(ctx, GTP_EINVAL, "run_power: a window is listed twice");
     any_events |= ws[i]->n_events > 0;
@@ -562,6 +570,12 @@ void gtp_destroy(gtp_ctx* ctx) {
   cudaDeviceSynchronize();
   drop_graphs(ctx);
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  for (int i = 0; i < 2; ++i) {
+    if (ctx->ev_copied[i]) cudaEventDestroy(ctx->ev_copied[i]);
+    if (ctx->ev_walked[i]) cudaEventDestroy(ctx->ev_walked[i]);
+    ctx->chunk_buf[i].release();
+  }
   for (auto& kv : ctx->windows) kv.second.release();
   for (DevBuf* b : {&ctx->tab, &ctx->leak, &ctx->cells, &ctx->table_cell, &ctx->leak_cell, &ctx->escale, &ctx->lscale,
                     &ctx->cell, &ctx->load, &ctx->slew, &ctx->desc, &ctx->plan, &ctx->glist, &ctx->gtab, &ctx->gtab_bwd,
@@ -796,6 +810,7 @@ int gtp_load_events(gtp_ctx* ctx, int32_t window, int64_t window_ps, int64_t n_e
   // buffers are kept and grown as needed, so reloading a slot does not reallocate
   W.loaded = false;
   W.has_result = false;
+  W.streamed = false;
   W.borrowed = nullptr;
   const cudaMemcpyKind k = kind_in(flags);
   CU(W.offsets.reserve(sizeof(int64_t) * (G + 1)), "alloc offsets");
@@ -845,6 +860,157 @@ int gtp_run_power_batched(gtp_ctx* ctx, int32_t n_windows, const int32_t* window
   return run_forward(ctx, windows, n_windows, bin_ps, waveforms, flags, (flags & GTP_GRAPH) != 0);
 }
 
+int gtp_run_power_streamed(gtp_ctx* ctx, int32_t window, int64_t window_ps, int64_t n_events,
+                           const int64_t* gate_offsets, const gtp_event* events, const uint8_t* init_state,
+                           int32_t bin_ps, double* waveform_w, int32_t n_chunks, int flags) {
+  if (!ctx) return GTP_EINVAL;
+  if (!ctx->net_loaded) return fail(ctx, GTP_EINVAL, "run_power_streamed: load the netlist first");
+  if (window < 0 || window >= kMaxWindows) return fail(ctx, GTP_EINVAL, "run_power_streamed: window slot 0..1023");
+  if (window_ps <= 0 || window_ps >= (1ll << 31))
+    return fail(ctx, GTP_ERANGE, "run_power_streamed: window_ps must be in (0, 2^31)");
+  if (bin_ps <= 0 || window_ps % bin_ps != 0)
+    return fail(ctx, GTP_ERANGE, "run_power_streamed: window_ps must be a multiple of bin_ps > 0");
+  if (n_events < 0 || !gate_offsets || !init_state || (n_events > 0 && !events))
+    return fail(ctx, GTP_EINVAL, "run_power_streamed: null array or negative n_events");
+  if (n_chunks < 1 || n_chunks > kMaxWindows) return fail(ctx, GTP_EINVAL, "run_power_streamed: n_chunks 1..1024");
+  const int64_t G = ctx->N.n_gates;
+  // The offsets decide which host bytes are copied and which records the
+  // kernels read: each chunk's offsets are checked (in [0, n_events], not
+  // decreasing) on the host before its copy is enqueued, while earlier chunks
+  // are copied and walked.
+  if (gate_offsets[0] != 0 || gate_offsets[G] != n_events)
+    return fail(ctx, GTP_EINVAL, "run_power_streamed: offsets must start at 0 and end at n_events");
+  DeviceGuard dg(ctx->device);
+  const cudaStream_t st = ctx->stream;
+  if (!ctx->copy_stream) {
+    CU(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking), "copy stream");
+    for (int i = 0; i < 2; ++i) {
+      CU(cudaEventCreateWithFlags(&ctx->ev_copied[i], cudaEventDisableTiming), "event");
+      CU(cudaEventCreateWithFlags(&ctx->ev_walked[i], cudaEventDisableTiming), "event");
+    }
+  }
+  // chunks: gate ranges of about n_events / n_chunks records each
+  std::vector<int64_t> gb(n_chunks + 1);
+  gb[0] = 0;
+  gb[n_chunks] = G;
+  for (int c = 1; c < n_chunks; ++c) {
+    const int64_t target = n_events / n_chunks * c + (n_events % n_chunks) * c / n_chunks;
+    gb[c] = std::lower_bound(gate_offsets, gate_offsets + G + 1, target) - gate_offsets;
+    if (gb[c] < gb[c - 1]) gb[c] = gb[c - 1];
+    if (gb[c] > G) gb[c] = G;
+  }
+  auto clamped = [&](int64_t g) { return std::min(std::max(gate_offsets[g], (int64_t)0), n_events); };
+  int64_t max_chunk = 0;
+  for (int c = 0; c < n_chunks; ++c) max_chunk = std::max(max_chunk, clamped(gb[c + 1]) - clamped(gb[c]));
+  for (int i = 0; i < 2; ++i)
+    CU(ctx->chunk_buf[i].reserve(sizeof(uint2) * (size_t)(max_chunk + 2)), "alloc chunk buffer");
+  // the window: offsets and initial states on the device, records only chunk by chunk
+  CU(cudaStreamSynchronize(st), "run_power_streamed");
+  Window& W = ctx->windows[window];
+  W.loaded = false;
+  W.has_result = false;
+  W.streamed = false;
+  W.borrowed = nullptr;
+  CU(W.offsets.reserve(sizeof(int64_t) * (G + 1)), "alloc offsets");
+  CU(W.init.reserve((size_t)G), "alloc init");
+  CU(cudaMemcpyAsync(W.offsets.p, gate_offsets, sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, st), "copy offsets");
+  CU(cudaMemcpyAsync(W.init.p, init_state, (size_t)G, cudaMemcpyHostToDevice, st), "copy init");
+  W.window_ps = window_ps;
+  W.n_events = n_events;
+  W.loaded = true;
+  W.streamed = true;  // its records never become resident: other runs need them loaded again
+  double* wave = nullptr;
+  if (waveform_w) {
+    if (flags & GTP_DEVICE) {
+      wave = waveform_w;
+    } else {
+      CU(W.wave.reserve(sizeof(double) * (size_t)(window_ps / bin_ps)), "alloc waveform");
+      wave = W.wave.as<double>();
+    }
+  }
+  RC(ensure_gate_tables(ctx, false));
+  int64_t n_seg_total = 0, n_tiles_total = 0;
+  std::vector<Window*> ws{&W};
+  RC(build_plan(ctx, ws, bin_ps, std::vector<double*>{wave}, false, &n_seg_total, &n_tiles_total));
+  // one descriptor per chunk: the window's, with the chunk's gates and a record base that puts the
+  // chunk buffer at the chunk's first record index (only that chunk's records are ever read)
+  WinDesc* hw = plan_wins(ctx->h_plan);
+  for (int c = 0; c < n_chunks; ++c) {
+    hw[c] = hw[0];
+    hw[c].g0 = gb[c];
+    hw[c].g1 = gb[c + 1];
+    hw[c].keep_bins = c > 0;
+    hw[c].rec = ctx->chunk_buf[c & 1].as<uint2>() - gate_offsets[gb[c]];
+  }
+  RC(upload_plan(ctx, n_chunks, st));
+  CU(cudaMemsetAsync(plan_l0(ctx->plan.p), 0, sizeof(double), st), "zero l0");
+  CU(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(DevError), st), "zero status");
+  CU(ctx->first_bad.reserve(sizeof(unsigned long long)), "alloc trace check");
+  CU(cudaMemsetAsync(ctx->first_bad.p, 0xFF, sizeof(unsigned long long), st), "clear trace check");
+  // the copy stream starts after the uploads above
+  CU(cudaEventRecord(ctx->ev_walked[0], st), "event");
+  CU(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_walked[0], 0), "wait");
+  const uint2* host_rec = reinterpret_cast<const uint2*>(events);
+  for (int c = 0; c < n_chunks; ++c) {
+    const int b = c & 1;
+    bool ok = gate_offsets[gb[c]] >= 0 && gate_offsets[gb[c + 1]] <= n_events;
+    for (int64_t g = gb[c]; ok && g < gb[c + 1]; ++g) ok = gate_offsets[g + 1] >= gate_offsets[g];
+    if (!ok) {
+      cudaStreamSynchronize(ctx->copy_stream);
+      cudaStreamSynchronize(st);
+      return fail(ctx, GTP_EINVAL, "run_power_streamed: offsets must not decrease and must stay in [0, n_events]");
+    }
+    const int64_t r0 = gate_offsets[gb[c]], nr = gate_offsets[gb[c + 1]] - r0;
+    if (c >= 2) CU(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_walked[b], 0), "wait walk");
+    if (nr > 0)
+      CU(cudaMemcpyAsync(ctx->chunk_buf[b].p, host_rec + r0, sizeof(uint2) * (size_t)nr, cudaMemcpyHostToDevice,
+                         ctx->copy_stream), "copy chunk");
+    CU(cudaEventRecord(ctx->ev_copied[b], ctx->copy_stream), "event");
+    CU(cudaStreamWaitEvent(st, ctx->ev_copied[b], 0), "wait copy");
+    WalkArgs A = walk_args(ctx, 1);
+    A.wins = plan_wins(ctx->plan.p) + c;
+    A.n_gates = std::max<int64_t>(gb[c + 1] - gb[c], 1);
+    if (ctx->p_kernel == 1) {
+      CU(launch_prepare(ctx->L, ctx->N, A, false, st), "prepare");
+      if (nr > 0) CU(launch_walk_per_gate(ctx->L, ctx->N, A.wins, 1, ctx->d_err.as<DevError>(), st), "walk");
+    } else {
+      CU(launch_prepare(ctx->L, ctx->N, A, true, st), "prepare");
+      CU(launch_plan_scatter(ctx->N, A, st), "plan");
+      CU(launch_walk(ctx->L, ctx->N, A, false, st), "walk");
+    }
+    // locate a bad record while this chunk is still on the device (a no-op unless one was flagged)
+    CU(launch_validate_if(ctx->L, ctx->N, A.wins, ctx->d_err.as<DevError>(), A.n_gates,
+                          ctx->first_bad.as<unsigned long long>(), st), "trace check");
+    CU(cudaEventRecord(ctx->ev_walked[b], st), "event");
+    ctx->launches += ctx->p_kernel == 1 ? 3 : 4;
+  }
+  CU(launch_merge(plan_wins(ctx->plan.p), plan_tile_base(ctx->plan.p), 1, n_tiles_total, st), "merge");
+  ctx->launches += 3;
+  if (waveform_w && !(flags & GTP_DEVICE))
+    CU(cudaMemcpyAsync(waveform_w, wave, sizeof(double) * (size_t)(window_ps / bin_ps), cudaMemcpyDeviceToHost, st),
+       "copy waveform");
+  CU(cudaMemcpyAsync(ctx->h_err, ctx->d_err.p, sizeof(DevError), cudaMemcpyDeviceToHost, st), "read status");
+  unsigned long long key = ~0ull;
+  CU(cudaMemcpyAsync(&key, ctx->first_bad.p, sizeof key, cudaMemcpyDeviceToHost, st), "read trace check");
+  CU(cudaStreamSynchronize(st), "run_power_streamed");
+  int rc = GTP_OK;
+  if (ctx->h_err->code != 0) {
+    if (key != ~0ull) {
+      const int code = -(int)(key & 7ull);
+      const long long rec = (long long)((key >> 3) & ((1ull << 40) - 1ull));
+      char buf[200];
+      snprintf(buf, sizeof buf, "run_power_streamed: %s at record %lld", code_name(code), rec);
+      rc = fail(ctx, code, buf);
+    } else {
+      rc = check_device_error(ctx, "run_power_streamed");
+    }
+  }
+  W.has_result = rc == GTP_OK;
+  W.glitch_result = ctx->N.clock_ps > 0;
+  W.last_bin_ps = bin_ps;
+  return rc;
+}
+
 int gtp_gate_energy(gtp_ctx* ctx, int32_t window, double* e_leak, double* e_int, double* e_sw, int64_t* n_events,
                     uint8_t* final_state, int flags) {
   if (!ctx) return GTP_EINVAL;
@@ -878,7 +1044,7 @@ int gtp_run_power_backward(gtp_ctx* ctx, int32_t window, int32_t bin_ps, const f
                            float* d_escale, float* d_lscale) {
   if (!ctx) return GTP_EINVAL;
   Window* W = get_window(ctx, window);
-  if (!W) return fail(ctx, GTP_EINVAL, "run_power_backward: window not loaded");
+  if (!W || W->streamed) return fail(ctx, GTP_EINVAL, "run_power_backward: window not loaded");
   if (!dL_dP) return fail(ctx, GTP_EINVAL, "run_power_backward: dL_dP is required");
   if (bin_ps <= 0 || W->window_ps % bin_ps != 0)
     return fail(ctx, GTP_ERANGE, "window_ps must be a multiple of bin_ps > 0");

@@ -101,6 +101,7 @@ struct WinDesc {
   float* dC;                 // adjoint: [G]
   int64_t n_events;
   int64_t tile_base;         // first global merge tile of this window
+  int64_t g0, g1;            // the gates this descriptor covers: [g0, g1) (all gates, but for a streamed chunk)
   int32_t n_tiles;
   int32_t window_ps;
   int32_t bin_ps;
@@ -108,7 +109,7 @@ struct WinDesc {
   uint32_t bin_shift;
   int32_t n_bins;
   float g_total;             // adjoint: G(window_ps)
-  int32_t pad;
+  int32_t keep_bins;         // the preparation pass leaves the bins as they are (a streamed run's later chunks)
 };
 
 // ------------------------------------------------------------------ device helpers
@@ -224,6 +225,11 @@ cudaError_t launch_cells_out(const double* acc, int n_cells, float* d_escale, fl
 // = ((window << 40 | record) << 3) | -code, or ~0 if every record is valid.
 cudaError_t launch_validate(const LibView& L, const NetView& N, const WinDesc* wins, int n_win,
                             unsigned long long* first, cudaStream_t st);
+// The same check of one descriptor's gates, run only if `err` already holds
+// an error (a device-side test, so it can be enqueued unconditionally);
+// *first must have been set to ~0 beforehand.
+cudaError_t launch_validate_if(const LibView& L, const NetView& N, const WinDesc* win, const DevError* err,
+                               int64_t n_gates, unsigned long long* first, cudaStream_t st);
 int merge_tiles(int n_bins);
 
 }  // namespace gtp

@@ -183,7 +183,7 @@ __global__ void k_walk_per_gate(LibView L, NetView N, const WinDesc* __restrict_
   const SmemLib sl = stage_library(L, smem, true);
   const WinDesc& W = wins[blockIdx.y];
   const float T = (float)W.window_ps;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N.n_gates;
+  for (int64_t g = W.g0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < W.g1;
        g += (int64_t)gridDim.x * blockDim.x) {
     const int64_t a = W.offsets[g], b = W.offsets[g + 1];
     if (a == b) continue;
@@ -464,10 +464,12 @@ __global__ void k_cells_out(const double* __restrict__ acc, int n_cells, float* 
 // toggles its pin.  The smallest failing (window, record) wins, so the
 // reported error does not depend on the order in which threads ran:
 // key = ((window << 40 | record) << 3) | -code.
-__global__ void k_validate(LibView L, NetView N, const WinDesc* __restrict__ wins, unsigned long long* first) {
+__global__ void k_validate(LibView L, NetView N, const WinDesc* __restrict__ wins, const DevError* gate,
+                           unsigned long long* first) {
+  if (gate && gate->code == 0) return;
   const WinDesc& W = wins[blockIdx.y];
   const int32_t T = W.window_ps;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N.n_gates;
+  for (int64_t g = W.g0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < W.g1;
        g += (int64_t)gridDim.x * blockDim.x) {
     const int64_t a = W.offsets[g], b = W.offsets[g + 1];
     if (a == b) continue;
@@ -501,7 +503,15 @@ cudaError_t launch_validate(const LibView& L, const NetView& N, const WinDesc* w
   if (e != cudaSuccess) return e;
   int64_t blocks = (N.n_gates + 255) / 256;
   if (blocks > 1024) blocks = 1024;
-  k_validate<<<dim3((unsigned)(blocks < 1 ? 1 : blocks), (unsigned)n_win), 256, 0, st>>>(L, N, wins, first);
+  k_validate<<<dim3((unsigned)(blocks < 1 ? 1 : blocks), (unsigned)n_win), 256, 0, st>>>(L, N, wins, nullptr, first);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate_if(const LibView& L, const NetView& N, const WinDesc* win, const DevError* err,
+                               int64_t n_gates, unsigned long long* first, cudaStream_t st) {
+  int64_t blocks = (n_gates + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  k_validate<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, st>>>(L, N, win, err, first);
   return cudaGetLastError();
 }
 

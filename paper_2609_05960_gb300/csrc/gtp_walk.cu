@@ -103,21 +103,20 @@ __global__ void __launch_bounds__(256) k_prepare(LibView L, NetView N, const Win
   __shared__ bool s_last;
   const int nb = n_buckets(dmin);
   const WinDesc& W = wins[blockIdx.y];
-  const int64_t G = N.n_gates;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   if (PLAN) {
     for (int b = threadIdx.x; b < nb; b += blockDim.x) sh[b] = 0u;
     __syncthreads();
   }
-  if (GATE) {  // bins are 8-byte pairs in a 256-byte aligned buffer: two per 16-byte store
+  if (GATE && !W.keep_bins) {  // bins are 8-byte pairs in a 256-byte aligned buffer: two per 16-byte store
     float4* b4 = reinterpret_cast<float4*>(W.bins);
     const int64_t n4 = (int64_t)W.n_bins >> 1;
     for (int64_t i = tid; i < n4; i += stride) b4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (tid == 0 && (W.n_bins & 1)) W.bins[W.n_bins - 1] = make_float2(0.f, 0.f);
   }
   double p0 = 0.0;
-  for (int64_t g = tid; g < G; g += stride) {
+  for (int64_t g = W.g0 + tid; g < W.g1; g += stride) {
     const int64_t c = W.offsets[g + 1] - W.offsets[g];
     if (GATE) {
       const int32_t cell = N.cell[g];
@@ -166,17 +165,18 @@ __global__ void __launch_bounds__(256) k_prepare(LibView L, NetView N, const Win
   }
 }
 
-__global__ void k_plan_scatter(const WinDesc* __restrict__ wins, int64_t G, int64_t seg_len, int dmin, PlanBufs P) {
+__global__ void k_plan_scatter(const WinDesc* __restrict__ wins, int64_t seg_len, int dmin, PlanBufs P) {
   extern __shared__ unsigned long long sbase[];  // [0, nb): block bases; then [0, nb) local counts (32-bit)
   const int nb = n_buckets(dmin);
   unsigned int* sh = reinterpret_cast<unsigned int*>(sbase + nb);
   const WinDesc& W = wins[blockIdx.y];
   unsigned long long* cursor = P.counters + kCntHist + nb;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < G; base += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t base = W.g0 + (int64_t)blockIdx.x * blockDim.x; base < W.g1;
+       base += (int64_t)gridDim.x * blockDim.x) {  // block-uniform: the loop holds barriers
     for (int b = threadIdx.x; b < nb; b += blockDim.x) sh[b] = 0u;
     __syncthreads();
     const int64_t g = base + threadIdx.x;
-    const int64_t c = g < G ? W.offsets[g + 1] - W.offsets[g] : 0;
+    const int64_t c = g < W.g1 ? W.offsets[g + 1] - W.offsets[g] : 0;
     const int b = c > 0 ? work_bucket(c, dmin, seg_len) : -1;
     unsigned int local = 0u;
     if (b >= 0) local = atomicAdd(&sh[b], 1u);
@@ -229,7 +229,7 @@ cudaError_t launch_plan_scatter(const NetView& N, const WalkArgs& A, cudaStream_
   const size_t scatter_smem = nb * (sizeof(unsigned long long) + sizeof(unsigned int));
   cudaError_t e = cudaFuncSetAttribute(k_plan_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scatter_smem);
   if (e != cudaSuccess) return e;
-  k_plan_scatter<<<prepare_grid(A), 256, scatter_smem, st>>>(A.wins, A.n_gates, 32ll * A.rpt, dmin, A.plan);
+  k_plan_scatter<<<prepare_grid(A), 256, scatter_smem, st>>>(A.wins, 32ll * A.rpt, dmin, A.plan);
   return cudaGetLastError();
 }
 

@@ -28,7 +28,8 @@ CODE_NAMES = {GTP_EINVAL: "EINVAL", GTP_EORDER: "EORDER", GTP_ERANGE: "ERANGE", 
 ABI_SYMBOLS = ["gtp_create", "gtp_destroy", "gtp_set_stream", "gtp_last_error", "gtp_load_library",
                "gtp_set_scales", "gtp_load_netlist", "gtp_set_load", "gtp_load_events", "gtp_run_power",
                "gtp_gate_energy", "gtp_run_power_batched", "gtp_run_power_backward", "gtp_autotune",
-               "gtp_set_param", "gtp_get_param", "gtp_run_power_noalloc", "gtp_set_glitch", "gtp_gate_glitch"]
+               "gtp_set_param", "gtp_get_param", "gtp_run_power_noalloc", "gtp_set_glitch", "gtp_gate_glitch",
+               "gtp_run_power_streamed"]
 
 
 class GtpError(RuntimeError):
@@ -60,6 +61,7 @@ def load(path: str = LIB_PATH):
         "gtp_set_load": ([P, P, ctypes.c_int], ctypes.c_int),
         "gtp_set_glitch": ([P, I64, P, ctypes.c_int], ctypes.c_int),
         "gtp_gate_glitch": ([P, I32, P, ctypes.c_int], ctypes.c_int),
+        "gtp_run_power_streamed": ([P, I32, I64, I64, P, P, P, I32, P, I32, ctypes.c_int], ctypes.c_int),
         "gtp_load_events": ([P, I32, I64, I64, P, P, P, ctypes.c_int], ctypes.c_int),
         "gtp_run_power": ([P, I32, I32, P, ctypes.c_int], ctypes.c_int),
         "gtp_gate_energy": ([P, I32, P, P, P, P, P, ctypes.c_int], ctypes.c_int),
@@ -163,6 +165,21 @@ def gtp_set_glitch(ctx, clock_ps: int, out_slew=None) -> None:
     {fall, rise} output transition times in ps (float32)."""
     p, f, k = _ptr_flags(out_slew, np.float32)
     _check(ctx, load().gtp_set_glitch(ctx, int(clock_ps), p, f))
+
+
+def gtp_run_power_streamed(ctx, window: int, window_ps: int, gate_offsets, events, init_state, bin_ps: int,
+                           waveform=None, n_chunks: int = 8) -> None:
+    """Run a window from host arrays in n_chunks overlapped chunks (events
+    pinned for overlap); the waveform may be host or device."""
+    po, fo, ko = _ptr_flags(gate_offsets, np.int64)
+    pe, fe, ke = _ptr_flags(events, np.uint32)
+    pi, fi, ki = _ptr_flags(init_state, np.uint8)
+    if GTP_DEVICE in (fo, fe, fi):
+        raise ValueError("run_power_streamed takes host inputs")
+    pw, fw, kw = _ptr_flags(waveform, np.float64)
+    n = 0 if events is None else (events.shape[0] if hasattr(events, "shape") else len(events))
+    _check(ctx, load().gtp_run_power_streamed(ctx, int(window), int(window_ps), int(n), po, pe, pi, int(bin_ps), pw,
+                                              int(n_chunks), fw))
 
 
 def gtp_gate_glitch(ctx, window: int, e_gl) -> None:
@@ -326,6 +343,22 @@ class Engine:
         if out is None:
             out = torch.empty(nb, dtype=torch.float64, device=self.device)
         gtp_run_power(self.ctx, window, bin_ps, out, graph=graph)
+        return out
+
+    def run_power_streamed(self, window: int, trace=None, bin_ps: int = 10, out=None, n_chunks: int = 8, *,
+                           window_ps=None, offsets=None, records=None, init_state=None):
+        """Waveform (float64; on the device unless `out` is a host array) of a
+        window streamed from host arrays in n_chunks overlapped chunks."""
+        import torch
+        if trace is not None:  # explicit arrays take precedence (e.g. pinned records)
+            window_ps = trace.window_ps if window_ps is None else window_ps
+            offsets = trace.offsets if offsets is None else offsets
+            records = trace.records if records is None else records
+            init_state = trace.init_state if init_state is None else init_state
+        if out is None:
+            out = torch.empty(int(window_ps) // bin_ps, dtype=torch.float64, device=self.device)
+        gtp_run_power_streamed(self.ctx, window, window_ps, offsets, records, init_state, bin_ps, out, n_chunks)
+        self.windows[window] = dict(window_ps=int(window_ps))
         return out
 
     def gate_energy(self, window: int, device: bool = True):
