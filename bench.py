@@ -55,9 +55,11 @@ def parse():
     p.add_argument("--events", type=int, default=0,
                    help="scale the configuration to this many events (same gates and distribution; "
                         "for profiling a smaller case)")
-    p.add_argument("--sweep", default="", choices=["", "contention"],
-                   help="contention: uniform high activity (1, 2, 4, 8 events per gate per 1k bins) "
-                        "instead of the default run; one JSON line per density")
+    p.add_argument("--sweep", default="", choices=["", "contention", "streamed"],
+                   help="contention: uniform high activity (1, 2, 4, 8 events per gate per 1k bins); "
+                        "streamed: the large window streamed from pinned host memory in 1-32 chunks, "
+                        "against a plain copy of its records; instead of the default run, one JSON line "
+                        "per case")
     return p.parse_args()
 
 
@@ -556,10 +558,53 @@ def run_contention_sweep(args):
     eng.close()
 
 
+def run_streamed_sweep(args):
+    """gtp_run_power_streamed on the large window from pinned host memory,
+    for 1 to 32 chunks, next to a plain host-to-device copy of the same
+    records (the floor of any run that starts from host memory)."""
+    import torch
+
+    import synth
+    from paper_2609_05960_gb300 import Engine, gtpower
+
+    dev = torch.device("cuda", 0)
+    cfg = synth.CONFIGS["large"]
+    lib = synth.make_library(cfg.seed_lib)
+    net = synth.make_netlist(lib, cfg.n_gates, cfg.seed_net)
+    counts = synth.zipf_counts(cfg.n_gates, cfg.n_events, cfg.zipf_s, cfg.cap, cfg.seed_ev)
+    tr, rec = synth.make_trace_gpu(net, counts, cfg.window_ps, cfg.seed_ev, device=dev)
+    eng = Engine(0)
+    eng.load_library(lib)
+    eng.load_netlist(net)
+    rec_h = torch.empty(rec.shape, dtype=torch.int32, pin_memory=True)
+    rec_h.copy_(rec)
+    off_h = torch.from_numpy(tr.offsets).pin_memory()
+    init_h = torch.from_numpy(tr.init_state).pin_memory()
+    wave_h = torch.empty(cfg.window_ps // cfg.bin_ps, dtype=torch.float64, pin_memory=True)
+    steps = max(3, min(args.steps, 10))
+    ms_copy = _events_per_s(lambda: rec.copy_(rec_h, non_blocking=True), steps, dev)
+    del rec
+    torch.cuda.empty_cache()
+    n = int(tr.n_events)
+    print(json.dumps({"sweep": "streamed", "case": "plain host-to-device copy of the records",
+                      "bytes": n * 8, "ms": ms_copy, "gb_per_s": n * 8 / (ms_copy * 1e6)}), flush=True)
+    for nc in (1, 2, 4, 8, 16, 32):
+        run = lambda: gtpower.gtp_run_power_streamed(eng.ctx, 0, cfg.window_ps, off_h, rec_h, init_h, cfg.bin_ps,
+                                                     wave_h, nc)
+        ms = _events_per_s(run, steps, dev)
+        print(json.dumps({"sweep": "streamed", "case": f"gtp_run_power_streamed, {nc} chunks", "n_chunks": nc,
+                          "events": n, "ms": ms, "value": n / (ms * 1e-3), "unit": UNIT,
+                          "over_plain_copy": ms / ms_copy}), flush=True)
+    eng.close()
+
+
 def main():
     args = parse()
     if args.sweep == "contention":
         run_contention_sweep(args)
+        return
+    if args.sweep == "streamed":
+        run_streamed_sweep(args)
         return
     if args.impl == "reference":
         run_reference(args, args.config)
