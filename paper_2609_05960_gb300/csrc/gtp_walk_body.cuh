@@ -873,11 +873,13 @@ __host__ __device__ inline size_t union_area(int K, int n_leak, bool bwd, bool g
 
 // Persistent CTAs of 8 warps take work items from the shared counter: one big
 // gate per item (all 8 warps), 8 medium gates per item (one per warp), then
-// 256 sparse gates per item (one per thread).  The forward walk fits three
-// CTAs per SM (80 registers); the adjoint's larger tables allow two, so it
-// is given the registers of two.
+// 256 sparse gates per item (one per thread).  The forward walk with 4 or 8
+// records per lane fits three CTAs per SM (80 registers).  With 16 records
+// per lane it would spill at 80, and the adjoint's larger tables allow only
+// two CTAs per SM: both are given the registers of two (measured on the
+// large workload: 16 records per lane at two CTAs 1.18 ms, at three 1.38 ms).
 template <int K, bool BWD, bool GL>
-__global__ void __launch_bounds__(kWalkThreads, BWD ? 2 : 3) k_walk(LibView L, NetView N, WalkArgs A) {
+__global__ void __launch_bounds__(kWalkThreads, (BWD || K == 16) ? 2 : 3) k_walk(LibView L, NetView N, WalkArgs A) {
   constexpr int SEG = 32 * K;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t xfer[2][kWarps];
