@@ -109,6 +109,9 @@ struct DenseSmem {
   float* leak;     // [kLeakEntries] leakage per state (forward: scaled)
   uint2* halo;     // [2][2] per staging buffer: the records just before and just after the segment
   float* gsum;     // glitch detection: [8] rise + fall transition time of each pin
+  uint32_t* gprev; // glitch detection: [8][32] per pin and lane, the pin's previous event time + 1 (0: none)
+  uint32_t* gtot;  // glitch detection: [8] per pin, the segment's last event time + 1 (medium gates)
+  uint32_t* gcarry;// glitch detection: [8] per pin, the gate's last event time + 1 before the segment
   double* wacc;    // adjoint: [2 * n_cells] per-warp cell sums
 };
 
@@ -331,34 +334,37 @@ struct SegSums {
   float v0, v1, v2, v3;
 };
 
-// Time of the previous event on `pin` if it lies at or after c0 (the start
-// of the event's clock cycle): scan back from segment position j - 1
-// through the staged segment, then through the gate's earlier records in
-// memory.  Returns false if there is none in the cycle.
-template <int K>
-__device__ __forceinline__ bool prev_in_cycle(const DGate& d, const uint2* buf, int64_t s0, int j, uint32_t pin,
-                                              uint32_t c0, uint32_t& t_prev) {
-  for (int jj = j - 1; jj >= 0; --jj) {
-    const uint2 r = buf[row_base<K>(jj / K) ^ (uint32_t)(jj % K)];
-    if (r.x < c0) return false;
-    if ((r.y & 0xFu) == pin) {
-      t_prev = r.x;
-      return true;
+// Glitch detection, per staged segment: each pin's previous event time (+1;
+// 0: none) as the lane's first event sees it within the segment.  The lane
+// writes its records' times into its column of gprev (by pin), and a warp
+// max-scan per pin turns the columns into the last time on that pin in the
+// lanes before (times do not decrease along the segment).  The segment's
+// last time per pin goes to tot[pin].  The callers then fold in the gate's
+// earlier segments.
+template <int K, bool FULL>
+__device__ __forceinline__ void gl_segment_scan(const DGate& d, const uint2* buf, const Seg& q, uint32_t* gprev,
+                                                uint32_t* tot, int lane) {
+  for (uint32_t p = 0; p <= d.n_in; ++p) gprev[p * 32 + lane] = 0u;
+  const uint32_t rb = row_base<K>(lane);
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (FULL || k < q.nk) {
+      const uint2 r = buf[rb ^ (uint32_t)k];
+      gprev[min(r.y & 0xFu, 7u) * 32 + lane] = r.x + 1u;  // a bad pin is screened out before the replay
     }
-  }
-  for (int64_t i = s0 - 1; i >= d.ga; --i) {
-    const uint2 r = __ldg(d.rec + i);
-    if (r.x < c0) return false;
-    if ((r.y & 0xFu) == pin) {
-      t_prev = r.x;
-      return true;
+  for (uint32_t p = 0; p <= d.n_in; ++p) {
+    uint32_t inc = gprev[p * 32 + lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, inc, o);
+      if (lane >= o) inc = max(inc, y);
     }
+    const uint32_t ex = __shfl_up_sync(kFull, inc, 1);
+    gprev[p * 32 + lane] = lane == 0 ? 0u : ex;
+    if (lane == 31) tot[p] = inc;
   }
-  return false;
 }
 
-// Pass 2 of a staged segment whose incoming state is the absolute transfer
-// seg_in.  FULL: the segment holds 32 * K events.
 template <int K, bool BWD, bool TAB, bool FULL, bool GL>
 __device__ __forceinline__ SegSums seg_back(const LibView& L, const DGate& d, const DenseSmem& sm, const uint2* buf,
                                             const Seg& q, uint32_t seg_in, DevError* err, int lane) {
@@ -438,9 +444,10 @@ __device__ __forceinline__ SegSums seg_back(const LibView& L, const DGate& d, co
     }
     bool glitch = false;
     if (GL) {  // Sec. 2.4.1: an earlier event on this pin in the same clock cycle
-      uint32_t t_prev;
-      if (prev_in_cycle<K>(d, buf, q.s0, lane * K + k, pin, cycle_start(t, d.clk, d.cmagic, d.cshift), t_prev)) {
-        const float r = glitch_ratio(t - t_prev, sm.gsum[pin]);
+      const uint32_t pv = sm.gprev[pin * 32 + lane];
+      sm.gprev[pin * 32 + lane] = t + 1u;
+      if (pv != 0u && pv - 1u >= cycle_start(t, d.clk, d.cmagic, d.cshift)) {
+        const float r = glitch_ratio(t - (pv - 1u), sm.gsum[pin]);
         E *= r;
         dE *= r;
         glitch = true;
@@ -547,6 +554,7 @@ __device__ __forceinline__ void medium_gate(const LibView& L, const DGate& d, co
   __syncwarp();
   issue_segment<K>(d, 0, sm.rec, sm.halo, lane);
   if (TAB || GL) build_tables<BWD, TAB, GL>(L, d, sm, lane);
+  if (GL && lane <= (int)d.n_in) sm.gcarry[lane] = 0u;
   uint32_t carry = kXAbs | kXH | d.init | (d.init << 8);
   GateAcc<K> acc;
   Seg q;
@@ -556,12 +564,19 @@ __device__ __forceinline__ void medium_gate(const LibView& L, const DGate& d, co
     cp_async_wait_1();
     __syncwarp();
     const uint2* halo = sm.halo + (s & 1) * 2;
-    uint32_t tx;
-    if ((s + 1) * SEG <= d.n) {
-      tx = seg_front<K, true>(d, s, cur, halo, q, lane);
+    const bool full = (s + 1) * SEG <= d.n;
+    const uint32_t tx = full ? seg_front<K, true>(d, s, cur, halo, q, lane) : seg_front<K, false>(d, s, cur, halo, q, lane);
+    if (GL) {  // previous event times per pin: this segment's earlier lanes, then the gate's earlier segments
+      if (full) gl_segment_scan<K, true>(d, cur, q, sm.gprev, sm.gtot, lane);
+      else gl_segment_scan<K, false>(d, cur, q, sm.gprev, sm.gtot, lane);
+      __syncwarp();
+      for (uint32_t p = 0; p <= d.n_in; ++p) sm.gprev[p * 32 + lane] = max(sm.gprev[p * 32 + lane], sm.gcarry[p]);
+      __syncwarp();
+      if (lane <= (int)d.n_in) sm.gcarry[lane] = max(sm.gcarry[lane], sm.gtot[lane]);
+    }
+    if (full) {
       acc.add(seg_back<K, BWD, TAB, true, GL>(L, d, sm, cur, q, carry, err, lane), GL);
     } else {
-      tx = seg_front<K, false>(d, s, cur, halo, q, lane);
       acc.add(seg_back<K, BWD, TAB, false, GL>(L, d, sm, cur, q, carry, err, lane), GL);
     }
     carry = xcompose(carry, tx);
@@ -576,12 +591,14 @@ __device__ __forceinline__ void medium_gate(const LibView& L, const DGate& d, co
 // composed with the transfers of the chunk's earlier segments.
 template <int K, bool BWD, bool TAB, bool GL>
 __device__ __forceinline__ void big_gate(const LibView& L, const DGate& d, const DenseSmem& sm, DevError* err,
-                                         uint32_t (*xfer)[kWarps], double (*red)[4], int wib, int lane) {
+                                         uint32_t (*xfer)[kWarps], uint32_t (*gx)[kWarps][8], double (*red)[4],
+                                         int wib, int lane) {
   constexpr int SEG = 32 * K;
   const int64_t nchunk = (d.n + (int64_t)kWarps * SEG - 1) / ((int64_t)kWarps * SEG);
   __syncwarp();
   issue_segment<K>(d, wib, sm.rec, sm.halo, lane);
   if (TAB || GL) build_tables<BWD, TAB, GL>(L, d, sm, lane);
+  if (GL && lane <= (int)d.n_in) sm.gcarry[lane] = 0u;
   uint32_t carry = kXAbs | kXH | d.init | (d.init << 8);
   GateAcc<K> acc;
   Seg q;
@@ -594,8 +611,26 @@ __device__ __forceinline__ void big_gate(const LibView& L, const DGate& d, const
     const uint2* halo = sm.halo + (c & 1) * 2;
     const bool full = (s + 1) * SEG <= d.n;
     const uint32_t tx = full ? seg_front<K, true>(d, s, cur, halo, q, lane) : seg_front<K, false>(d, s, cur, halo, q, lane);
+    if (GL) {
+      if (full) gl_segment_scan<K, true>(d, cur, q, sm.gprev, gx[c & 1][wib], lane);
+      else gl_segment_scan<K, false>(d, cur, q, sm.gprev, gx[c & 1][wib], lane);
+    }
     if (lane == 0) xfer[c & 1][wib] = tx;
     __syncthreads();
+    if (GL) {  // fold in the chunk's earlier segments (other warps) and the earlier chunks
+      for (uint32_t p = 0; p <= d.n_in; ++p) {
+        uint32_t before = sm.gcarry[p], all = before;
+        for (int v = 0; v < kWarps; ++v) {
+          const uint32_t m = gx[c & 1][v][p];
+          if (v < wib) before = max(before, m);
+          all = max(all, m);
+        }
+        sm.gprev[p * 32 + lane] = max(sm.gprev[p * 32 + lane], before);
+        __syncwarp();
+        if (lane == 0) sm.gcarry[p] = all;
+        __syncwarp();
+      }
+    }
     uint32_t seg_in = carry;
 #pragma unroll
     for (int v = 0; v < kWarps; ++v) {
@@ -859,7 +894,8 @@ __device__ __forceinline__ void stage_gate_table(const float* __restrict__ gt, i
 // times and the sparse area each thread's per-pin previous event times.
 __host__ __device__ inline size_t dense_area(int K, bool bwd, bool gl) {
   return (size_t)kWarps * (2 * 32 * K * sizeof(uint2) + (bwd ? 2 : 1) * kTabEntries * sizeof(float) +
-                           kLeakEntries * sizeof(float) + 4 * sizeof(uint2) + (gl ? 8 * sizeof(float) : 0));
+                           kLeakEntries * sizeof(float) + 4 * sizeof(uint2) +
+                           (gl ? 8 * sizeof(float) + (8 * 32 + 16) * sizeof(uint32_t) : 0));
 }
 __host__ __device__ inline size_t sparse_area(int n_leak, bool bwd, bool gl) {
   return (size_t)(bwd ? 2 : 1) * kGateTab * kWalkThreads * sizeof(float) +
@@ -875,15 +911,18 @@ __host__ __device__ inline size_t union_area(int K, int n_leak, bool bwd, bool g
 // gate per item (all 8 warps), 8 medium gates per item (one per warp), then
 // 256 sparse gates per item (one per thread).  The forward walk with 4 or 8
 // records per lane fits three CTAs per SM (80 registers).  With 16 records
-// per lane it would spill at 80, and the adjoint's larger tables allow only
-// two CTAs per SM: both are given the registers of two (measured on the
-// large workload: 16 records per lane at two CTAs 1.18 ms, at three 1.38 ms).
+// per lane or glitch detection it would spill at 80, and the adjoint's
+// larger tables allow only two CTAs per SM: these are given the registers of
+// two (measured on the large workload: 16 records per lane at two CTAs
+// 1.18 ms, at three 1.38 ms).
 template <int K, bool BWD, bool GL>
-__global__ void __launch_bounds__(kWalkThreads, (BWD || K == 16) ? 2 : 3) k_walk(LibView L, NetView N, WalkArgs A) {
+__global__ void __launch_bounds__(kWalkThreads, (BWD || GL || K == 16) ? 2 : 3)
+    k_walk(LibView L, NetView N, WalkArgs A) {
   constexpr int SEG = 32 * K;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t xfer[2][kWarps];
   __shared__ double red[kWarps][4];
+  __shared__ uint32_t gx[GL ? 2 : 1][kWarps][8];  // glitch detection: each warp's segment-last time per pin
   __shared__ unsigned long long s_item;
   const int wib = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -904,6 +943,10 @@ __global__ void __launch_bounds__(kWalkThreads, (BWD || K == 16) ? 2 : 3) k_walk
   sm.halo = reinterpret_cast<uint2*>(sp) + (size_t)wib * 4;
   sp += (size_t)kWarps * 4 * sizeof(uint2);
   sm.gsum = reinterpret_cast<float*>(sp) + (size_t)wib * 8;
+  sp += (size_t)kWarps * 8 * sizeof(float);
+  sm.gprev = reinterpret_cast<uint32_t*>(sp) + (size_t)wib * (8 * 32 + 16);
+  sm.gtot = sm.gprev + 8 * 32;
+  sm.gcarry = sm.gtot + 8;
   // sparse view of the union area
   float* stab = reinterpret_cast<float*>(smem);
   uint2* sstg = reinterpret_cast<uint2*>(stab + (BWD ? 2 : 1) * kGateTab * kWalkThreads);
@@ -935,8 +978,8 @@ __global__ void __launch_bounds__(kWalkThreads, (BWD || K == 16) ? 2 : 3) k_walk
     const int64_t item = is_dense ? dense_before : n_dense_items + (pos - dense_before);
     if (item < n_big) {
       const DGate d = dense_gate<BWD, GL>(L, N, wins, P.glist[item]);
-      if (d.n_in <= (uint32_t)kTabMaxIn) big_gate<K, BWD, true, GL>(L, d, sm, err, xfer, red, wib, lane);
-      else big_gate<K, BWD, false, GL>(L, d, sm, err, xfer, red, wib, lane);
+      if (d.n_in <= (uint32_t)kTabMaxIn) big_gate<K, BWD, true, GL>(L, d, sm, err, xfer, gx, red, wib, lane);
+      else big_gate<K, BWD, false, GL>(L, d, sm, err, xfer, gx, red, wib, lane);
     } else if (item < n_dense_items) {
       const int64_t i = (item - n_big) * kWarps + wib;
       if (i < n_med) {
