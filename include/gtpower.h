@@ -164,6 +164,21 @@ int gtp_set_glitch(gtp_ctx* ctx, int64_t clock_ps, const float* out_slew_ps, int
 int gtp_gate_glitch(gtp_ctx* ctx, int32_t window, double* e_gl, int flags);
 
 /*
+ * Design-level power of the last run of `window` [Eq. average power,
+ * Sec. 2.4.1; peak power, Sec. 5], into out[7] (host, FP64):
+ *   out[0..3]  leakage, internal, switching and glitch power in W: the
+ *              per-gate energies summed over the design, over window_ps
+ *              (the paper divides by the end of its analysis, here the
+ *              window's end);
+ *   out[4]     their total;
+ *   out[5]     the peak bin power of waveform_w (W), out[6] its first bin
+ *              index; 0 and -1 when waveform_w is NULL.
+ * waveform_w [n_bins of that run]: the waveform the run wrote, or NULL;
+ * flags: GTP_HOST or GTP_DEVICE for it.
+ */
+int gtp_design_power(gtp_ctx* ctx, int32_t window, const double* waveform_w, int flags, double* out);
+
+/*
  * Load one stimulus window's events as slot `window` (0 <= window < 1024;
  * reloading a slot replaces it).
  *   window_ps     length of the analysis window, > 0, < 2^31

@@ -211,6 +211,20 @@ def bilinear_dload(slew_axis, load_axis, table, slew: float, load: float) -> flo
                                         float(slew), float(load))
 
 
+def design_power(result: dict, window_ps: int, bin_ps: int) -> dict:
+    """Design-level power from a walk() result (W) [Eq. average power,
+    Sec. 2.4.1: a component's energy over the analysis time, here the
+    window; peak power, Sec. 5: the largest bin of the waveform]."""
+    to_w = 1e-3 / float(window_ps)
+    p = {k: float(np.sum(result[e])) * to_w for k, e in (("p_leak", "e_leak"), ("p_int", "e_int"),
+                                                          ("p_sw", "e_sw"), ("p_gl", "e_gl"))}
+    p["p_total"] = p["p_leak"] + p["p_int"] + p["p_sw"] + p["p_gl"]
+    w = waveform_w(result["bins"], bin_ps)
+    p["peak_bin"] = int(np.argmax(w)) if len(w) else -1
+    p["p_peak"] = float(w[p["peak_bin"]]) if len(w) else 0.0
+    return p
+
+
 def waveform_w(bins_fj: np.ndarray, bin_ps: int) -> np.ndarray:
     """Power per bin in W from energy per bin in fJ: fJ/ps = mW."""
     return np.asarray(bins_fj, np.float64) * 1e-3 / float(bin_ps)

@@ -108,6 +108,7 @@ struct gtp_ctx {
   DevBuf d_err;
   DevBuf first_bad;  // trace check result (see launch_validate)
   DevBuf out_slew;   // glitch detection: [n_gates][2] output {fall, rise} transition times
+  DevBuf dp_scratch; // design-level power: sums, peak key and index
   // streamed runs: two chunk buffers, a copy stream and its events
   DevBuf chunk_buf[2];
   cudaStream_t copy_stream = nullptr;
@@ -579,7 +580,7 @@ void gtp_destroy(gtp_ctx* ctx) {
   for (auto& kv : ctx->windows) kv.second.release();
   for (DevBuf* b : {&ctx->tab, &ctx->leak, &ctx->cells, &ctx->table_cell, &ctx->leak_cell, &ctx->escale, &ctx->lscale,
                     &ctx->cell, &ctx->load, &ctx->slew, &ctx->desc, &ctx->plan, &ctx->glist, &ctx->gtab, &ctx->gtab_bwd,
-                    &ctx->counters, &ctx->first_bad, &ctx->out_slew,
+                    &ctx->counters, &ctx->first_bad, &ctx->out_slew, &ctx->dp_scratch,
                     &ctx->cell_acc, &ctx->grad, &ctx->gtiles, &ctx->dC_scratch, &ctx->d_err})
     b->release();
   if (ctx->h_err) cudaFreeHost(ctx->h_err);
@@ -760,6 +761,49 @@ int gtp_set_glitch(gtp_ctx* ctx, int64_t clock_ps, const float* out_slew_ps, int
   ctx->N.out_slew = ctx->out_slew.as<float>();
   ctx->N.clock_ps = (int32_t)clock_ps;
   bin_magic((int32_t)clock_ps, &ctx->N.clock_magic, &ctx->N.clock_shift);
+  return GTP_OK;
+}
+
+int gtp_design_power(gtp_ctx* ctx, int32_t window, const double* waveform_w, int flags, double* out) {
+  if (!ctx) return GTP_EINVAL;
+  Window* W = get_window(ctx, window);
+  if (!W || !W->has_result) return fail(ctx, GTP_EINVAL, "design_power: no result for this window");
+  if (!out) return fail(ctx, GTP_EINVAL, "design_power: null output");
+  DeviceGuard dg(ctx->device);
+  const int64_t G = ctx->N.n_gates;
+  const int64_t nb = W->last_bin_ps > 0 ? W->window_ps / W->last_bin_ps : 0;
+  const double* wave = nullptr;
+  if (waveform_w && nb > 0) {
+    if (flags & GTP_DEVICE) {
+      wave = waveform_w;
+    } else {
+      CU(W->wave.reserve(sizeof(double) * (size_t)nb), "alloc waveform");
+      CU(cudaMemcpyAsync(W->wave.p, waveform_w, sizeof(double) * (size_t)nb, cudaMemcpyHostToDevice, ctx->stream),
+         "copy waveform");
+      wave = W->wave.as<double>();
+    }
+  }
+  CU(ctx->dp_scratch.reserve(6 * sizeof(double)), "alloc design power");
+  CU(launch_design_power(W->e_leak.as<double>(), W->e_int.as<double>(), W->e_sw.as<double>(),
+                         W->glitch_result ? W->e_gl.as<double>() : nullptr, G, wave, nb,
+                         ctx->dp_scratch.as<double>(), ctx->stream), "design power");
+  ctx->launches += wave ? 2 : 1;
+  double h[6];
+  CU(cudaMemcpyAsync(h, ctx->dp_scratch.p, sizeof h, cudaMemcpyDeviceToHost, ctx->stream), "read design power");
+  CU(cudaStreamSynchronize(ctx->stream), "design_power");
+  const double to_w = 1e-3 / (double)W->window_ps;  // fJ over the window in ps -> W
+  for (int k = 0; k < 4; ++k) out[k] = h[k] * to_w;
+  out[4] = out[0] + out[1] + out[2] + out[3];
+  unsigned long long idx;
+  memcpy(&idx, h + 5, sizeof idx);
+  if (wave && idx < (unsigned long long)nb) {
+    CU(cudaMemcpyAsync(out + 5, wave + idx, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "read peak");
+    CU(cudaStreamSynchronize(ctx->stream), "design_power");
+    out[6] = (double)idx;
+  } else {
+    out[5] = 0.0;
+    out[6] = -1.0;
+  }
   return GTP_OK;
 }
 

@@ -143,6 +143,15 @@ __device__ __forceinline__ float glitch_ratio(uint32_t width, float sum) {
   return fminf(1.f, x * x);
 }
 
+// The same ratio from a pin's precomputed inv = 2 / (rise + fall), or -1 for
+// a pin without transition time: min(1, (width * inv)^2).
+__device__ __forceinline__ float glitch_inv(float sum) { return sum > 0.f ? 2.f / sum : -1.f; }
+__device__ __forceinline__ float glitch_ratio_inv(uint32_t width, float inv) {
+  if (inv < 0.f) return 1.f;
+  const float x = (float)width * inv;
+  return fminf(1.f, x * x);
+}
+
 // Start of the clock cycle holding t (glitch detection).
 __device__ __forceinline__ uint32_t cycle_start(uint32_t t, int32_t clock_ps, uint32_t magic, uint32_t shift) {
   return bin_of(t, magic, shift, (uint32_t)clock_ps) * (uint32_t)clock_ps;
@@ -221,6 +230,12 @@ cudaError_t launch_merge(const WinDesc* wins, const int64_t* tile_base, int n_wi
 cudaError_t launch_grad_prep(const WinDesc* wins, const float* dLdP, float2* grad, double* tiles, int n_tiles,
                              int n_bins, int bin_ps, float* g_total, cudaStream_t st);
 cudaError_t launch_cells_out(const double* acc, int n_cells, float* d_escale, float* d_lscale, cudaStream_t st);
+// Design-level sums of the per-gate energies and the waveform's peak:
+// scratch[0..3] = sum of e_leak, e_int, e_sw, e_gl (fJ; e_gl may be null),
+// scratch[4] = the peak bin's ordered key, scratch[5] = its first index (as
+// unsigned 64-bit; all ones without a waveform).
+cudaError_t launch_design_power(const double* e_leak, const double* e_int, const double* e_sw, const double* e_gl,
+                                int64_t G, const double* wave, int64_t n_bins, double* scratch, cudaStream_t st);
 // Exact first malformed record of the given windows (see k_validate): *first
 // = ((window << 40 | record) << 3) | -code, or ~0 if every record is valid.
 cudaError_t launch_validate(const LibView& L, const NetView& N, const WinDesc* wins, int n_win,

@@ -515,6 +515,70 @@ cudaError_t launch_validate_if(const LibView& L, const NetView& N, const WinDesc
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ design-level power
+// Key of a double that orders like the value (for an integer atomic max).
+__device__ __forceinline__ unsigned long long ordered_key(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
+// Sums of the per-gate energies (FP64; e_gl may be null) into sums[0..3] and
+// the largest waveform bin's key into *maxkey.
+__global__ void k_design_sums(const double* __restrict__ e_leak, const double* __restrict__ e_int,
+                              const double* __restrict__ e_sw, const double* __restrict__ e_gl, int64_t G,
+                              const double* __restrict__ wave, int64_t n_bins, double* sums,
+                              unsigned long long* maxkey) {
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  unsigned long long mk = 0ull;
+  const int64_t n = G > n_bins ? G : n_bins;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < G) {
+      a[0] += e_leak[i];
+      a[1] += e_int[i];
+      a[2] += e_sw[i];
+      if (e_gl) a[3] += e_gl[i];
+    }
+    if (wave && i < n_bins) mk = max(mk, ordered_key(wave[i]));
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    double v = a[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(sums + k, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) mk = max(mk, __shfl_down_sync(0xffffffffu, mk, o));
+  if ((threadIdx.x & 31) == 0 && wave) atomicMax(maxkey, mk);
+}
+
+// The first bin holding the largest value.
+__global__ void k_peak_index(const double* __restrict__ wave, int64_t n_bins, const unsigned long long* maxkey,
+                             unsigned long long* idx) {
+  const unsigned long long mk = *maxkey;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_bins; i += (int64_t)gridDim.x * blockDim.x)
+    if (ordered_key(wave[i]) == mk) atomicMin(idx, (unsigned long long)i);
+}
+
+cudaError_t launch_design_power(const double* e_leak, const double* e_int, const double* e_sw, const double* e_gl,
+                                int64_t G, const double* wave, int64_t n_bins, double* scratch, cudaStream_t st) {
+  // scratch: [0..3] sums, [4] max key, [5] peak index
+  cudaError_t e = cudaMemsetAsync(scratch, 0, 5 * sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(scratch + 5, 0xFF, sizeof(double), st)) != cudaSuccess) return e;
+  const int64_t n = G > n_bins ? G : n_bins;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(scratch + 4);
+  k_design_sums<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, st>>>(e_leak, e_int, e_sw, e_gl, G, wave, n_bins,
+                                                                      scratch, keys);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (wave && n_bins > 0) {
+    int64_t b2 = (n_bins + 255) / 256;
+    if (b2 > 1024) b2 = 1024;
+    k_peak_index<<<(unsigned)b2, 256, 0, st>>>(wave, n_bins, keys, keys + 1);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cells_out(const double* acc, int n_cells, float* d_escale, float* d_lscale, cudaStream_t st) {
   k_cells_out<<<(n_cells + 255) / 256, 256, 0, st>>>(acc, n_cells, d_escale, d_lscale);
   return cudaGetLastError();

@@ -108,7 +108,7 @@ struct DenseSmem {
   float* dtab;     // adjoint: [kTabEntries] escale * dE/dC
   float* leak;     // [kLeakEntries] leakage per state (forward: scaled)
   uint2* halo;     // [2][2] per staging buffer: the records just before and just after the segment
-  float* gsum;     // glitch detection: [8] rise + fall transition time of each pin
+  float* ginv;     // glitch detection: [8] per pin 2 / (rise + fall transition time), -1 for none
   uint32_t* gprev; // glitch detection: [8][32] per pin and lane, the pin's previous event time + 1 (0: none)
   uint32_t* gtot;  // glitch detection: [8] per pin, the segment's last event time + 1 (medium gates)
   uint32_t* gcarry;// glitch detection: [8] per pin, the gate's last event time + 1 before the segment
@@ -168,12 +168,12 @@ __device__ __forceinline__ DGate dense_gate(const LibView& L, const NetView& N, 
 
 // The gate's energy table and leakage row in the warp's shared memory (TAB:
 // cells of at most kTabMaxIn inputs) and, for glitch detection, each pin's
-// rise + fall transition time (any cell: at most 8 pins).
+// inverse transition time (any cell: at most 8 pins).
 template <bool BWD, bool TAB, bool GL>
 __device__ __forceinline__ void build_tables(const LibView& L, const DGate& d, const DenseSmem& sm, int lane) {
   if (GL && lane <= (int)d.n_in) {
     const float* sl = lane < (int)d.n_in ? d.islew + 2 * lane : d.oslew;
-    sm.gsum[lane] = __ldg(sl) + __ldg(sl + 1);
+    sm.ginv[lane] = glitch_inv(__ldg(sl) + __ldg(sl + 1));
   }
   if (!TAB) return;
   const int ne = (int)((d.n_in + 1u) << (d.n_in + 1u));
@@ -447,7 +447,7 @@ __device__ __forceinline__ SegSums seg_back(const LibView& L, const DGate& d, co
       const uint32_t pv = sm.gprev[pin * 32 + lane];
       sm.gprev[pin * 32 + lane] = t + 1u;
       if (pv != 0u && pv - 1u >= cycle_start(t, d.clk, d.cmagic, d.cshift)) {
-        const float r = glitch_ratio(t - (pv - 1u), sm.gsum[pin]);
+        const float r = glitch_ratio_inv(t - (pv - 1u), sm.ginv[pin]);
         E *= r;
         dE *= r;
         glitch = true;
@@ -715,7 +715,8 @@ struct WalkOut {
 // bin of consecutive events gets one reduction {energy, leakage step} into L2.
 //
 // Glitch detection (GL): `last` is this thread's column (stride
-// kWalkThreads) of each pin's previous event time.
+// kWalkThreads) of each pin's previous event time, followed by a column of
+// each pin's inverse transition time (8 * kWalkThreads further on).
 template <bool BWD, bool GL>
 __device__ __forceinline__ WalkOut walk_gate(const LibView& L, const NetView& N, const WinDesc& W, const float* tabl,
                                              uint2* col, const float* sleak, DevError* err, int64_t g,
@@ -739,8 +740,13 @@ __device__ __forceinline__ WalkOut walk_gate(const LibView& L, const NetView& N,
   float Pg = Pcur;        // leakage before the current group
   uint32_t spre = st;     // state before the current group
   Sums acc;
+  float* ginv = reinterpret_cast<float*>(last + 8 * kWalkThreads);
   if (GL)
-    for (uint32_t p = 0; p <= n_in; ++p) last[p * kWalkThreads] = kNoTime;
+    for (uint32_t p = 0; p <= n_in; ++p) {
+      last[p * kWalkThreads] = kNoTime;
+      const float* sl = p < n_in ? N.slew + ((size_t)g * N.stride + p) * 2 : N.out_slew + 2 * g;
+      ginv[p * kWalkThreads] = glitch_inv(__ldg(sl) + __ldg(sl + 1));
+    }
   float Gcur = 0.f;       // adjoint: G at the last group (G(0) = 0)
   uint32_t tp = 0u;
   uint32_t pb = kNoTime;
@@ -818,8 +824,7 @@ __device__ __forceinline__ WalkOut walk_gate(const LibView& L, const NetView& N,
         const uint32_t t_prev = last[pin * kWalkThreads];
         last[pin * kWalkThreads] = t;
         if (t_prev != kNoTime && t_prev >= cycle_start(t, N.clock_ps, N.clock_magic, N.clock_shift)) {
-          const float* sl = pin < n_in ? N.slew + ((size_t)g * N.stride + pin) * 2 : N.out_slew + 2 * g;
-          const float r = glitch_ratio(t - t_prev, __ldg(sl) + __ldg(sl + 1));
+          const float r = glitch_ratio_inv(t - t_prev, ginv[pin * kWalkThreads]);
           E *= r;
           dE *= r;
           glitch = true;
@@ -899,7 +904,7 @@ __host__ __device__ inline size_t dense_area(int K, bool bwd, bool gl) {
 }
 __host__ __device__ inline size_t sparse_area(int n_leak, bool bwd, bool gl) {
   return (size_t)(bwd ? 2 : 1) * kGateTab * kWalkThreads * sizeof(float) +
-         (size_t)kRounds * kStage * kWalkThreads * sizeof(uint2) + (gl ? (size_t)8 * kWalkThreads * sizeof(uint32_t) : 0) +
+         (size_t)kRounds * kStage * kWalkThreads * sizeof(uint2) + (gl ? (size_t)16 * kWalkThreads * sizeof(uint32_t) : 0) +
          (((size_t)n_leak * sizeof(float) + 15) & ~(size_t)15);
 }
 __host__ __device__ inline size_t union_area(int K, int n_leak, bool bwd, bool gl) {
@@ -942,7 +947,7 @@ __global__ void __launch_bounds__(kWalkThreads, (BWD || GL || K == 16) ? 2 : 3)
   sp += (size_t)kWarps * kLeakEntries * sizeof(float);
   sm.halo = reinterpret_cast<uint2*>(sp) + (size_t)wib * 4;
   sp += (size_t)kWarps * 4 * sizeof(uint2);
-  sm.gsum = reinterpret_cast<float*>(sp) + (size_t)wib * 8;
+  sm.ginv = reinterpret_cast<float*>(sp) + (size_t)wib * 8;
   sp += (size_t)kWarps * 8 * sizeof(float);
   sm.gprev = reinterpret_cast<uint32_t*>(sp) + (size_t)wib * (8 * 32 + 16);
   sm.gtot = sm.gprev + 8 * 32;
@@ -951,7 +956,7 @@ __global__ void __launch_bounds__(kWalkThreads, (BWD || GL || K == 16) ? 2 : 3)
   float* stab = reinterpret_cast<float*>(smem);
   uint2* sstg = reinterpret_cast<uint2*>(stab + (BWD ? 2 : 1) * kGateTab * kWalkThreads);
   uint32_t* slast = reinterpret_cast<uint32_t*>(sstg + kRounds * kStage * kWalkThreads);
-  float* sleak = reinterpret_cast<float*>(slast + (GL ? 8 * kWalkThreads : 0));
+  float* sleak = reinterpret_cast<float*>(slast + (GL ? 16 * kWalkThreads : 0));
   // adjoint cell sums, after the union
   sm.wacc = reinterpret_cast<double*>(smem + union_area(K, L.n_leak, BWD, GL)) + (size_t)wib * 2 * L.n_cells;
   if (BWD)

@@ -29,7 +29,7 @@ ABI_SYMBOLS = ["gtp_create", "gtp_destroy", "gtp_set_stream", "gtp_last_error", 
                "gtp_set_scales", "gtp_load_netlist", "gtp_set_load", "gtp_load_events", "gtp_run_power",
                "gtp_gate_energy", "gtp_run_power_batched", "gtp_run_power_backward", "gtp_autotune",
                "gtp_set_param", "gtp_get_param", "gtp_run_power_noalloc", "gtp_set_glitch", "gtp_gate_glitch",
-               "gtp_run_power_streamed"]
+               "gtp_run_power_streamed", "gtp_design_power"]
 
 
 class GtpError(RuntimeError):
@@ -61,6 +61,7 @@ def load(path: str = LIB_PATH):
         "gtp_set_load": ([P, P, ctypes.c_int], ctypes.c_int),
         "gtp_set_glitch": ([P, I64, P, ctypes.c_int], ctypes.c_int),
         "gtp_gate_glitch": ([P, I32, P, ctypes.c_int], ctypes.c_int),
+        "gtp_design_power": ([P, I32, P, ctypes.c_int, P], ctypes.c_int),
         "gtp_run_power_streamed": ([P, I32, I64, I64, P, P, P, I32, P, I32, ctypes.c_int], ctypes.c_int),
         "gtp_load_events": ([P, I32, I64, I64, P, P, P, ctypes.c_int], ctypes.c_int),
         "gtp_run_power": ([P, I32, I32, P, ctypes.c_int], ctypes.c_int),
@@ -180,6 +181,16 @@ def gtp_run_power_streamed(ctx, window: int, window_ps: int, gate_offsets, event
     n = 0 if events is None else (events.shape[0] if hasattr(events, "shape") else len(events))
     _check(ctx, load().gtp_run_power_streamed(ctx, int(window), int(window_ps), int(n), po, pe, pi, int(bin_ps), pw,
                                               int(n_chunks), fw))
+
+
+def gtp_design_power(ctx, window: int, waveform=None) -> dict:
+    """Design-level power of the window's last run (W): averages of each
+    component over the window, their total, and the waveform's peak."""
+    pw, fw, kw = _ptr_flags(waveform, np.float64)
+    out = np.zeros(7)
+    _check(ctx, load().gtp_design_power(ctx, int(window), pw, fw, out.ctypes.data))
+    return dict(p_leak=out[0], p_int=out[1], p_sw=out[2], p_gl=out[3], p_total=out[4], p_peak=out[5],
+                peak_bin=int(out[6]))
 
 
 def gtp_gate_glitch(ctx, window: int, e_gl) -> None:
@@ -319,6 +330,9 @@ class Engine:
 
     def set_glitch(self, clock_ps: int, out_slew=None) -> None:
         gtp_set_glitch(self.ctx, clock_ps, out_slew)
+
+    def design_power(self, window: int, waveform=None) -> dict:
+        return gtp_design_power(self.ctx, window, waveform)
 
     def gate_glitch(self, window: int, device: bool = True):
         """Per-gate glitch energy (fJ, float64) of the window's last run."""

@@ -180,3 +180,24 @@ def test_glitch_on_a_wide_cell(engine, params):
     ref = oracle.walk(lib, net, tr, 40, glitch=(120, out_slew))
     assert ref["e_gl"][0] > 0
     _check(engine, w, ref, 40)
+
+
+@pytest.mark.parametrize("host_wave", [False, True])
+def test_design_power_matches_oracle(engine, host_wave):
+    lib, net, tr = _hot_case(76)
+    out_slew = np.random.default_rng(76).uniform(5.0, 150.0, (net.n_gates, 2)).astype(np.float32)
+    _setup(engine, lib, net, None)
+    engine.set_glitch(600, out_slew)
+    engine.load_events(0, tr)
+    w = engine.run_power(0, 50)
+    got = engine.design_power(0, w.cpu().numpy() if host_wave else w)
+    ref_r = oracle.walk(lib, net, tr, 50, glitch=(600, out_slew))
+    ref = oracle.design_power(ref_r, tr.window_ps, 50)
+    for k in ("p_leak", "p_int", "p_sw", "p_gl", "p_total"):
+        assert got[k] == pytest.approx(ref[k], rel=1e-6), k
+    want_w = oracle.waveform_w(ref_r["bins"], 50)
+    assert got["p_peak"] == pytest.approx(ref["p_peak"], rel=TOL)
+    assert want_w[got["peak_bin"]] == pytest.approx(ref["p_peak"], rel=2 * TOL)
+    none = engine.design_power(0)
+    assert none["peak_bin"] == -1 and none["p_total"] == pytest.approx(ref["p_total"], rel=1e-6)
+    engine.set_glitch(0)

@@ -154,3 +154,18 @@ def test_adjoint_with_glitches_matches_central_differences():
         e2 = e1.copy()
         e2[c] = 2.0
         assert de[c] == pytest.approx(loss(load_ff=C, escale=e2) - loss(load_ff=C, escale=e1), rel=1e-9, abs=1e-12)
+
+
+def test_design_power_of_the_hand_worked_trace():
+    """Averages over the 2000 ps window (fJ / ps = 1e-3 W) and the peak bin:
+    bin 1 holds 2 + 0.72 fJ of dynamic energy plus 0.001 fJ of leakage."""
+    lib, net, tr, out_slew = _inverter_case()
+    r = oracle.walk(lib, net, tr, 100, glitch=(1000, out_slew))
+    p = oracle.design_power(r, 2000, 100)
+    e_sw = HALF_V2 * 1.0
+    assert p["p_int"] == pytest.approx(4.0 * 1e-3 / 2000)
+    assert p["p_sw"] == pytest.approx(2 * e_sw * 1e-3 / 2000)
+    assert p["p_gl"] == pytest.approx((6.72 + 0.16 * e_sw) * 1e-3 / 2000)
+    assert p["p_leak"] == pytest.approx(10.0 * 2000 * 1e-6 * 1e-3 / 2000)
+    assert p["p_total"] == pytest.approx(p["p_leak"] + p["p_int"] + p["p_sw"] + p["p_gl"])
+    assert p["peak_bin"] == 1 and p["p_peak"] == pytest.approx((2.72 + 0.001) * 1e-3 / 100)
