@@ -1,5 +1,6 @@
 // Work-list planning (the preparation pass and the scatter) and the walk
 // launcher; the walk itself is in gtp_walk_body.cuh.
+#include <algorithm>
 #include <cstdio>
 
 #include "gtp_walk_body.cuh"
@@ -165,26 +166,39 @@ __global__ void __launch_bounds__(256) k_prepare(LibView L, NetView N, const Win
   }
 }
 
+// Each block round places kScatterPer gates per thread, so the bucket
+// cursors see one atomic per bucket per 256 * kScatterPer gates.
+constexpr int kScatterPer = 8;
+
 __global__ void k_plan_scatter(const WinDesc* __restrict__ wins, int64_t seg_len, int dmin, PlanBufs P) {
   extern __shared__ unsigned long long sbase[];  // [0, nb): block bases; then [0, nb) local counts (32-bit)
   const int nb = n_buckets(dmin);
   unsigned int* sh = reinterpret_cast<unsigned int*>(sbase + nb);
   const WinDesc& W = wins[blockIdx.y];
   unsigned long long* cursor = P.counters + kCntHist + nb;
-  for (int64_t base = W.g0 + (int64_t)blockIdx.x * blockDim.x; base < W.g1;
-       base += (int64_t)gridDim.x * blockDim.x) {  // block-uniform: the loop holds barriers
+  const int64_t round = (int64_t)blockDim.x * kScatterPer;
+  for (int64_t base = W.g0 + (int64_t)blockIdx.x * round; base < W.g1;
+       base += (int64_t)gridDim.x * round) {  // block-uniform: the loop holds barriers
     for (int b = threadIdx.x; b < nb; b += blockDim.x) sh[b] = 0u;
     __syncthreads();
-    const int64_t g = base + threadIdx.x;
-    const int64_t c = g < W.g1 ? W.offsets[g + 1] - W.offsets[g] : 0;
-    const int b = c > 0 ? work_bucket(c, dmin, seg_len) : -1;
-    unsigned int local = 0u;
-    if (b >= 0) local = atomicAdd(&sh[b], 1u);
+    int bk[kScatterPer];
+    unsigned int local[kScatterPer];
+#pragma unroll
+    for (int j = 0; j < kScatterPer; ++j) {
+      const int64_t g = base + (int64_t)j * blockDim.x + threadIdx.x;
+      const int64_t c = g < W.g1 ? W.offsets[g + 1] - W.offsets[g] : 0;
+      bk[j] = c > 0 ? work_bucket(c, dmin, seg_len) : -1;
+      local[j] = bk[j] >= 0 ? atomicAdd(&sh[bk[j]], 1u) : 0u;
+    }
     __syncthreads();
     for (int k = threadIdx.x; k < nb; k += blockDim.x)
       if (sh[k]) sbase[k] = atomicAdd(cursor + k, (unsigned long long)sh[k]);
     __syncthreads();
-    if (b >= 0) P.glist[(int64_t)sbase[b] + local] = make_int2((int)blockIdx.y, (int)g);
+#pragma unroll
+    for (int j = 0; j < kScatterPer; ++j)
+      if (bk[j] >= 0)
+        P.glist[(int64_t)sbase[bk[j]] + local[j]] =
+            make_int2((int)blockIdx.y, (int)(base + (int64_t)j * blockDim.x + threadIdx.x));
     __syncthreads();
   }
 }
@@ -197,9 +211,13 @@ int plan_counter_slots(int dense_min) { return kCntHist + 2 * n_buckets(dense_mi
 
 namespace {
 
+// About 1024 blocks in all (at least 4 per window): every block ends with a
+// few same-address atomics (bucket counts, cursors, the done counter, L0),
+// so many windows of small blocks would serialise on them.
 dim3 prepare_grid(const WalkArgs& A) {
   int64_t blocks = (A.n_gates + 255) / 256;
-  if (blocks > 1024) blocks = 1024;
+  const int64_t cap = std::max<int64_t>(4, 1024 / std::max(A.n_win, 1));
+  if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   return dim3((unsigned)blocks, (unsigned)A.n_win);
 }
@@ -229,7 +247,9 @@ cudaError_t launch_plan_scatter(const NetView& N, const WalkArgs& A, cudaStream_
   const size_t scatter_smem = nb * (sizeof(unsigned long long) + sizeof(unsigned int));
   cudaError_t e = cudaFuncSetAttribute(k_plan_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scatter_smem);
   if (e != cudaSuccess) return e;
-  k_plan_scatter<<<prepare_grid(A), 256, scatter_smem, st>>>(A.wins, 32ll * A.rpt, dmin, A.plan);
+  dim3 grid = prepare_grid(A);
+  grid.x = (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid.x, (A.n_gates + 256 * kScatterPer - 1) / (256 * kScatterPer)));
+  k_plan_scatter<<<grid, 256, scatter_smem, st>>>(A.wins, 32ll * A.rpt, dmin, A.plan);
   return cudaGetLastError();
 }
 
