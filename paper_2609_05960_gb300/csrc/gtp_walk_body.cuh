@@ -90,16 +90,12 @@ __device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// Swizzled position (in records) of record k of lane `row` in a warp's
-// staging buffer: 16-byte chunks of a lane's row are XOR-permuted so that
-// both the transposing 8-byte copies and the lanes' 16-byte reads are free of
-// bank conflicts.
-template <int K>
-__device__ __forceinline__ int stage_pos(int row, int k) {
-  constexpr int kShift = K == 16 ? 0 : (K == 8 ? 1 : 2);
-  const int sw = (row >> kShift) & (K / 2 - 1);
-  return row * K + ((((k >> 1) ^ sw) << 1) | (k & 1));
-}
+// Staging layout of a warp's segment: lane `row` owns K consecutive records,
+// and record k of that row sits at word
+//   pos(row, k) = row * K + ((((k >> 1) ^ sw) << 1) | (k & 1)),
+//   sw = (row >> s) & (K/2 - 1),  s = 0, 1, 2 for K = 16, 8, 4:
+// the row's 16-byte pairs are XOR-permuted so that both the transposing
+// 8-byte copies and the lanes' 16-byte reads are free of bank conflicts.
 
 // Per-warp shared memory of the dense walk.
 struct DenseSmem {
@@ -201,9 +197,8 @@ __device__ __forceinline__ void build_tables(const LibView& L, const DGate& d, c
 }
 
 // Word offset of record 0 of lane `row` in a staging buffer: record k of
-// that row sits at row_base ^ k (the identity stage_pos(row, k) ==
-// stage_pos(row, 0) ^ k holds because the swizzle only permutes aligned
-// pairs within the row).
+// that row sits at row_base ^ k (pos(row, k) == pos(row, 0) ^ k, because the
+// swizzle only permutes aligned pairs within the row).
 template <int K>
 __device__ __forceinline__ uint32_t row_base(int row) {
   constexpr int kShift = K == 16 ? 0 : (K == 8 ? 1 : 2);
@@ -214,7 +209,7 @@ __device__ __forceinline__ uint32_t row_base(int row) {
 // its neighbouring records (the gate's record before the segment, if any, and
 // the one after it, if any) into `halo` (one commit group, possibly empty).
 // Lane l copies records m * 32 + l; their swizzled positions are
-// 32 * m + (c0 ^ (((2 * m) & (K/2 - 1)) << 1)) with c0 = stage_pos(l / K, l % K).
+// 32 * m + (c0 ^ (((2 * m) & (K/2 - 1)) << 1)) with c0 = pos(l / K, l % K).
 template <int K>
 __device__ __forceinline__ void issue_segment(const DGate& d, int64_t s, uint2* buf, uint2* halo, int lane) {
   constexpr int SEG = 32 * K;
