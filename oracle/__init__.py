@@ -71,7 +71,7 @@ def _lib():
         P = ctypes.c_void_p
         lib.oracle_walk.restype = ctypes.c_int
         lib.oracle_walk.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int64, P, P, ctypes.c_int64, P,
-                                    P, P, P, P, P, P, P, P]
+                                    P, P, P, P, P, P, P, P, P]
         lib.oracle_adjoint.restype = ctypes.c_int
         lib.oracle_adjoint.argtypes = [P, P, P, ctypes.c_int64, P, ctypes.c_int64, P, P, P, P, P]
         lib.oracle_bilinear.restype = ctypes.c_double
@@ -126,14 +126,15 @@ def _glitch(glitch, keep):
 
 
 def walk(lib, net, trace, bin_ps: int, escale=None, lscale=None, load_ff=None, gates=None,
-         sample_bins=None, waveform: bool = True, glitch=None):
+         sample_bins=None, waveform: bool = True, glitch=None, components: bool = False):
     """Run the FP64 walk.  Returns a dict with ``bins`` (fJ per bin; the
     sampled bins only if ``sample_bins`` is given), ``e_leak``, ``e_int``,
     ``e_sw``, ``e_gl`` (fJ per gate), ``n_events`` and ``final_state``.  With
     ``gates`` the per-gate outputs follow that order (and ``bins`` only
     receive those gates' contributions).  ``glitch`` = (clock_ps, out_slew
     [n_gates][2] {fall, rise} ps) turns on glitch detection; e_gl is 0
-    without it."""
+    without it.  ``components`` adds ``comp_bins`` [4][len(bins)]: the bins
+    split into leakage, internal, switching and glitch energy (fJ)."""
     L, N, T, keep = _structs(lib, net, trace, escale, lscale, load_ff)
     GL = _glitch(glitch, keep)
     n_bins = int(trace.window_ps) // int(bin_ps) if bin_ps > 0 else 0
@@ -150,6 +151,7 @@ def walk(lib, net, trace, bin_ps: int, escale=None, lscale=None, load_ff=None, g
         bins = np.zeros(len(sample_bins), np.float64)
     else:
         bins = np.zeros(max(n_bins, 0), np.float64)
+    comp = np.zeros((4, len(bins)), np.float64) if components else None
     out = {k: np.zeros(n_sel, np.float64) for k in ("e_leak", "e_int", "e_sw", "e_gl")}
     out["n_events"] = np.zeros(n_sel, np.int64)
     out["final_state"] = np.zeros(n_sel, np.uint8)
@@ -163,13 +165,16 @@ def walk(lib, net, trace, bin_ps: int, escale=None, lscale=None, load_ff=None, g
         sample_bins.ctypes.data if sample_bins is not None else nullp,
         out["e_leak"].ctypes.data, out["e_int"].ctypes.data, out["e_sw"].ctypes.data,
         out["n_events"].ctypes.data, out["final_state"].ctypes.data, ctypes.byref(bad),
-        ctypes.byref(GL) if GL is not None else nullp, out["e_gl"].ctypes.data)
+        ctypes.byref(GL) if GL is not None else nullp, out["e_gl"].ctypes.data,
+        comp.ctypes.data if comp is not None else nullp)
     del keep
     if rc == EINVAL:
         raise ValueError("invalid bin size / window")
     if rc != OK:
         raise OracleError(rc, bad.value)
     out["bins"] = bins
+    if comp is not None:
+        out["comp_bins"] = comp
     return out
 
 

@@ -45,8 +45,8 @@ def _tables(lib):
 
 
 def simulate(lib, net, trace, bin_ps: int, escale=None, lscale=None, load_ff=None, glitch=None):
-    """Returns dict(bins[fJ], e_leak, e_int, e_sw, e_gl, n_events,
-    final_state).  glitch = (clock_ps, out_slew[n_gates][2] {fall, rise})."""
+    """Returns dict(bins[fJ], comp_bins[4][n_bins] (leakage, internal,
+    switching, glitch), e_leak, e_int, e_sw, e_gl, n_events, final_state).  glitch = (clock_ps, out_slew[n_gates][2] {fall, rise})."""
     clock, out_slew = glitch if glitch is not None else (0, None)
     T = int(trace.window_ps)
     n_bins = T // bin_ps
@@ -58,6 +58,7 @@ def simulate(lib, net, trace, bin_ps: int, escale=None, lscale=None, load_ff=Non
     tabs, leaks = _tables(lib)
     vdd = float(lib.vdd)
     bins = np.zeros(n_bins)
+    comp = np.zeros((4, n_bins))
     out = dict(e_leak=np.zeros(n_gates), e_int=np.zeros(n_gates), e_sw=np.zeros(n_gates), e_gl=np.zeros(n_gates),
                n_events=np.zeros(n_gates, np.int64), final_state=np.zeros(n_gates, np.uint8))
     for g in range(n_gates):
@@ -97,20 +98,19 @@ def simulate(lib, net, trace, bin_ps: int, escale=None, lscale=None, load_ff=Non
                         E *= 1.0 if rise_fall <= 0 else min(1.0, (2.0 * width / rise_fall) ** 2)
                         is_glitch = True
                     last[pin] = tau
-                if is_glitch:
-                    out["e_gl"][g] += E
-                elif pin < n_in:
-                    out["e_int"][g] += E
-                else:
-                    out["e_sw"][g] += E
+                kind = 3 if is_glitch else (1 if pin < n_in else 2)
+                out[("e_leak", "e_int", "e_sw", "e_gl")[kind]][g] += E
+                comp[kind, tau // bin_ps] += E
                 bins[tau // bin_ps] += E
             for pin, value in at.get(tau, []):
                 bits[pin] = value
             state = sum(v << p for p, v in enumerate(bits))
             e = leaks[(c, state)] * lscale[c] * 1e-6
             bins[tau // bin_ps] += e
+            comp[0, tau // bin_ps] += e
             out["e_leak"][g] += e
         out["n_events"][g] = b - a
         out["final_state"][g] = sum(v << p for p, v in enumerate(bits))
     out["bins"] = bins
+    out["comp_bins"] = comp
     return out

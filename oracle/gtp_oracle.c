@@ -208,6 +208,9 @@ static void bin_add_interval(const binner* B, double P, int64_t a, int64_t b) {
  * bins in `sample`; NULL skips the waveform.  Per-gate outputs may be NULL.
  * On a malformed trace returns a negative code and the offending record
  * index in *bad_record.
+ * comp_bins (optional) receives the same bins split by component, as four
+ * consecutive rows of the bins' length: leakage, internal, switching and
+ * glitch energy (Sec. 2.4: the power components; their sum is `bins`).
  */
 /* Glitch scaling ratio of an event pulse_width ps after the previous event on
  * its pin, for rise + fall transition time sum_slew ps [Eq. glitch scaling
@@ -223,12 +226,18 @@ int oracle_walk(const oracle_lib* L, const oracle_net* N, const oracle_trace* T,
                 int64_t n_sel, const int64_t* gates,
                 double* bins, int64_t n_sample, const int64_t* sample,
                 double* e_leak, double* e_int, double* e_sw, int64_t* n_events, uint8_t* final_state,
-                int64_t* bad_record, const oracle_glitch* GL, double* e_gl) {
+                int64_t* bad_record, const oracle_glitch* GL, double* e_gl, double* comp_bins) {
   if (bin_ps <= 0 || T->window_ps <= 0 || T->window_ps % bin_ps != 0) return OR_EINVAL;
   int64_t* tab_base = (int64_t*)malloc(sizeof(int64_t) * (size_t)L->n_cells);
   int64_t* leak_base = (int64_t*)malloc(sizeof(int64_t) * (size_t)L->n_cells);
   cell_bases(L, tab_base, leak_base);
   binner B = {bin_ps, T->window_ps / bin_ps, bins, n_sample, sample};
+  int64_t n_out = n_sample ? n_sample : T->window_ps / bin_ps;
+  binner BC[4]; /* leakage, internal, switching, glitch */
+  for (int k = 0; k < 4; ++k) {
+    binner x = {bin_ps, T->window_ps / bin_ps, comp_bins ? comp_bins + k * n_out : NULL, n_sample, sample};
+    BC[k] = x;
+  }
   int64_t count = gates ? n_sel : N->n_gates;
   int rc = OR_OK;
   double half_v2 = 0.5 * L->vdd * L->vdd;
@@ -257,6 +266,7 @@ int oracle_walk(const oracle_lib* L, const oracle_net* N, const oracle_trace* T,
       double P = (double)leak[S] * ls;
       El += P * (double)(t - t_prev) * 1e-6;
       bin_add_interval(&B, P, t_prev, t);
+      bin_add_interval(&BC[0], P, t_prev, t);
       /* dynamic energy of each event in the group, at the pre-group state */
       uint32_t S_next = S;
       for (int64_t e = i; e < j; ++e) {
@@ -279,10 +289,13 @@ int oracle_walk(const oracle_lib* L, const oracle_net* N, const oracle_trace* T,
         if (GL && GL->clock_ps > 0 && last_t[pin] >= 0 && last_t[pin] / GL->clock_ps == t / GL->clock_ps) {
           E *= glitch_ratio((double)(t - last_t[pin]), sum_slew);
           Eg += E;
+          bin_add(&BC[3], t, E);
         } else if (pin < n_in) {
           Ei += E;
+          bin_add(&BC[1], t, E);
         } else {
           Es += E;
+          bin_add(&BC[2], t, E);
         }
         last_t[pin] = t;
         bin_add(&B, t, E);
@@ -296,6 +309,7 @@ int oracle_walk(const oracle_lib* L, const oracle_net* N, const oracle_trace* T,
     double P = (double)leak[S] * ls;
     El += P * (double)(T->window_ps - t_prev) * 1e-6;
     bin_add_interval(&B, P, t_prev, T->window_ps);
+    bin_add_interval(&BC[0], P, t_prev, T->window_ps);
     if (e_leak) e_leak[gi] = El;
     if (e_int) e_int[gi] = Ei;
     if (e_sw) e_sw[gi] = Es;
