@@ -357,6 +357,8 @@ def run_ours(args, cfg_name):
     extras = {}
     if rank == 0 and not args.no_extras and cfg_name == "large" and not args.events:
         extras["glitch"] = measure_glitch(eng, dev, cfg, wave, walk_s * 1e3, n_ev, max(3, min(args.steps // 10, 10)))
+        extras["components"] = measure_components(eng, dev, cfg, walk_s * 1e3, n_ev,
+                                                  max(3, min(args.steps // 10, 10)))
         extras["batched"] = measure_batched(eng, dev, max(3, min(args.steps // 10, 10)))
         extras["adjoint"] = measure_adjoint(eng, dev, max(3, min(args.steps // 10, 10)))
 
@@ -471,6 +473,31 @@ def measure_glitch(eng, dev, cfg, wave, walk_plain_ms, n_ev, steps):
             "walk_over_plain": walk_ms / walk_plain_ms,
             "glitch_share_of_dynamic_energy": float(e_gl.sum()) / dyn if dyn > 0 else 0.0,
             "out_slew": "uniform 10-200 ps per gate and edge, seed 7"}
+
+
+def measure_components(eng, dev, cfg, walk_plain_ms, n_ev, steps):
+    """The same window (slot 0) with the per-component waveforms (leakage,
+    internal, switching, glitch rows, on the device) as well as the total:
+    run time, and walk time against the plain walk."""
+    import torch
+
+    from paper_2609_05960_gb300 import gtpower
+
+    nb = cfg.window_ps // cfg.bin_ps
+    comp = torch.empty((4, nb), dtype=torch.float64, device=dev)
+    total = torch.empty(nb, dtype=torch.float64, device=dev)
+    run = lambda: gtpower.gtp_run_power_components(eng.ctx, 0, cfg.bin_ps, comp, total)
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize(dev)
+    eng.set_param("timing", 1)
+    ms = _events_per_s(run, steps, dev)
+    n_t = max(eng.get_param("n_timed"), 1)
+    walk_ms = eng.get_param("t_walk_ns") * 1e-6 / n_t
+    eng.set_param("timing", 0)
+    rel = float(((comp.sum(0) - total).abs() / total.abs()).max())
+    return {"ms_per_run": ms, "value": n_ev / (ms * 1e-3), "unit": UNIT, "walk_ms": walk_ms,
+            "walk_over_plain": walk_ms / walk_plain_ms, "max_rel_sum_of_components_vs_total": rel}
 
 
 def measure_adjoint(eng, dev, steps):

@@ -212,6 +212,24 @@ int gtp_load_events(gtp_ctx* ctx, int32_t window, int64_t window_ps, int64_t n_e
 int gtp_run_power(gtp_ctx* ctx, int32_t window, int32_t bin_ps, double* waveform_w, int flags);
 
 /*
+ * gtp_run_power that also returns the waveform of each power component
+ * [Sec. 2.4: leakage, internal, switching and glitch power; Sec. 2.4.1 for
+ * the glitch component, which is zero unless gtp_set_glitch set a clock].
+ *   components_w [4][n_bins] (FP64, W), component-major: row 0 leakage, row 1
+ *     internal (input-pin events that are not glitches), row 2 switching
+ *     (output-pin events that are not glitches), row 3 glitch energy.  Each
+ *     bin is that component's energy in the bin divided by bin_ps; the four
+ *     rows add up to waveform_w up to FP32 rounding.  Required.
+ *   waveform_w [n_bins] or NULL: the total, as gtp_run_power writes it.
+ * The walk keeps one more 16-byte accumulator per bin and issues one more
+ * reduction per bin update, so it costs more than gtp_run_power.  Per-gate
+ * results are kept as for gtp_run_power.  flags: GTP_HOST or GTP_DEVICE for
+ * both outputs; GTP_GRAPH is rejected (GTP_EINVAL).  Errors as gtp_run_power.
+ */
+int gtp_run_power_components(gtp_ctx* ctx, int32_t window, int32_t bin_ps, double* waveform_w,
+                             double* components_w, int flags);
+
+/*
  * One window run straight from host memory, in chunks [Sec. 5, event
  * chunking with the packing and copy of the next chunk overlapping the
  * kernel]: the window's records are copied to the GPU in n_chunks gate-range

@@ -48,13 +48,15 @@ struct Window {
   DevBuf offsets, records, init;
   const uint2* borrowed = nullptr;
   DevBuf e_leak, e_int, e_sw, e_gl, final_state, bins, tiles, wave;
+  DevBuf cbins, cwave;  // per-component runs: component accumulators and the host-bound waveforms
   bool has_result = false;
   bool glitch_result = false;  // the last run detected glitches (e_gl holds them)
   bool streamed = false;       // filled by a streamed run: results only, no resident records
   int32_t last_bin_ps = 0;
   const uint2* rec() const { return borrowed ? borrowed : records.as<uint2>(); }
   void release() {
-    for (DevBuf* b : {&offsets, &records, &init, &e_leak, &e_int, &e_sw, &e_gl, &final_state, &bins, &tiles, &wave})
+    for (DevBuf* b : {&offsets, &records, &init, &e_leak, &e_int, &e_sw, &e_gl, &final_state, &bins, &tiles, &wave,
+                      &cbins, &cwave})
       b->release();
     borrowed = nullptr;
     loaded = false;
@@ -251,7 +253,8 @@ int64_t seg_len_of(const gtp_ctx* ctx) { return 32 * ctx->p_rpt; }
 // Fill the descriptor table of a run in the pinned staging buffer, reserving
 // the windows' device buffers.  The upload is enqueued by upload_plan().
 int build_plan(gtp_ctx* ctx, const std::vector<Window*>& ws, int32_t bin_ps, const std::vector<double*>& waves,
-               bool backward, int64_t* n_seg_total, int64_t* n_tiles_total) {
+               bool backward, int64_t* n_seg_total, int64_t* n_tiles_total,
+               const std::vector<double*>* cwaves = nullptr) {
   const int n = (int)ws.size();
   if (n <= 0 || n > kMaxWindows) return fail(ctx, GTP_EINVAL, "between 1 and 1024 windows per run");
   WinDesc* hw = plan_wins(ctx->h_plan);
@@ -284,6 +287,13 @@ int build_plan(gtp_ctx* ctx, const std::vector<Window*>& ws, int32_t bin_ps, con
     d.e_gl = ctx->N.clock_ps > 0 ? W.e_gl.as<double>() : nullptr;
     d.final_state = W.final_state.as<uint8_t>();
     d.bins = W.bins.as<float2>();
+    d.cbins = nullptr;
+    d.cwave = nullptr;
+    if (cwaves && (*cwaves)[i]) {
+      CU(W.cbins.reserve(sizeof(float4) * nb), "alloc component bins");
+      d.cbins = W.cbins.as<float4>();
+      d.cwave = (*cwaves)[i];
+    }
     d.l0 = dl0 + i;
     d.tiles = W.tiles.as<double>();
     d.wave = waves.empty() ? nullptr : waves[i];
@@ -366,12 +376,13 @@ void collect_timing(gtp_ctx* ctx) {
 
 // Enqueue the forward pass of the planned windows (no synchronisation).
 int enqueue_forward(gtp_ctx* ctx, int n, int64_t n_seg_total, int64_t n_tiles_total, bool any_events,
-                    cudaStream_t st) {
+                    cudaStream_t st, bool comp = false) {
   const WinDesc* dw = plan_wins(ctx->plan.p);
   const int64_t* tile_base = plan_tile_base(ctx->plan.p);
   RC(upload_plan(ctx, n, st));
   CU(cudaMemsetAsync(plan_l0(ctx->plan.p), 0, sizeof(double) * n, st), "zero l0");
-  const WalkArgs A = walk_args(ctx, n);
+  WalkArgs A = walk_args(ctx, n);
+  A.comp = comp;
   const bool fused = any_events && ctx->p_kernel != 1;
   mark(ctx, 0, st);
   CU(launch_prepare(ctx->L, ctx->N, A, fused, st), "prepare");
@@ -461,7 +472,7 @@ __global__ void k_counts(const int64_t* off, int64_t n, int64_t* out) {
 
 // Forward run of a window list; waveforms per window (device or host).
 int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, double* const* waveforms, int flags,
-                bool use_graph) {
+                bool use_graph, double* const* components = nullptr) {
   if (!ctx->net_loaded) return fail(ctx, GTP_EINVAL, "run_power: load the library, netlist and events first");
   std::vector<Window*> ws(n);
   bool any_events = false;
@@ -483,9 +494,22 @@ int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, dou
       waves[i] = ws[i]->wave.as<double>();
     }
   }
+  std::vector<double*> cwaves(n, nullptr);
+  if (components) {
+    use_graph = false;
+    for (int i = 0; i < n; ++i) {
+      if (!components[i]) continue;
+      if (flags & GTP_DEVICE) {
+        cwaves[i] = components[i];
+      } else {
+        CU(ws[i]->cwave.reserve(4 * sizeof(double) * (size_t)(ws[i]->window_ps / bin_ps)), "alloc components");
+        cwaves[i] = ws[i]->cwave.as<double>();
+      }
+    }
+  }
   int64_t n_seg_total = 0, n_tiles_total = 0;
   RC(ensure_gate_tables(ctx, false));
-  RC(build_plan(ctx, ws, bin_ps, waves, false, &n_seg_total, &n_tiles_total));
+  RC(build_plan(ctx, ws, bin_ps, waves, false, &n_seg_total, &n_tiles_total, components ? &cwaves : nullptr));
   CU(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(DevError), ctx->stream), "zero status");
   if (use_graph) {
     const GraphKey key{std::vector<int32_t>(windows, windows + n), bin_ps, ctx->p_rpt,
@@ -515,13 +539,19 @@ int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, dou
     CU(cudaGraphLaunch(it->second, ctx->stream), "graph launch");
     ctx->launches += any_events ? (ctx->p_kernel == 1 ? 5 : 6) : 4;
   } else {
-    RC(enqueue_forward(ctx, n, n_seg_total, n_tiles_total, any_events, ctx->stream));
+    RC(enqueue_forward(ctx, n, n_seg_total, n_tiles_total, any_events, ctx->stream, components != nullptr));
   }
   if (waveforms && !(flags & GTP_DEVICE)) {
     for (int i = 0; i < n; ++i)
       if (waveforms[i])
         CU(cudaMemcpyAsync(waveforms[i], waves[i], sizeof(double) * (size_t)(ws[i]->window_ps / bin_ps),
                            cudaMemcpyDeviceToHost, ctx->stream), "copy waveform");
+  }
+  if (components && !(flags & GTP_DEVICE)) {
+    for (int i = 0; i < n; ++i)
+      if (components[i])
+        CU(cudaMemcpyAsync(components[i], cwaves[i], 4 * sizeof(double) * (size_t)(ws[i]->window_ps / bin_ps),
+                           cudaMemcpyDeviceToHost, ctx->stream), "copy components");
   }
   const int rc = check_walk_error(ctx, n, windows, "run_power");
   collect_timing(ctx);
@@ -891,6 +921,17 @@ int gtp_run_power(gtp_ctx* ctx, int32_t window, int32_t bin_ps, double* waveform
   DeviceGuard dg(ctx->device);
   double* const waves[1] = {waveform_w};
   return run_forward(ctx, &window, 1, bin_ps, waves, flags, (flags & GTP_GRAPH) != 0);
+}
+
+int gtp_run_power_components(gtp_ctx* ctx, int32_t window, int32_t bin_ps, double* waveform_w,
+                             double* components_w, int flags) {
+  if (!ctx) return GTP_EINVAL;
+  if (!components_w) return fail(ctx, GTP_EINVAL, "run_power_components: components_w is required");
+  if (flags & GTP_GRAPH) return fail(ctx, GTP_EINVAL, "run_power_components: no graph replay");
+  DeviceGuard dg(ctx->device);
+  double* const waves[1] = {waveform_w};
+  double* const comps[1] = {components_w};
+  return run_forward(ctx, &window, 1, bin_ps, waves, flags, false, comps);
 }
 
 int gtp_run_power_batched(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_t bin_ps,

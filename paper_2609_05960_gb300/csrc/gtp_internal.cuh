@@ -94,6 +94,9 @@ struct WinDesc {
   double* e_gl;              // [G] glitch energy, or null without glitch detection
   uint8_t* final_state;      // [G]
   float2* bins;              // [n_bins] accumulators
+  float4* cbins;             // [n_bins] component accumulators {internal, switching, glitch fJ, leakage in-bin
+                             // corrections fJ}, or null (no per-component waveform)
+  double* cwave;             // [4][n_bins] component waveforms (W): leakage, internal, switching, glitch, or null
   double* l0;                // sum over gates of P_leak(initial state), nW
   double* tiles;             // merge scratch
   double* wave;              // [n_bins] output waveform (W), or null
@@ -161,6 +164,13 @@ __device__ __forceinline__ uint32_t cycle_start(uint32_t t, int32_t clock_ps, ui
 __device__ __forceinline__ void red_bin(float2* bins, uint32_t b, float e, float dp) {
   float2* p = bins + b;
   asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(e), "f"(dp) : "memory");
+}
+
+// The same for a bin's component accumulators (one 16-byte reduction).
+__device__ __forceinline__ void red_cbin(float4* cbins, uint32_t b, float ei, float es, float eg, float lc) {
+  float4* p = cbins + b;
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(ei), "f"(es), "f"(eg), "f"(lc)
+               : "memory");
 }
 
 // Kahan-compensated FP32 accumulator.

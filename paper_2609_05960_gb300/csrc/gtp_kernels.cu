@@ -195,6 +195,7 @@ __global__ void k_walk_per_gate(LibView L, NetView N, const WinDesc* __restrict_
     float P = leak[st];
     int32_t t_prev = 0;
     Kahan El, Ei, Es, Eg;
+    float4* const cb = W.cbins;
     uint32_t last[8];  // glitch detection: each pin's previous event time
     for (int p = 0; p < 8; ++p) last[p] = 0xFFFFFFFFu;
     bool bad = false;
@@ -206,7 +207,7 @@ __global__ void k_walk_per_gate(LibView L, NetView N, const WinDesc* __restrict_
       El.add(P * (float)(t - t_prev) * 1e-6f);
       const uint32_t bin = bin_of((uint32_t)t, W.bin_magic, W.bin_shift, (uint32_t)W.bin_ps);
       uint32_t s_next = st;
-      float e_bin = 0.f;
+      float e_bin = 0.f, c_int = 0.f, c_sw = 0.f, c_gl = 0.f;
       int64_t j = i;
       for (; j < b; ++j) {
         const uint2 r = W.rec[j];
@@ -237,9 +238,16 @@ __global__ void k_walk_per_gate(LibView L, NetView N, const WinDesc* __restrict_
             glitch = true;
           }
         }
-        if (glitch) Eg.add(E);
-        else if (pin < n_in) Ei.add(E);
-        else Es.add(E);
+        if (glitch) {
+          Eg.add(E);
+          c_gl += E;
+        } else if (pin < n_in) {
+          Ei.add(E);
+          c_int += E;
+        } else {
+          Es.add(E);
+          c_sw += E;
+        }
         e_bin += E;
       }
       if (bad) break;
@@ -247,6 +255,7 @@ __global__ void k_walk_per_gate(LibView L, NetView N, const WinDesc* __restrict_
       const float dP = P_new - P;
       const float frac = (float)((int32_t)(bin + 1u) * W.bin_ps - t);
       red_bin(W.bins, bin, e_bin + dP * frac * 1e-6f, dP);
+      if (cb) red_cbin(cb, bin, c_int, c_sw, c_gl, dP * frac * 1e-6f);
       st = s_next;
       P = P_new;
       t_prev = t;
@@ -382,15 +391,31 @@ __global__ void k_finalize(const WinDesc* __restrict__ wins, const int64_t* __re
   }
   __shared__ double tot;
   const double pre = block_excl_scan((double)s, &tot) + W.tiles[tile] + *W.l0;
-  if (W.wave == nullptr) return;
   // W per bin: E (fJ) * 1e-3 / bin_ps + P (nW) * 1e-9
   const float to_w = (float)(1e-3 / (double)W.bin_ps);
   const double p0 = pre * 1e-9;
-  float dp = 0.f;
+  if (W.wave) {
+    float dp = 0.f;
 #pragma unroll
-  for (int k = 0; k < kMergePer; ++k) {
-    if (base + k < W.n_bins) W.wave[base + k] = (double)fmaf(v[k].x, to_w, dp * 1e-9f) + p0;
-    dp += v[k].y;
+    for (int k = 0; k < kMergePer; ++k) {
+      if (base + k < W.n_bins) W.wave[base + k] = (double)fmaf(v[k].x, to_w, dp * 1e-9f) + p0;
+      dp += v[k].y;
+    }
+  }
+  if (W.cwave) {  // components: the leakage is the step prefix plus its in-bin corrections
+    const int64_t nb = W.n_bins;
+    float dp = 0.f;
+#pragma unroll
+    for (int k = 0; k < kMergePer; ++k) {
+      if (base + k < W.n_bins) {
+        const float4 c = W.cbins[base + k];
+        W.cwave[base + k] = (double)fmaf(c.w, to_w, dp * 1e-9f) + p0;
+        W.cwave[nb + base + k] = (double)(c.x * to_w);
+        W.cwave[2 * nb + base + k] = (double)(c.y * to_w);
+        W.cwave[3 * nb + base + k] = (double)(c.z * to_w);
+      }
+      dp += v[k].y;
+    }
   }
 }
 

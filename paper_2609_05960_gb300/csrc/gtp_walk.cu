@@ -115,6 +115,8 @@ __global__ void __launch_bounds__(256) k_prepare(LibView L, NetView N, const Win
     const int64_t n4 = (int64_t)W.n_bins >> 1;
     for (int64_t i = tid; i < n4; i += stride) b4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (tid == 0 && (W.n_bins & 1)) W.bins[W.n_bins - 1] = make_float2(0.f, 0.f);
+    if (W.cbins)
+      for (int64_t i = tid; i < W.n_bins; i += stride) W.cbins[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   double p0 = 0.0;
   for (int64_t g = W.g0 + tid; g < W.g1; g += stride) {
@@ -260,6 +262,7 @@ cudaError_t launch_plan(const NetView& N, const LibView& L, const WalkArgs& A, c
 }
 
 cudaError_t launch_walk(const LibView& L, const NetView& N, const WalkArgs& A, bool backward, cudaStream_t st) {
+  if (!backward && A.comp) return launch_walk_components(L, N, A, st);
   if (N.clock_ps > 0) return launch_walk_glitch(L, N, A, backward, st);
   return launch_walk_gl<false>(L, N, A, backward, st);
 }

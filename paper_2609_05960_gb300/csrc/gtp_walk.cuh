@@ -44,6 +44,7 @@ struct WalkArgs {
   const float* gtab_bwd;    // adjoint gate tables [G][2 * kGateTab] (adjoint runs only)
   PlanBufs plan;
   int64_t n_gates;
+  bool comp;                // forward: also accumulate every window's component bins (WinDesc::cbins)
 };
 
 bool walk_rpt_supported(int rpt);
@@ -61,6 +62,9 @@ cudaError_t launch_plan(const NetView& N, const LibView& L, const WalkArgs& A, c
 cudaError_t launch_walk(const LibView& L, const NetView& N, const WalkArgs& A, bool backward, cudaStream_t st);
 // The walk with glitch detection (N.clock_ps > 0), in its own translation unit.
 cudaError_t launch_walk_glitch(const LibView& L, const NetView& N, const WalkArgs& A, bool backward, cudaStream_t st);
+// The forward walk (with or without glitch detection) that also accumulates
+// each window's component bins (WinDesc::cbins), in its own translation unit.
+cudaError_t launch_walk_components(const LibView& L, const NetView& N, const WalkArgs& A, cudaStream_t st);
 cudaError_t launch_gate_tables(const LibView& L, const NetView& N, float* gtab, float* gtab_bwd, cudaStream_t st);
 
 }  // namespace gtp

@@ -313,6 +313,17 @@ __device__ __forceinline__ void red_bin_if(bool p, float2* bins, uint32_t b, flo
       : "memory");
 }
 
+// The same for the bin's component accumulators {internal, switching,
+// glitch, leakage in-bin correction}.
+__device__ __forceinline__ void red_cbin_if(bool p, float4* cbins, uint32_t b, float ei, float es, float eg,
+                                            float lc) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %5, 0;\n\t@q red.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n\t}" ::"l"(
+          cbins + b),
+      "f"(ei), "f"(es), "f"(eg), "f"(lc), "r"((uint32_t)p)
+      : "memory");
+}
+
 // Bin of t (as bin_of) and the end of that bin in ps.
 __device__ __forceinline__ uint32_t bin_end_of(uint32_t t, const DGate& d, uint32_t& end) {
   uint32_t b = __umulhi(t, d.magic) >> d.shift;
@@ -360,7 +371,7 @@ __device__ __forceinline__ void gl_segment_scan(const DGate& d, const uint2* buf
   }
 }
 
-template <int K, bool BWD, bool TAB, bool FULL, bool GL>
+template <int K, bool BWD, bool TAB, bool FULL, bool GL, bool CMP>
 __device__ __forceinline__ SegSums seg_back(const LibView& L, const DGate& d, const DenseSmem& sm, const uint2* buf,
                                             const Seg& q, uint32_t seg_in, DevError* err, int lane) {
   SegSums out{0.f, 0.f, 0.f, 0.f};
@@ -394,6 +405,7 @@ __device__ __forceinline__ SegSums seg_back(const LibView& L, const DGate& d, co
   uint2 r = buf[rb];                       // the lane's next record
   uint32_t pb = bin_of(r.x, d.magic, d.shift, d.bin_ps);  // pending bin (garbage for a lane without events)
   float pe = 0.f, pdp = 0.f;
+  float pi = 0.f, ps = 0.f, pg = 0.f, pc = 0.f;  // CMP: the pending bin's components
   uint32_t tog = 1u;                       // bit 0 clears on an event that does not toggle its pin
   uint32_t tp = q.t_before;
   auto event = [&](int k, uint32_t t, uint32_t m, uint32_t tn) {
@@ -465,6 +477,13 @@ __device__ __forceinline__ SegSums seg_back(const LibView& L, const DGate& d, co
       const float add = dp * (float)(int32_t)(bend - t) * 1e-6f;
       const bool nb = bn != pb;
       red_bin_if(nb, d.W->bins, pb, pe, pdp);
+      if (CMP) {
+        red_cbin_if(nb, d.W->cbins, pb, pi, ps, pg, pc);
+        pi = (nb ? 0.f : pi) + (Er - Eo);
+        ps = (nb ? 0.f : ps) + Eo;
+        pg = (nb ? 0.f : pg) + Eg;
+        pc = (nb ? 0.f : pc) + add;
+      }
       pe = (nb ? 0.f : pe) + (E + add);
       pdp = (nb ? 0.f : pdp) + dp;
       pb = bn;
@@ -478,7 +497,10 @@ __device__ __forceinline__ SegSums seg_back(const LibView& L, const DGate& d, co
     if (k + 1 < K) r = buf[rb ^ (uint32_t)(k + 1)];
     event(k, t, m, (k + 1 < K && (FULL || k + 1 < q.nk)) ? r.x : q.t_after);
   }
-  if (!BWD && (FULL || q.nk > 0)) red_bin(d.W->bins, pb, pe, pdp);
+  if (!BWD && (FULL || q.nk > 0)) {
+    red_bin(d.W->bins, pb, pe, pdp);
+    if (CMP) red_cbin(d.W->cbins, pb, pi, ps, pg, pc);
+  }
   if (!(tog & 1u)) report_error(err, GTP_ENOTOGGLE, q.s0 + lane * K);  // located exactly by the host
   // gate end: leakage to the window end and the final state
   if (q.last_seg && q.nk > 0 && lane * K + q.nk == q.n_rem) {
@@ -541,7 +563,7 @@ __device__ __forceinline__ void store_gate(const LibView& L, const DGate& d, con
 }
 
 // A medium gate, walked by one warp segment by segment.
-template <int K, bool BWD, bool TAB, bool GL>
+template <int K, bool BWD, bool TAB, bool GL, bool CMP>
 __device__ __forceinline__ void medium_gate(const LibView& L, const DGate& d, const DenseSmem& sm, DevError* err,
                                             int lane) {
   constexpr int SEG = 32 * K;
@@ -570,9 +592,9 @@ __device__ __forceinline__ void medium_gate(const LibView& L, const DGate& d, co
       if (lane <= (int)d.n_in) sm.gcarry[lane] = max(sm.gcarry[lane], sm.gtot[lane]);
     }
     if (full) {
-      acc.add(seg_back<K, BWD, TAB, true, GL>(L, d, sm, cur, q, carry, err, lane), GL);
+      acc.add(seg_back<K, BWD, TAB, true, GL, CMP>(L, d, sm, cur, q, carry, err, lane), GL);
     } else {
-      acc.add(seg_back<K, BWD, TAB, false, GL>(L, d, sm, cur, q, carry, err, lane), GL);
+      acc.add(seg_back<K, BWD, TAB, false, GL, CMP>(L, d, sm, cur, q, carry, err, lane), GL);
     }
     carry = xcompose(carry, tx);
     __syncwarp();
@@ -584,7 +606,7 @@ __device__ __forceinline__ void medium_gate(const LibView& L, const DGate& d, co
 // A big gate, walked by the CTA's 8 warps in chunks of 8 consecutive
 // segments; the state entering each segment is the carry into the chunk
 // composed with the transfers of the chunk's earlier segments.
-template <int K, bool BWD, bool TAB, bool GL>
+template <int K, bool BWD, bool TAB, bool GL, bool CMP>
 __device__ __forceinline__ void big_gate(const LibView& L, const DGate& d, const DenseSmem& sm, DevError* err,
                                          uint32_t (*xfer)[kWarps], uint32_t (*gx)[kWarps][8], double (*red)[4],
                                          int wib, int lane) {
@@ -633,8 +655,8 @@ __device__ __forceinline__ void big_gate(const LibView& L, const DGate& d, const
       if (v == wib) seg_in = carry;
       carry = xcompose(carry, x);
     }
-    acc.add(full ? seg_back<K, BWD, TAB, true, GL>(L, d, sm, cur, q, seg_in, err, lane)
-                 : seg_back<K, BWD, TAB, false, GL>(L, d, sm, cur, q, seg_in, err, lane), GL);
+    acc.add(full ? seg_back<K, BWD, TAB, true, GL, CMP>(L, d, sm, cur, q, seg_in, err, lane)
+                 : seg_back<K, BWD, TAB, false, GL, CMP>(L, d, sm, cur, q, seg_in, err, lane), GL);
     __syncwarp();
   }
   acc.flush(GL);
@@ -712,7 +734,7 @@ struct WalkOut {
 // Glitch detection (GL): `last` is this thread's column (stride
 // kWalkThreads) of each pin's previous event time, followed by a column of
 // each pin's inverse transition time (8 * kWalkThreads further on).
-template <bool BWD, bool GL>
+template <bool BWD, bool GL, bool CMP>
 __device__ __forceinline__ WalkOut walk_gate(const LibView& L, const NetView& N, const WinDesc& W, const float* tabl,
                                              uint2* col, const float* sleak, DevError* err, int64_t g,
                                              const uint2* __restrict__ rec_g, uint32_t n, uint32_t st,
@@ -746,6 +768,7 @@ __device__ __forceinline__ WalkOut walk_gate(const LibView& L, const NetView& N,
   uint32_t tp = 0u;
   uint32_t pb = kNoTime;
   float pe = 0.f, pdp = 0.f;
+  float pi = 0.f, ps = 0.f, pg = 0.f, pc = 0.f;  // CMP: the pending bin's components
   bool live = true, bad = false, first = true;
   uint32_t u = 0u;  // first event of the current round
   int slot = 0, n_done = 0;
@@ -835,13 +858,21 @@ __device__ __forceinline__ WalkOut walk_gate(const LibView& L, const NetView& N,
         const float dp = tail ? Pn - Pg : 0.f;
         const float add = dp * (float)(int32_t)((bn + 1u) * bin_ps - t) * 1e-6f;
         if (bn != pb) {
-          if (pb != kNoTime) red_bin(W.bins, pb, pe, pdp);
+          if (pb != kNoTime) {
+            red_bin(W.bins, pb, pe, pdp);
+            if (CMP) red_cbin(W.cbins, pb, pi, ps, pg, pc);
+          }
           pb = bn;
           pe = 0.f;
           pdp = 0.f;
+          pi = ps = pg = pc = 0.f;
         }
         pe += E + add;
         pdp += dp;
+        if (CMP) {
+          if (GL && glitch) pg += E; else if (is_out) ps += E; else pi += E;
+          pc += add;
+        }
       }
       Pcur = tail ? Pn : Pcur;
       tp = t;
@@ -857,7 +888,10 @@ __device__ __forceinline__ WalkOut walk_gate(const LibView& L, const NetView& N,
     }
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");
-  if (!BWD && pb != kNoTime) red_bin(W.bins, pb, pe, pdp);
+  if (!BWD && pb != kNoTime) {
+    red_bin(W.bins, pb, pe, pdp);
+    if (CMP) red_cbin(W.cbins, pb, pi, ps, pg, pc);
+  }
   // the gate's end: leakage to the window end, and the final state
   if (!bad) {
     if (BWD) {
@@ -915,8 +949,8 @@ __host__ __device__ inline size_t union_area(int K, int n_leak, bool bwd, bool g
 // larger tables allow only two CTAs per SM: these are given the registers of
 // two (measured on the large workload: 16 records per lane at two CTAs
 // 1.18 ms, at three 1.38 ms).
-template <int K, bool BWD, bool GL>
-__global__ void __launch_bounds__(kWalkThreads, (BWD || GL || K == 16) ? 2 : 3)
+template <int K, bool BWD, bool GL, bool CMP>
+__global__ void __launch_bounds__(kWalkThreads, (BWD || GL || CMP || K == 16) ? 2 : 3)
     k_walk(LibView L, NetView N, WalkArgs A) {
   constexpr int SEG = 32 * K;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -978,14 +1012,14 @@ __global__ void __launch_bounds__(kWalkThreads, (BWD || GL || K == 16) ? 2 : 3)
     const int64_t item = is_dense ? dense_before : n_dense_items + (pos - dense_before);
     if (item < n_big) {
       const DGate d = dense_gate<BWD, GL>(L, N, wins, P.glist[item]);
-      if (d.n_in <= (uint32_t)kTabMaxIn) big_gate<K, BWD, true, GL>(L, d, sm, err, xfer, gx, red, wib, lane);
-      else big_gate<K, BWD, false, GL>(L, d, sm, err, xfer, gx, red, wib, lane);
+      if (d.n_in <= (uint32_t)kTabMaxIn) big_gate<K, BWD, true, GL, CMP>(L, d, sm, err, xfer, gx, red, wib, lane);
+      else big_gate<K, BWD, false, GL, CMP>(L, d, sm, err, xfer, gx, red, wib, lane);
     } else if (item < n_dense_items) {
       const int64_t i = (item - n_big) * kWarps + wib;
       if (i < n_med) {
         const DGate d = dense_gate<BWD, GL>(L, N, wins, P.glist[n_big + i]);
-        if (d.n_in <= (uint32_t)kTabMaxIn) medium_gate<K, BWD, true, GL>(L, d, sm, err, lane);
-        else medium_gate<K, BWD, false, GL>(L, d, sm, err, lane);
+        if (d.n_in <= (uint32_t)kTabMaxIn) medium_gate<K, BWD, true, GL, CMP>(L, d, sm, err, lane);
+        else medium_gate<K, BWD, false, GL, CMP>(L, d, sm, err, lane);
       }
     } else {
       // ---- 256 sparse gates, one per thread
@@ -1000,7 +1034,7 @@ __global__ void __launch_bounds__(kWalkThreads, (BWD || GL || K == 16) ? 2 : 3)
         const int64_t ga = W.offsets[g], ge = W.offsets[g + 1];
         float* my_tab = stab + threadIdx.x;
         if (L.cells[N.cell[g]].n_in <= kGateTabMaxIn) stage_gate_table<BWD>(gt, g, my_tab);
-        const WalkOut o = walk_gate<BWD, GL>(L, N, W, my_tab, sstg + threadIdx.x, sleak, err, g, W.rec + ga,
+        const WalkOut o = walk_gate<BWD, GL, CMP>(L, N, W, my_tab, sstg + threadIdx.x, sleak, err, g, W.rec + ga,
                                              (uint32_t)(ge - ga), (uint32_t)W.init[g], slast + threadIdx.x);
         if (BWD) {
           W.dC[g] = (float)o.v0;
@@ -1024,20 +1058,21 @@ __global__ void __launch_bounds__(kWalkThreads, (BWD || GL || K == 16) ? 2 : 3)
 }
 
 // ------------------------------------------------------------------ launchers
-template <int K, bool BWD, bool GL>
+template <int K, bool BWD, bool GL, bool CMP>
 cudaError_t launch_walk_k(const LibView& L, const NetView& N, const WalkArgs& A, cudaStream_t st) {
   const size_t smem =
       union_area(K, L.n_leak, BWD, GL) + (BWD ? (size_t)kWarps * 2 * L.n_cells * sizeof(double) : 0);
-  cudaError_t e = cudaFuncSetAttribute(k_walk<K, BWD, GL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_walk<K, BWD, GL, CMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int grid = A.grid;
   if (grid <= 0) {
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<K, BWD, GL>, kWalkThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<K, BWD, GL, CMP>, kWalkThreads, smem);
     if (e != cudaSuccess) return e;
     grid = (per_sm > 0 ? per_sm : 1) * A.n_sm;
   }
-  k_walk<K, BWD, GL><<<grid, kWalkThreads, smem, st>>>(L, N, A);
+  k_walk<K, BWD, GL, CMP><<<grid, kWalkThreads, smem, st>>>(L, N, A);
   return cudaGetLastError();
 }
 
@@ -1046,15 +1081,25 @@ template <bool GL>
 cudaError_t launch_walk_gl(const LibView& L, const NetView& N, const WalkArgs& A, bool backward, cudaStream_t st) {
   if (backward) {
     switch (A.rpt) {
-      case 4: return launch_walk_k<4, true, GL>(L, N, A, st);
-      case 16: return launch_walk_k<16, true, GL>(L, N, A, st);
-      default: return launch_walk_k<8, true, GL>(L, N, A, st);
+      case 4: return launch_walk_k<4, true, GL, false>(L, N, A, st);
+      case 16: return launch_walk_k<16, true, GL, false>(L, N, A, st);
+      default: return launch_walk_k<8, true, GL, false>(L, N, A, st);
     }
   }
   switch (A.rpt) {
-    case 4: return launch_walk_k<4, false, GL>(L, N, A, st);
-    case 16: return launch_walk_k<16, false, GL>(L, N, A, st);
-    default: return launch_walk_k<8, false, GL>(L, N, A, st);
+    case 4: return launch_walk_k<4, false, GL, false>(L, N, A, st);
+    case 16: return launch_walk_k<16, false, GL, false>(L, N, A, st);
+    default: return launch_walk_k<8, false, GL, false>(L, N, A, st);
+  }
+}
+
+// The forward walk that also accumulates the per-component bins.
+template <bool GL>
+cudaError_t launch_walk_cmp(const LibView& L, const NetView& N, const WalkArgs& A, cudaStream_t st) {
+  switch (A.rpt) {
+    case 4: return launch_walk_k<4, false, GL, true>(L, N, A, st);
+    case 16: return launch_walk_k<16, false, GL, true>(L, N, A, st);
+    default: return launch_walk_k<8, false, GL, true>(L, N, A, st);
   }
 }
 

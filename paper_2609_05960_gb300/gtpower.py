@@ -29,7 +29,7 @@ ABI_SYMBOLS = ["gtp_create", "gtp_destroy", "gtp_set_stream", "gtp_last_error", 
                "gtp_set_scales", "gtp_load_netlist", "gtp_set_load", "gtp_load_events", "gtp_run_power",
                "gtp_gate_energy", "gtp_run_power_batched", "gtp_run_power_backward", "gtp_autotune",
                "gtp_set_param", "gtp_get_param", "gtp_run_power_noalloc", "gtp_set_glitch", "gtp_gate_glitch",
-               "gtp_run_power_streamed", "gtp_design_power"]
+               "gtp_run_power_streamed", "gtp_design_power", "gtp_run_power_components"]
 
 
 class GtpError(RuntimeError):
@@ -65,6 +65,7 @@ def load(path: str = LIB_PATH):
         "gtp_run_power_streamed": ([P, I32, I64, I64, P, P, P, I32, P, I32, ctypes.c_int], ctypes.c_int),
         "gtp_load_events": ([P, I32, I64, I64, P, P, P, ctypes.c_int], ctypes.c_int),
         "gtp_run_power": ([P, I32, I32, P, ctypes.c_int], ctypes.c_int),
+        "gtp_run_power_components": ([P, I32, I32, P, P, ctypes.c_int], ctypes.c_int),
         "gtp_gate_energy": ([P, I32, P, P, P, P, P, ctypes.c_int], ctypes.c_int),
         "gtp_run_power_batched": ([P, I32, P, I32, P, ctypes.c_int], ctypes.c_int),
         "gtp_run_power_backward": ([P, I32, I32, P, P, P, P], ctypes.c_int),
@@ -214,6 +215,14 @@ def gtp_run_power(ctx, window: int, bin_ps: int, waveform=None, graph: bool = Fa
     _check(ctx, load().gtp_run_power(ctx, int(window), int(bin_ps), p, f | (GTP_GRAPH if graph else 0)))
 
 
+def gtp_run_power_components(ctx, window: int, bin_ps: int, components, waveform=None) -> None:
+    pc, fc, kc = _ptr_flags(components, np.float64)
+    pw, fw, kw = _ptr_flags(waveform, np.float64)
+    if pw is not None and fw != fc:
+        raise ValueError("components and waveform must both be host or both be device")
+    _check(ctx, load().gtp_run_power_components(ctx, int(window), int(bin_ps), pw, pc, fc))
+
+
 def gtp_gate_energy(ctx, window: int, e_leak=None, e_int=None, e_sw=None, n_events=None, final_state=None) -> None:
     args = [_ptr_flags(e_leak, np.float64), _ptr_flags(e_int, np.float64), _ptr_flags(e_sw, np.float64),
             _ptr_flags(n_events, np.int64), _ptr_flags(final_state, np.uint8)]
@@ -357,6 +366,17 @@ class Engine:
         if out is None:
             out = torch.empty(nb, dtype=torch.float64, device=self.device)
         gtp_run_power(self.ctx, window, bin_ps, out, graph=graph)
+        return out
+
+    def run_power_components(self, window: int, bin_ps: int, out=None, total=None):
+        """Per-component waveforms in W, [4][window_ps / bin_ps] float64 rows
+        leakage, internal, switching, glitch (a CUDA tensor unless `out` is a
+        host array); `total`, if given, receives the total waveform."""
+        import torch
+        nb = self.windows[window]["window_ps"] // bin_ps
+        if out is None:
+            out = torch.empty((4, nb), dtype=torch.float64, device=self.device)
+        gtp_run_power_components(self.ctx, window, bin_ps, out, total)
         return out
 
     def run_power_streamed(self, window: int, trace=None, bin_ps: int = 10, out=None, n_chunks: int = 8, *,
