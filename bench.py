@@ -55,11 +55,12 @@ def parse():
     p.add_argument("--events", type=int, default=0,
                    help="scale the configuration to this many events (same gates and distribution; "
                         "for profiling a smaller case)")
-    p.add_argument("--sweep", default="", choices=["", "contention", "streamed"],
+    p.add_argument("--sweep", default="", choices=["", "contention", "streamed", "schemes"],
                    help="contention: uniform high activity (1, 2, 4, 8 events per gate per 1k bins); "
                         "streamed: the large window streamed from pinned host memory in 1-32 chunks, "
-                        "against a plain copy of its records; instead of the default run, one JSON line "
-                        "per case")
+                        "against a plain copy of its records; schemes: the paper's GPU schemes (naive, "
+                        "state-indexed lookup, density-aware partitioning, fused kernel) against this "
+                        "engine's walk; instead of the default run, one JSON line per case")
     return p.parse_args()
 
 
@@ -625,8 +626,78 @@ def run_streamed_sweep(args):
     eng.close()
 
 
+def run_schemes_sweep(args):
+    """The paper's own schemes (gtp_run_power_scheme: Naive-D + Naive-L with
+    state-pattern traversal, + state-indexed lookup, + event-density-aware
+    partitioning, the fused kernel) against this engine's gtp_run_power on
+    the same window: the tiny workload, a mid-sized one (200k gates, 20M
+    events, 10k bins of 100 ps) and, for the fused kernel alone, the large
+    one.  Scheme times are the device time of their kernels (CUDA events
+    inside the call, median of the steps); the engine's is the CUDA-event
+    time of graph-replayed runs (preparation, walk and merge)."""
+    import torch
+
+    import synth
+    from paper_2609_05960_gb300 import Engine, gtpower
+
+    dev = torch.device("cuda", 0)
+    steps = max(3, min(args.steps, 10))
+    cases = [("tiny", synth.CONFIGS["tiny"], None, ["naive", "sipl", "density", "fused"]),
+             ("mid: 200,000 gates, 20,000,000 events, Zipf 1.2, cap 100000, 1 us window, 100 ps bins (10,000 bins)",
+              None, (200_000, 20_000_000, 1_000_000, 100), ["naive", "sipl", "density", "fused"]),
+             ("large", synth.CONFIGS["large"], None, ["fused"])]
+    eng = Engine(0)
+    for name, cfg, shape, schemes in cases:
+        lib = synth.make_library(1)
+        if cfg is not None:
+            G, n_ev, window_ps, bin_ps = cfg.n_gates, cfg.n_events, cfg.window_ps, cfg.bin_ps
+            net = synth.make_netlist(lib, G, cfg.seed_net)
+            counts = synth.zipf_counts(G, n_ev, cfg.zipf_s, cfg.cap, cfg.seed_ev)
+            seed = cfg.seed_ev
+        else:
+            G, n_ev, window_ps, bin_ps = shape
+            net = synth.make_netlist(lib, G, 2)
+            counts = synth.zipf_counts(G, n_ev, 1.2, 100_000, 5)
+            seed = 5
+        tr, rec = synth.make_trace_gpu(net, counts, window_ps, seed, device=dev)
+        off = torch.from_numpy(tr.offsets).to(dev)
+        init = torch.from_numpy(tr.init_state).to(dev)
+        eng.load_library(lib)
+        eng.load_netlist(net)
+        eng.load_events(0, window_ps=window_ps, offsets=off, records=rec, init_state=init, borrow=True)
+        for key in ("records_per_thread", "ctas_per_sm", "dense_min"):
+            eng.set_param(key, -1)
+        nb = window_ps // bin_ps
+        wave = torch.empty(nb, dtype=torch.float64, device=dev)
+        run = lambda: gtpower.gtp_run_power(eng.ctx, 0, bin_ps, wave, graph=True)
+        for _ in range(3):
+            run()
+        ms_engine = _events_per_s(run, steps, dev)
+        ref = wave.clone()
+        n = int(tr.n_events)
+        line = {"sweep": "schemes", "workload": name, "gates": G, "events": n, "bins": nb,
+                "engine_ms": ms_engine, "engine_value": n / (ms_engine * 1e-3), "unit": UNIT, "schemes": {}}
+        for sc in schemes:
+            gtpower.gtp_run_power_scheme(eng.ctx, 0, bin_ps, sc, wave)  # builds the pin streams and block plan
+            reps = 1 if name == "large" else steps
+            ms = sorted(gtpower.gtp_run_power_scheme(eng.ctx, 0, bin_ps, sc, wave) for _ in range(reps))[reps // 2]
+            rel = float(((wave - ref).abs() / ref.abs()).max())
+            line["schemes"][sc] = {"kernel_ms": ms, "over_engine": ms / ms_engine, "max_rel_diff_vs_engine": rel}
+        if "naive" in line["schemes"]:
+            for sc in line["schemes"].values():
+                sc["over_naive"] = sc["kernel_ms"] / line["schemes"]["naive"]["kernel_ms"]
+        line["partitioning"] = {k: eng.get_param(k) for k in ("scheme_evt_tgt", "scheme_thr_floor", "scheme_ncyc_fix")}
+        print(json.dumps(line), flush=True)
+        del rec, off, init, wave, ref
+        torch.cuda.empty_cache()
+    eng.close()
+
+
 def main():
     args = parse()
+    if args.sweep == "schemes":
+        run_schemes_sweep(args)
+        return
     if args.sweep == "contention":
         run_contention_sweep(args)
         return

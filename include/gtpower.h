@@ -230,6 +230,41 @@ int gtp_run_power_components(gtp_ctx* ctx, int32_t window, int32_t bin_ps, doubl
                              double* components_w, int flags);
 
 /*
+ * The paper's own GPU schemes, for comparison with gtp_run_power on the same
+ * window (they compute the same waveform and per-gate results):
+ *   GTP_SCHEME_NAIVE    Naive-D (one thread per event, the gate state rebuilt
+ *                       by binary searches in each pin's event stream,
+ *                       Sec. 3.2.1) and Naive-L (one thread per gate and
+ *                       window of scheme_ncyc_fix bins, leakage added to every
+ *                       overlapped bin, Sec. 3.2.2), with state-dependent
+ *                       energies found by traversing the state patterns
+ *                       (Sec. 4, challenge 1);
+ *   GTP_SCHEME_SIPL     the same with state-indexed lookup (Sec. 4.1);
+ *   GTP_SCHEME_DENSITY  and Naive-L's windows sized per gate by event density
+ *                       (Sec. 4.2: scheme_evt_tgt events a thread, parallelism
+ *                       floor scheme_thr_floor);
+ *   GTP_SCHEME_FUSED    one fused kernel over the density-aware windows
+ *                       (Sec. 4.3, Algorithm 1) and the two-phase per-gate
+ *                       reduction (Sec. 4.4).
+ * The waveform bin plays the part of the paper's clock cycle; glitch
+ * detection follows gtp_set_glitch.  Bins and per-gate sums are FP64
+ * atomics.  The first call on a window builds its per-pin event streams
+ * (checking the trace as gtp_run_power does) and, for the density-aware
+ * schemes, the block plan; later calls reuse them.  *kernel_ms (may be NULL)
+ * receives the device time of the scheme's kernels alone (CUDA events).
+ * Per-gate results are kept for gtp_gate_energy.  flags: GTP_HOST or
+ * GTP_DEVICE for waveform_w (may be NULL); GTP_GRAPH is rejected.  Device
+ * memory: 8 B per event, 72 B per gate of streams, 4 KB per gate of reduction
+ * rows, 8 B per bin.
+ */
+#define GTP_SCHEME_NAIVE 0
+#define GTP_SCHEME_SIPL 1
+#define GTP_SCHEME_DENSITY 2
+#define GTP_SCHEME_FUSED 3
+int gtp_run_power_scheme(gtp_ctx* ctx, int32_t window, int32_t bin_ps, int32_t scheme, double* waveform_w,
+                         int flags, float* kernel_ms);
+
+/*
  * One window run straight from host memory, in chunks [Sec. 5, event
  * chunking with the packing and copy of the next chunk overlapping the
  * kernel]: the window's records are copied to the GPU in n_chunks gate-range
@@ -300,7 +335,9 @@ int gtp_autotune(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_
  * "records_per_thread" (4, 8, 16; events per lane of a dense segment),
  * "ctas_per_sm" (0 = full occupancy), "dense_min" (gates with more events are cut into segments; 1..4096),
  * "kernel" (0 = density-split walk,
- * 1 = one thread per gate, a plain cross-check), "timing" (1 = time the
+ * 1 = one thread per gate, a plain cross-check), "scheme_evt_tgt" (8),
+ * "scheme_thr_floor" (512) and "scheme_ncyc_fix" (1) for gtp_run_power_scheme,
+ * "timing" (1 = time the
  * phases of later runs with CUDA events; read back with gtp_get_param keys
  * "t_gate_pass_ns" (the preparation launch: bins cleared, gate pass and
  * work-list histogram), "t_plan_ns" (work-list scatter), "t_walk_ns",

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "gtp_internal.cuh"
+#include "gtp_scheme.cuh"
 #include "gtp_walk.cuh"
 
 using namespace gtp;
@@ -49,6 +50,12 @@ struct Window {
   const uint2* borrowed = nullptr;
   DevBuf e_leak, e_int, e_sw, e_gl, final_state, bins, tiles, wave;
   DevBuf cbins, cwave;  // per-component runs: component accumulators and the host-bound waveforms
+  // the paper's schemes: per-pin event streams (built once per load) and the
+  // density-aware block plan (per bin count and partitioning parameters)
+  DevBuf ps_off, ps_ev, ps_slot, blk_gate, blk_first, ncyc;
+  bool ps_ok = false;
+  int64_t dplan_key[3] = {-1, -1, -1};
+  int64_t n_blocks = 0;
   bool has_result = false;
   bool glitch_result = false;  // the last run detected glitches (e_gl holds them)
   bool streamed = false;       // filled by a streamed run: results only, no resident records
@@ -56,11 +63,13 @@ struct Window {
   const uint2* rec() const { return borrowed ? borrowed : records.as<uint2>(); }
   void release() {
     for (DevBuf* b : {&offsets, &records, &init, &e_leak, &e_int, &e_sw, &e_gl, &final_state, &bins, &tiles, &wave,
-                      &cbins, &cwave})
+                      &cbins, &cwave, &ps_off, &ps_ev, &ps_slot, &blk_gate, &blk_first, &ncyc})
       b->release();
     borrowed = nullptr;
     loaded = false;
     has_result = false;
+    ps_ok = false;
+    dplan_key[0] = -1;
   }
 };
 
@@ -111,6 +120,12 @@ struct gtp_ctx {
   DevBuf first_bad;  // trace check result (see launch_validate)
   DevBuf out_slew;   // glitch detection: [n_gates][2] output {fall, rise} transition times
   DevBuf dp_scratch; // design-level power: sums, peak key and index
+  // the paper's schemes: state patterns of the library's tables and leakage
+  // entries, FP64 bins, per-gate reduction rows, timing events
+  DevBuf pat_int, pat_leak, sch_ebins, sch_R;
+  bool pat_ok = false;
+  cudaEvent_t sch_ev[2] = {};
+  int64_t p_evt_tgt = 8, p_thr_floor = 512, p_ncyc_fix = 1;
   // streamed runs: two chunk buffers, a copy stream and its events
   DevBuf chunk_buf[2];
   cudaStream_t copy_stream = nullptr;
@@ -563,6 +578,77 @@ int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, dou
   return rc;
 }
 
+// State patterns of the library for the schemes' traversal: each table's
+// side-input state and each leakage entry's full state, in the library's
+// order (the same order SIPL indexes).
+int ensure_patterns(gtp_ctx* ctx) {
+  if (ctx->pat_ok) return GTP_OK;
+  std::vector<uint16_t> pi, pl;
+  for (int32_t n : ctx->n_in) {
+    for (int pin = 0; pin < n; ++pin)
+      for (int e = 0; e < 2; ++e)
+        for (int s = 0; s < (1 << (n - 1)); ++s) pi.push_back((uint16_t)s);
+    for (int s = 0; s < (2 << n); ++s) pl.push_back((uint16_t)s);
+  }
+  CU(ctx->pat_int.reserve(sizeof(uint16_t) * pi.size()), "alloc patterns");
+  CU(ctx->pat_leak.reserve(sizeof(uint16_t) * pl.size()), "alloc patterns");
+  CU(cudaMemcpyAsync(ctx->pat_int.p, pi.data(), sizeof(uint16_t) * pi.size(), cudaMemcpyHostToDevice, ctx->stream),
+     "copy patterns");
+  CU(cudaMemcpyAsync(ctx->pat_leak.p, pl.data(), sizeof(uint16_t) * pl.size(), cudaMemcpyHostToDevice, ctx->stream),
+     "copy patterns");
+  CU(cudaStreamSynchronize(ctx->stream), "copy patterns");
+  ctx->pat_ok = true;
+  return GTP_OK;
+}
+
+// Event-density-aware partitioning of a window (Sec. 4.2), planned on the
+// host: rho_g = N_evt(g) / N_cyc, rho_floor = n_evt_tgt / ceil(N_cyc /
+// N_thr_floor), n_cyc(g) = round(n_evt_tgt / (rho_g + rho_floor)) clamped to
+// [1, N_cyc], ceil(N_cyc / n_cyc(g)) threads in blocks of 128 per gate.
+int plan_density(gtp_ctx* ctx, Window* W, int64_t n_bins) {
+  const int64_t key[3] = {n_bins, ctx->p_evt_tgt, ctx->p_thr_floor};
+  if (W->dplan_key[0] == key[0] && W->dplan_key[1] == key[1] && W->dplan_key[2] == key[2]) return GTP_OK;
+  const int64_t G = ctx->N.n_gates;
+  std::vector<int64_t> off((size_t)G + 1);
+  CU(cudaMemcpyAsync(off.data(), W->offsets.p, sizeof(int64_t) * (G + 1), cudaMemcpyDeviceToHost, ctx->stream),
+     "read offsets");
+  CU(cudaStreamSynchronize(ctx->stream), "read offsets");
+  const double tgt = (double)ctx->p_evt_tgt;
+  const int64_t n_cyc_floor = (n_bins + ctx->p_thr_floor - 1) / ctx->p_thr_floor;
+  const double rho_floor = tgt / (double)n_cyc_floor;
+  std::vector<int32_t> ncyc((size_t)G);
+  std::vector<int64_t> first((size_t)G);
+  int64_t B = 0;
+  for (int64_t g = 0; g < G; ++g) {
+    const double rho = (double)(off[g + 1] - off[g]) / (double)n_bins;
+    int64_t n = std::llround(tgt / (rho + rho_floor));
+    n = std::min<int64_t>(std::max<int64_t>(n, 1), n_bins);
+    const int64_t thr = (n_bins + n - 1) / n;
+    ncyc[g] = (int32_t)n;
+    first[g] = B;
+    B += (thr + kSchemeTpb - 1) / kSchemeTpb;
+  }
+  if (B > 0x7FFFFFFFll) return fail(ctx, GTP_ERANGE, "run_power_scheme: more than 2^31 blocks");
+  std::vector<int32_t> bg((size_t)B);
+  for (int64_t g = 0; g < G; ++g) {
+    const int64_t e = g + 1 < G ? first[g + 1] : B;
+    for (int64_t b = first[g]; b < e; ++b) bg[b] = (int32_t)g;
+  }
+  CU(W->blk_gate.reserve(sizeof(int32_t) * (size_t)B), "alloc block plan");
+  CU(W->blk_first.reserve(sizeof(int64_t) * (size_t)G), "alloc block plan");
+  CU(W->ncyc.reserve(sizeof(int32_t) * (size_t)G), "alloc block plan");
+  CU(cudaMemcpyAsync(W->blk_gate.p, bg.data(), sizeof(int32_t) * (size_t)B, cudaMemcpyHostToDevice, ctx->stream),
+     "copy block plan");
+  CU(cudaMemcpyAsync(W->blk_first.p, first.data(), sizeof(int64_t) * (size_t)G, cudaMemcpyHostToDevice, ctx->stream),
+     "copy block plan");
+  CU(cudaMemcpyAsync(W->ncyc.p, ncyc.data(), sizeof(int32_t) * (size_t)G, cudaMemcpyHostToDevice, ctx->stream),
+     "copy block plan");
+  CU(cudaStreamSynchronize(ctx->stream), "copy block plan");
+  W->n_blocks = B;
+  for (int i = 0; i < 3; ++i) W->dplan_key[i] = key[i];
+  return GTP_OK;
+}
+
 }  // namespace
 
 // =================================================================== C ABI
@@ -611,8 +697,11 @@ void gtp_destroy(gtp_ctx* ctx) {
   for (DevBuf* b : {&ctx->tab, &ctx->leak, &ctx->cells, &ctx->table_cell, &ctx->leak_cell, &ctx->escale, &ctx->lscale,
                     &ctx->cell, &ctx->load, &ctx->slew, &ctx->desc, &ctx->plan, &ctx->glist, &ctx->gtab, &ctx->gtab_bwd,
                     &ctx->counters, &ctx->first_bad, &ctx->out_slew, &ctx->dp_scratch,
-                    &ctx->cell_acc, &ctx->grad, &ctx->gtiles, &ctx->dC_scratch, &ctx->d_err})
+                    &ctx->cell_acc, &ctx->grad, &ctx->gtiles, &ctx->dC_scratch, &ctx->d_err, &ctx->pat_int,
+                    &ctx->pat_leak, &ctx->sch_ebins, &ctx->sch_R})
     b->release();
+  for (auto& e : ctx->sch_ev)
+    if (e) cudaEventDestroy(e);
   if (ctx->h_err) cudaFreeHost(ctx->h_err);
   if (ctx->h_plan) cudaFreeHost(ctx->h_plan);
   for (auto& e : ctx->ev)
@@ -708,6 +797,8 @@ int gtp_load_library(gtp_ctx* ctx, int32_t n_cells, const int32_t* n_in, float v
   ctx->n_in.assign(n_in, n_in + n_cells);
   ctx->max_in = max_in;
   ctx->lib_loaded = true;
+  ctx->pat_ok = false;
+  for (auto& kv : ctx->windows) kv.second.ps_ok = false;
   ctx->gtab_ok = false;
   ctx->gtab_bwd_ok = false;
   ctx->net_loaded = false;
@@ -765,6 +856,10 @@ int gtp_load_netlist(gtp_ctx* ctx, int64_t n_gates, const int32_t* cell, const f
   RC(ensure_netlist_coords(ctx));
   CU(cudaStreamSynchronize(ctx->stream), "load_netlist");
   ctx->net_loaded = true;
+  for (auto& kv : ctx->windows) {
+    kv.second.ps_ok = false;
+    kv.second.dplan_key[0] = -1;
+  }
   for (auto& kv : ctx->windows) kv.second.release();
   ctx->windows.clear();
   return GTP_OK;
@@ -886,6 +981,8 @@ int gtp_load_events(gtp_ctx* ctx, int32_t window, int64_t window_ps, int64_t n_e
   W.has_result = false;
   W.streamed = false;
   W.borrowed = nullptr;
+  W.ps_ok = false;
+  W.dplan_key[0] = -1;
   const cudaMemcpyKind k = kind_in(flags);
   CU(W.offsets.reserve(sizeof(int64_t) * (G + 1)), "alloc offsets");
   CU(W.init.reserve((size_t)G), "alloc init");
@@ -932,6 +1029,83 @@ int gtp_run_power_components(gtp_ctx* ctx, int32_t window, int32_t bin_ps, doubl
   double* const waves[1] = {waveform_w};
   double* const comps[1] = {components_w};
   return run_forward(ctx, &window, 1, bin_ps, waves, flags, false, comps);
+}
+
+int gtp_run_power_scheme(gtp_ctx* ctx, int32_t window, int32_t bin_ps, int32_t scheme, double* waveform_w,
+                         int flags, float* kernel_ms) {
+  if (!ctx) return GTP_EINVAL;
+  if (scheme < kSchemeNaive || scheme > kSchemeFused) return fail(ctx, GTP_EINVAL, "run_power_scheme: unknown scheme");
+  if (flags & GTP_GRAPH) return fail(ctx, GTP_EINVAL, "run_power_scheme: no graph replay");
+  if (!ctx->net_loaded) return fail(ctx, GTP_EINVAL, "run_power_scheme: load the library, netlist and events first");
+  DeviceGuard dg(ctx->device);
+  Window* W = get_window(ctx, window);
+  if (!W || W->streamed) return fail(ctx, GTP_EINVAL, "run_power_scheme: window not loaded");
+  if (bin_ps <= 0 || W->window_ps % bin_ps != 0) return fail(ctx, GTP_ERANGE, "window_ps must be a multiple of bin_ps > 0");
+  const int64_t nb = W->window_ps / bin_ps;
+  const int64_t G = ctx->N.n_gates;
+  double* wave = nullptr;
+  if (waveform_w) {
+    if (flags & GTP_DEVICE) {
+      wave = waveform_w;
+    } else {
+      CU(W->wave.reserve(sizeof(double) * (size_t)nb), "alloc waveform");
+      wave = W->wave.as<double>();
+    }
+  }
+  int64_t n_seg_total = 0, n_tiles_total = 0;
+  RC(build_plan(ctx, std::vector<Window*>{W}, bin_ps, std::vector<double*>{wave}, false, &n_seg_total,
+                &n_tiles_total));
+  RC(upload_plan(ctx, 1, ctx->stream));
+  CU(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(DevError), ctx->stream), "zero status");
+  const WinDesc* dw = plan_wins(ctx->plan.p);
+  if (!W->ps_ok) {  // the paper's input form: one event stream per (gate, pin), checked as the walk checks
+    CU(W->ps_off.reserve(sizeof(int64_t) * 9 * (size_t)G), "alloc pin streams");
+    CU(W->ps_ev.reserve(sizeof(uint32_t) * (size_t)W->n_events), "alloc pin streams");
+    CU(W->ps_slot.reserve(sizeof(uint32_t) * (size_t)W->n_events), "alloc pin streams");
+    CU(launch_pin_streams(ctx->L, ctx->N, dw,
+                          PinStreams{W->ps_off.as<int64_t>(), W->ps_ev.as<uint32_t>(), W->ps_slot.as<uint32_t>()},
+                          ctx->d_err.as<DevError>(), ctx->stream), "pin streams");
+    RC(check_walk_error(ctx, 1, &window, "run_power_scheme"));
+    W->ps_ok = true;
+  }
+  RC(ensure_patterns(ctx));
+  if (scheme >= kSchemeDensity) RC(plan_density(ctx, W, nb));
+  CU(ctx->sch_ebins.reserve(sizeof(double) * (size_t)nb), "alloc scheme bins");
+  const size_t r_bytes = sizeof(double) * 4 * kSchemeTpb * (size_t)G;
+  if (ctx->sch_R.bytes < r_bytes) {  // rows start at zero and the reduction leaves them at zero
+    CU(ctx->sch_R.reserve(r_bytes), "alloc reduction rows");
+    CU(cudaMemsetAsync(ctx->sch_R.p, 0, r_bytes, ctx->stream), "zero reduction rows");
+  }
+  if (!ctx->sch_ev[0])
+    for (auto& e : ctx->sch_ev) CU(cudaEventCreate(&e), "event create");
+  SchemeArgs A{};
+  A.win = dw;
+  A.ps = PinStreams{W->ps_off.as<int64_t>(), W->ps_ev.as<uint32_t>(), W->ps_slot.as<uint32_t>()};
+  A.pat_int = ctx->pat_int.as<uint16_t>();
+  A.pat_leak = ctx->pat_leak.as<uint16_t>();
+  A.ebins = ctx->sch_ebins.as<double>();
+  A.R = ctx->sch_R.as<double>();
+  A.blk_gate = W->blk_gate.as<int32_t>();
+  A.blk_first = W->blk_first.as<int64_t>();
+  A.ncyc = W->ncyc.as<int32_t>();
+  A.n_blocks = scheme >= kSchemeDensity ? W->n_blocks : 0;
+  A.ncyc_fix = (int32_t)std::min<int64_t>(ctx->p_ncyc_fix, nb);
+  CU(cudaEventRecord(ctx->sch_ev[0], ctx->stream), "event record");
+  CU(cudaMemsetAsync(A.ebins, 0, sizeof(double) * (size_t)nb, ctx->stream), "zero scheme bins");
+  CU(launch_scheme(scheme, ctx->L, ctx->N, A, W->n_events, (int32_t)nb, ctx->stream), "scheme kernels");
+  CU(cudaEventRecord(ctx->sch_ev[1], ctx->stream), "event record");
+  ctx->launches += 4;
+  if (waveform_w && !(flags & GTP_DEVICE))
+    CU(cudaMemcpyAsync(waveform_w, wave, sizeof(double) * (size_t)nb, cudaMemcpyDeviceToHost, ctx->stream),
+       "copy waveform");
+  RC(check_walk_error(ctx, 1, &window, "run_power_scheme"));
+  float ms = 0.f;
+  CU(cudaEventElapsedTime(&ms, ctx->sch_ev[0], ctx->sch_ev[1]), "event time");
+  if (kernel_ms) *kernel_ms = ms;
+  W->has_result = true;
+  W->glitch_result = ctx->N.clock_ps > 0;
+  W->last_bin_ps = bin_ps;
+  return GTP_OK;
 }
 
 int gtp_run_power_batched(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_t bin_ps,
@@ -996,6 +1170,8 @@ int gtp_run_power_streamed(gtp_ctx* ctx, int32_t window, int64_t window_ps, int6
   W.has_result = false;
   W.streamed = false;
   W.borrowed = nullptr;
+  W.ps_ok = false;
+  W.dplan_key[0] = -1;
   CU(W.offsets.reserve(sizeof(int64_t) * (G + 1)), "alloc offsets");
   CU(W.init.reserve((size_t)G), "alloc init");
   CU(cudaMemcpyAsync(W.offsets.p, gate_offsets, sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, st), "copy offsets");
@@ -1243,6 +1419,15 @@ int gtp_set_param(gtp_ctx* ctx, const char* key, int64_t value) {
   } else if (k == "dense_min") {
     if (value == 0 || value > 4096) return fail(ctx, GTP_ERANGE, "dense_min must be 1..4096");
     ctx->p_dense_min = value < 0 ? 256 : value;
+  } else if (k == "scheme_evt_tgt") {
+    if (value == 0 || value > (1 << 20)) return fail(ctx, GTP_ERANGE, "scheme_evt_tgt must be 1..2^20");
+    ctx->p_evt_tgt = value < 0 ? 8 : value;
+  } else if (k == "scheme_thr_floor") {
+    if (value == 0 || value > (1 << 20)) return fail(ctx, GTP_ERANGE, "scheme_thr_floor must be 1..2^20");
+    ctx->p_thr_floor = value < 0 ? 512 : value;
+  } else if (k == "scheme_ncyc_fix") {
+    if (value == 0 || value > (1 << 30)) return fail(ctx, GTP_ERANGE, "scheme_ncyc_fix must be 1..2^30");
+    ctx->p_ncyc_fix = value < 0 ? 1 : value;
   } else if (k == "timing") {
     // 1: time the phases of every following run with CUDA events; any value resets the totals
     DeviceGuard dg(ctx->device);
@@ -1265,6 +1450,9 @@ int64_t gtp_get_param(const gtp_ctx* ctx, const char* key) {
   if (k == "records_per_thread") return ctx->p_rpt;
   if (k == "ctas_per_sm") return ctx->p_ctas_per_sm;
   if (k == "dense_min") return ctx->p_dense_min;
+  if (k == "scheme_evt_tgt") return ctx->p_evt_tgt;
+  if (k == "scheme_thr_floor") return ctx->p_thr_floor;
+  if (k == "scheme_ncyc_fix") return ctx->p_ncyc_fix;
   if (k == "n_sm") return ctx->n_sm;
   if (k == "timing") return ctx->timing ? 1 : 0;
   if (k == "t_gate_pass_ns") return ctx->t_ns[0];

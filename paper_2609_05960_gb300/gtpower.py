@@ -29,7 +29,8 @@ ABI_SYMBOLS = ["gtp_create", "gtp_destroy", "gtp_set_stream", "gtp_last_error", 
                "gtp_set_scales", "gtp_load_netlist", "gtp_set_load", "gtp_load_events", "gtp_run_power",
                "gtp_gate_energy", "gtp_run_power_batched", "gtp_run_power_backward", "gtp_autotune",
                "gtp_set_param", "gtp_get_param", "gtp_run_power_noalloc", "gtp_set_glitch", "gtp_gate_glitch",
-               "gtp_run_power_streamed", "gtp_design_power", "gtp_run_power_components"]
+               "gtp_run_power_streamed", "gtp_design_power", "gtp_run_power_components",
+               "gtp_run_power_scheme"]
 
 
 class GtpError(RuntimeError):
@@ -66,6 +67,7 @@ def load(path: str = LIB_PATH):
         "gtp_load_events": ([P, I32, I64, I64, P, P, P, ctypes.c_int], ctypes.c_int),
         "gtp_run_power": ([P, I32, I32, P, ctypes.c_int], ctypes.c_int),
         "gtp_run_power_components": ([P, I32, I32, P, P, ctypes.c_int], ctypes.c_int),
+        "gtp_run_power_scheme": ([P, I32, I32, I32, P, ctypes.c_int, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
         "gtp_gate_energy": ([P, I32, P, P, P, P, P, ctypes.c_int], ctypes.c_int),
         "gtp_run_power_batched": ([P, I32, P, I32, P, ctypes.c_int], ctypes.c_int),
         "gtp_run_power_backward": ([P, I32, I32, P, P, P, P], ctypes.c_int),
@@ -223,6 +225,19 @@ def gtp_run_power_components(ctx, window: int, bin_ps: int, components, waveform
     _check(ctx, load().gtp_run_power_components(ctx, int(window), int(bin_ps), pw, pc, fc))
 
 
+SCHEMES = {"naive": 0, "sipl": 1, "density": 2, "fused": 3}
+
+
+def gtp_run_power_scheme(ctx, window: int, bin_ps: int, scheme, waveform=None) -> float:
+    """One run of one of the paper's schemes; returns the device time (ms)
+    of its kernels."""
+    s = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+    p, f, k = _ptr_flags(waveform, np.float64)
+    ms = ctypes.c_float(0.0)
+    _check(ctx, load().gtp_run_power_scheme(ctx, int(window), int(bin_ps), s, p, f, ctypes.byref(ms)))
+    return float(ms.value)
+
+
 def gtp_gate_energy(ctx, window: int, e_leak=None, e_int=None, e_sw=None, n_events=None, final_state=None) -> None:
     args = [_ptr_flags(e_leak, np.float64), _ptr_flags(e_int, np.float64), _ptr_flags(e_sw, np.float64),
             _ptr_flags(n_events, np.int64), _ptr_flags(final_state, np.uint8)]
@@ -378,6 +393,17 @@ class Engine:
             out = torch.empty((4, nb), dtype=torch.float64, device=self.device)
         gtp_run_power_components(self.ctx, window, bin_ps, out, total)
         return out
+
+    def run_power_scheme(self, window: int, bin_ps: int, scheme, out=None):
+        """Waveform (W, float64 CUDA tensor unless `out` is a host array) by
+        one of the paper's schemes ("naive", "sipl", "density", "fused");
+        returns (waveform, kernel ms)."""
+        import torch
+        nb = self.windows[window]["window_ps"] // bin_ps
+        if out is None:
+            out = torch.empty(nb, dtype=torch.float64, device=self.device)
+        ms = gtp_run_power_scheme(self.ctx, window, bin_ps, scheme, out)
+        return out, ms
 
     def run_power_streamed(self, window: int, trace=None, bin_ps: int = 10, out=None, n_chunks: int = 8, *,
                            window_ps=None, offsets=None, records=None, init_state=None):
