@@ -116,6 +116,35 @@ int gtp_load_library(gtp_ctx* ctx, int32_t n_cells, const int32_t* n_in, float v
                      const float* e_int, int64_t n_e_int, const float* p_leak, int64_t n_p_leak);
 
 /*
+ * State-indexed lookup construction from Liberty-style state patterns
+ * [Sec. 4.1], for one cell; host only (no context, no GPU).  Writes the
+ * cell's part of gtp_load_library's e_int and p_leak arrays.
+ *   Internal power: n_int_pat patterns.  Pattern k applies to input pin
+ *     int_pin[k] (0..n_in-1) and edge int_edge[k] (0 fall, 1 rise, -1 both);
+ *     its condition fixes the pins in int_care[k] (bit q = pin q; only other
+ *     input pins) to the values in int_val[k] (a subset of int_care[k]) and
+ *     leaves the rest don't-care; its table is int_tab[k * n_slew * n_load ..]
+ *     (slew-major, fJ).  int_default[(pin * 2 + edge) * n_slew * n_load ..]
+ *     is the table of a (pin, edge, side state) no pattern covers.
+ *   Leakage: n_leak_pat patterns over all pins, output (bit n_in) included:
+ *     leak_care[k], leak_val[k], power leak_pw[k] (nW); leak_default for the
+ *     states none covers.
+ *   Each pattern's don't-care pins are enumerated; an entry takes the item of
+ *   the first pattern in list order that covers it (overlapping conditions
+ *   resolve as a scan of the list in order would).
+ *   e_int  out: n_in * 2 * 2^(n_in-1) * n_slew * n_load floats (the layout of
+ *               gtp_load_library's e_int for this cell)
+ *   p_leak out: 2^(n_in+1) floats
+ * Returns GTP_ERANGE for n_in outside 1..GTP_MAX_PINS-1 or axes outside
+ * 2..GTP_MAX_AXIS, GTP_EINVAL for a null array, a pin or edge out of range,
+ * a condition on a pin it may not name, or values outside the care mask.
+ */
+int gtp_sipl_expand(int32_t n_in, int32_t n_slew, int32_t n_load, int32_t n_int_pat, const int32_t* int_pin,
+                    const int32_t* int_edge, const uint32_t* int_care, const uint32_t* int_val, const float* int_tab,
+                    const float* int_default, int32_t n_leak_pat, const uint32_t* leak_care, const uint32_t* leak_val,
+                    const float* leak_pw, float leak_default, float* e_int, float* p_leak);
+
+/*
  * Per-cell multipliers on internal energy and on leakage power (host arrays
  * of n_cells; NULL leaves that scale at 1).  They are the parameters the
  * adjoint differentiates.

@@ -30,7 +30,7 @@ ABI_SYMBOLS = ["gtp_create", "gtp_destroy", "gtp_set_stream", "gtp_last_error", 
                "gtp_gate_energy", "gtp_run_power_batched", "gtp_run_power_backward", "gtp_autotune",
                "gtp_set_param", "gtp_get_param", "gtp_run_power_noalloc", "gtp_set_glitch", "gtp_gate_glitch",
                "gtp_run_power_streamed", "gtp_design_power", "gtp_run_power_components",
-               "gtp_run_power_scheme"]
+               "gtp_run_power_scheme", "gtp_sipl_expand"]
 
 
 class GtpError(RuntimeError):
@@ -67,6 +67,7 @@ def load(path: str = LIB_PATH):
         "gtp_load_events": ([P, I32, I64, I64, P, P, P, ctypes.c_int], ctypes.c_int),
         "gtp_run_power": ([P, I32, I32, P, ctypes.c_int], ctypes.c_int),
         "gtp_run_power_components": ([P, I32, I32, P, P, ctypes.c_int], ctypes.c_int),
+        "gtp_sipl_expand": ([I32, I32, I32, I32, P, P, P, P, P, P, I32, P, P, P, F, P, P], ctypes.c_int),
         "gtp_run_power_scheme": ([P, I32, I32, I32, P, ctypes.c_int, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
         "gtp_gate_energy": ([P, I32, P, P, P, P, P, ctypes.c_int], ctypes.c_int),
         "gtp_run_power_batched": ([P, I32, P, I32, P, ctypes.c_int], ctypes.c_int),
@@ -223,6 +224,38 @@ def gtp_run_power_components(ctx, window: int, bin_ps: int, components, waveform
     if pw is not None and fw != fc:
         raise ValueError("components and waveform must both be host or both be device")
     _check(ctx, load().gtp_run_power_components(ctx, int(window), int(bin_ps), pw, pc, fc))
+
+
+def gtp_sipl_expand(n_in: int, n_slew: int, n_load: int, int_patterns, int_default, leak_patterns,
+                    leak_default: float):
+    """One cell's state-indexed arrays (e_int, p_leak) from Liberty-style
+    patterns: int_patterns = [(pin, edge or -1, care, val, table)];
+    int_default = [n_in][2] tables (or scalars); leak_patterns =
+    [(care, val, nW)].  Tables are n_slew x n_load (or scalars)."""
+    shape = (n_slew, n_load)
+    ip = np.array([p[0] for p in int_patterns], np.int32)
+    ie = np.array([p[1] for p in int_patterns], np.int32)
+    ic = np.array([p[2] for p in int_patterns], np.uint32)
+    iv = np.array([p[3] for p in int_patterns], np.uint32)
+    it = np.array([np.broadcast_to(np.asarray(p[4], np.float32), shape) for p in int_patterns], np.float32)
+    dflt = np.asarray(int_default, np.float32)
+    if 1 <= n_in < 8 and dflt.shape[:2] != (n_in, 2):
+        raise ValueError("int_default must hold [n_in][2] tables")
+    dflt = np.ascontiguousarray(np.broadcast_to(dflt.reshape(dflt.shape + (1, 1)) if dflt.ndim == 2 else dflt,
+                                                dflt.shape[:2] + shape), np.float32)
+    lc = np.array([p[0] for p in leak_patterns], np.uint32)
+    lv = np.array([p[1] for p in leak_patterns], np.uint32)
+    lp = np.array([p[2] for p in leak_patterns], np.float32)
+    ok = 1 <= n_in < 8
+    e_int = np.empty(n_in * 2 * (1 << (n_in - 1)) * n_slew * n_load if ok else 1, np.float32)
+    p_leak = np.empty(2 << n_in if ok else 1, np.float32)
+    ptr = lambda a: a.ctypes.data if a.size else None
+    rc = load().gtp_sipl_expand(int(n_in), int(n_slew), int(n_load), len(ip), ptr(ip), ptr(ie), ptr(ic), ptr(iv),
+                                ptr(it), dflt.ctypes.data, len(lc), ptr(lc), ptr(lv), ptr(lp), float(leak_default),
+                                e_int.ctypes.data, p_leak.ctypes.data)
+    if rc != GTP_OK:
+        raise GtpError(rc, "sipl_expand: bad pattern list")
+    return e_int, p_leak
 
 
 SCHEMES = {"naive": 0, "sipl": 1, "density": 2, "fused": 3}
