@@ -329,24 +329,40 @@ def run_ours(args, cfg_name):
         cnt_h = torch.empty(G, dtype=torch.int64, pin_memory=True)
         fin_h = torch.empty(G, dtype=torch.uint8, pin_memory=True)
 
-        def e2e_step():
+        # the packed transfer form (4.125 B a record), written once like the trace itself
+        pk_h = torch.empty(gtpower.packed_words(n_ev), dtype=torch.int32, pin_memory=True)
+        gtpower.gtp_pack_events(rec_h.numpy(), out=pk_h)
+
+        def e2e_step(packed):
             # records streamed from pinned host memory in 8 chunks, copies overlapping the walk
-            gtpower.gtp_run_power_streamed(ctx, 1, cfg.window_ps, off_h, rec_h, init_h, cfg.bin_ps, wave_h, 8)
+            if packed:
+                gtpower.gtp_run_power_streamed(ctx, 1, cfg.window_ps, off_h, pk_h, init_h, cfg.bin_ps, wave_h, 8,
+                                               n_events=n_ev, packed=True)
+            else:
+                gtpower.gtp_run_power_streamed(ctx, 1, cfg.window_ps, off_h, rec_h, init_h, cfg.bin_ps, wave_h, 8)
             gtpower.gtp_gate_energy(ctx, 1, outs_h[0], outs_h[1], outs_h[2], cnt_h, fin_h)
 
-        e2e_step()
-        torch.cuda.synchronize(dev)
-        barrier(pg)
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            e2e_step()
-        torch.cuda.synchronize(dev)
-        t_e2e = max_over_ranks(pg, time.perf_counter() - t0)
-        h2d = rec_h.numel() * 4 + off_h.nbytes + init_h.nbytes
+        def time_e2e(packed):
+            e2e_step(packed)
+            torch.cuda.synchronize(dev)
+            barrier(pg)
+            t0 = time.perf_counter()
+            for _ in range(args.e2e_steps):
+                e2e_step(packed)
+            torch.cuda.synchronize(dev)
+            return max_over_ranks(pg, time.perf_counter() - t0)
+
         d2h = n_bins * 8 + G * (8 * 3 + 8 + 1)
+        t_e2e = time_e2e(True)
+        h2d = pk_h.numel() * 4 + off_h.nbytes + init_h.nbytes
+        t_e2e8 = time_e2e(False)
+        h2d8 = rec_h.numel() * 4 + off_h.nbytes + init_h.nbytes
         e2e = {"value": ws * args.e2e_steps * n_ev / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * t_e2e / args.e2e_steps}
-        del rec_h
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * t_e2e / args.e2e_steps,
+               "input": "packed transfer form (gtp_pack_events, 4.125 B a record), streamed in 8 chunks",
+               "records_8b": {"value": ws * args.e2e_steps * n_ev / t_e2e8, "h2d_bytes_per_step": int(h2d8),
+                              "ms_per_step": 1e3 * t_e2e8 / args.e2e_steps}}
+        del rec_h, pk_h
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -623,6 +639,22 @@ def run_streamed_sweep(args):
         print(json.dumps({"sweep": "streamed", "case": f"gtp_run_power_streamed, {nc} chunks", "n_chunks": nc,
                           "events": n, "ms": ms, "value": n / (ms * 1e-3), "unit": UNIT,
                           "over_plain_copy": ms / ms_copy}), flush=True)
+    # the packed transfer form: 4.125 B a record over the host link, unpacked on the device
+    pk_h = torch.empty(gtpower.packed_words(n), dtype=torch.int32, pin_memory=True)
+    gtpower.gtp_pack_events(rec_h.numpy(), out=pk_h)
+    pk_d = torch.empty_like(pk_h, device=dev)
+    ms_pcopy = _events_per_s(lambda: pk_d.copy_(pk_h, non_blocking=True), steps, dev)
+    del pk_d
+    print(json.dumps({"sweep": "streamed", "case": "plain host-to-device copy of the packed records",
+                      "bytes": pk_h.numel() * 4, "ms": ms_pcopy, "gb_per_s": pk_h.numel() * 4 / (ms_pcopy * 1e6)}),
+          flush=True)
+    for nc in (2, 4, 8, 16):
+        run = lambda: gtpower.gtp_run_power_streamed(eng.ctx, 0, cfg.window_ps, off_h, pk_h, init_h, cfg.bin_ps,
+                                                     wave_h, nc, n_events=n, packed=True)
+        ms = _events_per_s(run, steps, dev)
+        print(json.dumps({"sweep": "streamed", "case": f"gtp_run_power_streamed, packed, {nc} chunks",
+                          "n_chunks": nc, "events": n, "ms": ms, "value": n / (ms * 1e-3), "unit": UNIT,
+                          "over_plain_copy_of_packed": ms / ms_pcopy}), flush=True)
     eng.close()
 
 

@@ -57,6 +57,8 @@ extern "C" {
                                its first call and replay it on later calls with
                                the same window list, bin size, window sizes,
                                tuning and phase-timing setting */
+#define GTP_PACKED 8        /* gtp_run_power_streamed only: `events` holds the
+                               packed transfer form of gtp_pack_events */
 
 /* Limits of this engine: at most 7 input pins per cell (8 pins, so the gate
  * state fits in one byte), at most 16 points per interpolation axis, and
@@ -74,6 +76,19 @@ typedef struct gtp_event {
   int32_t t_ps;
   uint32_t meta;
 } gtp_event;
+
+/*
+ * Packed transfer form of n_events records, for runs bound by the host link
+ * (gtp_run_power_streamed with GTP_PACKED): 4.125 bytes a record instead of
+ * 8.  Records are taken in blocks of 32 (the last block may be shorter);
+ * each block has one uint32 anchor, the smallest t_ps in the block, and each
+ * record one uint32 word, (t_ps - anchor) << 5 | meta.  Layout: packed[0 ..
+ * nb) the anchors, nb = (n_events + 31) / 32, then packed[nb .. nb +
+ * n_events) the words.  Host only (no context, no GPU).  Returns GTP_ERANGE
+ * if a record has t_ps < 0 or reserved meta bits set, or if a block spans
+ * 2^27 ps or more (any window up to 134 us fits), GTP_EINVAL for null arrays.
+ */
+int gtp_pack_events(int64_t n_events, const gtp_event* events, uint32_t* packed);
 
 typedef struct gtp_ctx gtp_ctx;
 
@@ -306,7 +321,11 @@ int gtp_run_power_scheme(gtp_ctx* ctx, int32_t window, int32_t bin_ps, int32_t s
  *   gate_offsets [n_gates+1], events [n_events] and init_state [n_gates]
  *   are host memory (events pinned for the copies to overlap), as for
  *   gtp_load_events; waveform_w [n_bins] as for gtp_run_power.
- *   n_chunks: 1..1024.  flags: GTP_HOST or GTP_DEVICE for waveform_w.
+ *   n_chunks: 1..1024.  flags: GTP_HOST or GTP_DEVICE for waveform_w,
+ *   optionally | GTP_PACKED: `events` is then the packed transfer form of
+ *   gtp_pack_events (cast to const gtp_event*), of which each chunk's
+ *   anchors and words are copied and unpacked on the device; record indices
+ *   in errors are those of the unpacked records.
  * Synchronous.  Errors as gtp_load_events and gtp_run_power (offsets are
  * checked on the host before any copy).
  */

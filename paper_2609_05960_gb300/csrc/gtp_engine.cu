@@ -128,6 +128,7 @@ struct gtp_ctx {
   int64_t p_evt_tgt = 8, p_thr_floor = 512, p_ncyc_fix = 1;
   // streamed runs: two chunk buffers, a copy stream and its events
   DevBuf chunk_buf[2];
+  DevBuf pk_buf[2];  // packed transfer form of a chunk: words, then the anchors of its blocks
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_copied[2] = {}, ev_walked[2] = {};
   DevError* h_err = nullptr;
@@ -692,6 +693,7 @@ void gtp_destroy(gtp_ctx* ctx) {
     if (ctx->ev_copied[i]) cudaEventDestroy(ctx->ev_copied[i]);
     if (ctx->ev_walked[i]) cudaEventDestroy(ctx->ev_walked[i]);
     ctx->chunk_buf[i].release();
+    ctx->pk_buf[i].release();
   }
   for (auto& kv : ctx->windows) kv.second.release();
   for (DevBuf* b : {&ctx->tab, &ctx->leak, &ctx->cells, &ctx->table_cell, &ctx->leak_cell, &ctx->escale, &ctx->lscale,
@@ -1119,6 +1121,25 @@ int gtp_run_power_batched(gtp_ctx* ctx, int32_t n_windows, const int32_t* window
   return run_forward(ctx, windows, n_windows, bin_ps, waveforms, flags, (flags & GTP_GRAPH) != 0);
 }
 
+int gtp_pack_events(int64_t n_events, const gtp_event* events, uint32_t* packed) {
+  if (n_events < 0 || (n_events > 0 && (!events || !packed))) return GTP_EINVAL;
+  const int64_t nb = (n_events + 31) / 32;
+  uint32_t* word = packed + nb;
+  for (int64_t b = 0; b < nb; ++b) {
+    const int64_t i0 = 32 * b, i1 = std::min<int64_t>(i0 + 32, n_events);
+    int32_t lo = events[i0].t_ps, hi = lo;
+    for (int64_t i = i0; i < i1; ++i) {
+      if (events[i].t_ps < 0 || (events[i].meta >> 5) != 0u) return GTP_ERANGE;
+      lo = std::min(lo, events[i].t_ps);
+      hi = std::max(hi, events[i].t_ps);
+    }
+    if ((int64_t)hi - lo >= (1ll << 27)) return GTP_ERANGE;
+    packed[b] = (uint32_t)lo;
+    for (int64_t i = i0; i < i1; ++i) word[i] = ((uint32_t)(events[i].t_ps - lo) << 5) | events[i].meta;
+  }
+  return GTP_OK;
+}
+
 int gtp_run_power_streamed(gtp_ctx* ctx, int32_t window, int64_t window_ps, int64_t n_events,
                            const int64_t* gate_offsets, const gtp_event* events, const uint8_t* init_state,
                            int32_t bin_ps, double* waveform_w, int32_t n_chunks, int flags) {
@@ -1163,6 +1184,11 @@ int gtp_run_power_streamed(gtp_ctx* ctx, int32_t window, int64_t window_ps, int6
   for (int c = 0; c < n_chunks; ++c) max_chunk = std::max(max_chunk, clamped(gb[c + 1]) - clamped(gb[c]));
   for (int i = 0; i < 2; ++i)
     CU(ctx->chunk_buf[i].reserve(sizeof(uint2) * (size_t)(max_chunk + 2)), "alloc chunk buffer");
+  const bool packed = (flags & GTP_PACKED) != 0;
+  const int64_t pk_words = (max_chunk + 3) & ~(int64_t)3;  // the anchors start 16-byte aligned
+  if (packed)
+    for (int i = 0; i < 2; ++i)
+      CU(ctx->pk_buf[i].reserve(sizeof(uint32_t) * (size_t)(pk_words + max_chunk / 32 + 2)), "alloc packed buffer");
   // the window: offsets and initial states on the device, records only chunk by chunk
   CU(cudaStreamSynchronize(st), "run_power_streamed");
   Window& W = ctx->windows[window];
@@ -1212,6 +1238,8 @@ int gtp_run_power_streamed(gtp_ctx* ctx, int32_t window, int64_t window_ps, int6
   CU(cudaEventRecord(ctx->ev_walked[0], st), "event");
   CU(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_walked[0], 0), "wait");
   const uint2* host_rec = reinterpret_cast<const uint2*>(events);
+  const uint32_t* host_anchor = reinterpret_cast<const uint32_t*>(events);
+  const uint32_t* host_word = host_anchor + (n_events + 31) / 32;
   for (int c = 0; c < n_chunks; ++c) {
     const int b = c & 1;
     bool ok = gate_offsets[gb[c]] >= 0 && gate_offsets[gb[c + 1]] <= n_events;
@@ -1223,11 +1251,24 @@ int gtp_run_power_streamed(gtp_ctx* ctx, int32_t window, int64_t window_ps, int6
     }
     const int64_t r0 = gate_offsets[gb[c]], nr = gate_offsets[gb[c + 1]] - r0;
     if (c >= 2) CU(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_walked[b], 0), "wait walk");
-    if (nr > 0)
+    uint32_t* pk_word = ctx->pk_buf[b].as<uint32_t>();
+    uint32_t* pk_anchor = pk_word + pk_words;
+    if (nr > 0 && !packed)
       CU(cudaMemcpyAsync(ctx->chunk_buf[b].p, host_rec + r0, sizeof(uint2) * (size_t)nr, cudaMemcpyHostToDevice,
                          ctx->copy_stream), "copy chunk");
+    if (nr > 0 && packed) {
+      const int64_t a0 = r0 >> 5, a1 = (r0 + nr - 1) >> 5;
+      CU(cudaMemcpyAsync(pk_word, host_word + r0, sizeof(uint32_t) * (size_t)nr, cudaMemcpyHostToDevice,
+                         ctx->copy_stream), "copy chunk");
+      CU(cudaMemcpyAsync(pk_anchor, host_anchor + a0, sizeof(uint32_t) * (size_t)(a1 - a0 + 1),
+                         cudaMemcpyHostToDevice, ctx->copy_stream), "copy chunk anchors");
+    }
     CU(cudaEventRecord(ctx->ev_copied[b], ctx->copy_stream), "event");
     CU(cudaStreamWaitEvent(st, ctx->ev_copied[b], 0), "wait copy");
+    if (nr > 0 && packed) {
+      CU(launch_unpack(pk_anchor, pk_word, r0, nr, ctx->chunk_buf[b].as<uint2>(), st), "unpack");
+      ctx->launches += 1;
+    }
     WalkArgs A = walk_args(ctx, 1);
     A.wins = plan_wins(ctx->plan.p) + c;
     A.n_gates = std::max<int64_t>(gb[c + 1] - gb[c], 1);

@@ -256,5 +256,10 @@ cudaError_t launch_validate(const LibView& L, const NetView& N, const WinDesc* w
 cudaError_t launch_validate_if(const LibView& L, const NetView& N, const WinDesc* win, const DevError* err,
                                int64_t n_gates, unsigned long long* first, cudaStream_t st);
 int merge_tiles(int n_bins);
+// Unpack records [r0, r0 + n) of the packed transfer form into out[0, n):
+// `anchors` holds the anchors of blocks r0 / 32 .. (r0 + n - 1) / 32, `words`
+// the n words (16-byte aligned).
+cudaError_t launch_unpack(const uint32_t* anchors, const uint32_t* words, int64_t r0, int64_t n, uint2* out,
+                          cudaStream_t st);
 
 }  // namespace gtp

@@ -283,6 +283,40 @@ cudaError_t launch_walk_per_gate(const LibView& L, const NetView& N, const WinDe
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ packed transfer form
+// Four records a thread: one 16-byte load of words, two 16-byte stores of
+// records; t = anchor of the record's block + the word's high 27 bits.
+static __global__ void k_unpack(const uint32_t* __restrict__ anchors, const uint32_t* __restrict__ words, int64_t r0,
+                         int64_t n, uint2* __restrict__ out) {
+  const int64_t a0 = r0 >> 5;
+  const int64_t n4 = n >> 2;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 w = reinterpret_cast<const uint4*>(words)[q];
+    const int64_t r = r0 + 4 * q;
+    const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
+    uint32_t t[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) t[k] = __ldg(anchors + (((r + k) >> 5) - a0)) + (wv[k] >> 5);
+    uint4* o = reinterpret_cast<uint4*>(out + 4 * q);
+    o[0] = make_uint4(t[0], wv[0] & 31u, t[1], wv[1] & 31u);
+    o[1] = make_uint4(t[2], wv[2] & 31u, t[3], wv[3] & 31u);
+  }
+  if (blockIdx.x == 0 && threadIdx.x < (n & 3)) {
+    const int64_t i = 4 * n4 + threadIdx.x;
+    const uint32_t wv = words[i];
+    out[i] = make_uint2(anchors[((r0 + i) >> 5) - a0] + (wv >> 5), wv & 31u);
+  }
+}
+
+cudaError_t launch_unpack(const uint32_t* anchors, const uint32_t* words, int64_t r0, int64_t n, uint2* out,
+                          cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int64_t blocks = ((n >> 2) + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_unpack<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, st>>>(anchors, words, r0, n, out);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ merge
 // out[b] = (E[b] + bin_ps * 1e-6 * (L0 + sum_{b' < b} dP[b'])) * 1e-3 / bin_ps   (W)
 constexpr int kMergeThreads = 256;

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libgtpower.so")
 
 GTP_OK, GTP_EINVAL, GTP_EORDER, GTP_ERANGE, GTP_ENOTOGGLE = 0, -1, -2, -3, -4
 GTP_ENOMEM, GTP_ECUDA, GTP_ETIMEOUT, GTP_EDEVICE = -5, -6, -7, -8
-GTP_HOST, GTP_DEVICE, GTP_BORROW, GTP_GRAPH = 0, 1, 2, 4
+GTP_HOST, GTP_DEVICE, GTP_BORROW, GTP_GRAPH, GTP_PACKED = 0, 1, 2, 4, 8
 GTP_NOALLOC_MAX_BINS = 1 << 19
 
 CODE_NAMES = {GTP_EINVAL: "EINVAL", GTP_EORDER: "EORDER", GTP_ERANGE: "ERANGE", GTP_ENOTOGGLE: "ENOTOGGLE",
@@ -30,7 +30,8 @@ ABI_SYMBOLS = ["gtp_create", "gtp_destroy", "gtp_set_stream", "gtp_last_error", 
                "gtp_gate_energy", "gtp_run_power_batched", "gtp_run_power_backward", "gtp_autotune",
                "gtp_set_param", "gtp_get_param", "gtp_run_power_noalloc", "gtp_set_glitch", "gtp_gate_glitch",
                "gtp_run_power_streamed", "gtp_design_power", "gtp_run_power_components",
-               "gtp_run_power_scheme", "gtp_sipl_expand"]
+               "gtp_run_power_scheme", "gtp_sipl_expand",
+               "gtp_pack_events"]
 
 
 class GtpError(RuntimeError):
@@ -67,6 +68,7 @@ def load(path: str = LIB_PATH):
         "gtp_load_events": ([P, I32, I64, I64, P, P, P, ctypes.c_int], ctypes.c_int),
         "gtp_run_power": ([P, I32, I32, P, ctypes.c_int], ctypes.c_int),
         "gtp_run_power_components": ([P, I32, I32, P, P, ctypes.c_int], ctypes.c_int),
+        "gtp_pack_events": ([I64, P, P], ctypes.c_int),
         "gtp_sipl_expand": ([I32, I32, I32, I32, P, P, P, P, P, P, I32, P, P, P, F, P, P], ctypes.c_int),
         "gtp_run_power_scheme": ([P, I32, I32, I32, P, ctypes.c_int, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
         "gtp_gate_energy": ([P, I32, P, P, P, P, P, ctypes.c_int], ctypes.c_int),
@@ -172,19 +174,47 @@ def gtp_set_glitch(ctx, clock_ps: int, out_slew=None) -> None:
     _check(ctx, load().gtp_set_glitch(ctx, int(clock_ps), p, f))
 
 
+def packed_words(n_events: int) -> int:
+    """Length (uint32 words) of the packed transfer form of n_events records."""
+    return (int(n_events) + 31) // 32 + int(n_events)
+
+
+def gtp_pack_events(events, out=None):
+    """Packed transfer form (uint32, packed_words(n) long) of [n][2] records;
+    `out` may be a preallocated (e.g. pinned) uint32/int32 array or tensor."""
+    rec = np.ascontiguousarray(np.asarray(events).view(np.uint32).reshape(-1, 2))
+    n = rec.shape[0]
+    if out is None:
+        out = np.empty(packed_words(n), np.uint32)
+    po, fo, ko = _ptr_flags(out, np.uint32)
+    if fo != GTP_HOST or (out.shape[0] if hasattr(out, "shape") else len(out)) < packed_words(n):
+        raise ValueError("out must be a host array of packed_words(n) words")
+    rc = load().gtp_pack_events(int(n), rec.ctypes.data if n else None, po if n else None)
+    if rc != GTP_OK:
+        raise GtpError(rc, "pack_events: a negative time, reserved bits, or a block spanning 2^27 ps")
+    return out
+
+
 def gtp_run_power_streamed(ctx, window: int, window_ps: int, gate_offsets, events, init_state, bin_ps: int,
-                           waveform=None, n_chunks: int = 8) -> None:
+                           waveform=None, n_chunks: int = 8, n_events=None, packed: bool = False) -> None:
     """Run a window from host arrays in n_chunks overlapped chunks (events
-    pinned for overlap); the waveform may be host or device."""
+    pinned for overlap); the waveform may be host or device.  packed: events
+    is the packed transfer form of n_events records (gtp_pack_events)."""
     po, fo, ko = _ptr_flags(gate_offsets, np.int64)
     pe, fe, ke = _ptr_flags(events, np.uint32)
     pi, fi, ki = _ptr_flags(init_state, np.uint8)
     if GTP_DEVICE in (fo, fe, fi):
         raise ValueError("run_power_streamed takes host inputs")
     pw, fw, kw = _ptr_flags(waveform, np.float64)
-    n = 0 if events is None else (events.shape[0] if hasattr(events, "shape") else len(events))
+    if packed:
+        n = int(n_events) if n_events is not None else int(gate_offsets[-1])
+        size = events.shape[0] if hasattr(events, "shape") else len(events)
+        if size < packed_words(n):
+            raise ValueError("packed events shorter than packed_words(n_events)")
+    else:
+        n = 0 if events is None else (events.shape[0] if hasattr(events, "shape") else len(events))
     _check(ctx, load().gtp_run_power_streamed(ctx, int(window), int(window_ps), int(n), po, pe, pi, int(bin_ps), pw,
-                                              int(n_chunks), fw))
+                                              int(n_chunks), fw | (GTP_PACKED if packed else 0)))
 
 
 def gtp_design_power(ctx, window: int, waveform=None) -> dict:
@@ -439,9 +469,10 @@ class Engine:
         return out, ms
 
     def run_power_streamed(self, window: int, trace=None, bin_ps: int = 10, out=None, n_chunks: int = 8, *,
-                           window_ps=None, offsets=None, records=None, init_state=None):
+                           window_ps=None, offsets=None, records=None, init_state=None, packed=None):
         """Waveform (float64; on the device unless `out` is a host array) of a
-        window streamed from host arrays in n_chunks overlapped chunks."""
+        window streamed from host arrays in n_chunks overlapped chunks;
+        `packed` (the gtp_pack_events form) replaces the records."""
         import torch
         if trace is not None:  # explicit arrays take precedence (e.g. pinned records)
             window_ps = trace.window_ps if window_ps is None else window_ps
@@ -450,7 +481,11 @@ class Engine:
             init_state = trace.init_state if init_state is None else init_state
         if out is None:
             out = torch.empty(int(window_ps) // bin_ps, dtype=torch.float64, device=self.device)
-        gtp_run_power_streamed(self.ctx, window, window_ps, offsets, records, init_state, bin_ps, out, n_chunks)
+        if packed is not None:
+            gtp_run_power_streamed(self.ctx, window, window_ps, offsets, packed, init_state, bin_ps, out, n_chunks,
+                                   n_events=int(np.asarray(offsets)[-1]), packed=True)
+        else:
+            gtp_run_power_streamed(self.ctx, window, window_ps, offsets, records, init_state, bin_ps, out, n_chunks)
         self.windows[window] = dict(window_ps=int(window_ps))
         return out
 

@@ -36,6 +36,12 @@ def _pinned(tr):
     return rec
 
 
+def _packed(tr):
+    import torch
+    from paper_2609_05960_gb300 import gtpower
+    return torch.from_numpy(gtpower.gtp_pack_events(tr.records).view(np.int32)).pin_memory()
+
+
 def _check(engine, w, ref, bin_ps, window):
     want = oracle.waveform_w(ref["bins"], bin_ps)
     rel = np.abs(w - want) / np.abs(want)
@@ -90,6 +96,32 @@ def test_streamed_equals_resident_run_and_then_needs_a_reload(engine):
     np.testing.assert_allclose(engine.run_power(1, 40).cpu().numpy(), resident, rtol=2e-6)
 
 
+@pytest.mark.parametrize("params", [dict(kernel=1), dict(kernel=0, records_per_thread=8)], ids=["per_gate", "k8"])
+@pytest.mark.parametrize("n_chunks", [1, 3, 8, 64])
+def test_packed_streamed_matches_oracle(engine, params, n_chunks):
+    """The packed transfer form (4.125 B a record) streamed and unpacked on
+    the device gives the oracle's results."""
+    lib, net, tr = synth.make_inputs(synth.CONFIGS["tiny"])
+    _setup(engine, lib, net, params)
+    w = engine.run_power_streamed(3, tr, 100, n_chunks=n_chunks, packed=_packed(tr), window_ps=tr.window_ps,
+                                  offsets=tr.offsets, init_state=tr.init_state).cpu().numpy()
+    _check(engine, w, oracle.walk(lib, net, tr, 100), 100, 3)
+
+
+def test_packed_streamed_equals_the_unpacked_run(engine):
+    lib, net, tr = small_random(n_gates=700, n_events=123_457, window_ps=400_000, seed=96, tie_p=0.03, zipf_s=1.3)
+    _setup(engine, lib, net)
+    kw = dict(window_ps=tr.window_ps, offsets=tr.offsets, init_state=tr.init_state)
+    plain = engine.run_power_streamed(1, tr, 40, n_chunks=5, records=_pinned(tr), **kw).cpu().numpy()
+    e_plain = engine.gate_energy(1, device=False)
+    packed = engine.run_power_streamed(1, None, 40, n_chunks=5, packed=_packed(tr), **kw).cpu().numpy()
+    np.testing.assert_allclose(packed, plain, rtol=2e-6)
+    e_packed = engine.gate_energy(1, device=False)
+    np.testing.assert_array_equal(e_packed["n_events"], e_plain["n_events"])
+    np.testing.assert_array_equal(e_packed["final_state"], e_plain["final_state"])
+    np.testing.assert_allclose(e_packed["e_int"], e_plain["e_int"], rtol=1e-6)
+
+
 def test_streamed_empty_window(engine):
     lib, net, _ = small_random(n_gates=50, n_events=10, window_ps=10_000, seed=93)
     tr = trace_from([[] for _ in range(50)], np.random.default_rng(0).integers(0, 2, 50), 10_000)
@@ -99,8 +131,9 @@ def test_streamed_empty_window(engine):
     _check(engine, w.cpu().numpy(), oracle.walk(lib, net, tr, 100), 100, 0)
 
 
+@pytest.mark.parametrize("packed", [False, True], ids=["records", "packed"])
 @pytest.mark.parametrize("chunks", [1, 4])
-def test_streamed_reports_the_first_bad_record(engine, chunks):
+def test_streamed_reports_the_first_bad_record(engine, chunks, packed):
     from paper_2609_05960_gb300 import GtpError
     lib = single_cell_library(2, lambda *a: 1.0, lambda s: 1.0 + s)
     rng = np.random.default_rng(94)
@@ -120,9 +153,10 @@ def test_streamed_reports_the_first_bad_record(engine, chunks):
     net = netlist_from(lib, [0] * 40, [1.0] * 40)
     tr = trace_from(gates, [0] * 40, 200_000)
     _setup(engine, lib, net, dict(dense_min=64))
+    src = dict(packed=_packed(tr)) if packed else dict(records=_pinned(tr))
     with pytest.raises(GtpError) as ei:
-        engine.run_power_streamed(0, tr, 100, n_chunks=chunks, records=_pinned(tr), window_ps=tr.window_ps,
-                                  offsets=tr.offsets, init_state=tr.init_state)
+        engine.run_power_streamed(0, None, 100, n_chunks=chunks, window_ps=tr.window_ps, offsets=tr.offsets,
+                                  init_state=tr.init_state, **src)
     want = int(tr.offsets[27]) + 100
     assert ei.value.code == -4 and f"at record {want}" in str(ei.value)
     with pytest.raises(oracle.OracleError) as eo:
