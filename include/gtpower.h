@@ -57,7 +57,8 @@ extern "C" {
                                its first call and replay it on later calls with
                                the same window list, bin size, window sizes,
                                tuning and phase-timing setting */
-#define GTP_PACKED 8        /* gtp_run_power_streamed only: `events` holds the
+#define GTP_PACKED 8        /* gtp_load_events (not with GTP_BORROW) and
+                               gtp_run_power_streamed: `events` holds the
                                packed transfer form of gtp_pack_events */
 
 /* Limits of this engine: at most 7 input pins per cell (8 pins, so the gate
@@ -232,7 +233,9 @@ int gtp_design_power(gtp_ctx* ctx, int32_t window, const double* waveform_w, int
  *                 (ties allowed: events sharing a timestamp form one group)
  *   events        [n_events] records
  *   init_state    [n_gates] state of every gate at t = 0 (bit p = pin p)
- * flags: GTP_HOST, GTP_DEVICE, or GTP_DEVICE|GTP_BORROW (events only).
+ * flags: GTP_HOST, GTP_DEVICE, or GTP_DEVICE|GTP_BORROW (events only);
+ * GTP_PACKED: `events` is the packed transfer form (gtp_pack_events) of the
+ * n_events records, unpacked on the device.
  * The CSR structure is checked here (GTP_EINVAL); timestamps, pins and
  * toggles are checked by the walk and reported by gtp_run_power.
  */

@@ -975,6 +975,8 @@ int gtp_load_events(gtp_ctx* ctx, int32_t window, int64_t window_ps, int64_t n_e
   if (borrow && !(flags & GTP_DEVICE)) return fail(ctx, GTP_EINVAL, "load_events: GTP_BORROW needs GTP_DEVICE");
   if (borrow && (((uintptr_t)events) & 15))
     return fail(ctx, GTP_EINVAL, "load_events: borrowed events must be 16-byte aligned");
+  const bool packed = (flags & GTP_PACKED) != 0;
+  if (packed && borrow) return fail(ctx, GTP_EINVAL, "load_events: packed events cannot be borrowed");
   DeviceGuard dg(ctx->device);
   const int64_t G = ctx->N.n_gates;
   Window& W = ctx->windows[window];
@@ -992,6 +994,20 @@ int gtp_load_events(gtp_ctx* ctx, int32_t window, int64_t window_ps, int64_t n_e
   CU(cudaMemcpyAsync(W.init.p, init_state, (size_t)G, k, ctx->stream), "copy init");
   if (borrow) {
     W.borrowed = reinterpret_cast<const uint2*>(events);
+  } else if (packed) {
+    // the packed transfer form: words and anchors into an aligned staging buffer, then unpacked
+    const int64_t nb = (n_events + 31) / 32, nw = (n_events + 3) & ~(int64_t)3;
+    CU(W.records.reserve(sizeof(uint2) * (size_t)(n_events + 2)), "alloc records");
+    CU(cudaMemsetAsync(W.records.as<uint2>() + n_events, 0, 2 * sizeof(uint2), ctx->stream), "zero padding");
+    if (n_events > 0) {
+      CU(ctx->pk_buf[0].reserve(sizeof(uint32_t) * (size_t)(nw + nb)), "alloc packed buffer");
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(events);
+      uint32_t* pk = ctx->pk_buf[0].as<uint32_t>();
+      CU(cudaMemcpyAsync(pk, src + nb, sizeof(uint32_t) * (size_t)n_events, k, ctx->stream), "copy packed words");
+      CU(cudaMemcpyAsync(pk + nw, src, sizeof(uint32_t) * (size_t)nb, k, ctx->stream), "copy packed anchors");
+      CU(launch_unpack(pk + nw, pk, 0, n_events, W.records.as<uint2>(), ctx->stream), "unpack");
+      ctx->launches += 1;
+    }
   } else {
     // padded by two records so that 16-byte vector loads stay in bounds
     const size_t bytes = sizeof(uint2) * (size_t)(n_events + 2);

@@ -232,14 +232,22 @@ def gtp_gate_glitch(ctx, window: int, e_gl) -> None:
     _check(ctx, load().gtp_gate_glitch(ctx, int(window), p, f))
 
 
-def gtp_load_events(ctx, window: int, window_ps: int, gate_offsets, events, init_state, borrow: bool = False) -> None:
+def gtp_load_events(ctx, window: int, window_ps: int, gate_offsets, events, init_state, borrow: bool = False,
+                    packed: bool = False) -> None:
+    """packed: events is the packed transfer form (gtp_pack_events) of
+    gate_offsets[-1] records."""
     po, fo, ko = _ptr_flags(gate_offsets, np.int64)
     pe, fe, ke = _ptr_flags(events, np.uint32)
     pi, fi, ki = _ptr_flags(init_state, np.uint8)
     if not (fo == fe == fi):
         raise ValueError("event arrays must all be host or all be device")
-    n_events = int(events.shape[0]) if events is not None else 0
-    flags = fo | (GTP_BORROW if borrow else 0)
+    if packed:
+        n_events = int(gate_offsets[-1])
+        if (events.shape[0] if hasattr(events, "shape") else len(events)) < packed_words(n_events):
+            raise ValueError("packed events shorter than packed_words(n_events)")
+    else:
+        n_events = int(events.shape[0]) if events is not None else 0
+    flags = fo | (GTP_BORROW if borrow else 0) | (GTP_PACKED if packed else 0)
     _check(ctx, load().gtp_load_events(ctx, int(window), int(window_ps), n_events, po, pe, pi, flags))
 
 
@@ -430,10 +438,15 @@ class Engine:
         return out
 
     def load_events(self, window: int, trace=None, *, window_ps=None, offsets=None, records=None, init_state=None,
-                    borrow: bool = False) -> None:
+                    borrow: bool = False, packed=None) -> None:
+        """Load a window from a trace or explicit arrays; `packed` (the
+        gtp_pack_events form) replaces the records."""
         if trace is not None:
             window_ps, offsets, records, init_state = trace.window_ps, trace.offsets, trace.records, trace.init_state
-        gtp_load_events(self.ctx, window, window_ps, offsets, records, init_state, borrow=borrow)
+        if packed is not None:
+            gtp_load_events(self.ctx, window, window_ps, offsets, packed, init_state, packed=True)
+        else:
+            gtp_load_events(self.ctx, window, window_ps, offsets, records, init_state, borrow=borrow)
         self.windows[window] = dict(window_ps=int(window_ps))
 
     def run_power(self, window: int, bin_ps: int, out=None, graph: bool = False):

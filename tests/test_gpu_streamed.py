@@ -122,6 +122,25 @@ def test_packed_streamed_equals_the_unpacked_run(engine):
     np.testing.assert_allclose(e_packed["e_int"], e_plain["e_int"], rtol=1e-6)
 
 
+@pytest.mark.parametrize("on_device", [False, True], ids=["host", "device"])
+def test_packed_load_equals_the_record_load(engine, on_device):
+    import torch
+    from paper_2609_05960_gb300 import gtpower
+    lib, net, tr = small_random(n_gates=300, n_events=50_001, window_ps=300_000, seed=97, tie_p=0.05, zipf_s=1.3)
+    _setup(engine, lib, net)
+    engine.load_events(2, tr)
+    want = engine.run_power(2, 50).cpu().numpy()
+    pk = gtpower.gtp_pack_events(tr.records)
+    off, init = tr.offsets, tr.init_state
+    if on_device:
+        dev = engine.device
+        pk = torch.from_numpy(pk.view(np.int32)).to(dev)
+        off, init = torch.from_numpy(off).to(dev), torch.from_numpy(init).to(dev)
+    engine.load_events(2, window_ps=tr.window_ps, offsets=off, init_state=init, packed=pk)
+    np.testing.assert_allclose(engine.run_power(2, 50).cpu().numpy(), want, rtol=2e-6)
+    _check(engine, engine.run_power(2, 50).cpu().numpy(), oracle.walk(lib, net, tr, 50), 50, 2)
+
+
 def test_streamed_empty_window(engine):
     lib, net, _ = small_random(n_gates=50, n_events=10, window_ps=10_000, seed=93)
     tr = trace_from([[] for _ in range(50)], np.random.default_rng(0).integers(0, 2, 50), 10_000)
