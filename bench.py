@@ -55,12 +55,13 @@ def parse():
     p.add_argument("--events", type=int, default=0,
                    help="scale the configuration to this many events (same gates and distribution; "
                         "for profiling a smaller case)")
-    p.add_argument("--sweep", default="", choices=["", "contention", "streamed", "schemes"],
+    p.add_argument("--sweep", default="", choices=["", "contention", "streamed", "schemes", "adjoint"],
                    help="contention: uniform high activity (1, 2, 4, 8 events per gate per 1k bins); "
                         "streamed: the large window streamed from pinned host memory in 1-32 chunks, "
                         "against a plain copy of its records; schemes: the paper's GPU schemes (naive, "
                         "state-indexed lookup, density-aware partitioning, fused kernel) against this "
-                        "engine's walk; instead of the default run, one JSON line per case")
+                        "engine's walk; adjoint: the adjoint workload's forward and backward alone (--events "
+                        "scales it); instead of the default run, one JSON line per case")
     return p.parse_args()
 
 
@@ -110,9 +111,9 @@ def config_of(args, cfg_name):
     return cfg
 
 
-def workload_desc(cfg, n_bins):
+def workload_desc(cfg, n_bins, n_events=0):
     cap = f", cap {cfg.cap:g}" if cfg.cap else ""
-    return (f"{cfg.name}: {cfg.n_gates:,} gates, {cfg.n_events:,} events, Zipf {cfg.zipf_s}{cap}, "
+    return (f"{cfg.name}: {cfg.n_gates:,} gates, {n_events or cfg.n_events:,} events, Zipf {cfg.zipf_s}{cap}, "
             f"{cfg.window_ps / 1e6:g} us window, {cfg.bin_ps} ps bins ({n_bins:,} bins)")
 
 
@@ -517,9 +518,10 @@ def measure_components(eng, dev, cfg, walk_plain_ms, n_ev, steps):
             "walk_over_plain": walk_ms / walk_plain_ms, "max_rel_sum_of_components_vs_total": rel}
 
 
-def measure_adjoint(eng, dev, steps):
-    """500k gates, 100M events, 5 us, 10 ps bins: the adjoint walk (gradients
-    of sum P^2 + tau*LSE(P/tau)) against the forward walk on the same window."""
+def measure_adjoint(eng, dev, steps, n_events=0):
+    """500k gates, 100M events (or n_events), 5 us, 10 ps bins: the adjoint
+    walk (gradients of sum P^2 + tau*LSE(P/tau)) against the forward walk on
+    the same window."""
     import torch
 
     import synth
@@ -530,7 +532,7 @@ def measure_adjoint(eng, dev, steps):
     net = synth.make_netlist(lib, cfg.n_gates, cfg.seed_net)
     eng.load_library(lib)
     eng.load_netlist(net)
-    counts = synth.zipf_counts(cfg.n_gates, cfg.n_events, cfg.zipf_s, cfg.cap, cfg.seed_ev)
+    counts = synth.zipf_counts(cfg.n_gates, n_events or cfg.n_events, cfg.zipf_s, cfg.cap, cfg.seed_ev)
     tr, rec = synth.make_trace_gpu(net, counts, cfg.window_ps, cfg.seed_ev, device=dev)
     off = torch.from_numpy(tr.offsets).to(dev)
     init = torch.from_numpy(tr.init_state).to(dev)
@@ -546,7 +548,7 @@ def measure_adjoint(eng, dev, steps):
     ms_f = _events_per_s(lambda: gtpower.gtp_run_power(eng.ctx, 0, cfg.bin_ps, wave), steps, dev)
     ms_b = _events_per_s(lambda: gtpower.gtp_run_power_backward(eng.ctx, 0, cfg.bin_ps, g, dC, de, dl), steps, dev)
     n = tr.n_events
-    return {"workload": workload_desc(cfg, nb), "events": n, "ms_per_backward": ms_b, "value": n / (ms_b * 1e-3),
+    return {"workload": workload_desc(cfg, nb, n), "events": n, "ms_per_backward": ms_b, "value": n / (ms_b * 1e-3),
             "unit": UNIT, "forward_ms": ms_f, "forward_value": n / (ms_f * 1e-3), "backward_over_forward": ms_b / ms_f,
             "loss": "sum P^2 + tau*logsumexp(P/tau), P in mW, tau = 0.01*mean(P)"}
 
@@ -725,8 +727,24 @@ def run_schemes_sweep(args):
     eng.close()
 
 
+def run_adjoint_sweep(args):
+    """The adjoint measurement alone (as in the default run's extras)."""
+    import torch
+
+    from paper_2609_05960_gb300 import Engine
+
+    dev = torch.device("cuda", 0)
+    eng = Engine(0)
+    out = measure_adjoint(eng, dev, max(1, min(args.steps, 20)), args.events)
+    print(json.dumps({"sweep": "adjoint", **out}), flush=True)
+    eng.close()
+
+
 def main():
     args = parse()
+    if args.sweep == "adjoint":
+        run_adjoint_sweep(args)
+        return
     if args.sweep == "schemes":
         run_schemes_sweep(args)
         return

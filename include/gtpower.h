@@ -340,7 +340,9 @@ int gtp_run_power_streamed(gtp_ctx* ctx, int32_t window, int64_t window_ps, int6
  * Per-gate results of the last gtp_run_power / batched run of `window`:
  * leakage, internal and switching energy (fJ, FP64), event count and the
  * state after the last event.  Any pointer may be NULL.
- * flags: GTP_HOST or GTP_DEVICE for all outputs.
+ * flags: GTP_HOST or GTP_DEVICE for all outputs.  Host outputs are complete
+ * on return; device outputs are written in order on the context's stream
+ * (no host synchronisation).
  */
 int gtp_gate_energy(gtp_ctx* ctx, int32_t window, double* e_leak, double* e_int, double* e_sw,
                     int64_t* n_events, uint8_t* final_state, int flags);

@@ -1354,7 +1354,8 @@ int gtp_gate_energy(gtp_ctx* ctx, int32_t window, double* e_leak, double* e_int,
       for (int64_t g = 0; g < G; ++g) n_events[g] = off[g + 1] - off[g];
     }
   }
-  CU(cudaStreamSynchronize(ctx->stream), "gate_energy");
+  // device outputs are stream-ordered on the context's stream; host outputs are complete on return
+  if (!(flags & GTP_DEVICE)) CU(cudaStreamSynchronize(ctx->stream), "gate_energy");
   return GTP_OK;
 }
 
