@@ -36,6 +36,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "events/sec and % of HBM roofline; batched and adjoint vs plain kernel"
+# DRAM bytes (read + write) of one walk launch (k_walk<8,0,0,0>) on the full large workload, from
+# one ncu capture (profiles/k_walk_large_dram_200m.md); reported as roofline.traffic for that
+# workload and plan only
+WALK_TRAFFIC = {("large", 8, 256): 2_020_312_000 + 80_774_912}
 UNIT = "events/s"
 
 
@@ -392,7 +396,11 @@ def run_ours(args, cfg_name):
                        "records_per_thread": eng.get_param("records_per_thread"),
                        "dense_min": eng.get_param("dense_min")},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "k_walk",
+                         "frac": achieved / peak, "kernel": "k_walk",
+                         "traffic": None if args.events else WALK_TRAFFIC.get(
+                             (cfg.name, eng.get_param("records_per_thread"), eng.get_param("dense_min"))),
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one walk launch "
+                                           "(profiles/k_walk_large_dram_200m.md)",
                          "algorithmic_bytes": alg, "walk_ms": walk_s * 1e3, "peak_source": peak_src,
                          "frac_of_nominal_8tbs": achieved / 8000.0},
             "phases_ms": {"prepare": gate_s * 1e3, "scatter": plan_s * 1e3, "walk": walk_s * 1e3,
