@@ -309,6 +309,7 @@ int build_plan(gtp_ctx* ctx, const std::vector<Window*>& ws, int32_t bin_ps, con
       CU(W.cbins.reserve(sizeof(float4) * nb), "alloc component bins");
       d.cbins = W.cbins.as<float4>();
       d.cwave = (*cwaves)[i];
+      d.cpack = ctx->N.clock_ps > 0 ? 0 : 1;
     }
     d.l0 = dl0 + i;
     d.tiles = W.tiles.as<double>();

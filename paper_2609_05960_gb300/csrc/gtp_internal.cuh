@@ -94,8 +94,11 @@ struct WinDesc {
   double* e_gl;              // [G] glitch energy, or null without glitch detection
   uint8_t* final_state;      // [G]
   float2* bins;              // [n_bins] accumulators
-  float4* cbins;             // [n_bins] component accumulators {internal, switching, glitch fJ, leakage in-bin
-                             // corrections fJ}, or null (no per-component waveform)
+  float4* cbins;             // [n_bins] component accumulators, or null (no per-component waveform):
+                             //   cpack 0: {internal, switching, glitch fJ, leakage in-bin corrections fJ},
+                             //            beside the bins as usual (runs with glitch detection)
+                             //   cpack 1: {internal, switching fJ, leakage in-bin corrections fJ,
+                             //            leakage step nW}, the bins unused (runs without)
   double* cwave;             // [4][n_bins] component waveforms (W): leakage, internal, switching, glitch, or null
   double* l0;                // sum over gates of P_leak(initial state), nW
   double* tiles;             // merge scratch
@@ -113,6 +116,7 @@ struct WinDesc {
   int32_t n_bins;
   float g_total;             // adjoint: G(window_ps)
   int32_t keep_bins;         // the preparation pass leaves the bins as they are (a streamed run's later chunks)
+  int32_t cpack;             // layout of cbins (see there)
 };
 
 // ------------------------------------------------------------------ device helpers

@@ -254,8 +254,12 @@ __global__ void k_walk_per_gate(LibView L, NetView N, const WinDesc* __restrict_
       const float P_new = leak[s_next];
       const float dP = P_new - P;
       const float frac = (float)((int32_t)(bin + 1u) * W.bin_ps - t);
-      red_bin(W.bins, bin, e_bin + dP * frac * 1e-6f, dP);
-      if (cb) red_cbin(cb, bin, c_int, c_sw, c_gl, dP * frac * 1e-6f);
+      if (cb && W.cpack) {
+        red_cbin(cb, bin, c_int, c_sw, dP * frac * 1e-6f, dP);
+      } else {
+        red_bin(W.bins, bin, e_bin + dP * frac * 1e-6f, dP);
+        if (cb) red_cbin(cb, bin, c_int, c_sw, c_gl, dP * frac * 1e-6f);
+      }
       st = s_next;
       P = P_new;
       t_prev = t;
@@ -385,7 +389,7 @@ __global__ void k_tile_sums(const WinDesc* __restrict__ wins, const int64_t* __r
   float s = 0.f;
 #pragma unroll
   for (int k = 0; k < kMergePer; ++k)
-    if (base + k < W.n_bins) s += W.bins[base + k].y;
+    if (base + k < W.n_bins) s += W.cpack ? W.cbins[base + k].w : W.bins[base + k].y;
   const double tot = block_sum((double)s);
   if (threadIdx.x == 0) W.tiles[tile] = tot;
 }
@@ -420,7 +424,12 @@ __global__ void k_finalize(const WinDesc* __restrict__ wins, const int64_t* __re
   float s = 0.f;
 #pragma unroll
   for (int k = 0; k < kMergePer; ++k) {
-    v[k] = base + k < W.n_bins ? W.bins[base + k] : make_float2(0.f, 0.f);
+    if (W.cpack) {  // {internal, switching, correction, step}: the bin's energy is the first three
+      const float4 c = base + k < W.n_bins ? W.cbins[base + k] : make_float4(0.f, 0.f, 0.f, 0.f);
+      v[k] = make_float2(c.x + c.y + c.z, c.w);
+    } else {
+      v[k] = base + k < W.n_bins ? W.bins[base + k] : make_float2(0.f, 0.f);
+    }
     s += v[k].y;
   }
   __shared__ double tot;
@@ -443,10 +452,11 @@ __global__ void k_finalize(const WinDesc* __restrict__ wins, const int64_t* __re
     for (int k = 0; k < kMergePer; ++k) {
       if (base + k < W.n_bins) {
         const float4 c = W.cbins[base + k];
-        W.cwave[base + k] = (double)fmaf(c.w, to_w, dp * 1e-9f) + p0;
+        const float corr = W.cpack ? c.z : c.w, gl = W.cpack ? 0.f : c.z;
+        W.cwave[base + k] = (double)fmaf(corr, to_w, dp * 1e-9f) + p0;
         W.cwave[nb + base + k] = (double)(c.x * to_w);
         W.cwave[2 * nb + base + k] = (double)(c.y * to_w);
-        W.cwave[3 * nb + base + k] = (double)(c.z * to_w);
+        W.cwave[3 * nb + base + k] = (double)(gl * to_w);
       }
       dp += v[k].y;
     }

@@ -476,9 +476,13 @@ __device__ __forceinline__ SegSums seg_back(const LibView& L, const DGate& d, co
       const float dp = tail ? Pn - Pg : 0.f;
       const float add = dp * (float)(int32_t)(bend - t) * 1e-6f;
       const bool nb = bn != pb;
-      red_bin_if(nb, d.W->bins, pb, pe, pdp);
+      if (CMP && !GL) {  // components without glitches: one {internal, switching, correction, step} reduction
+        red_cbin_if(nb, d.W->cbins, pb, pi, ps, pc, pdp);
+      } else {
+        red_bin_if(nb, d.W->bins, pb, pe, pdp);
+        if (CMP) red_cbin_if(nb, d.W->cbins, pb, pi, ps, pg, pc);
+      }
       if (CMP) {
-        red_cbin_if(nb, d.W->cbins, pb, pi, ps, pg, pc);
         pi = (nb ? 0.f : pi) + (Er - Eo);
         ps = (nb ? 0.f : ps) + Eo;
         pg = (nb ? 0.f : pg) + Eg;
@@ -498,8 +502,12 @@ __device__ __forceinline__ SegSums seg_back(const LibView& L, const DGate& d, co
     event(k, t, m, (k + 1 < K && (FULL || k + 1 < q.nk)) ? r.x : q.t_after);
   }
   if (!BWD && (FULL || q.nk > 0)) {
-    red_bin(d.W->bins, pb, pe, pdp);
-    if (CMP) red_cbin(d.W->cbins, pb, pi, ps, pg, pc);
+    if (CMP && !GL) {
+      red_cbin(d.W->cbins, pb, pi, ps, pc, pdp);
+    } else {
+      red_bin(d.W->bins, pb, pe, pdp);
+      if (CMP) red_cbin(d.W->cbins, pb, pi, ps, pg, pc);
+    }
   }
   if (!(tog & 1u)) report_error(err, GTP_ENOTOGGLE, q.s0 + lane * K);  // located exactly by the host
   // gate end: leakage to the window end and the final state
@@ -859,8 +867,12 @@ __device__ __forceinline__ WalkOut walk_gate(const LibView& L, const NetView& N,
         const float add = dp * (float)(int32_t)((bn + 1u) * bin_ps - t) * 1e-6f;
         if (bn != pb) {
           if (pb != kNoTime) {
-            red_bin(W.bins, pb, pe, pdp);
-            if (CMP) red_cbin(W.cbins, pb, pi, ps, pg, pc);
+            if (CMP && !GL) {
+              red_cbin(W.cbins, pb, pi, ps, pc, pdp);
+            } else {
+              red_bin(W.bins, pb, pe, pdp);
+              if (CMP) red_cbin(W.cbins, pb, pi, ps, pg, pc);
+            }
           }
           pb = bn;
           pe = 0.f;
@@ -889,8 +901,12 @@ __device__ __forceinline__ WalkOut walk_gate(const LibView& L, const NetView& N,
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   if (!BWD && pb != kNoTime) {
-    red_bin(W.bins, pb, pe, pdp);
-    if (CMP) red_cbin(W.cbins, pb, pi, ps, pg, pc);
+    if (CMP && !GL) {
+      red_cbin(W.cbins, pb, pi, ps, pc, pdp);
+    } else {
+      red_bin(W.bins, pb, pe, pdp);
+      if (CMP) red_cbin(W.cbins, pb, pi, ps, pg, pc);
+    }
   }
   // the gate's end: leakage to the window end, and the final state
   if (!bad) {
@@ -950,7 +966,7 @@ __host__ __device__ inline size_t union_area(int K, int n_leak, bool bwd, bool g
 // two (measured on the large workload: 16 records per lane at two CTAs
 // 1.18 ms, at three 1.38 ms).
 template <int K, bool BWD, bool GL, bool CMP>
-__global__ void __launch_bounds__(kWalkThreads, (BWD || GL || CMP || K == 16) ? 2 : 3)
+__global__ void __launch_bounds__(kWalkThreads, (BWD || GL || K == 16) ? 2 : 3)
     k_walk(LibView L, NetView N, WalkArgs A) {
   constexpr int SEG = 32 * K;
   extern __shared__ __align__(16) unsigned char smem[];
