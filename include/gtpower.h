@@ -268,9 +268,9 @@ int gtp_run_power(gtp_ctx* ctx, int32_t window, int32_t bin_ps, double* waveform
  *     bin is that component's energy in the bin divided by bin_ps; the four
  *     rows add up to waveform_w up to FP32 rounding.  Required.
  *   waveform_w [n_bins] or NULL: the total, as gtp_run_power writes it.
- * The walk keeps one more 16-byte accumulator per bin and issues one more
- * reduction per bin update, so it costs more than gtp_run_power.  Per-gate
- * results are kept as for gtp_run_power.  flags: GTP_HOST or GTP_DEVICE for
+ * The walk keeps 16-byte accumulators per bin: without glitch detection it
+ * costs about what gtp_run_power costs; with it, one more reduction per bin
+ * update.  Per-gate results are kept as for gtp_run_power.  flags: GTP_HOST or GTP_DEVICE for
  * both outputs; GTP_GRAPH is rejected (GTP_EINVAL).  Errors as gtp_run_power.
  */
 int gtp_run_power_components(gtp_ctx* ctx, int32_t window, int32_t bin_ps, double* waveform_w,
