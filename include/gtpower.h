@@ -185,7 +185,7 @@ int gtp_load_netlist(gtp_ctx* ctx, int64_t n_gates, const int32_t* cell, const f
 int gtp_set_load(gtp_ctx* ctx, const float* load_ff, int flags);
 
 /*
- * Clock-cycle glitch detection [Sec. 2.4.1, Eq. glitch scaling ratio,
+ * Clock-cycle glitch detection [Sec. 2.4.1, Eq. 2,
  * Algorithm 1 GlitchDetectUpdate] for the following runs (forward, batched
  * and adjoint).  With clock_ps > 0, an event on a pin that already had an
  * event earlier in the same clock cycle floor(t / clock_ps) (t in window
@@ -209,7 +209,7 @@ int gtp_set_glitch(gtp_ctx* ctx, int64_t clock_ps, const float* out_slew_ps, int
 int gtp_gate_glitch(gtp_ctx* ctx, int32_t window, double* e_gl, int flags);
 
 /*
- * Design-level power of the last run of `window` [Eq. average power,
+ * Design-level power of the last run of `window` [Eq. 3,
  * Sec. 2.4.1; peak power, Sec. 5], into out[7] (host, FP64):
  *   out[0..3]  leakage, internal, switching and glitch power in W: the
  *              per-gate energies summed over the design, over window_ps
@@ -260,7 +260,7 @@ int gtp_run_power(gtp_ctx* ctx, int32_t window, int32_t bin_ps, double* waveform
 
 /*
  * gtp_run_power that also returns the waveform of each power component
- * [Sec. 2.4: leakage, internal, switching and glitch power; Sec. 2.4.1 for
+ * [Sec. 2.2: leakage, internal, switching and glitch power; Sec. 2.4.1 for
  * the glitch component, which is zero unless gtp_set_glitch set a clock].
  *   components_w [4][n_bins] (FP64, W), component-major: row 0 leakage, row 1
  *     internal (input-pin events that are not glitches), row 2 switching
@@ -281,11 +281,11 @@ int gtp_run_power_components(gtp_ctx* ctx, int32_t window, int32_t bin_ps, doubl
  * window (they compute the same waveform and per-gate results):
  *   GTP_SCHEME_NAIVE    Naive-D (one thread per event, the gate state rebuilt
  *                       by binary searches in each pin's event stream,
- *                       Sec. 3.2.1) and Naive-L (one thread per gate and
+ *                       Sec. 2.4.1) and Naive-L (one thread per gate and
  *                       window of scheme_ncyc_fix bins, leakage added to every
- *                       overlapped bin, Sec. 3.2.2), with state-dependent
+ *                       overlapped bin, Sec. 2.4.2), with state-dependent
  *                       energies found by traversing the state patterns
- *                       (Sec. 4, challenge 1);
+ *                       (Sec. 3.1);
  *   GTP_SCHEME_SIPL     the same with state-indexed lookup (Sec. 4.1);
  *   GTP_SCHEME_DENSITY  and Naive-L's windows sized per gate by event density
  *                       (Sec. 4.2: scheme_evt_tgt events a thread, parallelism

@@ -11,7 +11,7 @@ objects with the fields of ``synth.Library``, ``synth.Netlist`` and
 ``synth.Trace`` work.
 
 Paper anchors: events and gate state (Sec. 2.1); power models (Sec. 2.2);
-switching energy equation and leakage energy equation (Sec. 2.4); per-bin
+switching energy (Eq. 1, Sec. 2.4.1) and leakage energy (Eq. 4, Sec. 2.4.2); per-bin
 leakage split (Sec. 2.4.2); timestamp-group semantics (Algorithm 1);
 state-indexed lookup (Sec. 4.1).
 """
@@ -217,7 +217,7 @@ def bilinear_dload(slew_axis, load_axis, table, slew: float, load: float) -> flo
 
 
 def design_power(result: dict, window_ps: int, bin_ps: int) -> dict:
-    """Design-level power from a walk() result (W) [Eq. average power,
+    """Design-level power from a walk() result (W) [Eq. 3,
     Sec. 2.4.1: a component's energy over the analysis time, here the
     window; peak power, Sec. 5: the largest bin of the waveform]."""
     to_w = 1e-3 / float(window_ps)

@@ -18,9 +18,9 @@
  *     interpolated bilinearly at (input slew, output load), times the cell's
  *     energy scale [Sec. 2.2; Sec. 4.1 state-indexed lookup].
  *   * Switching energy of an output-pin event: 0.5*C*Vdd^2 per output toggle
- *     [Eq. switching energy, read as half of c*v^2 per toggle].
+ *     [Eq. 1, read as half of c*v^2 per toggle].
  *   * Leakage: the state-dependent leakage power holds between events; the
- *     energy of an interval is P*dt [Eq. leakage energy], and each interval
+ *     energy of an interval is P*dt [Eq. 4], and each interval
  *     is split over the time bins it overlaps in proportion to the overlap
  *     [Sec. 2.4.2, waveform accumulation].
  *   * Dynamic energy goes to the bin containing the event time.
@@ -28,8 +28,8 @@
  *     already had an event earlier in the same clock cycle floor(t / T_clk)
  *     is a glitch event [Sec. 2.4.1, clock-cycle glitch detection;
  *     Algorithm 1, GlitchDetectUpdate].  Its dynamic energy is scaled by
- *     r_gl = min(1, (2 * pulse_width / (rSlew + fSlew))^2) [Eq. glitch
- *     scaling ratio], with pulse_width the time since that pin's previous
+ *     r_gl = min(1, (2 * pulse_width / (rSlew + fSlew))^2) [Eq. 2], with
+ *     pulse_width the time since that pin's previous
  *     event and rSlew, fSlew the pin's rise and fall transition times; the
  *     scaled energy is glitch energy (not internal or switching energy) and
  *     goes to the event's bin.
@@ -210,11 +210,10 @@ static void bin_add_interval(const binner* B, double P, int64_t a, int64_t b) {
  * index in *bad_record.
  * comp_bins (optional) receives the same bins split by component, as four
  * consecutive rows of the bins' length: leakage, internal, switching and
- * glitch energy (Sec. 2.4: the power components; their sum is `bins`).
+ * glitch energy (Sec. 2.2: the power components; their sum is `bins`).
  */
 /* Glitch scaling ratio of an event pulse_width ps after the previous event on
- * its pin, for rise + fall transition time sum_slew ps [Eq. glitch scaling
- * ratio]; a pin without transition time (sum <= 0) swings fully: ratio 1. */
+ * its pin, for rise + fall transition time sum_slew ps [Eq. 2]; a pin without transition time (sum <= 0) swings fully: ratio 1. */
 static double glitch_ratio(double pulse_width, double sum_slew) {
   if (sum_slew <= 0.0) return 1.0;
   double x = 2.0 * pulse_width / sum_slew;

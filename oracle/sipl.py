@@ -1,7 +1,7 @@
 """Liberty-style state patterns resolved by traversal.
 
 TEST INFRASTRUCTURE ONLY (imported by ``tests/``).  This is the plain
-definition that state-indexed lookup replaces (Sec. 4, challenge 1, and the
+definition that state-indexed lookup replaces (Sec. 3.1, and the
 fallback path of Sec. 4.1): to find the power item of a state, scan the
 cell's state patterns in list order and take the first whose fixed pins
 match the state; a state no pattern matches takes the default item.  A

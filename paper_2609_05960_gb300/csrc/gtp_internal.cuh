@@ -140,7 +140,7 @@ __device__ __forceinline__ uint32_t bin_of(uint32_t t, uint32_t magic, uint32_t 
   return b + (((b + 1u) * bin_ps <= t) ? 1u : 0u);
 }
 
-// Glitch scaling ratio (Eq. glitch scaling ratio) of an event `width` ps
+// Glitch scaling ratio (Eq. 2) of an event `width` ps
 // after the previous event on its pin, for the pin's rise + fall transition
 // time sum: min(1, (2 * width / sum)^2); a pin without transition time
 // (sum <= 0) swings fully.

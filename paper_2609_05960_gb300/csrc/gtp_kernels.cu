@@ -83,8 +83,8 @@ __global__ void k_event_desc(LibView L, NetView N, uint4* __restrict__ desc) {
 // ------------------------------------------------------------------ per-gate energy tables
 // For each gate whose cell has at most kGateTabMaxIn inputs, the energy of
 // every (input pin, edge, side state) lookup at the gate's slews and load,
-// i.e. the bilinear NLDM value of Sec. 2.3 on the state-indexed table of
-// Sec. 4.1, and the switching energy of its output (Eq. switching).  Entry
+// i.e. the bilinear NLDM value of Sec. 2.2.1 on the state-indexed table of
+// Sec. 4.1, and the switching energy of its output (Eq. 1).  Entry
 // (pin << n_in) | s, with s the input-pin state before the event: the pin's
 // own bit in s is its old value (so the edge is its complement) and the other
 // bits are the side state; the output pin is pin n_in.  Forward table:

@@ -90,7 +90,7 @@ __device__ __forceinline__ int na_segment(const float* axis, int n, float x) {
 
 // One thread per gate (Algorithm 1 on one gate): timestamp groups looked up
 // at the pre-group state, the state updated after the group, leakage held
-// between groups (Sec. 2.4.2), bilinear internal energy (Sec. 2.3) and
+// between groups (Sec. 2.4.2), bilinear internal energy (Sec. 2.2.1) and
 // 0.5 * C * Vdd^2 per output toggle (Sec. 2.4.1).  Bins receive the same
 // {energy, leakage step} pairs as the engine's walks.
 __global__ void __launch_bounds__(kNaThreads) k_noalloc_walk(NaArgs a) {

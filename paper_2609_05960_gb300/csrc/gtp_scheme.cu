@@ -45,7 +45,7 @@ __device__ float lut_energy(const LibView& L, const float* __restrict__ tab, flo
 
 // Internal-power table of (cell, pin, edge) at side-input state `side`.
 // SIPL (Sec. 4.1) indexes it; without SIPL the group's state patterns are
-// scanned, pin by pin, until one matches (Sec. 4, challenge 1: O(n_pin *
+// scanned, pin by pin, until one matches (Sec. 3.1: O(n_pin *
 // n_sd) per lookup).
 template <bool SIPL>
 __device__ int64_t int_table(const SchemeArgs& A, const CellInfo& ci, uint32_t pin, uint32_t edge, uint32_t side) {
@@ -97,7 +97,7 @@ __device__ __forceinline__ float slew_sum(const NetView& N, const CellInfo& ci, 
 }
 
 // Leakage power P (nW) held over [a, b) into every bin it overlaps, one
-// atomic per bin (the cycle-side work of Sec. 3.2.2); returns the energy (fJ).
+// atomic per bin (the cycle-side work of Sec. 2.4.2); returns the energy (fJ).
 __device__ double leak_into_bins(double* ebins, float P, uint32_t a, uint32_t b, uint32_t bin_ps) {
   double tot = 0.0;
   uint32_t k = a / bin_ps;
@@ -169,7 +169,7 @@ __global__ void k_pin_streams(LibView L, NetView N, const WinDesc* __restrict__ 
 }
 
 // ------------------------------------------------------------------ Naive-D
-// One thread per event (Sec. 3.2.1): reconstruct the gate state before the
+// One thread per event (Sec. 2.4.1): reconstruct the gate state before the
 // event by a binary search in each pin's stream, look up and interpolate the
 // energy, detect a glitch from the previous event of the pin's stream, add
 // the energy to its bin and to the gate's reduction row.
@@ -249,7 +249,7 @@ __device__ __forceinline__ void apply_group(const SchemeArgs& A, WindowCursor& c
     }
 }
 
-// Naive-L's work for one gate and window [t0, t1) (Sec. 3.2.2): leakage of
+// Naive-L's work for one gate and window [t0, t1) (Sec. 2.4.2): leakage of
 // every inter-event interval into the bins it overlaps.
 template <bool SIPL>
 __device__ void leak_window(const LibView& L, const NetView& N, const SchemeArgs& A, const WinDesc& W, int64_t g,
@@ -325,7 +325,7 @@ __device__ void fused_window(const LibView& L, const NetView& N, const SchemeArg
     if (sum[k] != 0.0) atomicAdd(row + k, sum[k]);
 }
 
-// Naive-L: one thread per gate and window of ncyc_fix bins (Sec. 3.2.2).
+// Naive-L: one thread per gate and window of ncyc_fix bins (Sec. 2.4.2).
 template <bool SIPL>
 __global__ void __launch_bounds__(kSchemeTpb) k_naive_l(LibView L, NetView N, SchemeArgs A, int64_t thr_per_gate,
                                                          int64_t total) {

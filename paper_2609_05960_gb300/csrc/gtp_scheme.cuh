@@ -1,7 +1,7 @@
 // The paper's own GPU schemes, restated as sm_103a kernels for the ablation
-// against the engine's walk: Naive-D (one event per thread, Sec. 3.2.1),
-// Naive-L (one window of n_cyc bins per thread and gate, Sec. 3.2.2), the
-// state-pattern traversal they start from (Sec. 4: challenge 1) and its
+// against the engine's walk: Naive-D (one event per thread, Sec. 2.4.1),
+// Naive-L (one window of n_cyc bins per thread and gate, Sec. 2.4.2), the
+// state-pattern traversal they start from (Sec. 3.1) and its
 // replacement by state-indexed lookup (SIPL, Sec. 4.1), event-density-aware
 // per-gate partitioning (Sec. 4.2), and the fused kernel (Sec. 4.3,
 // Algorithm 1) with the two-phase per-gate reduction (Sec. 4.4).

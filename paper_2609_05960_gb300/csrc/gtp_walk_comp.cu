@@ -1,5 +1,5 @@
 // The fused forward walk that also keeps the power components' bins apart
-// (leakage, internal, switching and glitch energy, Sec. 2.4), compiled apart
+// (leakage, internal, switching and glitch energy, Sec. 2.2), compiled apart
 // from the plain walk so that the two build in parallel.
 #include "gtp_walk_body.cuh"
 

@@ -1,4 +1,4 @@
-"""Per-component waveforms (leakage, internal, switching, glitch; Sec. 2.4)
+"""Per-component waveforms (leakage, internal, switching, glitch; Sec. 2.2)
 on the GPU against the FP64 oracle, through the C ABI, for every walk (one
 thread per gate, the density-split walk at three segment lengths), with and
 without glitch detection.

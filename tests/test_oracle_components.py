@@ -1,4 +1,4 @@
-"""Pins for the oracle's per-component waveform (Sec. 2.4: the leakage,
+"""Pins for the oracle's per-component waveform (Sec. 2.2: the leakage,
 internal, switching and glitch components of the power; Sec. 2.4.1 glitch
 energy): a hand-worked trace, the per-picosecond simulator, and the
 conservation identities that tie the components to the total waveform and to

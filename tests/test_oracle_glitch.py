@@ -1,5 +1,5 @@
 """Pins for the oracle's glitch detection and scaling (Sec. 2.4.1 clock-cycle
-glitch detection; Eq. glitch scaling ratio; Algorithm 1 GlitchDetectUpdate):
+glitch detection; Eq. 2; Algorithm 1 GlitchDetectUpdate):
 a hand-worked trace, closed forms, the per-picosecond counter simulator, the
 conservation of energy when every ratio is one, and central differences of
 the adjoint.  CPU only."""
