@@ -327,8 +327,8 @@ def run_ours(args, cfg_name):
     if not args.no_e2e:
         rec_h = torch.empty((n_ev, 2), dtype=torch.int32, pin_memory=True)
         rec_h.copy_(rec)
-        off_h = trace.offsets
-        init_h = trace.init_state
+        off_h = torch.from_numpy(trace.offsets).pin_memory()
+        init_h = torch.from_numpy(trace.init_state).pin_memory()
         wave_h = torch.empty(n_bins, dtype=torch.float64, pin_memory=True)
         outs_h = [torch.empty(G, dtype=torch.float64, pin_memory=True) for _ in range(3)]
         cnt_h = torch.empty(G, dtype=torch.int64, pin_memory=True)
@@ -359,9 +359,9 @@ def run_ours(args, cfg_name):
 
         d2h = n_bins * 8 + G * (8 * 3 + 8 + 1)
         t_e2e = time_e2e(True)
-        h2d = pk_h.numel() * 4 + off_h.nbytes + init_h.nbytes
+        h2d = pk_h.numel() * 4 + off_h.numel() * 8 + init_h.numel()
         t_e2e8 = time_e2e(False)
-        h2d8 = rec_h.numel() * 4 + off_h.nbytes + init_h.nbytes
+        h2d8 = rec_h.numel() * 4 + off_h.numel() * 8 + init_h.numel()
         e2e = {"value": ws * args.e2e_steps * n_ev / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * t_e2e / args.e2e_steps,
                "input": "packed transfer form (gtp_pack_events, 4.125 B a record), streamed in 8 chunks",

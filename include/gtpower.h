@@ -315,9 +315,11 @@ int gtp_run_power_scheme(gtp_ctx* ctx, int32_t window, int32_t bin_ps, int32_t s
  * One window run straight from host memory, in chunks [Sec. 5, event
  * chunking with the packing and copy of the next chunk overlapping the
  * kernel]: the window's records are copied to the GPU in n_chunks gate-range
- * chunks of about n_events / n_chunks records, through two device buffers of
- * the largest chunk's size, and the walk of each chunk overlaps the copy of
- * the next.  A trace larger than the device memory runs this way.  Results
+ * chunks, through two device buffers of the largest chunk's size, and the
+ * walk of each chunk overlaps the copy of the next.  Chunks hold about equal
+ * numbers of records, except that with three or more chunks the first holds
+ * half and the last a quarter of the others' share (the first copy and the
+ * last walk are the parts that cannot overlap).  A trace larger than the device memory runs this way.  Results
  * equal gtp_load_events + gtp_run_power on the same inputs; the per-gate
  * results are kept for gtp_gate_energy / gtp_gate_glitch, but the records
  * are not: the window must be loaded again for any other run.

@@ -1186,12 +1186,17 @@ int gtp_run_power_streamed(gtp_ctx* ctx, int32_t window, int64_t window_ps, int6
       CU(cudaEventCreateWithFlags(&ctx->ev_walked[i], cudaEventDisableTiming), "event");
     }
   }
-  // chunks: gate ranges of about n_events / n_chunks records each
+  // chunks: gate ranges by record count, the first at half and the last at a
+  // quarter of the others (with three or more chunks): only the first chunk's
+  // host checks and copy, and the last chunk's walk, stay outside the overlap
+  std::vector<double> cum(n_chunks + 1, 0.0);
+  for (int c = 0; c < n_chunks; ++c)
+    cum[c + 1] = cum[c] + (n_chunks < 3 ? 1.0 : c == 0 ? 0.5 : c == n_chunks - 1 ? 0.25 : 1.0);
   std::vector<int64_t> gb(n_chunks + 1);
   gb[0] = 0;
   gb[n_chunks] = G;
   for (int c = 1; c < n_chunks; ++c) {
-    const int64_t target = n_events / n_chunks * c + (n_events % n_chunks) * c / n_chunks;
+    const int64_t target = (int64_t)((double)n_events * (cum[c] / cum[n_chunks]));
     gb[c] = std::lower_bound(gate_offsets, gate_offsets + G + 1, target) - gate_offsets;
     if (gb[c] < gb[c - 1]) gb[c] = gb[c - 1];
     if (gb[c] > G) gb[c] = G;
@@ -1260,7 +1265,9 @@ int gtp_run_power_streamed(gtp_ctx* ctx, int32_t window, int64_t window_ps, int6
   for (int c = 0; c < n_chunks; ++c) {
     const int b = c & 1;
     bool ok = gate_offsets[gb[c]] >= 0 && gate_offsets[gb[c + 1]] <= n_events;
-    for (int64_t g = gb[c]; ok && g < gb[c + 1]; ++g) ok = gate_offsets[g + 1] >= gate_offsets[g];
+    int bad = 0;  // branch-free, so that the compiler vectorises the scan
+    for (int64_t g = gb[c]; g < gb[c + 1]; ++g) bad |= gate_offsets[g + 1] < gate_offsets[g];
+    ok = ok && !bad;
     if (!ok) {
       cudaStreamSynchronize(ctx->copy_stream);
       cudaStreamSynchronize(st);
