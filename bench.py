@@ -403,15 +403,20 @@ def run_ours(args, cfg_name):
                 gtpower.gtp_run_power_streamed(ctx, 1, cfg.window_ps, off_h, rec_h, init_h, cfg.bin_ps, wave_h, 8)
             gtpower.gtp_gate_energy(ctx, 1, outs_h[0], outs_h[1], outs_h[2], cnt_h, fin_h)
 
-        def time_e2e(packed):
+        def time_e2e(packed, trials=5):
+            # the host link and host memory are shared with the machine's other jobs: the median of a few
+            # trials of e2e_steps steps each keeps a transient slowdown out of the figure
             e2e_step(packed)
             torch.cuda.synchronize(dev)
-            barrier(pg)
-            t0 = time.perf_counter()
-            for _ in range(args.e2e_steps):
-                e2e_step(packed)
-            torch.cuda.synchronize(dev)
-            return max_over_ranks(pg, time.perf_counter() - t0)
+            times = []
+            for _ in range(trials):
+                barrier(pg)
+                t0 = time.perf_counter()
+                for _ in range(args.e2e_steps):
+                    e2e_step(packed)
+                torch.cuda.synchronize(dev)
+                times.append(max_over_ranks(pg, time.perf_counter() - t0))
+            return statistics.median(times)
 
         d2h = n_bins * 8 + G * (8 * 3 + 8 + 1)
         t_e2e = time_e2e(True)
@@ -421,6 +426,7 @@ def run_ours(args, cfg_name):
         e2e = {"value": ws * args.e2e_steps * n_ev / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * t_e2e / args.e2e_steps,
                "input": "packed transfer form (gtp_pack_events, 4.125 B a record), streamed in 8 chunks",
+               "timing": f"median of 5 trials of {args.e2e_steps} steps, host clock around CUDA-synchronised steps",
                "records_8b": {"value": ws * args.e2e_steps * n_ev / t_e2e8, "h2d_bytes_per_step": int(h2d8),
                               "ms_per_step": 1e3 * t_e2e8 / args.e2e_steps}}
         del rec_h, pk_h
