@@ -59,12 +59,13 @@ def parse():
     p.add_argument("--events", type=int, default=0,
                    help="scale the configuration to this many events (same gates and distribution; "
                         "for profiling a smaller case)")
-    p.add_argument("--sweep", default="", choices=["", "contention", "streamed", "schemes", "adjoint"],
+    p.add_argument("--sweep", default="", choices=["", "contention", "streamed", "schemes", "adjoint", "glitch"],
                    help="contention: uniform high activity (1, 2, 4, 8 events per gate per 1k bins); "
                         "streamed: the large window streamed from pinned host memory in 1-32 chunks, "
                         "against a plain copy of its records; schemes: the paper's GPU schemes (naive, "
                         "state-indexed lookup, density-aware partitioning, fused kernel) against this "
                         "engine's walk; adjoint: the adjoint workload's forward and backward alone (--events "
+                        "scales it); glitch: the large workload's plain walk, then with glitch detection (--events "
                         "scales it); instead of the default run, one JSON line per case")
     return p.parse_args()
 
@@ -815,8 +816,48 @@ def run_adjoint_sweep(args):
     eng.close()
 
 
+def run_glitch_sweep(args):
+    """The large workload (scaled by --events): the plain walk, then the same
+    window with glitch detection (as in the default run's extras)."""
+    import torch
+
+    import synth
+    from paper_2609_05960_gb300 import Engine, gtpower
+
+    dev = torch.device("cuda", 0)
+    cfg = config_of(args, "large")
+    lib = synth.make_library(cfg.seed_lib)
+    net = synth.make_netlist(lib, cfg.n_gates, cfg.seed_net)
+    counts = synth.zipf_counts(cfg.n_gates, cfg.n_events, cfg.zipf_s, cfg.cap, cfg.seed_ev)
+    tr, rec = synth.make_trace_gpu(net, counts, cfg.window_ps, cfg.seed_ev, cfg.tie_p, device=dev)
+    eng = Engine(0)
+    eng.load_library(lib)
+    eng.load_netlist(net)
+    eng.load_events(0, window_ps=cfg.window_ps, offsets=torch.from_numpy(tr.offsets).to(dev), records=rec,
+                    init_state=torch.from_numpy(tr.init_state).to(dev), borrow=True)
+    nb = cfg.window_ps // cfg.bin_ps
+    wave = torch.empty(nb, dtype=torch.float64, device=dev)
+    steps = max(1, min(args.steps, 20))
+    run = lambda: gtpower.gtp_run_power(eng.ctx, 0, cfg.bin_ps, wave, graph=True)
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize(dev)
+    eng.set_param("timing", 1)
+    _events_per_s(run, steps, dev)
+    walk_ms = eng.get_param("t_walk_ns") * 1e-6 / max(eng.get_param("n_timed"), 1)
+    eng.set_param("timing", 0)
+    n = int(tr.n_events)
+    out = measure_glitch(eng, dev, cfg, wave, walk_ms, n, steps)
+    print(json.dumps({"sweep": "glitch", "workload": workload_desc(cfg, nb), "events": n, "plain_walk_ms": walk_ms,
+                      **out}), flush=True)
+    eng.close()
+
+
 def main():
     args = parse()
+    if args.sweep == "glitch":
+        run_glitch_sweep(args)
+        return
     if args.sweep == "adjoint":
         run_adjoint_sweep(args)
         return
