@@ -386,6 +386,17 @@ int gtp_run_power_backward(gtp_ctx* ctx, int32_t window, int32_t bin_ps, const f
 int gtp_autotune(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_t bin_ps, int32_t iters,
                  double* best_ms);
 
+/*
+ * The GPU's rate for the walk's bin updates, measured: n_red
+ * fire-and-forget float reductions of `width` floats (2: the 8-byte
+ * {energy, leakage step} update of a bin; 4: the 16-byte update of the
+ * component runs) into places of an array of n_slots entries (use the bin
+ * count) picked by an integer hash, timed with CUDA events after one
+ * warm-up launch.  *per_s receives reductions per second.  The array is
+ * context scratch of 16 B a slot.  Errors: GTP_EINVAL for bad arguments.
+ */
+int gtp_measure_reductions(gtp_ctx* ctx, int32_t n_slots, int32_t width, int64_t n_red, double* per_s);
+
 /* Engine tuning knobs; value < 0 restores the default.  Keys:
  * "records_per_thread" (4, 8, 16; events per lane of a dense segment),
  * "ctas_per_sm" (0 = full occupancy), "dense_min" (gates with more events are cut into segments; 1..4096),

@@ -123,6 +123,7 @@ struct gtp_ctx {
   // the paper's schemes: state patterns of the library's tables and leakage
   // entries, FP64 bins, per-gate reduction rows, timing events
   DevBuf pat_int, pat_leak, sch_ebins, sch_R;
+  DevBuf probe;  // reduction-rate probe scratch
   bool pat_ok = false;
   cudaEvent_t sch_ev[2] = {};
   int64_t p_evt_tgt = 8, p_thr_floor = 512, p_ncyc_fix = 1;
@@ -701,7 +702,7 @@ void gtp_destroy(gtp_ctx* ctx) {
                     &ctx->cell, &ctx->load, &ctx->slew, &ctx->desc, &ctx->plan, &ctx->glist, &ctx->gtab, &ctx->gtab_bwd,
                     &ctx->counters, &ctx->first_bad, &ctx->out_slew, &ctx->dp_scratch,
                     &ctx->cell_acc, &ctx->grad, &ctx->gtiles, &ctx->dC_scratch, &ctx->d_err, &ctx->pat_int,
-                    &ctx->pat_leak, &ctx->sch_ebins, &ctx->sch_R})
+                    &ctx->pat_leak, &ctx->sch_ebins, &ctx->sch_R, &ctx->probe})
     b->release();
   for (auto& e : ctx->sch_ev)
     if (e) cudaEventDestroy(e);
@@ -1467,6 +1468,32 @@ int gtp_autotune(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_
   ctx->timing = keep_timing;
   if (best_ms) *best_ms = best;
   return rc;
+}
+
+int gtp_measure_reductions(gtp_ctx* ctx, int32_t n_slots, int32_t width, int64_t n_red, double* per_s) {
+  if (!ctx) return GTP_EINVAL;
+  if (n_slots <= 0 || (width != 2 && width != 4) || n_red <= 0 || !per_s)
+    return fail(ctx, GTP_EINVAL, "measure_reductions: n_slots > 0, width 2 or 4, n_red > 0 and an output");
+  DeviceGuard dg(ctx->device);
+  CU(ctx->probe.reserve(sizeof(float4) * (size_t)n_slots), "alloc probe");
+  CU(cudaMemsetAsync(ctx->probe.p, 0, sizeof(float4) * (size_t)n_slots, ctx->stream), "zero probe");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CU(cudaEventCreate(&e0), "event");
+  CU(cudaEventCreate(&e1), "event");
+  float4* slots = ctx->probe.as<float4>();
+  cudaError_t e = launch_red_probe(slots, (uint32_t)n_slots, width, n_red, ctx->n_sm, ctx->stream);  // warm-up
+  if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+  if (e == cudaSuccess) e = launch_red_probe(slots, (uint32_t)n_slots, width, n_red, ctx->n_sm, ctx->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CU(e, "measure_reductions");
+  ctx->launches += 2;
+  *per_s = ms > 0.f ? (double)n_red / (ms * 1e-3) : 0.0;
+  return GTP_OK;
 }
 
 int gtp_set_param(gtp_ctx* ctx, const char* key, int64_t value) {

@@ -260,6 +260,9 @@ cudaError_t launch_validate(const LibView& L, const NetView& N, const WinDesc* w
 cudaError_t launch_validate_if(const LibView& L, const NetView& N, const WinDesc* win, const DevError* err,
                                int64_t n_gates, unsigned long long* first, cudaStream_t st);
 int merge_tiles(int n_bins);
+// The reduction-rate probe: n_red reductions of `width` (2 or 4) floats into
+// hashed places of slots[n_slots] (16 B a slot).
+cudaError_t launch_red_probe(float4* slots, uint32_t n_slots, int width, int64_t n_red, int n_sm, cudaStream_t st);
 // Unpack records [r0, r0 + n) of the packed transfer form into out[0, n):
 // `anchors` holds the anchors of blocks r0 / 32 .. (r0 + n - 1) / 32, `words`
 // the n words (16-byte aligned).

@@ -287,6 +287,40 @@ cudaError_t launch_walk_per_gate(const LibView& L, const NetView& N, const WinDe
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ reduction-rate probe
+// n_red fire-and-forget float reductions of W floats (2: the walk's {energy,
+// step} bin update; 4: the component runs' update) into places of an
+// n_slots array picked by an integer mix of the reduction's number: the rate
+// the L2 sustains for the walk's bin updates.
+__device__ __forceinline__ uint32_t probe_mix(uint32_t x) {
+  x = (x ^ 61u) ^ (x >> 16);
+  x *= 9u;
+  x ^= x >> 4;
+  x *= 0x27d4eb2du;
+  return x ^ (x >> 15);
+}
+
+template <int W>
+static __global__ void k_red_probe(float4* __restrict__ slots, uint32_t n_slots, int64_t n_red) {
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_red; r += nth) {
+    const uint32_t i = probe_mix((uint32_t)r) % n_slots;
+    if (W == 2)
+      asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(reinterpret_cast<float2*>(slots) + i), "f"(1.f),
+                   "f"(0.5f)
+                   : "memory");
+    else
+      red_cbin(slots, i, 1.f, 0.5f, 0.25f, 0.125f);
+  }
+}
+
+cudaError_t launch_red_probe(float4* slots, uint32_t n_slots, int width, int64_t n_red, int n_sm, cudaStream_t st) {
+  const unsigned grid = (unsigned)(n_sm > 0 ? n_sm * 8 : 1024);
+  if (width == 4) k_red_probe<4><<<grid, 256, 0, st>>>(slots, n_slots, n_red);
+  else k_red_probe<2><<<grid, 256, 0, st>>>(slots, n_slots, n_red);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ packed transfer form
 // Four records a thread: one 16-byte load of words, two 16-byte stores of
 // records; t = anchor of the record's block + the word's high 27 bits.

@@ -31,7 +31,7 @@ ABI_SYMBOLS = ["gtp_create", "gtp_destroy", "gtp_set_stream", "gtp_last_error", 
                "gtp_set_param", "gtp_get_param", "gtp_run_power_noalloc", "gtp_set_glitch", "gtp_gate_glitch",
                "gtp_run_power_streamed", "gtp_design_power", "gtp_run_power_components",
                "gtp_run_power_scheme", "gtp_sipl_expand",
-               "gtp_pack_events"]
+               "gtp_pack_events", "gtp_measure_reductions"]
 
 
 class GtpError(RuntimeError):
@@ -69,6 +69,7 @@ def load(path: str = LIB_PATH):
         "gtp_run_power": ([P, I32, I32, P, ctypes.c_int], ctypes.c_int),
         "gtp_run_power_components": ([P, I32, I32, P, P, ctypes.c_int], ctypes.c_int),
         "gtp_pack_events": ([I64, P, P], ctypes.c_int),
+        "gtp_measure_reductions": ([P, I32, I32, I64, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "gtp_sipl_expand": ([I32, I32, I32, I32, P, P, P, P, P, P, I32, P, P, P, F, P, P], ctypes.c_int),
         "gtp_run_power_scheme": ([P, I32, I32, I32, P, ctypes.c_int, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
         "gtp_gate_energy": ([P, I32, P, P, P, P, P, ctypes.c_int], ctypes.c_int),
@@ -172,6 +173,13 @@ def gtp_set_glitch(ctx, clock_ps: int, out_slew=None) -> None:
     {fall, rise} output transition times in ps (float32)."""
     p, f, k = _ptr_flags(out_slew, np.float32)
     _check(ctx, load().gtp_set_glitch(ctx, int(clock_ps), p, f))
+
+
+def gtp_measure_reductions(ctx, n_slots: int, width: int = 2, n_red: int = 160_000_000) -> float:
+    """Bin-update reductions per second the GPU sustains (see the header)."""
+    out = ctypes.c_double(0.0)
+    _check(ctx, load().gtp_measure_reductions(ctx, int(n_slots), int(width), int(n_red), ctypes.byref(out)))
+    return float(out.value)
 
 
 def packed_words(n_events: int) -> int:
