@@ -42,7 +42,9 @@ extern "C" {
 #define GTP_ENOTOGGLE (-4)  /* an event sets a pin to the value it already has */
 #define GTP_ENOMEM (-5)     /* device or host allocation failed */
 #define GTP_ECUDA (-6)      /* a CUDA runtime call failed */
-#define GTP_ETIMEOUT (-7)   /* a bounded device wait expired */
+#define GTP_ETIMEOUT (-7)   /* a bounded device wait expired; reserved: no
+                               kernel of this engine waits on another block,
+                               so no call returns it at present */
 #define GTP_EDEVICE (-8)    /* a kernel reported an internal inconsistency */
 
 /* ---- memory-space flags ---------------------------------------------- */
@@ -162,8 +164,12 @@ int gtp_sipl_expand(int32_t n_in, int32_t n_slew, int32_t n_load, int32_t n_int_
 
 /*
  * Per-cell multipliers on internal energy and on leakage power (host arrays
- * of n_cells; NULL leaves that scale at 1).  They are the parameters the
- * adjoint differentiates.
+ * of n_cells; NULL leaves that scale at 1).  The paper has no counterpart:
+ * they are parameters of this engine's adjoint (gtp_run_power_backward).  An
+ * internal energy of cell c (the bilinear NLDM value of Sec. 2.2 / 2.4.1) is
+ * multiplied by escale[c]; a leakage power of cell c (the state-indexed
+ * value of Eq. 4) by lscale[c]; switching energy (Eq. 1) is not scaled.
+ * Errors: GTP_EINVAL without a library.
  */
 int gtp_set_scales(gtp_ctx* ctx, const float* escale, const float* lscale);
 
@@ -181,7 +187,9 @@ int gtp_load_netlist(gtp_ctx* ctx, int64_t n_gates, const int32_t* cell, const f
                      const float* slew_ps, int32_t slew_stride, int flags);
 
 /* Replace every gate's output load (fF) without reloading the netlist
- * (e.g. inside an optimisation loop driven by the adjoint). */
+ * (e.g. inside an optimisation loop driven by the adjoint).  The load is the
+ * c of the switching energy (Eq. 1) and the load coordinate of the NLDM
+ * interpolation (Sec. 2.4.1).  flags: GTP_HOST or GTP_DEVICE. */
 int gtp_set_load(gtp_ctx* ctx, const float* load_ff, int flags);
 
 /*
@@ -204,8 +212,9 @@ int gtp_set_load(gtp_ctx* ctx, const float* load_ff, int flags);
  */
 int gtp_set_glitch(gtp_ctx* ctx, int64_t clock_ps, const float* out_slew_ps, int flags);
 
-/* Per-gate glitch energy (fJ, FP64) of the last run of `window`: zeros if
- * that run did not detect glitches.  flags: GTP_HOST or GTP_DEVICE. */
+/* Per-gate glitch energy (fJ, FP64; the E_gl of Eq. 2 summed per gate,
+ * Sec. 4.3) of the last run of `window`: zeros if that run did not detect
+ * glitches.  flags: GTP_HOST or GTP_DEVICE. */
 int gtp_gate_glitch(gtp_ctx* ctx, int32_t window, double* e_gl, int flags);
 
 /*
@@ -225,7 +234,10 @@ int gtp_design_power(gtp_ctx* ctx, int32_t window, const double* waveform_w, int
 
 /*
  * Load one stimulus window's events as slot `window` (0 <= window < 1024;
- * reloading a slot replaces it).
+ * reloading a slot replaces it).  An event is a (value, timestamp) pair on
+ * one pin (Sec. 2.1); the paper keeps one stream per pin and merges them on
+ * the fly (Sec. 2.4.2, Algorithm 1), while here each gate's events arrive
+ * already merged into one time-ordered stream.
  *   window_ps     length of the analysis window, > 0, < 2^31
  *   n_events      number of records (may be 0)
  *   gate_offsets  [n_gates+1] int64 CSR offsets: gate g's records are
@@ -245,7 +257,16 @@ int gtp_load_events(gtp_ctx* ctx, int32_t window, int64_t window_ps, int64_t n_e
 
 /*
  * Run the power walk of one window with bins of bin_ps ps
- * (n_bins = window_ps / bin_ps; window_ps % bin_ps must be 0).
+ * (n_bins = window_ps / bin_ps; window_ps % bin_ps must be 0).  This is the
+ * fused computation of Sec. 4.3 (Algorithm 1) over every gate: per
+ * timestamp group the lookups use the state before the group and the state
+ * is updated after it; internal energy is the state-indexed NLDM value
+ * (Sec. 2.2, Sec. 4.1) interpolated at (slew, load); switching energy is
+ * 0.5*C*Vdd^2 per output toggle (Eq. 1, one half per edge); leakage power
+ * of the current state holds between groups (Eq. 4) and is split over the
+ * bins each interval overlaps in proportion to the overlap (Sec. 2.4.2);
+ * dynamic energy goes to the bin holding the event (Sec. 2.4.1).  The bin
+ * plays the part of the paper's clock cycle.
  * Writes waveform_w[n_bins] (FP64, W): the mean power of each bin, i.e. the
  * energy of all events in the bin (dynamic energy goes to the bin holding the
  * event time; a time on a bin boundary belongs to the later bin) plus the
@@ -341,7 +362,10 @@ int gtp_run_power_streamed(gtp_ctx* ctx, int32_t window, int64_t window_ps, int6
 /*
  * Per-gate results of the last gtp_run_power / batched run of `window`:
  * leakage, internal and switching energy (fJ, FP64), event count and the
- * state after the last event.  Any pointer may be NULL.
+ * state after the last event.  These are the per-gate power results the
+ * paper reduces per gate (Sec. 4.4, the R^(g) buffers; reported per gate,
+ * Sec. 5) kept as energies (divide by the window for power, Eq. 3).  Any
+ * pointer may be NULL.  Errors: GTP_EINVAL if the window has no result.
  * flags: GTP_HOST or GTP_DEVICE for all outputs.  Host outputs are complete
  * on return; device outputs are written in order on the context's stream
  * (no host synchronisation).
@@ -350,6 +374,8 @@ int gtp_gate_energy(gtp_ctx* ctx, int32_t window, double* e_leak, double* e_int,
                     int64_t* n_events, uint8_t* final_state, int flags);
 
 /*
+ * The paper has no batched form: this is gtp_run_power (Sec. 4.3,
+ * Algorithm 1) for many stimulus windows of one netlist at once.
  * Run n_windows (<= 1024) distinct loaded windows over the same netlist: one
  * gate-pass launch, one seed pass and one persistent walk launch whose warps
  * take segments from a single list covering every window, and one merge
@@ -362,6 +388,10 @@ int gtp_run_power_batched(gtp_ctx* ctx, int32_t n_windows, const int32_t* window
                           double* const* waveforms, int flags);
 
 /*
+ * The paper has no adjoint; this differentiates gtp_run_power's waveform,
+ * whose energies are the bilinear internal energy (Sec. 2.2, Sec. 2.4.1),
+ * 0.5*C*Vdd^2 switching energy (Eq. 1) and leakage P*dt (Eq. 4) split over
+ * the bins (Sec. 2.4.2).
  * Adjoint of gtp_run_power for one window: given dL_dP[n_bins] (device,
  * FP32, the gradient of a scalar loss with respect to each bin's power in W),
  * write the gradients with respect to every gate's load (dC[n_gates]) and
@@ -377,6 +407,9 @@ int gtp_run_power_backward(gtp_ctx* ctx, int32_t window, int32_t bin_ps, const f
                            float* d_escale, float* d_lscale);
 
 /*
+ * The counterpart of the paper's parameter study of its density-aware
+ * partitioning (Sec. 4.2, Eqs. 7-13: the target events per thread and the
+ * parallelism floor; Sec. 6.4) for this engine's partitioning parameters.
  * Autotuner: time the walk of the given windows for every candidate
  * (records per lane 4/8/16 = segment length 128/256/512 events, dense_min
  * 64/256/1024), `iters` timed runs each, keep the fastest as the context's
@@ -430,10 +463,13 @@ int64_t gtp_get_param(const gtp_ctx* ctx, const char* key);
  *
  * Runs on the calling thread's current device, enqueues on cuda_stream (a
  * cudaStream_t of that device; NULL = the legacy default stream) and
- * synchronises it before returning.  The first call on a device looks up the
- * scratch array's device address (cudaGetSymbolAddress) and keeps it for
- * later calls; make that first call outside any stream capture.  Calls no
- * cudaMalloc, cudaFree or other allocating routine.
+ * synchronises it before returning (it reads the kernel's status word back).
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) and keeps it for later calls; make that first call
+ * outside any stream capture.  Because every call waits for its stream, no
+ * call may be made while that stream is being captured: such a call returns
+ * GTP_EINVAL and enqueues nothing.  Calls no cudaMalloc, cudaFree or other
+ * allocating routine.
  *
  * Every call on a device shares the one scratch array and starts by clearing
  * what must begin at zero (bins, L0, error word).  Calls whose GPU work

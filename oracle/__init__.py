@@ -72,6 +72,9 @@ def _lib():
         lib.oracle_walk.restype = ctypes.c_int
         lib.oracle_walk.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int64, P, P, ctypes.c_int64, P,
                                     P, P, P, P, P, P, P, P, P]
+        lib.oracle_walk_range.restype = ctypes.c_int
+        lib.oracle_walk_range.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int64, P, P, P, P, P, P, P, P, P, P,
+                                          P]
         lib.oracle_adjoint.restype = ctypes.c_int
         lib.oracle_adjoint.argtypes = [P, P, P, ctypes.c_int64, P, ctypes.c_int64, P, P, P, P, P]
         lib.oracle_bilinear.restype = ctypes.c_double
@@ -126,7 +129,8 @@ def _glitch(glitch, keep):
 
 
 def walk(lib, net, trace, bin_ps: int, escale=None, lscale=None, load_ff=None, gates=None,
-         sample_bins=None, waveform: bool = True, glitch=None, components: bool = False):
+         sample_bins=None, waveform: bool = True, glitch=None, components: bool = False,
+         leak_range: bool = False):
     """Run the FP64 walk.  Returns a dict with ``bins`` (fJ per bin; the
     sampled bins only if ``sample_bins`` is given), ``e_leak``, ``e_int``,
     ``e_sw``, ``e_gl`` (fJ per gate), ``n_events`` and ``final_state``.  With
@@ -134,7 +138,11 @@ def walk(lib, net, trace, bin_ps: int, escale=None, lscale=None, load_ff=None, g
     receive those gates' contributions).  ``glitch`` = (clock_ps, out_slew
     [n_gates][2] {fall, rise} ps) turns on glitch detection; e_gl is 0
     without it.  ``components`` adds ``comp_bins`` [4][len(bins)]: the bins
-    split into leakage, internal, switching and glitch energy (fJ)."""
+    split into leakage, internal, switching and glitch energy (fJ).
+    ``leak_range`` (all bins only) uses the range-mode leakage split of the
+    C walk: the same bins up to FP64 addition order, in time proportional to
+    events + bins rather than gates x bins (pinned against the plain split in
+    tests/test_oracle_range.py)."""
     L, N, T, keep = _structs(lib, net, trace, escale, lscale, load_ff)
     GL = _glitch(glitch, keep)
     n_bins = int(trace.window_ps) // int(bin_ps) if bin_ps > 0 else 0
@@ -157,6 +165,24 @@ def walk(lib, net, trace, bin_ps: int, escale=None, lscale=None, load_ff=None, g
     out["final_state"] = np.zeros(n_sel, np.uint8)
     bad = ctypes.c_int64(-1)
     nullp = None
+    if leak_range and sample_bins is None:
+        rc = _lib().oracle_walk_range(
+            ctypes.byref(L), ctypes.byref(N), ctypes.byref(T), int(bin_ps), n_sel,
+            gates.ctypes.data if gates is not None else nullp,
+            bins.ctypes.data if waveform else nullp,
+            out["e_leak"].ctypes.data, out["e_int"].ctypes.data, out["e_sw"].ctypes.data,
+            out["n_events"].ctypes.data, out["final_state"].ctypes.data, ctypes.byref(bad),
+            ctypes.byref(GL) if GL is not None else nullp, out["e_gl"].ctypes.data,
+            comp.ctypes.data if comp is not None else nullp)
+        del keep
+        if rc == EINVAL:
+            raise ValueError("invalid bin size / window")
+        if rc != OK:
+            raise OracleError(rc, bad.value)
+        out["bins"] = bins
+        if comp is not None:
+            out["comp_bins"] = comp
+        return out
     rc = _lib().oracle_walk(
         ctypes.byref(L), ctypes.byref(N), ctypes.byref(T), int(bin_ps), n_sel,
         gates.ctypes.data if gates is not None else nullp,

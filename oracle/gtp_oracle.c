@@ -160,6 +160,8 @@ typedef struct {
   double* out;              /* all bins, or the sampled bins */
   int64_t n_sample;         /* 0 = all bins */
   const int64_t* sample;    /* sorted bin indices */
+  double* diff;             /* range mode only: [n_bins + 1] differences of the
+                               whole-bin leakage shares (see bin_add_interval) */
 } binner;
 
 static int64_t first_sample_at_or_after(const binner* B, int64_t b) {
@@ -179,10 +181,34 @@ static void bin_add(const binner* B, int64_t t, double e) {
   if (k < B->n_sample && B->sample[k] == b) B->out[k] += e;
 }
 
-/* Leakage of power P (nW) over [a, b) ps, split over the overlapped bins. */
+/* Leakage of power P (nW) over [a, b) ps, split over the overlapped bins
+ * [Sec. 2.4.2]: each bin receives P times its overlap with the interval.
+ *
+ * Range mode (B->diff set, all bins): the same split, with the bins the
+ * interval covers whole (every bin strictly between the first and the last
+ * one) receiving their equal share P * bin_ps through a difference array,
+ * diff[k0 + 1] += share, diff[k1] -= share, which range_flush() turns into
+ * the per-bin amounts with one running sum.  Only the order of the FP64
+ * additions differs from the plain split; this mode exists so that the
+ * oracle can check full-size waveforms, where the plain split costs
+ * gates x bins additions. */
 static void bin_add_interval(const binner* B, double P, int64_t a, int64_t b) {
   if (!B->out || b <= a) return;
   int64_t k0 = a / B->bin_ps, k1 = (b - 1) / B->bin_ps;
+  if (B->diff && B->n_sample == 0) {
+    if (k0 == k1) {
+      B->out[k0] += P * (double)(b - a) * 1e-6;
+      return;
+    }
+    B->out[k0] += P * (double)((k0 + 1) * B->bin_ps - a) * 1e-6;
+    B->out[k1] += P * (double)(b - k1 * B->bin_ps) * 1e-6;
+    if (k1 > k0 + 1) {
+      double share = P * (double)B->bin_ps * 1e-6;
+      B->diff[k0 + 1] += share;
+      B->diff[k1] -= share;
+    }
+    return;
+  }
   if (B->n_sample == 0) {
     for (int64_t k = k0; k <= k1; ++k) {
       int64_t lo = a > k * B->bin_ps ? a : k * B->bin_ps;
@@ -197,6 +223,19 @@ static void bin_add_interval(const binner* B, double P, int64_t a, int64_t b) {
     int64_t hi = b < (k + 1) * B->bin_ps ? b : (k + 1) * B->bin_ps;
     B->out[s] += P * (double)(hi - lo) * 1e-6;
   }
+}
+
+/* Range mode: add the whole-bin leakage shares recorded in B->diff to the
+ * bins (a running sum of the differences) and clear the differences. */
+static void range_flush(const binner* B) {
+  if (!B->diff || !B->out) return;
+  double run = 0.0;
+  for (int64_t k = 0; k < B->n_bins; ++k) {
+    run += B->diff[k];
+    B->out[k] += run;
+    B->diff[k] = 0.0;
+  }
+  B->diff[B->n_bins] = 0.0;
 }
 
 /* ---------------------------------------------------------------- the walk */
@@ -221,20 +260,26 @@ static double glitch_ratio(double pulse_width, double sum_slew) {
   return r < 1.0 ? r : 1.0;
 }
 
-int oracle_walk(const oracle_lib* L, const oracle_net* N, const oracle_trace* T, int64_t bin_ps,
-                int64_t n_sel, const int64_t* gates,
-                double* bins, int64_t n_sample, const int64_t* sample,
-                double* e_leak, double* e_int, double* e_sw, int64_t* n_events, uint8_t* final_state,
-                int64_t* bad_record, const oracle_glitch* GL, double* e_gl, double* comp_bins) {
+static int walk_impl(const oracle_lib* L, const oracle_net* N, const oracle_trace* T, int64_t bin_ps,
+                     int64_t n_sel, const int64_t* gates,
+                     double* bins, int64_t n_sample, const int64_t* sample,
+                     double* e_leak, double* e_int, double* e_sw, int64_t* n_events, uint8_t* final_state,
+                     int64_t* bad_record, const oracle_glitch* GL, double* e_gl, double* comp_bins,
+                     int leak_range) {
   if (bin_ps <= 0 || T->window_ps <= 0 || T->window_ps % bin_ps != 0) return OR_EINVAL;
+  int64_t n_bins_all = T->window_ps / bin_ps;
+  int ranged = leak_range && n_sample == 0;
   int64_t* tab_base = (int64_t*)malloc(sizeof(int64_t) * (size_t)L->n_cells);
   int64_t* leak_base = (int64_t*)malloc(sizeof(int64_t) * (size_t)L->n_cells);
+  double* diff = ranged ? (double*)calloc((size_t)(n_bins_all + 1), sizeof(double)) : NULL;
+  double* cdiff = ranged && comp_bins ? (double*)calloc((size_t)(n_bins_all + 1), sizeof(double)) : NULL;
   cell_bases(L, tab_base, leak_base);
-  binner B = {bin_ps, T->window_ps / bin_ps, bins, n_sample, sample};
-  int64_t n_out = n_sample ? n_sample : T->window_ps / bin_ps;
+  binner B = {bin_ps, n_bins_all, bins, n_sample, sample, diff};
+  int64_t n_out = n_sample ? n_sample : n_bins_all;
   binner BC[4]; /* leakage, internal, switching, glitch */
   for (int k = 0; k < 4; ++k) {
-    binner x = {bin_ps, T->window_ps / bin_ps, comp_bins ? comp_bins + k * n_out : NULL, n_sample, sample};
+    binner x = {bin_ps, n_bins_all, comp_bins ? comp_bins + k * n_out : NULL, n_sample, sample,
+                k == 0 ? cdiff : NULL};
     BC[k] = x;
   }
   int64_t count = gates ? n_sel : N->n_gates;
@@ -316,9 +361,33 @@ int oracle_walk(const oracle_lib* L, const oracle_net* N, const oracle_trace* T,
     if (n_events) n_events[gi] = b - a;
     if (final_state) final_state[gi] = (uint8_t)S;
   }
+  range_flush(&B);
+  range_flush(&BC[0]);
+  free(diff);
+  free(cdiff);
   free(tab_base);
   free(leak_base);
   return rc;
+}
+
+int oracle_walk(const oracle_lib* L, const oracle_net* N, const oracle_trace* T, int64_t bin_ps,
+                int64_t n_sel, const int64_t* gates,
+                double* bins, int64_t n_sample, const int64_t* sample,
+                double* e_leak, double* e_int, double* e_sw, int64_t* n_events, uint8_t* final_state,
+                int64_t* bad_record, const oracle_glitch* GL, double* e_gl, double* comp_bins) {
+  return walk_impl(L, N, T, bin_ps, n_sel, gates, bins, n_sample, sample, e_leak, e_int, e_sw, n_events,
+                   final_state, bad_record, GL, e_gl, comp_bins, 0);
+}
+
+/* oracle_walk with the range-mode leakage split (see bin_add_interval): the
+ * same bins up to the order of FP64 additions, in time proportional to
+ * events + bins instead of gates x bins.  For full-size waveforms. */
+int oracle_walk_range(const oracle_lib* L, const oracle_net* N, const oracle_trace* T, int64_t bin_ps,
+                      int64_t n_sel, const int64_t* gates, double* bins,
+                      double* e_leak, double* e_int, double* e_sw, int64_t* n_events, uint8_t* final_state,
+                      int64_t* bad_record, const oracle_glitch* GL, double* e_gl, double* comp_bins) {
+  return walk_impl(L, N, T, bin_ps, n_sel, gates, bins, 0, NULL, e_leak, e_int, e_sw, n_events, final_state,
+                   bad_record, GL, e_gl, comp_bins, 1);
 }
 
 /* ---------------------------------------------------------------- adjoint */

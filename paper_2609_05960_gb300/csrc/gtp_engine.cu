@@ -194,15 +194,6 @@ struct DeviceGuard {
 cudaMemcpyKind kind_in(int flags) { return (flags & GTP_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
 cudaMemcpyKind kind_out(int flags) { return (flags & GTP_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
 
-void bin_magic(int32_t d, uint32_t* magic, uint32_t* shift) {
-  uint32_t s = 0;
-  while ((2ull << s) <= (uint64_t)d) ++s;  // s = floor(log2 d)
-  unsigned __int128 m = (((unsigned __int128)1) << (32 + s)) / (uint64_t)d;
-  if (m > 0xFFFFFFFFull) m = 0xFFFFFFFFull;
-  *magic = (uint32_t)m;
-  *shift = s;
-}
-
 const char* code_name(int code) {
   switch (code) {
     case GTP_EORDER: return "timestamps decrease within a gate";
@@ -1477,19 +1468,20 @@ int gtp_measure_reductions(gtp_ctx* ctx, int32_t n_slots, int32_t width, int64_t
   DeviceGuard dg(ctx->device);
   CU(ctx->probe.reserve(sizeof(float4) * (size_t)n_slots), "alloc probe");
   CU(cudaMemsetAsync(ctx->probe.p, 0, sizeof(float4) * (size_t)n_slots, ctx->stream), "zero probe");
+  // both events are created before any early return and destroyed on every path below
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  CU(cudaEventCreate(&e0), "event");
-  CU(cudaEventCreate(&e1), "event");
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
   float4* slots = ctx->probe.as<float4>();
-  cudaError_t e = launch_red_probe(slots, (uint32_t)n_slots, width, n_red, ctx->n_sm, ctx->stream);  // warm-up
+  if (e == cudaSuccess) e = launch_red_probe(slots, (uint32_t)n_slots, width, n_red, ctx->n_sm, ctx->stream);  // warm-up
   if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
   if (e == cudaSuccess) e = launch_red_probe(slots, (uint32_t)n_slots, width, n_red, ctx->n_sm, ctx->stream);
   if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
   if (e == cudaSuccess) e = cudaEventSynchronize(e1);
   float ms = 0.f;
   if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
   CU(e, "measure_reductions");
   ctx->launches += 2;
   *per_s = ms > 0.f ? (double)n_red / (ms * 1e-3) : 0.0;

@@ -134,7 +134,17 @@ __device__ __forceinline__ uint32_t side_bits(uint32_t S, uint32_t pin, uint32_t
 
 // floor(t / bin_ps) for 0 <= t < 2^31: the multiply-high estimate is q or
 // q - 1 (magic = min(floor(2^(32+s) / d), 2^32 - 1), s = floor(log2 d)), and
-// one correction step makes it exact.
+// one correction step makes it exact.  bin_magic() builds the two constants
+// on the host; every path that bins events uses this one definition.
+inline void bin_magic(int32_t d, uint32_t* magic, uint32_t* shift) {
+  uint32_t s = 0;
+  while ((2ull << s) <= (uint64_t)d) ++s;  // s = floor(log2 d)
+  unsigned __int128 m = (((unsigned __int128)1) << (32 + s)) / (uint64_t)d;
+  if (m > 0xFFFFFFFFull) m = 0xFFFFFFFFull;
+  *magic = (uint32_t)m;
+  *shift = s;
+}
+
 __device__ __forceinline__ uint32_t bin_of(uint32_t t, uint32_t magic, uint32_t shift, uint32_t bin_ps) {
   uint32_t b = __umulhi(t, magic) >> shift;
   return b + (((b + 1u) * bin_ps <= t) ? 1u : 0u);

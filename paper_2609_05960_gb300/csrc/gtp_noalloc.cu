@@ -203,15 +203,6 @@ __global__ void __launch_bounds__(kNaThreads) k_noalloc_walk(NaArgs a) {
   }
 }
 
-void na_bin_magic(int32_t d, uint32_t* magic, uint32_t* shift) {
-  uint32_t s = 0;
-  while ((2ull << s) <= (uint64_t)d) ++s;
-  unsigned __int128 m = (((unsigned __int128)1) << (32 + s)) / (uint64_t)d;
-  if (m > 0xFFFFFFFFull) m = 0xFFFFFFFFull;
-  *magic = (uint32_t)m;
-  *shift = s;
-}
-
 // Device address of the scratch on the current device (set-up on first use).
 int na_scratch(unsigned char** out) {
   int dev = -1;
@@ -278,6 +269,13 @@ extern "C" int gtp_run_power_noalloc(void* cuda_stream, int32_t n_cells, const i
     h.axes[3 * kMaxAxis + i] = i + 1 < n_load ? 1.0f / (load_axis[i + 1] - load_axis[i]) : 0.f;
   }
 
+  // ---- the call ends by waiting for its stream, which a capturing stream
+  // does not allow: refuse before anything is enqueued
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return GTP_ECUDA;
+  if (cs != cudaStreamCaptureStatusNone) return GTP_EINVAL;
+
   // ---- scratch of this device
   unsigned char* base = nullptr;
   const int rc = na_scratch(&base);
@@ -299,7 +297,7 @@ extern "C" int gtp_run_power_noalloc(void* cuda_stream, int32_t n_cells, const i
   w.tile_base = 0;
   w.window_ps = (int32_t)window_ps;
   w.bin_ps = bin_ps;
-  na_bin_magic(bin_ps, &w.bin_magic, &w.bin_shift);
+  bin_magic(bin_ps, &w.bin_magic, &w.bin_shift);
   w.n_bins = (int32_t)n_bins;
 
   NaArgs a{};
@@ -334,7 +332,6 @@ extern "C" int gtp_run_power_noalloc(void* cuda_stream, int32_t n_cells, const i
 
   // ---- enqueue: header (error word and L0 start at zero), cleared bins,
   // the walk, the merge; then read the error word back.
-  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   if (cudaMemcpyAsync(d_hdr, &h, sizeof(NaHeader), cudaMemcpyHostToDevice, st) != cudaSuccess) return GTP_ECUDA;
   if (cudaMemsetAsync(d_bins, 0, sizeof(float2) * (size_t)n_bins, st) != cudaSuccess) return GTP_ECUDA;
   int64_t blocks = (n_gates + kNaThreads - 1) / kNaThreads;

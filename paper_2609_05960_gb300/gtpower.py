@@ -20,6 +20,7 @@ GTP_OK, GTP_EINVAL, GTP_EORDER, GTP_ERANGE, GTP_ENOTOGGLE = 0, -1, -2, -3, -4
 GTP_ENOMEM, GTP_ECUDA, GTP_ETIMEOUT, GTP_EDEVICE = -5, -6, -7, -8
 GTP_HOST, GTP_DEVICE, GTP_BORROW, GTP_GRAPH, GTP_PACKED = 0, 1, 2, 4, 8
 GTP_NOALLOC_MAX_BINS = 1 << 19
+GTP_MAX_PINS = 8
 
 CODE_NAMES = {GTP_EINVAL: "EINVAL", GTP_EORDER: "EORDER", GTP_ERANGE: "ERANGE", GTP_ENOTOGGLE: "ENOTOGGLE",
               GTP_ENOMEM: "ENOMEM", GTP_ECUDA: "ECUDA", GTP_ETIMEOUT: "ETIMEOUT", GTP_EDEVICE: "EDEVICE"}
@@ -359,34 +360,100 @@ def gtp_get_param(ctx, key: str) -> int:
     return int(load().gtp_get_param(ctx, key.encode()))
 
 
+def _noalloc_validate(n_in, e_int, p_leak, cell, load_ff, slew_ps, window_ps, gate_offsets, events, init_state,
+                      bin_ps, slew_axis_len, load_axis_len, outputs, require_cuda: bool = True):
+    """Every check gtp_run_power_noalloc's arguments need before the call.
+    The C side cannot see the length of a device array, so a short output or
+    input here would become an out-of-bounds device access there; the device
+    of every tensor must also be the one the call runs on.  Returns
+    (n_gates, slew_stride, device).  Raises TypeError or ValueError."""
+    import torch
+    ni = np.ascontiguousarray(n_in, np.int32)
+    want = [("e_int", e_int, torch.float32), ("p_leak", p_leak, torch.float32), ("cell", cell, torch.int32),
+            ("load_ff", load_ff, torch.float32), ("slew_ps", slew_ps, torch.float32),
+            ("gate_offsets", gate_offsets, torch.int64), ("events", events, torch.int32),
+            ("init_state", init_state, torch.uint8)]
+    want += [(k, v, torch.uint8 if k == "final_state" else torch.float64) for k, v in outputs.items()]
+    device = None
+    for name, t, dt in want:
+        if t is None:
+            if name in outputs:
+                continue
+            raise TypeError(f"gtp_run_power_noalloc: {name} is required")
+        if not isinstance(t, torch.Tensor) or t.dtype != dt or not t.is_contiguous():
+            raise TypeError(f"gtp_run_power_noalloc: {name} must be a contiguous {dt} tensor")
+        if require_cuda and not t.is_cuda:
+            raise TypeError(f"gtp_run_power_noalloc: {name} must be a CUDA tensor")
+        if device is None:
+            device = t.device
+        elif t.device != device:
+            raise ValueError(f"gtp_run_power_noalloc: {name} is on {t.device}, other arrays on {device}")
+    if len(ni) == 0 or (ni < 1).any() or (ni >= GTP_MAX_PINS).any():
+        raise ValueError("gtp_run_power_noalloc: n_in must hold 1..7 inputs per cell")
+    tsize = int(slew_axis_len) * int(load_axis_len)
+    n_tab = int(sum(int(k) * (2 << (int(k) - 1)) for k in ni))
+    n_leak = int(sum(2 << int(k) for k in ni))
+    if e_int.numel() != n_tab * tsize:
+        raise ValueError(f"gtp_run_power_noalloc: e_int holds {e_int.numel()} floats, the library needs {n_tab * tsize}")
+    if p_leak.numel() != n_leak:
+        raise ValueError(f"gtp_run_power_noalloc: p_leak holds {p_leak.numel()} floats, the library needs {n_leak}")
+    G = int(cell.numel())
+    if G <= 0:
+        raise ValueError("gtp_run_power_noalloc: no gates")
+    for name, t in (("load_ff", load_ff), ("init_state", init_state)):
+        if t.numel() != G:
+            raise ValueError(f"gtp_run_power_noalloc: {name} has {t.numel()} entries for {G} gates")
+    if gate_offsets.numel() != G + 1:
+        raise ValueError(f"gtp_run_power_noalloc: gate_offsets has {gate_offsets.numel()} entries, needs {G + 1}")
+    if slew_ps.dim() == 3:
+        if slew_ps.shape[0] != G or slew_ps.shape[2] != 2:
+            raise ValueError(f"gtp_run_power_noalloc: slew_ps is {tuple(slew_ps.shape)}, needs [{G}, stride, 2]")
+        stride = int(slew_ps.shape[1])
+    else:
+        if slew_ps.numel() % (2 * G):
+            raise ValueError("gtp_run_power_noalloc: slew_ps must hold n_gates * stride * 2 floats")
+        stride = int(slew_ps.numel() // (2 * G))
+    if stride < int(ni.max()):
+        raise ValueError(f"gtp_run_power_noalloc: slew stride {stride} below the widest cell's {int(ni.max())} inputs")
+    if events.dim() != 2 or events.shape[1] != 2:
+        raise ValueError(f"gtp_run_power_noalloc: events must be [n_events, 2] int32, got {tuple(events.shape)}")
+    if int(bin_ps) <= 0 or int(window_ps) <= 0 or int(window_ps) % int(bin_ps):
+        raise ValueError("gtp_run_power_noalloc: window_ps must be a positive multiple of bin_ps > 0")
+    n_bins = int(window_ps) // int(bin_ps)
+    wf = outputs.get("waveform")
+    if wf is not None and wf.numel() != n_bins:
+        raise ValueError(f"gtp_run_power_noalloc: waveform has {wf.numel()} entries for {n_bins} bins")
+    for name in ("e_leak", "e_int_out", "e_sw", "final_state"):
+        t = outputs.get(name)
+        if t is not None and t.numel() != G:
+            raise ValueError(f"gtp_run_power_noalloc: {name} has {t.numel()} entries for {G} gates")
+    return G, stride, device
+
+
 def gtp_run_power_noalloc(n_in, vdd, slew_axis, load_axis, e_int, p_leak, cell, load_ff, slew_ps, window_ps: int,
                           gate_offsets, events, init_state, bin_ps: int, waveform=None, e_leak=None, e_int_out=None,
                           e_sw=None, final_state=None, stream: Optional[int] = None) -> None:
     """The allocation-free single-window walk.  n_in and the axes are host
-    arrays; every other array is a contiguous CUDA tensor on the current
-    device (slew_ps shaped [G, stride, 2], events [E, 2] int32); outputs may
-    be None.  Raises GtpError with the returned code."""
+    arrays; every other array is a contiguous CUDA tensor, all on one device
+    (slew_ps shaped [G, stride, 2], events [E, 2] int32); outputs may be None.
+    Every length is checked here, and the call runs with the tensors' device
+    current.  Raises TypeError / ValueError before the call, GtpError with the
+    returned code after it."""
     import torch
     ni = np.ascontiguousarray(n_in, np.int32)
     sa = np.ascontiguousarray(slew_axis, np.float32)
     la = np.ascontiguousarray(load_axis, np.float32)
-    want = [(e_int, torch.float32), (p_leak, torch.float32), (cell, torch.int32), (load_ff, torch.float32),
-            (slew_ps, torch.float32), (gate_offsets, torch.int64), (events, torch.int32), (init_state, torch.uint8),
-            (waveform, torch.float64), (e_leak, torch.float64), (e_int_out, torch.float64), (e_sw, torch.float64),
-            (final_state, torch.uint8)]
-    for t, dt in want:
-        if t is not None and (not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dt
-                              or not t.is_contiguous()):
-            raise TypeError(f"gtp_run_power_noalloc: expected a contiguous CUDA {dt} tensor")
+    outputs = dict(waveform=waveform, e_leak=e_leak, e_int_out=e_int_out, e_sw=e_sw, final_state=final_state)
+    G, stride, device = _noalloc_validate(ni, e_int, p_leak, cell, load_ff, slew_ps, window_ps, gate_offsets, events,
+                                          init_state, bin_ps, len(sa), len(la), outputs)
     ptr = lambda t: None if t is None else t.data_ptr()
-    G = int(cell.numel())
-    rc = load().gtp_run_power_noalloc(stream, len(ni), ni.ctypes.data, float(vdd), len(sa), sa.ctypes.data, len(la),
-                                      la.ctypes.data, ptr(e_int), int(e_int.numel()), ptr(p_leak),
-                                      int(p_leak.numel()), G, ptr(cell), ptr(load_ff), ptr(slew_ps),
-                                      int(slew_ps.shape[1]) if slew_ps.dim() == 3 else int(slew_ps.numel() // (2 * G)),
-                                      int(window_ps), int(events.shape[0]), ptr(gate_offsets), ptr(events),
-                                      ptr(init_state), int(bin_ps), ptr(waveform), ptr(e_leak), ptr(e_int_out),
-                                      ptr(e_sw), ptr(final_state))
+    with torch.cuda.device(device):
+        rc = load().gtp_run_power_noalloc(stream, len(ni), ni.ctypes.data, float(vdd), len(sa), sa.ctypes.data,
+                                          len(la), la.ctypes.data, ptr(e_int), int(e_int.numel()), ptr(p_leak),
+                                          int(p_leak.numel()), G, ptr(cell), ptr(load_ff), ptr(slew_ps), stride,
+                                          int(window_ps), int(events.shape[0]), ptr(gate_offsets), ptr(events),
+                                          ptr(init_state), int(bin_ps), ptr(waveform), ptr(e_leak), ptr(e_int_out),
+                                          ptr(e_sw), ptr(final_state))
     if rc != GTP_OK:
         raise GtpError(rc, "gtp_run_power_noalloc failed")
 
