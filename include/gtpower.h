@@ -433,6 +433,11 @@ int gtp_measure_reductions(gtp_ctx* ctx, int32_t n_slots, int32_t width, int64_t
 /* Engine tuning knobs; value < 0 restores the default.  Keys:
  * "records_per_thread" (4, 8, 16; events per lane of a dense segment),
  * "ctas_per_sm" (0 = full occupancy), "dense_min" (gates with more events are cut into segments; 1..4096),
+ * "tile_min" (single-window runs without glitch detection or component
+ * waveforms: gates with at least this many events, and at most 3 inputs,
+ * take the time-sliced walk, which keeps each 16,384-bin slice of the
+ * waveform in shared memory as exact integer sums and merges slices in FP64;
+ * 0 = off, the default),
  * "kernel" (0 = density-split walk,
  * 1 = one thread per gate, a plain cross-check), "scheme_evt_tgt" (8),
  * "scheme_thr_floor" (512) and "scheme_ncyc_fix" (1) for gtp_run_power_scheme,

@@ -49,6 +49,7 @@ struct Window {
   DevBuf offsets, records, init;
   const uint2* borrowed = nullptr;
   DevBuf e_leak, e_int, e_sw, e_gl, final_state, bins, tiles, wave;
+  DevBuf tbins;  // the time-sliced walk's FP64 bins
   DevBuf cbins, cwave;  // per-component runs: component accumulators and the host-bound waveforms
   // the paper's schemes: per-pin event streams (built once per load) and the
   // density-aware block plan (per bin count and partitioning parameters)
@@ -62,7 +63,7 @@ struct Window {
   int32_t last_bin_ps = 0;
   const uint2* rec() const { return borrowed ? borrowed : records.as<uint2>(); }
   void release() {
-    for (DevBuf* b : {&offsets, &records, &init, &e_leak, &e_int, &e_sw, &e_gl, &final_state, &bins, &tiles, &wave,
+    for (DevBuf* b : {&offsets, &records, &init, &e_leak, &e_int, &e_sw, &e_gl, &final_state, &bins, &tbins, &tiles, &wave,
                       &cbins, &cwave, &ps_off, &ps_ev, &ps_slot, &blk_gate, &blk_first, &ncyc})
       b->release();
     borrowed = nullptr;
@@ -76,13 +77,13 @@ struct Window {
 struct GraphKey {
   std::vector<int32_t> windows;
   int32_t bin_ps;
-  int64_t rpt, ctas, kernel, dmin, plan_gen;
+  int64_t rpt, ctas, kernel, dmin, tmin, plan_gen;
   int64_t n_tiles;  // launch sizes baked into the graph
   bool any_events;  // whether the walk was captured
   bool timing;      // whether phase events were captured
   bool operator<(const GraphKey& o) const {
-    return std::tie(windows, bin_ps, rpt, ctas, kernel, dmin, plan_gen, n_tiles, any_events, timing) <
-           std::tie(o.windows, o.bin_ps, o.rpt, o.ctas, o.kernel, o.dmin, o.plan_gen, o.n_tiles, o.any_events,
+    return std::tie(windows, bin_ps, rpt, ctas, kernel, dmin, tmin, plan_gen, n_tiles, any_events, timing) <
+           std::tie(o.windows, o.bin_ps, o.rpt, o.ctas, o.kernel, o.dmin, o.tmin, o.plan_gen, o.n_tiles, o.any_events,
                     o.timing);
   }
 };
@@ -113,6 +114,7 @@ struct gtp_ctx {
   unsigned char* h_plan = nullptr;
   // device-side work plan: dense segments, their seeds, sorted sparse gates, counters
   DevBuf glist, counters;
+  DevBuf chunks;         // the tiled walk's chunk starts
   int64_t gcap = 0;
   int64_t plan_gen = 0;  // bumped whenever a plan buffer moves (captured graphs hold its pointers)
   DevBuf cell_acc, grad, gtiles, dC_scratch;
@@ -140,10 +142,11 @@ struct gtp_ctx {
   int64_t p_rpt = 8;
   int64_t p_ctas_per_sm = 0;
   int64_t p_dense_min = 256;
+  int64_t p_tile_min = 0;  // gates with this many events or more take the time-sliced walk (0: none)
   // phase timing (CUDA events on the context stream) and launch counting
   bool timing = false;
-  cudaEvent_t ev[8] = {};
-  int64_t t_ns[4] = {0, 0, 0, 0};  // gate pass, plan, walk, merge
+  cudaEvent_t ev[10] = {};
+  int64_t t_ns[5] = {0, 0, 0, 0, 0};  // gate pass, plan, walk (both walks), merge, the tiled walk alone
   int64_t n_timed = 0;
   int64_t launches = 0;
 };
@@ -262,7 +265,7 @@ int64_t seg_len_of(const gtp_ctx* ctx) { return 32 * ctx->p_rpt; }
 // the windows' device buffers.  The upload is enqueued by upload_plan().
 int build_plan(gtp_ctx* ctx, const std::vector<Window*>& ws, int32_t bin_ps, const std::vector<double*>& waves,
                bool backward, int64_t* n_seg_total, int64_t* n_tiles_total,
-               const std::vector<double*>* cwaves = nullptr) {
+               const std::vector<double*>* cwaves = nullptr, bool tiled = false) {
   const int n = (int)ws.size();
   if (n <= 0 || n > kMaxWindows) return fail(ctx, GTP_EINVAL, "between 1 and 1024 windows per run");
   WinDesc* hw = plan_wins(ctx->h_plan);
@@ -295,6 +298,11 @@ int build_plan(gtp_ctx* ctx, const std::vector<Window*>& ws, int32_t bin_ps, con
     d.e_gl = ctx->N.clock_ps > 0 ? W.e_gl.as<double>() : nullptr;
     d.final_state = W.final_state.as<uint8_t>();
     d.bins = W.bins.as<float2>();
+    d.tbins = nullptr;
+    if (tiled) {
+      CU(W.tbins.reserve(sizeof(double2) * nb), "alloc tiled bins");
+      d.tbins = W.tbins.as<double2>();
+    }
     d.cbins = nullptr;
     d.cwave = nullptr;
     if (cwaves && (*cwaves)[i]) {
@@ -361,6 +369,8 @@ WalkArgs walk_args(gtp_ctx* ctx, int n) {
   A.plan.counters = ctx->counters.as<unsigned long long>();
   A.plan.gcap = ctx->gcap;
   A.n_gates = ctx->N.n_gates;
+  A.tile_min = 0;
+  A.chunks = ctx->chunks.as<int32_t>();
   return A;
 }
 
@@ -375,12 +385,20 @@ void mark(gtp_ctx* ctx, int i, cudaStream_t st) {
 
 void collect_timing(gtp_ctx* ctx) {
   if (!ctx->timing) return;
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < 5; ++k) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, ctx->ev[2 * k], ctx->ev[2 * k + 1]) == cudaSuccess)
       ctx->t_ns[k] += (int64_t)(ms * 1e6);
   }
   ctx->n_timed += 1;
+}
+
+// Whether a forward run takes the time-sliced walk for its busiest gates:
+// one window, no per-component bins, no glitch detection, the fused walk, a
+// library whose leakage table fits, and the chunk buffer in place.
+bool tiling_on(const gtp_ctx* ctx, int n, bool comp) {
+  return n == 1 && !comp && ctx->N.clock_ps == 0 && ctx->p_kernel != 1 && ctx->p_tile_min > 0 &&
+         tiled_fits(ctx->L) && ctx->chunks.p != nullptr;
 }
 
 // Enqueue the forward pass of the planned windows (no synchronisation).
@@ -393,6 +411,8 @@ int enqueue_forward(gtp_ctx* ctx, int n, int64_t n_seg_total, int64_t n_tiles_to
   WalkArgs A = walk_args(ctx, n);
   A.comp = comp;
   const bool fused = any_events && ctx->p_kernel != 1;
+  const bool tiled = fused && tiling_on(ctx, n, comp);
+  if (tiled) A.tile_min = ctx->p_tile_min;
   mark(ctx, 0, st);
   CU(launch_prepare(ctx->L, ctx->N, A, fused, st), "prepare");
   mark(ctx, 1, st);
@@ -405,9 +425,15 @@ int enqueue_forward(gtp_ctx* ctx, int n, int64_t n_seg_total, int64_t n_tiles_to
       CU(launch_walk_per_gate(ctx->L, ctx->N, dw, n, ctx->d_err.as<DevError>(), st), "walk (per gate)");
       ctx->launches += 1;
     } else {
-      CU(launch_plan_scatter(ctx->N, A, st), "plan");
+      CU(launch_plan_scatter(ctx->L, ctx->N, A, st), "plan");
       mark(ctx, 3, st);
       mark(ctx, 4, st);
+      mark(ctx, 8, st);
+      if (tiled) {
+        CU(launch_tiled(ctx->L, ctx->N, A, plan_wins(ctx->h_plan)[0].n_bins, st), "tiled walk");
+        ctx->launches += 2;
+      }
+      mark(ctx, 9, st);
       CU(launch_walk(ctx->L, ctx->N, A, false, st), "walk");
       ctx->launches += 2;
     }
@@ -518,11 +544,21 @@ int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, dou
   }
   int64_t n_seg_total = 0, n_tiles_total = 0;
   RC(ensure_gate_tables(ctx, false));
-  RC(build_plan(ctx, ws, bin_ps, waves, false, &n_seg_total, &n_tiles_total, components ? &cwaves : nullptr));
+  const bool want_tiled = n == 1 && !components && ctx->N.clock_ps == 0 && ctx->p_kernel != 1 &&
+                          ctx->p_tile_min > 0 && tiled_fits(ctx->L) && any_events;
+  if (want_tiled) {  // the tiled walk's chunk list (allocated here, never under capture)
+    const size_t need = sizeof(int32_t) * (size_t)(tile_chunk_cap(ctx->N.n_gates) + 2);
+    if (ctx->chunks.bytes < need) {
+      CU(ctx->chunks.reserve(need), "alloc tile chunks");
+      ++ctx->plan_gen;
+    }
+  }
+  RC(build_plan(ctx, ws, bin_ps, waves, false, &n_seg_total, &n_tiles_total, components ? &cwaves : nullptr,
+                want_tiled && tiling_on(ctx, n, false)));
   CU(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(DevError), ctx->stream), "zero status");
   if (use_graph) {
     const GraphKey key{std::vector<int32_t>(windows, windows + n), bin_ps, ctx->p_rpt,
-                       ctx->p_ctas_per_sm, ctx->p_kernel, ctx->p_dense_min, ctx->plan_gen,
+                       ctx->p_ctas_per_sm, ctx->p_kernel, ctx->p_dense_min, ctx->p_tile_min, ctx->plan_gen,
                        n_tiles_total, any_events, ctx->timing};
     auto it = ctx->graphs.find(key);
     if (it == ctx->graphs.end()) {
@@ -546,7 +582,7 @@ int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, dou
     }
     // the graph's first node uploads the descriptor table from the staging buffer
     CU(cudaGraphLaunch(it->second, ctx->stream), "graph launch");
-    ctx->launches += any_events ? (ctx->p_kernel == 1 ? 5 : 6) : 4;
+    ctx->launches += any_events ? (ctx->p_kernel == 1 ? 5 : (tiling_on(ctx, n, false) ? 8 : 6)) : 4;
   } else {
     RC(enqueue_forward(ctx, n, n_seg_total, n_tiles_total, any_events, ctx->stream, components != nullptr));
   }
@@ -1293,7 +1329,7 @@ int gtp_run_power_streamed(gtp_ctx* ctx, int32_t window, int64_t window_ps, int6
       if (nr > 0) CU(launch_walk_per_gate(ctx->L, ctx->N, A.wins, 1, ctx->d_err.as<DevError>(), st), "walk");
     } else {
       CU(launch_prepare(ctx->L, ctx->N, A, true, st), "prepare");
-      CU(launch_plan_scatter(ctx->N, A, st), "plan");
+      CU(launch_plan_scatter(ctx->L, ctx->N, A, st), "plan");
       CU(launch_walk(ctx->L, ctx->N, A, false, st), "walk");
     }
     // locate a bad record while this chunk is still on the device (a no-op unless one was flagged)
@@ -1504,6 +1540,9 @@ int gtp_set_param(gtp_ctx* ctx, const char* key, int64_t value) {
   } else if (k == "dense_min") {
     if (value == 0 || value > 4096) return fail(ctx, GTP_ERANGE, "dense_min must be 1..4096");
     ctx->p_dense_min = value < 0 ? 256 : value;
+  } else if (k == "tile_min") {
+    if (value > (1ll << 31)) return fail(ctx, GTP_ERANGE, "tile_min must be 0..2^31");
+    ctx->p_tile_min = value < 0 ? 0 : value;
   } else if (k == "scheme_evt_tgt") {
     if (value == 0 || value > (1 << 20)) return fail(ctx, GTP_ERANGE, "scheme_evt_tgt must be 1..2^20");
     ctx->p_evt_tgt = value < 0 ? 8 : value;
@@ -1535,6 +1574,8 @@ int64_t gtp_get_param(const gtp_ctx* ctx, const char* key) {
   if (k == "records_per_thread") return ctx->p_rpt;
   if (k == "ctas_per_sm") return ctx->p_ctas_per_sm;
   if (k == "dense_min") return ctx->p_dense_min;
+  if (k == "tile_min") return ctx->p_tile_min;
+  if (k == "t_tiled_ns") return ctx->t_ns[4];
   if (k == "scheme_evt_tgt") return ctx->p_evt_tgt;
   if (k == "scheme_thr_floor") return ctx->p_thr_floor;
   if (k == "scheme_ncyc_fix") return ctx->p_ncyc_fix;

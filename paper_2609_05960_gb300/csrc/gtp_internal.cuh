@@ -94,6 +94,7 @@ struct WinDesc {
   double* e_gl;              // [G] glitch energy, or null without glitch detection
   uint8_t* final_state;      // [G]
   float2* bins;              // [n_bins] accumulators
+  double2* tbins;            // [n_bins] {energy fJ, leakage step nW} of the time-sliced walk (FP64), or null
   float4* cbins;             // [n_bins] component accumulators, or null (no per-component waveform):
                              //   cpack 0: {internal, switching, glitch fJ, leakage in-bin corrections fJ},
                              //            beside the bins as usual (runs with glitch detection)

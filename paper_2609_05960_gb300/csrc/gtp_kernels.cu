@@ -421,10 +421,14 @@ __global__ void k_tile_sums(const WinDesc* __restrict__ wins, const int64_t* __r
   if (tile >= W.n_tiles) return;
   const int base = tile * kMergeTile + threadIdx.x * kMergePer;
   float s = 0.f;
+  double st = 0.0;  // the time-sliced walk's FP64 steps
 #pragma unroll
   for (int k = 0; k < kMergePer; ++k)
-    if (base + k < W.n_bins) s += W.cpack ? W.cbins[base + k].w : W.bins[base + k].y;
-  const double tot = block_sum((double)s);
+    if (base + k < W.n_bins) {
+      s += W.cpack ? W.cbins[base + k].w : W.bins[base + k].y;
+      if (W.tbins) st += W.tbins[base + k].y;
+    }
+  const double tot = block_sum((double)s + st);
   if (threadIdx.x == 0) W.tiles[tile] = tot;
 }
 
@@ -456,6 +460,7 @@ __global__ void k_finalize(const WinDesc* __restrict__ wins, const int64_t* __re
   const int base = tile * kMergeTile + threadIdx.x * kMergePer;
   float2 v[kMergePer];
   float s = 0.f;
+  double st = 0.0;
 #pragma unroll
   for (int k = 0; k < kMergePer; ++k) {
     if (W.cpack) {  // {internal, switching, correction, step}: the bin's energy is the first three
@@ -465,18 +470,33 @@ __global__ void k_finalize(const WinDesc* __restrict__ wins, const int64_t* __re
       v[k] = base + k < W.n_bins ? W.bins[base + k] : make_float2(0.f, 0.f);
     }
     s += v[k].y;
+    if (W.tbins && base + k < W.n_bins) st += W.tbins[base + k].y;
   }
   __shared__ double tot;
-  const double pre = block_excl_scan((double)s, &tot) + W.tiles[tile] + *W.l0;
+  const double pre = block_excl_scan((double)s + st, &tot) + W.tiles[tile] + *W.l0;
   // W per bin: E (fJ) * 1e-3 / bin_ps + P (nW) * 1e-9
   const float to_w = (float)(1e-3 / (double)W.bin_ps);
   const double p0 = pre * 1e-9;
   if (W.wave) {
     float dp = 0.f;
+    if (W.tbins) {  // plus the time-sliced walk's FP64 energies and steps
+      const double to_wd = 1e-3 / (double)W.bin_ps;
+      double dpt = 0.0;
 #pragma unroll
-    for (int k = 0; k < kMergePer; ++k) {
-      if (base + k < W.n_bins) W.wave[base + k] = (double)fmaf(v[k].x, to_w, dp * 1e-9f) + p0;
-      dp += v[k].y;
+      for (int k = 0; k < kMergePer; ++k) {
+        if (base + k < W.n_bins) {
+          const double2 t = W.tbins[base + k];
+          W.wave[base + k] = (double)fmaf(v[k].x, to_w, dp * 1e-9f) + p0 + (t.x * to_wd + dpt * 1e-9);
+          dpt += t.y;
+        }
+        dp += v[k].y;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kMergePer; ++k) {
+        if (base + k < W.n_bins) W.wave[base + k] = (double)fmaf(v[k].x, to_w, dp * 1e-9f) + p0;
+        dp += v[k].y;
+      }
     }
   }
   if (W.cwave) {  // components: the leakage is the step prefix plus its in-bin corrections

@@ -17,19 +17,23 @@ constexpr int kSparseBase = kBigBuckets + kWarps;
 //   big    (c > kWarps * seg_len):        0..31 by decreasing floor(log2 c)
 //   medium (dense_min < c, <= 8 segments): 32..39 by decreasing segment count
 //   sparse (c <= dense_min):              40..40+dense_min-1 by decreasing c
-__device__ __forceinline__ int work_bucket(int64_t c, int dmin, int64_t seg_len) {
+//   tiled  (see is_tiled; walked by the time-sliced walk, gtp_tiled.cu):
+//          the 32 buckets after the sparse ones, by decreasing floor(log2 c)
+__device__ __forceinline__ int work_bucket(int64_t c, int dmin, int64_t seg_len, bool tiled) {
+  if (tiled) return kSparseBase + dmin + 31 - min(31, 63 - __clzll((unsigned long long)c));
   if (c <= dmin) return kSparseBase + dmin - (int)c;
   if (c > kWarps * seg_len) return kBigBuckets - 1 - min(kBigBuckets - 1, 63 - __clzll((unsigned long long)c));
   return kSparseBase - (int)((c + seg_len - 1) / seg_len);
 }
 
-__host__ __device__ constexpr int n_buckets(int dmin) { return kSparseBase + dmin; }
+__host__ __device__ constexpr int n_buckets(int dmin) { return kSparseBase + dmin + 32; }
 
 // Plan counters: [0] big, [1] medium, [2] sparse gates; [3] the walk's work
-// counter; [4] blocks of the preparation pass that have finished; then the
+// counter; [4] blocks of the preparation pass that have finished; [5] tiled
+// gates, [6] the tiled walk's work counter, [7] its chunks; then the
 // work-list histogram [nb] and the bucket cursors [nb].
 constexpr int kCntDone = 4;
-constexpr int kCntHist = 5;
+constexpr int kCntHist = kPlanCntHist;
 
 // Block-wide exclusive scan of one value per thread (blockDim.x a multiple of
 // 32); returns the thread's exclusive prefix and writes the block total.
@@ -68,7 +72,8 @@ __device__ unsigned long long block_excl_scan_u64(unsigned long long v, unsigned
 __device__ void plan_bucket_starts(int nb, PlanBufs P) {
   const unsigned long long* hist = P.counters + kCntHist;
   unsigned long long* cursor = P.counters + kCntHist + nb;
-  __shared__ unsigned long long starts[2], tot;
+  __shared__ unsigned long long starts[3], tot;
+  const int tiled_base = nb - 32;
   const int per = (nb + (int)blockDim.x - 1) / (int)blockDim.x;
   const int b0 = min(nb, (int)threadIdx.x * per), b1 = min(nb, b0 + per);
   unsigned long long sum = 0ull;
@@ -77,6 +82,7 @@ __device__ void plan_bucket_starts(int nb, PlanBufs P) {
   for (int b = b0; b < b1; ++b) {
     if (b == kBigBuckets) starts[0] = pre;
     if (b == kSparseBase) starts[1] = pre;
+    if (b == tiled_base) starts[2] = pre;
     cursor[b] = pre;
     pre += __ldcg(hist + b);
   }
@@ -84,7 +90,8 @@ __device__ void plan_bucket_starts(int nb, PlanBufs P) {
   if (threadIdx.x == 0) {
     P.counters[0] = starts[0];
     P.counters[1] = starts[1] - starts[0];
-    P.counters[2] = tot - starts[1];
+    P.counters[2] = starts[2] - starts[1];
+    P.counters[kPlanCntTiled] = tot - starts[2];
   }
 }
 
@@ -98,7 +105,8 @@ __device__ void plan_bucket_starts(int nb, PlanBufs P) {
 //         finishes last turns it into bucket starts.
 template <bool GATE, bool PLAN>
 __global__ void __launch_bounds__(256) k_prepare(LibView L, NetView N, const WinDesc* __restrict__ wins,
-                                                 DevError* err, int64_t seg_len, int dmin, PlanBufs P) {
+                                                 DevError* err, int64_t seg_len, int dmin, PlanBufs P,
+                                                 int64_t tmin) {
   extern __shared__ unsigned int sh[];  // PLAN: [nb] bucket counts of this block
   __shared__ double red[32];
   __shared__ bool s_last;
@@ -117,10 +125,13 @@ __global__ void __launch_bounds__(256) k_prepare(LibView L, NetView N, const Win
     if (tid == 0 && (W.n_bins & 1)) W.bins[W.n_bins - 1] = make_float2(0.f, 0.f);
     if (W.cbins)
       for (int64_t i = tid; i < W.n_bins; i += stride) W.cbins[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (W.tbins)
+      for (int64_t i = tid; i < W.n_bins; i += stride) W.tbins[i] = make_double2(0.0, 0.0);
   }
   double p0 = 0.0;
   for (int64_t g = W.g0 + tid; g < W.g1; g += stride) {
     const int64_t c = W.offsets[g + 1] - W.offsets[g];
+    const bool tiled = PLAN && is_tiled(c, tmin, (uint32_t)L.cells[N.cell[g]].n_in);
     if (GATE) {
       const int32_t cell = N.cell[g];
       const CellInfo ci = L.cells[cell];
@@ -131,7 +142,7 @@ __global__ void __launch_bounds__(256) k_prepare(LibView L, NetView N, const Win
       }
       const float Pl = L.leak[ci.leak_base + s0] * L.lscale[cell];
       p0 += (double)Pl;
-      if (!PLAN || c == 0) {
+      if (!PLAN || c == 0 || tiled) {  // the tiled walk adds into its gates' sums
         W.e_leak[g] = c == 0 ? (double)Pl * (double)W.window_ps * 1e-6 : 0.0;
         W.e_int[g] = 0.0;
         W.e_sw[g] = 0.0;
@@ -139,7 +150,7 @@ __global__ void __launch_bounds__(256) k_prepare(LibView L, NetView N, const Win
         W.final_state[g] = (uint8_t)s0;
       }
     }
-    if (PLAN && c > 0) atomicAdd(&sh[work_bucket(c, dmin, seg_len)], 1u);
+    if (PLAN && c > 0) atomicAdd(&sh[work_bucket(c, dmin, seg_len, tiled)], 1u);
   }
   if (GATE) {
     for (int o = 16; o > 0; o >>= 1) p0 += __shfl_down_sync(0xffffffffu, p0, o);
@@ -172,7 +183,8 @@ __global__ void __launch_bounds__(256) k_prepare(LibView L, NetView N, const Win
 // cursors see one atomic per bucket per 256 * kScatterPer gates.
 constexpr int kScatterPer = 8;
 
-__global__ void k_plan_scatter(const WinDesc* __restrict__ wins, int64_t seg_len, int dmin, PlanBufs P) {
+__global__ void k_plan_scatter(const WinDesc* __restrict__ wins, int64_t seg_len, int dmin, PlanBufs P,
+                               const int32_t* __restrict__ gcell, const CellInfo* __restrict__ cells, int64_t tmin) {
   extern __shared__ unsigned long long sbase[];  // [0, nb): block bases; then [0, nb) local counts (32-bit)
   const int nb = n_buckets(dmin);
   unsigned int* sh = reinterpret_cast<unsigned int*>(sbase + nb);
@@ -189,7 +201,8 @@ __global__ void k_plan_scatter(const WinDesc* __restrict__ wins, int64_t seg_len
     for (int j = 0; j < kScatterPer; ++j) {
       const int64_t g = base + (int64_t)j * blockDim.x + threadIdx.x;
       const int64_t c = g < W.g1 ? W.offsets[g + 1] - W.offsets[g] : 0;
-      bk[j] = c > 0 ? work_bucket(c, dmin, seg_len) : -1;
+      const bool tiled = c > 0 && is_tiled(c, tmin, (uint32_t)cells[gcell[g]].n_in);
+      bk[j] = c > 0 ? work_bucket(c, dmin, seg_len, tiled) : -1;
       local[j] = bk[j] >= 0 ? atomicAdd(&sh[bk[j]], 1u) : 0u;
     }
     __syncthreads();
@@ -230,7 +243,7 @@ cudaError_t launch_prepare_plan(const LibView& L, const NetView& N, const WalkAr
   cudaError_t e = cudaMemsetAsync(A.plan.counters, 0, sizeof(unsigned long long) * plan_counter_slots(dmin), st);
   if (e != cudaSuccess) return e;
   k_prepare<GATE, true><<<prepare_grid(A), 256, sizeof(unsigned int) * (size_t)n_buckets(dmin), st>>>(
-      L, N, A.wins, A.err, 32ll * A.rpt, dmin, A.plan);
+      L, N, A.wins, A.err, 32ll * A.rpt, dmin, A.plan, GATE ? A.tile_min : 0);
   return cudaGetLastError();
 }
 
@@ -238,12 +251,11 @@ cudaError_t launch_prepare_plan(const LibView& L, const NetView& N, const WalkAr
 
 cudaError_t launch_prepare(const LibView& L, const NetView& N, const WalkArgs& A, bool plan, cudaStream_t st) {
   if (plan) return launch_prepare_plan<true>(L, N, A, st);
-  k_prepare<true, false><<<prepare_grid(A), 256, 0, st>>>(L, N, A.wins, A.err, 32ll * A.rpt, A.dense_min, A.plan);
+  k_prepare<true, false><<<prepare_grid(A), 256, 0, st>>>(L, N, A.wins, A.err, 32ll * A.rpt, A.dense_min, A.plan, 0);
   return cudaGetLastError();
 }
 
-cudaError_t launch_plan_scatter(const NetView& N, const WalkArgs& A, cudaStream_t st) {
-  (void)N;
+cudaError_t launch_plan_scatter(const LibView& L, const NetView& N, const WalkArgs& A, cudaStream_t st) {
   const int dmin = A.dense_min;
   const size_t nb = (size_t)n_buckets(dmin);
   const size_t scatter_smem = nb * (sizeof(unsigned long long) + sizeof(unsigned int));
@@ -251,14 +263,16 @@ cudaError_t launch_plan_scatter(const NetView& N, const WalkArgs& A, cudaStream_
   if (e != cudaSuccess) return e;
   dim3 grid = prepare_grid(A);
   grid.x = (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid.x, (A.n_gates + 256 * kScatterPer - 1) / (256 * kScatterPer)));
-  k_plan_scatter<<<grid, 256, scatter_smem, st>>>(A.wins, 32ll * A.rpt, dmin, A.plan);
+  k_plan_scatter<<<grid, 256, scatter_smem, st>>>(A.wins, 32ll * A.rpt, dmin, A.plan, N.cell, L.cells, A.tile_min);
   return cudaGetLastError();
 }
 
 cudaError_t launch_plan(const NetView& N, const LibView& L, const WalkArgs& A, cudaStream_t st) {
-  cudaError_t e = launch_prepare_plan<false>(L, N, A, st);
+  WalkArgs B = A;
+  B.tile_min = 0;  // the whole list for the walk (the adjoint has no tiled form)
+  cudaError_t e = launch_prepare_plan<false>(L, N, B, st);
   if (e != cudaSuccess) return e;
-  return launch_plan_scatter(N, A, st);
+  return launch_plan_scatter(L, N, B, st);
 }
 
 cudaError_t launch_walk(const LibView& L, const NetView& N, const WalkArgs& A, bool backward, cudaStream_t st) {

@@ -27,9 +27,23 @@ struct PlanBufs {
 
 // counters[0] = big gates, [1] = medium gates, [2] = sparse gates, [3] = work
 // items handed out so far (the walk's work counter), [4] = blocks of the
-// preparation pass that finished, then the work-list histogram and its bucket
-// cursors.
+// preparation pass that finished, [5] = tiled gates, [6] = the tiled walk's
+// work counter, [7] = the tiled walk's chunks, then the work-list histogram
+// and its bucket cursors.  The work list holds big, medium, sparse, then
+// tiled gates.
+constexpr int kPlanCntTiled = 5;
+constexpr int kPlanCntTiledWork = 6;
+constexpr int kPlanCntChunks = 7;
+constexpr int kPlanCntHist = 8;
 int plan_counter_slots(int dense_min);
+
+// Gates walked by the time-sliced walk (gtp_tiled.cu) instead of the
+// persistent walk: at least tmin events (tmin > 0), fewer than 2^31 (the walk
+// keeps run offsets within a gate in 32 bits) and a cell with a per-gate
+// energy table.
+__host__ __device__ inline bool is_tiled(int64_t c, int64_t tmin, uint32_t n_in) {
+  return tmin > 0 && c >= tmin && c < (1ll << 31) && n_in <= (uint32_t)kGateTabMaxIn;
+}
 
 struct WalkArgs {
   const WinDesc* wins;      // device array of n_win descriptors
@@ -45,6 +59,9 @@ struct WalkArgs {
   PlanBufs plan;
   int64_t n_gates;
   bool comp;                // forward: also accumulate every window's component bins (WinDesc::cbins)
+  int64_t tile_min;         // single-window plain forward runs: gates with this many events or more go
+                            // to the time-sliced walk (0: none)
+  int32_t* chunks;          // tiled walk: chunk starts in the tiled list (capacity tile_chunk_cap(n_gates))
 };
 
 bool walk_rpt_supported(int rpt);
@@ -53,9 +70,17 @@ bool walk_rpt_supported(int rpt);
 // events), and with `plan` the work-list histogram and bucket starts.
 cudaError_t launch_prepare(const LibView& L, const NetView& N, const WalkArgs& A, bool plan, cudaStream_t st);
 // Scatter of the (window, gate) pairs with events into the work list: big
-// gates (largest first), medium gates, sparse gates.  Follows launch_prepare
-// with plan, or launch_plan's histogram.
-cudaError_t launch_plan_scatter(const NetView& N, const WalkArgs& A, cudaStream_t st);
+// gates (largest first), medium gates, sparse gates, tiled gates.  Follows
+// launch_prepare with plan, or launch_plan's histogram.
+cudaError_t launch_plan_scatter(const LibView& L, const NetView& N, const WalkArgs& A, cudaStream_t st);
+
+// The time-sliced walk of the tiled gates (gtp_tiled.cu): chunking of the
+// tiled list (one block), then the persistent walk over (chunk, slice) items.
+// Single window (A.wins[0]), plain forward walk only.
+int64_t tile_chunk_cap(int64_t n_gates);
+// Whether the library's leakage table fits the tiled walk's shared memory.
+bool tiled_fits(const LibView& L);
+cudaError_t launch_tiled(const LibView& L, const NetView& N, const WalkArgs& A, int32_t n_bins, cudaStream_t st);
 // The whole work list without the gate pass (the adjoint): histogram, bucket
 // starts and scatter (no host synchronisation).
 cudaError_t launch_plan(const NetView& N, const LibView& L, const WalkArgs& A, cudaStream_t st);

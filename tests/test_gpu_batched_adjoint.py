@@ -22,7 +22,7 @@ def engine():
 
 
 def _reset(engine):
-    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm"):
+    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm", "tile_min"):
         engine.set_param(k, -1)
 
 

@@ -73,7 +73,7 @@ def _totals_agree(wave, ge, bin_ps):
 
 
 def _defaults(engine):
-    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm"):
+    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm", "tile_min"):
         engine.set_param(k, -1)
 
 

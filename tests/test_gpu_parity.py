@@ -19,8 +19,10 @@ KERNELS = [
     dict(kernel=0, records_per_thread=4, dense_min=16),
     dict(kernel=0, records_per_thread=8),
     dict(kernel=0, records_per_thread=16, dense_min=64),
+    dict(kernel=0, records_per_thread=8, tile_min=1),    # every gate through the time-sliced walk
+    dict(kernel=0, records_per_thread=4, dense_min=16, tile_min=40),
 ]
-KID = ["per_gate", "seg_k4", "seg_k8", "seg_k16"]
+KID = ["per_gate", "seg_k4", "seg_k8", "seg_k16", "tiled_all", "tiled40"]
 
 
 @pytest.fixture(scope="module")
@@ -34,7 +36,7 @@ def engine():
 def run(engine, lib, net, tr, bin_ps, params=None, escale=None, lscale=None, window=0):
     engine.load_library(lib)
     engine.load_netlist(net)
-    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm"):
+    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm", "tile_min"):
         engine.set_param(k, -1)
     for k, v in (params or {}).items():
         engine.set_param(k, v)
@@ -278,7 +280,7 @@ def test_device_resident_events(engine, borrow):
     lib, net, tr = small_random(n_gates=100, n_events=20_001, window_ps=200_000, seed=51, tie_p=0.02)
     engine.load_library(lib)
     engine.load_netlist(net)
-    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm"):
+    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm", "tile_min"):
         engine.set_param(k, -1)
     dev = engine.device
     off = torch.from_numpy(tr.offsets).to(dev)
