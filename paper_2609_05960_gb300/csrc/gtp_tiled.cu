@@ -57,7 +57,7 @@ constexpr int kTSeg = 32 * kTK;
 constexpr int kSliceBins = 16384;        // bins of one slice
 constexpr int kChunkMaxGates = 512;      // gates of one chunk
 constexpr int kTLeakMax = 512;           // leakage entries staged per CTA
-constexpr int kT2 = 256;                 // a warp's event-energy table: (input state << 5) | meta
+constexpr int kT4 = 64;                  // a warp's event table: (state << 2) | pin
 constexpr int kFlushBins = 4096;         // bins converted to FP64 per bulk reduction (64 KB)
 constexpr float kEScale = 16777216.f;    // energy words: units of 2^-24 fJ
 constexpr float kSScale = 4194304.f;     // leakage-step words: units of 2^-22 nW
@@ -70,7 +70,7 @@ constexpr uint32_t kVEnd = 1u << 31;     //   the run ends at the gate's last re
 constexpr size_t kTBinsBytes = sizeof(int2) * kSliceBins;
 constexpr size_t kTRecBytes = sizeof(uint2) * kTWarps * 2 * kTSeg;
 constexpr size_t kTHaloBytes = sizeof(uint2) * kTWarps * 4;
-constexpr size_t kTT2Bytes = sizeof(float) * kTWarps * kT2;
+constexpr size_t kTT2Bytes = sizeof(float4) * kTWarps * kT4 + sizeof(float) * kTWarps * kGateTab;
 constexpr size_t kTLeakBytes = sizeof(float) * kTLeakMax;
 constexpr size_t kTVisitBytes = (sizeof(int64_t) + 3 * sizeof(int32_t) + 1) * kChunkMaxGates;
 constexpr size_t kTSmem = kTBinsBytes + kTRecBytes + kTHaloBytes + kTT2Bytes + kTLeakBytes + kTVisitBytes;
@@ -80,7 +80,9 @@ struct TSmem {
   int2* bins;     // [kSliceBins] {energy word, step word}, signed
   uint2* rec;     // this warp's [2][kTSeg] staged records
   uint2* halo;    // this warp's [2][2]: the records just before and just after a segment
-  float* t2;      // this warp's [kT2] energy of an event with meta m at input state s: [(s << 5) | m]
+  float4* t4;     // this warp's [kT4] table of a toggle of pin p at gate state s, entry (s << 2) | p:
+                  //   {energy, leakage after, leakage change * 1e-6, leakage change in step units (int bits)}
+  float* gt;      // this warp's copy of the gate's energy table [kGateTab] (timestamp groups with ties)
   float* leak;    // [n_leak] leakage per state, times lscale
   int64_t* vr0;   // [kChunkMaxGates] the chunk's runs in this slice: first record
   int32_t* vn;    //   records in the run
@@ -186,22 +188,36 @@ __device__ __forceinline__ TV load_visit(const TSmem& sm, int i) {
   return v;
 }
 
-// The warp's event-energy table for a visit: entry (s << 5) | m is the energy
-// of an event with meta m (pin | value << 4) when the input pins' state before
-// its timestamp group is s.  Filled from the gate's 32-entry table (lane l
-// holds entry l), whose entry (pin << n_in) | s' is indexed by the input state
-// with the pin's own bit at its old value (the complement of the new value).
-__device__ __forceinline__ void build_t2(float* t2, float gt, uint32_t n_in, int lane) {
+// The warp's tables for a visit.  sm.gt holds the gate's 32-entry energy
+// table (lane l brought entry l in `gt`), entry (pin << n_in) | s indexed by
+// the input pins' state with the pin's own bit at its old value.  sm.t4 holds,
+// for a toggle of pin p in gate state s (a valid event: its new value is the
+// complement of bit p of s), entry (s << 2) | p: the event's energy, the
+// leakage power after it, the leakage change times 1e-6 and the change in
+// step-word units.  Returns false if a leakage change is too large for a
+// step word (the visit then takes the general path).
+__device__ __forceinline__ bool build_t4(const TSmem& sm, float gt, uint32_t n_in, const float* leak, int lane) {
+  sm.gt[lane] = gt;
   const uint32_t inmask = (1u << n_in) - 1u;
-  const uint32_t pin = (uint32_t)lane & 0xFu, val = ((uint32_t)lane >> 4) & 1u;
-  const uint32_t bitp = 1u << pin;
-  const uint32_t own = (val - 1u) & bitp & inmask;
-  for (uint32_t s = 0; s < (1u << n_in); ++s) {
-    const uint32_t idx = ((pin << n_in) | (s & inmask & ~bitp) | own) & 31u;
-    const float e = __shfl_sync(kFull, gt, (int)idx);
-    t2[(s << 5) | (uint32_t)lane] = pin <= n_in ? e : 0.f;
+  bool ok = true;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const uint32_t e = (uint32_t)lane + 32u * h;
+    const uint32_t st = e >> 2, pin = e & 3u;
+    const bool valid = pin <= n_in && st < (2u << n_in);
+    const float E = __shfl_sync(kFull, gt, (int)(((pin << n_in) | (st & inmask)) & 31u));
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) {
+      const float P0 = leak[st], P1 = leak[st ^ (1u << pin)];
+      const float dp = P1 - P0;
+      const float x = dp * kSScale;
+      ok = ok && fabsf(x) < kQMax;
+      v = make_float4(E, P1, dp * 1e-6f, __int_as_float(fabsf(x) < kQMax ? __float2int_rn(x) : 0));
+    }
+    sm.t4[e] = v;
   }
   __syncwarp();
+  return __all_sync(kFull, ok);
 }
 
 // Copy segment s of visit v into `buf`, with the record before it (if the
@@ -308,13 +324,33 @@ __device__ __forceinline__ void acc_word(int* w, float v, float scale, double* g
   }
 }
 
+// acc_word for a term already in word units (q).
+__device__ __forceinline__ void acc_int(int* w, int q, float scale, double* gaddr) {
+  const int old = atomicAdd(w, q);
+  const int now = (int)((unsigned)old + (unsigned)q);
+  if (((old ^ now) & (q ^ now)) < 0) red_f64(gaddr, q > 0 ? 4294967296.0 / scale : -4294967296.0 / scale);
+}
+
+// v * 2^-sh as a double, built with integer operations (the FP64 pipe is
+// narrow on this GPU); exact for every 32-bit v.
+__device__ __forceinline__ double i2d_scaled(int v, int sh) {
+  if (v == 0) return 0.0;
+  const unsigned long long sign = v < 0 ? 1ull << 63 : 0ull;
+  const uint32_t a = v < 0 ? 0u - (uint32_t)v : (uint32_t)v;
+  const int lz = __clz(a);
+  const unsigned long long frac = ((unsigned long long)a << (lz + 21)) & ((1ull << 52) - 1ull);
+  const unsigned long long ex = (unsigned long long)(1023 + 31 - lz - sh);
+  return __longlong_as_double((long long)(sign | (ex << 52) | frac));
+}
+
 struct TSums {
-  float leak, dyn, sw;  // leakage (nW*ps), all dynamic energy, switching (fJ)
+  float leak, dyn, sw;  // leakage (nW*ps), internal energy (fJ), output events (switching energy = count * Esw)
 };
 
 // Replay of a screened segment into the slice's shared bins.
 __device__ __forceinline__ TSums t_back(const TSlice& sl, const TSmem& sm, const TV& v, const WinDesc& W,
-                                        const uint2* buf, const TSeg& q, uint32_t seg_in, DevError* err, int lane) {
+                                        const uint2* buf, const TSeg& q, uint32_t seg_in, bool fast_ok, DevError* err,
+                                        int lane) {
   TSums out{0.f, 0.f, 0.f};
   if (__any_sync(kFull, q.bad)) {
     if (q.bad) report_error(err, GTP_ERANGE, q.s0 + lane * kTK);
@@ -332,35 +368,33 @@ __device__ __forceinline__ TSums t_back(const TSlice& sl, const TSmem& sm, const
   uint32_t tp = q.t_before;
   const uint32_t rb = row_base<kTK>(lane);
   bool lb_bad = false;
-  if (q.fast) {  // no ties: every event is the head and the tail of its own group
+  if (q.fast && fast_ok) {  // no ties: every event is the head and the tail of its own group
 #pragma unroll
     for (int k = 0; k < kTK; ++k) {
       if (k < q.nk) {
         const uint2 rc = buf[rb ^ (uint32_t)k];
         const uint32_t t = rc.x, m = rc.y;
-        const uint32_t pin = m & 0xFu;
-        const float E = sm.t2[((st & inmask) << 5) | (m & 31u)];
+        const uint32_t pin = m & 3u;  // tiled gates have at most 4 pins (screened)
         tog &= (st >> pin) ^ (m >> 4);
+        const float4 T4 = sm.t4[(st << 2) | pin];
         st ^= 1u << pin;
-        const float Pn = leak[st];
-        const float dp = Pn - Pcur;
         v0 = fmaf(Pcur, (float)(int32_t)(t - tp), v0);
+        Pcur = T4.y;
         uint32_t bn = __umulhi(t, sl.magic) >> sl.shift;
         uint32_t bend = (bn + 1u) * sl.bin_ps;
         if (bend <= t) {
           ++bn;
           bend += sl.bin_ps;
         }
-        vd += E;
-        vw += pin == n_in ? E : 0.f;
+        vd += pin < n_in ? T4.x : 0.f;
+        vw += pin == n_in ? 1.f : 0.f;
         const uint32_t lb = bn - sl.b0;
         if (lb < sl.nb) {
-          acc_word(&sm.bins[lb].x, fmaf(dp, (float)(int32_t)(bend - t) * 1e-6f, E), kEScale, &sl.gbins[bn].x);
-          acc_word(&sm.bins[lb].y, dp, kSScale, &sl.gbins[bn].y);
+          acc_word(&sm.bins[lb].x, fmaf(T4.z, (float)(int32_t)(bend - t), T4.x), kEScale, &sl.gbins[bn].x);
+          acc_int(&sm.bins[lb].y, __float_as_int(T4.w), kSScale, &sl.gbins[bn].y);
         } else {
           lb_bad = true;
         }
-        Pcur = Pn;
         tp = t;
       }
     }
@@ -377,9 +411,11 @@ __device__ __forceinline__ TSums t_back(const TSlice& sl, const TSmem& sm, const
         v0 = head ? fmaf(Pcur, (float)(int32_t)(t - tp), v0) : v0;
         spre = head ? st : spre;
         Pg = head ? Pcur : Pg;
-        const float E = sm.t2[((spre & inmask) << 5) | (m & 31u)];
+        const uint32_t bitp = 1u << pin;
+        const uint32_t own = ((m >> 4) - 1u) & bitp & inmask;
+        const float E = sm.gt[((pin << n_in) | (spre & inmask & ~bitp) | own) & 31u];
         tog &= (st >> pin) ^ (m >> 4);
-        st = (st ^ (1u << pin)) & pmask;
+        st = (st ^ bitp) & pmask;
         const bool tail = tn != t;
         const float Pn = tail ? leak[st] : Pcur;
         const float dp = tail ? Pn - Pg : 0.f;
@@ -389,8 +425,8 @@ __device__ __forceinline__ TSums t_back(const TSlice& sl, const TSmem& sm, const
           ++bn;
           bend += sl.bin_ps;
         }
-        vd += E;
-        vw += pin == n_in ? E : 0.f;
+        vd += pin < n_in ? E : 0.f;
+        vw += pin == n_in ? 1.f : 0.f;
         const uint32_t lb = bn - sl.b0;
         if (lb < sl.nb) {
           acc_word(&sm.bins[lb].x, fmaf(dp, (float)(int32_t)(bend - t) * 1e-6f, E), kEScale, &sl.gbins[bn].x);
@@ -516,7 +552,8 @@ __global__ void __launch_bounds__(kTThreads, 1) k_tiled(LibView L, NetView N, Wa
   p += kTRecBytes;
   sm.halo = reinterpret_cast<uint2*>(p) + (size_t)wib * 4;
   p += kTHaloBytes;
-  sm.t2 = reinterpret_cast<float*>(p) + (size_t)wib * kT2;
+  sm.t4 = reinterpret_cast<float4*>(p) + (size_t)wib * kT4;
+  sm.gt = reinterpret_cast<float*>(reinterpret_cast<float4*>(p) + (size_t)kTWarps * kT4) + (size_t)wib * kGateTab;
   p += kTT2Bytes;
   sm.leak = reinterpret_cast<float*>(p);
   p += kTLeakBytes;
@@ -592,11 +629,13 @@ __global__ void __launch_bounds__(kTThreads, 1) k_tiled(LibView L, NetView N, Wa
     };
     int cur = grab();
     TV vc{}, vn{};
-    float gt_next = 0.f;
+    float gt_next = 0.f, gt_cur = 0.f;
+    bool fast_ok = false;
     if (cur >= 0) {
       vc = load_visit(sm, cur);
       if (lane == 0) s_any = 1;
-      build_t2(sm.t2, __ldg(A.gtab + (size_t)vc.g * kGateTab + lane), vc.inf & 0xFu, lane);
+      gt_cur = __ldg(A.gtab + (size_t)vc.g * kGateTab + lane);
+      fast_ok = build_t4(sm, gt_cur, vc.inf & 0xFu, sm.leak + ((vc.inf >> 4) & 0x3FFFFFu), lane);
       t_issue(sl, vc, 0, sm.rec, sm.halo, lane);
     }
     int s = 0, kb = 0;
@@ -623,7 +662,7 @@ __global__ void __launch_bounds__(kTThreads, 1) k_tiled(LibView L, NetView N, Wa
       const uint2* buf = sm.rec + (kb & 1) * kTSeg;
       TSeg q;
       const uint32_t tx = t_front(sl, vc, s, buf, sm.halo + (kb & 1) * 2, q, lane);
-      const TSums o = t_back(sl, sm, vc, W, buf, q, carry, err, lane);
+      const TSums o = t_back(sl, sm, vc, W, buf, q, carry, fast_ok, err, lane);
       carry = xcompose(carry, tx);
       f0 += o.leak;
       f1 += o.dyn;
@@ -640,10 +679,12 @@ __global__ void __launch_bounds__(kTThreads, 1) k_tiled(LibView L, NetView N, Wa
         a0 += (double)warp_sum(f0);
         a1 += (double)warp_sum(f1);
         a2 += (double)warp_sum(f2);
+        const uint32_t vin = vc.inf & 0xFu;
+        const float esw = __shfl_sync(kFull, gt_cur, (int)((vin << vin) & 31u));  // the output pin's energy
         if (lane == 0) {
           atomicAdd(W.e_leak + vc.g, a0 * 1e-6);
-          atomicAdd(W.e_int + vc.g, a1 - a2);
-          atomicAdd(W.e_sw + vc.g, a2);
+          atomicAdd(W.e_int + vc.g, a1);
+          atomicAdd(W.e_sw + vc.g, a2 * (double)esw);
         }
         f0 = f1 = f2 = 0.f;
         a0 = a1 = a2 = 0.0;
@@ -651,7 +692,8 @@ __global__ void __launch_bounds__(kTThreads, 1) k_tiled(LibView L, NetView N, Wa
         cur = nxt;
         if (cur >= 0) {
           vc = vn;
-          build_t2(sm.t2, gt_next, vc.inf & 0xFu, lane);
+          gt_cur = gt_next;
+          fast_ok = build_t4(sm, gt_cur, vc.inf & 0xFu, sm.leak + ((vc.inf >> 4) & 0x3FFFFFu), lane);
           carry = kXAbs | kXH | vc.entry | (vc.entry << 8);
         }
       }
@@ -669,7 +711,7 @@ __global__ void __launch_bounds__(kTThreads, 1) k_tiled(LibView L, NetView N, Wa
         const uint32_t nf = min((uint32_t)kFlushBins, sl.nb - f0);
         for (uint32_t i = threadIdx.x; i < nf; i += kTThreads) {
           const int2 w = sm.bins[f0 + i];
-          fb[i] = make_double2((double)w.x * (1.0 / kEScale), (double)w.y * (1.0 / kSScale));
+          fb[i] = make_double2(i2d_scaled(w.x, 24), i2d_scaled(w.y, 22));
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
