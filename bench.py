@@ -36,9 +36,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "events/sec and % of HBM roofline; batched and adjoint vs plain kernel"
-# DRAM bytes (read + write) of one walk launch (k_walk<8,0,0,0>) on the full large workload, from
-# one ncu capture (profiles/k_walk_large_dram_200m.md); reported as roofline.traffic for that
-# workload and plan only
+# DRAM bytes (read + write) of one walk launch (k_walk<8,0,0,0>) on the full large workload with
+# the default plan, from one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum (one
+# pass); reported as roofline.traffic for that workload and plan only, and to be captured again
+# whenever the walk changes
 WALK_TRAFFIC = {("large", 8, 256): 2_020_312_000 + 80_774_912}
 UNIT = "events/s"
 
@@ -55,7 +56,11 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
-    p.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the glitch, components, batched, adjoint, load-change and stress measurements")
+    p.add_argument("--no-oracle-check", action="store_true",
+                   help="skip the FP64 oracle over every bin and gate of each measured workload")
+    p.add_argument("--no-stress", action="store_true", help="skip the stress workload (10M gates, 2B events)")
     p.add_argument("--events", type=int, default=0,
                    help="scale the configuration to this many events (same gates and distribution; "
                         "for profiling a smaller case)")
@@ -310,6 +315,11 @@ def run_ours(args, cfg_name):
     from paper_2609_05960_gb300 import Engine, gtpower
 
     ws, rank, local, pg = dist_init()
+    # the FP64 oracle on every host core, for each measured result's error (spawned workers)
+    opool = None
+    if rank == 0 and not args.no_oracle_check:
+        from oracle import fullsize
+        opool = fullsize.Pool()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     cfg = config_of(args, cfg_name)
@@ -377,10 +387,18 @@ def run_ours(args, cfg_name):
     peak_src = "measured" if peak else "fallback"
     peak = peak or 6800.0
     alg = algorithmic_bytes(n_ev, n_active, G, n_bins)
-    # the bound the walk actually meets: one 8-byte bin reduction per event, against the rate this GPU
-    # sustains for such reductions, measured here
+    # a reference rate for the walk's bin updates: 8-byte reductions into as many hashed slots as bins
     red_peak = gtpower.gtp_measure_reductions(ctx, n_bins, 2)
     achieved = alg / walk_s / 1e9 if walk_s > 0 else 0.0
+    oracle_err = None
+    if opool is not None:  # every bin and every gate of this run against the FP64 oracle
+        from oracle import fullsize
+        ref = opool.walk(fullsize.Workload.of(cfg, seed_ev=seed_ev), cfg.bin_ps)
+        got = {"e_leak": g_leak.cpu().numpy(), "e_int": g_int.cpu().numpy(), "e_sw": g_sw.cpu().numpy(),
+               "n_events": g_cnt.cpu().numpy(), "final_state": g_fin.cpu().numpy()}
+        oracle_err = {**fullsize.bin_errors(wave.cpu().numpy(), ref["bins"], cfg.bin_ps),
+                      **fullsize.gate_errors(got, ref)}
+        del ref
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -423,16 +441,19 @@ def run_ours(args, cfg_name):
             return statistics.median(times)
 
         d2h = n_bins * 8 + G * (8 * 3 + 8 + 1)
-        t_e2e = time_e2e(True)
-        h2d = pk_h.numel() * 4 + off_h.numel() * 8 + init_h.numel()
         t_e2e8 = time_e2e(False)
         h2d8 = rec_h.numel() * 4 + off_h.numel() * 8 + init_h.numel()
-        e2e = {"value": ws * args.e2e_steps * n_ev / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * t_e2e / args.e2e_steps,
-               "input": "packed transfer form (gtp_pack_events, 4.125 B a record), streamed in 8 chunks",
+        t_e2e = time_e2e(True)
+        h2d = pk_h.numel() * 4 + off_h.numel() * 8 + init_h.numel()
+        e2e = {"value": ws * args.e2e_steps * n_ev / t_e2e8, "unit": UNIT, "h2d_bytes_per_step": int(h2d8),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * t_e2e8 / args.e2e_steps,
+               "input": "the ABI's 8-byte records from pinned host memory, streamed in 8 chunks "
+                        "(gtp_run_power_streamed), then per-gate results to host memory (gtp_gate_energy)",
                "timing": f"median of 5 trials of {args.e2e_steps} steps, host clock around CUDA-synchronised steps",
-               "records_8b": {"value": ws * args.e2e_steps * n_ev / t_e2e8, "h2d_bytes_per_step": int(h2d8),
-                              "ms_per_step": 1e3 * t_e2e8 / args.e2e_steps}}
+               "packed": {"value": ws * args.e2e_steps * n_ev / t_e2e, "h2d_bytes_per_step": int(h2d),
+                          "ms_per_step": 1e3 * t_e2e / args.e2e_steps,
+                          "input": "the packed transfer form (gtp_pack_events, 4.125 B a record), streamed in 8 "
+                                   "chunks; the packing runs once before the timed region, like writing the trace"}}
         del rec_h, pk_h
 
     cpu = None
@@ -449,11 +470,22 @@ def run_ours(args, cfg_name):
 
     extras = {}
     if rank == 0 and not args.no_extras and cfg_name == "large" and not args.events:
-        extras["glitch"] = measure_glitch(eng, dev, cfg, wave, walk_s * 1e3, n_ev, max(3, min(args.steps // 10, 10)))
-        extras["components"] = measure_components(eng, dev, cfg, walk_s * 1e3, n_ev,
-                                                  max(3, min(args.steps // 10, 10)))
-        extras["batched"] = measure_batched(eng, dev, max(3, min(args.steps // 10, 10)))
-        extras["adjoint"] = measure_adjoint(eng, dev, max(3, min(args.steps // 10, 10)))
+        xs = max(3, min(args.steps // 10, 10))
+        wl_large = None
+        if opool is not None:
+            from oracle import fullsize
+            wl_large = fullsize.Workload.of(cfg, seed_ev=seed_ev)
+        extras["load_change"] = measure_load_change(eng, dev, cfg, wave, n_ev, ms_max / args.steps, xs, net.load_ff)
+        extras["glitch"] = measure_glitch(eng, dev, cfg, wave, walk_s * 1e3, n_ev, xs, opool, wl_large)
+        extras["components"] = measure_components(eng, dev, cfg, walk_s * 1e3, n_ev, xs, opool, wl_large)
+        del rec
+        torch.cuda.empty_cache()
+        extras["batched"] = measure_batched(eng, dev, xs, peak, value, opool)
+        extras["adjoint"] = measure_adjoint(eng, dev, xs, peak=peak, opool=opool)
+        if not args.no_stress:
+            extras["stress"] = measure_stress(eng, dev, xs, peak, opool)
+    if opool is not None:
+        opool.close()
 
     if rank == 0:
         out = {
@@ -470,16 +502,20 @@ def run_ours(args, cfg_name):
                          "frac": achieved / peak, "kernel": "k_walk",
                          "traffic": None if args.events else WALK_TRAFFIC.get(
                              (cfg.name, eng.get_param("records_per_thread"), eng.get_param("dense_min"))),
-                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one walk launch "
-                                           "(profiles/k_walk_large_dram_200m.md)",
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one walk launch of "
+                                           "this kernel on this workload and plan",
+                         "peak_kind": "burst copy bandwidth (the walk is timed alone, per launch)",
                          "algorithmic_bytes": alg, "walk_ms": walk_s * 1e3, "peak_source": peak_src,
                          "frac_of_nominal_8tbs": achieved / 8000.0,
                          "l2_reductions": {"achieved_per_s": n_ev / walk_s if walk_s > 0 else 0.0,
-                                           "peak_per_s": red_peak,
-                                           "frac": (n_ev / walk_s) / red_peak if walk_s > 0 and red_peak > 0 else 0.0,
-                                           "note": "one bin reduction per event (ncu counts 40.0 M reduction sectors "
-                                                   "for 40 M events); peak = gtp_measure_reductions, 8-byte "
-                                                   "reductions into as many hashed slots as bins, in this run"}},
+                                           "reference_rate_per_s": red_peak,
+                                           "ratio": (n_ev / walk_s) / red_peak if walk_s > 0 and red_peak > 0
+                                           else 0.0,
+                                           "note": "about one bin reduction per event; the reference rate is "
+                                                   "gtp_measure_reductions (8-byte reductions spread by a hash "
+                                                   "over as many slots as bins, in this run), not a roofline: "
+                                                   "the walk's own updates are local in time"}},
+            "oracle_error": oracle_err,
             "phases_ms": {"prepare": gate_s * 1e3, "scatter": plan_s * 1e3, "walk": walk_s * 1e3,
                           "merge": merge_s * 1e3},
             "e2e": e2e,
@@ -506,10 +542,71 @@ def _events_per_s(fn, steps, dev):
     return e0.elapsed_time(e1) / steps  # ms
 
 
-def measure_batched(eng, dev, steps):
+def roofline(alg_bytes, walk_ms, peak):
+    """HBM roofline of a walk: its algorithmic bytes over its measured time."""
+    ach = alg_bytes / (walk_ms * 1e-3) / 1e9 if walk_ms > 0 else 0.0
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak if peak else None,
+            "algorithmic_bytes": int(alg_bytes), "walk_ms": walk_ms}
+
+
+def _timed_walk(eng, fn, steps, dev):
+    """(ms per call, walk-phase ms per call) of fn, with the engine's phase
+    timing on."""
+    eng.set_param("timing", 1)
+    ms = _events_per_s(fn, steps, dev)
+    n_t = max(eng.get_param("n_timed"), 1)
+    walk_ms = eng.get_param("t_walk_ns") * 1e-6 / n_t
+    eng.set_param("timing", 0)
+    return ms, walk_ms
+
+
+def _gate_results(eng, w, glitch=False):
+    ge = eng.gate_energy(w, device=False)
+    if glitch:
+        ge["e_gl"] = eng.gate_glitch(w, device=False)
+    return ge
+
+
+def _oracle_errors(opool, wl, bin_ps, wave, ge, keys=("e_leak", "e_int", "e_sw")):
+    from oracle import fullsize
+    ref = opool.walk(wl, bin_ps)
+    w = wave.cpu().numpy() if hasattr(wave, "cpu") else np.asarray(wave)
+    return {**fullsize.bin_errors(w, ref["bins"], bin_ps), **fullsize.gate_errors(ge, ref, keys)}
+
+
+def measure_load_change(eng, dev, cfg, wave, n_ev, step_ms, steps, load_ff):
+    """The step of an optimisation loop over the large window (slot 0): a new
+    load per gate (gtp_set_load, which rebuilds the interpolation
+    coordinates and the per-gate energy tables) and then the run."""
+    import torch
+
+    from paper_2609_05960_gb300 import gtpower
+
+    base = torch.from_numpy(np.ascontiguousarray(load_ff, dtype=np.float32)).to(dev)
+    k = [0]
+
+    def step():
+        k[0] += 1
+        gtpower.gtp_set_load(eng.ctx, base * (1.0 + 1e-3 * (k[0] & 1)))
+        gtpower.gtp_run_power(eng.ctx, 0, cfg.bin_ps, wave, graph=True)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize(dev)
+    ms = _events_per_s(step, steps, dev)
+    gtpower.gtp_set_load(eng.ctx, base)
+    return {"ms_per_step": ms, "value": n_ev / (ms * 1e-3), "unit": UNIT,
+            "over_plain_step": ms / step_ms if step_ms > 0 else None,
+            "what": "gtp_set_load (new load per gate: interpolation coordinates and per-gate energy tables rebuilt) "
+                    "+ gtp_run_power, as in an optimisation loop"}
+
+
+def measure_batched(eng, dev, steps, peak, plain_value, opool=None):
     """64 windows of uneven length over a 200k-gate netlist: autotuned plan,
-    one persistent launch per run, replayed from a CUDA graph, against the
-    same windows run one at a time through gtp_run_power."""
+    one persistent launch per run, replayed from a CUDA graph.  Reported with
+    its walk's roofline, against the plain large window's rate (one window of
+    200M events), against the same windows run one at a time, and each
+    window's error against the oracle."""
     import torch
 
     import synth
@@ -520,7 +617,7 @@ def measure_batched(eng, dev, steps):
     eng.load_library(lib)
     eng.load_netlist(net)
     wins = synth.batched_windows()
-    keep, total = [], 0
+    keep, total, alg, specs = [], 0, 0, []
     for w, spec in enumerate(wins):
         counts = synth.zipf_counts(synth.BATCHED_GATES, spec["n_events"], 1.2, 100_000, spec["seed"])
         tr, rec = synth.make_trace_gpu(net, counts, spec["window_ps"], spec["seed"], device=dev)
@@ -529,28 +626,52 @@ def measure_batched(eng, dev, steps):
         eng.load_events(w, window_ps=spec["window_ps"], offsets=off, records=rec, init_state=init, borrow=True)
         keep.append((rec, off, init))
         total += tr.n_events
+        alg += algorithmic_bytes(tr.n_events, int((counts > 0).sum()), synth.BATCHED_GATES, spec["window_ps"] // 10)
+        specs.append((spec, int(counts.sum())))
     ids = list(range(len(wins)))
     tuned_ms = eng.autotune(ids, 10, iters=2)
     plan = {k: eng.get_param(k) for k in ("records_per_thread", "ctas_per_sm", "dense_min")}
     outs = [torch.empty(s["window_ps"] // 10, dtype=torch.float64, device=dev) for s in wins]
-    ms_b = _events_per_s(lambda: gtpower.gtp_run_power_batched(eng.ctx, ids, 10, outs, graph=True), steps, dev)
+    run = lambda: gtpower.gtp_run_power_batched(eng.ctx, ids, 10, outs, graph=True)
+    run()
+    ms_b, walk_ms = _timed_walk(eng, run, steps, dev)
     ref = [o.clone() for o in outs]
     ms_p = _events_per_s(lambda: [gtpower.gtp_run_power(eng.ctx, w, 10, outs[w]) for w in ids], steps, dev)
     diff = max(float(((o - r).abs() / r.abs()).max()) for o, r in zip(outs, ref))
+    err = None
+    if opool is not None:
+        from oracle import fullsize
+        worst = {}
+        for w, (spec, n) in enumerate(specs):
+            wl = fullsize.Workload(synth.BATCHED_GATES, spec["n_events"], 1.2, 100_000, spec["window_ps"], 1, 2,
+                                   spec["seed"])
+            e = _oracle_errors(opool, wl, 10, ref[w], _gate_results(eng, w))
+            for k, v in e.items():
+                if k.startswith("max_rel") or k.endswith("mismatches"):
+                    worst[k] = max(worst.get(k, 0), v)
+            worst["mean_rel_bin_err"] = worst.get("mean_rel_bin_err", 0.0) + e["mean_rel_bin_err"] * e["bins"]
+            worst["bins"] = worst.get("bins", 0) + e["bins"]
+        worst["mean_rel_bin_err"] /= max(worst["bins"], 1)
+        err = worst
     del keep
+    value = total / (ms_b * 1e-3)
     return {"workload": f"{len(wins)} windows over {synth.BATCHED_GATES:,} gates, {total:,} events, "
                         f"1k-100k bins of 10 ps", "events": total, "ms_per_run": ms_b,
-            "value": total / (ms_b * 1e-3), "unit": UNIT, "plain_ms_per_run": ms_p,
-            "plain_value": total / (ms_p * 1e-3), "speedup_vs_plain": ms_p / ms_b,
-            "max_rel_diff_vs_plain": diff, "autotuned_plan": plan, "autotune_best_ms": tuned_ms,
-            "graph": True}
+            "value": value, "unit": UNIT, "roofline": roofline(alg, walk_ms, peak),
+            "vs_one_plain_window": value / plain_value if plain_value else None,
+            "one_plain_window": "the large window (200M events in one window) timed above",
+            "separate_runs_ms": ms_p, "speedup_vs_separate_runs": ms_p / ms_b,
+            "max_rel_diff_vs_separate_runs": diff, "oracle_error": err, "autotuned_plan": plan,
+            "autotune_best_ms": tuned_ms, "graph": True}
 
 
-def measure_glitch(eng, dev, cfg, wave, walk_plain_ms, n_ev, steps):
+def measure_glitch(eng, dev, cfg, wave, walk_plain_ms, n_ev, steps, opool=None, wl=None):
     """The same window (still loaded in slot 0) with clock-cycle glitch
     detection at a 1 GHz clock (output transition times 10-200 ps, seeded):
-    run time, walk time against the plain walk, and the glitch share of the
-    dynamic energy."""
+    run time, walk time against the plain walk, the glitch share of the
+    dynamic energy, and the error against the oracle."""
+    import dataclasses
+
     import torch
 
     from paper_2609_05960_gb300 import gtpower
@@ -563,25 +684,25 @@ def measure_glitch(eng, dev, cfg, wave, walk_plain_ms, n_ev, steps):
     for _ in range(3):
         run()
     torch.cuda.synchronize(dev)
-    eng.set_param("timing", 1)
-    ms = _events_per_s(run, steps, dev)
-    n_t = max(eng.get_param("n_timed"), 1)
-    walk_ms = eng.get_param("t_walk_ns") * 1e-6 / n_t
-    eng.set_param("timing", 0)
-    ge = eng.gate_energy(0)
-    e_gl = eng.gate_glitch(0)
-    dyn = float(ge["e_int"].sum() + ge["e_sw"].sum() + e_gl.sum())
+    ms, walk_ms = _timed_walk(eng, run, steps, dev)
+    ge = _gate_results(eng, 0, glitch=True)
+    dyn = float(ge["e_int"].sum() + ge["e_sw"].sum() + ge["e_gl"].sum())
+    err = None
+    if opool is not None and wl is not None:
+        err = _oracle_errors(opool, dataclasses.replace(wl, clock_ps=clock_ps), cfg.bin_ps, wave, ge,
+                             ("e_leak", "e_int", "e_sw", "e_gl"))
     eng.set_glitch(0)
     return {"clock_ps": clock_ps, "ms_per_run": ms, "value": n_ev / (ms * 1e-3), "unit": UNIT, "walk_ms": walk_ms,
             "walk_over_plain": walk_ms / walk_plain_ms,
-            "glitch_share_of_dynamic_energy": float(e_gl.sum()) / dyn if dyn > 0 else 0.0,
-            "out_slew": "uniform 10-200 ps per gate and edge, seed 7"}
+            "glitch_share_of_dynamic_energy": float(ge["e_gl"].sum()) / dyn if dyn > 0 else 0.0,
+            "out_slew": "uniform 10-200 ps per gate and edge, seed 7", "oracle_error": err}
 
 
-def measure_components(eng, dev, cfg, walk_plain_ms, n_ev, steps):
+def measure_components(eng, dev, cfg, walk_plain_ms, n_ev, steps, opool=None, wl=None):
     """The same window (slot 0) with the per-component waveforms (leakage,
     internal, switching, glitch rows, on the device) as well as the total:
-    run time, and walk time against the plain walk."""
+    run time, walk time against the plain walk, and each row's error against
+    the oracle's component bins."""
     import torch
 
     from paper_2609_05960_gb300 import gtpower
@@ -593,31 +714,52 @@ def measure_components(eng, dev, cfg, walk_plain_ms, n_ev, steps):
     for _ in range(3):
         run()
     torch.cuda.synchronize(dev)
-    eng.set_param("timing", 1)
-    ms = _events_per_s(run, steps, dev)
-    n_t = max(eng.get_param("n_timed"), 1)
-    walk_ms = eng.get_param("t_walk_ns") * 1e-6 / n_t
-    eng.set_param("timing", 0)
+    ms, walk_ms = _timed_walk(eng, run, steps, dev)
     rel = float(((comp.sum(0) - total).abs() / total.abs()).max())
+    err = None
+    if opool is not None and wl is not None:
+        from oracle import fullsize
+        ref = opool.walk(wl, cfg.bin_ps, components=True)
+        c = comp.cpu().numpy()
+        err = {"total": fullsize.bin_errors(total.cpu().numpy(), ref["bins"], cfg.bin_ps)}
+        for i, name in enumerate(("leakage", "internal", "switching")):
+            err[name] = fullsize.bin_errors(c[i], ref["comp_bins"][i], cfg.bin_ps)
+        err["glitch_max_abs_w"] = float(np.abs(c[3]).max())
     return {"ms_per_run": ms, "value": n_ev / (ms * 1e-3), "unit": UNIT, "walk_ms": walk_ms,
-            "walk_over_plain": walk_ms / walk_plain_ms, "max_rel_sum_of_components_vs_total": rel}
+            "walk_over_plain": walk_ms / walk_plain_ms, "max_rel_sum_of_components_vs_total": rel,
+            "oracle_error": err}
 
 
-def measure_adjoint(eng, dev, steps, n_events=0):
+def adjoint_bytes(n_events, n_active, n_gates, n_bins):
+    """Bytes the adjoint walk must move: 8 per record; per gate with events
+    the cell id, load, 6 slews, CSR offset and initial state (41 B); the
+    per-bin gradient table read once (8 B a bin: dL/dE and its prefix G); dC
+    written (4 B a gate)."""
+    return 8 * n_events + 41 * n_active + 8 * n_bins + 4 * n_gates
+
+
+def measure_adjoint(eng, dev, steps, n_events=0, peak=None, opool=None, cfg_name="adjoint"):
     """500k gates, 100M events (or n_events), 5 us, 10 ps bins: the adjoint
     walk (gradients of sum P^2 + tau*LSE(P/tau)) against the forward walk on
-    the same window."""
+    the same window, both with their rooflines; the forward waveform and
+    per-gate results against the oracle in full, the load gradients of
+    sampled gates against the oracle's adjoint."""
+    import dataclasses
+
     import torch
 
+    import oracle
     import synth
     from paper_2609_05960_gb300 import gtpower, peak_loss
 
-    cfg = synth.CONFIGS["adjoint"]
+    cfg = synth.CONFIGS[cfg_name]
+    if n_events:
+        cfg = dataclasses.replace(cfg, n_events=n_events)
     lib = synth.make_library(cfg.seed_lib)
     net = synth.make_netlist(lib, cfg.n_gates, cfg.seed_net)
     eng.load_library(lib)
     eng.load_netlist(net)
-    counts = synth.zipf_counts(cfg.n_gates, n_events or cfg.n_events, cfg.zipf_s, cfg.cap, cfg.seed_ev)
+    counts = synth.zipf_counts(cfg.n_gates, cfg.n_events, cfg.zipf_s, cfg.cap, cfg.seed_ev)
     tr, rec = synth.make_trace_gpu(net, counts, cfg.window_ps, cfg.seed_ev, device=dev)
     off = torch.from_numpy(tr.offsets).to(dev)
     init = torch.from_numpy(tr.init_state).to(dev)
@@ -630,12 +772,120 @@ def measure_adjoint(eng, dev, steps, n_events=0):
     g = P.grad.to(torch.float32).contiguous()
     kw = dict(dtype=torch.float32, device=dev)
     dC, de, dl = torch.empty(cfg.n_gates, **kw), torch.empty(lib.n_cells, **kw), torch.empty(lib.n_cells, **kw)
-    ms_f = _events_per_s(lambda: gtpower.gtp_run_power(eng.ctx, 0, cfg.bin_ps, wave), steps, dev)
-    ms_b = _events_per_s(lambda: gtpower.gtp_run_power_backward(eng.ctx, 0, cfg.bin_ps, g, dC, de, dl), steps, dev)
+    ms_f, walk_f = _timed_walk(eng, lambda: gtpower.gtp_run_power(eng.ctx, 0, cfg.bin_ps, wave), steps, dev)
+    ms_b, walk_b = _timed_walk(eng, lambda: gtpower.gtp_run_power_backward(eng.ctx, 0, cfg.bin_ps, g, dC, de, dl),
+                               steps, dev)
     n = tr.n_events
-    return {"workload": workload_desc(cfg, nb, n), "events": n, "ms_per_backward": ms_b, "value": n / (ms_b * 1e-3),
-            "unit": UNIT, "forward_ms": ms_f, "forward_value": n / (ms_f * 1e-3), "backward_over_forward": ms_b / ms_f,
-            "loss": "sum P^2 + tau*logsumexp(P/tau), P in mW, tau = 0.01*mean(P)"}
+    act = int((counts > 0).sum())
+    out = {"workload": workload_desc(cfg, nb, n), "events": n, "ms_per_backward": ms_b, "value": n / (ms_b * 1e-3),
+           "unit": UNIT, "forward_ms": ms_f, "forward_value": n / (ms_f * 1e-3), "backward_over_forward": ms_b / ms_f,
+           "walk_backward_ms": walk_b, "walk_forward_ms": walk_f, "walk_backward_over_forward": walk_b / walk_f,
+           "loss": "sum P^2 + tau*logsumexp(P/tau), P in mW, tau = 0.01*mean(P)"}
+    if peak:
+        out["roofline_backward"] = roofline(adjoint_bytes(n, act, cfg.n_gates, nb), walk_b, peak)
+        out["roofline_forward"] = roofline(algorithmic_bytes(n, act, cfg.n_gates, nb), walk_f, peak)
+    if opool is not None:
+        from oracle import fullsize
+        out["oracle_error_forward"] = _oracle_errors(opool, fullsize.Workload.of(cfg), cfg.bin_ps, wave,
+                                                     _gate_results(eng, 0))
+        rng = np.random.default_rng(0)
+        gates = np.unique(np.concatenate([np.argsort(-counts, kind="stable")[:8],
+                                          rng.choice(cfg.n_gates, 400, replace=False)]))
+        off_s, rec_s = synth.gate_records(net, tr, gates)
+        sub_net = synth.Netlist(net.cell[gates], net.load_ff[gates], np.ascontiguousarray(net.slew_ps[gates]),
+                                net.n_pins[gates], net.level[gates], net.fanin[gates])
+        sub_tr = synth.Trace(tr.window_ps, off_s, rec_s, tr.init_state[gates], tr.seed, tr.tie24)
+        rC, _, _ = oracle.adjoint(lib, sub_net, sub_tr, cfg.bin_ps, g.cpu().numpy().astype(np.float64))
+        got = dC.cpu().numpy()[gates]
+        scale = float(np.abs(rC).max())
+        out["oracle_error_dC"] = {"gates": int(len(gates)),
+                                  "max_abs_err_over_max": float(np.abs(got - rC).max() / scale) if scale else 0.0,
+                                  "bar": "|dC - oracle| <= 1e-4 |oracle| + 1e-5 max|oracle|",
+                                  "within_bar": bool(np.all(np.abs(got - rC) <= 1e-4 * np.abs(rC) + 1e-5 * scale))}
+    del rec, off, init
+    return out
+
+
+def measure_stress(eng, dev, steps, peak, opool=None):
+    """The stress workload (10M gates, 2B events, 16 GB of records, Zipf 1.5,
+    100 us in 10M bins of 10 ps) in its three forms on one GPU: the plain
+    run, the batched run of four windows of 500M events each, and the adjoint
+    (gradients of sum P^2 + tau*LSE(P/tau)); each with events/s, its walk's
+    roofline and its error against the oracle over every bin and gate."""
+    import dataclasses
+
+    import torch
+
+    import synth
+    from paper_2609_05960_gb300 import gtpower, peak_loss
+
+    cfg = synth.CONFIGS["stress"]
+    lib = synth.make_library(cfg.seed_lib)
+    net = synth.make_netlist(lib, cfg.n_gates, cfg.seed_net)
+    eng.load_library(lib)
+    eng.load_netlist(net)
+    for k in ("records_per_thread", "ctas_per_sm", "dense_min"):
+        eng.set_param(k, -1)
+    nb = cfg.window_ps // cfg.bin_ps
+    counts = synth.zipf_counts(cfg.n_gates, cfg.n_events, cfg.zipf_s, cfg.cap, cfg.seed_ev)
+    tr, rec = synth.make_trace_gpu(net, counts, cfg.window_ps, cfg.seed_ev, device=dev)
+    off = torch.from_numpy(tr.offsets).to(dev)
+    init = torch.from_numpy(tr.init_state).to(dev)
+    eng.load_events(0, window_ps=cfg.window_ps, offsets=off, records=rec, init_state=init, borrow=True)
+    wave = torch.empty(nb, dtype=torch.float64, device=dev)
+    run = lambda: gtpower.gtp_run_power(eng.ctx, 0, cfg.bin_ps, wave, graph=True)
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize(dev)
+    ms, walk = _timed_walk(eng, run, steps, dev)
+    n = tr.n_events
+    act = int((counts > 0).sum())
+    plain = {"workload": workload_desc(cfg, nb, n), "events": n, "ms_per_run": ms, "value": n / (ms * 1e-3),
+             "unit": UNIT, "roofline": roofline(algorithmic_bytes(n, act, cfg.n_gates, nb), walk, peak)}
+    from oracle import fullsize
+    if opool is not None:
+        plain["oracle_error"] = _oracle_errors(opool, fullsize.Workload.of(cfg), cfg.bin_ps, wave,
+                                               _gate_results(eng, 0))
+    # adjoint form on the same window
+    P = wave.clone().requires_grad_(True)
+    peak_loss(P).backward()
+    g = P.grad.to(torch.float32).contiguous()
+    kw = dict(dtype=torch.float32, device=dev)
+    dC, de, dl = torch.empty(cfg.n_gates, **kw), torch.empty(lib.n_cells, **kw), torch.empty(lib.n_cells, **kw)
+    ms_b, walk_b = _timed_walk(eng, lambda: gtpower.gtp_run_power_backward(eng.ctx, 0, cfg.bin_ps, g, dC, de, dl),
+                               steps, dev)
+    adj = {"events": n, "ms_per_backward": ms_b, "value": n / (ms_b * 1e-3), "unit": UNIT,
+           "backward_over_forward": ms_b / ms, "walk_backward_over_forward": walk_b / walk,
+           "roofline": roofline(adjoint_bytes(n, act, cfg.n_gates, nb), walk_b, peak)}
+    del rec, off, init, P, g, dC
+    torch.cuda.empty_cache()
+    # batched form: four windows of 500M events
+    keep, wls, alg, total = [], [], 0, 0
+    for w in range(4):
+        c4 = dataclasses.replace(cfg, n_events=cfg.n_events // 4, seed_ev=cfg.seed_ev + 10 * (w + 1))
+        cnt = synth.zipf_counts(c4.n_gates, c4.n_events, c4.zipf_s, c4.cap, c4.seed_ev)
+        t4, r4 = synth.make_trace_gpu(net, cnt, c4.window_ps, c4.seed_ev, device=dev)
+        o4 = torch.from_numpy(t4.offsets).to(dev)
+        i4 = torch.from_numpy(t4.init_state).to(dev)
+        eng.load_events(w, window_ps=c4.window_ps, offsets=o4, records=r4, init_state=i4, borrow=True)
+        keep.append((r4, o4, i4))
+        wls.append(fullsize.Workload.of(c4))
+        alg += algorithmic_bytes(t4.n_events, int((cnt > 0).sum()), c4.n_gates, nb)
+        total += t4.n_events
+    outs = [torch.empty(nb, dtype=torch.float64, device=dev) for _ in range(4)]
+    runb = lambda: gtpower.gtp_run_power_batched(eng.ctx, [0, 1, 2, 3], cfg.bin_ps, outs, graph=True)
+    runb()
+    ms4, walk4 = _timed_walk(eng, runb, steps, dev)
+    bat = {"windows": 4, "events": total, "ms_per_run": ms4, "value": total / (ms4 * 1e-3), "unit": UNIT,
+           "roofline": roofline(alg, walk4, peak), "vs_plain": (total / ms4) / (n / ms)}
+    if opool is not None:
+        errs = [_oracle_errors(opool, wls[w], cfg.bin_ps, outs[w], _gate_results(eng, w)) for w in range(4)]
+        bat["oracle_error"] = {k: max(e[k] for e in errs) for k in errs[0] if k.startswith("max_rel")
+                               or k.endswith("mismatches")}
+        bat["oracle_error"]["bins"] = sum(e["bins"] for e in errs)
+    del keep, outs
+    torch.cuda.empty_cache()
+    return {"plain": plain, "adjoint": adj, "batched": bat}
 
 
 def run_contention_sweep(args):

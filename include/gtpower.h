@@ -433,6 +433,12 @@ int gtp_measure_reductions(gtp_ctx* ctx, int32_t n_slots, int32_t width, int64_t
 /* Engine tuning knobs; value < 0 restores the default.  Keys:
  * "records_per_thread" (4, 8, 16; events per lane of a dense segment),
  * "ctas_per_sm" (0 = full occupancy), "dense_min" (gates with more events are cut into segments; 1..4096),
+ * "piece_len" (a gate with more events than this is walked as several
+ * work items of piece_len events, each starting from the state its earlier
+ * records leave, so that one very busy gate cannot hold up a run; -1 = chosen
+ * per run: at least 65,536 and about a sixth of an SM's even share of the
+ * run's events, the default; 0 = never; other values round up to a multiple
+ * of 4,096),
  * "tile_min" (single-window runs without glitch detection or component
  * waveforms: gates with at least this many events, and at most 3 inputs,
  * take the time-sliced walk, which keeps each 16,384-bin slice of the

@@ -63,18 +63,22 @@ def _build(wl: Workload):
     return lib, net, counts, trace, out_slew
 
 
-def _init(wl: Workload):
-    _STATE["wl"] = wl
-    _STATE["inputs"] = _build(wl)
+def _inputs(wl: Workload):
+    """The workload's inputs in this worker, built once (the last one kept)."""
+    cache = _STATE.setdefault("cache", {})
+    if wl not in cache:
+        while len(cache) >= 1:
+            cache.pop(next(iter(cache)))
+        cache[wl] = _build(wl)
+    return cache[wl]
 
 
 def _task(job):
-    """Gates [g0, g1) in sub-ranges of about `chunk` events."""
+    """Gates [g0, g1) of a workload, in sub-ranges of about `chunk` events."""
     import oracle
     import synth
-    g0, g1, bin_ps, chunk, escale, lscale, components = job
-    wl = _STATE["wl"]
-    lib, net, counts, trace, out_slew = _STATE["inputs"]
+    wl, g0, g1, bin_ps, chunk, escale, lscale, components = job
+    lib, net, counts, trace, out_slew = _inputs(wl)
     n_bins = wl.window_ps // bin_ps
     bins = np.zeros(n_bins, np.float64)
     comp = np.zeros((4, n_bins), np.float64) if components else None
@@ -105,28 +109,25 @@ def _task(job):
 
 
 def walk(wl: Workload, bin_ps: int, n_proc: Optional[int] = None, escale=None, lscale=None,
-         components: bool = False, pool=None) -> dict:
+         components: bool = False) -> dict:
     """The oracle's full result for a workload: ``bins`` (fJ, every bin),
     the per-gate outputs of every gate, and ``comp_bins`` with components.
     Runs on n_proc spawned processes (default: every host core)."""
-    if pool is not None:
-        return pool.walk(bin_ps, escale=escale, lscale=lscale, components=components)
-    with Pool(wl, n_proc) as p:
-        return p.walk(bin_ps, escale=escale, lscale=lscale, components=components)
+    with Pool(n_proc) as p:
+        return p.walk(wl, bin_ps, escale=escale, lscale=lscale, components=components)
 
 
 class Pool:
-    """Spawned worker processes holding one workload's inputs, for several
-    walks of it (different bin sizes or scales)."""
+    """Spawned worker processes that walk workloads for the parent; each
+    worker builds a workload's inputs from its seeds the first time it sees
+    it.  Start it before the parent uses the GPU, or use it from a process
+    that never does: the workers are spawned, not forked."""
 
-    def __init__(self, wl: Workload, n_proc: Optional[int] = None):
+    def __init__(self, n_proc: Optional[int] = None):
         import oracle
         oracle.build()  # once here, not concurrently in the workers
-        self.wl = wl
         self.n = max(1, n_proc or os.cpu_count() or 1)
-        self.pool = mp.get_context("spawn").Pool(self.n, initializer=_init, initargs=(wl,))
-        import synth
-        self.counts = synth.zipf_counts(wl.n_gates, wl.n_events, wl.zipf_s, wl.cap, wl.seed_ev)
+        self.pool = mp.get_context("spawn").Pool(self.n)
 
     def __enter__(self):
         return self
@@ -140,18 +141,19 @@ class Pool:
             self.pool.join()
             self.pool = None
 
-    def walk(self, bin_ps: int, escale=None, lscale=None, components: bool = False) -> dict:
-        wl = self.wl
+    def walk(self, wl: Workload, bin_ps: int, escale=None, lscale=None, components: bool = False) -> dict:
+        import synth
+        counts = synth.zipf_counts(wl.n_gates, wl.n_events, wl.zipf_s, wl.cap, wl.seed_ev)
         n_bins = wl.window_ps // bin_ps
         # about 4 tasks a process, split by events plus a gate's fixed cost
         n_tasks = 4 * self.n
-        weight = np.cumsum(self.counts + 8)
+        weight = np.cumsum(counts + 8)
         cuts = np.searchsorted(weight, np.linspace(0, weight[-1], n_tasks + 1)[1:-1])
         edges = np.unique(np.concatenate([[0], cuts, [wl.n_gates]]))
         chunk = max(4_000_000, 2 * n_bins)
         es = None if escale is None else np.asarray(escale, np.float64)
         ls = None if lscale is None else np.asarray(lscale, np.float64)
-        jobs = [(int(a), int(b), int(bin_ps), chunk, es, ls, components) for a, b in zip(edges[:-1], edges[1:])]
+        jobs = [(wl, int(a), int(b), int(bin_ps), chunk, es, ls, components) for a, b in zip(edges[:-1], edges[1:])]
         out = {k: np.zeros(wl.n_gates, np.float64) for k in ("e_leak", "e_int", "e_sw", "e_gl")}
         out["n_events"] = np.zeros(wl.n_gates, np.int64)
         out["final_state"] = np.zeros(wl.n_gates, np.uint8)
@@ -180,3 +182,16 @@ def bin_errors(got_w: np.ndarray, ref_bins_fj: np.ndarray, bin_ps: int) -> dict:
     return {"max_rel_bin_err": float(rel.max()) if rel.size else 0.0,
             "mean_rel_bin_err": float(rel.mean()) if rel.size else 0.0,
             "worst_bin": int(rel.argmax()) if rel.size else -1, "bins": int(rel.size)}
+
+
+def gate_errors(got: dict, ref: dict, keys=("e_leak", "e_int", "e_sw")) -> dict:
+    """Per-gate results against the oracle's: mismatched event counts and
+    final states (must be 0), and the largest relative error of each energy
+    (1e-9 fJ absolute floor for exact zeros)."""
+    out = {"count_mismatches": int(np.sum(np.asarray(got["n_events"]) != ref["n_events"])),
+           "state_mismatches": int(np.sum(np.asarray(got["final_state"]) != ref["final_state"]))}
+    for k in keys:
+        g = np.asarray(got[k], np.float64)
+        err = np.abs(g - ref[k]) / np.maximum(np.abs(ref[k]), 1e-9 / 1e-5)
+        out[f"max_rel_{k}_err"] = float(err.max()) if err.size else 0.0
+    return out

@@ -77,13 +77,14 @@ struct Window {
 struct GraphKey {
   std::vector<int32_t> windows;
   int32_t bin_ps;
-  int64_t rpt, ctas, kernel, dmin, tmin, plan_gen;
+  int64_t rpt, ctas, kernel, dmin, tmin, piece, plan_gen;
   int64_t n_tiles;  // launch sizes baked into the graph
   bool any_events;  // whether the walk was captured
   bool timing;      // whether phase events were captured
   bool operator<(const GraphKey& o) const {
-    return std::tie(windows, bin_ps, rpt, ctas, kernel, dmin, tmin, plan_gen, n_tiles, any_events, timing) <
-           std::tie(o.windows, o.bin_ps, o.rpt, o.ctas, o.kernel, o.dmin, o.tmin, o.plan_gen, o.n_tiles, o.any_events,
+    return std::tie(windows, bin_ps, rpt, ctas, kernel, dmin, tmin, piece, plan_gen, n_tiles, any_events, timing) <
+           std::tie(o.windows, o.bin_ps, o.rpt, o.ctas, o.kernel, o.dmin, o.tmin, o.piece, o.plan_gen, o.n_tiles,
+                    o.any_events,
                     o.timing);
   }
 };
@@ -143,6 +144,8 @@ struct gtp_ctx {
   int64_t p_ctas_per_sm = 0;
   int64_t p_dense_min = 256;
   int64_t p_tile_min = 0;  // gates with this many events or more take the time-sliced walk (0: none)
+  int64_t p_piece_len = -1;   // gates with more events are split into pieces (0: never, -1: chosen per run)
+  int64_t run_piece_len = 0;  // the piece length of the run being planned
   // phase timing (CUDA events on the context stream) and launch counting
   bool timing = false;
   cudaEvent_t ev[10] = {};
@@ -332,9 +335,19 @@ int build_plan(gtp_ctx* ctx, const std::vector<Window*>& ws, int32_t bin_ps, con
     tb += nt;
   }
   ht[n] = tb;
-  if ((int64_t)n * G > ctx->gcap) {
-    CU(ctx->glist.reserve(sizeof(int2) * (size_t)n * G), "alloc work list");
-    ctx->gcap = (int64_t)n * G;
+  // pieces: a gate with more than piece_len events is walked as several big items, so that no single gate
+  // of a skewed trace walks longer than about a sixth of an SM's even share of the run
+  int64_t e_total = 0;
+  for (Window* w : ws) e_total += w->n_events;
+  int64_t pl = ctx->p_piece_len;
+  if (pl < 0) pl = std::max<int64_t>(65536, e_total / (6 * std::max(ctx->n_sm, 1)));
+  if (pl > 0) pl = (pl + kPieceUnit - 1) / kPieceUnit * kPieceUnit;
+  if (pl > 0 && e_total / pl >= (int64_t)1 << 20) pl = (e_total >> 20) / kPieceUnit * kPieceUnit + kPieceUnit;
+  ctx->run_piece_len = pl;
+  const int64_t cap = (int64_t)n * G + (pl > 0 ? e_total / pl + n : 0);
+  if (cap > ctx->gcap) {
+    CU(ctx->glist.reserve(sizeof(int2) * (size_t)cap), "alloc work list");
+    ctx->gcap = cap;
     ++ctx->plan_gen;
   }
   if (!ctx->counters.p) {
@@ -371,6 +384,7 @@ WalkArgs walk_args(gtp_ctx* ctx, int n) {
   A.n_gates = ctx->N.n_gates;
   A.tile_min = 0;
   A.chunks = ctx->chunks.as<int32_t>();
+  A.piece_len = ctx->run_piece_len;
   return A;
 }
 
@@ -558,7 +572,8 @@ int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, dou
   CU(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(DevError), ctx->stream), "zero status");
   if (use_graph) {
     const GraphKey key{std::vector<int32_t>(windows, windows + n), bin_ps, ctx->p_rpt,
-                       ctx->p_ctas_per_sm, ctx->p_kernel, ctx->p_dense_min, ctx->p_tile_min, ctx->plan_gen,
+                       ctx->p_ctas_per_sm, ctx->p_kernel, ctx->p_dense_min, ctx->p_tile_min, ctx->run_piece_len,
+                       ctx->plan_gen,
                        n_tiles_total, any_events, ctx->timing};
     auto it = ctx->graphs.find(key);
     if (it == ctx->graphs.end()) {
@@ -1425,21 +1440,34 @@ int gtp_run_power_backward(gtp_ctx* ctx, int32_t window, int32_t bin_ps, const f
   RC(upload_plan(ctx, 1, st));
   CU(cudaMemsetAsync(dc, 0, sizeof(float) * G, st), "zero dC");
   CU(cudaMemsetAsync(ctx->cell_acc.p, 0, sizeof(double) * 2 * ctx->L.n_cells, st), "zero cell sums");
+  // phases as in a forward run: gradient prefix and gate pass, plan, walk, cell outputs
+  mark(ctx, 0, st);
   CU(launch_grad_prep(plan_wins(ctx->plan.p), dL_dP, ctx->grad.as<float2>(), ctx->gtiles.as<double>(), nt, (int)nb,
                       bin_ps, &plan_wins(ctx->plan.p)[0].g_total, st), "gradient prefix");
   CU(launch_gate_pass_bwd(ctx->L, ctx->N, plan_wins(ctx->plan.p), ctx->cell_acc.as<double>(), st), "gate pass");
+  mark(ctx, 1, st);
   ctx->launches += 4;
+  mark(ctx, 2, st);
+  const WalkArgs A = walk_args(ctx, 1);
+  if (W->n_events > 0) CU(launch_plan(ctx->N, ctx->L, A, st), "plan");
+  mark(ctx, 3, st);
+  mark(ctx, 4, st);
+  mark(ctx, 8, st);
+  mark(ctx, 9, st);
   if (W->n_events > 0) {
-    const WalkArgs A = walk_args(ctx, 1);
-    CU(launch_plan(ctx->N, ctx->L, A, st), "plan");
     CU(launch_walk(ctx->L, ctx->N, A, true, st), "adjoint walk");
     ctx->launches += 4;
   }
+  mark(ctx, 5, st);
+  mark(ctx, 6, st);
   if (d_escale || d_lscale) {
     CU(launch_cells_out(ctx->cell_acc.as<double>(), ctx->L.n_cells, d_escale, d_lscale, st), "cell gradients");
     ctx->launches += 1;
   }
-  return check_walk_error(ctx, W->n_events > 0 ? 1 : 0, &window, "run_power_backward");
+  mark(ctx, 7, st);
+  const int rc = check_walk_error(ctx, W->n_events > 0 ? 1 : 0, &window, "run_power_backward");
+  collect_timing(ctx);
+  return rc;
 }
 
 int gtp_autotune(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_t bin_ps, int32_t iters,
@@ -1540,6 +1568,8 @@ int gtp_set_param(gtp_ctx* ctx, const char* key, int64_t value) {
   } else if (k == "dense_min") {
     if (value == 0 || value > 4096) return fail(ctx, GTP_ERANGE, "dense_min must be 1..4096");
     ctx->p_dense_min = value < 0 ? 256 : value;
+  } else if (k == "piece_len") {
+    ctx->p_piece_len = value < 0 ? -1 : value;
   } else if (k == "tile_min") {
     if (value > (1ll << 31)) return fail(ctx, GTP_ERANGE, "tile_min must be 0..2^31");
     ctx->p_tile_min = value < 0 ? 0 : value;
@@ -1575,6 +1605,8 @@ int64_t gtp_get_param(const gtp_ctx* ctx, const char* key) {
   if (k == "ctas_per_sm") return ctx->p_ctas_per_sm;
   if (k == "dense_min") return ctx->p_dense_min;
   if (k == "tile_min") return ctx->p_tile_min;
+  if (k == "piece_len") return ctx->p_piece_len;
+  if (k == "run_piece_len") return ctx->run_piece_len;
   if (k == "t_tiled_ns") return ctx->t_ns[4];
   if (k == "scheme_evt_tgt") return ctx->p_evt_tgt;
   if (k == "scheme_thr_floor") return ctx->p_thr_floor;

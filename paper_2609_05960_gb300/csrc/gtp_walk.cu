@@ -19,10 +19,11 @@ constexpr int kSparseBase = kBigBuckets + kWarps;
 //   sparse (c <= dense_min):              40..40+dense_min-1 by decreasing c
 //   tiled  (see is_tiled; walked by the time-sliced walk, gtp_tiled.cu):
 //          the 32 buckets after the sparse ones, by decreasing floor(log2 c)
-__device__ __forceinline__ int work_bucket(int64_t c, int dmin, int64_t seg_len, bool tiled) {
+__device__ __forceinline__ int work_bucket(int64_t c, int dmin, int64_t seg_len, bool tiled, bool piece = false) {
   if (tiled) return kSparseBase + dmin + 31 - min(31, 63 - __clzll((unsigned long long)c));
+  if (piece || c > kWarps * seg_len)  // the pieces of a split gate are always big items
+    return kBigBuckets - 1 - min(kBigBuckets - 1, 63 - __clzll((unsigned long long)c));
   if (c <= dmin) return kSparseBase + dmin - (int)c;
-  if (c > kWarps * seg_len) return kBigBuckets - 1 - min(kBigBuckets - 1, 63 - __clzll((unsigned long long)c));
   return kSparseBase - (int)((c + seg_len - 1) / seg_len);
 }
 
@@ -106,7 +107,7 @@ __device__ void plan_bucket_starts(int nb, PlanBufs P) {
 template <bool GATE, bool PLAN>
 __global__ void __launch_bounds__(256) k_prepare(LibView L, NetView N, const WinDesc* __restrict__ wins,
                                                  DevError* err, int64_t seg_len, int dmin, PlanBufs P,
-                                                 int64_t tmin) {
+                                                 int64_t tmin, int64_t piece_len) {
   extern __shared__ unsigned int sh[];  // PLAN: [nb] bucket counts of this block
   __shared__ double red[32];
   __shared__ bool s_last;
@@ -142,7 +143,8 @@ __global__ void __launch_bounds__(256) k_prepare(LibView L, NetView N, const Win
       }
       const float Pl = L.leak[ci.leak_base + s0] * L.lscale[cell];
       p0 += (double)Pl;
-      if (!PLAN || c == 0 || tiled) {  // the tiled walk adds into its gates' sums
+      const bool split = PLAN && !tiled && gate_items(c, piece_len) > 1;
+      if (!PLAN || c == 0 || tiled || split) {  // the tiled walk and the pieces of a split gate add into its sums
         W.e_leak[g] = c == 0 ? (double)Pl * (double)W.window_ps * 1e-6 : 0.0;
         W.e_int[g] = 0.0;
         W.e_sw[g] = 0.0;
@@ -150,7 +152,10 @@ __global__ void __launch_bounds__(256) k_prepare(LibView L, NetView N, const Win
         W.final_state[g] = (uint8_t)s0;
       }
     }
-    if (PLAN && c > 0) atomicAdd(&sh[work_bucket(c, dmin, seg_len, tiled)], 1u);
+    if (PLAN && c > 0) {
+      const int64_t items = tiled ? 1 : gate_items(c, piece_len);
+      atomicAdd(&sh[work_bucket(items > 1 ? piece_len : c, dmin, seg_len, tiled, items > 1)], (unsigned int)items);
+    }
   }
   if (GATE) {
     for (int o = 16; o > 0; o >>= 1) p0 += __shfl_down_sync(0xffffffffu, p0, o);
@@ -184,7 +189,8 @@ __global__ void __launch_bounds__(256) k_prepare(LibView L, NetView N, const Win
 constexpr int kScatterPer = 8;
 
 __global__ void k_plan_scatter(const WinDesc* __restrict__ wins, int64_t seg_len, int dmin, PlanBufs P,
-                               const int32_t* __restrict__ gcell, const CellInfo* __restrict__ cells, int64_t tmin) {
+                               const int32_t* __restrict__ gcell, const CellInfo* __restrict__ cells, int64_t tmin,
+                               int64_t piece_len) {
   extern __shared__ unsigned long long sbase[];  // [0, nb): block bases; then [0, nb) local counts (32-bit)
   const int nb = n_buckets(dmin);
   unsigned int* sh = reinterpret_cast<unsigned int*>(sbase + nb);
@@ -196,14 +202,15 @@ __global__ void k_plan_scatter(const WinDesc* __restrict__ wins, int64_t seg_len
     for (int b = threadIdx.x; b < nb; b += blockDim.x) sh[b] = 0u;
     __syncthreads();
     int bk[kScatterPer];
-    unsigned int local[kScatterPer];
+    unsigned int local[kScatterPer], items[kScatterPer];
 #pragma unroll
     for (int j = 0; j < kScatterPer; ++j) {
       const int64_t g = base + (int64_t)j * blockDim.x + threadIdx.x;
       const int64_t c = g < W.g1 ? W.offsets[g + 1] - W.offsets[g] : 0;
       const bool tiled = c > 0 && is_tiled(c, tmin, (uint32_t)cells[gcell[g]].n_in);
-      bk[j] = c > 0 ? work_bucket(c, dmin, seg_len, tiled) : -1;
-      local[j] = bk[j] >= 0 ? atomicAdd(&sh[bk[j]], 1u) : 0u;
+      items[j] = (unsigned int)(tiled ? 1 : gate_items(c, piece_len));
+      bk[j] = c > 0 ? work_bucket(items[j] > 1 ? piece_len : c, dmin, seg_len, tiled, items[j] > 1) : -1;
+      local[j] = bk[j] >= 0 ? atomicAdd(&sh[bk[j]], items[j]) : 0u;
     }
     __syncthreads();
     for (int k = threadIdx.x; k < nb; k += blockDim.x)
@@ -212,8 +219,9 @@ __global__ void k_plan_scatter(const WinDesc* __restrict__ wins, int64_t seg_len
 #pragma unroll
     for (int j = 0; j < kScatterPer; ++j)
       if (bk[j] >= 0)
-        P.glist[(int64_t)sbase[bk[j]] + local[j]] =
-            make_int2((int)blockIdx.y, (int)(base + (int64_t)j * blockDim.x + threadIdx.x));
+        for (unsigned int p = 0; p < items[j]; ++p)  // a split gate: one entry per piece
+          P.glist[(int64_t)sbase[bk[j]] + local[j] + p] =
+              make_int2((int)(blockIdx.y | (p << kPieceShift)), (int)(base + (int64_t)j * blockDim.x + threadIdx.x));
     __syncthreads();
   }
 }
@@ -243,7 +251,7 @@ cudaError_t launch_prepare_plan(const LibView& L, const NetView& N, const WalkAr
   cudaError_t e = cudaMemsetAsync(A.plan.counters, 0, sizeof(unsigned long long) * plan_counter_slots(dmin), st);
   if (e != cudaSuccess) return e;
   k_prepare<GATE, true><<<prepare_grid(A), 256, sizeof(unsigned int) * (size_t)n_buckets(dmin), st>>>(
-      L, N, A.wins, A.err, 32ll * A.rpt, dmin, A.plan, GATE ? A.tile_min : 0);
+      L, N, A.wins, A.err, 32ll * A.rpt, dmin, A.plan, GATE ? A.tile_min : 0, A.piece_len);
   return cudaGetLastError();
 }
 
@@ -251,7 +259,8 @@ cudaError_t launch_prepare_plan(const LibView& L, const NetView& N, const WalkAr
 
 cudaError_t launch_prepare(const LibView& L, const NetView& N, const WalkArgs& A, bool plan, cudaStream_t st) {
   if (plan) return launch_prepare_plan<true>(L, N, A, st);
-  k_prepare<true, false><<<prepare_grid(A), 256, 0, st>>>(L, N, A.wins, A.err, 32ll * A.rpt, A.dense_min, A.plan, 0);
+  k_prepare<true, false><<<prepare_grid(A), 256, 0, st>>>(L, N, A.wins, A.err, 32ll * A.rpt, A.dense_min, A.plan, 0,
+                                                          0);
   return cudaGetLastError();
 }
 
@@ -263,7 +272,8 @@ cudaError_t launch_plan_scatter(const LibView& L, const NetView& N, const WalkAr
   if (e != cudaSuccess) return e;
   dim3 grid = prepare_grid(A);
   grid.x = (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid.x, (A.n_gates + 256 * kScatterPer - 1) / (256 * kScatterPer)));
-  k_plan_scatter<<<grid, 256, scatter_smem, st>>>(A.wins, 32ll * A.rpt, dmin, A.plan, N.cell, L.cells, A.tile_min);
+  k_plan_scatter<<<grid, 256, scatter_smem, st>>>(A.wins, 32ll * A.rpt, dmin, A.plan, N.cell, L.cells, A.tile_min,
+                                                  A.piece_len);
   return cudaGetLastError();
 }
 

@@ -62,7 +62,19 @@ struct WalkArgs {
   int64_t tile_min;         // single-window plain forward runs: gates with this many events or more go
                             // to the time-sliced walk (0: none)
   int32_t* chunks;          // tiled walk: chunk starts in the tiled list (capacity tile_chunk_cap(n_gates))
+  int64_t piece_len;        // gates with more events are split into pieces of this many (0: none); a
+                            // multiple of kPieceUnit
 };
+
+// Work-list entries are {window | piece << kPieceShift, gate}.
+constexpr int kPieceShift = 10;
+constexpr int kWindowMask = (1 << kPieceShift) - 1;
+// Pieces are multiples of the longest chunk a big gate is walked in (8 warps x 32 lanes x 16 records).
+constexpr int64_t kPieceUnit = 4096;
+// Work items of a gate with c events: its pieces, or 1.
+__host__ __device__ inline int64_t gate_items(int64_t c, int64_t piece_len) {
+  return (piece_len > 0 && c > piece_len) ? (c + piece_len - 1) / piece_len : 1;
+}
 
 bool walk_rpt_supported(int rpt);
 // Forward preparation in one launch over (window, gate): clear the windows'

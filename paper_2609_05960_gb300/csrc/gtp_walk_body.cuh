@@ -115,7 +115,9 @@ struct DenseSmem {
 struct DGate {
   const WinDesc* W;
   const uint2* rec;
-  int64_t g, ga, n;          // gate, first record, events
+  int64_t g, ga, n;          // gate, first record, events (of the piece, for a gate split into pieces)
+  int64_t gs, ge;            // the whole gate's records [gs, ge)
+  bool starts, ends, split;  // the piece starts / ends the gate; the gate is split into pieces
   const uint4* dsc;          // the gate's event descriptors
   const float* gleak;        // the cell's leakage entries (unscaled)
   uint32_t cell, n_in, pmask, inmask, init;
@@ -129,15 +131,29 @@ struct DGate {
   const float* oslew;
 };
 
+// A work-list entry {window | piece << kPieceShift, gate}: a gate of more
+// than piece_len events (piece_len > 0) is split into pieces of piece_len
+// events (a multiple of the longest chunk, so only a gate's last piece can
+// end in a partial segment), each its own big item.
 template <bool BWD, bool GL>
 __device__ __forceinline__ DGate dense_gate(const LibView& L, const NetView& N, const WinDesc* __restrict__ wins,
-                                            int2 wg) {
+                                            int2 wg, int64_t piece_len) {
   DGate d;
-  d.W = wins + wg.x;
+  d.W = wins + (wg.x & kWindowMask);
   d.rec = d.W->rec;
   d.g = wg.y;
-  d.ga = d.W->offsets[d.g];
-  d.n = d.W->offsets[d.g + 1] - d.ga;
+  d.gs = d.W->offsets[d.g];
+  d.ge = d.W->offsets[d.g + 1];
+  d.split = piece_len > 0 && d.ge - d.gs > piece_len;
+  if (d.split) {
+    d.ga = d.gs + (int64_t)((uint32_t)wg.x >> kPieceShift) * piece_len;
+    d.n = min(piece_len, d.ge - d.ga);
+  } else {
+    d.ga = d.gs;
+    d.n = d.ge - d.gs;
+  }
+  d.starts = d.ga == d.gs;
+  d.ends = d.ga + d.n == d.ge;
   d.cell = (uint32_t)N.cell[d.g];
   const CellInfo ci = L.cells[d.cell];
   d.n_in = (uint32_t)ci.n_in;
@@ -225,8 +241,8 @@ __device__ __forceinline__ void issue_segment(const DGate& d, int64_t s, uint2* 
       const uint32_t cm = 8u * ((((uint32_t)(2 * m)) & M) << 1);
       if (m * 32 + lane < n_rem) cp_async8(sb + 256u * m + (c0 ^ cm), src + m * 32);
     }
-    if (lane == 0 && s > 0) cp_async8(smem_addr(halo), d.rec + s0 - 1);
-    if (lane == 31 && s * SEG + SEG < d.n) cp_async8(smem_addr(halo + 1), d.rec + s0 + SEG);
+    if (lane == 0 && (s > 0 || !d.starts)) cp_async8(smem_addr(halo), d.rec + s0 - 1);
+    if (lane == 31 && (s * SEG + SEG < d.n || (!d.ends && n_rem == SEG))) cp_async8(smem_addr(halo + 1), d.rec + s0 + SEG);
   }
   cp_async_commit();
 }
@@ -255,13 +271,13 @@ __device__ __forceinline__ uint32_t seg_front(const DGate& d, int64_t s, const u
   q.n_rem = FULL ? SEG : (int)max((int64_t)0, min((int64_t)SEG, d.n - s * SEG));
   const int j0 = lane * K;
   q.nk = FULL ? K : max(0, min(K, q.n_rem - j0));
-  q.last_seg = s * SEG + SEG >= d.n;
-  q.fh = s == 0 && lane == 0;
+  q.last_seg = s * SEG + SEG >= d.n && d.ends;  // the segment ends the gate
+  q.fh = s == 0 && lane == 0 && d.starts;
   q.bad = false;
   q.ex = 0u;
   if (!FULL && q.n_rem == 0) return 0u;
-  const uint32_t seg_before = s > 0 ? halo[0].x : 0u;
-  const uint32_t seg_after = q.last_seg ? 0xFFFFFFFFu : halo[1].x;
+  const uint32_t seg_before = (s > 0 || !d.starts) ? halo[0].x : 0u;
+  const uint32_t seg_after = q.last_seg ? 0xFFFFFFFFu : halo[1].x;  // (a piece's end reads the next piece's first)
   const uint32_t t_prev_lane = buf[row_base<K>(max(lane - 1, 0)) ^ (uint32_t)(K - 1)].x;  // garbage where unused
   const uint32_t t_next_lane = buf[row_base<K>(min(lane + 1, 31))].x;
   q.t_before = lane == 0 ? seg_before : t_prev_lane;
@@ -555,19 +571,66 @@ struct GateAcc {
 };
 
 // Per-gate results from the gate's totals.
+// (The pieces of a split gate add their totals: its outputs start at zero.)
 template <bool BWD, bool GL>
 __device__ __forceinline__ void store_gate(const LibView& L, const DGate& d, const DenseSmem& sm, double a0,
                                            double a1, double a2, double a3) {
   if (BWD) {
-    d.W->dC[d.g] = (float)a0;
+    if (d.split) atomicAdd(d.W->dC + d.g, (float)a0);
+    else d.W->dC[d.g] = (float)a0;
     sm.wacc[d.cell] += a1;
     sm.wacc[L.n_cells + d.cell] += a2 * 1e-6;
+  } else if (d.split) {
+    atomicAdd(d.W->e_leak + d.g, a0 * 1e-6);
+    atomicAdd(d.W->e_int + d.g, a1);
+    atomicAdd(d.W->e_sw + d.g, a2);
+    if (GL) atomicAdd(d.W->e_gl + d.g, a3);
   } else {
     d.W->e_leak[d.g] = a0 * 1e-6;
     d.W->e_int[d.g] = a1;
     d.W->e_sw[d.g] = a2;
     if (GL) d.W->e_gl[d.g] = a3;
   }
+}
+
+// The transfer word entering a piece that does not start its gate: the
+// state after every earlier record and the state before the timestamp group
+// the piece starts in (these differ only if that group began in the earlier
+// piece).  Each pin's value is the value written by the last earlier event
+// on it (events carry their new value, Sec. 2.1); a pin without one keeps its
+// initial value.  The warp reads 32 earlier records at a time, newest in
+// lane 0.  With glitch detection, gcarry[p] receives the time + 1 of pin p's
+// last earlier event (0: none).
+template <bool GL>
+__device__ __forceinline__ uint32_t piece_entry(const DGate& d, const DenseSmem& sm, int lane) {
+  const uint32_t t0 = d.rec[d.ga].x;
+  uint32_t needS = d.pmask, needP = d.pmask, S = 0u, Sp = 0u, last = 0u;
+  for (int64_t i = d.ga; (needS | needP) && i > d.gs; i -= 32) {
+    const int64_t j = i - 1 - lane;
+    const bool ok = j >= d.gs;
+    const uint2 r = ok ? d.rec[j] : make_uint2(0xFFFFFFFFu, 0xFu);
+    const uint32_t pin = r.y & 0xFu, val = (r.y >> 4) & 1u;
+    for (uint32_t p = 0; p <= d.n_in; ++p) {
+      const uint32_t bit = 1u << p;
+      const unsigned bs = __ballot_sync(kFull, ok && pin == p);
+      const unsigned bp = __ballot_sync(kFull, ok && pin == p && r.x < t0);
+      if ((needS & bit) && bs) {
+        const int src = __ffs(bs) - 1;
+        S |= __shfl_sync(kFull, val, src) << p;
+        const uint32_t tl = __shfl_sync(kFull, r.x, src);
+        if (GL && lane == (int)p) last = tl + 1u;
+        needS &= ~bit;
+      }
+      if ((needP & bit) && bp) {
+        Sp |= __shfl_sync(kFull, val, __ffs(bp) - 1) << p;
+        needP &= ~bit;
+      }
+    }
+  }
+  S |= d.init & needS;
+  Sp |= d.init & needP;
+  if (GL && lane <= (int)d.n_in) sm.gcarry[lane] = last;
+  return kXAbs | kXH | S | (Sp << 8);
 }
 
 // A medium gate, walked by one warp segment by segment.
@@ -581,6 +644,10 @@ __device__ __forceinline__ void medium_gate(const LibView& L, const DGate& d, co
   if (TAB || GL) build_tables<BWD, TAB, GL>(L, d, sm, lane);
   if (GL && lane <= (int)d.n_in) sm.gcarry[lane] = 0u;
   uint32_t carry = kXAbs | kXH | d.init | (d.init << 8);
+  if (!d.starts) {  // a later piece of a split gate (pieces are big items; kept correct here too)
+    __syncwarp();
+    carry = piece_entry<GL>(d, sm, lane);
+  }
   GateAcc<K> acc;
   Seg q;
   for (int64_t s = 0; s < nseg; ++s) {
@@ -625,6 +692,10 @@ __device__ __forceinline__ void big_gate(const LibView& L, const DGate& d, const
   if (TAB || GL) build_tables<BWD, TAB, GL>(L, d, sm, lane);
   if (GL && lane <= (int)d.n_in) sm.gcarry[lane] = 0u;
   uint32_t carry = kXAbs | kXH | d.init | (d.init << 8);
+  if (!d.starts) {  // a later piece of a split gate: every warp reads the state it starts from
+    __syncwarp();
+    carry = piece_entry<GL>(d, sm, lane);
+  }
   GateAcc<K> acc;
   Seg q;
   for (int64_t c = 0; c < nchunk; ++c) {
@@ -1027,13 +1098,13 @@ __global__ void __launch_bounds__(kWalkThreads, (BWD || GL || K == 16) ? 2 : 3)
     const bool is_dense = (pos + 1) * n_dense_items / n_items > dense_before;
     const int64_t item = is_dense ? dense_before : n_dense_items + (pos - dense_before);
     if (item < n_big) {
-      const DGate d = dense_gate<BWD, GL>(L, N, wins, P.glist[item]);
+      const DGate d = dense_gate<BWD, GL>(L, N, wins, P.glist[item], A.piece_len);
       if (d.n_in <= (uint32_t)kTabMaxIn) big_gate<K, BWD, true, GL, CMP>(L, d, sm, err, xfer, gx, red, wib, lane);
       else big_gate<K, BWD, false, GL, CMP>(L, d, sm, err, xfer, gx, red, wib, lane);
     } else if (item < n_dense_items) {
       const int64_t i = (item - n_big) * kWarps + wib;
       if (i < n_med) {
-        const DGate d = dense_gate<BWD, GL>(L, N, wins, P.glist[n_big + i]);
+        const DGate d = dense_gate<BWD, GL>(L, N, wins, P.glist[n_big + i], A.piece_len);
         if (d.n_in <= (uint32_t)kTabMaxIn) medium_gate<K, BWD, true, GL, CMP>(L, d, sm, err, lane);
         else medium_gate<K, BWD, false, GL, CMP>(L, d, sm, err, lane);
       }
@@ -1045,7 +1116,7 @@ __global__ void __launch_bounds__(kWalkThreads, (BWD || GL || K == 16) ? 2 : 3)
       const int64_t i = (item - n_dense_items) * kWalkThreads + threadIdx.x;
       if (i < n_sparse) {
         const int2 wg = P.glist[n_big + n_med + i];
-        const WinDesc& W = wins[wg.x];
+        const WinDesc& W = wins[wg.x & kWindowMask];
         const int64_t g = wg.y;
         const int64_t ga = W.offsets[g], ge = W.offsets[g + 1];
         float* my_tab = stab + threadIdx.x;

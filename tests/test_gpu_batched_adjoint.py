@@ -22,7 +22,7 @@ def engine():
 
 
 def _reset(engine):
-    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm", "tile_min"):
+    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm", "tile_min", "piece_len"):
         engine.set_param(k, -1)
 
 

@@ -1,8 +1,11 @@
 """Full-size workloads on the GPU, in the launch configuration the benchmark
-times.  The oracle checks sampled outputs one by one (per-gate results of
-random, hot and empty gates; sampled waveform bins where the host can hold
-the trace), and invariants that hold at any size are checked on everything:
-sum over bins = sum over gates, and merging pairs of fine bins = coarse bins.
+times, against the FP64 oracle on every bin and every gate.  The oracle runs
+over the whole workload on every host core (oracle/fullsize.py: gate ranges
+in spawned processes, each regenerating its gates' records from the seeds,
+with the range-mode leakage split), so every waveform bin is compared within
+1e-5 relative and every gate's count and final state bit-exactly, its
+energies within 1e-5.  Invariants that hold at any size are checked too: sum
+over bins = sum over gates, and merging pairs of fine bins = coarse bins.
 
 Workloads (synthetic, seeded; see synth.CONFIGS):
   large    1M gates, 200M events, Zipf 1.2 cap 1e5, 10 us, 10 ps bins
@@ -17,10 +20,34 @@ import pytest
 
 import oracle
 import synth
+from oracle import fullsize
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def opool():
+    p = fullsize.Pool()
+    yield p
+    p.close()
+
+
+def _full_check(wave, ge, ref, bin_ps, e_gl=None):
+    """Every bin within TOL relative; every gate's count and final state
+    exact and energies within TOL (1e-9 fJ floor)."""
+    err = fullsize.bin_errors(wave.cpu().numpy() if hasattr(wave, "cpu") else wave, ref["bins"], bin_ps)
+    assert err["max_rel_bin_err"] <= TOL, err
+    got = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in ge.items()}
+    if e_gl is not None:
+        got["e_gl"] = e_gl.cpu().numpy() if hasattr(e_gl, "cpu") else e_gl
+    ge_err = fullsize.gate_errors(got, ref, ("e_leak", "e_int", "e_sw") + (("e_gl",) if e_gl is not None else ()))
+    assert ge_err["count_mismatches"] == 0 and ge_err["state_mismatches"] == 0, ge_err
+    for k, v in ge_err.items():
+        if k.startswith("max_rel"):
+            assert v <= TOL, ge_err
+    return err
 
 
 @pytest.fixture(scope="module")
@@ -73,11 +100,11 @@ def _totals_agree(wave, ge, bin_ps):
 
 
 def _defaults(engine):
-    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm", "tile_min"):
+    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm", "tile_min", "piece_len"):
         engine.set_param(k, -1)
 
 
-def test_large_full_size(engine):
+def test_large_full_size(engine, opool):
     cfg = synth.CONFIGS["large"]
     lib = synth.make_library(cfg.seed_lib)
     net = synth.make_netlist(lib, cfg.n_gates, cfg.seed_net)
@@ -87,36 +114,29 @@ def test_large_full_size(engine):
     _defaults(engine)
     tr, rec, off, init = _gpu_trace(engine, net, cfg, counts)
     engine.load_events(0, window_ps=cfg.window_ps, offsets=off, records=rec, init_state=init, borrow=True)
-    wave = engine.run_power(0, cfg.bin_ps)
+    wave = engine.run_power(0, cfg.bin_ps, graph=False)
     ge = engine.gate_energy(0, device=True)
-    gates = _sample_gates(counts)
-    _, _, ref = _oracle_gates(lib, net, tr, gates, cfg.bin_ps)
-    _check_gates(ge, ref, gates)
+    # the GPU generator writes the host generator's bits
+    host = synth.gate_records(net, tr, np.arange(4))[1]
+    assert np.array_equal(host, rec[:len(host)].cpu().numpy().view(np.uint32))
+    ref = opool.walk(fullsize.Workload.of(cfg), cfg.bin_ps)
+    _full_check(wave, ge, ref, cfg.bin_ps)
     _totals_agree(wave, ge, cfg.bin_ps)
-    # sampled bins against the oracle over the whole trace (host copy of the records)
-    host = synth.make_trace(net, counts, cfg.window_ps, cfg.seed_ev, cfg.tie_p)
-    assert np.array_equal(host.records[:1000], rec[:1000].cpu().numpy().view(np.uint32))
-    sample = np.unique(np.concatenate([[0, 1, cfg.window_ps // cfg.bin_ps - 1],
-                                       np.random.default_rng(1).integers(0, cfg.window_ps // cfg.bin_ps, 40)]))
-    rb = oracle.walk(lib, net, host, cfg.bin_ps, sample_bins=sample)
-    want = oracle.waveform_w(rb["bins"], cfg.bin_ps)
-    got = wave.cpu().numpy()[sample]
-    assert (np.abs(got - want) / want).max() <= TOL
-    del host
     # coarse bins = merged fine bins
     wave2 = engine.run_power(0, 2 * cfg.bin_ps)
     np.testing.assert_allclose(wave.view(-1, 2).mean(1).cpu().numpy(), wave2.cpu().numpy(), rtol=TOL)
 
 
-def test_large_full_size_with_glitches(engine):
-    """Large with clock-cycle glitch detection at a 1 GHz clock: sampled
-    gates (including the hot ones, with ~10 events per cycle) against the
-    oracle, and the totals over bins and gates, glitch energy included."""
+def test_large_full_size_with_glitches(engine, opool):
+    """Large with clock-cycle glitch detection at a 1 GHz clock: every bin and
+    every gate (glitch energy included) against the oracle, and the totals
+    over bins and gates."""
     cfg = synth.CONFIGS["large"]
     lib = synth.make_library(cfg.seed_lib)
     net = synth.make_netlist(lib, cfg.n_gates, cfg.seed_net)
     counts = synth.zipf_counts(cfg.n_gates, cfg.n_events, cfg.zipf_s, cfg.cap, cfg.seed_ev)
-    out_slew = np.random.default_rng(7).uniform(10.0, 200.0, (cfg.n_gates, 2)).astype(np.float32)
+    wl = fullsize.Workload.of(cfg, clock_ps=1000)
+    out_slew = np.random.default_rng(wl.out_slew_seed).uniform(*wl.out_slew_range, (cfg.n_gates, 2)).astype(np.float32)
     engine.load_library(lib)
     engine.load_netlist(net)
     _defaults(engine)
@@ -126,24 +146,16 @@ def test_large_full_size_with_glitches(engine):
     wave = engine.run_power(0, cfg.bin_ps)
     ge = engine.gate_energy(0, device=True)
     e_gl = engine.gate_glitch(0, device=True)
-    gates = _sample_gates(counts)
-    goff, grec = synth.gate_records(net, tr, gates)
-    sub_net = synth.Netlist(net.cell[gates], net.load_ff[gates], np.ascontiguousarray(net.slew_ps[gates]),
-                            net.n_pins[gates], net.level[gates], net.fanin[gates])
-    sub_tr = synth.Trace(tr.window_ps, goff, grec, tr.init_state[gates], tr.seed, tr.tie24)
-    ref = oracle.walk(lib, sub_net, sub_tr, cfg.bin_ps, waveform=False, glitch=(1000, out_slew[gates]))
+    ref = opool.walk(wl, cfg.bin_ps)
     assert ref["e_gl"].sum() > 0
-    _check_gates(ge, ref, gates)
-    got = e_gl.cpu().numpy()[gates]
-    bad = np.abs(got - ref["e_gl"]) > TOL * np.abs(ref["e_gl"]) + 1e-9
-    assert not bad.any(), f"e_gl: gate {gates[np.argmax(bad)]}"
+    _full_check(wave, ge, ref, cfg.bin_ps, e_gl=e_gl)
     e_bins = float((wave.double() * (cfg.bin_ps * 1e3)).sum())
     e_gates = float(ge["e_leak"].sum() + ge["e_int"].sum() + ge["e_sw"].sum() + e_gl.sum())
     assert e_bins == pytest.approx(e_gates, rel=1e-6)
     engine.set_glitch(0)
 
 
-def test_adjoint_full_size(engine):
+def test_adjoint_full_size(engine, opool):
     import torch
     from paper_2609_05960_gb300 import peak_loss
     cfg = synth.CONFIGS["adjoint"]
@@ -156,6 +168,9 @@ def test_adjoint_full_size(engine):
     tr, rec, off, init = _gpu_trace(engine, net, cfg, counts)
     engine.load_events(0, window_ps=cfg.window_ps, offsets=off, records=rec, init_state=init, borrow=True)
     P = engine.run_power(0, cfg.bin_ps).clone().requires_grad_(True)
+    # the forward waveform and per-gate results, in full, against the oracle
+    _full_check(P.detach(), engine.gate_energy(0, device=True), opool.walk(fullsize.Workload.of(cfg), cfg.bin_ps),
+                cfg.bin_ps)
     peak_loss(P).backward()
     g = P.grad.to(torch.float32)
     dC, de, dl = engine.run_power_backward(0, cfg.bin_ps, g)
@@ -184,7 +199,9 @@ def test_adjoint_full_size(engine):
     engine.set_scales(None, None)
 
 
-def test_batched_full_size(engine):
+def test_batched_full_size(engine, opool):
+    """All 64 windows of the batched workload, replayed from a CUDA graph:
+    every bin and every gate of every window against the oracle."""
     import torch
     lib = synth.make_library(1)
     net = synth.make_netlist(lib, synth.BATCHED_GATES, 2)
@@ -193,7 +210,7 @@ def test_batched_full_size(engine):
     engine.load_netlist(net)
     _defaults(engine)
     keep = []
-    traces = []
+    cfgs = []
     for w, spec in enumerate(wins):
         cfg = synth.Config(f"w{w}", synth.BATCHED_GATES, spec["n_events"], 1.2, 100_000, spec["window_ps"], 10,
                            seed_ev=spec["seed"])
@@ -201,29 +218,25 @@ def test_batched_full_size(engine):
         tr, rec, off, init = _gpu_trace(engine, net, cfg, counts)
         engine.load_events(w, window_ps=cfg.window_ps, offsets=off, records=rec, init_state=init, borrow=True)
         keep.append((rec, off, init))
-        traces.append((cfg, counts, tr))
+        cfgs.append(cfg)
     ids = list(range(len(wins)))
     outs = [torch.empty(s["window_ps"] // 10, dtype=torch.float64, device=engine.device) for s in wins]
     engine.run_power_batched(ids, 10, outs=outs, graph=True)
     engine.run_power_batched(ids, 10, outs=outs, graph=True)  # graph replay
+    worst = 0.0
     for w in ids:
         ge = engine.gate_energy(w, device=True)
         _totals_agree(outs[w], ge, 10)
-        if w % 8 == 0:
-            cfg, counts, tr = traces[w]
-            gates = _sample_gates(counts, n_random=200, n_hot=4, seed=w)
-            _, _, ref = _oracle_gates(lib, net, tr, gates, 10)
-            _check_gates(ge, ref, gates)
-    # the smallest window in full against the oracle
-    w = int(np.argmin([s["n_events"] for s in wins]))
-    cfg, counts, _ = traces[w]
-    host = synth.make_trace(net, counts, cfg.window_ps, cfg.seed_ev)
-    want = oracle.waveform_w(oracle.walk(lib, net, host, 10)["bins"], 10)
-    got = outs[w].cpu().numpy()
-    assert (np.abs(got - want) / want).max() <= TOL
+        err = _full_check(outs[w], ge, opool.walk(fullsize.Workload.of(cfgs[w]), 10), 10)
+        worst = max(worst, err["max_rel_bin_err"])
+    assert worst <= TOL
 
 
-def test_stress_full_size(engine):
+def test_stress_full_size(engine, opool):
+    """Stress (10M gates, 2B events, 10M bins): every bin and every gate
+    against the oracle in the plain form, sampled load gradients in the
+    adjoint form, and every bin and gate of each window in the batched form
+    (four windows of 500M events)."""
     import torch
     cfg = synth.CONFIGS["stress"]
     lib = synth.make_library(cfg.seed_lib)
@@ -236,14 +249,12 @@ def test_stress_full_size(engine):
     engine.load_events(0, window_ps=cfg.window_ps, offsets=off, records=rec, init_state=init, borrow=True)
     wave = engine.run_power(0, cfg.bin_ps)
     ge = engine.gate_energy(0, device=True)
-    gates = _sample_gates(counts, n_random=400, n_hot=4)
-    _, _, ref = _oracle_gates(lib, net, tr, gates, cfg.bin_ps)
-    _check_gates(ge, ref, gates)
+    _full_check(wave, ge, opool.walk(fullsize.Workload.of(cfg), cfg.bin_ps), cfg.bin_ps)
     _totals_agree(wave, ge, cfg.bin_ps)
     # adjoint form on the same window: sampled load gradients
     g = torch.linspace(1.0, 2.0, wave.numel(), device=engine.device, dtype=torch.float32)
     dC, de, dl = engine.run_power_backward(0, cfg.bin_ps, g)
-    few = gates[:40]
+    few = _sample_gates(counts, n_random=400, n_hot=4)[:40]
     sub_net, sub_tr, _ = _oracle_gates(lib, net, tr, few, cfg.bin_ps)
     rC, _, _ = oracle.adjoint(lib, sub_net, sub_tr, cfg.bin_ps, g.cpu().numpy().astype(np.float64))
     got = dC.cpu().numpy()[few]
@@ -252,19 +263,16 @@ def test_stress_full_size(engine):
     torch.cuda.empty_cache()
     # batched form: 4 windows of 500M events
     keep = []
-    traces = []
+    cfgs = []
     for w in range(4):
         c4 = dataclasses.replace(cfg, n_events=cfg.n_events // 4, seed_ev=cfg.seed_ev + 10 * (w + 1))
         cnt = synth.zipf_counts(c4.n_gates, c4.n_events, c4.zipf_s, c4.cap, c4.seed_ev)
         t4, r4, o4, i4 = _gpu_trace(engine, net, c4, cnt)
         engine.load_events(w, window_ps=c4.window_ps, offsets=o4, records=r4, init_state=i4, borrow=True)
         keep.append((r4, o4, i4))
-        traces.append((cnt, t4))
+        cfgs.append(c4)
     outs = engine.run_power_batched([0, 1, 2, 3], cfg.bin_ps)
     for w in range(4):
         ge = engine.gate_energy(w, device=True)
         _totals_agree(outs[w], ge, cfg.bin_ps)
-        cnt, t4 = traces[w]
-        gs = _sample_gates(cnt, n_random=100, n_hot=2, seed=w)
-        _, _, ref = _oracle_gates(lib, net, t4, gs, cfg.bin_ps)
-        _check_gates(ge, ref, gs)
+        _full_check(outs[w], ge, opool.walk(fullsize.Workload.of(cfgs[w]), cfg.bin_ps), cfg.bin_ps)

@@ -73,9 +73,9 @@ def test_fullsize_runner_equals_the_serial_walk():
     lib, net, tr = synth.make_inputs(cfg)
     es = np.linspace(0.8, 1.2, lib.n_cells)
     want = oracle.walk(lib, net, tr, cfg.bin_ps, escale=es)
-    with fullsize.Pool(wl, n_proc=3) as pool:
-        got = pool.walk(cfg.bin_ps, escale=es)
-        got2 = pool.walk(2 * cfg.bin_ps, escale=es)
+    with fullsize.Pool(n_proc=3) as pool:
+        got = pool.walk(wl, cfg.bin_ps, escale=es)
+        got2 = pool.walk(wl, 2 * cfg.bin_ps, escale=es)
     _close(got["bins"], want["bins"])
     for k in ("e_leak", "e_int", "e_sw", "n_events", "final_state"):
         np.testing.assert_array_equal(got[k], want[k])
