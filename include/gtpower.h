@@ -439,6 +439,11 @@ int gtp_measure_reductions(gtp_ctx* ctx, int32_t n_slots, int32_t width, int64_t
  * per run: at least 65,536 and about a sixth of an SM's even share of the
  * run's events, the default; 0 = never; other values round up to a multiple
  * of 4,096),
+ * "group_bin_bytes" (a forward run over several windows walks them in
+ * groups of consecutive windows whose bins, 8 B each, add up to at most
+ * this many bytes (a window with more is a group of its own), one group after
+ * another, so that the bins a walk reduces into stay in L2; default 96 MiB;
+ * gtp_get_param "run_groups" returns the last run's group count),
  * "tile_min" (single-window runs without glitch detection or component
  * waveforms: gates with at least this many events, and at most 3 inputs,
  * take the time-sliced walk, which keeps each 16,384-bin slice of the

@@ -21,6 +21,10 @@ using namespace gtp;
 namespace {
 
 constexpr int kMaxWindows = 1024;
+// Default bin bytes (8 a bin) of the windows one walk launch reduces into
+// at most, unless a single window has more: well inside the 129 MB L2,
+// beside the records streaming through it.
+constexpr int64_t kGroupBinBytes = 96ll << 20;
 
 struct DevBuf {
   void* p = nullptr;
@@ -81,11 +85,11 @@ struct GraphKey {
   int64_t n_tiles;  // launch sizes baked into the graph
   bool any_events;  // whether the walk was captured
   bool timing;      // whether phase events were captured
+  std::vector<int32_t> groups;  // first window of each window group
   bool operator<(const GraphKey& o) const {
-    return std::tie(windows, bin_ps, rpt, ctas, kernel, dmin, tmin, piece, plan_gen, n_tiles, any_events, timing) <
-           std::tie(o.windows, o.bin_ps, o.rpt, o.ctas, o.kernel, o.dmin, o.tmin, o.piece, o.plan_gen, o.n_tiles,
-                    o.any_events,
-                    o.timing);
+    return std::tie(windows, bin_ps, rpt, ctas, kernel, dmin, tmin, piece, plan_gen, n_tiles, any_events, timing,
+                    groups) < std::tie(o.windows, o.bin_ps, o.rpt, o.ctas, o.kernel, o.dmin, o.tmin, o.piece,
+                                       o.plan_gen, o.n_tiles, o.any_events, o.timing, o.groups);
   }
 };
 
@@ -146,6 +150,8 @@ struct gtp_ctx {
   int64_t p_tile_min = 0;  // gates with this many events or more take the time-sliced walk (0: none)
   int64_t p_piece_len = -1;   // gates with more events are split into pieces (0: never, -1: chosen per run)
   int64_t run_piece_len = 0;  // the piece length of the run being planned
+  std::vector<std::pair<int, int>> run_groups;  // the run's window groups [first, end), walked one after another
+  int64_t p_group_bytes = kGroupBinBytes;       // bin bytes of a window group at most
   // phase timing (CUDA events on the context stream) and launch counting
   bool timing = false;
   cudaEvent_t ev[10] = {};
@@ -335,16 +341,38 @@ int build_plan(gtp_ctx* ctx, const std::vector<Window*>& ws, int32_t bin_ps, con
     tb += nt;
   }
   ht[n] = tb;
-  // pieces: a gate with more than piece_len events is walked as several big items, so that no single gate
-  // of a skewed trace walks longer than about a sixth of an SM's even share of the run
+  // window groups: consecutive windows whose bins (8 B each) together stay within p_group_bytes are walked in one
+  // launch; a larger set is walked group after group, so that the bins the walk reduces into stay in L2
+  ctx->run_groups.clear();
   int64_t e_total = 0;
-  for (Window* w : ws) e_total += w->n_events;
+  {
+    int a = 0;
+    int64_t bytes = 0, ev = 0;
+    for (int i = 0; i < n; ++i) {
+      const int64_t b = (int64_t)sizeof(float2) * hw[i].n_bins;
+      if (i > a && bytes + b > ctx->p_group_bytes) {
+        ctx->run_groups.emplace_back(a, i);
+        e_total = std::max(e_total, ev);
+        a = i;
+        bytes = 0;
+        ev = 0;
+      }
+      bytes += b;
+      ev += ws[i]->n_events;
+    }
+    ctx->run_groups.emplace_back(a, n);
+    e_total = std::max(e_total, ev);
+  }
+  // pieces: a gate with more than piece_len events is walked as several big items, so that no single gate
+  // of a skewed trace walks longer than about a sixth of an SM's even share of its group's walk
   int64_t pl = ctx->p_piece_len;
   if (pl < 0) pl = std::max<int64_t>(65536, e_total / (6 * std::max(ctx->n_sm, 1)));
   if (pl > 0) pl = (pl + kPieceUnit - 1) / kPieceUnit * kPieceUnit;
-  if (pl > 0 && e_total / pl >= (int64_t)1 << 20) pl = (e_total >> 20) / kPieceUnit * kPieceUnit + kPieceUnit;
+  int64_t e_all = 0;
+  for (Window* w : ws) e_all += w->n_events;
+  if (pl > 0 && e_all / pl >= (int64_t)1 << 20) pl = (e_all >> 20) / kPieceUnit * kPieceUnit + kPieceUnit;
   ctx->run_piece_len = pl;
-  const int64_t cap = (int64_t)n * G + (pl > 0 ? e_total / pl + n : 0);
+  const int64_t cap = (int64_t)n * G + (pl > 0 ? e_all / pl + n : 0);
   if (cap > ctx->gcap) {
     CU(ctx->glist.reserve(sizeof(int2) * (size_t)cap), "alloc work list");
     ctx->gcap = cap;
@@ -427,33 +455,46 @@ int enqueue_forward(gtp_ctx* ctx, int n, int64_t n_seg_total, int64_t n_tiles_to
   const bool fused = any_events && ctx->p_kernel != 1;
   const bool tiled = fused && tiling_on(ctx, n, comp);
   if (tiled) A.tile_min = ctx->p_tile_min;
-  mark(ctx, 0, st);
-  CU(launch_prepare(ctx->L, ctx->N, A, fused, st), "prepare");
-  mark(ctx, 1, st);
-  ctx->launches += 1;
-  mark(ctx, 2, st);
-  if (any_events) {
-    if (!fused) {
-      mark(ctx, 3, st);
-      mark(ctx, 4, st);
-      CU(launch_walk_per_gate(ctx->L, ctx->N, dw, n, ctx->d_err.as<DevError>(), st), "walk (per gate)");
-      ctx->launches += 1;
-    } else {
-      CU(launch_plan_scatter(ctx->L, ctx->N, A, st), "plan");
-      mark(ctx, 3, st);
-      mark(ctx, 4, st);
-      mark(ctx, 8, st);
-      if (tiled) {
-        CU(launch_tiled(ctx->L, ctx->N, A, plan_wins(ctx->h_plan)[0].n_bins, st), "tiled walk");
+  // the fused walk takes the window groups one after another (a later group's preparation and plan are timed
+  // as walk time); the per-gate walk and runs without events take all windows at once
+  const std::vector<std::pair<int, int>> all{{0, n}};
+  const auto& groups = fused ? ctx->run_groups : all;
+  for (size_t k = 0; k < groups.size(); ++k) {
+    WalkArgs Ag = A;
+    Ag.wins = A.wins + groups[k].first;
+    Ag.n_win = groups[k].second - groups[k].first;
+    if (k == 0) mark(ctx, 0, st);
+    CU(launch_prepare(ctx->L, ctx->N, Ag, fused, st), "prepare");
+    ctx->launches += 1;
+    if (k == 0) {
+      mark(ctx, 1, st);
+      mark(ctx, 2, st);
+    }
+    if (any_events) {
+      if (!fused) {
+        mark(ctx, 3, st);
+        mark(ctx, 4, st);
+        CU(launch_walk_per_gate(ctx->L, ctx->N, dw, n, ctx->d_err.as<DevError>(), st), "walk (per gate)");
+        ctx->launches += 1;
+      } else {
+        CU(launch_plan_scatter(ctx->L, ctx->N, Ag, st), "plan");
+        if (k == 0) {
+          mark(ctx, 3, st);
+          mark(ctx, 4, st);
+          mark(ctx, 8, st);
+        }
+        if (tiled) {
+          CU(launch_tiled(ctx->L, ctx->N, Ag, plan_wins(ctx->h_plan)[0].n_bins, st), "tiled walk");
+          ctx->launches += 2;
+        }
+        if (k == 0) mark(ctx, 9, st);
+        CU(launch_walk(ctx->L, ctx->N, Ag, false, st), "walk");
         ctx->launches += 2;
       }
-      mark(ctx, 9, st);
-      CU(launch_walk(ctx->L, ctx->N, A, false, st), "walk");
-      ctx->launches += 2;
+    } else {
+      mark(ctx, 3, st);
+      mark(ctx, 4, st);
     }
-  } else {
-    mark(ctx, 3, st);
-    mark(ctx, 4, st);
   }
   mark(ctx, 5, st);
   mark(ctx, 6, st);
@@ -571,10 +612,11 @@ int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, dou
                 want_tiled && tiling_on(ctx, n, false)));
   CU(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(DevError), ctx->stream), "zero status");
   if (use_graph) {
-    const GraphKey key{std::vector<int32_t>(windows, windows + n), bin_ps, ctx->p_rpt,
+    GraphKey key{std::vector<int32_t>(windows, windows + n), bin_ps, ctx->p_rpt,
                        ctx->p_ctas_per_sm, ctx->p_kernel, ctx->p_dense_min, ctx->p_tile_min, ctx->run_piece_len,
                        ctx->plan_gen,
-                       n_tiles_total, any_events, ctx->timing};
+                       n_tiles_total, any_events, ctx->timing, {}};
+    for (const auto& gr : ctx->run_groups) key.groups.push_back(gr.first);
     auto it = ctx->graphs.find(key);
     if (it == ctx->graphs.end()) {
       if (!ctx->capture_stream) CU(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking), "stream");
@@ -597,7 +639,8 @@ int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, dou
     }
     // the graph's first node uploads the descriptor table from the staging buffer
     CU(cudaGraphLaunch(it->second, ctx->stream), "graph launch");
-    ctx->launches += any_events ? (ctx->p_kernel == 1 ? 5 : (tiling_on(ctx, n, false) ? 8 : 6)) : 4;
+    const int64_t ng = (int64_t)ctx->run_groups.size();
+    ctx->launches += any_events ? (ctx->p_kernel == 1 ? 5 : 3 * ng + 3 + (tiling_on(ctx, n, false) ? 2 : 0)) : 4;
   } else {
     RC(enqueue_forward(ctx, n, n_seg_total, n_tiles_total, any_events, ctx->stream, components != nullptr));
   }
@@ -1570,6 +1613,8 @@ int gtp_set_param(gtp_ctx* ctx, const char* key, int64_t value) {
     ctx->p_dense_min = value < 0 ? 256 : value;
   } else if (k == "piece_len") {
     ctx->p_piece_len = value < 0 ? -1 : value;
+  } else if (k == "group_bin_bytes") {
+    ctx->p_group_bytes = value < 0 ? kGroupBinBytes : value;
   } else if (k == "tile_min") {
     if (value > (1ll << 31)) return fail(ctx, GTP_ERANGE, "tile_min must be 0..2^31");
     ctx->p_tile_min = value < 0 ? 0 : value;
@@ -1607,6 +1652,8 @@ int64_t gtp_get_param(const gtp_ctx* ctx, const char* key) {
   if (k == "tile_min") return ctx->p_tile_min;
   if (k == "piece_len") return ctx->p_piece_len;
   if (k == "run_piece_len") return ctx->run_piece_len;
+  if (k == "group_bin_bytes") return ctx->p_group_bytes;
+  if (k == "run_groups") return (int64_t)ctx->run_groups.size();
   if (k == "t_tiled_ns") return ctx->t_ns[4];
   if (k == "scheme_evt_tgt") return ctx->p_evt_tgt;
   if (k == "scheme_thr_floor") return ctx->p_thr_floor;

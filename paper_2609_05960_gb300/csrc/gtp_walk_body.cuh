@@ -116,7 +116,6 @@ struct DGate {
   const WinDesc* W;
   const uint2* rec;
   int64_t g, ga, n;          // gate, first record, events (of the piece, for a gate split into pieces)
-  int64_t gs, ge;            // the whole gate's records [gs, ge)
   bool starts, ends, split;  // the piece starts / ends the gate; the gate is split into pieces
   const uint4* dsc;          // the gate's event descriptors
   const float* gleak;        // the cell's leakage entries (unscaled)
@@ -142,18 +141,17 @@ __device__ __forceinline__ DGate dense_gate(const LibView& L, const NetView& N, 
   d.W = wins + (wg.x & kWindowMask);
   d.rec = d.W->rec;
   d.g = wg.y;
-  d.gs = d.W->offsets[d.g];
-  d.ge = d.W->offsets[d.g + 1];
-  d.split = piece_len > 0 && d.ge - d.gs > piece_len;
+  const int64_t gs = d.W->offsets[d.g], ge = d.W->offsets[d.g + 1];
+  d.split = piece_len > 0 && ge - gs > piece_len;
   if (d.split) {
-    d.ga = d.gs + (int64_t)((uint32_t)wg.x >> kPieceShift) * piece_len;
-    d.n = min(piece_len, d.ge - d.ga);
+    d.ga = gs + (int64_t)((uint32_t)wg.x >> kPieceShift) * piece_len;
+    d.n = min(piece_len, ge - d.ga);
   } else {
-    d.ga = d.gs;
-    d.n = d.ge - d.gs;
+    d.ga = gs;
+    d.n = ge - gs;
   }
-  d.starts = d.ga == d.gs;
-  d.ends = d.ga + d.n == d.ge;
+  d.starts = d.ga == gs;
+  d.ends = d.ga + d.n == ge;
   d.cell = (uint32_t)N.cell[d.g];
   const CellInfo ci = L.cells[d.cell];
   d.n_in = (uint32_t)ci.n_in;
@@ -604,10 +602,11 @@ __device__ __forceinline__ void store_gate(const LibView& L, const DGate& d, con
 template <bool GL>
 __device__ __forceinline__ uint32_t piece_entry(const DGate& d, const DenseSmem& sm, int lane) {
   const uint32_t t0 = d.rec[d.ga].x;
+  const int64_t gs = d.W->offsets[d.g];
   uint32_t needS = d.pmask, needP = d.pmask, S = 0u, Sp = 0u, last = 0u;
-  for (int64_t i = d.ga; (needS | needP) && i > d.gs; i -= 32) {
+  for (int64_t i = d.ga; (needS | needP) && i > gs; i -= 32) {
     const int64_t j = i - 1 - lane;
-    const bool ok = j >= d.gs;
+    const bool ok = j >= gs;
     const uint2 r = ok ? d.rec[j] : make_uint2(0xFFFFFFFFu, 0xFu);
     const uint32_t pin = r.y & 0xFu, val = (r.y >> 4) & 1u;
     for (uint32_t p = 0; p <= d.n_in; ++p) {

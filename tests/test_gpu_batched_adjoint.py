@@ -22,7 +22,7 @@ def engine():
 
 
 def _reset(engine):
-    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm", "tile_min", "piece_len"):
+    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm", "tile_min", "piece_len", "group_bin_bytes"):
         engine.set_param(k, -1)
 
 
@@ -37,6 +37,43 @@ def _windows(net, n_win, seed0=100, bin_ps=20):
         tr = synth.make_trace(net, counts, n_bins * bin_ps, seed0 + w, tie_p=0.02 * (w % 3))
         out.append(tr)
     return out
+
+
+@pytest.mark.parametrize("group_bytes,piece", [(1, -1), (20_000, -1), (20_000, 4096), (-1, 4096)])
+def test_window_groups_match_oracle(engine, group_bytes, piece):
+    """Windows walked group after group (group_bin_bytes 1: each window its
+    own group; 20,000 B: groups of a few windows; the default: one group),
+    with and without pieces, repeated (graph replay), against the oracle."""
+    lib = synth.make_library(1)
+    net = synth.make_netlist(lib, 300, seed=7)
+    trs = _windows(net, 11, seed0=300)
+    engine.load_library(lib)
+    engine.load_netlist(net)
+    _reset(engine)
+    engine.set_param("group_bin_bytes", group_bytes)
+    engine.set_param("piece_len", piece)
+    for w, tr in enumerate(trs):
+        engine.load_events(w, tr)
+    order = [3, 0, 7, 1, 10, 2, 9, 4, 8, 5, 6]
+    for it in range(3):
+        waves = engine.run_power_batched(order, 20, graph=it > 0)
+        n_groups = engine.get_param("run_groups")
+        if group_bytes == 1:
+            assert n_groups == len(order)
+        elif group_bytes < 0:
+            assert n_groups == 1
+        else:
+            assert 1 < n_groups < len(order)
+        for k, w in enumerate(order):
+            ref = oracle.walk(lib, net, trs[w], 20)
+            want = oracle.waveform_w(ref["bins"], 20)
+            got = waves[k].cpu().numpy()
+            assert (np.abs(got - want) / np.abs(want)).max() <= TOL, f"window {w}"
+            ge = engine.gate_energy(w, device=False)
+            np.testing.assert_array_equal(ge["final_state"], ref["final_state"])
+            np.testing.assert_array_equal(ge["n_events"], ref["n_events"])
+            for key in ("e_leak", "e_int", "e_sw"):
+                assert np.all(np.abs(ge[key] - ref[key]) <= TOL * np.abs(ref[key]) + 1e-9), (w, key)
 
 
 @pytest.mark.parametrize("rpt", [4, 8, 16])

@@ -100,7 +100,7 @@ def _totals_agree(wave, ge, bin_ps):
 
 
 def _defaults(engine):
-    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm", "tile_min", "piece_len"):
+    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm", "tile_min", "piece_len", "group_bin_bytes"):
         engine.set_param(k, -1)
 
 

@@ -36,7 +36,7 @@ def engine():
 def run(engine, lib, net, tr, bin_ps, params=None, escale=None, lscale=None, window=0):
     engine.load_library(lib)
     engine.load_netlist(net)
-    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm", "tile_min", "piece_len"):
+    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm", "tile_min", "piece_len", "group_bin_bytes"):
         engine.set_param(k, -1)
     for k, v in (params or {}).items():
         engine.set_param(k, v)
@@ -280,7 +280,7 @@ def test_device_resident_events(engine, borrow):
     lib, net, tr = small_random(n_gates=100, n_events=20_001, window_ps=200_000, seed=51, tie_p=0.02)
     engine.load_library(lib)
     engine.load_netlist(net)
-    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm", "tile_min", "piece_len"):
+    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm", "tile_min", "piece_len", "group_bin_bytes"):
         engine.set_param(k, -1)
     dev = engine.device
     off = torch.from_numpy(tr.offsets).to(dev)

@@ -34,7 +34,7 @@ def engine():
 def setup(engine, lib, net, piece_len=PIECE, rpt=8):
     engine.load_library(lib)
     engine.load_netlist(net)
-    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm", "tile_min", "piece_len"):
+    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm", "tile_min", "piece_len", "group_bin_bytes"):
         engine.set_param(k, -1)
     engine.set_param("piece_len", piece_len)
     engine.set_param("records_per_thread", rpt)

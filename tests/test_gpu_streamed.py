@@ -24,7 +24,7 @@ def engine():
 def _setup(engine, lib, net, params=None):
     engine.load_library(lib)
     engine.load_netlist(net)
-    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm", "tile_min", "piece_len"):
+    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm", "tile_min", "piece_len", "group_bin_bytes"):
         engine.set_param(k, -1)
     for k, v in (params or {}).items():
         engine.set_param(k, v)

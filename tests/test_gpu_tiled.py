@@ -35,7 +35,7 @@ def engine():
 def run(engine, lib, net, tr, bin_ps, tile_min, escale=None, lscale=None, dense_min=-1):
     engine.load_library(lib)
     engine.load_netlist(net)
-    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm", "tile_min", "piece_len"):
+    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm", "tile_min", "piece_len", "group_bin_bytes"):
         engine.set_param(k, -1)
     engine.set_param("tile_min", tile_min)
     engine.set_param("dense_min", dense_min)
