@@ -114,3 +114,68 @@ def simulate(lib, net, trace, bin_ps: int, escale=None, lscale=None, load_ff=Non
     out["bins"] = bins
     out["comp_bins"] = comp
     return out
+
+
+def simulate_patterns(plib, pnet, ptrace, bin_ps: int, clock: int = 0):
+    """The same per-picosecond stepping for gates whose cells are given by
+    state patterns (up to 32 pins; synth.patterns layout): each lookup scans
+    the cell's patterns in list order (oracle/sipl.py) at the state held
+    before the picosecond's events; tables are interpolated by
+    RegularGridInterpolator.  Output transition times for glitch detection
+    are pnet.out_slew_ps.  Returns bins (fJ) and per-gate results."""
+    from . import sipl
+
+    T = int(ptrace.window_ps)
+    n_bins = T // bin_ps
+    G = pnet.n_gates
+    axes = (np.asarray(plib.slew_axis, np.float64), np.asarray(plib.load_axis, np.float64))
+    vdd = float(plib.vdd)
+    bins = np.zeros(n_bins)
+    out = dict(e_leak=np.zeros(G), e_int=np.zeros(G), e_sw=np.zeros(G), e_gl=np.zeros(G),
+               n_events=np.zeros(G, np.int64), final_state=np.zeros(G, np.uint32))
+    for g in range(G):
+        n_in, ip, dflt, lp, ld = plib.cell(int(pnet.cell[g]))
+        n_pins = n_in + 1
+        C = float(pnet.load_ff[g])
+        bits = [(int(ptrace.init_state[g]) >> p) & 1 for p in range(n_pins)]
+        at = {}
+        a, b = int(ptrace.offsets[g]), int(ptrace.offsets[g + 1])
+        for k in range(a, b):
+            at.setdefault(int(ptrace.t_ps[k]), []).append((int(ptrace.pin[k]), int(ptrace.value[k])))
+        count = [0] * n_pins
+        last = [0] * n_pins
+        cycle = -1
+        for tau in range(T):
+            if clock and tau // clock != cycle:
+                cycle = tau // clock
+                count = [0] * n_pins
+            state = sum(v << p for p, v in enumerate(bits))
+            for pin, value in at.get(tau, []):
+                if pin < n_in:
+                    tab = sipl.internal_item(pin, value, state & ((1 << n_in) - 1), ip, dflt)
+                    f = RegularGridInterpolator(axes, np.asarray(tab, np.float64), method="linear",
+                                                bounds_error=False, fill_value=None)
+                    E = float(f([[float(pnet.slew_ps[g, pin, value]), C]])[0])
+                    rise_fall = float(pnet.slew_ps[g, pin, 0]) + float(pnet.slew_ps[g, pin, 1])
+                else:
+                    E = 0.5 * C * vdd * vdd
+                    rise_fall = float(pnet.out_slew_ps[g, 0]) + float(pnet.out_slew_ps[g, 1])
+                kind = 1 if pin < n_in else 2
+                if clock:
+                    count[pin] += 1
+                    if count[pin] > 1:
+                        E *= 1.0 if rise_fall <= 0 else min(1.0, (2.0 * (tau - last[pin]) / rise_fall) ** 2)
+                        kind = 3
+                    last[pin] = tau
+                out[("e_leak", "e_int", "e_sw", "e_gl")[kind]][g] += E
+                bins[tau // bin_ps] += E
+            for pin, value in at.get(tau, []):
+                bits[pin] = value
+            state = sum(v << p for p, v in enumerate(bits))
+            e = sipl.leakage_item(state, lp, ld) * 1e-6
+            bins[tau // bin_ps] += e
+            out["e_leak"][g] += e
+        out["n_events"][g] = b - a
+        out["final_state"][g] = sum(v << p for p, v in enumerate(bits))
+    out["bins"] = bins
+    return out
