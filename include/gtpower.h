@@ -162,6 +162,102 @@ int gtp_sipl_expand(int32_t n_in, int32_t n_slew, int32_t n_load, int32_t n_int_
                     const float* int_default, int32_t n_leak_pat, const uint32_t* leak_care, const uint32_t* leak_val,
                     const float* leak_pw, float leak_default, float* e_int, float* p_leak);
 
+/* ------------------------------------------------------------------------
+ * Pattern gates: gates whose cells are given by Liberty-style state patterns,
+ * up to GTP_MAX_PATTERN_PINS pins (inputs and one output), such as the wide
+ * cells and macros (SRAMs) the state-indexed library above cannot hold
+ * [Sec. 4.1: state-indexed lookup for gates of at most 16 pins, direct
+ * traversal of the state patterns for wider ones].  A pattern cell with at
+ * most "sipl_max_pins" pins (gtp_set_param; default 16, the paper's
+ * threshold; at most GTP_MAX_INDEXED_PINS) is walked through state-indexed
+ * arrays the engine builds on the device from its patterns at the first run
+ * after a change (each entry takes the first pattern covering it, as the
+ * paper's don't-care enumeration fills it); a wider one scans its patterns
+ * at every lookup.  Both give the same power items, so the threshold changes
+ * speed and memory (4 * (n_in * 2^n_in + 2^(n_in+1)) bytes for a cell of
+ * n_in inputs), never results.  The pattern gates of a window are walked
+ * with its ordinary gates by gtp_run_power and gtp_run_power_batched, by the
+ * same definition (Algorithm 1: groups of equal timestamps, lookups at the
+ * pre-group state; Sec. 2.2, Eq. 1, Eq. 4, Sec. 2.4.2; glitch detection of
+ * Sec. 2.4.1 and Eq. 2 when gtp_set_glitch is on, with the transition times
+ * given here), and add into the same waveform; gtp_design_power includes
+ * them.  gtp_run_power_components, gtp_run_power_backward and
+ * gtp_run_power_scheme return GTP_EINVAL for a window with pattern gates.
+ * ------------------------------------------------------------------------ */
+#define GTP_MAX_PATTERN_PINS 32
+#define GTP_MAX_INDEXED_PINS 24
+
+/*
+ * Load the pattern cells [Sec. 4.1: Liberty state patterns over a fixed pin
+ * order] (host arrays; replaces earlier ones and drops the
+ * pattern netlist and every window's pattern events).
+ *   n_in[c]      input pins of cell c, 1..31; pin n_in[c] is its output
+ *   vdd, axes    supply (V) and the table axes, as in gtp_load_library
+ *   int_offsets  [n_cells + 1] from 0: cell c's internal patterns are
+ *                k in [int_offsets[c], int_offsets[c + 1]), in list order
+ *   int_pin[k], int_edge[k] (0 fall, 1 rise, -1 both), int_care[k],
+ *   int_val[k]   as in gtp_sipl_expand (care: other input pins only)
+ *   int_tab      [n_int][n_slew][n_load] fJ, pattern k's table
+ *   int_default  per cell, [n_in[c]][2][n_slew][n_load] fJ, cell-major: the
+ *                table of an event no pattern of its (pin, edge) matches
+ *   leak_offsets [n_cells + 1]; leak_care/val[k] over all the cell's pins,
+ *                leak_pw[k] nW; leak_default[c] nW
+ * Errors: GTP_ERANGE for n_in or axis lengths out of range, GTP_EINVAL for
+ * null arrays, decreasing offsets or a pattern naming a pin it may not.
+ */
+int gtp_load_pattern_cells(gtp_ctx* ctx, int32_t n_cells, const int32_t* n_in, float vdd, int32_t n_slew,
+                           const float* slew_axis, int32_t n_load, const float* load_axis,
+                           const int32_t* int_offsets, const int32_t* int_pin, const int32_t* int_edge,
+                           const uint32_t* int_care, const uint32_t* int_val, const float* int_tab,
+                           const float* int_default, const int32_t* leak_offsets, const uint32_t* leak_care,
+                           const uint32_t* leak_val, const float* leak_pw, const float* leak_default);
+
+/*
+ * Load the pattern gates [Sec. 2.2: per-gate load and transition times;
+ * Sec. 2.4.1 for the output transition times] (host arrays; drops every
+ * window's pattern events):
+ * cell[g] (a pattern cell), load_ff[g] (fF), slew_ps[g][slew_stride][2]
+ * input {fall, rise} transition times (ps; slew_stride >= the widest cell's
+ * inputs, <= 32), out_slew_ps[g][2] output {fall, rise} transition times for
+ * glitch detection (NULL: none, an output glitch swings fully).  The
+ * ordinary netlist (gtp_load_netlist) must be loaded for runs; loading it
+ * again drops the windows and their pattern events.
+ * Errors: GTP_EINVAL (no pattern cells, null arrays, stride), GTP_ERANGE
+ * (cell index).
+ */
+int gtp_load_pattern_netlist(gtp_ctx* ctx, int64_t n_gates, const int32_t* cell, const float* load_ff,
+                             const float* slew_ps, int32_t slew_stride, const float* out_slew_ps);
+
+/*
+ * Load a window's pattern-gate events [Sec. 2.1: an event is a pin's new
+ * value at a time] (the window must be loaded by
+ * gtp_load_events first, which fixes its window_ps; loading it again drops
+ * them).  Arrays are host memory, or device memory with GTP_DEVICE; they are
+ * copied.  gate_offsets[n_gates + 1] (CSR over the pattern gates, from 0 to
+ * n_events); per event t_ps (non-decreasing within a gate), pin (< the
+ * gate's pin count) and value (the pin's new value, 0 or 1, which must
+ * differ from its current value); init_state[g] the gate's initial state
+ * (bit q = pin q; no bits past its pins).  Times, pins and values are checked
+ * by the run, which reports the first malformed record as gtp_run_power does
+ * ("at pattern record N").
+ * Errors: GTP_EINVAL (no pattern netlist, window not loaded, offsets),
+ * GTP_ERANGE (initial state).
+ */
+int gtp_load_pattern_events(gtp_ctx* ctx, int32_t window, int64_t n_events, const int64_t* gate_offsets,
+                            const int32_t* t_ps, const uint8_t* pin, const uint8_t* value,
+                            const uint32_t* init_state, int flags);
+
+/*
+ * Per-pattern-gate results of the window's last run [Sec. 2.2 components;
+ * Eq. 3 sums them]: energies in fJ (FP64;
+ * e_gl is zero without glitch detection), event counts and final states
+ * (uint32: up to 32 pins).  NULL outputs are skipped; outputs are host
+ * memory, or device memory with GTP_DEVICE.
+ * Errors: GTP_EINVAL when the window has no pattern-gate result.
+ */
+int gtp_pattern_gate_energy(gtp_ctx* ctx, int32_t window, double* e_leak, double* e_int, double* e_sw, double* e_gl,
+                            int64_t* n_events, uint32_t* final_state, int flags);
+
 /*
  * Per-cell multipliers on internal energy and on leakage power (host arrays
  * of n_cells; NULL leaves that scale at 1).  The paper has no counterpart:
@@ -439,6 +535,10 @@ int gtp_measure_reductions(gtp_ctx* ctx, int32_t n_slots, int32_t width, int64_t
  * per run: at least 65,536 and about a sixth of an SM's even share of the
  * run's events, the default; 0 = never; other values round up to a multiple
  * of 4,096),
+ * "sipl_max_pins" (pattern cells with at most this many pins are walked
+ * through state-indexed arrays, wider ones by pattern traversal; 0..24,
+ * default 16; gtp_get_param "pattern_indexed_cells" and
+ * "pattern_index_bytes" report the arrays built at the last run, -1 before),
  * "group_bin_bytes" (a forward run over several windows walks them in
  * groups of consecutive windows whose bins, 8 B each, add up to at most
  * this many bytes (a window with more is a group of its own), one group after

@@ -65,11 +65,26 @@ struct Window {
   bool glitch_result = false;  // the last run detected glitches (e_gl holds them)
   bool streamed = false;       // filled by a streamed run: results only, no resident records
   int32_t last_bin_ps = 0;
+  // pattern gates: records {t, pin | value << 8}, initial states, items, and per-gate results
+  bool pat_loaded = false;
+  int64_t pat_n_events = 0, pat_n_items = 0;
+  std::vector<int64_t> pat_h_off;
+  DevBuf pat_off, pat_rec, pat_init, pat_items, pat_first, pat_mask, pat_e_leak, pat_e_int, pat_e_sw, pat_e_gl,
+      pat_final;
+  void release_patterns() {
+    for (DevBuf* b : {&pat_off, &pat_rec, &pat_init, &pat_items, &pat_first, &pat_mask, &pat_e_leak, &pat_e_int,
+                      &pat_e_sw, &pat_e_gl, &pat_final})
+      b->release();
+    pat_h_off.clear();
+    pat_loaded = false;
+    pat_n_events = pat_n_items = 0;
+  }
   const uint2* rec() const { return borrowed ? borrowed : records.as<uint2>(); }
   void release() {
     for (DevBuf* b : {&offsets, &records, &init, &e_leak, &e_int, &e_sw, &e_gl, &final_state, &bins, &tbins, &tiles, &wave,
                       &cbins, &cwave, &ps_off, &ps_ev, &ps_slot, &blk_gate, &blk_first, &ncyc})
       b->release();
+    release_patterns();
     borrowed = nullptr;
     loaded = false;
     has_result = false;
@@ -86,10 +101,12 @@ struct GraphKey {
   bool any_events;  // whether the walk was captured
   bool timing;      // whether phase events were captured
   std::vector<int32_t> groups;  // first window of each window group
+  int64_t pat_items;            // pattern walk launch size (-1: no pattern gates)
   bool operator<(const GraphKey& o) const {
     return std::tie(windows, bin_ps, rpt, ctas, kernel, dmin, tmin, piece, plan_gen, n_tiles, any_events, timing,
-                    groups) < std::tie(o.windows, o.bin_ps, o.rpt, o.ctas, o.kernel, o.dmin, o.tmin, o.piece,
-                                       o.plan_gen, o.n_tiles, o.any_events, o.timing, o.groups);
+                    groups, pat_items) < std::tie(o.windows, o.bin_ps, o.rpt, o.ctas, o.kernel, o.dmin, o.tmin,
+                                                  o.piece, o.plan_gen, o.n_tiles, o.any_events, o.timing, o.groups,
+                                                  o.pat_items);
   }
 };
 
@@ -152,6 +169,18 @@ struct gtp_ctx {
   int64_t run_piece_len = 0;  // the piece length of the run being planned
   std::vector<std::pair<int, int>> run_groups;  // the run's window groups [first, end), walked one after another
   int64_t p_group_bytes = kGroupBinBytes;       // bin bytes of a window group at most
+  // pattern cells (state patterns, up to 32 pins) and pattern gates
+  bool pat_cells_ok = false, pat_net_ok = false, pat_index_ok = false;
+  std::vector<PatCell> h_pat_cells;
+  DevBuf pc_cells, pc_ip, pc_ipo, pc_lp, pc_tab, pc_iidx, pc_lidx;
+  PatLib P{};
+  DevBuf pn_cell, pn_load, pn_slew, pn_oslew;
+  PatNet Q{};
+  int64_t p_sipl_max_pins = 16;  // pattern cells with at most this many pins get state-indexed arrays
+  int64_t pat_index_bytes = 0;
+  int32_t pat_indexed = 0;
+  DevBuf pat_bad;  // smallest error key of the pattern walk
+  int64_t run_pat_items = -1;  // the run's pattern walk launch size (-1: none)
   // phase timing (CUDA events on the context stream) and launch counting
   bool timing = false;
   cudaEvent_t ev[10] = {};
@@ -308,9 +337,26 @@ int build_plan(gtp_ctx* ctx, const std::vector<Window*>& ws, int32_t bin_ps, con
     d.final_state = W.final_state.as<uint8_t>();
     d.bins = W.bins.as<float2>();
     d.tbins = nullptr;
-    if (tiled) {
-      CU(W.tbins.reserve(sizeof(double2) * nb), "alloc tiled bins");
+    const bool pat = W.pat_loaded && ctx->pat_net_ok && !backward;
+    if (tiled || pat) {
+      CU(W.tbins.reserve(sizeof(double2) * nb), "alloc FP64 bins");
       d.tbins = W.tbins.as<double2>();
+    }
+    d.p_n_items = 0;
+    d.p_off = nullptr;
+    if (pat) {
+      d.p_off = W.pat_off.as<int64_t>();
+      d.p_rec = W.pat_rec.as<uint2>();
+      d.p_init = W.pat_init.as<uint32_t>();
+      d.p_items = W.pat_items.as<int2>();
+      d.p_first = W.pat_first.as<int64_t>();
+      d.p_mask = W.pat_mask.as<uint32_t>();
+      d.p_e_leak = W.pat_e_leak.as<double>();
+      d.p_e_int = W.pat_e_int.as<double>();
+      d.p_e_sw = W.pat_e_sw.as<double>();
+      d.p_e_gl = W.pat_e_gl.as<double>();
+      d.p_final = W.pat_final.as<uint32_t>();
+      d.p_n_items = W.pat_n_items;
     }
     d.cbins = nullptr;
     d.cwave = nullptr;
@@ -496,6 +542,12 @@ int enqueue_forward(gtp_ctx* ctx, int n, int64_t n_seg_total, int64_t n_tiles_to
       mark(ctx, 4, st);
     }
   }
+  if (ctx->run_pat_items >= 0) {  // the pattern gates, into the windows' FP64 bins and L0 (timed as walk)
+    CU(cudaMemsetAsync(ctx->pat_bad.p, 0xFF, sizeof(unsigned long long), st), "reset pattern status");
+    CU(launch_pattern_walk(ctx->P, ctx->Q, dw, n, ctx->run_pat_items, ctx->N.clock_ps,
+                           ctx->pat_bad.as<unsigned long long>(), st), "pattern walk");
+    ctx->launches += ctx->run_pat_items > 0 ? 3 : 1;
+  }
   mark(ctx, 5, st);
   mark(ctx, 6, st);
   CU(launch_merge(dw, tile_base, n, n_tiles_total, st), "merge");
@@ -560,6 +612,67 @@ __global__ void k_counts(const int64_t* off, int64_t n, int64_t* out) {
     out[g] = off[g + 1] - off[g];
 }
 
+// State-indexed arrays of the pattern cells with at most p_sipl_max_pins
+// pins (and at most GTP_MAX_INDEXED_PINS), built on the device from their
+// patterns; the others are walked by traversal.
+int ensure_pattern_index(gtp_ctx* ctx) {
+  if (ctx->pat_index_ok) return GTP_OK;
+  int64_t ni = 0, nl = 0;
+  int32_t n_idx = 0;
+  for (PatCell& c : ctx->h_pat_cells) {
+    const int pins = c.n_in + 1;
+    if (pins <= ctx->p_sipl_max_pins && pins <= GTP_MAX_INDEXED_PINS) {
+      c.iidx = ni;
+      c.lidx = nl;
+      ni += (int64_t)c.n_in << c.n_in;  // n_in pins x 2 edges x 2^(n_in - 1) side states
+      nl += 2ll << c.n_in;
+      ++n_idx;
+    } else {
+      c.iidx = c.lidx = -1;
+    }
+  }
+  drop_graphs(ctx);
+  CU(cudaStreamSynchronize(ctx->stream), "pattern index");
+  if (ni > 0) {
+    CU(ctx->pc_iidx.reserve(sizeof(int32_t) * (size_t)ni), "alloc pattern index");
+    CU(ctx->pc_lidx.reserve(sizeof(float) * (size_t)nl), "alloc pattern index");
+  }
+  CU(cudaMemcpyAsync(ctx->pc_cells.p, ctx->h_pat_cells.data(), sizeof(PatCell) * ctx->h_pat_cells.size(),
+                     cudaMemcpyHostToDevice, ctx->stream), "copy pattern cells");
+  ctx->P.iidx = ctx->pc_iidx.as<int32_t>();
+  ctx->P.lidx = ctx->pc_lidx.as<float>();
+  for (size_t c = 0; c < ctx->h_pat_cells.size(); ++c)
+    if (ctx->h_pat_cells[c].iidx >= 0) {
+      CU(launch_pattern_index(ctx->P, (int32_t)c, ctx->h_pat_cells[c].n_in, ctx->stream), "pattern index");
+      ctx->launches += 1;
+    }
+  CU(cudaStreamSynchronize(ctx->stream), "pattern index");
+  ctx->pat_index_bytes = 4 * (ni + nl);
+  ctx->pat_indexed = n_idx;
+  ctx->pat_index_ok = true;
+  return GTP_OK;
+}
+
+// Status of the pattern walk of a run over windows ids[0, n_win): its
+// smallest error key (see launch_pattern_walk), or GTP_OK.
+int check_pattern_error(gtp_ctx* ctx, int n_win, const int32_t* ids, const char* what) {
+  unsigned long long key = ~0ull;
+  CU(cudaMemcpyAsync(&key, ctx->pat_bad.p, sizeof key, cudaMemcpyDeviceToHost, ctx->stream), "read pattern status");
+  CU(cudaStreamSynchronize(ctx->stream), what);
+  if (key == ~0ull) return GTP_OK;
+  const int code = -(int)(key & 7ull);
+  const long long rec = (long long)((key >> 3) & ((1ull << 40) - 1ull));
+  const int w = (int)(key >> 43);
+  char buf[256];
+  if (n_win > 1)
+    snprintf(buf, sizeof buf, "%s: %s at pattern record %lld of window %d", what, code_name(code), rec, ids[w]);
+  else
+    snprintf(buf, sizeof buf, "%s: %s at pattern record %lld", what, code_name(code), rec);
+  ctx->h_err->code = code;
+  ctx->h_err->index = rec;
+  return fail(ctx, code, buf);
+}
+
 // Forward run of a window list; waveforms per window (device or host).
 int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, double* const* waveforms, int flags,
                 bool use_graph, double* const* components = nullptr) {
@@ -574,6 +687,17 @@ int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, dou
     any_events |= ws[i]->n_events > 0;
   }
   if (bin_ps <= 0) return fail(ctx, GTP_ERANGE, "window_ps must be a multiple of bin_ps > 0");
+  // pattern gates of the windows: the launch size of their walk (-1: none)
+  ctx->run_pat_items = -1;
+  if (ctx->pat_net_ok)
+    for (Window* w : ws)
+      if (w->pat_loaded) ctx->run_pat_items = std::max(ctx->run_pat_items, w->pat_n_items);
+  if (ctx->run_pat_items >= 0) {
+    if (components) return fail(ctx, GTP_EINVAL, "run_power_components: windows with pattern gates are walked by "
+                                                 "gtp_run_power and gtp_run_power_batched only");
+    RC(ensure_pattern_index(ctx));
+    CU(ctx->pat_bad.reserve(sizeof(unsigned long long)), "alloc pattern status");
+  }
   std::vector<double*> waves(n, nullptr);
   for (int i = 0; i < n; ++i) {
     if (!waveforms || !waveforms[i]) continue;
@@ -615,7 +739,7 @@ int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, dou
     GraphKey key{std::vector<int32_t>(windows, windows + n), bin_ps, ctx->p_rpt,
                        ctx->p_ctas_per_sm, ctx->p_kernel, ctx->p_dense_min, ctx->p_tile_min, ctx->run_piece_len,
                        ctx->plan_gen,
-                       n_tiles_total, any_events, ctx->timing, {}};
+                       n_tiles_total, any_events, ctx->timing, {}, ctx->run_pat_items};
     for (const auto& gr : ctx->run_groups) key.groups.push_back(gr.first);
     auto it = ctx->graphs.find(key);
     if (it == ctx->graphs.end()) {
@@ -641,6 +765,7 @@ int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, dou
     CU(cudaGraphLaunch(it->second, ctx->stream), "graph launch");
     const int64_t ng = (int64_t)ctx->run_groups.size();
     ctx->launches += any_events ? (ctx->p_kernel == 1 ? 5 : 3 * ng + 3 + (tiling_on(ctx, n, false) ? 2 : 0)) : 4;
+    if (ctx->run_pat_items >= 0) ctx->launches += ctx->run_pat_items > 0 ? 3 : 1;
   } else {
     RC(enqueue_forward(ctx, n, n_seg_total, n_tiles_total, any_events, ctx->stream, components != nullptr));
   }
@@ -656,7 +781,8 @@ int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, dou
         CU(cudaMemcpyAsync(components[i], cwaves[i], 4 * sizeof(double) * (size_t)(ws[i]->window_ps / bin_ps),
                            cudaMemcpyDeviceToHost, ctx->stream), "copy components");
   }
-  const int rc = check_walk_error(ctx, n, windows, "run_power");
+  int rc = check_walk_error(ctx, n, windows, "run_power");
+  if (rc == GTP_OK && ctx->run_pat_items >= 0) rc = check_pattern_error(ctx, n, windows, "run_power");
   collect_timing(ctx);
   for (Window* w : ws) {
     w->has_result = (rc == GTP_OK);
@@ -787,7 +913,9 @@ void gtp_destroy(gtp_ctx* ctx) {
                     &ctx->cell, &ctx->load, &ctx->slew, &ctx->desc, &ctx->plan, &ctx->glist, &ctx->gtab, &ctx->gtab_bwd,
                     &ctx->counters, &ctx->first_bad, &ctx->out_slew, &ctx->dp_scratch,
                     &ctx->cell_acc, &ctx->grad, &ctx->gtiles, &ctx->dC_scratch, &ctx->d_err, &ctx->pat_int,
-                    &ctx->pat_leak, &ctx->sch_ebins, &ctx->sch_R, &ctx->probe})
+                    &ctx->pat_leak, &ctx->sch_ebins, &ctx->sch_R, &ctx->probe, &ctx->chunks, &ctx->pc_cells,
+                    &ctx->pc_ip, &ctx->pc_ipo, &ctx->pc_lp, &ctx->pc_tab, &ctx->pc_iidx, &ctx->pc_lidx,
+                    &ctx->pn_cell, &ctx->pn_load, &ctx->pn_slew, &ctx->pn_oslew, &ctx->pat_bad})
     b->release();
   for (auto& e : ctx->sch_ev)
     if (e) cudaEventDestroy(e);
@@ -1005,6 +1133,17 @@ int gtp_design_power(gtp_ctx* ctx, int32_t window, const double* waveform_w, int
   double h[6];
   CU(cudaMemcpyAsync(h, ctx->dp_scratch.p, sizeof h, cudaMemcpyDeviceToHost, ctx->stream), "read design power");
   CU(cudaStreamSynchronize(ctx->stream), "design_power");
+  if (W->pat_loaded && ctx->pat_net_ok) {  // the pattern gates' energies, added in gate order
+    const int64_t Gp = ctx->Q.n_gates;
+    std::vector<double> e((size_t)Gp);
+    DevBuf* src[4] = {&W->pat_e_leak, &W->pat_e_int, &W->pat_e_sw, &W->pat_e_gl};
+    for (int k = 0; k < 4; ++k) {
+      CU(cudaMemcpyAsync(e.data(), src[k]->p, sizeof(double) * (size_t)Gp, cudaMemcpyDeviceToHost, ctx->stream),
+         "read pattern energies");
+      CU(cudaStreamSynchronize(ctx->stream), "design_power");
+      for (double x : e) h[k] += x;
+    }
+  }
   const double to_w = 1e-3 / (double)W->window_ps;  // fJ over the window in ps -> W
   for (int k = 0; k < 4; ++k) out[k] = h[k] * to_w;
   out[4] = out[0] + out[1] + out[2] + out[3];
@@ -1067,7 +1206,11 @@ int gtp_load_events(gtp_ctx* ctx, int32_t window, int64_t window_ps, int64_t n_e
   DeviceGuard dg(ctx->device);
   const int64_t G = ctx->N.n_gates;
   Window& W = ctx->windows[window];
-  // buffers are kept and grown as needed, so reloading a slot does not reallocate
+  // buffers are kept and grown as needed, so reloading a slot does not reallocate; its pattern events go
+  if (W.pat_loaded) {
+    CU(cudaStreamSynchronize(ctx->stream), "load_events");
+    W.release_patterns();
+  }
   W.loaded = false;
   W.has_result = false;
   W.streamed = false;
@@ -1145,6 +1288,9 @@ int gtp_run_power_scheme(gtp_ctx* ctx, int32_t window, int32_t bin_ps, int32_t s
   DeviceGuard dg(ctx->device);
   Window* W = get_window(ctx, window);
   if (!W || W->streamed) return fail(ctx, GTP_EINVAL, "run_power_scheme: window not loaded");
+  if (W->pat_loaded && ctx->pat_net_ok)
+    return fail(ctx, GTP_EINVAL, "run_power_scheme: windows with pattern gates are walked by gtp_run_power and "
+                                 "gtp_run_power_batched only");
   if (bin_ps <= 0 || W->window_ps % bin_ps != 0) return fail(ctx, GTP_ERANGE, "window_ps must be a multiple of bin_ps > 0");
   const int64_t nb = W->window_ps / bin_ps;
   const int64_t G = ctx->N.n_gates;
@@ -1458,6 +1604,9 @@ int gtp_run_power_backward(gtp_ctx* ctx, int32_t window, int32_t bin_ps, const f
   if (!ctx) return GTP_EINVAL;
   Window* W = get_window(ctx, window);
   if (!W || W->streamed) return fail(ctx, GTP_EINVAL, "run_power_backward: window not loaded");
+  if (W->pat_loaded && ctx->pat_net_ok)
+    return fail(ctx, GTP_EINVAL, "run_power_backward: windows with pattern gates are walked by gtp_run_power and "
+                                 "gtp_run_power_batched only");
   if (!dL_dP) return fail(ctx, GTP_EINVAL, "run_power_backward: dL_dP is required");
   if (bin_ps <= 0 || W->window_ps % bin_ps != 0)
     return fail(ctx, GTP_ERANGE, "window_ps must be a multiple of bin_ps > 0");
@@ -1595,6 +1744,260 @@ int gtp_measure_reductions(gtp_ctx* ctx, int32_t n_slots, int32_t width, int64_t
   return GTP_OK;
 }
 
+int gtp_load_pattern_cells(gtp_ctx* ctx, int32_t n_cells, const int32_t* n_in, float vdd, int32_t n_slew,
+                           const float* slew_axis, int32_t n_load, const float* load_axis, const int32_t* int_offsets,
+                           const int32_t* int_pin, const int32_t* int_edge, const uint32_t* int_care,
+                           const uint32_t* int_val, const float* int_tab, const float* int_default,
+                           const int32_t* leak_offsets, const uint32_t* leak_care, const uint32_t* leak_val,
+                           const float* leak_pw, const float* leak_default) {
+  if (!ctx) return GTP_EINVAL;
+  if (n_cells <= 0 || n_cells > (1 << 20) || !n_in || !slew_axis || !load_axis || !int_offsets || !int_default ||
+      !leak_offsets || !leak_default)
+    return fail(ctx, GTP_EINVAL, "load_pattern_cells: need 1 <= n_cells <= 2^20 and non-null arrays");
+  if (n_slew < 2 || n_slew > GTP_MAX_AXIS || n_load < 2 || n_load > GTP_MAX_AXIS)
+    return fail(ctx, GTP_ERANGE, "load_pattern_cells: axis lengths must be 2..16");
+  for (int i = 0; i + 1 < n_slew; ++i)
+    if (!(slew_axis[i] < slew_axis[i + 1])) return fail(ctx, GTP_EINVAL, "load_pattern_cells: slew axis not increasing");
+  for (int i = 0; i + 1 < n_load; ++i)
+    if (!(load_axis[i] < load_axis[i + 1])) return fail(ctx, GTP_EINVAL, "load_pattern_cells: load axis not increasing");
+  if (int_offsets[0] != 0 || leak_offsets[0] != 0)
+    return fail(ctx, GTP_EINVAL, "load_pattern_cells: offsets must start at 0");
+  int64_t n_def = 0;
+  for (int32_t c = 0; c < n_cells; ++c) {
+    if (n_in[c] < 1 || n_in[c] > GTP_MAX_PATTERN_PINS - 1)
+      return fail(ctx, GTP_ERANGE, "load_pattern_cells: n_in must be 1..31");
+    if (int_offsets[c + 1] < int_offsets[c] || leak_offsets[c + 1] < leak_offsets[c])
+      return fail(ctx, GTP_EINVAL, "load_pattern_cells: offsets must not decrease");
+    n_def += 2ll * n_in[c];
+  }
+  const int64_t n_int = int_offsets[n_cells], n_lp = leak_offsets[n_cells];
+  if (n_int > 0 && (!int_pin || !int_edge || !int_care || !int_val || !int_tab))
+    return fail(ctx, GTP_EINVAL, "load_pattern_cells: null internal pattern arrays");
+  if (n_lp > 0 && (!leak_care || !leak_val || !leak_pw))
+    return fail(ctx, GTP_EINVAL, "load_pattern_cells: null leakage pattern arrays");
+  if (n_int + n_def >= (1ll << 31)) return fail(ctx, GTP_ERANGE, "load_pattern_cells: too many tables");
+  const size_t T = (size_t)n_slew * n_load;
+  std::vector<uint4> ip;
+  std::vector<int32_t> ipo;
+  std::vector<uint4> lp((size_t)n_lp);
+  std::vector<PatCell> cells((size_t)n_cells);
+  int64_t d0 = n_int;
+  for (int32_t c = 0; c < n_cells; ++c) {
+    const uint32_t n = (uint32_t)n_in[c];
+    const uint32_t inputs = (1u << n) - 1u;
+    const uint32_t all = n >= 31 ? 0xFFFFFFFFu : (2u << n) - 1u;
+    for (int32_t k = int_offsets[c]; k < int_offsets[c + 1]; ++k) {
+      const int32_t p = int_pin[k];
+      if (p < 0 || p >= (int32_t)n || int_edge[k] < -1 || int_edge[k] > 1)
+        return fail(ctx, GTP_EINVAL, "load_pattern_cells: internal pattern " + std::to_string(k) + ": bad pin or edge");
+      if ((int_care[k] & ~(inputs & ~(1u << p))) || (int_val[k] & ~int_care[k]))
+        return fail(ctx, GTP_EINVAL, "load_pattern_cells: internal pattern " + std::to_string(k) +
+                                         ": care must hold only other input pins, val only cared pins");
+    }
+    for (int32_t k = leak_offsets[c]; k < leak_offsets[c + 1]; ++k) {
+      if ((leak_care[k] & ~all) || (leak_val[k] & ~leak_care[k]))
+        return fail(ctx, GTP_EINVAL, "load_pattern_cells: leakage pattern " + std::to_string(k) +
+                                         ": care must hold only the cell's pins, val only cared pins");
+      uint32_t bits;
+      memcpy(&bits, leak_pw + k, 4);
+      lp[(size_t)k] = make_uint4(leak_care[k], leak_val[k], bits, 0u);
+    }
+    PatCell& pc = cells[(size_t)c];
+    pc.n_in = (int32_t)n;
+    pc.ipo = (int32_t)ipo.size();
+    for (uint32_t p = 0; p < n; ++p) {  // each pin's patterns, in list order
+      ipo.push_back((int32_t)ip.size());
+      for (int32_t k = int_offsets[c]; k < int_offsets[c + 1]; ++k)
+        if (int_pin[k] == (int32_t)p)
+          ip.push_back(make_uint4(int_care[k], int_val[k], (uint32_t)int_edge[k], (uint32_t)k));
+    }
+    ipo.push_back((int32_t)ip.size());
+    pc.lp0 = leak_offsets[c];
+    pc.lp1 = leak_offsets[c + 1];
+    pc.dtab = (int32_t)d0;
+    d0 += 2ll * n;
+    pc.leak_def = leak_default[c];
+    pc.iidx = pc.lidx = -1;
+  }
+  DeviceGuard dg(ctx->device);
+  CU(cudaStreamSynchronize(ctx->stream), "load_pattern_cells");
+  drop_graphs(ctx);
+  for (auto& kv : ctx->windows) kv.second.release_patterns();
+  ctx->pat_cells_ok = ctx->pat_net_ok = ctx->pat_index_ok = false;
+  CU(ctx->pc_cells.reserve(sizeof(PatCell) * cells.size()), "alloc pattern cells");
+  CU(ctx->pc_ip.reserve(sizeof(uint4) * std::max<size_t>(ip.size(), 1)), "alloc patterns");
+  CU(ctx->pc_ipo.reserve(sizeof(int32_t) * ipo.size()), "alloc patterns");
+  CU(ctx->pc_lp.reserve(sizeof(uint4) * std::max<size_t>(lp.size(), 1)), "alloc patterns");
+  CU(ctx->pc_tab.reserve(sizeof(float) * T * (size_t)(n_int + n_def)), "alloc pattern tables");
+  CU(cudaMemcpy(ctx->pc_cells.p, cells.data(), sizeof(PatCell) * cells.size(), cudaMemcpyHostToDevice), "copy cells");
+  if (!ip.empty()) CU(cudaMemcpy(ctx->pc_ip.p, ip.data(), sizeof(uint4) * ip.size(), cudaMemcpyHostToDevice), "copy");
+  CU(cudaMemcpy(ctx->pc_ipo.p, ipo.data(), sizeof(int32_t) * ipo.size(), cudaMemcpyHostToDevice), "copy patterns");
+  if (!lp.empty()) CU(cudaMemcpy(ctx->pc_lp.p, lp.data(), sizeof(uint4) * lp.size(), cudaMemcpyHostToDevice), "copy");
+  if (n_int > 0)
+    CU(cudaMemcpy(ctx->pc_tab.p, int_tab, sizeof(float) * T * (size_t)n_int, cudaMemcpyHostToDevice), "copy tables");
+  CU(cudaMemcpy(ctx->pc_tab.as<float>() + T * (size_t)n_int, int_default, sizeof(float) * T * (size_t)n_def,
+                cudaMemcpyHostToDevice), "copy default tables");
+  ctx->h_pat_cells = cells;
+  PatLib& P = ctx->P;
+  P = PatLib{};
+  P.cells = ctx->pc_cells.as<PatCell>();
+  P.ip = ctx->pc_ip.as<uint4>();
+  P.ipo = ctx->pc_ipo.as<int32_t>();
+  P.lp = ctx->pc_lp.as<uint4>();
+  P.tab = ctx->pc_tab.as<float>();
+  P.n_cells = n_cells;
+  P.ns = n_slew;
+  P.nl = n_load;
+  P.tsize = (int32_t)T;
+  P.half_v2 = 0.5f * vdd * vdd;
+  for (int i = 0; i < kMaxAxis; ++i) {
+    P.slew_axis[i] = slew_axis[std::min(i, n_slew - 1)];
+    P.load_axis[i] = load_axis[std::min(i, n_load - 1)];
+  }
+  ctx->pat_cells_ok = true;
+  return GTP_OK;
+}
+
+int gtp_load_pattern_netlist(gtp_ctx* ctx, int64_t n_gates, const int32_t* cell, const float* load_ff,
+                             const float* slew_ps, int32_t slew_stride, const float* out_slew_ps) {
+  if (!ctx) return GTP_EINVAL;
+  if (!ctx->pat_cells_ok) return fail(ctx, GTP_EINVAL, "load_pattern_netlist: load the pattern cells first");
+  if (n_gates <= 0 || n_gates >= (1ll << 31) || !cell || !load_ff || !slew_ps)
+    return fail(ctx, GTP_EINVAL, "load_pattern_netlist: need 1 <= n_gates < 2^31 and non-null arrays");
+  int32_t widest = 0;
+  for (int64_t g = 0; g < n_gates; ++g) {
+    if (cell[g] < 0 || cell[g] >= ctx->P.n_cells)
+      return fail(ctx, GTP_ERANGE, "load_pattern_netlist: cell index out of range at gate " + std::to_string(g));
+    widest = std::max(widest, ctx->h_pat_cells[(size_t)cell[g]].n_in);
+  }
+  if (slew_stride < widest || slew_stride > GTP_MAX_PATTERN_PINS)
+    return fail(ctx, GTP_EINVAL, "load_pattern_netlist: slew_stride must cover the widest cell (and be <= 32)");
+  DeviceGuard dg(ctx->device);
+  CU(cudaStreamSynchronize(ctx->stream), "load_pattern_netlist");
+  drop_graphs(ctx);
+  for (auto& kv : ctx->windows) kv.second.release_patterns();
+  ctx->pat_net_ok = false;
+  const size_t n = (size_t)n_gates;
+  CU(ctx->pn_cell.reserve(sizeof(int32_t) * n), "alloc pattern netlist");
+  CU(ctx->pn_load.reserve(sizeof(float) * n), "alloc pattern netlist");
+  CU(ctx->pn_slew.reserve(sizeof(float) * 2 * (size_t)slew_stride * n), "alloc pattern netlist");
+  CU(ctx->pn_oslew.reserve(sizeof(float) * 2 * n), "alloc pattern netlist");
+  CU(cudaMemcpy(ctx->pn_cell.p, cell, sizeof(int32_t) * n, cudaMemcpyHostToDevice), "copy pattern netlist");
+  CU(cudaMemcpy(ctx->pn_load.p, load_ff, sizeof(float) * n, cudaMemcpyHostToDevice), "copy pattern netlist");
+  CU(cudaMemcpy(ctx->pn_slew.p, slew_ps, sizeof(float) * 2 * (size_t)slew_stride * n, cudaMemcpyHostToDevice),
+     "copy pattern netlist");
+  if (out_slew_ps)
+    CU(cudaMemcpy(ctx->pn_oslew.p, out_slew_ps, sizeof(float) * 2 * n, cudaMemcpyHostToDevice), "copy out slews");
+  else
+    CU(cudaMemset(ctx->pn_oslew.p, 0, sizeof(float) * 2 * n), "zero out slews");
+  ctx->Q = PatNet{ctx->pn_cell.as<int32_t>(), ctx->pn_load.as<float>(), ctx->pn_slew.as<float>(),
+                  ctx->pn_oslew.as<float>(), n_gates, slew_stride};
+  ctx->pat_net_ok = true;
+  return GTP_OK;
+}
+
+int gtp_load_pattern_events(gtp_ctx* ctx, int32_t window, int64_t n_events, const int64_t* gate_offsets,
+                            const int32_t* t_ps, const uint8_t* pin, const uint8_t* value,
+                            const uint32_t* init_state, int flags) {
+  if (!ctx) return GTP_EINVAL;
+  if (!ctx->pat_net_ok) return fail(ctx, GTP_EINVAL, "load_pattern_events: load the pattern netlist first");
+  Window* W = get_window(ctx, window);
+  if (!W || W->streamed) return fail(ctx, GTP_EINVAL, "load_pattern_events: load the window's events first");
+  if (n_events < 0 || n_events >= (1ll << 40) || !gate_offsets || !init_state ||
+      (n_events > 0 && (!t_ps || !pin || !value)))
+    return fail(ctx, GTP_EINVAL, "load_pattern_events: need 0 <= n_events < 2^40 and non-null arrays");
+  DeviceGuard dg(ctx->device);
+  const int64_t G = ctx->Q.n_gates;
+  const bool dev = (flags & GTP_DEVICE) != 0;
+  CU(cudaStreamSynchronize(ctx->stream), "load_pattern_events");
+  drop_graphs(ctx);
+  W->release_patterns();
+  W->has_result = false;
+  std::vector<int64_t> off((size_t)G + 1);
+  std::vector<uint32_t> init((size_t)G);
+  CU(cudaMemcpy(off.data(), gate_offsets, sizeof(int64_t) * (G + 1), dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost),
+     "read pattern offsets");
+  CU(cudaMemcpy(init.data(), init_state, sizeof(uint32_t) * G, dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost),
+     "read initial states");
+  if (off[0] != 0 || off[(size_t)G] != n_events)
+    return fail(ctx, GTP_EINVAL, "load_pattern_events: offsets must run from 0 to n_events");
+  std::vector<int2> items;
+  std::vector<int64_t> first((size_t)G + 1);
+  std::vector<int32_t> cell((size_t)G);
+  CU(cudaMemcpy(cell.data(), ctx->pn_cell.p, sizeof(int32_t) * G, cudaMemcpyDeviceToHost), "read pattern cells");
+  for (int64_t g = 0; g < G; ++g) {
+    if (off[(size_t)g + 1] < off[(size_t)g])
+      return fail(ctx, GTP_EINVAL, "load_pattern_events: offsets decrease at gate " + std::to_string(g));
+    const int n_in = ctx->h_pat_cells[(size_t)cell[(size_t)g]].n_in;
+    if (n_in < 31 && (init[(size_t)g] >> (n_in + 1)))
+      return fail(ctx, GTP_ERANGE, "load_pattern_events: initial state has bits past the pins at gate " +
+                                       std::to_string(g));
+    first[(size_t)g] = (int64_t)items.size();
+    const int64_t n = off[(size_t)g + 1] - off[(size_t)g];
+    for (int64_t k = 0; k * kPatPiece < n; ++k) items.push_back(make_int2((int)g, (int)k));
+  }
+  first[(size_t)G] = (int64_t)items.size();
+  const size_t ni = std::max<size_t>(items.size(), 1);
+  CU(W->pat_off.reserve(sizeof(int64_t) * (G + 1)), "alloc pattern events");
+  CU(W->pat_rec.reserve(sizeof(uint2) * (size_t)std::max<int64_t>(n_events, 1)), "alloc pattern events");
+  CU(W->pat_init.reserve(sizeof(uint32_t) * G), "alloc pattern events");
+  CU(W->pat_items.reserve(sizeof(int2) * ni), "alloc pattern items");
+  CU(W->pat_first.reserve(sizeof(int64_t) * (G + 1)), "alloc pattern items");
+  CU(W->pat_mask.reserve(sizeof(uint32_t) * ni), "alloc pattern items");
+  for (DevBuf* b : {&W->pat_e_leak, &W->pat_e_int, &W->pat_e_sw, &W->pat_e_gl})
+    CU(b->reserve(sizeof(double) * G), "alloc pattern results");
+  CU(W->pat_final.reserve(sizeof(uint32_t) * G), "alloc pattern results");
+  CU(cudaMemcpy(W->pat_off.p, off.data(), sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice), "copy offsets");
+  CU(cudaMemcpy(W->pat_init.p, init.data(), sizeof(uint32_t) * G, cudaMemcpyHostToDevice), "copy initial states");
+  if (!items.empty())
+    CU(cudaMemcpy(W->pat_items.p, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice), "copy items");
+  CU(cudaMemcpy(W->pat_first.p, first.data(), sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice), "copy items");
+  if (n_events > 0) {
+    if (dev) {
+      CU(launch_pattern_pack(t_ps, pin, value, n_events, W->pat_rec.as<uint2>(), ctx->stream), "pack records");
+      ctx->launches += 1;
+      CU(cudaStreamSynchronize(ctx->stream), "pack records");
+    } else {
+      std::vector<uint2> rec((size_t)n_events);
+      for (int64_t i = 0; i < n_events; ++i)
+        rec[(size_t)i] = make_uint2((uint32_t)t_ps[i], (uint32_t)pin[i] | (value[i] > 1 ? 0x200u : (uint32_t)value[i] << 8));
+      CU(cudaMemcpy(W->pat_rec.p, rec.data(), sizeof(uint2) * (size_t)n_events, cudaMemcpyHostToDevice), "copy records");
+    }
+  }
+  W->pat_h_off = std::move(off);
+  W->pat_n_events = n_events;
+  W->pat_n_items = (int64_t)items.size();
+  W->pat_loaded = true;
+  return GTP_OK;
+}
+
+int gtp_pattern_gate_energy(gtp_ctx* ctx, int32_t window, double* e_leak, double* e_int, double* e_sw, double* e_gl,
+                            int64_t* n_events, uint32_t* final_state, int flags) {
+  if (!ctx) return GTP_EINVAL;
+  Window* W = get_window(ctx, window);
+  if (!W || !W->has_result || !W->pat_loaded || !ctx->pat_net_ok)
+    return fail(ctx, GTP_EINVAL, "pattern_gate_energy: no pattern gate result for this window");
+  DeviceGuard dg(ctx->device);
+  const size_t G = (size_t)ctx->Q.n_gates;
+  const cudaMemcpyKind k = kind_out(flags);
+  if (e_leak) CU(cudaMemcpyAsync(e_leak, W->pat_e_leak.p, sizeof(double) * G, k, ctx->stream), "copy e_leak");
+  if (e_int) CU(cudaMemcpyAsync(e_int, W->pat_e_int.p, sizeof(double) * G, k, ctx->stream), "copy e_int");
+  if (e_sw) CU(cudaMemcpyAsync(e_sw, W->pat_e_sw.p, sizeof(double) * G, k, ctx->stream), "copy e_sw");
+  if (e_gl) CU(cudaMemcpyAsync(e_gl, W->pat_e_gl.p, sizeof(double) * G, k, ctx->stream), "copy e_gl");
+  if (final_state)
+    CU(cudaMemcpyAsync(final_state, W->pat_final.p, sizeof(uint32_t) * G, k, ctx->stream), "copy final state");
+  std::vector<int64_t> cnt;
+  if (n_events) {
+    cnt.resize(G);
+    for (size_t g = 0; g < G; ++g) cnt[g] = W->pat_h_off[g + 1] - W->pat_h_off[g];
+    CU(cudaMemcpyAsync(n_events, cnt.data(), sizeof(int64_t) * G,
+                       (flags & GTP_DEVICE) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, ctx->stream),
+       "copy counts");
+  }
+  CU(cudaStreamSynchronize(ctx->stream), "pattern_gate_energy");
+  return GTP_OK;
+}
+
 int gtp_set_param(gtp_ctx* ctx, const char* key, int64_t value) {
   if (!ctx || !key) return GTP_EINVAL;
   const std::string k(key);
@@ -1613,6 +2016,11 @@ int gtp_set_param(gtp_ctx* ctx, const char* key, int64_t value) {
     ctx->p_dense_min = value < 0 ? 256 : value;
   } else if (k == "piece_len") {
     ctx->p_piece_len = value < 0 ? -1 : value;
+  } else if (k == "sipl_max_pins") {
+    if (value > GTP_MAX_INDEXED_PINS) return fail(ctx, GTP_ERANGE, "sipl_max_pins must be <= 24");
+    const int64_t v = value < 0 ? 16 : value;
+    if (v != ctx->p_sipl_max_pins) ctx->pat_index_ok = false;
+    ctx->p_sipl_max_pins = v;
   } else if (k == "group_bin_bytes") {
     ctx->p_group_bytes = value < 0 ? kGroupBinBytes : value;
   } else if (k == "tile_min") {
@@ -1653,6 +2061,9 @@ int64_t gtp_get_param(const gtp_ctx* ctx, const char* key) {
   if (k == "piece_len") return ctx->p_piece_len;
   if (k == "run_piece_len") return ctx->run_piece_len;
   if (k == "group_bin_bytes") return ctx->p_group_bytes;
+  if (k == "sipl_max_pins") return ctx->p_sipl_max_pins;
+  if (k == "pattern_indexed_cells") return ctx->pat_index_ok ? ctx->pat_indexed : -1;
+  if (k == "pattern_index_bytes") return ctx->pat_index_ok ? ctx->pat_index_bytes : -1;
   if (k == "run_groups") return (int64_t)ctx->run_groups.size();
   if (k == "t_tiled_ns") return ctx->t_ns[4];
   if (k == "scheme_evt_tgt") return ctx->p_evt_tgt;

@@ -75,6 +75,44 @@ struct NetView {
   const float* out_slew;
 };
 
+// Pattern cells: cells given by state patterns, up to 32 pins (Sec. 4.1's
+// fallback for wide cells).  A cell's internal patterns are stored per pin,
+// in list order within the pin (the first match of the pin's list is the
+// first match of the whole list: the other pins' patterns never match).
+struct PatCell {
+  int32_t n_in;      // input pins; the output pin is pin n_in
+  int32_t ipo;       // first of the cell's n_in + 1 entries of PatLib::ipo
+  int32_t lp0, lp1;  // leakage patterns [lp0, lp1) of PatLib::lp
+  int32_t dtab;      // default table of (pin, edge): dtab + 2 * pin + edge
+  float leak_def;    // default leakage, nW
+  int64_t iidx;      // state-indexed table ids [n_in][2][2^(n_in-1)] at PatLib::iidx + iidx, or -1: traversal
+  int64_t lidx;      // state-indexed leakage [2^(n_in+1)] at PatLib::lidx + lidx, or -1: traversal
+};
+
+struct PatLib {
+  const PatCell* cells;
+  const uint4* ip;           // {care, val, edge (0xFFFFFFFF: either), table}
+  const int32_t* ipo;        // per cell, n_in + 1 offsets into ip (pin p: [ipo[p], ipo[p + 1]))
+  const uint4* lp;           // {care, val, power (float bits, nW), 0}
+  const float* tab;          // [n_tab][ns * nl] fJ: the patterns' tables, then the defaults
+  const int32_t* iidx;       // state-indexed table ids of the indexed cells
+  const float* lidx;         // state-indexed leakage of the indexed cells
+  int32_t n_cells;
+  int32_t ns, nl, tsize;
+  float half_v2;             // 0.5 * Vdd^2
+  float slew_axis[kMaxAxis];
+  float load_axis[kMaxAxis];
+};
+
+struct PatNet {
+  const int32_t* cell;       // [Gp]
+  const float* load;         // [Gp] fF
+  const float* slew;         // [Gp][stride][2] input transition times, ps
+  const float* oslew;        // [Gp][2] output {fall, rise} transition times, ps
+  int64_t n_gates;
+  int32_t stride;
+};
+
 // First failure seen by a kernel: code and record index.
 struct DevError {
   int32_t code;
@@ -118,6 +156,19 @@ struct WinDesc {
   float g_total;             // adjoint: G(window_ps)
   int32_t keep_bins;         // the preparation pass leaves the bins as they are (a streamed run's later chunks)
   int32_t cpack;             // layout of cbins (see there)
+  // the window's pattern gates (p_n_items == 0: none), walked into tbins
+  const int64_t* p_off;      // [Gp + 1]
+  const uint2* p_rec;        // [Ep] {t, pin | value << 8}
+  const uint32_t* p_init;    // [Gp]
+  const int2* p_items;       // [p_n_items] {gate, piece}: the gate's records from piece * kPatPiece on
+  const int64_t* p_first;    // [Gp + 1] first item of each gate
+  uint32_t* p_mask;          // [p_n_items] XOR of the pin bits of each item's records
+  double* p_e_leak;          // [Gp]
+  double* p_e_int;
+  double* p_e_sw;
+  double* p_e_gl;
+  uint32_t* p_final;         // [Gp]
+  int64_t p_n_items;
 };
 
 // ------------------------------------------------------------------ device helpers
@@ -271,6 +322,19 @@ cudaError_t launch_validate(const LibView& L, const NetView& N, const WinDesc* w
 cudaError_t launch_validate_if(const LibView& L, const NetView& N, const WinDesc* win, const DevError* err,
                                int64_t n_gates, unsigned long long* first, cudaStream_t st);
 int merge_tiles(int n_bins);
+// Pattern gates: a gate's records are cut into items of kPatPiece records
+// (each item extended to the end of the timestamp group it ends in).
+constexpr int64_t kPatPiece = 2048;
+// Pattern records {t, pin | value << 8} from the ABI's arrays (device).
+cudaError_t launch_pattern_pack(const int32_t* t, const uint8_t* pin, const uint8_t* value, int64_t n, uint2* out,
+                                cudaStream_t st);
+// State-indexed arrays of pattern cell c (its iidx / lidx set).
+cudaError_t launch_pattern_index(const PatLib& P, int32_t c, int32_t n_in, cudaStream_t st);
+// The pattern gates of the windows: initial leakage, items' pin masks, and
+// the walk into each window's tbins; errors as the smallest key
+// ((window << 40 | record) << 3) | -code in *bad (see launch_validate).
+cudaError_t launch_pattern_walk(const PatLib& P, const PatNet& Q, const WinDesc* wins, int n_win,
+                                int64_t max_items, int32_t clock_ps, unsigned long long* bad, cudaStream_t st);
 // The reduction-rate probe: n_red reductions of `width` (2 or 4) floats into
 // hashed places of slots[n_slots] (16 B a slot).
 cudaError_t launch_red_probe(float4* slots, uint32_t n_slots, int width, int64_t n_red, int n_sm, cudaStream_t st);

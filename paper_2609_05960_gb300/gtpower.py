@@ -21,6 +21,8 @@ GTP_ENOMEM, GTP_ECUDA, GTP_ETIMEOUT, GTP_EDEVICE = -5, -6, -7, -8
 GTP_HOST, GTP_DEVICE, GTP_BORROW, GTP_GRAPH, GTP_PACKED = 0, 1, 2, 4, 8
 GTP_NOALLOC_MAX_BINS = 1 << 19
 GTP_MAX_PINS = 8
+GTP_MAX_PATTERN_PINS = 32
+GTP_MAX_INDEXED_PINS = 24
 
 CODE_NAMES = {GTP_EINVAL: "EINVAL", GTP_EORDER: "EORDER", GTP_ERANGE: "ERANGE", GTP_ENOTOGGLE: "ENOTOGGLE",
               GTP_ENOMEM: "ENOMEM", GTP_ECUDA: "ECUDA", GTP_ETIMEOUT: "ETIMEOUT", GTP_EDEVICE: "EDEVICE"}
@@ -32,7 +34,8 @@ ABI_SYMBOLS = ["gtp_create", "gtp_destroy", "gtp_set_stream", "gtp_last_error", 
                "gtp_set_param", "gtp_get_param", "gtp_run_power_noalloc", "gtp_set_glitch", "gtp_gate_glitch",
                "gtp_run_power_streamed", "gtp_design_power", "gtp_run_power_components",
                "gtp_run_power_scheme", "gtp_sipl_expand",
-               "gtp_pack_events", "gtp_measure_reductions"]
+               "gtp_pack_events", "gtp_measure_reductions", "gtp_load_pattern_cells", "gtp_load_pattern_netlist",
+               "gtp_load_pattern_events", "gtp_pattern_gate_energy"]
 
 
 class GtpError(RuntimeError):
@@ -79,6 +82,10 @@ def load(path: str = LIB_PATH):
         "gtp_autotune": ([P, I32, P, I32, I32, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "gtp_set_param": ([P, ctypes.c_char_p, I64], ctypes.c_int),
         "gtp_get_param": ([P, ctypes.c_char_p], I64),
+        "gtp_load_pattern_cells": ([P, I32, P, F, I32, P, I32, P] + [P] * 12, ctypes.c_int),
+        "gtp_load_pattern_netlist": ([P, I64, P, P, P, I32, P], ctypes.c_int),
+        "gtp_load_pattern_events": ([P, I32, I64, P, P, P, P, P, ctypes.c_int], ctypes.c_int),
+        "gtp_pattern_gate_energy": ([P, I32, P, P, P, P, P, P, ctypes.c_int], ctypes.c_int),
         "gtp_run_power_noalloc": ([P, I32, P, F, I32, P, I32, P, P, I64, P, I64, I64, P, P, P, I32, I64, I64, P, P, P,
                                    I32, P, P, P, P, P], ctypes.c_int),
     }
@@ -305,6 +312,62 @@ def gtp_sipl_expand(n_in: int, n_slew: int, n_load: int, int_patterns, int_defau
     return e_int, p_leak
 
 
+def gtp_load_pattern_cells(ctx, plib) -> None:
+    """Pattern cells from a synth.patterns.PatternLibrary-shaped object."""
+    ns, nl = len(plib.slew_axis), len(plib.load_axis)
+    a = dict(n_in=np.ascontiguousarray(plib.n_in, np.int32), sa=np.ascontiguousarray(plib.slew_axis, np.float32),
+             la=np.ascontiguousarray(plib.load_axis, np.float32),
+             io=np.ascontiguousarray(plib.int_offsets, np.int32), ip=np.ascontiguousarray(plib.int_pin, np.int32),
+             ie=np.ascontiguousarray(plib.int_edge, np.int32), ic=np.ascontiguousarray(plib.int_care, np.uint32),
+             iv=np.ascontiguousarray(plib.int_val, np.uint32),
+             it=np.ascontiguousarray(np.asarray(plib.int_tab, np.float32).reshape(-1, ns * nl)),
+             idf=np.ascontiguousarray(np.asarray(plib.int_default, np.float32).reshape(-1)),
+             lo=np.ascontiguousarray(plib.leak_offsets, np.int32), lc=np.ascontiguousarray(plib.leak_care, np.uint32),
+             lv=np.ascontiguousarray(plib.leak_val, np.uint32), lp=np.ascontiguousarray(plib.leak_pw, np.float32),
+             ld=np.ascontiguousarray(plib.leak_default, np.float32))
+    ptr = lambda x: x.ctypes.data if x.size else None
+    _check(ctx, load().gtp_load_pattern_cells(
+        ctx, len(a["n_in"]), ptr(a["n_in"]), float(plib.vdd), ns, ptr(a["sa"]), nl, ptr(a["la"]), ptr(a["io"]),
+        ptr(a["ip"]), ptr(a["ie"]), ptr(a["ic"]), ptr(a["iv"]), ptr(a["it"]), ptr(a["idf"]), ptr(a["lo"]),
+        ptr(a["lc"]), ptr(a["lv"]), ptr(a["lp"]), ptr(a["ld"])))
+
+
+def gtp_load_pattern_netlist(ctx, pnet) -> None:
+    """Pattern gates from a synth.patterns.PatternNetlist-shaped object."""
+    cell = np.ascontiguousarray(pnet.cell, np.int32)
+    load_ff = np.ascontiguousarray(pnet.load_ff, np.float32)
+    slew = np.ascontiguousarray(pnet.slew_ps, np.float32)
+    oslew = None if getattr(pnet, "out_slew_ps", None) is None else np.ascontiguousarray(pnet.out_slew_ps, np.float32)
+    _check(ctx, load().gtp_load_pattern_netlist(ctx, len(cell), cell.ctypes.data, load_ff.ctypes.data,
+                                                slew.ctypes.data, int(slew.shape[1]),
+                                                None if oslew is None else oslew.ctypes.data))
+
+
+def gtp_load_pattern_events(ctx, window: int, gate_offsets, t_ps, pin, value, init_state) -> None:
+    """A window's pattern-gate events (host arrays or CUDA tensors, all alike)."""
+    po, fo, ko = _ptr_flags(gate_offsets, np.int64)
+    pt, ft, kt = _ptr_flags(t_ps, np.int32)
+    pp, fp, kp = _ptr_flags(pin, np.uint8)
+    pv, fv, kv = _ptr_flags(value, np.uint8)
+    pi, fi, ki = _ptr_flags(init_state, np.uint32)
+    if len({fo, ft, fp, fv, fi}) > 1:
+        raise ValueError("pattern event arrays must all be host or all be device")
+    n = int(t_ps.shape[0]) if hasattr(t_ps, "shape") else len(t_ps)
+    _check(ctx, load().gtp_load_pattern_events(ctx, int(window), n, po, pt if n else None, pp if n else None,
+                                               pv if n else None, pi, fo))
+
+
+def gtp_pattern_gate_energy(ctx, window: int, e_leak=None, e_int=None, e_sw=None, e_gl=None, n_events=None,
+                            final_state=None) -> None:
+    args = [_ptr_flags(e_leak, np.float64), _ptr_flags(e_int, np.float64), _ptr_flags(e_sw, np.float64),
+            _ptr_flags(e_gl, np.float64), _ptr_flags(n_events, np.int64), _ptr_flags(final_state, np.uint32)]
+    flags = {a[1] for a in args if a[0] is not None}
+    if len(flags) > 1:
+        raise ValueError("outputs must all be host or all be device")
+    f = flags.pop() if flags else GTP_HOST
+    _check(ctx, load().gtp_pattern_gate_energy(ctx, int(window), *[a[0] for a in args], f))
+
+
 SCHEMES = {"naive": 0, "sipl": 1, "density": 2, "fused": 3}
 
 
@@ -470,6 +533,7 @@ class Engine:
         self.stream = stream
         self.ctx = gtp_create(device, stream.cuda_stream)
         self.n_gates = 0
+        self.n_pattern_gates = 0
         self.n_cells = 0
         self.windows: Dict[int, dict] = {}
 
@@ -510,6 +574,40 @@ class Engine:
         out = (torch.empty(self.n_gates, dtype=torch.float64, device=self.device) if device
                else np.empty(self.n_gates))
         gtp_gate_glitch(self.ctx, window, out)
+        return out
+
+    def load_pattern_cells(self, plib) -> None:
+        gtp_load_pattern_cells(self.ctx, plib)
+
+    def load_pattern_netlist(self, pnet) -> None:
+        gtp_load_pattern_netlist(self.ctx, pnet)
+        self.n_pattern_gates = len(pnet.cell)
+
+    def load_pattern_events(self, window: int, ptrace=None, *, offsets=None, t_ps=None, pin=None, value=None,
+                            init_state=None) -> None:
+        """A window's pattern-gate events from a synth.patterns.PatternTrace
+        or explicit arrays (load the window's ordinary events first)."""
+        if ptrace is not None:
+            offsets, t_ps, pin, value, init_state = (ptrace.offsets, ptrace.t_ps, ptrace.pin, ptrace.value,
+                                                     ptrace.init_state)
+        gtp_load_pattern_events(self.ctx, window, offsets, t_ps, pin, value, init_state)
+
+    def pattern_gate_energy(self, window: int, device: bool = False) -> Dict[str, object]:
+        """Per-pattern-gate results of the window's last run (numpy, or CUDA
+        tensors with device=True)."""
+        n = self.n_pattern_gates
+        if device:
+            import torch
+            out = {k: torch.empty(n, dtype=torch.float64, device=self.device) for k in ("e_leak", "e_int", "e_sw",
+                                                                                        "e_gl")}
+            out["n_events"] = torch.empty(n, dtype=torch.int64, device=self.device)
+            out["final_state"] = torch.empty(n, dtype=torch.int32, device=self.device)
+        else:
+            out = {k: np.empty(n) for k in ("e_leak", "e_int", "e_sw", "e_gl")}
+            out["n_events"] = np.empty(n, np.int64)
+            out["final_state"] = np.empty(n, np.uint32)
+        gtp_pattern_gate_energy(self.ctx, window, out["e_leak"], out["e_int"], out["e_sw"], out["e_gl"],
+                                out["n_events"], out["final_state"])
         return out
 
     def load_events(self, window: int, trace=None, *, window_ps=None, offsets=None, records=None, init_state=None,
