@@ -36,11 +36,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "events/sec and % of HBM roofline; batched and adjoint vs plain kernel"
-# DRAM bytes (read + write) of one walk launch (k_walk<8,0,0,0>) on the full large workload with
+# DRAM bytes (read + write) of one walk launch (k_walk<8,0,0,0,0>, the build without pieces) on the full large workload with
 # the default plan, from one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum (one
 # pass); reported as roofline.traffic for that workload and plan only, and to be captured again
 # whenever the walk changes
-WALK_TRAFFIC = {("large", 8, 256): 2_020_312_000 + 80_774_912}
+WALK_TRAFFIC = {("large", 8, 256): 2_020_797_184 + 81_159_680}
 UNIT = "events/s"
 
 
@@ -61,17 +61,21 @@ def parse():
     p.add_argument("--no-oracle-check", action="store_true",
                    help="skip the FP64 oracle over every bin and gate of each measured workload")
     p.add_argument("--no-stress", action="store_true", help="skip the stress workload (10M gates, 2B events)")
+    p.add_argument("--no-patterns", action="store_true", help="skip the pattern-gate threshold sweep")
     p.add_argument("--events", type=int, default=0,
                    help="scale the configuration to this many events (same gates and distribution; "
                         "for profiling a smaller case)")
-    p.add_argument("--sweep", default="", choices=["", "contention", "streamed", "schemes", "adjoint", "glitch"],
+    p.add_argument("--sweep", default="", choices=["", "contention", "streamed", "schemes", "adjoint", "glitch", "tiled",
+                                                    "patterns"],
                    help="contention: uniform high activity (1, 2, 4, 8 events per gate per 1k bins); "
                         "streamed: the large window streamed from pinned host memory in 1-32 chunks, "
                         "against a plain copy of its records; schemes: the paper's GPU schemes (naive, "
                         "state-indexed lookup, density-aware partitioning, fused kernel) against this "
                         "engine's walk; adjoint: the adjoint workload's forward and backward alone (--events "
                         "scales it); glitch: the large workload's plain walk, then with glitch detection (--events "
-                        "scales it); instead of the default run, one JSON line per case")
+                        "scales it); tiled: the large workload with the time-sliced walk at tile_min 0, 32768, "
+                        "8192, 2048; patterns: the pattern-gate pin-threshold study alone; instead of the "
+                        "default run, one JSON line per case")
     return p.parse_args()
 
 
@@ -478,6 +482,8 @@ def run_ours(args, cfg_name):
         extras["load_change"] = measure_load_change(eng, dev, cfg, wave, n_ev, ms_max / args.steps, xs, net.load_ff)
         extras["glitch"] = measure_glitch(eng, dev, cfg, wave, walk_s * 1e3, n_ev, xs, opool, wl_large)
         extras["components"] = measure_components(eng, dev, cfg, walk_s * 1e3, n_ev, xs, opool, wl_large)
+        if not args.no_patterns:
+            extras["patterns"] = measure_patterns(eng, dev, cfg, wave, n_ev, xs)
         del rec
         torch.cuda.empty_cache()
         extras["batched"] = measure_batched(eng, dev, xs, peak, value, opool)
@@ -663,6 +669,95 @@ def measure_batched(eng, dev, steps, peak, plain_value, opool=None):
             "separate_runs_ms": ms_p, "speedup_vs_separate_runs": ms_p / ms_b,
             "max_rel_diff_vs_separate_runs": diff, "oracle_error": err, "autotuned_plan": plan,
             "autotune_best_ms": tuned_ms, "graph": True}
+
+
+# pattern gates beside the large window: cells of 5 to 21 pins given by state patterns
+PATTERN_GATES = 2_000
+PATTERN_EVENTS = 6_000_000
+PATTERN_WEIGHTS = [0.0, 0.25, 0.2, 0.2, 0.15, 0.1, 0.05, 0.05]  # over synth.patterns.PATTERN_CELLS (4-pin AOI3P: none)
+
+
+def measure_patterns(eng, dev, cfg, wave, n_ev, steps):
+    """The large window (slot 0) plus 2,000 gates of wide cells given by
+    state patterns (0.2 % of the gates) carrying 6M events (3 %), and the
+    state-indexed threshold swept in the spirit of the paper's pin-threshold
+    study (Sec. 6.4.1: thresholds 4 to 32): per threshold, the share of gates
+    and events that take the traversal fallback, the pattern walk's time,
+    the run's time against the plain window, and the index memory.  Every
+    threshold gives the same per-gate results; sampled pattern gates are
+    checked against the oracle (oracle/patterns.py)."""
+    import torch
+
+    from oracle import patterns as opat
+    from paper_2609_05960_gb300 import gtpower
+    from synth import patterns as spat
+
+    plib = spat.make_pattern_library(cfg.seed_lib)
+    pnet = spat.make_pattern_netlist(plib, PATTERN_GATES, seed=cfg.seed_net, weights=PATTERN_WEIGHTS)
+    counts = synth_zipf(PATTERN_GATES, PATTERN_EVENTS, 1.2, 100_000, cfg.seed_ev + 100)
+    ptr = spat.make_pattern_trace(pnet, counts, cfg.window_ps, cfg.seed_ev + 100, tie_p=0.02, clock_pin_share=0.3)
+    run = lambda: gtpower.gtp_run_power(eng.ctx, 0, cfg.bin_ps, wave, graph=True)
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize(dev)
+    plain_run_ms = _events_per_s(run, steps, dev)
+    eng.load_pattern_cells(plib)
+    eng.load_pattern_netlist(pnet)
+    eng.load_pattern_events(0, ptr)
+    pins = (plib.n_in + 1)[pnet.cell]
+    G_all = eng.n_gates + PATTERN_GATES
+    E_all = n_ev + PATTERN_EVENTS
+    # oracle sample: a few gates of every cell, about 150k events
+    rng = np.random.default_rng(11)
+    sample = []
+    for c in range(plib.n_cells):
+        idx = np.flatnonzero(pnet.cell == c)
+        idx = idx[counts[idx] <= 40_000]
+        sample += list(rng.choice(idx, size=min(8, len(idx)), replace=False)) if len(idx) else []
+    sample = np.sort(np.array(sample, np.int64))
+    ref = opat.walk(plib, pnet, ptr, cfg.bin_ps, gates=sample)
+    rows, first = [], None
+    for thr in (0, 4, 8, 12, 16, 20, 24):
+        eng.set_param("sipl_max_pins", thr)
+        for _ in range(3):
+            run()
+        torch.cuda.synchronize(dev)
+        eng.set_param("timing", 1)
+        ms = _events_per_s(run, steps, dev)
+        n_t = max(eng.get_param("n_timed"), 1)
+        pat_ms = eng.get_param("t_pattern_ns") * 1e-6 / n_t
+        eng.set_param("timing", 0)
+        pe = eng.pattern_gate_energy(0)
+        err = {k: float(np.max(np.abs(pe[k][sample] - ref[k]) / np.maximum(np.abs(ref[k]), 1e-4)))
+               for k in ("e_leak", "e_int", "e_sw")}
+        err["count_mismatches"] = int(np.sum(pe["n_events"][sample] != ref["n_events"]))
+        err["state_mismatches"] = int(np.sum(pe["final_state"][sample] != ref["final_state"]))
+        if first is None:
+            first = pe
+        fb = pins > thr
+        rows.append({"sipl_max_pins": thr, "fallback_gates": int(fb.sum()),
+                     "fallback_gate_share": float(fb.sum()) / G_all,
+                     "fallback_event_share": float(counts[fb].sum()) / E_all,
+                     "pattern_walk_ms": pat_ms, "pattern_events_per_s": PATTERN_EVENTS / (pat_ms * 1e-3),
+                     "ms_per_run": ms, "over_plain_run": ms / plain_run_ms,
+                     "indexed_cells": eng.get_param("pattern_indexed_cells"),
+                     "index_bytes": eng.get_param("pattern_index_bytes"),
+                     "max_rel_diff_vs_threshold_0": float(max(
+                         np.max(np.abs(pe[k] - first[k]) / np.maximum(np.abs(first[k]), 1e-4))
+                         for k in ("e_leak", "e_int", "e_sw"))),
+                     "oracle_error_sampled_gates": err})
+    eng.set_param("sipl_max_pins", -1)
+    return {"workload": f"the large window plus {PATTERN_GATES:,} pattern gates (cells of 5-21 pins: "
+                        f"5 25%, 6 20%, 9 20%, 12 15%, 16 10%, 20 5%, 21 5%) carrying {PATTERN_EVENTS:,} events "
+                        f"(Zipf 1.2, cap 1e5, clock pin 30%, ties 2%)",
+            "oracle_sample": f"{len(sample)} pattern gates, {int(counts[sample].sum()):,} events, per-gate results",
+            "plain_run_ms": plain_run_ms,
+            "sweep": rows}
+
+
+def synth_zipf(n, total, s, cap, seed):
+    import synth
+    return synth.zipf_counts(n, total, s, cap, seed)
 
 
 def measure_glitch(eng, dev, cfg, wave, walk_plain_ms, n_ev, steps, opool=None, wl=None):
@@ -1112,8 +1207,72 @@ def run_glitch_sweep(args):
     eng.close()
 
 
+def _large_engine(args):
+    """(engine, device, config, waveform tensor, events) with the large
+    workload (scaled by --events) loaded in window 0 from device records."""
+    import torch
+
+    import synth
+    from paper_2609_05960_gb300 import Engine
+
+    dev = torch.device("cuda", 0)
+    cfg = config_of(args, "large")
+    lib = synth.make_library(cfg.seed_lib)
+    net = synth.make_netlist(lib, cfg.n_gates, cfg.seed_net)
+    counts = synth.zipf_counts(cfg.n_gates, cfg.n_events, cfg.zipf_s, cfg.cap, cfg.seed_ev)
+    tr, rec = synth.make_trace_gpu(net, counts, cfg.window_ps, cfg.seed_ev, cfg.tie_p, device=dev)
+    eng = Engine(0)
+    eng.load_library(lib)
+    eng.load_netlist(net)
+    eng.load_events(0, window_ps=cfg.window_ps, offsets=torch.from_numpy(tr.offsets).to(dev), records=rec,
+                    init_state=torch.from_numpy(tr.init_state).to(dev), borrow=True)
+    eng._keep = rec
+    wave = torch.empty(cfg.window_ps // cfg.bin_ps, dtype=torch.float64, device=dev)
+    return eng, dev, cfg, wave, int(tr.n_events)
+
+
+def run_tiled_sweep(args):
+    """The time-sliced walk (tile_min) on the large workload: walk time and
+    the tiled part's time per threshold (0 = off, the default)."""
+    import torch
+
+    from paper_2609_05960_gb300 import gtpower
+
+    eng, dev, cfg, wave, n = _large_engine(args)
+    steps = max(1, min(args.steps, 20))
+    run = lambda: gtpower.gtp_run_power(eng.ctx, 0, cfg.bin_ps, wave, graph=True)
+    for tmin in (0, 32768, 8192, 2048):
+        eng.set_param("tile_min", tmin)
+        for _ in range(3):
+            run()
+        torch.cuda.synchronize(dev)
+        eng.set_param("timing", 1)
+        ms = _events_per_s(run, steps, dev)
+        k = max(eng.get_param("n_timed"), 1)
+        print(json.dumps({"sweep": "tiled", "tile_min": tmin, "ms_per_run": ms,
+                          "walk_ms": eng.get_param("t_walk_ns") * 1e-6 / k,
+                          "tiled_ms": eng.get_param("t_tiled_ns") * 1e-6 / k if tmin else 0.0, "events": n}),
+              flush=True)
+        eng.set_param("timing", 0)
+    eng.close()
+
+
+def run_patterns_sweep(args):
+    """The pattern-gate threshold study alone (bench extra `patterns`)."""
+    eng, dev, cfg, wave, n = _large_engine(args)
+    out = measure_patterns(eng, dev, cfg, wave, n, max(3, min(args.steps, 10)))
+    print(json.dumps({"sweep": "patterns", **out}), flush=True)
+    eng.close()
+
+
 def main():
     args = parse()
+    if args.sweep == "tiled":
+        run_tiled_sweep(args)
+        return
+    if args.sweep == "patterns":
+        run_patterns_sweep(args)
+        return
     if args.sweep == "glitch":
         run_glitch_sweep(args)
         return

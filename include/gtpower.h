@@ -534,7 +534,8 @@ int gtp_measure_reductions(gtp_ctx* ctx, int32_t n_slots, int32_t width, int64_t
  * records leave, so that one very busy gate cannot hold up a run; -1 = chosen
  * per run: at least 65,536 and about a sixth of an SM's even share of the
  * run's events, the default; 0 = never; other values round up to a multiple
- * of 4,096),
+ * of 4,096; gtp_get_param "run_piece_len" and "run_whole" (1: no gate of
+ * the last run was split) report the last run's choice),
  * "sipl_max_pins" (pattern cells with at most this many pins are walked
  * through state-indexed arrays, wider ones by pattern traversal; 0..24,
  * default 16; gtp_get_param "pattern_indexed_cells" and
@@ -556,7 +557,8 @@ int gtp_measure_reductions(gtp_ctx* ctx, int32_t n_slots, int32_t width, int64_t
  * phases of later runs with CUDA events; read back with gtp_get_param keys
  * "t_gate_pass_ns" (the preparation launch: bins cleared, gate pass and
  * work-list histogram), "t_plan_ns" (work-list scatter), "t_walk_ns",
- * "t_merge_ns", "n_timed", and "launches" = kernels launched since timing
+ * "t_merge_ns", "t_pattern_ns" (the pattern gates' walk, also inside
+ * "t_walk_ns"), "n_timed", and "launches" = kernels launched since timing
  * was last set). */
 int gtp_set_param(gtp_ctx* ctx, const char* key, int64_t value);
 int64_t gtp_get_param(const gtp_ctx* ctx, const char* key);

@@ -21,6 +21,7 @@ using namespace gtp;
 namespace {
 
 constexpr int kMaxWindows = 1024;
+constexpr size_t kStatusBytes = sizeof(DevError) + 16;  // DevError, then a 64-bit count
 // Default bin bytes (8 a bin) of the windows one walk launch reduces into
 // at most, unless a single window has more: well inside the 129 MB L2,
 // beside the records streaming through it.
@@ -66,6 +67,7 @@ struct Window {
   bool streamed = false;       // filled by a streamed run: results only, no resident records
   int32_t last_bin_ps = 0;
   // pattern gates: records {t, pin | value << 8}, initial states, items, and per-gate results
+  unsigned long long max_count = 0;  // the busiest gate's events (set by gtp_load_events)
   bool pat_loaded = false;
   int64_t pat_n_events = 0, pat_n_items = 0;
   std::vector<int64_t> pat_h_off;
@@ -102,11 +104,12 @@ struct GraphKey {
   bool timing;      // whether phase events were captured
   std::vector<int32_t> groups;  // first window of each window group
   int64_t pat_items;            // pattern walk launch size (-1: no pattern gates)
+  bool whole;                   // the walk without pieces
   bool operator<(const GraphKey& o) const {
     return std::tie(windows, bin_ps, rpt, ctas, kernel, dmin, tmin, piece, plan_gen, n_tiles, any_events, timing,
-                    groups, pat_items) < std::tie(o.windows, o.bin_ps, o.rpt, o.ctas, o.kernel, o.dmin, o.tmin,
-                                                  o.piece, o.plan_gen, o.n_tiles, o.any_events, o.timing, o.groups,
-                                                  o.pat_items);
+                    groups, pat_items, whole) < std::tie(o.windows, o.bin_ps, o.rpt, o.ctas, o.kernel, o.dmin,
+                                                         o.tmin, o.piece, o.plan_gen, o.n_tiles, o.any_events,
+                                                         o.timing, o.groups, o.pat_items, o.whole);
   }
 };
 
@@ -167,6 +170,7 @@ struct gtp_ctx {
   int64_t p_tile_min = 0;  // gates with this many events or more take the time-sliced walk (0: none)
   int64_t p_piece_len = -1;   // gates with more events are split into pieces (0: never, -1: chosen per run)
   int64_t run_piece_len = 0;  // the piece length of the run being planned
+  bool run_whole = false;     // no gate of the run being planned is split into pieces
   std::vector<std::pair<int, int>> run_groups;  // the run's window groups [first, end), walked one after another
   int64_t p_group_bytes = kGroupBinBytes;       // bin bytes of a window group at most
   // pattern cells (state patterns, up to 32 pins) and pattern gates
@@ -183,8 +187,8 @@ struct gtp_ctx {
   int64_t run_pat_items = -1;  // the run's pattern walk launch size (-1: none)
   // phase timing (CUDA events on the context stream) and launch counting
   bool timing = false;
-  cudaEvent_t ev[10] = {};
-  int64_t t_ns[5] = {0, 0, 0, 0, 0};  // gate pass, plan, walk (both walks), merge, the tiled walk alone
+  cudaEvent_t ev[12] = {};
+  int64_t t_ns[6] = {0, 0, 0, 0, 0, 0};  // gate pass, plan, walk (all walks), merge; the tiled and pattern walks
   int64_t n_timed = 0;
   int64_t launches = 0;
 };
@@ -418,6 +422,9 @@ int build_plan(gtp_ctx* ctx, const std::vector<Window*>& ws, int32_t bin_ps, con
   for (Window* w : ws) e_all += w->n_events;
   if (pl > 0 && e_all / pl >= (int64_t)1 << 20) pl = (e_all >> 20) / kPieceUnit * kPieceUnit + kPieceUnit;
   ctx->run_piece_len = pl;
+  ctx->run_whole = true;
+  for (Window* w : ws)
+    if (pl > 0 && (w->streamed || (int64_t)w->max_count > pl)) ctx->run_whole = false;
   const int64_t cap = (int64_t)n * G + (pl > 0 ? e_all / pl + n : 0);
   if (cap > ctx->gcap) {
     CU(ctx->glist.reserve(sizeof(int2) * (size_t)cap), "alloc work list");
@@ -459,6 +466,7 @@ WalkArgs walk_args(gtp_ctx* ctx, int n) {
   A.tile_min = 0;
   A.chunks = ctx->chunks.as<int32_t>();
   A.piece_len = ctx->run_piece_len;
+  A.whole = false;
   return A;
 }
 
@@ -473,7 +481,7 @@ void mark(gtp_ctx* ctx, int i, cudaStream_t st) {
 
 void collect_timing(gtp_ctx* ctx) {
   if (!ctx->timing) return;
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < (ctx->run_pat_items >= 0 ? 6 : 5); ++k) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, ctx->ev[2 * k], ctx->ev[2 * k + 1]) == cudaSuccess)
       ctx->t_ns[k] += (int64_t)(ms * 1e6);
@@ -498,6 +506,7 @@ int enqueue_forward(gtp_ctx* ctx, int n, int64_t n_seg_total, int64_t n_tiles_to
   CU(cudaMemsetAsync(plan_l0(ctx->plan.p), 0, sizeof(double) * n, st), "zero l0");
   WalkArgs A = walk_args(ctx, n);
   A.comp = comp;
+  A.whole = ctx->run_whole;
   const bool fused = any_events && ctx->p_kernel != 1;
   const bool tiled = fused && tiling_on(ctx, n, comp);
   if (tiled) A.tile_min = ctx->p_tile_min;
@@ -544,8 +553,10 @@ int enqueue_forward(gtp_ctx* ctx, int n, int64_t n_seg_total, int64_t n_tiles_to
   }
   if (ctx->run_pat_items >= 0) {  // the pattern gates, into the windows' FP64 bins and L0 (timed as walk)
     CU(cudaMemsetAsync(ctx->pat_bad.p, 0xFF, sizeof(unsigned long long), st), "reset pattern status");
+    mark(ctx, 10, st);
     CU(launch_pattern_walk(ctx->P, ctx->Q, dw, n, ctx->run_pat_items, ctx->N.clock_ps,
                            ctx->pat_bad.as<unsigned long long>(), st), "pattern walk");
+    mark(ctx, 11, st);
     ctx->launches += ctx->run_pat_items > 0 ? 3 : 1;
   }
   mark(ctx, 5, st);
@@ -598,10 +609,27 @@ __global__ void k_check_cells(const int32_t* cell, int64_t n, int32_t n_cells, D
     if (cell[g] < 0 || cell[g] >= n_cells) report_error(err, GTP_ERANGE, -1 - g);
 }
 
-__global__ void k_check_offsets(const int64_t* off, int64_t n_gates, int64_t n_events, DevError* err) {
+// Offsets checked (from 0 to n_events, never decreasing), and the busiest
+// gate's event count into *max_count.
+__global__ void k_check_offsets(const int64_t* off, int64_t n_gates, int64_t n_events, DevError* err,
+                                unsigned long long* max_count) {
+  int64_t mx = 0;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_gates;
        g += (int64_t)gridDim.x * blockDim.x) {
-    if (off[g + 1] < off[g]) report_error(err, GTP_EINVAL, -1 - g);
+    const int64_t c = off[g + 1] - off[g];
+    if (c < 0) report_error(err, GTP_EINVAL, -1 - g);
+    mx = c > mx ? c : mx;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const int64_t y = __shfl_xor_sync(0xFFFFFFFFu, mx, o);
+    mx = y > mx ? y : mx;
+  }
+  __shared__ int64_t wmax[32];  // one atomic a block
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = wmax[w] > mx ? wmax[w] : mx;
+    if (mx > 0) atomicMax(max_count, (unsigned long long)mx);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0 && (off[0] != 0 || off[n_gates] != n_events))
     report_error(err, GTP_EINVAL, -1);
@@ -739,7 +767,7 @@ int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, dou
     GraphKey key{std::vector<int32_t>(windows, windows + n), bin_ps, ctx->p_rpt,
                        ctx->p_ctas_per_sm, ctx->p_kernel, ctx->p_dense_min, ctx->p_tile_min, ctx->run_piece_len,
                        ctx->plan_gen,
-                       n_tiles_total, any_events, ctx->timing, {}, ctx->run_pat_items};
+                       n_tiles_total, any_events, ctx->timing, {}, ctx->run_pat_items, ctx->run_whole};
     for (const auto& gr : ctx->run_groups) key.groups.push_back(gr.first);
     auto it = ctx->graphs.find(key);
     if (it == ctx->graphs.end()) {
@@ -879,8 +907,9 @@ int gtp_create(gtp_ctx** out, int device, void* cuda_stream) {
   ctx->stream = (cudaStream_t)cuda_stream;
   DeviceGuard dg(device);
   cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device);
-  if (ctx->d_err.reserve(sizeof(DevError)) != cudaSuccess || ctx->plan.reserve(plan_bytes()) != cudaSuccess ||
-      cudaMallocHost(&ctx->h_err, sizeof(DevError)) != cudaSuccess ||
+  // status word: the first error, then the busiest gate's event count of the last load_events
+  if (ctx->d_err.reserve(kStatusBytes) != cudaSuccess || ctx->plan.reserve(plan_bytes()) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_err, kStatusBytes) != cudaSuccess ||
       cudaMallocHost(&ctx->h_plan, plan_bytes()) != cudaSuccess) {
     ctx->d_err.release();
     ctx->plan.release();
@@ -889,7 +918,7 @@ int gtp_create(gtp_ctx** out, int device, void* cuda_stream) {
     return GTP_ENOMEM;
   }
   memset(ctx->h_plan, 0, plan_bytes());
-  cudaMemset(ctx->d_err.p, 0, sizeof(DevError));
+  cudaMemset(ctx->d_err.p, 0, kStatusBytes);
   *out = ctx;
   return GTP_OK;
 }
@@ -1246,13 +1275,19 @@ int gtp_load_events(gtp_ctx* ctx, int32_t window, int64_t window_ps, int64_t n_e
     if (n_events > 0)
       CU(cudaMemcpyAsync(W.records.p, events, sizeof(uint2) * (size_t)n_events, k, ctx->stream), "copy records");
   }
-  CU(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(DevError), ctx->stream), "zero status");
-  k_check_offsets<<<1024, 256, 0, ctx->stream>>>(W.offsets.as<int64_t>(), G, n_events, ctx->d_err.as<DevError>());
+  CU(cudaMemsetAsync(ctx->d_err.p, 0, kStatusBytes, ctx->stream), "zero status");
+  unsigned long long* max_count =
+      reinterpret_cast<unsigned long long*>(static_cast<unsigned char*>(ctx->d_err.p) + sizeof(DevError));
+  k_check_offsets<<<1024, 256, 0, ctx->stream>>>(W.offsets.as<int64_t>(), G, n_events, ctx->d_err.as<DevError>(),
+                                                 max_count);
   CU(cudaGetLastError(), "check offsets");
   ctx->launches += 1;
-  const int rc = check_device_error(ctx, "load_events");
-  if (rc != GTP_OK)
+  CU(cudaMemcpyAsync(ctx->h_err, ctx->d_err.p, sizeof(DevError) + sizeof(unsigned long long),
+                     cudaMemcpyDeviceToHost, ctx->stream), "read status");
+  CU(cudaStreamSynchronize(ctx->stream), "load_events");
+  if (ctx->h_err->code != 0)
     return fail(ctx, GTP_EINVAL, "load_events: offsets must start at 0, end at n_events and not decrease");
+  memcpy(&W.max_count, reinterpret_cast<unsigned char*>(ctx->h_err) + sizeof(DevError), sizeof(W.max_count));
   W.window_ps = window_ps;
   W.n_events = n_events;
   W.loaded = true;
@@ -1607,6 +1642,7 @@ int gtp_run_power_backward(gtp_ctx* ctx, int32_t window, int32_t bin_ps, const f
   if (W->pat_loaded && ctx->pat_net_ok)
     return fail(ctx, GTP_EINVAL, "run_power_backward: windows with pattern gates are walked by gtp_run_power and "
                                  "gtp_run_power_batched only");
+  ctx->run_pat_items = -1;
   if (!dL_dP) return fail(ctx, GTP_EINVAL, "run_power_backward: dL_dP is required");
   if (bin_ps <= 0 || W->window_ps % bin_ps != 0)
     return fail(ctx, GTP_ERANGE, "window_ps must be a multiple of bin_ps > 0");
@@ -2060,12 +2096,14 @@ int64_t gtp_get_param(const gtp_ctx* ctx, const char* key) {
   if (k == "tile_min") return ctx->p_tile_min;
   if (k == "piece_len") return ctx->p_piece_len;
   if (k == "run_piece_len") return ctx->run_piece_len;
+  if (k == "run_whole") return ctx->run_whole ? 1 : 0;
   if (k == "group_bin_bytes") return ctx->p_group_bytes;
   if (k == "sipl_max_pins") return ctx->p_sipl_max_pins;
   if (k == "pattern_indexed_cells") return ctx->pat_index_ok ? ctx->pat_indexed : -1;
   if (k == "pattern_index_bytes") return ctx->pat_index_ok ? ctx->pat_index_bytes : -1;
   if (k == "run_groups") return (int64_t)ctx->run_groups.size();
   if (k == "t_tiled_ns") return ctx->t_ns[4];
+  if (k == "t_pattern_ns") return ctx->t_ns[5];
   if (k == "scheme_evt_tgt") return ctx->p_evt_tgt;
   if (k == "scheme_thr_floor") return ctx->p_thr_floor;
   if (k == "scheme_ncyc_fix") return ctx->p_ncyc_fix;

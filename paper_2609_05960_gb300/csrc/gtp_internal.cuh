@@ -324,7 +324,7 @@ cudaError_t launch_validate_if(const LibView& L, const NetView& N, const WinDesc
 int merge_tiles(int n_bins);
 // Pattern gates: a gate's records are cut into items of kPatPiece records
 // (each item extended to the end of the timestamp group it ends in).
-constexpr int64_t kPatPiece = 2048;
+constexpr int64_t kPatPiece = 512;
 // Pattern records {t, pin | value << 8} from the ABI's arrays (device).
 cudaError_t launch_pattern_pack(const int32_t* t, const uint8_t* pin, const uint8_t* value, int64_t n, uint2* out,
                                 cudaStream_t st);

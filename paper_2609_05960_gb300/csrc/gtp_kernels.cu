@@ -51,8 +51,11 @@ __global__ void k_event_desc(LibView L, NetView N, uint4* __restrict__ desc) {
     ax[3 * kMaxAxis + threadIdx.x] = L.load_rw[threadIdx.x];
   }
   __syncthreads();
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N.n_gates;
-       g += (int64_t)gridDim.x * blockDim.x) {
+  // one thread a descriptor (gate g, pin p, edge e), so consecutive threads write consecutive 16-byte entries
+  const int64_t n = N.n_gates * N.dstride;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t g = k / N.dstride;
+    const int pe = (int)(k - g * N.dstride), p = pe >> 1, e = pe & 1;
     const int32_t c = N.cell[g];
     const CellInfo ci = L.cells[c];
     const int n_in = ci.n_in;
@@ -60,23 +63,19 @@ __global__ void k_event_desc(LibView L, NetView N, uint4* __restrict__ desc) {
     const int j = segment_of(ax + kMaxAxis, L.nl, C);
     const float fl = (C - ax[kMaxAxis + j]) * ax[3 * kMaxAxis + j];
     const uint32_t hi_bits = ((uint32_t)c << 16) | ((uint32_t)j << 25);
-    for (int p = 0; p <= N.stride; ++p) {
-      for (int e = 0; e < 2; ++e) {
-        uint4 d;
-        if (p < n_in) {
-          const float s = N.slew[((size_t)g * N.stride + p) * 2 + e];
-          const int i = segment_of(ax, L.ns, s);
-          const uint32_t tab = (uint32_t)(ci.tab_base + ((p * 2 + e) << (n_in - 1))) * (uint32_t)L.tsize +
-                               (uint32_t)(i * L.nl + j);
-          d = make_uint4(__float_as_uint((s - ax[i]) * ax[2 * kMaxAxis + i]), __float_as_uint(fl),
-                         tab | hi_bits, __float_as_uint(ax[3 * kMaxAxis + j]));
-        } else {  // output pin (and any pin past it): switching energy
-          d = make_uint4(0u, 0u, ((uint32_t)ci.tab_base * (uint32_t)L.tsize) | hi_bits | (1u << 24),
-                         __float_as_uint(L.half_v2 * C));
-        }
-        desc[(size_t)g * N.dstride + p * 2 + e] = d;
-      }
+    uint4 d;
+    if (p < n_in) {
+      const float sl = N.slew[((size_t)g * N.stride + p) * 2 + e];
+      const int i = segment_of(ax, L.ns, sl);
+      const uint32_t tab = (uint32_t)(ci.tab_base + ((p * 2 + e) << (n_in - 1))) * (uint32_t)L.tsize +
+                           (uint32_t)(i * L.nl + j);
+      d = make_uint4(__float_as_uint((sl - ax[i]) * ax[2 * kMaxAxis + i]), __float_as_uint(fl), tab | hi_bits,
+                     __float_as_uint(ax[3 * kMaxAxis + j]));
+    } else {  // output pin (and any pin past it): switching energy
+      d = make_uint4(0u, 0u, ((uint32_t)ci.tab_base * (uint32_t)L.tsize) | hi_bits | (1u << 24),
+                     __float_as_uint(L.half_v2 * C));
     }
+    desc[k] = d;
   }
 }
 
@@ -90,36 +89,51 @@ __global__ void k_event_desc(LibView L, NetView N, uint4* __restrict__ desc) {
 // bits are the side state; the output pin is pin n_in.  Forward table:
 // energies times escale, output slots 0.5 * C * Vdd^2.  Adjoint table:
 // unscaled energies (output slots 0), then their load derivatives (the slope
-// of the located load segment; output slots 0.5 * Vdd^2).
+// of the located load segment; output slots 0.5 * Vdd^2).  One warp builds
+// one gate's table, lane e its entry e, so each row is written as one
+// coalesced 128-byte line (slots past the cell's entries are left unwritten:
+// nothing reads them).
 __global__ void k_gate_tables(LibView L, NetView N, float* __restrict__ gtab, float* __restrict__ gbwd) {
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N.n_gates;
-       g += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t c = N.cell[g];
-    const CellInfo ci = L.cells[c];
-    const uint32_t n_in = (uint32_t)ci.n_in;
-    if (n_in > (uint32_t)kGateTabMaxIn) continue;
-    const uint4* dsc = N.desc + (size_t)g * N.dstride;
-    const float esc = L.escale[c];
-    const float e_sw = __uint_as_float(dsc[2u * n_in].w);
-    const uint32_t inmask = (1u << n_in) - 1u;
-    for (uint32_t e = 0; e < ((n_in + 1u) << n_in); ++e) {
-      const uint32_t pin = e >> n_in, s = e & inmask;
-      float eu, ed;
+  constexpr int kG = 4;  // gates a warp takes at once: their loads are independent and overlap
+  const uint32_t e = threadIdx.x & 31u;
+  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t g0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kG; g0 < N.n_gates;
+       g0 += n_warps * kG) {
+    int32_t c[kG];
+    CellInfo ci[kG];
+    uint4 d[kG];
+#pragma unroll
+    for (int k = 0; k < kG; ++k) c[k] = g0 + k < N.n_gates ? __ldg(N.cell + g0 + k) : 0;
+#pragma unroll
+    for (int k = 0; k < kG; ++k) ci[k] = L.cells[c[k]];
+#pragma unroll
+    for (int k = 0; k < kG; ++k) {
+      const uint32_t n_in = (uint32_t)ci[k].n_in;
+      const uint32_t pin = min(e >> n_in, n_in), s = e & ((1u << n_in) - 1u);
+      const uint32_t val = pin < n_in ? (((s >> pin) & 1u) ^ 1u) : 0u;  // own bit: the value before the edge
+      d[k] = g0 + k < N.n_gates ? __ldg(N.desc + (size_t)(g0 + k) * N.dstride + pin * 2u + val) : make_uint4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int k = 0; k < kG; ++k) {
+      const int64_t g = g0 + k;
+      const uint32_t n_in = (uint32_t)ci[k].n_in;
+      if (g >= N.n_gates || n_in > (uint32_t)kGateTabMaxIn || e >= ((n_in + 1u) << n_in)) continue;
+      const uint32_t pin = e >> n_in, s = e & ((1u << n_in) - 1u);
+      float eu, ed, ef;
       if (pin < n_in) {
-        const uint32_t val = ((s >> pin) & 1u) ^ 1u;  // the pin's own bit is its value before the edge
-        const uint4 d = dsc[pin * 2u + val];
-        const float* p = L.tab + (d.z & 0xFFFFu) + side_bits(s, pin, n_in) * (uint32_t)L.tsize;
-        const float a0 = p[0], a1 = p[1], b0 = p[L.nl], b1 = p[L.nl + 1];
-        const float fl = __uint_as_float(d.y), fs = __uint_as_float(d.x);
+        const float* p = L.tab + (d[k].z & 0xFFFFu) + side_bits(s, pin, n_in) * (uint32_t)L.tsize;
+        const float a0 = __ldg(p), a1 = __ldg(p + 1), b0 = __ldg(p + L.nl), b1 = __ldg(p + L.nl + 1);
+        const float fl = __uint_as_float(d[k].y), fs = __uint_as_float(d[k].x);
         const float lo = fmaf(fl, a1 - a0, a0), hi = fmaf(fl, b1 - b0, b0);
         eu = fmaf(fs, hi - lo, lo);
-        ed = fmaf(fs, (b1 - b0) - (a1 - a0), a1 - a0) * __uint_as_float(d.w);
-        if (gtab) gtab[(size_t)g * kGateTab + e] = eu * esc;
+        ed = fmaf(fs, (b1 - b0) - (a1 - a0), a1 - a0) * __uint_as_float(d[k].w);
+        ef = eu * L.escale[c[k]];
       } else {
         eu = 0.f;
         ed = L.half_v2;
-        if (gtab) gtab[(size_t)g * kGateTab + e] = e_sw;
+        ef = __uint_as_float(d[k].w);  // the output pin's descriptor: 0.5 * C * Vdd^2
       }
+      if (gtab) gtab[(size_t)g * kGateTab + e] = ef;
       if (gbwd) {
         gbwd[(size_t)g * 2 * kGateTab + e] = eu;
         gbwd[(size_t)g * 2 * kGateTab + kGateTab + e] = ed;
@@ -129,14 +143,14 @@ __global__ void k_gate_tables(LibView L, NetView N, float* __restrict__ gtab, fl
 }
 
 cudaError_t launch_gate_tables(const LibView& L, const NetView& N, float* gtab, float* gtab_bwd, cudaStream_t st) {
-  int64_t blocks = (N.n_gates + 255) / 256;
-  if (blocks > 8192) blocks = 8192;
+  int64_t blocks = (N.n_gates + 31) / 32;  // 8 warps of 4 gates a block
+  if (blocks > 16384) blocks = 16384;
   k_gate_tables<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, st>>>(L, N, gtab, gtab_bwd);
   return cudaGetLastError();
 }
 
 cudaError_t launch_event_desc(const LibView& L, NetView N, uint4* desc, cudaStream_t st) {
-  int64_t blocks = (N.n_gates + 255) / 256;
+  int64_t blocks = (N.n_gates * N.dstride + 255) / 256;
   if (blocks > 8192) blocks = 8192;
   k_event_desc<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, st>>>(L, N, desc);
   return cudaGetLastError();

@@ -237,14 +237,22 @@ __global__ void __launch_bounds__(kPatWarps * 32) k_pat_walk(PatLib P, PatNet Q,
     }
   }
   double ei = 0.0, es = 0.0, eg = 0.0, el = 0.0;
+  // records are read 32 at a time, the next 32 loaded while these are walked; every lane reads its record
+  // while it lies inside the gate, so the time after the item's last record comes from the lane after it
+  constexpr uint2 kNone = {0xFFFFFFFFu, 0u};
+  uint2 qc = s + lane < gb ? W.p_rec[s + lane] : kNone;
   for (int64_t base = s; base < e; base += 32) {
     const int64_t r = base + lane;
     const bool valid = r < e;
-    const uint2 q = valid ? W.p_rec[r] : make_uint2(0u, 0u);
+    const uint2 qn = (r + 32 < gb && (base + 32 < e || lane == 0)) ? W.p_rec[r + 32] : kNone;
+    const uint2 q = valid ? qc : make_uint2(0u, 0u);
     const uint32_t t = q.x, pin = q.y & 0xFFu, v = (q.y >> 8) & 1u;
     const int last_lane = (int)min((int64_t)31, e - 1 - base);
-    uint32_t tn = __shfl_down_sync(kFull, t, 1);
-    if (lane == last_lane) tn = r + 1 < gb ? __ldg(&W.p_rec[r + 1].x) : 0xFFFFFFFFu;
+    uint32_t tn = __shfl_down_sync(kFull, qc.x, 1);
+    const uint32_t tn31 = __shfl_sync(kFull, qn.x, 0);
+    if (lane == 31) tn = tn31;
+    if (r + 1 >= gb) tn = 0xFFFFFFFFu;
+    qc = qn;
     uint32_t tp = __shfl_up_sync(kFull, t, 1);
     if (lane == 0) tp = t_last;
     const bool head = valid && (r == s || t != tp);

@@ -133,8 +133,9 @@ struct DGate {
 // A work-list entry {window | piece << kPieceShift, gate}: a gate of more
 // than piece_len events (piece_len > 0) is split into pieces of piece_len
 // events (a multiple of the longest chunk, so only a gate's last piece can
-// end in a partial segment), each its own big item.
-template <bool BWD, bool GL>
+// end in a partial segment), each its own big item.  PC = false compiles a
+// walk for runs in which no gate is split: every item is a whole gate.
+template <bool BWD, bool GL, bool PC>
 __device__ __forceinline__ DGate dense_gate(const LibView& L, const NetView& N, const WinDesc* __restrict__ wins,
                                             int2 wg, int64_t piece_len) {
   DGate d;
@@ -142,6 +143,7 @@ __device__ __forceinline__ DGate dense_gate(const LibView& L, const NetView& N, 
   d.rec = d.W->rec;
   d.g = wg.y;
   const int64_t gs = d.W->offsets[d.g], ge = d.W->offsets[d.g + 1];
+  if (!PC) piece_len = 0;
   d.split = piece_len > 0 && ge - gs > piece_len;
   if (d.split) {
     d.ga = gs + (int64_t)((uint32_t)wg.x >> kPieceShift) * piece_len;
@@ -1035,8 +1037,15 @@ __host__ __device__ inline size_t union_area(int K, int n_leak, bool bwd, bool g
 // larger tables allow only two CTAs per SM: these are given the registers of
 // two (measured on the large workload: 16 records per lane at two CTAs
 // 1.18 ms, at three 1.38 ms).
-template <int K, bool BWD, bool GL, bool CMP>
-__global__ void __launch_bounds__(kWalkThreads, (BWD || GL || K == 16) ? 2 : 3)
+#ifndef GTP_WALK_MINB_GL
+#define GTP_WALK_MINB_GL 2  // resident CTAs an SM the glitch walk is compiled for (registers: 128)
+#endif
+#ifndef GTP_WALK_MINB_BWD
+#define GTP_WALK_MINB_BWD 2  // the same for the adjoint walk
+#endif
+template <int K, bool BWD, bool GL, bool CMP, bool PC>
+__global__ void __launch_bounds__(kWalkThreads,
+                                  K == 16 ? 2 : (BWD ? GTP_WALK_MINB_BWD : (GL ? GTP_WALK_MINB_GL : 3)))
     k_walk(LibView L, NetView N, WalkArgs A) {
   constexpr int SEG = 32 * K;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1097,13 +1106,13 @@ __global__ void __launch_bounds__(kWalkThreads, (BWD || GL || K == 16) ? 2 : 3)
     const bool is_dense = (pos + 1) * n_dense_items / n_items > dense_before;
     const int64_t item = is_dense ? dense_before : n_dense_items + (pos - dense_before);
     if (item < n_big) {
-      const DGate d = dense_gate<BWD, GL>(L, N, wins, P.glist[item], A.piece_len);
+      const DGate d = dense_gate<BWD, GL, PC>(L, N, wins, P.glist[item], A.piece_len);
       if (d.n_in <= (uint32_t)kTabMaxIn) big_gate<K, BWD, true, GL, CMP>(L, d, sm, err, xfer, gx, red, wib, lane);
       else big_gate<K, BWD, false, GL, CMP>(L, d, sm, err, xfer, gx, red, wib, lane);
     } else if (item < n_dense_items) {
       const int64_t i = (item - n_big) * kWarps + wib;
       if (i < n_med) {
-        const DGate d = dense_gate<BWD, GL>(L, N, wins, P.glist[n_big + i], A.piece_len);
+        const DGate d = dense_gate<BWD, GL, PC>(L, N, wins, P.glist[n_big + i], A.piece_len);
         if (d.n_in <= (uint32_t)kTabMaxIn) medium_gate<K, BWD, true, GL, CMP>(L, d, sm, err, lane);
         else medium_gate<K, BWD, false, GL, CMP>(L, d, sm, err, lane);
       }
@@ -1144,22 +1153,32 @@ __global__ void __launch_bounds__(kWalkThreads, (BWD || GL || K == 16) ? 2 : 3)
 }
 
 // ------------------------------------------------------------------ launchers
-template <int K, bool BWD, bool GL, bool CMP>
+template <int K, bool BWD, bool GL, bool CMP, bool PC = true>
 cudaError_t launch_walk_k(const LibView& L, const NetView& N, const WalkArgs& A, cudaStream_t st) {
   const size_t smem =
       union_area(K, L.n_leak, BWD, GL) + (BWD ? (size_t)kWarps * 2 * L.n_cells * sizeof(double) : 0);
   cudaError_t e =
-      cudaFuncSetAttribute(k_walk<K, BWD, GL, CMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(k_walk<K, BWD, GL, CMP, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int grid = A.grid;
   if (grid <= 0) {
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<K, BWD, GL, CMP>, kWalkThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<K, BWD, GL, CMP, PC>, kWalkThreads, smem);
     if (e != cudaSuccess) return e;
     grid = (per_sm > 0 ? per_sm : 1) * A.n_sm;
   }
-  k_walk<K, BWD, GL, CMP><<<grid, kWalkThreads, smem, st>>>(L, N, A);
+  k_walk<K, BWD, GL, CMP, PC><<<grid, kWalkThreads, smem, st>>>(L, N, A);
   return cudaGetLastError();
+}
+
+// The plain forward walk of a run with no gate split into pieces.
+template <bool GL>
+cudaError_t launch_walk_whole(const LibView& L, const NetView& N, const WalkArgs& A, cudaStream_t st) {
+  switch (A.rpt) {
+    case 4: return launch_walk_k<4, false, GL, false, false>(L, N, A, st);
+    case 16: return launch_walk_k<16, false, GL, false, false>(L, N, A, st);
+    default: return launch_walk_k<8, false, GL, false, false>(L, N, A, st);
+  }
 }
 
 // The walk of one glitch setting: GL = whether glitch detection is on.

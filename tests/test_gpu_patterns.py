@@ -8,7 +8,7 @@ patterns at every lookup (the paper's fallback).  The oracle is
 oracle/patterns.py (every lookup a traversal by oracle/sipl.py) for the
 pattern gates plus oracle.walk for the ordinary gates of the same window.
 Cases: the 20-pin SRAM-like macro and the 21-pin multiplexer with busy
-clock pins, gates of many items (2,048 records each) with ties across item
+clock pins, gates of many items (512 records each) with ties across item
 boundaries, every threshold from 0 (all traversal) to 24 (every cell
 indexed), glitch detection, batched windows, graph replay, malformed records
 in a later item, and the calls that refuse windows with pattern gates.
@@ -98,14 +98,14 @@ def test_every_threshold_matches_the_oracle(engine):
 
 @pytest.mark.parametrize("clock", [0, 700])
 def test_sram_macros_many_items(engine, clock):
-    """Eight 20-pin SRAM-like macros of 5k-40k events (3 to 20 items each),
+    """Eight 20-pin SRAM-like macros of 512-40k events (1 to 79 items each),
     the clock pin busy, ties at about a third of the records (so groups
     cross the nominal item boundaries), with and without glitch detection."""
     plib = spat.make_pattern_library(2)
     w = [1.0 if n == "SRAM20" else 0.0 for n in plib.names]
     lib, net, tr = small_random(n_gates=200, n_events=5000, window_ps=100_000, seed=21, tie_p=0.02)
     pnet = spat.make_pattern_netlist(plib, 8, seed=22, weights=w)
-    counts = np.array([40_000, 5_000, 20_000, 2048, 4096, 2049, 12_345, 30_000])
+    counts = np.array([40_000, 5_000, 20_000, 512, 1024, 513, 12_345, 30_000])
     ptr = spat.make_pattern_trace(pnet, counts, 100_000, 23, tie_p=0.3, clock_pin_share=0.5)
     out_slew = np.random.default_rng(4).uniform(10, 200, (net.n_gates, 2)).astype(np.float32)
     ref = oracle.walk(lib, net, tr, 20, glitch=(clock, out_slew) if clock else None)
@@ -175,7 +175,7 @@ def test_design_power_includes_pattern_gates(engine):
 
 @pytest.mark.parametrize("kind,code", [("order", -2), ("time", -3), ("pin", -3), ("toggle", -4), ("value", -3)])
 def test_malformed_pattern_record_in_a_later_item(engine, kind, code):
-    """One bad record deep in a 10k-event macro (its fourth item) and a later
+    """One bad record deep in a 10k-event macro (its thirteenth item) and a later
     bad one in another gate: the run reports the first, as the oracle does."""
     from paper_2609_05960_gb300 import GtpError
     plib = spat.make_pattern_library(1)

@@ -98,12 +98,14 @@ def _hot_gates():
 def test_pieces_match_the_oracle(engine, rpt):
     lib, net, tr = _hot_gates()
     ref = oracle.walk(lib, net, tr, 100)
-    for piece in (PIECE, 0):
+    for piece in (PIECE, 0, 100_000):
         setup(engine, lib, net, piece, rpt)
         engine.load_events(0, tr)
         w = engine.run_power(0, 100).cpu().numpy()
         ge = engine.gate_energy(0, device=False)
         check(w, ge, ref, 100)
+        # no gate longer than the piece length: the walk compiled without pieces ran
+        assert engine.get_param("run_whole") == (0 if piece == PIECE else 1)
     setup(engine, lib, net, PIECE, rpt)
     engine.load_events(0, tr)
     engine.run_power(0, 100)
