@@ -178,7 +178,7 @@ struct gtp_ctx {
   std::vector<PatCell> h_pat_cells;
   DevBuf pc_cells, pc_ip, pc_ipo, pc_lp, pc_tab, pc_iidx, pc_lidx;
   PatLib P{};
-  DevBuf pn_cell, pn_load, pn_slew, pn_oslew;
+  DevBuf pn_cell, pn_load, pn_slew, pn_oslew, pn_desc;
   PatNet Q{};
   int64_t p_sipl_max_pins = 16;  // pattern cells with at most this many pins get state-indexed arrays
   int64_t pat_index_bytes = 0;
@@ -944,7 +944,7 @@ void gtp_destroy(gtp_ctx* ctx) {
                     &ctx->cell_acc, &ctx->grad, &ctx->gtiles, &ctx->dC_scratch, &ctx->d_err, &ctx->pat_int,
                     &ctx->pat_leak, &ctx->sch_ebins, &ctx->sch_R, &ctx->probe, &ctx->chunks, &ctx->pc_cells,
                     &ctx->pc_ip, &ctx->pc_ipo, &ctx->pc_lp, &ctx->pc_tab, &ctx->pc_iidx, &ctx->pc_lidx,
-                    &ctx->pn_cell, &ctx->pn_load, &ctx->pn_slew, &ctx->pn_oslew, &ctx->pat_bad})
+                    &ctx->pn_cell, &ctx->pn_load, &ctx->pn_slew, &ctx->pn_oslew, &ctx->pn_desc, &ctx->pat_bad})
     b->release();
   for (auto& e : ctx->sch_ev)
     if (e) cudaEventDestroy(e);
@@ -1926,8 +1926,35 @@ int gtp_load_pattern_netlist(gtp_ctx* ctx, int64_t n_gates, const int32_t* cell,
     CU(cudaMemcpy(ctx->pn_oslew.p, out_slew_ps, sizeof(float) * 2 * n, cudaMemcpyHostToDevice), "copy out slews");
   else
     CU(cudaMemset(ctx->pn_oslew.p, 0, sizeof(float) * 2 * n), "zero out slews");
+  // the interpolation point of every (gate, input pin, edge): lower knots (segments clamped to the edge ones,
+  // so points outside the axes extrapolate) and the slew fraction; the load fraction is found per walk item
+  {
+    const PatLib& P = ctx->P;
+    auto seg = [](const float* ax, int na, float x) {
+      int i = 0;
+      while (i < na - 2 && x >= ax[i + 1]) ++i;
+      return i;
+    };
+    std::vector<uint2> desc(n * (size_t)slew_stride * 2, make_uint2(0u, 0u));
+    for (int64_t g = 0; g < n_gates; ++g) {
+      const int j = seg(P.load_axis, P.nl, load_ff[g]);
+      const int n_in = ctx->h_pat_cells[(size_t)cell[g]].n_in;
+      for (int p = 0; p < n_in; ++p)
+        for (int e = 0; e < 2; ++e) {
+          const float sl = slew_ps[((size_t)g * slew_stride + p) * 2 + e];
+          const int i = seg(P.slew_axis, P.ns, sl);
+          const float fs = (sl - P.slew_axis[i]) / (P.slew_axis[i + 1] - P.slew_axis[i]);
+          uint32_t fb;
+          memcpy(&fb, &fs, 4);
+          desc[((size_t)g * slew_stride + p) * 2 + e] = make_uint2((uint32_t)(i * P.nl + j), fb);
+        }
+    }
+    CU(ctx->pn_desc.reserve(sizeof(uint2) * desc.size()), "alloc pattern descriptors");
+    CU(cudaMemcpy(ctx->pn_desc.p, desc.data(), sizeof(uint2) * desc.size(), cudaMemcpyHostToDevice),
+       "copy pattern descriptors");
+  }
   ctx->Q = PatNet{ctx->pn_cell.as<int32_t>(), ctx->pn_load.as<float>(), ctx->pn_slew.as<float>(),
-                  ctx->pn_oslew.as<float>(), n_gates, slew_stride};
+                  ctx->pn_oslew.as<float>(), ctx->pn_desc.as<uint2>(), n_gates, slew_stride};
   ctx->pat_net_ok = true;
   return GTP_OK;
 }

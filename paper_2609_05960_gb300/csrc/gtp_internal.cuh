@@ -109,6 +109,8 @@ struct PatNet {
   const float* load;         // [Gp] fF
   const float* slew;         // [Gp][stride][2] input transition times, ps
   const float* oslew;        // [Gp][2] output {fall, rise} transition times, ps
+  const uint2* desc;         // [Gp][stride][2] per (gate, input pin, edge): {table element of the lower slew
+                             //   and load knots, slew fraction (float bits)}, located once per netlist
   int64_t n_gates;
   int32_t stride;
 };

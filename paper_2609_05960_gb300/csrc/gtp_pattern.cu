@@ -283,11 +283,9 @@ __global__ void __launch_bounds__(kPatWarps * 32) k_pat_walk(PatLib P, PatNet Q,
     if (valid && code == 0) {
       if (pin < n_in) {
         const int32_t tb = pat_table(P, c, pin, v, Spre);
-        const float sl = slew[pin * 2 + v];
-        int i = 0;
-        while (i < P.ns - 2 && sl >= ax[0][i + 1]) ++i;
-        const float fs = (sl - ax[0][i]) / (ax[0][i + 1] - ax[0][i]);
-        const float* tp4 = P.tab + (int64_t)tb * P.tsize + i * P.nl + j;
+        const uint2 dd = __ldg(Q.desc + ((int64_t)g * Q.stride + pin) * 2 + v);  // {knots' element, slew fraction}
+        const float fs = __uint_as_float(dd.y);
+        const float* tp4 = P.tab + (int64_t)tb * P.tsize + dd.x;
         const float t00 = __ldg(tp4), t01 = __ldg(tp4 + 1), t10 = __ldg(tp4 + P.nl), t11 = __ldg(tp4 + P.nl + 1);
         E = (1.f - fs) * ((1.f - fl) * t00 + fl * t01) + fs * ((1.f - fl) * t10 + fl * t11);
         kind = 1;
@@ -330,17 +328,19 @@ __global__ void __launch_bounds__(kPatWarps * 32) k_pat_walk(PatLib P, PatNet Q,
       y = dP;
       el += dP * (double)(T - t) * 1e-6;
     }
+    const uint32_t bprev = __shfl_up_sync(kFull, b, 1);
+    if (__any_sync(kFull, lane > 0 && b != 0xFFFFFFFFu && bprev == b)) {  // lanes share a bin: sum them first
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const double xo = __shfl_down_sync(kFull, x, o);
-      const double yo = __shfl_down_sync(kFull, y, o);
-      const uint32_t bo = __shfl_down_sync(kFull, b, o);
-      if (lane + o < 32 && bo == b) {
-        x += xo;
-        y += yo;
+      for (int o = 1; o < 32; o <<= 1) {
+        const double xo = __shfl_down_sync(kFull, x, o);
+        const double yo = __shfl_down_sync(kFull, y, o);
+        const uint32_t bo = __shfl_down_sync(kFull, b, o);
+        if (lane + o < 32 && bo == b) {
+          x += xo;
+          y += yo;
+        }
       }
     }
-    const uint32_t bprev = __shfl_up_sync(kFull, b, 1);
     if (b != 0xFFFFFFFFu && (lane == 0 || bprev != b)) {
       double* tb2 = reinterpret_cast<double*>(W.tbins + b);
       if (x != 0.0) atomicAdd(tb2, x);

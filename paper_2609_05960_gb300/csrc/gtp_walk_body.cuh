@@ -122,12 +122,6 @@ struct DGate {
   uint32_t cell, n_in, pmask, inmask, init;
   float esc, lsc;            // energy scale; leakage scale (1 in the adjoint)
   uint32_t T, bin_ps, magic, shift;
-  // glitch detection: clock and its division constants, the gate's input
-  // slews [stride][2] and output {fall, rise} transition times
-  int32_t clk;
-  uint32_t cmagic, cshift;
-  const float* islew;
-  const float* oslew;
 };
 
 // A work-list entry {window | piece << kPieceShift, gate}: a gate of more
@@ -168,13 +162,7 @@ __device__ __forceinline__ DGate dense_gate(const LibView& L, const NetView& N, 
   d.bin_ps = (uint32_t)d.W->bin_ps;
   d.magic = d.W->bin_magic;
   d.shift = d.W->bin_shift;
-  if (GL) {
-    d.clk = N.clock_ps;
-    d.cmagic = N.clock_magic;
-    d.cshift = N.clock_shift;
-    d.islew = N.slew + (size_t)d.g * N.stride * 2;
-    d.oslew = N.out_slew + 2 * d.g;
-  }
+  (void)GL;
   return d;
 }
 
@@ -182,9 +170,10 @@ __device__ __forceinline__ DGate dense_gate(const LibView& L, const NetView& N, 
 // cells of at most kTabMaxIn inputs) and, for glitch detection, each pin's
 // inverse transition time (any cell: at most 8 pins).
 template <bool BWD, bool TAB, bool GL>
-__device__ __forceinline__ void build_tables(const LibView& L, const DGate& d, const DenseSmem& sm, int lane) {
+__device__ __forceinline__ void build_tables(const LibView& L, const NetView& N, const DGate& d, const DenseSmem& sm,
+                                             int lane) {
   if (GL && lane <= (int)d.n_in) {
-    const float* sl = lane < (int)d.n_in ? d.islew + 2 * lane : d.oslew;
+    const float* sl = lane < (int)d.n_in ? N.slew + ((size_t)d.g * N.stride + lane) * 2 : N.out_slew + 2 * d.g;
     sm.ginv[lane] = glitch_inv(__ldg(sl) + __ldg(sl + 1));
   }
   if (!TAB) return;
@@ -388,7 +377,8 @@ __device__ __forceinline__ void gl_segment_scan(const DGate& d, const uint2* buf
 }
 
 template <int K, bool BWD, bool TAB, bool FULL, bool GL, bool CMP>
-__device__ __forceinline__ SegSums seg_back(const LibView& L, const DGate& d, const DenseSmem& sm, const uint2* buf,
+__device__ __forceinline__ SegSums seg_back(const LibView& L, const NetView& N, const DGate& d, const DenseSmem& sm,
+                                            const uint2* buf,
                                             const Seg& q, uint32_t seg_in, DevError* err, int lane) {
   SegSums out{0.f, 0.f, 0.f, 0.f};
   if (!FULL && q.n_rem == 0) return out;
@@ -469,7 +459,7 @@ __device__ __forceinline__ SegSums seg_back(const LibView& L, const DGate& d, co
     if (GL) {  // Sec. 2.4.1: an earlier event on this pin in the same clock cycle
       const uint32_t pv = sm.gprev[pin * 32 + lane];
       sm.gprev[pin * 32 + lane] = t + 1u;
-      if (pv != 0u && pv - 1u >= cycle_start(t, d.clk, d.cmagic, d.cshift)) {
+      if (pv != 0u && pv - 1u >= cycle_start(t, N.clock_ps, N.clock_magic, N.clock_shift)) {
         const float r = glitch_ratio_inv(t - (pv - 1u), sm.ginv[pin]);
         E *= r;
         dE *= r;
@@ -636,13 +626,14 @@ __device__ __forceinline__ uint32_t piece_entry(const DGate& d, const DenseSmem&
 
 // A medium gate, walked by one warp segment by segment.
 template <int K, bool BWD, bool TAB, bool GL, bool CMP>
-__device__ __forceinline__ void medium_gate(const LibView& L, const DGate& d, const DenseSmem& sm, DevError* err,
+__device__ __forceinline__ void medium_gate(const LibView& L, const NetView& N, const DGate& d, const DenseSmem& sm,
+                                            DevError* err,
                                             int lane) {
   constexpr int SEG = 32 * K;
   const int64_t nseg = (d.n + SEG - 1) / SEG;
   __syncwarp();
   issue_segment<K>(d, 0, sm.rec, sm.halo, lane);
-  if (TAB || GL) build_tables<BWD, TAB, GL>(L, d, sm, lane);
+  if (TAB || GL) build_tables<BWD, TAB, GL>(L, N, d, sm, lane);
   if (GL && lane <= (int)d.n_in) sm.gcarry[lane] = 0u;
   uint32_t carry = kXAbs | kXH | d.init | (d.init << 8);
   if (!d.starts) {  // a later piece of a split gate (pieces are big items; kept correct here too)
@@ -668,9 +659,9 @@ __device__ __forceinline__ void medium_gate(const LibView& L, const DGate& d, co
       if (lane <= (int)d.n_in) sm.gcarry[lane] = max(sm.gcarry[lane], sm.gtot[lane]);
     }
     if (full) {
-      acc.add(seg_back<K, BWD, TAB, true, GL, CMP>(L, d, sm, cur, q, carry, err, lane), GL);
+      acc.add(seg_back<K, BWD, TAB, true, GL, CMP>(L, N, d, sm, cur, q, carry, err, lane), GL);
     } else {
-      acc.add(seg_back<K, BWD, TAB, false, GL, CMP>(L, d, sm, cur, q, carry, err, lane), GL);
+      acc.add(seg_back<K, BWD, TAB, false, GL, CMP>(L, N, d, sm, cur, q, carry, err, lane), GL);
     }
     carry = xcompose(carry, tx);
     __syncwarp();
@@ -683,14 +674,15 @@ __device__ __forceinline__ void medium_gate(const LibView& L, const DGate& d, co
 // segments; the state entering each segment is the carry into the chunk
 // composed with the transfers of the chunk's earlier segments.
 template <int K, bool BWD, bool TAB, bool GL, bool CMP>
-__device__ __forceinline__ void big_gate(const LibView& L, const DGate& d, const DenseSmem& sm, DevError* err,
+__device__ __forceinline__ void big_gate(const LibView& L, const NetView& N, const DGate& d, const DenseSmem& sm,
+                                         DevError* err,
                                          uint32_t (*xfer)[kWarps], uint32_t (*gx)[kWarps][8], double (*red)[4],
                                          int wib, int lane) {
   constexpr int SEG = 32 * K;
   const int64_t nchunk = (d.n + (int64_t)kWarps * SEG - 1) / ((int64_t)kWarps * SEG);
   __syncwarp();
   issue_segment<K>(d, wib, sm.rec, sm.halo, lane);
-  if (TAB || GL) build_tables<BWD, TAB, GL>(L, d, sm, lane);
+  if (TAB || GL) build_tables<BWD, TAB, GL>(L, N, d, sm, lane);
   if (GL && lane <= (int)d.n_in) sm.gcarry[lane] = 0u;
   uint32_t carry = kXAbs | kXH | d.init | (d.init << 8);
   if (!d.starts) {  // a later piece of a split gate: every warp reads the state it starts from
@@ -735,8 +727,8 @@ __device__ __forceinline__ void big_gate(const LibView& L, const DGate& d, const
       if (v == wib) seg_in = carry;
       carry = xcompose(carry, x);
     }
-    acc.add(full ? seg_back<K, BWD, TAB, true, GL, CMP>(L, d, sm, cur, q, seg_in, err, lane)
-                 : seg_back<K, BWD, TAB, false, GL, CMP>(L, d, sm, cur, q, seg_in, err, lane), GL);
+    acc.add(full ? seg_back<K, BWD, TAB, true, GL, CMP>(L, N, d, sm, cur, q, seg_in, err, lane)
+                 : seg_back<K, BWD, TAB, false, GL, CMP>(L, N, d, sm, cur, q, seg_in, err, lane), GL);
     __syncwarp();
   }
   acc.flush(GL);
@@ -760,6 +752,23 @@ __device__ __forceinline__ void big_gate(const LibView& L, const DGate& d, const
 }
 
 // ------------------------------------------------------------------ sparse gates, one per thread
+#ifndef GTP_BWD_TAB_L1
+#define GTP_BWD_TAB_L1 1
+#endif
+// The adjoint's sparse threads read their gate tables in place (through L1)
+// instead of staging them in shared memory (64 KB a CTA), so that three
+// adjoint CTAs fit an SM (Large: 1.49 ms against 1.68 ms staged at two).
+constexpr bool kBwdTabL1 = GTP_BWD_TAB_L1 != 0;
+#ifndef GTP_FWD_TAB_L1
+#define GTP_FWD_TAB_L1 0
+#endif
+constexpr bool kFwdTabL1 = GTP_FWD_TAB_L1 != 0;  // the same for the forward walk
+template <bool BWD>
+constexpr bool kTabL1 = BWD ? kBwdTabL1 : kFwdTabL1;
+// Stride between a sparse thread's gate-table entries: its shared-memory
+// column, or the table in place.
+template <bool BWD>
+constexpr int kTabStride = kTabL1<BWD> ? 1 : kWalkThreads;
 constexpr int kChunk = 4;                  // events a thread walks per staged round
 constexpr int kStage = kChunk + 1;         // records staged per round: its events and the one after them
 constexpr int kRounds = 2;                 // rounds in flight (a power of two)
@@ -902,8 +911,8 @@ __device__ __forceinline__ WalkOut walk_gate(const LibView& L, const NetView& N,
         // entry (pin, input state with the pin's own bit = its value before the edge)
         const uint32_t own = (val - 1u) & bitp & inmask;
         const uint32_t idx = (pin << n_in) | (spre & inmask & ~bitp) | own;
-        E = tabl[idx * kWalkThreads];
-        if (BWD) dE = tabl[(kGateTab + idx) * kWalkThreads] * (is_out ? 1.f : esc);
+        E = tabl[idx * kTabStride<BWD>];
+        if (BWD) dE = tabl[(kGateTab + idx) * kTabStride<BWD>] * (is_out ? 1.f : esc);
       } else if (is_out) {
         E = BWD ? 0.f : __uint_as_float(__ldg(dsc + 2u * n_in).w);
         dE = L.half_v2;
@@ -1020,7 +1029,7 @@ __host__ __device__ inline size_t dense_area(int K, bool bwd, bool gl) {
                            (gl ? 8 * sizeof(float) + (8 * 32 + 16) * sizeof(uint32_t) : 0));
 }
 __host__ __device__ inline size_t sparse_area(int n_leak, bool bwd, bool gl) {
-  return (size_t)(bwd ? 2 : 1) * kGateTab * kWalkThreads * sizeof(float) +
+  return (size_t)(bwd ? (kBwdTabL1 ? 0 : 2) : (kFwdTabL1 ? 0 : 1)) * kGateTab * kWalkThreads * sizeof(float) +
          (size_t)kRounds * kStage * kWalkThreads * sizeof(uint2) + (gl ? (size_t)16 * kWalkThreads * sizeof(uint32_t) : 0) +
          (((size_t)n_leak * sizeof(float) + 15) & ~(size_t)15);
 }
@@ -1032,20 +1041,24 @@ __host__ __device__ inline size_t union_area(int K, int n_leak, bool bwd, bool g
 // Persistent CTAs of 8 warps take work items from the shared counter: one big
 // gate per item (all 8 warps), 8 medium gates per item (one per warp), then
 // 256 sparse gates per item (one per thread).  The forward walk with 4 or 8
-// records per lane fits three CTAs per SM (80 registers).  With 16 records
-// per lane or glitch detection it would spill at 80, and the adjoint's
-// larger tables allow only two CTAs per SM: these are given the registers of
-// two (measured on the large workload: 16 records per lane at two CTAs
-// 1.18 ms, at three 1.38 ms).
+// records per lane fits three CTAs per SM (80 registers), and so does the
+// adjoint with its gate tables read in place (a few bytes spilled).  With 16
+// records per lane or glitch detection the walk would spill at 80: these
+// are given the registers of two CTAs (measured on the large workload: 16
+// records per lane at two CTAs 1.18 ms, at three 1.38 ms; glitch detection
+// at two 2.11 ms, at three 2.19 ms).
+#ifndef GTP_WALK_MINB
+#define GTP_WALK_MINB 3  // resident CTAs an SM the forward walk is compiled for (registers: 80)
+#endif
 #ifndef GTP_WALK_MINB_GL
 #define GTP_WALK_MINB_GL 2  // resident CTAs an SM the glitch walk is compiled for (registers: 128)
 #endif
 #ifndef GTP_WALK_MINB_BWD
-#define GTP_WALK_MINB_BWD 2  // the same for the adjoint walk
+#define GTP_WALK_MINB_BWD 3  // the same for the adjoint walk (80 registers, a few bytes spilled)
 #endif
 template <int K, bool BWD, bool GL, bool CMP, bool PC>
 __global__ void __launch_bounds__(kWalkThreads,
-                                  K == 16 ? 2 : (BWD ? GTP_WALK_MINB_BWD : (GL ? GTP_WALK_MINB_GL : 3)))
+                                  K == 16 ? 2 : (BWD ? GTP_WALK_MINB_BWD : (GL ? GTP_WALK_MINB_GL : GTP_WALK_MINB)))
     k_walk(LibView L, NetView N, WalkArgs A) {
   constexpr int SEG = 32 * K;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1078,7 +1091,7 @@ __global__ void __launch_bounds__(kWalkThreads,
   sm.gcarry = sm.gtot + 8;
   // sparse view of the union area
   float* stab = reinterpret_cast<float*>(smem);
-  uint2* sstg = reinterpret_cast<uint2*>(stab + (BWD ? 2 : 1) * kGateTab * kWalkThreads);
+  uint2* sstg = reinterpret_cast<uint2*>(stab + (BWD ? (kBwdTabL1 ? 0 : 2) : (kFwdTabL1 ? 0 : 1)) * kGateTab * kWalkThreads);
   uint32_t* slast = reinterpret_cast<uint32_t*>(sstg + kRounds * kStage * kWalkThreads);
   float* sleak = reinterpret_cast<float*>(slast + (GL ? 16 * kWalkThreads : 0));
   // adjoint cell sums, after the union
@@ -1107,14 +1120,14 @@ __global__ void __launch_bounds__(kWalkThreads,
     const int64_t item = is_dense ? dense_before : n_dense_items + (pos - dense_before);
     if (item < n_big) {
       const DGate d = dense_gate<BWD, GL, PC>(L, N, wins, P.glist[item], A.piece_len);
-      if (d.n_in <= (uint32_t)kTabMaxIn) big_gate<K, BWD, true, GL, CMP>(L, d, sm, err, xfer, gx, red, wib, lane);
-      else big_gate<K, BWD, false, GL, CMP>(L, d, sm, err, xfer, gx, red, wib, lane);
+      if (d.n_in <= (uint32_t)kTabMaxIn) big_gate<K, BWD, true, GL, CMP>(L, N, d, sm, err, xfer, gx, red, wib, lane);
+      else big_gate<K, BWD, false, GL, CMP>(L, N, d, sm, err, xfer, gx, red, wib, lane);
     } else if (item < n_dense_items) {
       const int64_t i = (item - n_big) * kWarps + wib;
       if (i < n_med) {
         const DGate d = dense_gate<BWD, GL, PC>(L, N, wins, P.glist[n_big + i], A.piece_len);
-        if (d.n_in <= (uint32_t)kTabMaxIn) medium_gate<K, BWD, true, GL, CMP>(L, d, sm, err, lane);
-        else medium_gate<K, BWD, false, GL, CMP>(L, d, sm, err, lane);
+        if (d.n_in <= (uint32_t)kTabMaxIn) medium_gate<K, BWD, true, GL, CMP>(L, N, d, sm, err, lane);
+        else medium_gate<K, BWD, false, GL, CMP>(L, N, d, sm, err, lane);
       }
     } else {
       // ---- 256 sparse gates, one per thread
@@ -1127,8 +1140,11 @@ __global__ void __launch_bounds__(kWalkThreads,
         const WinDesc& W = wins[wg.x & kWindowMask];
         const int64_t g = wg.y;
         const int64_t ga = W.offsets[g], ge = W.offsets[g + 1];
-        float* my_tab = stab + threadIdx.x;
-        if (L.cells[N.cell[g]].n_in <= kGateTabMaxIn) stage_gate_table<BWD>(gt, g, my_tab);
+        const float* my_tab = stab + threadIdx.x;
+        if (kTabL1<BWD>)
+          my_tab = gt + (size_t)g * (BWD ? 2 : 1) * kGateTab;  // read in place, through L1
+        else if (L.cells[N.cell[g]].n_in <= kGateTabMaxIn)
+          stage_gate_table<BWD>(gt, g, stab + threadIdx.x);
         const WalkOut o = walk_gate<BWD, GL, CMP>(L, N, W, my_tab, sstg + threadIdx.x, sleak, err, g, W.rec + ga,
                                              (uint32_t)(ge - ga), (uint32_t)W.init[g], slast + threadIdx.x);
         if (BWD) {
