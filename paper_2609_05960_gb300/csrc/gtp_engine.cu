@@ -342,7 +342,7 @@ int build_plan(gtp_ctx* ctx, const std::vector<Window*>& ws, int32_t bin_ps, con
     d.bins = W.bins.as<float2>();
     d.tbins = nullptr;
     const bool pat = W.pat_loaded && ctx->pat_net_ok && !backward;
-    if (tiled || pat) {
+    if (tiled) {
       CU(W.tbins.reserve(sizeof(double2) * nb), "alloc FP64 bins");
       d.tbins = W.tbins.as<double2>();
     }

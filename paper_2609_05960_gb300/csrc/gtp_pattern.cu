@@ -20,14 +20,18 @@
 // state before the group's first record (Algorithm 1: lookups of a group use
 // the state held before it, the state changes after the whole group).  An
 // item starts from the initial state XOR the pin bits of the gate's earlier
-// items (k_pat_masks).  Leakage uses the step form of the merge: at the end
-// of each group the gate's leakage power changes by dP (Eq. 4 per interval,
-// Sec. 2.4.2 for the split over bins), which adds dP * ((b + 1) * bin_ps - t)
-// to the group's bin b and dP to its step accumulator; the initial power goes
-// into the window's L0.  All bin updates are FP64 reductions into the
-// window's tbins, one per distinct bin of the 32 records.  Glitch detection
-// (Sec. 2.4.1, Eq. 2) keeps each pin's last event time in shared memory; an
-// item first looks back over the earlier records of its first clock cycle.
+// items (k_pat_masks).  Leakage: at the end of each group the gate's power
+// changes to that of the state after the group, which holds until the next
+// group or the window's end (Eq. 4); the per-gate sum takes each such
+// interval, and the bins take the change in the merge's step form (Sec.
+// 2.4.2): dP * ((b + 1) * bin_ps - t) into the group's bin b and dP into its
+// step accumulator; the initial power goes into the window's L0.  Per-event
+// arithmetic is FP32 (the FP64 pipe of this GPU is slow): one {energy, step}
+// reduction per distinct bin of the 32 records into the window's bin
+// accumulators, per-gate sums in FP32 within an item and FP64 across items.
+// Glitch detection (Sec. 2.4.1, Eq. 2) keeps each pin's last event time in
+// shared memory; an item first looks back over the earlier records of its
+// first clock cycle.
 #include "gtp_internal.cuh"
 
 namespace gtp {
@@ -143,7 +147,10 @@ __global__ void __launch_bounds__(256) k_pat_prepare(PatLib P, PatNet Q, const W
       const uint32_t s0 = W.p_init[g];
       const float Pl = pat_leak(P, c, s0);
       p0 += (double)Pl;
-      W.p_e_leak[g] = (double)Pl * (double)W.window_ps * 1e-6;
+      // the initial state's leakage until the first group (the walk adds each later interval)
+      const int64_t a = W.p_off[g];
+      const uint32_t t1 = a < W.p_off[g + 1] ? min(W.p_rec[a].x, (uint32_t)W.window_ps) : (uint32_t)W.window_ps;
+      W.p_e_leak[g] = (double)Pl * (double)t1 * 1e-6;
       W.p_e_int[g] = 0.0;
       W.p_e_sw[g] = 0.0;
       W.p_e_gl[g] = 0.0;
@@ -236,7 +243,7 @@ __global__ void __launch_bounds__(kPatWarps * 32) k_pat_walk(PatLib P, PatNet Q,
       if (__ballot_sync(kFull, !in)) break;
     }
   }
-  double ei = 0.0, es = 0.0, eg = 0.0, el = 0.0;
+  float ei = 0.f, es = 0.f, eg = 0.f, el = 0.f;  // FP32 within the item (at most 16 terms a lane)
   // records are read 32 at a time, the next 32 loaded while these are walked; every lane reads its record
   // while it lies inside the gate, so the time after the item's last record comes from the lane after it
   constexpr uint2 kNone = {0xFFFFFFFFu, 0u};
@@ -313,27 +320,28 @@ __global__ void __launch_bounds__(kPatWarps * 32) k_pat_walk(PatLib P, PatNet Q,
     if (kind == 1) ei += E;
     else if (kind == 2) es += E;
     else if (kind == 3) eg += E;
-    // leakage: the change of power at the end of each group
+    // leakage: at the end of each group the power changes to that of the state after it, which holds until
+    // the next group (or the window's end); the bins take the change in step form
     const float Ppost = (tail && code == 0) ? pat_leak(P, c, Xi) : 0.f;
     const unsigned tl = __ballot_sync(kFull, tail) & ((1u << lane) - 1u);
     const float Pt = __shfl_sync(kFull, Ppost, tl ? 31 - __clz(tl) : 0);
     const float Pbefore = tl ? Pt : Pc;
-    const double dP = (tail && code == 0) ? (double)Ppost - (double)Pbefore : 0.0;
-    // bin updates: one FP64 reduction pair per distinct bin of the 32 records
+    const float dP = (tail && code == 0) ? Ppost - Pbefore : 0.f;
+    if (tail && code == 0) el += Ppost * (float)((tn < T ? tn : T) - t);
+    // bin updates: one {energy, step} reduction per distinct bin of the 32 records
     uint32_t b = 0xFFFFFFFFu;
-    double x = 0.0, y = 0.0;
+    float x = 0.f, y = 0.f;
     if (valid && code == 0) {
       b = bin_of(t, W.bin_magic, W.bin_shift, bin_ps);
-      x = (double)E + dP * (double)((b + 1u) * bin_ps - t) * 1e-6;
+      x = E + dP * (float)((b + 1u) * bin_ps - t) * 1e-6f;
       y = dP;
-      el += dP * (double)(T - t) * 1e-6;
     }
     const uint32_t bprev = __shfl_up_sync(kFull, b, 1);
     if (__any_sync(kFull, lane > 0 && b != 0xFFFFFFFFu && bprev == b)) {  // lanes share a bin: sum them first
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const double xo = __shfl_down_sync(kFull, x, o);
-        const double yo = __shfl_down_sync(kFull, y, o);
+        const float xo = __shfl_down_sync(kFull, x, o);
+        const float yo = __shfl_down_sync(kFull, y, o);
         const uint32_t bo = __shfl_down_sync(kFull, b, o);
         if (lane + o < 32 && bo == b) {
           x += xo;
@@ -341,11 +349,7 @@ __global__ void __launch_bounds__(kPatWarps * 32) k_pat_walk(PatLib P, PatNet Q,
         }
       }
     }
-    if (b != 0xFFFFFFFFu && (lane == 0 || bprev != b)) {
-      double* tb2 = reinterpret_cast<double*>(W.tbins + b);
-      if (x != 0.0) atomicAdd(tb2, x);
-      if (y != 0.0) atomicAdd(tb2 + 1, y);
-    }
+    if (b != 0xFFFFFFFFu && (lane == 0 || bprev != b)) red_bin(W.bins, b, x, y);
     // carries into the next 32 records
     const uint32_t Sg_n = tail ? Xi : Spre;
     const float Pc_n = tail ? Ppost : Pbefore;
@@ -354,15 +358,13 @@ __global__ void __launch_bounds__(kPatWarps * 32) k_pat_walk(PatLib P, PatNet Q,
     t_last = __shfl_sync(kFull, t, last_lane);
     S = __shfl_sync(kFull, Xi, 31);
   }
-  ei = warp_sum(ei);
-  es = warp_sum(es);
-  eg = warp_sum(eg);
-  el = warp_sum(el);
+  const double di = warp_sum((double)ei), ds = warp_sum((double)es), dg = warp_sum((double)eg),
+               dl = warp_sum((double)el) * 1e-6;
   if (lane == 0) {
-    if (ei != 0.0) atomicAdd(W.p_e_int + g, ei);
-    if (es != 0.0) atomicAdd(W.p_e_sw + g, es);
-    if (eg != 0.0) atomicAdd(W.p_e_gl + g, eg);
-    if (el != 0.0) atomicAdd(W.p_e_leak + g, el);
+    if (di != 0.0) atomicAdd(W.p_e_int + g, di);
+    if (ds != 0.0) atomicAdd(W.p_e_sw + g, ds);
+    if (dg != 0.0) atomicAdd(W.p_e_gl + g, dg);
+    if (dl != 0.0) atomicAdd(W.p_e_leak + g, dl);
     if (e == gb) W.p_final[g] = S;
   }
 }
