@@ -393,6 +393,8 @@ def run_ours(args, cfg_name):
     alg = algorithmic_bytes(n_ev, n_active, G, n_bins)
     # a reference rate for the walk's bin updates: 8-byte reductions into as many hashed slots as bins
     red_peak = gtpower.gtp_measure_reductions(ctx, n_bins, 2)
+    # and the window's own reduction stream alone (its records' bins, 8 records a thread), a floor for the walk
+    replay_ms = gtpower.gtp_measure_replay(ctx, 0, cfg.bin_ps)
     achieved = alg / walk_s / 1e9 if walk_s > 0 else 0.0
     oracle_err = None
     if opool is not None:  # every bin and every gate of this run against the FP64 oracle
@@ -517,10 +519,15 @@ def run_ours(args, cfg_name):
                                            "reference_rate_per_s": red_peak,
                                            "ratio": (n_ev / walk_s) / red_peak if walk_s > 0 and red_peak > 0
                                            else 0.0,
+                                           "replay_ms": replay_ms,
+                                           "walk_over_replay": walk_s * 1e3 / replay_ms if replay_ms > 0 else None,
                                            "note": "about one bin reduction per event; the reference rate is "
                                                    "gtp_measure_reductions (8-byte reductions spread by a hash "
                                                    "over as many slots as bins, in this run), not a roofline: "
-                                                   "the walk's own updates are local in time"}},
+                                                   "the walk's own updates are local in time; replay_ms is "
+                                                   "gtp_measure_replay, the window's own records' bin reductions "
+                                                   "alone (reading the records, one reduction per distinct bin of "
+                                                   "8 consecutive records), a floor for the walk"}},
             "oracle_error": oracle_err,
             "phases_ms": {"prepare": gate_s * 1e3, "scatter": plan_s * 1e3, "walk": walk_s * 1e3,
                           "merge": merge_s * 1e3},

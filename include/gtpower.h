@@ -526,6 +526,17 @@ int gtp_autotune(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_
  */
 int gtp_measure_reductions(gtp_ctx* ctx, int32_t n_slots, int32_t width, int64_t n_red, double* per_s);
 
+/*
+ * The bin reductions of a loaded window's own records, alone: each thread
+ * takes 8 consecutive records and issues one 8-byte reduction per distinct
+ * bin among them (the pattern of the walk's dense segments), into context
+ * scratch laid out as the walk's 8-byte bins; records outside the window
+ * are skipped.  Timed with CUDA events after one warm-up launch; *ms
+ * receives the time of one pass.  It is the walk's own reduction stream
+ * without the walk, a floor for it on this GPU.  Errors: GTP_EINVAL.
+ */
+int gtp_measure_replay(gtp_ctx* ctx, int32_t window, int32_t bin_ps, double* ms);
+
 /* Engine tuning knobs; value < 0 restores the default.  Keys:
  * "records_per_thread" (4, 8, 16; events per lane of a dense segment),
  * "ctas_per_sm" (0 = full occupancy), "dense_min" (gates with more events are cut into segments; 1..4096),

@@ -1780,6 +1780,37 @@ int gtp_measure_reductions(gtp_ctx* ctx, int32_t n_slots, int32_t width, int64_t
   return GTP_OK;
 }
 
+int gtp_measure_replay(gtp_ctx* ctx, int32_t window, int32_t bin_ps, double* ms) {
+  if (!ctx) return GTP_EINVAL;
+  Window* W = get_window(ctx, window);
+  if (!W || W->streamed || !ms || bin_ps <= 0 || W->window_ps % bin_ps != 0)
+    return fail(ctx, GTP_EINVAL, "measure_replay: a loaded window, bin_ps dividing its window_ps and an output");
+  DeviceGuard dg(ctx->device);
+  const int64_t nb = W->window_ps / bin_ps;
+  CU(ctx->probe.reserve(sizeof(float4) * (size_t)nb), "alloc probe");
+  CU(cudaMemsetAsync(ctx->probe.p, 0, sizeof(float4) * (size_t)nb, ctx->stream), "zero probe");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float4* slots = ctx->probe.as<float4>();
+  const uint2* rec = W->rec();
+  if (e == cudaSuccess)  // warm-up
+    e = launch_red_replay(rec, W->n_events, (int32_t)W->window_ps, bin_ps, slots, ctx->n_sm, ctx->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+  if (e == cudaSuccess)
+    e = launch_red_replay(rec, W->n_events, (int32_t)W->window_ps, bin_ps, slots, ctx->n_sm, ctx->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  CU(e, "measure_replay");
+  ctx->launches += 2;
+  *ms = (double)t;
+  return GTP_OK;
+}
+
 int gtp_load_pattern_cells(gtp_ctx* ctx, int32_t n_cells, const int32_t* n_in, float vdd, int32_t n_slew,
                            const float* slew_axis, int32_t n_load, const float* load_axis, const int32_t* int_offsets,
                            const int32_t* int_pin, const int32_t* int_edge, const uint32_t* int_care,

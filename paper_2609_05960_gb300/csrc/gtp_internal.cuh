@@ -340,6 +340,10 @@ cudaError_t launch_pattern_walk(const PatLib& P, const PatNet& Q, const WinDesc*
 // The reduction-rate probe: n_red reductions of `width` (2 or 4) floats into
 // hashed places of slots[n_slots] (16 B a slot).
 cudaError_t launch_red_probe(float4* slots, uint32_t n_slots, int width, int64_t n_red, int n_sm, cudaStream_t st);
+// The bin reductions of n records alone, one 8-byte reduction per distinct
+// bin of 8 consecutive records, into slots[window_ps / bin_ps] (16 B each).
+cudaError_t launch_red_replay(const uint2* rec, int64_t n, int32_t window_ps, int32_t bin_ps, float4* slots, int n_sm,
+                              cudaStream_t st);
 // Unpack records [r0, r0 + n) of the packed transfer form into out[0, n):
 // `anchors` holds the anchors of blocks r0 / 32 .. (r0 + n - 1) / 32, `words`
 // the n words (16-byte aligned).

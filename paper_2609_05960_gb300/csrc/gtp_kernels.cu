@@ -335,6 +335,45 @@ cudaError_t launch_red_probe(float4* slots, uint32_t n_slots, int width, int64_t
   return cudaGetLastError();
 }
 
+// The bin reductions of a window's own records, without the rest of the
+// walk: lane l of a warp takes 8 consecutive records and issues one 8-byte
+// reduction per distinct bin among them (the walk's dense-segment pattern),
+// into 8-byte bins laid out as the walk's (`slots` holds at least the
+// window's bin count of 16-byte slots).  Records out of the window are
+// skipped.
+static __global__ void k_red_replay(const uint2* __restrict__ rec, int64_t n, uint32_t T, uint32_t bin_ps,
+                                    uint32_t magic, uint32_t shift, float4* __restrict__ slots) {
+  constexpr int kPer = 8;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q * kPer < n; q += nth) {
+    const int64_t r0 = q * kPer;
+    uint32_t pb = 0xFFFFFFFFu;
+    float pe = 0.f;
+    for (int k = 0; k < kPer && r0 + k < n; ++k) {
+      const uint32_t t = rec[r0 + k].x;
+      if (t >= T) continue;
+      const uint32_t b = bin_of(t, magic, shift, bin_ps);
+      if (b != pb) {
+        if (pb != 0xFFFFFFFFu) red_bin(reinterpret_cast<float2*>(slots), pb, pe, 0.5f);
+        pb = b;
+        pe = 0.f;
+      }
+      pe += 1.f;
+    }
+    if (pb != 0xFFFFFFFFu) red_bin(reinterpret_cast<float2*>(slots), pb, pe, 0.5f);
+  }
+}
+
+cudaError_t launch_red_replay(const uint2* rec, int64_t n, int32_t window_ps, int32_t bin_ps, float4* slots, int n_sm,
+                              cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  uint32_t magic, shift;
+  bin_magic(bin_ps, &magic, &shift);
+  const unsigned grid = (unsigned)(n_sm > 0 ? n_sm * 8 : 1024);
+  k_red_replay<<<grid, 256, 0, st>>>(rec, n, (uint32_t)window_ps, (uint32_t)bin_ps, magic, shift, slots);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ packed transfer form
 // Four records a thread: one 16-byte load of words, two 16-byte stores of
 // records; t = anchor of the record's block + the word's high 27 bits.

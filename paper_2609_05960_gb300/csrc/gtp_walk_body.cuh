@@ -1058,7 +1058,7 @@ __host__ __device__ inline size_t union_area(int K, int n_leak, bool bwd, bool g
 #endif
 template <int K, bool BWD, bool GL, bool CMP, bool PC>
 __global__ void __launch_bounds__(kWalkThreads,
-                                  K == 16 ? 2 : (BWD ? GTP_WALK_MINB_BWD : (GL ? GTP_WALK_MINB_GL : GTP_WALK_MINB)))
+                                  K == 16 ? 2 : (GL ? GTP_WALK_MINB_GL : (BWD ? GTP_WALK_MINB_BWD : GTP_WALK_MINB)))
     k_walk(LibView L, NetView N, WalkArgs A) {
   constexpr int SEG = 32 * K;
   extern __shared__ __align__(16) unsigned char smem[];

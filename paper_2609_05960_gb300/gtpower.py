@@ -35,7 +35,7 @@ ABI_SYMBOLS = ["gtp_create", "gtp_destroy", "gtp_set_stream", "gtp_last_error", 
                "gtp_run_power_streamed", "gtp_design_power", "gtp_run_power_components",
                "gtp_run_power_scheme", "gtp_sipl_expand",
                "gtp_pack_events", "gtp_measure_reductions", "gtp_load_pattern_cells", "gtp_load_pattern_netlist",
-               "gtp_load_pattern_events", "gtp_pattern_gate_energy"]
+               "gtp_load_pattern_events", "gtp_pattern_gate_energy", "gtp_measure_replay"]
 
 
 class GtpError(RuntimeError):
@@ -74,6 +74,7 @@ def load(path: str = LIB_PATH):
         "gtp_run_power_components": ([P, I32, I32, P, P, ctypes.c_int], ctypes.c_int),
         "gtp_pack_events": ([I64, P, P], ctypes.c_int),
         "gtp_measure_reductions": ([P, I32, I32, I64, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "gtp_measure_replay": ([P, I32, I32, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "gtp_sipl_expand": ([I32, I32, I32, I32, P, P, P, P, P, P, I32, P, P, P, F, P, P], ctypes.c_int),
         "gtp_run_power_scheme": ([P, I32, I32, I32, P, ctypes.c_int, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
         "gtp_gate_energy": ([P, I32, P, P, P, P, P, ctypes.c_int], ctypes.c_int),
@@ -187,6 +188,13 @@ def gtp_measure_reductions(ctx, n_slots: int, width: int = 2, n_red: int = 160_0
     """Bin-update reductions per second the GPU sustains (see the header)."""
     out = ctypes.c_double(0.0)
     _check(ctx, load().gtp_measure_reductions(ctx, int(n_slots), int(width), int(n_red), ctypes.byref(out)))
+    return float(out.value)
+
+
+def gtp_measure_replay(ctx, window: int, bin_ps: int) -> float:
+    """Time (ms) of the window's own bin reductions alone (see the header)."""
+    out = ctypes.c_double(0.0)
+    _check(ctx, load().gtp_measure_replay(ctx, int(window), int(bin_ps), ctypes.byref(out)))
     return float(out.value)
 
 

@@ -66,7 +66,7 @@ def _declarations():
 
 # Handle and plumbing calls of the boundary that carry no method of the paper.
 PLUMBING = {"gtp_create", "gtp_destroy", "gtp_set_stream", "gtp_last_error", "gtp_set_param", "gtp_get_param",
-            "gtp_measure_reductions", "gtp_pack_events"}
+            "gtp_measure_reductions", "gtp_measure_replay", "gtp_pack_events"}
 
 
 def test_every_method_entry_point_cites_its_source():
