@@ -1676,7 +1676,8 @@ int gtp_run_power_backward(gtp_ctx* ctx, int32_t window, int32_t bin_ps, const f
   mark(ctx, 1, st);
   ctx->launches += 4;
   mark(ctx, 2, st);
-  const WalkArgs A = walk_args(ctx, 1);
+  WalkArgs A = walk_args(ctx, 1);
+  A.whole = ctx->run_whole;
   if (W->n_events > 0) CU(launch_plan(ctx->N, ctx->L, A, st), "plan");
   mark(ctx, 3, st);
   mark(ctx, 4, st);

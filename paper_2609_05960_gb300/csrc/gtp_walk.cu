@@ -290,8 +290,11 @@ cudaError_t launch_plan(const NetView& N, const LibView& L, const WalkArgs& A, c
 
 cudaError_t launch_walk(const LibView& L, const NetView& N, const WalkArgs& A, bool backward, cudaStream_t st) {
   if (!backward && A.comp) return launch_walk_components(L, N, A, st);
-  if (N.clock_ps > 0) return launch_walk_glitch(L, N, A, backward, st);
-  if (!backward && A.whole) return launch_walk_plain_whole(L, N, A, st);
+  if (N.clock_ps > 0) {
+    if (!backward && A.whole) return launch_walk_glitch_whole(L, N, A, st);
+    return launch_walk_glitch(L, N, A, backward, st);
+  }
+  if (A.whole) return backward ? launch_walk_adjoint_whole(L, N, A, st) : launch_walk_plain_whole(L, N, A, st);
   return launch_walk_gl<false>(L, N, A, backward, st);
 }
 

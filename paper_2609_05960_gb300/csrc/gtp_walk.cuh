@@ -64,8 +64,8 @@ struct WalkArgs {
   int32_t* chunks;          // tiled walk: chunk starts in the tiled list (capacity tile_chunk_cap(n_gates))
   int64_t piece_len;        // gates with more events are split into pieces of this many (0: none); a
                             // multiple of kPieceUnit
-  bool whole;               // plain forward runs: no gate of the run has more than piece_len events, so the
-                            // walk compiled without pieces is launched
+  bool whole;               // no gate of the run has more than piece_len events, so the walk compiled without
+                            // pieces is launched (forward and adjoint runs)
 };
 
 // Work-list entries are {window | piece << kPieceShift, gate}.
@@ -104,8 +104,11 @@ cudaError_t launch_walk_glitch(const LibView& L, const NetView& N, const WalkArg
 // The forward walk (with or without glitch detection) that also accumulates
 // each window's component bins (WinDesc::cbins), in its own translation unit.
 cudaError_t launch_walk_components(const LibView& L, const NetView& N, const WalkArgs& A, cudaStream_t st);
-// The plain forward walk compiled for runs without split gates (A.whole).
+// The forward walk (plain or with glitch detection) and the adjoint walk
+// compiled for runs without split gates (A.whole).
 cudaError_t launch_walk_plain_whole(const LibView& L, const NetView& N, const WalkArgs& A, cudaStream_t st);
+cudaError_t launch_walk_glitch_whole(const LibView& L, const NetView& N, const WalkArgs& A, cudaStream_t st);
+cudaError_t launch_walk_adjoint_whole(const LibView& L, const NetView& N, const WalkArgs& A, cudaStream_t st);
 cudaError_t launch_gate_tables(const LibView& L, const NetView& N, float* gtab, float* gtab_bwd, cudaStream_t st);
 
 }  // namespace gtp

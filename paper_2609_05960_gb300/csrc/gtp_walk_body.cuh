@@ -1187,13 +1187,13 @@ cudaError_t launch_walk_k(const LibView& L, const NetView& N, const WalkArgs& A,
   return cudaGetLastError();
 }
 
-// The plain forward walk of a run with no gate split into pieces.
-template <bool GL>
+// The walk of a run with no gate split into pieces (BWD: the adjoint).
+template <bool BWD, bool GL>
 cudaError_t launch_walk_whole(const LibView& L, const NetView& N, const WalkArgs& A, cudaStream_t st) {
   switch (A.rpt) {
-    case 4: return launch_walk_k<4, false, GL, false, false>(L, N, A, st);
-    case 16: return launch_walk_k<16, false, GL, false, false>(L, N, A, st);
-    default: return launch_walk_k<8, false, GL, false, false>(L, N, A, st);
+    case 4: return launch_walk_k<4, BWD, GL, false, false>(L, N, A, st);
+    case 16: return launch_walk_k<16, BWD, GL, false, false>(L, N, A, st);
+    default: return launch_walk_k<8, BWD, GL, false, false>(L, N, A, st);
   }
 }
 

@@ -7,7 +7,7 @@
 namespace gtp {
 
 cudaError_t launch_walk_plain_whole(const LibView& L, const NetView& N, const WalkArgs& A, cudaStream_t st) {
-  return launch_walk_whole<false>(L, N, A, st);
+  return launch_walk_whole<false, false>(L, N, A, st);
 }
 
 }  // namespace gtp
