@@ -93,22 +93,23 @@ __global__ void k_event_desc(LibView L, NetView N, uint4* __restrict__ desc) {
 // one gate's table, lane e its entry e, so each row is written as one
 // coalesced 128-byte line (slots past the cell's entries are left unwritten:
 // nothing reads them).
-__global__ void k_gate_tables(LibView L, NetView N, float* __restrict__ gtab, float* __restrict__ gbwd) {
+__global__ void __launch_bounds__(256, 4) k_gate_tables(LibView L, NetView N, float* __restrict__ gtab,
+                                                     float* __restrict__ gbwd) {
   constexpr int kG = 4;  // gates a warp takes at once: their loads are independent and overlap
   const uint32_t e = threadIdx.x & 31u;
   const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t g0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kG; g0 < N.n_gates;
        g0 += n_warps * kG) {
     int32_t c[kG];
-    CellInfo ci[kG];
+    uint32_t nin[kG];
     uint4 d[kG];
 #pragma unroll
     for (int k = 0; k < kG; ++k) c[k] = g0 + k < N.n_gates ? __ldg(N.cell + g0 + k) : 0;
 #pragma unroll
-    for (int k = 0; k < kG; ++k) ci[k] = L.cells[c[k]];
+    for (int k = 0; k < kG; ++k) nin[k] = (uint32_t)L.cells[c[k]].n_in;
 #pragma unroll
     for (int k = 0; k < kG; ++k) {
-      const uint32_t n_in = (uint32_t)ci[k].n_in;
+      const uint32_t n_in = nin[k];
       const uint32_t pin = min(e >> n_in, n_in), s = e & ((1u << n_in) - 1u);
       const uint32_t val = pin < n_in ? (((s >> pin) & 1u) ^ 1u) : 0u;  // own bit: the value before the edge
       d[k] = g0 + k < N.n_gates ? __ldg(N.desc + (size_t)(g0 + k) * N.dstride + pin * 2u + val) : make_uint4(0, 0, 0, 0);
@@ -116,7 +117,7 @@ __global__ void k_gate_tables(LibView L, NetView N, float* __restrict__ gtab, fl
 #pragma unroll
     for (int k = 0; k < kG; ++k) {
       const int64_t g = g0 + k;
-      const uint32_t n_in = (uint32_t)ci[k].n_in;
+      const uint32_t n_in = nin[k];
       if (g >= N.n_gates || n_in > (uint32_t)kGateTabMaxIn || e >= ((n_in + 1u) << n_in)) continue;
       const uint32_t pin = e >> n_in, s = e & ((1u << n_in) - 1u);
       float eu, ed, ef;

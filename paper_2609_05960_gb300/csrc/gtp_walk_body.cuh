@@ -404,7 +404,7 @@ __device__ __forceinline__ SegSums seg_back(const LibView& L, const NetView& N, 
   float Gcur = 0.f;
   if (BWD && q.t_before < d.T && !q.fh) {
     const uint32_t bb = bin_of(q.t_before, d.magic, d.shift, d.bin_ps);
-    const float2 gv = d.W->grad[bb];
+    const float2 gv = __ldg(d.W->grad + bb);
     Gcur = gv.y + gv.x * (float)(q.t_before - bb * d.bin_ps);
   }
   const uint32_t rb = row_base<K>(lane);
@@ -422,7 +422,7 @@ __device__ __forceinline__ SegSums seg_back(const LibView& L, const NetView& N, 
     const uint32_t bn = bin_end_of(t, d, bend);
     float Gt = 0.f, gE = 0.f;
     if (BWD) {
-      const float2 gv = d.W->grad[bn];
+      const float2 gv = __ldg(d.W->grad + bn);
       gE = gv.x;
       Gt = gv.y + gv.x * (float)(t - (bend - d.bin_ps));
       v2 = head ? fmaf(Pcur, Gt - Gcur, v2) : v2;
@@ -893,7 +893,7 @@ __device__ __forceinline__ WalkOut walk_gate(const LibView& L, const NetView& N,
       const uint32_t bn = bin_of(t, magic, shift, bin_ps);
       float gE = 0.f, Gt = 0.f;
       if (BWD) {
-        const float2 gv = W.grad[bn];
+        const float2 gv = __ldg(W.grad + bn);
         gE = gv.x;
         Gt = gv.y + gv.x * (float)(t - bn * bin_ps);
         if (head) acc.f2 += Pcur * (Gt - Gcur);
@@ -911,8 +911,13 @@ __device__ __forceinline__ WalkOut walk_gate(const LibView& L, const NetView& N,
         // entry (pin, input state with the pin's own bit = its value before the edge)
         const uint32_t own = (val - 1u) & bitp & inmask;
         const uint32_t idx = (pin << n_in) | (spre & inmask & ~bitp) | own;
-        E = tabl[idx * kTabStride<BWD>];
-        if (BWD) dE = tabl[(kGateTab + idx) * kTabStride<BWD>] * (is_out ? 1.f : esc);
+        if (kTabL1<BWD>) {  // the table in place: read-only loads
+          E = __ldg(tabl + idx);
+          if (BWD) dE = __ldg(tabl + kGateTab + idx) * (is_out ? 1.f : esc);
+        } else {
+          E = tabl[idx * kTabStride<BWD>];
+          if (BWD) dE = tabl[(kGateTab + idx) * kTabStride<BWD>] * (is_out ? 1.f : esc);
+        }
       } else if (is_out) {
         E = BWD ? 0.f : __uint_as_float(__ldg(dsc + 2u * n_in).w);
         dE = L.half_v2;
