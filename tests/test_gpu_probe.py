@@ -19,3 +19,29 @@ def test_reduction_probe_rates_and_rejections():
                 gtpower.gtp_measure_reductions(e.ctx, *bad)
     finally:
         e.close()
+
+
+def test_replay_probe_times_a_window_and_rejects_bad_arguments():
+    """gtp_measure_replay: a positive time that grows with the records, and
+    the argument checks (no such window, a bin size that does not divide the
+    window)."""
+    import synth
+    from paper_2609_05960_gb300 import Engine, GtpError, gtpower
+    lib = synth.make_library(1)
+    net = synth.make_netlist(lib, 20_000, seed=2)
+    e = Engine(0)
+    try:
+        e.load_library(lib)
+        e.load_netlist(net)
+        times = []
+        for w, n_ev in enumerate((200_000, 4_000_000)):
+            tr = synth.make_trace(net, synth.zipf_counts(net.n_gates, n_ev, 1.2, None, 3 + w), 1_000_000, 3 + w)
+            e.load_events(w, tr)
+            times.append(gtpower.gtp_measure_replay(e.ctx, w, 10))
+        assert 0.0 < times[0] < times[1]
+        with pytest.raises(GtpError):
+            gtpower.gtp_measure_replay(e.ctx, 7, 10)
+        with pytest.raises(GtpError):
+            gtpower.gtp_measure_replay(e.ctx, 0, 7)
+    finally:
+        e.close()
