@@ -671,7 +671,8 @@ int ensure_pattern_index(gtp_ctx* ctx) {
   ctx->P.lidx = ctx->pc_lidx.as<float>();
   for (size_t c = 0; c < ctx->h_pat_cells.size(); ++c)
     if (ctx->h_pat_cells[c].iidx >= 0) {
-      CU(launch_pattern_index(ctx->P, (int32_t)c, ctx->h_pat_cells[c].n_in, ctx->stream), "pattern index");
+      CU(launch_pattern_index(ctx->P, (int32_t)c, ctx->h_pat_cells[c].n_in, ctx->pc_iidx.as<int32_t>(),
+                              ctx->pc_lidx.as<float>(), ctx->stream), "pattern index");
       ctx->launches += 1;
     }
   CU(cudaStreamSynchronize(ctx->stream), "pattern index");

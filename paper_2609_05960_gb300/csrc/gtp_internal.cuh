@@ -326,12 +326,17 @@ cudaError_t launch_validate_if(const LibView& L, const NetView& N, const WinDesc
 int merge_tiles(int n_bins);
 // Pattern gates: a gate's records are cut into items of kPatPiece records
 // (each item extended to the end of the timestamp group it ends in).
-constexpr int64_t kPatPiece = 512;
+#ifndef GTP_PAT_PIECE
+#define GTP_PAT_PIECE 512
+#endif
+constexpr int64_t kPatPiece = GTP_PAT_PIECE;
 // Pattern records {t, pin | value << 8} from the ABI's arrays (device).
 cudaError_t launch_pattern_pack(const int32_t* t, const uint8_t* pin, const uint8_t* value, int64_t n, uint2* out,
                                 cudaStream_t st);
-// State-indexed arrays of pattern cell c (its iidx / lidx set).
-cudaError_t launch_pattern_index(const PatLib& P, int32_t c, int32_t n_in, cudaStream_t st);
+// State-indexed arrays of pattern cell c (its iidx / lidx offsets set) into
+// iidx / lidx, the arrays PatLib::iidx / lidx point to.
+cudaError_t launch_pattern_index(const PatLib& P, int32_t c, int32_t n_in, int32_t* iidx, float* lidx,
+                                 cudaStream_t st);
 // The pattern gates of the windows: initial leakage, items' pin masks, and
 // the walk into each window's tbins; errors as the smallest key
 // ((window << 40 | record) << 3) | -code in *bad (see launch_validate).

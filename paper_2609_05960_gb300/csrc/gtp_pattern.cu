@@ -75,14 +75,16 @@ __device__ __forceinline__ float pat_leak(const PatLib& P, const PatCell& c, uin
 }
 
 // ------------------------------------------------------------------ state-indexed arrays
-__global__ void k_pat_index(PatLib P, int32_t c) {
+// Cell c's arrays: table ids into iidx_all + its iidx, leakage into
+// lidx_all + its lidx (the PatLib's arrays, written here only).
+__global__ void k_pat_index(PatLib P, int32_t c, int32_t* __restrict__ iidx_all, float* __restrict__ lidx_all) {
   const PatCell cell = P.cells[c];
   const int n_in = cell.n_in;
   const int64_t n_side = 1ll << (n_in - 1);
   const int64_t n_int = (int64_t)n_in * 2 * n_side;
   const int64_t n_leak = 2ll << n_in;
-  int32_t* iidx = const_cast<int32_t*>(P.iidx) + cell.iidx;
-  float* lidx = const_cast<float*>(P.lidx) + cell.lidx;
+  int32_t* iidx = iidx_all + cell.iidx;
+  float* lidx = lidx_all + cell.lidx;
   PatCell scan = cell;
   scan.iidx = -1;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_int + n_leak;
@@ -390,11 +392,12 @@ cudaError_t launch_pattern_pack(const int32_t* t, const uint8_t* pin, const uint
   return cudaGetLastError();
 }
 
-cudaError_t launch_pattern_index(const PatLib& P, int32_t c, int32_t n_in, cudaStream_t st) {
+cudaError_t launch_pattern_index(const PatLib& P, int32_t c, int32_t n_in, int32_t* iidx, float* lidx,
+                                 cudaStream_t st) {
   const int64_t n = (int64_t)n_in * (1ll << n_in) + (2ll << n_in);
   int64_t blocks = (n + 255) / 256;
   if (blocks > 8192) blocks = 8192;
-  k_pat_index<<<(unsigned)blocks, 256, 0, st>>>(P, c);
+  k_pat_index<<<(unsigned)blocks, 256, 0, st>>>(P, c, iidx, lidx);
   return cudaGetLastError();
 }
 
