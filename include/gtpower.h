@@ -180,8 +180,9 @@ int gtp_sipl_expand(int32_t n_in, int32_t n_slew, int32_t n_load, int32_t n_int_
  * same definition (Algorithm 1: groups of equal timestamps, lookups at the
  * pre-group state; Sec. 2.2, Eq. 1, Eq. 4, Sec. 2.4.2; glitch detection of
  * Sec. 2.4.1 and Eq. 2 when gtp_set_glitch is on, with the transition times
- * given here), and add into the same waveform; gtp_design_power includes
- * them.  gtp_run_power_components, gtp_run_power_backward and
+ * given here), and add into the same waveform (and, in
+ * gtp_run_power_components, into the component waveforms);
+ * gtp_design_power includes them.  gtp_run_power_backward and
  * gtp_run_power_scheme return GTP_EINVAL for a window with pattern gates.
  * ------------------------------------------------------------------------ */
 #define GTP_MAX_PATTERN_PINS 32

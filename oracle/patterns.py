@@ -70,16 +70,21 @@ def _split_range(bins, diff, P, a, b, bin_ps):
         diff[k1] -= P * bin_ps * 1e-6
 
 
-def walk(plib, pnet, ptrace, bin_ps: int, glitch_clock_ps: int = 0, gates=None, range_split: bool = True) -> dict:
+def walk(plib, pnet, ptrace, bin_ps: int, glitch_clock_ps: int = 0, gates=None, range_split: bool = True,
+         components: bool = False) -> dict:
     """Bins (fJ) and per-gate results (e_leak, e_int, e_sw, e_gl in fJ,
     n_events, final_state as uint32) of the selected gates (default all).
-    The output transition times for glitch detection are pnet.out_slew_ps."""
+    The output transition times for glitch detection are pnet.out_slew_ps.
+    With ``components``, ``comp_bins`` [4][n_bins] splits the bins into
+    leakage, internal, switching and glitch energy (Sec. 2.2's components)."""
     T = int(ptrace.window_ps)
     if bin_ps <= 0 or T % bin_ps:
         raise ValueError("window_ps must be a multiple of bin_ps")
     n_bins = T // bin_ps
     bins = np.zeros(n_bins, np.float64)
     diff = np.zeros(n_bins + 1, np.float64) if range_split else None
+    comp = np.zeros((4, n_bins), np.float64) if components else None
+    cdiff = np.zeros(n_bins + 1, np.float64) if components and range_split else None
     sel = np.arange(pnet.n_gates) if gates is None else np.asarray(gates, np.int64)
     out = {k: np.zeros(len(sel), np.float64) for k in ("e_leak", "e_int", "e_sw", "e_gl")}
     out["n_events"] = np.zeros(len(sel), np.int64)
@@ -87,8 +92,15 @@ def walk(plib, pnet, ptrace, bin_ps: int, glitch_clock_ps: int = 0, gates=None, 
     half_v2 = 0.5 * float(plib.vdd) * float(plib.vdd)
     cells = {}
     clk = int(glitch_clock_ps)
-    split = (lambda P, a, b: _split_range(bins, diff, P, a, b, bin_ps)) if range_split else \
-        (lambda P, a, b: _split(bins, P, a, b, bin_ps))
+    def split(P, a, b):
+        if range_split:
+            _split_range(bins, diff, P, a, b, bin_ps)
+            if comp is not None:
+                _split_range(comp[0], cdiff, P, a, b, bin_ps)
+        else:
+            _split(bins, P, a, b, bin_ps)
+            if comp is not None:
+                _split(comp[0], P, a, b, bin_ps)
     for i, g in enumerate(sel):
         g = int(g)
         c = int(pnet.cell[g])
@@ -137,10 +149,15 @@ def walk(plib, pnet, ptrace, bin_ps: int, glitch_clock_ps: int = 0, gates=None, 
                         x = 2.0 * (t - last[pin]) / sum_slew
                         E *= min(1.0, x * x)
                     Eg += E
+                    kind = 3
                 elif pin < n_in:
                     Ei += E
+                    kind = 1
                 else:
                     Es += E
+                    kind = 2
+                if comp is not None:
+                    comp[kind, t // bin_ps] += E
                 last[pin] = t
                 bins[t // bin_ps] += E
             S = S_next
@@ -154,5 +171,9 @@ def walk(plib, pnet, ptrace, bin_ps: int, glitch_clock_ps: int = 0, gates=None, 
         out["final_state"][i] = S
     if range_split:
         bins += np.cumsum(diff[:-1])
+        if comp is not None:
+            comp[0] += np.cumsum(cdiff[:-1])
     out["bins"] = bins
+    if comp is not None:
+        out["comp_bins"] = comp
     return out

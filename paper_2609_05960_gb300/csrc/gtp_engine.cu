@@ -722,8 +722,6 @@ int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, dou
     for (Window* w : ws)
       if (w->pat_loaded) ctx->run_pat_items = std::max(ctx->run_pat_items, w->pat_n_items);
   if (ctx->run_pat_items >= 0) {
-    if (components) return fail(ctx, GTP_EINVAL, "run_power_components: windows with pattern gates are walked by "
-                                                 "gtp_run_power and gtp_run_power_batched only");
     RC(ensure_pattern_index(ctx));
     CU(ctx->pat_bad.reserve(sizeof(unsigned long long)), "alloc pattern status");
   }
@@ -1325,8 +1323,9 @@ int gtp_run_power_scheme(gtp_ctx* ctx, int32_t window, int32_t bin_ps, int32_t s
   Window* W = get_window(ctx, window);
   if (!W || W->streamed) return fail(ctx, GTP_EINVAL, "run_power_scheme: window not loaded");
   if (W->pat_loaded && ctx->pat_net_ok)
-    return fail(ctx, GTP_EINVAL, "run_power_scheme: windows with pattern gates are walked by gtp_run_power and "
-                                 "gtp_run_power_batched only");
+    return fail(ctx, GTP_EINVAL,
+                "run_power_scheme: windows with pattern gates are walked by gtp_run_power, gtp_run_power_batched "
+                "and gtp_run_power_components only");
   if (bin_ps <= 0 || W->window_ps % bin_ps != 0) return fail(ctx, GTP_ERANGE, "window_ps must be a multiple of bin_ps > 0");
   const int64_t nb = W->window_ps / bin_ps;
   const int64_t G = ctx->N.n_gates;
@@ -1641,8 +1640,9 @@ int gtp_run_power_backward(gtp_ctx* ctx, int32_t window, int32_t bin_ps, const f
   Window* W = get_window(ctx, window);
   if (!W || W->streamed) return fail(ctx, GTP_EINVAL, "run_power_backward: window not loaded");
   if (W->pat_loaded && ctx->pat_net_ok)
-    return fail(ctx, GTP_EINVAL, "run_power_backward: windows with pattern gates are walked by gtp_run_power and "
-                                 "gtp_run_power_batched only");
+    return fail(ctx, GTP_EINVAL,
+                "run_power_backward: windows with pattern gates are walked by gtp_run_power, gtp_run_power_batched "
+                "and gtp_run_power_components only");
   ctx->run_pat_items = -1;
   if (!dL_dP) return fail(ctx, GTP_EINVAL, "run_power_backward: dL_dP is required");
   if (bin_ps <= 0 || W->window_ps % bin_ps != 0)

@@ -28,7 +28,10 @@
 // step accumulator; the initial power goes into the window's L0.  Per-event
 // arithmetic is FP32 (the FP64 pipe of this GPU is slow): one {energy, step}
 // reduction per distinct bin of the 32 records into the window's bin
-// accumulators, per-gate sums in FP32 within an item and FP64 across items.
+// accumulators (in a component run, each record's internal, switching,
+// glitch and leakage-correction parts into the component accumulators, as
+// the fused walk lays them out), per-gate sums in FP32 within an item and
+// FP64 across items.
 // Glitch detection (Sec. 2.4.1, Eq. 2) keeps each pin's last event time in
 // shared memory; an item first looks back over the earlier records of its
 // first clock cycle.
@@ -332,26 +335,39 @@ __global__ void __launch_bounds__(kPatWarps * 32) k_pat_walk(PatLib P, PatNet Q,
     if (tail && code == 0) el += Ppost * (float)((tn < T ? tn : T) - t);
     // bin updates: one {energy, step} reduction per distinct bin of the 32 records
     uint32_t b = 0xFFFFFFFFu;
-    float x = 0.f, y = 0.f;
+    float x = 0.f, y = 0.f, corr = 0.f;
     if (valid && code == 0) {
       b = bin_of(t, W.bin_magic, W.bin_shift, bin_ps);
-      x = E + dP * (float)((b + 1u) * bin_ps - t) * 1e-6f;
+      corr = dP * (float)((b + 1u) * bin_ps - t) * 1e-6f;  // the step's share of this bin
+      x = E + corr;
       y = dP;
     }
-    const uint32_t bprev = __shfl_up_sync(kFull, b, 1);
-    if (__any_sync(kFull, lane > 0 && b != 0xFFFFFFFFu && bprev == b)) {  // lanes share a bin: sum them first
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const float xo = __shfl_down_sync(kFull, x, o);
-        const float yo = __shfl_down_sync(kFull, y, o);
-        const uint32_t bo = __shfl_down_sync(kFull, b, o);
-        if (lane + o < 32 && bo == b) {
-          x += xo;
-          y += yo;
+    if (W.cbins) {  // a component run: every record's components, laid out as the fused walk's (WinDesc::cbins)
+      if (b != 0xFFFFFFFFu) {
+        const float ki = kind == 1 ? E : 0.f, ks = kind == 2 ? E : 0.f, kg = kind == 3 ? E : 0.f;
+        if (W.cpack) {
+          red_cbin(W.cbins, b, ki, ks, corr, y);
+        } else {
+          red_bin(W.bins, b, x, y);
+          red_cbin(W.cbins, b, ki, ks, kg, corr);
         }
       }
+    } else {
+      const uint32_t bprev = __shfl_up_sync(kFull, b, 1);
+      if (__any_sync(kFull, lane > 0 && b != 0xFFFFFFFFu && bprev == b)) {  // lanes share a bin: sum them first
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const float xo = __shfl_down_sync(kFull, x, o);
+          const float yo = __shfl_down_sync(kFull, y, o);
+          const uint32_t bo = __shfl_down_sync(kFull, b, o);
+          if (lane + o < 32 && bo == b) {
+            x += xo;
+            y += yo;
+          }
+        }
+      }
+      if (b != 0xFFFFFFFFu && (lane == 0 || bprev != b)) red_bin(W.bins, b, x, y);
     }
-    if (b != 0xFFFFFFFFu && (lane == 0 || bprev != b)) red_bin(W.bins, b, x, y);
     // carries into the next 32 records
     const uint32_t Sg_n = tail ? Xi : Spre;
     const float Pc_n = tail ? Ppost : Pbefore;

@@ -182,3 +182,24 @@ def test_generator_toggles_every_pin():
         for p, v in zip(ptr.pin[a:b], ptr.value[a:b]):
             assert p < pnet.n_pins[g] and ((S >> int(p)) & 1) != v
             S ^= 1 << int(p)
+
+
+@pytest.mark.parametrize("clock", [0, 300])
+def test_components_equal_the_c_oracle_and_add_up(clock):
+    """The per-component bins (leakage, internal, switching, glitch) on small
+    cells equal the C oracle's, and on the wide cells they add up to the bins
+    and, per component, to the per-gate energies."""
+    plib, pnet, ptr, small = _small_case(6, n_events=5000, window=10000)
+    lib, net, tr = _dense_equivalent(plib, pnet, ptr, small)
+    want = oracle.walk(lib, net, tr, 20, glitch=(clock, pnet.out_slew_ps) if clock else None, components=True)
+    got = opat.walk(plib, pnet, ptr, 20, glitch_clock_ps=clock, components=True)
+    _close(got["comp_bins"], want["comp_bins"])
+    plib = spat.make_pattern_library(2)
+    w = [1.0 if plib.n_in[c] >= 11 else 0.0 for c in range(plib.n_cells)]
+    pnet = spat.make_pattern_netlist(plib, 10, seed=5, weights=w)
+    ptr = spat.make_pattern_trace(pnet, np.array([300, 20, 0, 900, 5, 40, 600, 1, 2, 77]), 20000, 6, tie_p=0.1,
+                                  clock_pin_share=0.3)
+    r = opat.walk(plib, pnet, ptr, 50, glitch_clock_ps=clock, components=True)
+    _close(r["comp_bins"].sum(axis=0), r["bins"])
+    for row, k in enumerate(("e_leak", "e_int", "e_sw", "e_gl")):
+        _close(r["comp_bins"][row].sum(), r[k].sum())
