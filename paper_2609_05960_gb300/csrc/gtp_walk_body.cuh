@@ -1009,11 +1009,14 @@ __device__ __forceinline__ WalkOut walk_gate(const LibView& L, const NetView& N,
 
 // This thread's gate table into its column of the CTA's staged tables.
 template <bool BWD>
-__device__ __forceinline__ void stage_gate_table(const float* __restrict__ gt, int64_t g, float* stab) {
+__device__ __forceinline__ void stage_gate_table(const float* __restrict__ gt, int64_t g, float* stab, uint32_t n_in) {
   constexpr int kN = BWD ? 2 * kGateTab : kGateTab;
   const float4* src = reinterpret_cast<const float4*>(gt + (size_t)g * kN);
+  // only the cell's entries: 4, 12 or 32 for 1, 2 or 3 inputs (the forward table; the adjoint's two halves whole)
+  const int nq = BWD ? kN / 4 : (int)((((n_in + 1u) << n_in) + 3u) >> 2);
 #pragma unroll
   for (int q = 0; q < kN / 4; ++q) {
+    if (q >= nq) break;
     const float4 v = __ldg(src + q);
     stab[(4 * q + 0) * kWalkThreads] = v.x;
     stab[(4 * q + 1) * kWalkThreads] = v.y;
@@ -1148,8 +1151,8 @@ __global__ void __launch_bounds__(kWalkThreads,
         const float* my_tab = stab + threadIdx.x;
         if (kTabL1<BWD>)
           my_tab = gt + (size_t)g * (BWD ? 2 : 1) * kGateTab;  // read in place, through L1
-        else if (L.cells[N.cell[g]].n_in <= kGateTabMaxIn)
-          stage_gate_table<BWD>(gt, g, stab + threadIdx.x);
+        else if (const uint32_t nin = (uint32_t)L.cells[N.cell[g]].n_in; nin <= (uint32_t)kGateTabMaxIn)
+          stage_gate_table<BWD>(gt, g, stab + threadIdx.x, nin);
         const WalkOut o = walk_gate<BWD, GL, CMP>(L, N, W, my_tab, sstg + threadIdx.x, sleak, err, g, W.rec + ga,
                                              (uint32_t)(ge - ga), (uint32_t)W.init[g], slast + threadIdx.x);
         if (BWD) {
