@@ -101,7 +101,7 @@ struct GraphKey {
   int64_t rpt, ctas, kernel, dmin, tmin, piece, plan_gen;
   int64_t n_tiles;  // launch sizes baked into the graph
   bool any_events;  // whether the walk was captured
-  bool timing;      // whether phase events were captured
+  int timing;       // the phase-timing level the graph was captured with
   std::vector<int32_t> groups;  // first window of each window group
   int64_t pat_items;            // pattern walk launch size (-1: no pattern gates)
   bool whole;                   // the walk without pieces
@@ -143,6 +143,7 @@ struct gtp_ctx {
   int64_t gcap = 0;
   int64_t plan_gen = 0;  // bumped whenever a plan buffer moves (captured graphs hold its pointers)
   DevBuf cell_acc, grad, gtiles, dC_scratch;
+  DevBuf counts;  // per-gate event counts for host outputs of gtp_gate_energy
   DevBuf d_err;
   DevBuf first_bad;  // trace check result (see launch_validate)
   DevBuf out_slew;   // glitch detection: [n_gates][2] output {fall, rise} transition times
@@ -185,8 +186,8 @@ struct gtp_ctx {
   int32_t pat_indexed = 0;
   DevBuf pat_bad;  // smallest error key of the pattern walk
   int64_t run_pat_items = -1;  // the run's pattern walk launch size (-1: none)
-  // phase timing (CUDA events on the context stream) and launch counting
-  bool timing = false;
+  // phase timing (CUDA events on the context stream) and launch counting: 0 off, 1 every phase, 2 the walk only
+  int timing = 0;
   cudaEvent_t ev[12] = {};
   int64_t t_ns[6] = {0, 0, 0, 0, 0, 0};  // gate pass, plan, walk (all walks), merge; the tiled and pattern walks
   int64_t n_timed = 0;
@@ -473,7 +474,7 @@ WalkArgs walk_args(gtp_ctx* ctx, int n) {
 // Phase boundary i (0..7); on a capturing stream the record becomes an
 // event-record node of the graph and is re-recorded at every replay.
 void mark(gtp_ctx* ctx, int i, cudaStream_t st) {
-  if (!ctx->timing) return;
+  if (!ctx->timing || (ctx->timing == 2 && i != 4 && i != 5)) return;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(st, &cs);
   cudaEventRecordWithFlags(ctx->ev[i], st, cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u);
@@ -482,6 +483,7 @@ void mark(gtp_ctx* ctx, int i, cudaStream_t st) {
 void collect_timing(gtp_ctx* ctx) {
   if (!ctx->timing) return;
   for (int k = 0; k < (ctx->run_pat_items >= 0 ? 6 : 5); ++k) {
+    if (ctx->timing == 2 && k != 2) continue;  // only the walk's pair was recorded
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, ctx->ev[2 * k], ctx->ev[2 * k + 1]) == cudaSuccess)
       ctx->t_ns[k] += (int64_t)(ms * 1e6);
@@ -610,15 +612,22 @@ __global__ void k_check_cells(const int32_t* cell, int64_t n, int32_t n_cells, D
 }
 
 // Offsets checked (from 0 to n_events, never decreasing), and the busiest
-// gate's event count into *max_count.
-__global__ void k_check_offsets(const int64_t* off, int64_t n_gates, int64_t n_events, DevError* err,
-                                unsigned long long* max_count) {
+// gate's event count into *max_count.  With device inputs the same pass
+// copies the offsets (src -> dst) and the initial states (init_src ->
+// init_dst) into the window's buffers, so a load is one launch and one
+// readback; with host inputs they were copied before (src == dst, no init).
+__global__ void k_load_offsets(const int64_t* src, int64_t* dst, const uint8_t* init_src, uint8_t* init_dst,
+                               int64_t n_gates, int64_t n_events, DevError* err, unsigned long long* max_count) {
   int64_t mx = 0;
+  const bool copy = src != dst;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_gates;
        g += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = off[g + 1] - off[g];
+    const int64_t o0 = src[g], o1 = src[g + 1];
+    const int64_t c = o1 - o0;
     if (c < 0) report_error(err, GTP_EINVAL, -1 - g);
     mx = c > mx ? c : mx;
+    if (copy) dst[g] = o0;
+    if (init_dst) init_dst[g] = init_src[g];
   }
   for (int o = 16; o > 0; o >>= 1) {
     const int64_t y = __shfl_xor_sync(0xFFFFFFFFu, mx, o);
@@ -631,13 +640,25 @@ __global__ void k_check_offsets(const int64_t* off, int64_t n_gates, int64_t n_e
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = wmax[w] > mx ? wmax[w] : mx;
     if (mx > 0) atomicMax(max_count, (unsigned long long)mx);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0 && (off[0] != 0 || off[n_gates] != n_events))
-    report_error(err, GTP_EINVAL, -1);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int64_t last = src[n_gates];
+    if (copy) dst[n_gates] = last;
+    if (src[0] != 0 || last != n_events) report_error(err, GTP_EINVAL, -1);
+  }
 }
 
-__global__ void k_counts(const int64_t* off, int64_t n, int64_t* out) {
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
-    out[g] = off[g + 1] - off[g];
+// Per-gate results of a run into device outputs in one pass (null outputs
+// are skipped): energies and final states copied, counts from the offsets.
+__global__ void k_gate_out(const double* el, const double* ei, const double* es, const uint8_t* fs,
+                           const int64_t* off, int64_t n, double* o_el, double* o_ei, double* o_es, int64_t* o_cnt,
+                           uint8_t* o_fs) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    if (o_el) o_el[g] = el[g];
+    if (o_ei) o_ei[g] = ei[g];
+    if (o_es) o_es[g] = es[g];
+    if (o_cnt) o_cnt[g] = off[g + 1] - off[g];
+    if (o_fs) o_fs[g] = fs[g];
+  }
 }
 
 // State-indexed arrays of the pattern cells with at most p_sipl_max_pins
@@ -1248,8 +1269,11 @@ int gtp_load_events(gtp_ctx* ctx, int32_t window, int64_t window_ps, int64_t n_e
   const cudaMemcpyKind k = kind_in(flags);
   CU(W.offsets.reserve(sizeof(int64_t) * (G + 1)), "alloc offsets");
   CU(W.init.reserve((size_t)G), "alloc init");
-  CU(cudaMemcpyAsync(W.offsets.p, gate_offsets, sizeof(int64_t) * (G + 1), k, ctx->stream), "copy offsets");
-  CU(cudaMemcpyAsync(W.init.p, init_state, (size_t)G, k, ctx->stream), "copy init");
+  const bool dev_in = (flags & GTP_DEVICE) != 0;  // device offsets and states are copied by the check pass
+  if (!dev_in) {
+    CU(cudaMemcpyAsync(W.offsets.p, gate_offsets, sizeof(int64_t) * (G + 1), k, ctx->stream), "copy offsets");
+    CU(cudaMemcpyAsync(W.init.p, init_state, (size_t)G, k, ctx->stream), "copy init");
+  }
   if (borrow) {
     W.borrowed = reinterpret_cast<const uint2*>(events);
   } else if (packed) {
@@ -1277,8 +1301,9 @@ int gtp_load_events(gtp_ctx* ctx, int32_t window, int64_t window_ps, int64_t n_e
   CU(cudaMemsetAsync(ctx->d_err.p, 0, kStatusBytes, ctx->stream), "zero status");
   unsigned long long* max_count =
       reinterpret_cast<unsigned long long*>(static_cast<unsigned char*>(ctx->d_err.p) + sizeof(DevError));
-  k_check_offsets<<<1024, 256, 0, ctx->stream>>>(W.offsets.as<int64_t>(), G, n_events, ctx->d_err.as<DevError>(),
-                                                 max_count);
+  k_load_offsets<<<1024, 256, 0, ctx->stream>>>(dev_in ? gate_offsets : W.offsets.as<int64_t>(), W.offsets.as<int64_t>(),
+                                                dev_in ? init_state : nullptr, dev_in ? W.init.as<uint8_t>() : nullptr,
+                                                G, n_events, ctx->d_err.as<DevError>(), max_count);
   CU(cudaGetLastError(), "check offsets");
   ctx->launches += 1;
   CU(cudaMemcpyAsync(ctx->h_err, ctx->d_err.p, sizeof(DevError) + sizeof(unsigned long long),
@@ -1611,26 +1636,31 @@ int gtp_gate_energy(gtp_ctx* ctx, int32_t window, double* e_leak, double* e_int,
   if (!W || !W->has_result) return fail(ctx, GTP_EINVAL, "gate_energy: no result for this window");
   DeviceGuard dg(ctx->device);
   const int64_t G = ctx->N.n_gates;
+  if (flags & GTP_DEVICE) {  // device outputs: one pass, stream-ordered on the context's stream
+    if (e_leak || e_int || e_sw || n_events || final_state) {
+      k_gate_out<<<1024, 256, 0, ctx->stream>>>(W->e_leak.as<double>(), W->e_int.as<double>(), W->e_sw.as<double>(),
+                                                W->final_state.as<uint8_t>(), W->offsets.as<int64_t>(), G, e_leak,
+                                                e_int, e_sw, n_events, final_state);
+      CU(cudaGetLastError(), "gate outputs");
+      ctx->launches += 1;
+    }
+    return GTP_OK;
+  }
   const cudaMemcpyKind k = kind_out(flags);
   if (e_leak) CU(cudaMemcpyAsync(e_leak, W->e_leak.p, sizeof(double) * G, k, ctx->stream), "copy e_leak");
   if (e_int) CU(cudaMemcpyAsync(e_int, W->e_int.p, sizeof(double) * G, k, ctx->stream), "copy e_int");
   if (e_sw) CU(cudaMemcpyAsync(e_sw, W->e_sw.p, sizeof(double) * G, k, ctx->stream), "copy e_sw");
   if (final_state) CU(cudaMemcpyAsync(final_state, W->final_state.p, (size_t)G, k, ctx->stream), "copy final_state");
-  if (n_events) {
-    if (flags & GTP_DEVICE) {
-      k_counts<<<1024, 256, 0, ctx->stream>>>(W->offsets.as<int64_t>(), G, n_events);
-      CU(cudaGetLastError(), "counts");
-      ctx->launches += 1;
-    } else {
-      std::vector<int64_t> off(G + 1);
-      CU(cudaMemcpyAsync(off.data(), W->offsets.p, sizeof(int64_t) * (G + 1), cudaMemcpyDeviceToHost, ctx->stream),
-         "copy offsets");
-      CU(cudaStreamSynchronize(ctx->stream), "gate_energy");
-      for (int64_t g = 0; g < G; ++g) n_events[g] = off[g + 1] - off[g];
-    }
+  if (n_events) {  // counts from the offsets on the device, then one copy into the caller's array
+    CU(ctx->counts.reserve(sizeof(int64_t) * (size_t)std::max<int64_t>(G, 1)), "alloc counts");
+    k_gate_out<<<1024, 256, 0, ctx->stream>>>(nullptr, nullptr, nullptr, nullptr, W->offsets.as<int64_t>(), G,
+                                              nullptr, nullptr, nullptr, ctx->counts.as<int64_t>(), nullptr);
+    CU(cudaGetLastError(), "counts");
+    ctx->launches += 1;
+    CU(cudaMemcpyAsync(n_events, ctx->counts.p, sizeof(int64_t) * G, k, ctx->stream), "copy counts");
   }
-  // device outputs are stream-ordered on the context's stream; host outputs are complete on return
-  if (!(flags & GTP_DEVICE)) CU(cudaStreamSynchronize(ctx->stream), "gate_energy");
+  // host outputs are complete on return
+  CU(cudaStreamSynchronize(ctx->stream), "gate_energy");
   return GTP_OK;
 }
 
@@ -1707,9 +1737,9 @@ int gtp_autotune(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_
   DeviceGuard dg(ctx->device);
   if (iters <= 0) iters = 3;
   const int64_t keep_kernel = ctx->p_kernel;
-  const bool keep_timing = ctx->timing;
+  const int keep_timing = ctx->timing;
   ctx->p_kernel = 0;
-  ctx->timing = false;
+  ctx->timing = 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CU(cudaEventCreate(&e0), "event");
   CU(cudaEventCreate(&e1), "event");
@@ -2132,11 +2162,13 @@ int gtp_set_param(gtp_ctx* ctx, const char* key, int64_t value) {
     if (value == 0 || value > (1 << 30)) return fail(ctx, GTP_ERANGE, "scheme_ncyc_fix must be 1..2^30");
     ctx->p_ncyc_fix = value < 0 ? 1 : value;
   } else if (k == "timing") {
-    // 1: time the phases of every following run with CUDA events; any value resets the totals
+    // 1: time the phases of every following run with CUDA events; 2: the walk only (two events a run, so
+    // the timing barely adds to a step); any value resets the totals
     DeviceGuard dg(ctx->device);
     if (value > 0 && !ctx->ev[0])
       for (auto& e : ctx->ev) CU(cudaEventCreate(&e), "event create");
-    ctx->timing = value > 0;
+    if (value > 2) return fail(ctx, GTP_ERANGE, "timing must be 0, 1 or 2");
+    ctx->timing = value > 0 ? (int)value : 0;
     for (auto& t : ctx->t_ns) t = 0;
     ctx->n_timed = 0;
     ctx->launches = 0;
@@ -2168,7 +2200,7 @@ int64_t gtp_get_param(const gtp_ctx* ctx, const char* key) {
   if (k == "scheme_thr_floor") return ctx->p_thr_floor;
   if (k == "scheme_ncyc_fix") return ctx->p_ncyc_fix;
   if (k == "n_sm") return ctx->n_sm;
-  if (k == "timing") return ctx->timing ? 1 : 0;
+  if (k == "timing") return ctx->timing;
   if (k == "t_gate_pass_ns") return ctx->t_ns[0];
   if (k == "t_plan_ns") return ctx->t_ns[1];
   if (k == "t_walk_ns") return ctx->t_ns[2];

@@ -318,3 +318,94 @@ def test_bin_and_gate_totals_agree(engine):
     assert e_bins == pytest.approx(e_gates, rel=1e-6)
     w2, _ = run(engine, lib, net, tr, 20)
     np.testing.assert_allclose(w.reshape(-1, 2).mean(1), w2, rtol=TOL)
+
+
+@pytest.mark.parametrize("fault", ["decreasing", "first", "last"])
+def test_device_offsets_checked_and_copied(engine, fault):
+    """Device offsets and initial states are copied by the load's check pass:
+    malformed offsets are rejected, and a later load of good device arrays
+    (the caller's copies overwritten afterwards) walks as the oracle does."""
+    import torch
+    from paper_2609_05960_gb300 import GtpError, gtpower
+    lib, net, tr = small_random(n_gates=300, n_events=30_001, window_ps=300_000, seed=53, tie_p=0.02)
+    engine.load_library(lib)
+    engine.load_netlist(net)
+    for k in ("kernel", "records_per_thread", "dense_min", "ctas_per_sm", "tile_min", "piece_len", "group_bin_bytes"):
+        engine.set_param(k, -1)
+    dev = engine.device
+    bad = tr.offsets.copy()
+    if fault == "decreasing":
+        bad[150] = bad[152] + 1
+    elif fault == "first":
+        bad[0] = 1
+    else:
+        bad[-1] -= 1
+    rec = torch.from_numpy(tr.records.view(np.int32)).to(dev)
+    with pytest.raises(GtpError) as ei:
+        engine.load_events(2, window_ps=tr.window_ps, offsets=torch.from_numpy(bad).to(dev), records=rec,
+                           init_state=torch.from_numpy(tr.init_state).to(dev), borrow=True)
+    assert ei.value.code == gtpower.GTP_EINVAL
+    off = torch.from_numpy(tr.offsets).to(dev)
+    init = torch.from_numpy(tr.init_state).to(dev)
+    engine.load_events(2, window_ps=tr.window_ps, offsets=off, records=rec, init_state=init, borrow=True)
+    off.fill_(0)   # the window keeps its own copies of offsets and states
+    init.fill_(0)
+    w = engine.run_power(2, 100).cpu().numpy()
+    ge = {k: v.cpu().numpy() for k, v in engine.gate_energy(2, device=True).items()}
+    assert_matches(w, ge, oracle.walk(lib, net, tr, 100), 100)
+
+
+def test_gate_energy_device_outputs_any_subset(engine):
+    """Per-gate device outputs come from one pass that skips null outputs."""
+    import torch
+    from paper_2609_05960_gb300 import gtpower
+    lib, net, tr = small_random(n_gates=500, n_events=40_000, window_ps=400_000, seed=54)
+    engine.load_library(lib)
+    engine.load_netlist(net)
+    engine.load_events(0, tr)
+    engine.run_power(0, 100)
+    full = {k: v.cpu().numpy() for k, v in engine.gate_energy(0, device=True).items()}
+    G = net.n_gates
+    kw = dict(device=engine.device)
+    sentinel = {"e_leak": torch.full((G,), -7.0, dtype=torch.float64, **kw),
+                "e_int": torch.full((G,), -7.0, dtype=torch.float64, **kw),
+                "e_sw": torch.full((G,), -7.0, dtype=torch.float64, **kw),
+                "n_events": torch.full((G,), -7, dtype=torch.int64, **kw),
+                "final_state": torch.full((G,), 77, dtype=torch.uint8, **kw)}
+    names = list(sentinel)
+    for keep in ([0], [3], [1, 4], [0, 2, 3], []):
+        outs = {k: (sentinel[k].clone() if i in keep else None) for i, k in enumerate(names)}
+        gtpower.gtp_gate_energy(engine.ctx, 0, outs["e_leak"], outs["e_int"], outs["e_sw"], outs["n_events"],
+                                outs["final_state"])
+        torch.cuda.synchronize()
+        for i, k in enumerate(names):
+            if i in keep:
+                np.testing.assert_array_equal(outs[k].cpu().numpy(), full[k])
+    np.testing.assert_array_equal(full["n_events"], np.diff(tr.offsets))
+
+
+def test_timing_levels(engine):
+    """Timing level 2 records only the walk's pair of events; 1 every phase."""
+    from paper_2609_05960_gb300 import GtpError, gtpower
+    lib, net, tr = small_random(n_gates=200, n_events=50_000, window_ps=500_000, seed=55)
+    engine.load_library(lib)
+    engine.load_netlist(net)
+    engine.load_events(0, tr)
+    for graph in (False, True):
+        for level in (2, 1):
+            engine.set_param("timing", level)
+            assert engine.get_param("timing") == level
+            engine.run_power(0, 100, graph=graph)
+            w = engine.run_power(0, 100, graph=graph)
+            assert engine.get_param("n_timed") == 2
+            assert engine.get_param("t_walk_ns") > 0
+            if level == 2:
+                assert engine.get_param("t_plan_ns") == 0 and engine.get_param("t_merge_ns") == 0
+            else:
+                assert engine.get_param("t_merge_ns") > 0
+            ref = oracle.waveform_w(oracle.walk(lib, net, tr, 100)["bins"], 100)
+            assert (np.abs(w.cpu().numpy() - ref) / ref).max() <= TOL
+    engine.set_param("timing", 0)
+    with pytest.raises(GtpError) as ei:
+        engine.set_param("timing", 3)
+    assert ei.value.code == gtpower.GTP_ERANGE
