@@ -66,7 +66,7 @@ def parse():
                    help="scale the configuration to this many events (same gates and distribution; "
                         "for profiling a smaller case)")
     p.add_argument("--sweep", default="", choices=["", "contention", "streamed", "schemes", "adjoint", "glitch", "tiled",
-                                                    "patterns"],
+                                                    "patterns", "prep"],
                    help="contention: uniform high activity (1, 2, 4, 8 events per gate per 1k bins); "
                         "streamed: the large window streamed from pinned host memory in 1-32 chunks, "
                         "against a plain copy of its records; schemes: the paper's GPU schemes (naive, "
@@ -74,8 +74,9 @@ def parse():
                         "engine's walk; adjoint: the adjoint workload's forward and backward alone (--events "
                         "scales it); glitch: the large workload's plain walk, then with glitch detection (--events "
                         "scales it); tiled: the large workload with the time-sliced walk at tile_min 0, 32768, "
-                        "8192, 2048; patterns: the pattern-gate pin-threshold study alone; instead of the "
-                        "default run, one JSON line per case")
+                        "8192, 2048; patterns: the pattern-gate pin-threshold study alone; prep: the pass "
+                        "that rebuilds event descriptors and gate tables after a load change, on the large "
+                        "netlist; instead of the default run, one JSON line per case")
     return p.parse_args()
 
 
@@ -491,7 +492,7 @@ def run_ours(args, cfg_name):
         if opool is not None:
             from oracle import fullsize
             wl_large = fullsize.Workload.of(cfg, seed_ev=seed_ev)
-        extras["load_change"] = measure_load_change(eng, dev, cfg, wave, n_ev, ms_max / args.steps, xs, net.load_ff)
+        extras["load_change"] = measure_load_change(eng, dev, cfg, wave, n_ev, ms_max / args.steps, xs, lib, net)
         extras["glitch"] = measure_glitch(eng, dev, cfg, wave, walk_s * 1e3, n_ev, xs, opool, wl_large)
         extras["components"] = measure_components(eng, dev, cfg, walk_s * 1e3, n_ev, xs, opool, wl_large)
         if not args.no_patterns:
@@ -599,7 +600,7 @@ def _oracle_errors(opool, wl, bin_ps, wave, ge, keys=("e_leak", "e_int", "e_sw")
     return {**fullsize.bin_errors(w, ref["bins"], bin_ps), **fullsize.gate_errors(ge, ref, keys)}
 
 
-def measure_load_change(eng, dev, cfg, wave, n_ev, step_ms, steps, load_ff):
+def measure_load_change(eng, dev, cfg, wave, n_ev, step_ms, steps, lib, net):
     """The step of an optimisation loop over the large window (slot 0): a new
     load per gate (gtp_set_load, which rebuilds the interpolation
     coordinates and the per-gate energy tables) and then the run."""
@@ -607,7 +608,7 @@ def measure_load_change(eng, dev, cfg, wave, n_ev, step_ms, steps, load_ff):
 
     from paper_2609_05960_gb300 import gtpower
 
-    base = torch.from_numpy(np.ascontiguousarray(load_ff, dtype=np.float32)).to(dev)
+    base = torch.from_numpy(np.ascontiguousarray(net.load_ff, dtype=np.float32)).to(dev)
     k = [0]
 
     def step():
@@ -619,11 +620,39 @@ def measure_load_change(eng, dev, cfg, wave, n_ev, step_ms, steps, load_ff):
         step()
     torch.cuda.synchronize(dev)
     ms = _events_per_s(step, steps, dev)
+    # the preparation pass alone (CUDA events around its launch, timing level 1, a separate pass)
+    eng.set_param("timing", 1)
+    for _ in range(10):
+        step()
+    torch.cuda.synchronize(dev)
+    prep_ms = eng.get_param("t_prep_ns") * 1e-6 / max(eng.get_param("n_timed"), 1)
+    eng.set_param("timing", 0)
     gtpower.gtp_set_load(eng.ctx, base)
+    alg = gate_prep_bytes(lib, net)
     return {"ms_per_step": ms, "value": n_ev / (ms * 1e-3), "unit": UNIT,
             "over_plain_step": ms / step_ms if step_ms > 0 else None,
-            "what": "gtp_set_load (new load per gate: interpolation coordinates and per-gate energy tables rebuilt) "
-                    "+ gtp_run_power, as in an optimisation loop"}
+            "what": "gtp_set_load (new load per gate) + gtp_run_power, whose first launch rebuilds the event "
+                    "descriptors and per-gate energy tables (k_gate_prep), as in an optimisation loop",
+            "gate_prep": {"ms": prep_ms, "algorithmic_bytes": alg,
+                          "roofline": roofline(alg, prep_ms, peak_gbs()) if prep_ms > 0 else None,
+                          "bytes": "per gate: cell 4 + load 4 + slews 8 x stride read; descriptors 16 x "
+                                   "2 (stride + 1) and the cell's (n_in + 1) 2^n_in table entries x 4 written"}}
+
+
+def gate_prep_bytes(lib, net):
+    """Algorithmic bytes of one preparation pass over the netlist."""
+    stride = net.slew_stride
+    n_in = np.asarray(lib.n_in)[np.asarray(net.cell)]
+    entries = np.where(n_in <= 3, (n_in + 1) << n_in, 0)
+    G = len(n_in)
+    return int(G * (8 + 8 * stride + 16 * 2 * (stride + 1)) + 4 * int(entries.sum()))
+
+
+def peak_gbs():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return json.load(open(path)).get("hbm_gbs") or 6800.0
+    return 6800.0
 
 
 def measure_batched(eng, dev, steps, peak, plain_value, opool=None):
@@ -1284,8 +1313,51 @@ def run_patterns_sweep(args):
     eng.close()
 
 
+def run_prep_sweep(args):
+    """The descriptor and gate-table pass alone: the large netlist (1M gates)
+    with a small window (--events, default 100k), its loads changed before
+    every run; one JSON line with the pass's time and roofline."""
+    import torch
+
+    import synth
+    from paper_2609_05960_gb300 import Engine, gtpower
+
+    dev = torch.device("cuda", 0)
+    cfg = config_of(args, "large")
+    n_ev = int(args.events) if args.events else 100_000
+    lib = synth.make_library(cfg.seed_lib)
+    net = synth.make_netlist(lib, cfg.n_gates, cfg.seed_net)
+    counts = synth.zipf_counts(cfg.n_gates, n_ev, cfg.zipf_s, cfg.cap, cfg.seed_ev)
+    tr, rec = synth.make_trace_gpu(net, counts, cfg.window_ps, cfg.seed_ev, cfg.tie_p, device=dev)
+    eng = Engine(0)
+    eng.load_library(lib)
+    eng.load_netlist(net)
+    eng.load_events(0, window_ps=cfg.window_ps, offsets=torch.from_numpy(tr.offsets).to(dev), records=rec,
+                    init_state=torch.from_numpy(tr.init_state).to(dev), borrow=True)
+    wave = torch.empty(cfg.window_ps // cfg.bin_ps, dtype=torch.float64, device=dev)
+    base = torch.from_numpy(np.ascontiguousarray(net.load_ff, dtype=np.float32)).to(dev)
+    loads = [base, base * 1.001]
+    steps = max(3, min(args.steps, 50))
+    for i in range(args.warmup + steps):
+        if i == args.warmup:
+            torch.cuda.synchronize(dev)
+            eng.set_param("timing", 1)
+        gtpower.gtp_set_load(eng.ctx, loads[i & 1])
+        gtpower.gtp_run_power(eng.ctx, 0, cfg.bin_ps, wave)
+    torch.cuda.synchronize(dev)
+    prep_ms = eng.get_param("t_prep_ns") * 1e-6 / max(eng.get_param("n_timed"), 1)
+    eng.set_param("timing", 0)
+    alg = gate_prep_bytes(lib, net)
+    print(json.dumps({"sweep": "prep", "gates": cfg.n_gates, "events": n_ev, "steps": steps, "prep_ms": prep_ms,
+                      "algorithmic_bytes": alg, "roofline": roofline(alg, prep_ms, peak_gbs())}), flush=True)
+    eng.close()
+
+
 def main():
     args = parse()
+    if args.sweep == "prep":
+        run_prep_sweep(args)
+        return
     if args.sweep == "tiled":
         run_tiled_sweep(args)
         return

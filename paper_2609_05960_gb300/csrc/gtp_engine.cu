@@ -133,6 +133,7 @@ struct gtp_ctx {
   // per-gate energy tables (forward: scaled; adjoint: unscaled + load derivative), rebuilt when stale
   DevBuf gtab, gtab_bwd;
   bool gtab_ok = false, gtab_bwd_ok = false;
+  bool desc_ok = false;  // the event descriptors match the netlist and loads
   std::map<int, Window> windows;
   // launch plan: device descriptor table and its pinned host staging copy
   DevBuf plan;  // WinDesc[kMaxWindows] | tile_base[kMaxWindows+1] | l0[kMaxWindows+1]
@@ -188,8 +189,10 @@ struct gtp_ctx {
   int64_t run_pat_items = -1;  // the run's pattern walk launch size (-1: none)
   // phase timing (CUDA events on the context stream) and launch counting: 0 off, 1 every phase, 2 the walk only
   int timing = 0;
-  cudaEvent_t ev[12] = {};
-  int64_t t_ns[6] = {0, 0, 0, 0, 0, 0};  // gate pass, plan, walk (all walks), merge; the tiled and pattern walks
+  cudaEvent_t ev[14] = {};
+  // gate pass, plan, walk (all walks), merge; the tiled and pattern walks; the descriptor and gate-table pass
+  int64_t t_ns[7] = {0, 0, 0, 0, 0, 0, 0};
+  bool prep_marked = false;  // the run rebuilt descriptors and gate tables under timing level 1
   int64_t n_timed = 0;
   int64_t launches = 0;
 };
@@ -474,7 +477,7 @@ WalkArgs walk_args(gtp_ctx* ctx, int n) {
 // Phase boundary i (0..7); on a capturing stream the record becomes an
 // event-record node of the graph and is re-recorded at every replay.
 void mark(gtp_ctx* ctx, int i, cudaStream_t st) {
-  if (!ctx->timing || (ctx->timing == 2 && i != 4 && i != 5)) return;
+  if (!ctx->timing || (ctx->timing == 2 && i != 4 && i != 5)) return;  // marks 12, 13: the preparation pass
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(st, &cs);
   cudaEventRecordWithFlags(ctx->ev[i], st, cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u);
@@ -487,6 +490,11 @@ void collect_timing(gtp_ctx* ctx) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, ctx->ev[2 * k], ctx->ev[2 * k + 1]) == cudaSuccess)
       ctx->t_ns[k] += (int64_t)(ms * 1e6);
+  }
+  if (ctx->prep_marked) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->ev[12], ctx->ev[13]) == cudaSuccess) ctx->t_ns[6] += (int64_t)(ms * 1e6);
+    ctx->prep_marked = false;
   }
   ctx->n_timed += 1;
 }
@@ -569,35 +577,38 @@ int enqueue_forward(gtp_ctx* ctx, int n, int64_t n_seg_total, int64_t n_tiles_to
   return GTP_OK;
 }
 
+// The event descriptors of a new netlist or load are built with the gate
+// tables, at the next run (ensure_gate_tables).
 int ensure_netlist_coords(gtp_ctx* ctx) {
   const int64_t G = ctx->N.n_gates;
   ctx->N.dstride = 2 * (ctx->N.stride + 1);
   CU(ctx->desc.reserve(sizeof(uint4) * ctx->N.dstride * G), "alloc event descriptors");
   ctx->N.desc = ctx->desc.as<uint4>();
-  CU(launch_event_desc(ctx->L, ctx->N, ctx->desc.as<uint4>(), ctx->stream), "event descriptors");
-  ctx->launches += 1;
+  ctx->desc_ok = false;
   ctx->gtab_ok = false;
   ctx->gtab_bwd_ok = false;
   return GTP_OK;
 }
 
-// Per-gate energy tables for the walk (forward: scaled energies; adjoint:
-// unscaled energies and load derivatives), rebuilt after a netlist, load,
-// scale or library change.
+// Event descriptors and per-gate energy tables for the walk (forward: scaled
+// energies; adjoint: unscaled energies and load derivatives), rebuilt in one
+// pass after a netlist, load, scale or library change.  Every run calls this
+// before its first launch that reads them.
 int ensure_gate_tables(gtp_ctx* ctx, bool backward) {
   const int64_t G = ctx->N.n_gates;
-  if (!ctx->gtab_ok) {
-    CU(ctx->gtab.reserve(sizeof(float) * kGateTab * (size_t)G), "alloc gate tables");
-    CU(launch_gate_tables(ctx->L, ctx->N, ctx->gtab.as<float>(), nullptr, ctx->stream), "gate tables");
-    ctx->launches += 1;
-    ctx->gtab_ok = true;
-  }
-  if (backward && !ctx->gtab_bwd_ok) {
-    CU(ctx->gtab_bwd.reserve(sizeof(float) * 2 * kGateTab * (size_t)G), "alloc adjoint gate tables");
-    CU(launch_gate_tables(ctx->L, ctx->N, nullptr, ctx->gtab_bwd.as<float>(), ctx->stream), "adjoint gate tables");
-    ctx->launches += 1;
-    ctx->gtab_bwd_ok = true;
-  }
+  const bool need_d = !ctx->desc_ok, need_f = !ctx->gtab_ok, need_b = backward && !ctx->gtab_bwd_ok;
+  if (!need_d && !need_f && !need_b) return GTP_OK;
+  if (need_f) CU(ctx->gtab.reserve(sizeof(float) * kGateTab * (size_t)G), "alloc gate tables");
+  if (need_b) CU(ctx->gtab_bwd.reserve(sizeof(float) * 2 * kGateTab * (size_t)G), "alloc adjoint gate tables");
+  mark(ctx, 12, ctx->stream);
+  CU(launch_gate_prep(ctx->L, ctx->N, need_d ? ctx->desc.as<uint4>() : nullptr, need_f ? ctx->gtab.as<float>() : nullptr,
+                      need_b ? ctx->gtab_bwd.as<float>() : nullptr, ctx->stream), "gate tables");
+  mark(ctx, 13, ctx->stream);
+  ctx->prep_marked = ctx->timing == 1;
+  ctx->launches += 1;
+  ctx->desc_ok = true;
+  ctx->gtab_ok |= need_f;
+  ctx->gtab_bwd_ok |= need_b;
   return GTP_OK;
 }
 
@@ -1065,6 +1076,7 @@ int gtp_load_library(gtp_ctx* ctx, int32_t n_cells, const int32_t* n_in, float v
   ctx->lib_loaded = true;
   ctx->pat_ok = false;
   for (auto& kv : ctx->windows) kv.second.ps_ok = false;
+  ctx->desc_ok = false;
   ctx->gtab_ok = false;
   ctx->gtab_bwd_ok = false;
   ctx->net_loaded = false;
@@ -2170,6 +2182,7 @@ int gtp_set_param(gtp_ctx* ctx, const char* key, int64_t value) {
     if (value > 2) return fail(ctx, GTP_ERANGE, "timing must be 0, 1 or 2");
     ctx->timing = value > 0 ? (int)value : 0;
     for (auto& t : ctx->t_ns) t = 0;
+    ctx->prep_marked = false;
     ctx->n_timed = 0;
     ctx->launches = 0;
   } else {
@@ -2196,6 +2209,7 @@ int64_t gtp_get_param(const gtp_ctx* ctx, const char* key) {
   if (k == "run_groups") return (int64_t)ctx->run_groups.size();
   if (k == "t_tiled_ns") return ctx->t_ns[4];
   if (k == "t_pattern_ns") return ctx->t_ns[5];
+  if (k == "t_prep_ns") return ctx->t_ns[6];
   if (k == "scheme_evt_tgt") return ctx->p_evt_tgt;
   if (k == "scheme_thr_floor") return ctx->p_thr_floor;
   if (k == "scheme_ncyc_fix") return ctx->p_ncyc_fix;

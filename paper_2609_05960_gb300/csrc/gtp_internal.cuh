@@ -53,7 +53,7 @@ struct LibView {
 };
 
 // Event descriptor of one (gate, pin, edge), 16 bytes, built once per
-// netlist / load update (k_event_desc):
+// netlist / load update, before the next run (k_gate_prep):
 //   input pin:  x = slew fraction, y = load fraction, w = 1 / load-segment width
 //   output pin: w = 0.5 * C * Vdd^2 (the switching energy)
 //   z = table element offset without the side bits (bits 0-15; for the
@@ -297,7 +297,6 @@ __device__ __forceinline__ SmemLib stage_library(const LibView& L, unsigned char
 }
 
 // ------------------------------------------------------------------ launchers (host)
-cudaError_t launch_event_desc(const LibView& L, NetView N, uint4* desc, cudaStream_t st);
 cudaError_t launch_gate_pass_bwd(const LibView& L, const NetView& N, const WinDesc* wins, double* cell_acc,
                                  cudaStream_t st);
 cudaError_t launch_walk_per_gate(const LibView& L, const NetView& N, const WinDesc* wins, int n_win,

@@ -37,123 +37,140 @@ __device__ __forceinline__ int window_of(const int64_t* base, int n_win, int64_t
 
 }  // namespace
 
-// ------------------------------------------------------------------ event descriptors
+// ------------------------------------------------------------------ lookup points and per-gate energy tables
 // The NLDM lookup point of every (gate, input pin, edge) is static: its slew
 // segment and fraction and the gate's load segment and fraction are located
-// once per netlist (or load update), together with the table element and the
-// switching energy, instead of once per event.
-__global__ void k_event_desc(LibView L, NetView N, uint4* __restrict__ desc) {
-  __shared__ float ax[4 * kMaxAxis];
-  if (threadIdx.x < kMaxAxis) {
-    ax[threadIdx.x] = L.slew_axis[threadIdx.x];
-    ax[kMaxAxis + threadIdx.x] = L.load_axis[threadIdx.x];
-    ax[2 * kMaxAxis + threadIdx.x] = L.slew_rw[threadIdx.x];
-    ax[3 * kMaxAxis + threadIdx.x] = L.load_rw[threadIdx.x];
-  }
-  __syncthreads();
-  // one thread a descriptor (gate g, pin p, edge e), so consecutive threads write consecutive 16-byte entries
-  const int64_t n = N.n_gates * N.dstride;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t g = k / N.dstride;
-    const int pe = (int)(k - g * N.dstride), p = pe >> 1, e = pe & 1;
-    const int32_t c = N.cell[g];
-    const CellInfo ci = L.cells[c];
-    const int n_in = ci.n_in;
-    const float C = N.load[g];
-    const int j = segment_of(ax + kMaxAxis, L.nl, C);
-    const float fl = (C - ax[kMaxAxis + j]) * ax[3 * kMaxAxis + j];
-    const uint32_t hi_bits = ((uint32_t)c << 16) | ((uint32_t)j << 25);
-    uint4 d;
-    if (p < n_in) {
-      const float sl = N.slew[((size_t)g * N.stride + p) * 2 + e];
-      const int i = segment_of(ax, L.ns, sl);
-      const uint32_t tab = (uint32_t)(ci.tab_base + ((p * 2 + e) << (n_in - 1))) * (uint32_t)L.tsize +
-                           (uint32_t)(i * L.nl + j);
-      d = make_uint4(__float_as_uint((sl - ax[i]) * ax[2 * kMaxAxis + i]), __float_as_uint(fl), tab | hi_bits,
-                     __float_as_uint(ax[3 * kMaxAxis + j]));
-    } else {  // output pin (and any pin past it): switching energy
-      d = make_uint4(0u, 0u, ((uint32_t)ci.tab_base * (uint32_t)L.tsize) | hi_bits | (1u << 24),
-                     __float_as_uint(L.half_v2 * C));
-    }
-    desc[k] = d;
-  }
-}
-
-// ------------------------------------------------------------------ per-gate energy tables
-// For each gate whose cell has at most kGateTabMaxIn inputs, the energy of
-// every (input pin, edge, side state) lookup at the gate's slews and load,
-// i.e. the bilinear NLDM value of Sec. 2.2.1 on the state-indexed table of
-// Sec. 4.1, and the switching energy of its output (Eq. 1).  Entry
+// once per netlist, load or scale change (with the table element and the
+// switching energy) into the gate's event descriptors, instead of once per
+// event.  Descriptor (pin p, edge e) of gate g is desc[g * dstride + 2p + e];
+// pins from the cell's output on hold the switching energy 0.5 * C * Vdd^2
+// (Eq. 1).
+//
+// For each gate whose cell has at most kGateTabMaxIn inputs, the same pass
+// evaluates every (input pin, edge, side state) lookup at the gate's slews
+// and load, i.e. the bilinear NLDM value of Sec. 2.2.1 on the state-indexed
+// table of Sec. 4.1, and the switching energy of its output.  Entry
 // (pin << n_in) | s, with s the input-pin state before the event: the pin's
 // own bit in s is its old value (so the edge is its complement) and the other
 // bits are the side state; the output pin is pin n_in.  Forward table:
 // energies times escale, output slots 0.5 * C * Vdd^2.  Adjoint table:
 // unscaled energies (output slots 0), then their load derivatives (the slope
-// of the located load segment; output slots 0.5 * Vdd^2).  One warp builds
-// one gate's table, lane e its entry e, so each row is written as one
-// coalesced 128-byte line (slots past the cell's entries are left unwritten:
-// nothing reads them).
-__global__ void __launch_bounds__(256, 4) k_gate_tables(LibView L, NetView N, float* __restrict__ gtab,
-                                                     float* __restrict__ gbwd) {
-  constexpr int kG = 4;  // gates a warp takes at once: their loads are independent and overlap
-  const uint32_t e = threadIdx.x & 31u;
+// of the located load segment; output slots 0.5 * Vdd^2).
+//
+// A warp takes four consecutive gates at a time.  First its lanes compute
+// the four gates' descriptors, one (gate, pin, edge) a lane (the descriptors
+// of consecutive gates are consecutive, so the writes coalesce), from the
+// gates' cells, loads and slews (loaded together; cell data in shared memory)
+// into a shared-memory copy; then, gate by gate, lane k of the table reads
+// its entry's descriptor there and interpolates.  Every gate costs one round
+// of independent loads.  Null outputs are not written.
+__device__ __forceinline__ int segment_bsearch(const float* axis, int n, float x) {
+  // the last knot i in [0, n - 2] with axis[i] <= x (0 below the axis): the loop of segment_of, branch-free
+  int i = 0;
+#pragma unroll
+  for (int step = 8; step > 0; step >>= 1)
+    if (i + step <= n - 2 && x >= axis[i + step]) i += step;
+  return i;
+}
+
+__global__ void __launch_bounds__(256, 4) k_gate_prep(LibView L, NetView N, uint4* __restrict__ desc,
+                                                   float* __restrict__ gtab, float* __restrict__ gbwd) {
+  constexpr int kG = 4;
+  constexpr int kMaxDesc = 2 * (GTP_MAX_PINS + 1);
+  __shared__ float ax[4 * kMaxAxis];
+  __shared__ CellInfo cells[256];  // cell indices are bytes in the library's tables
+  __shared__ float esc[256];
+  __shared__ uint4 sdesc[8][kG * kMaxDesc];  // per warp: its four gates' descriptors
+  __shared__ int32_t scell[8][kG];
+  for (int i = threadIdx.x; i < kMaxAxis; i += blockDim.x) {
+    ax[i] = L.slew_axis[i];
+    ax[kMaxAxis + i] = L.load_axis[i];
+    ax[2 * kMaxAxis + i] = L.slew_rw[i];
+    ax[3 * kMaxAxis + i] = L.load_rw[i];
+  }
+  for (int i = threadIdx.x; i < L.n_cells && i < 256; i += blockDim.x) {
+    cells[i] = L.cells[i];
+    esc[i] = L.escale[i];
+  }
+  __syncthreads();
+  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+  uint4* const sd = sdesc[wib];
+  const int ds = N.dstride;
+  const int n_items = kG * ds;
   const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t g0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kG; g0 < N.n_gates;
        g0 += n_warps * kG) {
-    int32_t c[kG];
-    uint32_t nin[kG];
-    uint4 d[kG];
-#pragma unroll
-    for (int k = 0; k < kG; ++k) c[k] = g0 + k < N.n_gates ? __ldg(N.cell + g0 + k) : 0;
-#pragma unroll
-    for (int k = 0; k < kG; ++k) nin[k] = (uint32_t)L.cells[c[k]].n_in;
-#pragma unroll
-    for (int k = 0; k < kG; ++k) {
-      const uint32_t n_in = nin[k];
-      const uint32_t pin = min(e >> n_in, n_in), s = e & ((1u << n_in) - 1u);
-      const uint32_t val = pin < n_in ? (((s >> pin) & 1u) ^ 1u) : 0u;  // own bit: the value before the edge
-      d[k] = g0 + k < N.n_gates ? __ldg(N.desc + (size_t)(g0 + k) * N.dstride + pin * 2u + val) : make_uint4(0, 0, 0, 0);
+    // descriptors of gates g0 .. g0 + 3: item i is gate i / ds, (pin, edge) i % ds
+    for (int i = (int)lane; i < n_items; i += 32) {
+      const int k = (i >= ds) + (i >= 2 * ds) + (i >= 3 * ds);
+      const int idx = i - k * ds, p = idx >> 1, e = idx & 1;
+      const int64_t g = g0 + k;
+      if (g >= N.n_gates) continue;
+      const int32_t c = __ldg(N.cell + g);
+      const float C = __ldg(N.load + g);
+      const float sl = p < N.stride ? __ldg(N.slew + (size_t)g * N.stride * 2 + idx) : 0.f;
+      if (idx == 0) scell[wib][k] = c;
+      const CellInfo ci = cells[c];
+      const int n_in = ci.n_in;
+      const int j = segment_bsearch(ax + kMaxAxis, L.nl, C);
+      const float fl = (C - ax[kMaxAxis + j]) * ax[3 * kMaxAxis + j];
+      const uint32_t hi_bits = ((uint32_t)c << 16) | ((uint32_t)j << 25);
+      uint4 d;
+      if (p < n_in) {
+        const int si = segment_bsearch(ax, L.ns, sl);
+        const uint32_t tab = (uint32_t)(ci.tab_base + ((p * 2 + e) << (n_in - 1))) * (uint32_t)L.tsize +
+                             (uint32_t)(si * L.nl + j);
+        d = make_uint4(__float_as_uint((sl - ax[si]) * ax[2 * kMaxAxis + si]), __float_as_uint(fl), tab | hi_bits,
+                       __float_as_uint(ax[3 * kMaxAxis + j]));
+      } else {  // output pin (and any pin past it): switching energy
+        d = make_uint4(0u, 0u, ((uint32_t)ci.tab_base * (uint32_t)L.tsize) | hi_bits | (1u << 24),
+                       __float_as_uint(L.half_v2 * C));
+      }
+      sd[i] = d;
+      if (desc) desc[(size_t)g0 * ds + i] = d;
     }
+    if (!gtab && !gbwd) continue;
+    __syncwarp();
 #pragma unroll
     for (int k = 0; k < kG; ++k) {
       const int64_t g = g0 + k;
-      const uint32_t n_in = nin[k];
-      if (g >= N.n_gates || n_in > (uint32_t)kGateTabMaxIn || e >= ((n_in + 1u) << n_in)) continue;
-      const uint32_t pin = e >> n_in, s = e & ((1u << n_in) - 1u);
+      if (g >= N.n_gates) break;
+      const int32_t c = scell[wib][k];
+      const uint32_t n_in = (uint32_t)cells[c].n_in;
+      if (n_in > (uint32_t)kGateTabMaxIn || lane >= ((n_in + 1u) << n_in)) continue;
+      const uint32_t pin = lane >> n_in, s = lane & ((1u << n_in) - 1u);
+      const uint32_t val = pin < n_in ? (((s >> pin) & 1u) ^ 1u) : 0u;  // own bit: the value before the edge
+      const uint4 q = sd[k * ds + (int)(pin * 2u + val)];                 // pin <= n_in <= stride
       float eu, ed, ef;
       if (pin < n_in) {
-        const float* p = L.tab + (d[k].z & 0xFFFFu) + side_bits(s, pin, n_in) * (uint32_t)L.tsize;
-        const float a0 = __ldg(p), a1 = __ldg(p + 1), b0 = __ldg(p + L.nl), b1 = __ldg(p + L.nl + 1);
-        const float fl = __uint_as_float(d[k].y), fs = __uint_as_float(d[k].x);
+        const float* tp = L.tab + (q.z & 0xFFFFu) + side_bits(s, pin, n_in) * (uint32_t)L.tsize;
+        const float a0 = __ldg(tp), a1 = __ldg(tp + 1), b0 = __ldg(tp + L.nl), b1 = __ldg(tp + L.nl + 1);
+        const float fl = __uint_as_float(q.y), fs = __uint_as_float(q.x);
         const float lo = fmaf(fl, a1 - a0, a0), hi = fmaf(fl, b1 - b0, b0);
         eu = fmaf(fs, hi - lo, lo);
-        ed = fmaf(fs, (b1 - b0) - (a1 - a0), a1 - a0) * __uint_as_float(d[k].w);
-        ef = eu * L.escale[c[k]];
+        ed = fmaf(fs, (b1 - b0) - (a1 - a0), a1 - a0) * __uint_as_float(q.w);
+        ef = eu * esc[c];
       } else {
         eu = 0.f;
         ed = L.half_v2;
-        ef = __uint_as_float(d[k].w);  // the output pin's descriptor: 0.5 * C * Vdd^2
+        ef = __uint_as_float(q.w);  // the output pin's descriptor: 0.5 * C * Vdd^2
       }
-      if (gtab) gtab[(size_t)g * kGateTab + e] = ef;
+      if (gtab) gtab[(size_t)g * kGateTab + lane] = ef;
       if (gbwd) {
-        gbwd[(size_t)g * 2 * kGateTab + e] = eu;
-        gbwd[(size_t)g * 2 * kGateTab + kGateTab + e] = ed;
+        gbwd[(size_t)g * 2 * kGateTab + lane] = eu;
+        gbwd[(size_t)g * 2 * kGateTab + kGateTab + lane] = ed;
       }
     }
+    __syncwarp();  // the next gates' descriptors overwrite this copy
   }
 }
 
-cudaError_t launch_gate_tables(const LibView& L, const NetView& N, float* gtab, float* gtab_bwd, cudaStream_t st) {
+cudaError_t launch_gate_prep(const LibView& L, const NetView& N, uint4* desc, float* gtab, float* gtab_bwd,
+                             cudaStream_t st) {
+  if (L.n_cells > 256 || N.dstride > 2 * (GTP_MAX_PINS + 1)) return cudaErrorInvalidValue;
   int64_t blocks = (N.n_gates + 31) / 32;  // 8 warps of 4 gates a block
   if (blocks > 16384) blocks = 16384;
-  k_gate_tables<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, st>>>(L, N, gtab, gtab_bwd);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_event_desc(const LibView& L, NetView N, uint4* desc, cudaStream_t st) {
-  int64_t blocks = (N.n_gates * N.dstride + 255) / 256;
-  if (blocks > 8192) blocks = 8192;
-  k_event_desc<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, st>>>(L, N, desc);
+  k_gate_prep<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, st>>>(L, N, desc, gtab, gtab_bwd);
   return cudaGetLastError();
 }
 

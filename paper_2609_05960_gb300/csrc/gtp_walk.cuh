@@ -7,7 +7,7 @@ namespace gtp {
 
 constexpr int kWalkThreads = 256;  // threads of a walk CTA
 
-// Per-gate energy tables (built by launch_gate_tables): for a gate whose cell
+// Per-gate energy tables (built by launch_gate_prep): for a gate whose cell
 // has at most kGateTabMaxIn inputs, entry (pin << n_in) | s holds the
 // energy of an event on `pin` when the input-pin state before it is s (the
 // pin's own bit being its old value): the internal energy (fJ, bilinear NLDM
@@ -109,6 +109,9 @@ cudaError_t launch_walk_components(const LibView& L, const NetView& N, const Wal
 cudaError_t launch_walk_plain_whole(const LibView& L, const NetView& N, const WalkArgs& A, cudaStream_t st);
 cudaError_t launch_walk_glitch_whole(const LibView& L, const NetView& N, const WalkArgs& A, cudaStream_t st);
 cudaError_t launch_walk_adjoint_whole(const LibView& L, const NetView& N, const WalkArgs& A, cudaStream_t st);
-cudaError_t launch_gate_tables(const LibView& L, const NetView& N, float* gtab, float* gtab_bwd, cudaStream_t st);
+// The gates' event descriptors and energy tables in one pass (null outputs
+// are skipped).
+cudaError_t launch_gate_prep(const LibView& L, const NetView& N, uint4* desc, float* gtab, float* gtab_bwd,
+                             cudaStream_t st);
 
 }  // namespace gtp

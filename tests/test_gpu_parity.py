@@ -409,3 +409,36 @@ def test_timing_levels(engine):
     with pytest.raises(GtpError) as ei:
         engine.set_param("timing", 3)
     assert ei.value.code == gtpower.GTP_ERANGE
+
+
+@pytest.mark.parametrize("params", KERNELS, ids=KID)
+def test_load_and_scale_changes_rebuild_lookups(engine, params):
+    """gtp_set_load and gtp_set_scales between runs: the next run rebuilds the
+    event descriptors and gate tables (one pass) and walks as the oracle does
+    with the new loads and scales, in the forward walk and the adjoint."""
+    import torch
+    lib, net, tr = small_random(n_gates=400, n_events=60_000, window_ps=600_000, seed=56, tie_p=0.02)
+    w, ge = run(engine, lib, net, tr, 100, params)
+    assert_matches(w, ge, oracle.walk(lib, net, tr, 100), 100)
+    rng = np.random.default_rng(5)
+    load2 = (net.load_ff * rng.uniform(0.2, 6.0, net.n_gates)).astype(np.float32)  # off the axes too
+    engine.set_load(torch.from_numpy(load2).to(engine.device))
+    w = engine.run_power(0, 100).cpu().numpy()
+    assert_matches(w, engine.gate_energy(0, device=False), oracle.walk(lib, net, tr, 100, load_ff=load2), 100)
+    es = rng.uniform(0.5, 2.0, lib.n_cells).astype(np.float32)
+    ls = rng.uniform(0.5, 2.0, lib.n_cells).astype(np.float32)
+    engine.set_scales(es, ls)
+    load3 = (net.load_ff * rng.uniform(0.5, 2.0, net.n_gates)).astype(np.float32)
+    engine.set_load(load3)  # host array
+    w = engine.run_power(0, 100).cpu().numpy()
+    ref = oracle.walk(lib, net, tr, 100, escale=es, lscale=ls, load_ff=load3)
+    assert_matches(w, engine.gate_energy(0, device=False), ref, 100)
+    if params.get("kernel", 0) == 0 and not params.get("tile_min"):
+        g = (rng.normal(size=tr.window_ps // 100) * 1e3).astype(np.float32)
+        dC, de, dl = engine.run_power_backward(0, 100, torch.from_numpy(g).to(engine.device))
+        rC, rde, rdl = oracle.adjoint(lib, net, tr, 100, g.astype(np.float64), escale=es.astype(np.float64),
+                                      lscale=ls.astype(np.float64), load_ff=load3)
+        for got, ref in ((dC, rC), (de, rde), (dl, rdl)):
+            got = got.cpu().numpy()
+            assert np.all(np.abs(got - ref) <= 1e-4 * np.abs(ref) + 1e-5 * np.abs(ref).max())
+    engine.set_scales(None, None)
