@@ -182,8 +182,10 @@ int gtp_sipl_expand(int32_t n_in, int32_t n_slew, int32_t n_load, int32_t n_int_
  * Sec. 2.4.1 and Eq. 2 when gtp_set_glitch is on, with the transition times
  * given here), and add into the same waveform (and, in
  * gtp_run_power_components, into the component waveforms);
- * gtp_design_power includes them.  gtp_run_power_backward and
- * gtp_run_power_scheme return GTP_EINVAL for a window with pattern gates.
+ * gtp_design_power includes them.  gtp_run_power_backward walks them too
+ * (their dL/dC through gtp_pattern_gate_gradient; pattern cells have no
+ * energy or leakage scales).  gtp_run_power_scheme returns GTP_EINVAL for a
+ * window with pattern gates.
  * ------------------------------------------------------------------------ */
 #define GTP_MAX_PATTERN_PINS 32
 #define GTP_MAX_INDEXED_PINS 24
@@ -258,6 +260,17 @@ int gtp_load_pattern_events(gtp_ctx* ctx, int32_t window, int64_t n_events, cons
  */
 int gtp_pattern_gate_energy(gtp_ctx* ctx, int32_t window, double* e_leak, double* e_int, double* e_sw, double* e_gl,
                             int64_t* n_events, uint32_t* final_state, int flags);
+
+/*
+ * dL/dC of the pattern gates from the window's last gtp_run_power_backward
+ * [the chain rule through Sec. 2.2's bilinear lookup in load and Eq. 1, a
+ * glitch event's derivative carrying its ratio of Eq. 2; leakage does not
+ * depend on the load]: dC[n_pattern_gates] float32, in the units of dL_dP
+ * per fF, host memory or device memory with GTP_DEVICE.
+ * Errors: GTP_EINVAL when the window has no pattern-gate gradient (no
+ * backward run since its pattern events were loaded) or dC is NULL.
+ */
+int gtp_pattern_gate_gradient(gtp_ctx* ctx, int32_t window, float* dC, int flags);
 
 /*
  * Per-cell multipliers on internal energy and on leakage power (host arrays
@@ -498,7 +511,9 @@ int gtp_run_power_batched(gtp_ctx* ctx, int32_t n_windows, const int32_t* window
  * load segment of the bilinear table (right derivative on a knot);
  * d(0.5*C*Vdd^2)/dC = 0.5*Vdd^2; leakage energy is linear in lscale and
  * internal energy in escale.  Uses the context's current scales and loads.
- * Synchronous; reports malformed traces like gtp_run_power.
+ * A window with pattern gates also gets their dL/dC, read with
+ * gtp_pattern_gate_gradient.  Synchronous; reports malformed traces (of
+ * either kind of gate) like gtp_run_power.
  */
 int gtp_run_power_backward(gtp_ctx* ctx, int32_t window, int32_t bin_ps, const float* dL_dP, float* dC,
                            float* d_escale, float* d_lscale);

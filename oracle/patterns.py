@@ -31,15 +31,20 @@ pin count (times are checked per group, at the group's first record), -2 for
 a time below the previous group's, -4 for a value equal to the pin's current
 value.
 
-Parity status: pinned against the C oracle walk on cells of up to 7 inputs
-(sipl.dense_cell turns the patterns into the C oracle's state-indexed
-library), and on a 20-pin cell by closed forms (tests/test_oracle_patterns.py).
+``adjoint`` is the chain rule through the same walk: dL/dC per pattern gate
+for a loss of the power waveform.
+
+Parity status: the walk is pinned against the C oracle walk on cells of up
+to 7 inputs (sipl.dense_cell turns the patterns into the C oracle's
+state-indexed library), and on a 20-pin cell by closed forms; the adjoint
+against the C oracle's adjoint on the same small cells and by central
+differences of the walk on the wide cells (tests/test_oracle_patterns.py).
 """
 from __future__ import annotations
 
 import numpy as np
 
-from . import OracleError, bilinear
+from . import OracleError, bilinear, bilinear_dload
 from . import sipl
 
 
@@ -177,3 +182,76 @@ def walk(plib, pnet, ptrace, bin_ps: int, glitch_clock_ps: int = 0, gates=None, 
     if comp is not None:
         out["comp_bins"] = comp
     return out
+
+
+def adjoint(plib, pnet, ptrace, bin_ps: int, dLdP, glitch_clock_ps: int = 0, gates=None) -> np.ndarray:
+    """dL/dC (fF^-1 units of L) of the selected pattern gates (default all),
+    for a loss L of the power waveform P_b = E_b * 1e-3 / bin_ps (W) given
+    dL/dP_b per bin.  Walks the gates as walk() does (same groups, states,
+    checks and glitch detection); only the dynamic energies depend on a
+    gate's load C:
+      * an input-pin event: the slope in load of its bilinear interpolation
+        on the located load segment [Sec. 2.2];
+      * an output-pin event: 0.5 * Vdd^2 [Eq. 1];
+      * a glitch event's derivative carries its ratio, which depends on
+        times and transition times only [Sec. 2.4.1, Eq. 2];
+    each times dL/dP of the event's bin and dP_b/dE_b = 1e-3 / bin_ps."""
+    T = int(ptrace.window_ps)
+    if bin_ps <= 0 or T % bin_ps:
+        raise ValueError("window_ps must be a multiple of bin_ps")
+    g_bin = np.asarray(dLdP, np.float64) * (1e-3 / bin_ps)
+    sel = np.arange(pnet.n_gates) if gates is None else np.asarray(gates, np.int64)
+    dC = np.zeros(len(sel), np.float64)
+    half_v2 = 0.5 * float(plib.vdd) * float(plib.vdd)
+    clk = int(glitch_clock_ps)
+    cells = {}
+    for i, g in enumerate(sel):
+        g = int(g)
+        c = int(pnet.cell[g])
+        if c not in cells:
+            cells[c] = plib.cell(c)
+        n_in, ip, dflt, _, _ = cells[c]
+        n_pins = n_in + 1
+        in_mask = (1 << n_in) - 1
+        C = float(pnet.load_ff[g])
+        S = int(ptrace.init_state[g])
+        a, b = int(ptrace.offsets[g]), int(ptrace.offsets[g + 1])
+        t_prev = 0
+        last = [-1] * n_pins
+        acc = 0.0
+        r = a
+        while r < b:
+            t = int(ptrace.t_ps[r])
+            j = r
+            while j < b and int(ptrace.t_ps[j]) == t:
+                j += 1
+            if t < 0 or t >= T:
+                raise OracleError(-3, r)
+            if t < t_prev:
+                raise OracleError(-2, r)
+            S_next = S
+            for e in range(r, j):
+                pin, v = int(ptrace.pin[e]), int(ptrace.value[e])
+                if pin >= n_pins:
+                    raise OracleError(-3, e)
+                if (S_next >> pin) & 1 == v:
+                    raise OracleError(-4, e)
+                S_next ^= 1 << pin
+                if pin < n_in:
+                    tab = sipl.internal_item(pin, v, S & in_mask, ip, dflt)
+                    sl = pnet.slew_ps[g, pin]
+                    dE = bilinear_dload(plib.slew_axis, plib.load_axis, tab, float(sl[v]), C)
+                    sum_slew = float(sl[0]) + float(sl[1])
+                else:
+                    dE = half_v2
+                    sum_slew = float(pnet.out_slew_ps[g, 0]) + float(pnet.out_slew_ps[g, 1])
+                if clk > 0 and last[pin] >= 0 and last[pin] // clk == t // clk and sum_slew > 0:
+                    x = 2.0 * (t - last[pin]) / sum_slew
+                    dE *= min(1.0, x * x)
+                last[pin] = t
+                acc += g_bin[t // bin_ps] * dE
+            S = S_next
+            t_prev = t
+            r = j
+        dC[i] = acc
+    return dC

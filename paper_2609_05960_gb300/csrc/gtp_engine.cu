@@ -72,13 +72,15 @@ struct Window {
   int64_t pat_n_events = 0, pat_n_items = 0;
   std::vector<int64_t> pat_h_off;
   DevBuf pat_off, pat_rec, pat_init, pat_items, pat_first, pat_mask, pat_e_leak, pat_e_int, pat_e_sw, pat_e_gl,
-      pat_final;
+      pat_final, pat_dC;
+  bool pat_grad = false;  // pat_dC holds the pattern gates' dL/dC of the last backward run
   void release_patterns() {
     for (DevBuf* b : {&pat_off, &pat_rec, &pat_init, &pat_items, &pat_first, &pat_mask, &pat_e_leak, &pat_e_int,
-                      &pat_e_sw, &pat_e_gl, &pat_final})
+                      &pat_e_sw, &pat_e_gl, &pat_final, &pat_dC})
       b->release();
     pat_h_off.clear();
     pat_loaded = false;
+    pat_grad = false;
     pat_n_events = pat_n_items = 0;
   }
   const uint2* rec() const { return borrowed ? borrowed : records.as<uint2>(); }
@@ -345,13 +347,14 @@ int build_plan(gtp_ctx* ctx, const std::vector<Window*>& ws, int32_t bin_ps, con
     d.final_state = W.final_state.as<uint8_t>();
     d.bins = W.bins.as<float2>();
     d.tbins = nullptr;
-    const bool pat = W.pat_loaded && ctx->pat_net_ok && !backward;
+    const bool pat = W.pat_loaded && ctx->pat_net_ok;
     if (tiled) {
       CU(W.tbins.reserve(sizeof(double2) * nb), "alloc FP64 bins");
       d.tbins = W.tbins.as<double2>();
     }
     d.p_n_items = 0;
     d.p_off = nullptr;
+    d.p_dC = nullptr;
     if (pat) {
       d.p_off = W.pat_off.as<int64_t>();
       d.p_rec = W.pat_rec.as<uint2>();
@@ -365,6 +368,11 @@ int build_plan(gtp_ctx* ctx, const std::vector<Window*>& ws, int32_t bin_ps, con
       d.p_e_gl = W.pat_e_gl.as<double>();
       d.p_final = W.pat_final.as<uint32_t>();
       d.p_n_items = W.pat_n_items;
+      d.p_dC = nullptr;
+      if (backward) {
+        CU(W.pat_dC.reserve(sizeof(float) * (size_t)std::max<int64_t>(ctx->Q.n_gates, 1)), "alloc pattern gradients");
+        d.p_dC = W.pat_dC.as<float>();
+      }
     }
     d.cbins = nullptr;
     d.cwave = nullptr;
@@ -1681,11 +1689,9 @@ int gtp_run_power_backward(gtp_ctx* ctx, int32_t window, int32_t bin_ps, const f
   if (!ctx) return GTP_EINVAL;
   Window* W = get_window(ctx, window);
   if (!W || W->streamed) return fail(ctx, GTP_EINVAL, "run_power_backward: window not loaded");
-  if (W->pat_loaded && ctx->pat_net_ok)
-    return fail(ctx, GTP_EINVAL,
-                "run_power_backward: windows with pattern gates are walked by gtp_run_power, gtp_run_power_batched "
-                "and gtp_run_power_components only");
-  ctx->run_pat_items = -1;
+  // the window's pattern gates are walked too: their dL/dC is read with gtp_pattern_gate_gradient
+  ctx->run_pat_items = (W->pat_loaded && ctx->pat_net_ok) ? W->pat_n_items : -1;
+  W->pat_grad = false;
   if (!dL_dP) return fail(ctx, GTP_EINVAL, "run_power_backward: dL_dP is required");
   if (bin_ps <= 0 || W->window_ps % bin_ps != 0)
     return fail(ctx, GTP_ERANGE, "window_ps must be a multiple of bin_ps > 0");
@@ -1693,6 +1699,10 @@ int gtp_run_power_backward(gtp_ctx* ctx, int32_t window, int32_t bin_ps, const f
   const int64_t nb = W->window_ps / bin_ps;
   const int nt = merge_tiles((int)nb);
   const int64_t G = ctx->N.n_gates;
+  if (ctx->run_pat_items >= 0) {
+    RC(ensure_pattern_index(ctx));
+    CU(ctx->pat_bad.reserve(sizeof(unsigned long long)), "alloc pattern status");
+  }
   CU(ctx->grad.reserve(sizeof(float2) * nb), "alloc grad");
   CU(ctx->gtiles.reserve(sizeof(double) * nt), "alloc grad tiles");
   float* dc = dC;
@@ -1730,6 +1740,14 @@ int gtp_run_power_backward(gtp_ctx* ctx, int32_t window, int32_t bin_ps, const f
     CU(launch_walk(ctx->L, ctx->N, A, true, st), "adjoint walk");
     ctx->launches += 4;
   }
+  if (ctx->run_pat_items >= 0) {  // the pattern gates' dL/dC (timed as walk)
+    CU(cudaMemsetAsync(ctx->pat_bad.p, 0xFF, sizeof(unsigned long long), st), "reset pattern status");
+    mark(ctx, 10, st);
+    CU(launch_pattern_walk(ctx->P, ctx->Q, plan_wins(ctx->plan.p), 1, ctx->run_pat_items, ctx->N.clock_ps,
+                           ctx->pat_bad.as<unsigned long long>(), st, true), "pattern adjoint walk");
+    mark(ctx, 11, st);
+    ctx->launches += ctx->run_pat_items > 0 ? 3 : 1;
+  }
   mark(ctx, 5, st);
   mark(ctx, 6, st);
   if (d_escale || d_lscale) {
@@ -1737,7 +1755,9 @@ int gtp_run_power_backward(gtp_ctx* ctx, int32_t window, int32_t bin_ps, const f
     ctx->launches += 1;
   }
   mark(ctx, 7, st);
-  const int rc = check_walk_error(ctx, W->n_events > 0 ? 1 : 0, &window, "run_power_backward");
+  int rc = check_walk_error(ctx, W->n_events > 0 ? 1 : 0, &window, "run_power_backward");
+  if (rc == GTP_OK && ctx->run_pat_items >= 0) rc = check_pattern_error(ctx, 1, &window, "run_power_backward");
+  W->pat_grad = rc == GTP_OK && ctx->run_pat_items >= 0;
   collect_timing(ctx);
   return rc;
 }
@@ -2133,6 +2153,18 @@ int gtp_pattern_gate_energy(gtp_ctx* ctx, int32_t window, double* e_leak, double
        "copy counts");
   }
   CU(cudaStreamSynchronize(ctx->stream), "pattern_gate_energy");
+  return GTP_OK;
+}
+
+int gtp_pattern_gate_gradient(gtp_ctx* ctx, int32_t window, float* dC, int flags) {
+  if (!ctx) return GTP_EINVAL;
+  Window* W = get_window(ctx, window);
+  if (!W || !W->pat_grad || !W->pat_loaded || !ctx->pat_net_ok || !dC)
+    return fail(ctx, GTP_EINVAL, "pattern_gate_gradient: no pattern gate gradient for this window");
+  DeviceGuard dg(ctx->device);
+  CU(cudaMemcpyAsync(dC, W->pat_dC.p, sizeof(float) * (size_t)ctx->Q.n_gates, kind_out(flags), ctx->stream),
+     "copy pattern gradients");
+  CU(cudaStreamSynchronize(ctx->stream), "pattern_gate_gradient");
   return GTP_OK;
 }
 

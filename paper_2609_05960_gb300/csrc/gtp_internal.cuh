@@ -170,6 +170,7 @@ struct WinDesc {
   double* p_e_sw;
   double* p_e_gl;
   uint32_t* p_final;         // [Gp]
+  float* p_dC;               // adjoint: [Gp] dL/dC of the pattern gates
   int64_t p_n_items;
 };
 
@@ -337,10 +338,12 @@ cudaError_t launch_pattern_pack(const int32_t* t, const uint8_t* pin, const uint
 cudaError_t launch_pattern_index(const PatLib& P, int32_t c, int32_t n_in, int32_t* iidx, float* lidx,
                                  cudaStream_t st);
 // The pattern gates of the windows: initial leakage, items' pin masks, and
-// the walk into each window's tbins; errors as the smallest key
+// the walk into each window's bins (backward: dL/dC of each pattern gate
+// into p_dC from the windows' gradient tables); errors as the smallest key
 // ((window << 40 | record) << 3) | -code in *bad (see launch_validate).
 cudaError_t launch_pattern_walk(const PatLib& P, const PatNet& Q, const WinDesc* wins, int n_win,
-                                int64_t max_items, int32_t clock_ps, unsigned long long* bad, cudaStream_t st);
+                                int64_t max_items, int32_t clock_ps, unsigned long long* bad, cudaStream_t st,
+                                bool backward = false);
 // The reduction-rate probe: n_red reductions of `width` (2 or 4) floats into
 // hashed places of slots[n_slots] (16 B a slot).
 cudaError_t launch_red_probe(float4* slots, uint32_t n_slots, int width, int64_t n_red, int n_sm, cudaStream_t st);

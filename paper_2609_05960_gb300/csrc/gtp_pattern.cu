@@ -140,10 +140,19 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // Per window and pattern gate: outputs initialised (the initial state's
 // leakage over the whole window; the walk adds each change of it), and the
-// initial leakage powers added into the window's L0.
+// initial leakage powers added into the window's L0.  In the adjoint only
+// dL/dC is initialised (leakage does not depend on the load).
+template <bool BWD>
 __global__ void __launch_bounds__(256) k_pat_prepare(PatLib P, PatNet Q, const WinDesc* __restrict__ wins) {
   __shared__ double red[8];
   const WinDesc& W = wins[blockIdx.y];
+  if (BWD) {
+    if (W.p_off)
+      for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < Q.n_gates;
+           g += (int64_t)gridDim.x * blockDim.x)
+        W.p_dC[g] = 0.f;
+    return;
+  }
   double p0 = 0.0;
   if (W.p_n_items > 0 || W.p_off) {
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < Q.n_gates;
@@ -192,7 +201,12 @@ __global__ void __launch_bounds__(kPatWarps * 32) k_pat_masks(const WinDesc* __r
 }
 
 // ------------------------------------------------------------------ the walk
-template <bool GL>
+// The adjoint (BWD) walks the same records with the same states, checks and
+// glitch detection, and sums dL/dC = sum over events of g_b(event) * dE/dC:
+// the slope in load of the event's bilinear interpolation (Sec. 2.2) or
+// 0.5 * Vdd^2 for the output pin (Eq. 1), times a glitch event's ratio
+// (Eq. 2); leakage does not depend on the load.
+template <bool GL, bool BWD>
 __global__ void __launch_bounds__(kPatWarps * 32) k_pat_walk(PatLib P, PatNet Q, const WinDesc* __restrict__ wins,
                                                              int32_t clk, unsigned long long* bad) {
   __shared__ float ax[2][kMaxAxis];
@@ -218,7 +232,8 @@ __global__ void __launch_bounds__(kPatWarps * 32) k_pat_walk(PatLib P, PatNet Q,
   const float C = Q.load[g];
   int j = 0;
   while (j < P.nl - 2 && C >= ax[1][j + 1]) ++j;
-  const float fl = (C - ax[1][j]) / (ax[1][j + 1] - ax[1][j]);
+  const float lrw = 1.f / (ax[1][j + 1] - ax[1][j]);
+  const float fl = (C - ax[1][j]) * lrw;
   const float esw = P.half_v2 * C;
   const float* slew = Q.slew + (int64_t)g * Q.stride * 2;
   // entry state: the initial state XOR the pin bits of the gate's earlier items (kept to the cell's pins:
@@ -249,6 +264,7 @@ __global__ void __launch_bounds__(kPatWarps * 32) k_pat_walk(PatLib P, PatNet Q,
     }
   }
   float ei = 0.f, es = 0.f, eg = 0.f, el = 0.f;  // FP32 within the item (at most 16 terms a lane)
+  float dc = 0.f;                                // adjoint: this lane's share of dL/dC
   // records are read 32 at a time, the next 32 loaded while these are walked; every lane reads its record
   // while it lies inside the gate, so the time after the item's last record comes from the lane after it
   constexpr uint2 kNone = {0xFFFFFFFFu, 0u};
@@ -299,11 +315,12 @@ __global__ void __launch_bounds__(kPatWarps * 32) k_pat_walk(PatLib P, PatNet Q,
         const float fs = __uint_as_float(dd.y);
         const float* tp4 = P.tab + (int64_t)tb * P.tsize + dd.x;
         const float t00 = __ldg(tp4), t01 = __ldg(tp4 + 1), t10 = __ldg(tp4 + P.nl), t11 = __ldg(tp4 + P.nl + 1);
-        E = (1.f - fs) * ((1.f - fl) * t00 + fl * t01) + fs * ((1.f - fl) * t10 + fl * t11);
+        if (BWD) E = ((1.f - fs) * (t01 - t00) + fs * (t11 - t10)) * lrw;  // dE/dC on the located load segment
+        else E = (1.f - fs) * ((1.f - fl) * t00 + fl * t01) + fs * ((1.f - fl) * t10 + fl * t11);
         kind = 1;
         if (GL) sum_slew = slew[pin * 2] + slew[pin * 2 + 1];
       } else {
-        E = esw;
+        E = BWD ? P.half_v2 : esw;
         kind = 2;
         if (GL) sum_slew = Q.oslew[2 * g] + Q.oslew[2 * g + 1];
       }
@@ -321,6 +338,14 @@ __global__ void __launch_bounds__(kPatWarps * 32) k_pat_walk(PatLib P, PatNet Q,
       __syncwarp();
       if (pv && (lane == 31 || (peers >> (lane + 1)) == 0u)) last_t[warp][pin] = (int32_t)t;
       __syncwarp();
+    }
+    if (BWD) {
+      if (kind != 0) dc += __ldcg(&W.grad[bin_of(t, W.bin_magic, W.bin_shift, bin_ps)].x) * E;
+      const uint32_t Sg_n = tail ? Xi : Spre;
+      Sg = __shfl_sync(kFull, Sg_n, last_lane);
+      t_last = __shfl_sync(kFull, t, last_lane);
+      S = __shfl_sync(kFull, Xi, 31);
+      continue;
     }
     if (kind == 1) ei += E;
     else if (kind == 2) es += E;
@@ -376,6 +401,11 @@ __global__ void __launch_bounds__(kPatWarps * 32) k_pat_walk(PatLib P, PatNet Q,
     t_last = __shfl_sync(kFull, t, last_lane);
     S = __shfl_sync(kFull, Xi, 31);
   }
+  if (BWD) {
+    const double d = warp_sum((double)dc);
+    if (lane == 0 && d != 0.0) atomicAdd(W.p_dC + g, (float)d);
+    return;
+  }
   const double di = warp_sum((double)ei), ds = warp_sum((double)es), dg = warp_sum((double)eg),
                dl = warp_sum((double)el) * 1e-6;
   if (lane == 0) {
@@ -418,18 +448,25 @@ cudaError_t launch_pattern_index(const PatLib& P, int32_t c, int32_t n_in, int32
 }
 
 cudaError_t launch_pattern_walk(const PatLib& P, const PatNet& Q, const WinDesc* wins, int n_win, int64_t max_items,
-                                int32_t clock_ps, unsigned long long* bad, cudaStream_t st) {
+                                int32_t clock_ps, unsigned long long* bad, cudaStream_t st, bool backward) {
   if (n_win <= 0) return cudaSuccess;
   int64_t pb = (Q.n_gates + 255) / 256;
   pb = pb < 1 ? 1 : (pb > 256 ? 256 : pb);
-  k_pat_prepare<<<dim3((unsigned)pb, (unsigned)n_win), 256, 0, st>>>(P, Q, wins);
+  if (backward) k_pat_prepare<true><<<dim3((unsigned)pb, (unsigned)n_win), 256, 0, st>>>(P, Q, wins);
+  else k_pat_prepare<false><<<dim3((unsigned)pb, (unsigned)n_win), 256, 0, st>>>(P, Q, wins);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || max_items <= 0) return e;
   const dim3 grid((unsigned)((max_items + kPatWarps - 1) / kPatWarps), (unsigned)n_win);
   k_pat_masks<<<grid, kPatWarps * 32, 0, st>>>(wins);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (clock_ps > 0) k_pat_walk<true><<<grid, kPatWarps * 32, 0, st>>>(P, Q, wins, clock_ps, bad);
-  else k_pat_walk<false><<<grid, kPatWarps * 32, 0, st>>>(P, Q, wins, clock_ps, bad);
+  const dim3 blk(kPatWarps * 32);
+  if (backward) {
+    if (clock_ps > 0) k_pat_walk<true, true><<<grid, blk, 0, st>>>(P, Q, wins, clock_ps, bad);
+    else k_pat_walk<false, true><<<grid, blk, 0, st>>>(P, Q, wins, clock_ps, bad);
+  } else {
+    if (clock_ps > 0) k_pat_walk<true, false><<<grid, blk, 0, st>>>(P, Q, wins, clock_ps, bad);
+    else k_pat_walk<false, false><<<grid, blk, 0, st>>>(P, Q, wins, clock_ps, bad);
+  }
   return cudaGetLastError();
 }
 

@@ -35,7 +35,7 @@ ABI_SYMBOLS = ["gtp_create", "gtp_destroy", "gtp_set_stream", "gtp_last_error", 
                "gtp_run_power_streamed", "gtp_design_power", "gtp_run_power_components",
                "gtp_run_power_scheme", "gtp_sipl_expand",
                "gtp_pack_events", "gtp_measure_reductions", "gtp_load_pattern_cells", "gtp_load_pattern_netlist",
-               "gtp_load_pattern_events", "gtp_pattern_gate_energy", "gtp_measure_replay"]
+               "gtp_load_pattern_events", "gtp_pattern_gate_energy", "gtp_pattern_gate_gradient", "gtp_measure_replay"]
 
 
 class GtpError(RuntimeError):
@@ -87,6 +87,7 @@ def load(path: str = LIB_PATH):
         "gtp_load_pattern_netlist": ([P, I64, P, P, P, I32, P], ctypes.c_int),
         "gtp_load_pattern_events": ([P, I32, I64, P, P, P, P, P, ctypes.c_int], ctypes.c_int),
         "gtp_pattern_gate_energy": ([P, I32, P, P, P, P, P, P, ctypes.c_int], ctypes.c_int),
+        "gtp_pattern_gate_gradient": ([P, I32, P, ctypes.c_int], ctypes.c_int),
         "gtp_run_power_noalloc": ([P, I32, P, F, I32, P, I32, P, P, I64, P, I64, I64, P, P, P, I32, I64, I64, P, P, P,
                                    I32, P, P, P, P, P], ctypes.c_int),
     }
@@ -376,6 +377,11 @@ def gtp_pattern_gate_energy(ctx, window: int, e_leak=None, e_int=None, e_sw=None
     _check(ctx, load().gtp_pattern_gate_energy(ctx, int(window), *[a[0] for a in args], f))
 
 
+def gtp_pattern_gate_gradient(ctx, window: int, dC) -> None:
+    p, f, k = _ptr_flags(dC, np.float32)
+    _check(ctx, load().gtp_pattern_gate_gradient(ctx, int(window), p, f))
+
+
 SCHEMES = {"naive": 0, "sipl": 1, "density": 2, "fused": 3}
 
 
@@ -616,6 +622,18 @@ class Engine:
             out["final_state"] = np.empty(n, np.uint32)
         gtp_pattern_gate_energy(self.ctx, window, out["e_leak"], out["e_int"], out["e_sw"], out["e_gl"],
                                 out["n_events"], out["final_state"])
+        return out
+
+    def pattern_gate_gradient(self, window: int, device: bool = False):
+        """dL/dC of the pattern gates from the window's last backward run
+        (numpy float32, or a CUDA tensor with device=True)."""
+        n = self.n_pattern_gates
+        if device:
+            import torch
+            out = torch.empty(n, dtype=torch.float32, device=self.device)
+        else:
+            out = np.empty(n, np.float32)
+        gtp_pattern_gate_gradient(self.ctx, window, out)
         return out
 
     def load_events(self, window: int, trace=None, *, window_ps=None, offsets=None, records=None, init_state=None,

@@ -11,8 +11,9 @@ Cases: the 20-pin SRAM-like macro and the 21-pin multiplexer with busy
 clock pins, gates of many items (512 records each) with ties across item
 boundaries, every threshold from 0 (all traversal) to 24 (every cell
 indexed), glitch detection, batched windows, graph replay, malformed records
-in a later item, component waveforms, and the calls that refuse windows with
-pattern gates.
+in a later item, component waveforms, the adjoint (dL/dC of the pattern
+gates against the oracle's chain rule, with the ordinary gates' gradients
+unchanged), and the calls that refuse windows with pattern gates.
 Bar as everywhere: states and counts bit-exact, bins and per-gate energies
 within 1e-5 relative."""
 import numpy as np
@@ -238,13 +239,12 @@ def test_component_waveforms_with_pattern_gates(engine, clock):
 
 
 def test_calls_without_pattern_support_refuse(engine):
-    import torch
     from paper_2609_05960_gb300 import GtpError
     lib, net, tr, plib, pnet, ptr = _design(seed=7, n_pat=5, pat_events=500, window_ps=20_000)
     _load(engine, lib, net, tr, plib, pnet, ptr)
     engine.run_power(0, 10)
     with pytest.raises(GtpError) as e2:
-        engine.run_power_backward(0, 10, torch.ones(2000, dtype=torch.float32, device=engine.device))
+        engine.pattern_gate_gradient(0)  # no backward run yet
     with pytest.raises(GtpError) as e3:
         engine.run_power_scheme(0, 10, "fused")
     assert e2.value.code == e3.value.code == -1
@@ -255,3 +255,69 @@ def test_calls_without_pattern_support_refuse(engine):
     assert (np.abs(w - want) / want).max() <= TOL
     with pytest.raises(GtpError):
         engine.pattern_gate_energy(0)
+
+
+def _grad_close(got, want, rtol=1e-4):
+    got = np.asarray(got, np.float64)
+    want = np.asarray(want, np.float64)
+    bad = np.abs(got - want) > rtol * np.abs(want) + 1e-5 * np.abs(want).max()
+    assert not bad.any(), f"{bad.sum()} off; first {np.argmax(bad)}: got {got[np.argmax(bad)]} want {want[np.argmax(bad)]}"
+
+
+@pytest.mark.parametrize("clock", [0, 700])
+def test_adjoint_with_pattern_gates(engine, clock):
+    """gtp_run_power_backward on a window with pattern gates: the ordinary
+    gates' dL/dC and scale gradients equal the C oracle's adjoint, the pattern
+    gates' dL/dC (gtp_pattern_gate_gradient) the pattern oracle's, with many
+    items per gate, ties across item boundaries, glitch detection and every
+    threshold's lookups."""
+    import torch
+    plib = spat.make_pattern_library(2)
+    lib, net, tr = small_random(n_gates=300, n_events=20_000, window_ps=100_000, seed=31, tie_p=0.02)
+    pnet = spat.make_pattern_netlist(plib, 30, seed=32)
+    counts = synth.zipf_counts(30, 60_000, 1.1, None, 33)
+    ptr = spat.make_pattern_trace(pnet, counts, 100_000, 33, tie_p=0.3, clock_pin_share=0.4)
+    bin_ps = 25
+    g = (np.random.default_rng(7).normal(size=100_000 // bin_ps) * 1e3).astype(np.float32)
+    out_slew = np.random.default_rng(4).uniform(10, 200, (net.n_gates, 2)).astype(np.float32)
+    glitch = (clock, out_slew) if clock else None
+    rC, rde, rdl = oracle.adjoint(lib, net, tr, bin_ps, g.astype(np.float64), glitch=glitch)
+    pC = opat.adjoint(plib, pnet, ptr, bin_ps, g.astype(np.float64), glitch_clock_ps=clock)
+    assert np.count_nonzero(pC) > 20
+    _load(engine, lib, net, tr, plib, pnet, ptr)
+    if clock:
+        engine.set_glitch(clock, out_slew)
+    gd = torch.from_numpy(g).to(engine.device)
+    for thr in (0, 16, 24):
+        engine.set_param("sipl_max_pins", thr)
+        engine.run_power(0, bin_ps)
+        dC, de, dl = engine.run_power_backward(0, bin_ps, gd)
+        _grad_close(dC.cpu().numpy(), rC)
+        _grad_close(de.cpu().numpy(), rde)
+        _grad_close(dl.cpu().numpy(), rdl)
+        _grad_close(engine.pattern_gate_gradient(0), pC)
+        _grad_close(engine.pattern_gate_gradient(0, device=True).cpu().numpy(), pC)
+    engine.set_glitch(0)
+
+
+def test_adjoint_reports_malformed_pattern_record(engine):
+    """A malformed pattern record makes the backward run fail with the
+    forward run's code and record, and leaves no pattern gradient."""
+    import torch
+    from paper_2609_05960_gb300 import GtpError
+    lib, net, tr, plib, pnet, ptr = _design(seed=9, n_pat=6, pat_events=4000, window_ps=50_000)
+    g = int(np.argmax(np.diff(ptr.offsets)))
+    pos = int(ptr.offsets[g]) + 700
+    t = ptr.t_ps.copy()
+    t[pos] = t[pos - 1] - 1  # out of order
+    bad = spat.PatternTrace(ptr.window_ps, ptr.offsets, t, ptr.pin, ptr.value, ptr.init_state)
+    with pytest.raises(oracle.OracleError) as eo:
+        opat.adjoint(plib, pnet, bad, 10, np.ones(50_000 // 10))
+    assert (eo.value.code, eo.value.record) == (-2, pos)
+    _load(engine, lib, net, tr, plib, pnet, bad)
+    gd = torch.ones(50_000 // 10, dtype=torch.float32, device=engine.device)
+    with pytest.raises(GtpError) as ei:
+        engine.run_power_backward(0, 10, gd)
+    assert ei.value.code == -2 and f"at pattern record {pos}" in str(ei.value)
+    with pytest.raises(GtpError):
+        engine.pattern_gate_gradient(0)

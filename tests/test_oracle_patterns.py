@@ -203,3 +203,53 @@ def test_components_equal_the_c_oracle_and_add_up(clock):
     _close(r["comp_bins"].sum(axis=0), r["bins"])
     for row, k in enumerate(("e_leak", "e_int", "e_sw", "e_gl")):
         _close(r["comp_bins"][row].sum(), r[k].sum())
+
+
+@pytest.mark.parametrize("clock", [0, 97])
+def test_adjoint_equals_c_oracle_on_small_cells(clock):
+    """dL/dC of the pattern oracle equals the C oracle's adjoint on the
+    state-indexed library built from the same patterns (unit scales)."""
+    import dataclasses
+    plib, pnet, ptr, small = _small_case(6, n_events=8000, window=10000)
+    lib, net, tr = _dense_equivalent(plib, pnet, ptr, small)
+    bin_ps = 20
+    dLdP = np.random.default_rng(3).normal(size=tr.window_ps // bin_ps) * 1e3
+    glitch = (clock, pnet.out_slew_ps) if clock else None
+    want, _, _ = oracle.adjoint(lib, net, tr, bin_ps, dLdP, glitch=glitch)
+    got = opat.adjoint(plib, pnet, ptr, bin_ps, dLdP, glitch_clock_ps=clock)
+    assert np.abs(want).max() > 0
+    _close(got, want, 1e-11)
+    sel = np.array([3, 0, 17])
+    _close(opat.adjoint(plib, pnet, ptr, bin_ps, dLdP, glitch_clock_ps=clock, gates=sel), want[sel], 1e-11)
+
+
+@pytest.mark.parametrize("clock", [0, 150])
+def test_adjoint_central_differences_on_wide_cells(clock):
+    """On 20- and 21-pin cells (pattern traversal), dL/dC equals central
+    differences of the walk's waveform: with the loads at mid-segment the
+    energies are affine in the load, so the difference is exact up to
+    rounding."""
+    import dataclasses
+    plib = spat.make_pattern_library(2)
+    wide = [c for c in range(plib.n_cells) if plib.n_in[c] >= 19]
+    w = [1.0 if c in wide else 0.0 for c in range(plib.n_cells)]
+    pnet = spat.make_pattern_netlist(plib, 4, seed=9, weights=w)
+    la = np.asarray(plib.load_axis, np.float64)
+    mids = 0.5 * (la[:-1] + la[1:])
+    pnet = dataclasses.replace(pnet, load_ff=mids[np.arange(4) % len(mids)].astype(np.float32))
+    counts = np.array([60, 45, 1, 30])
+    ptr = spat.make_pattern_trace(pnet, counts, 1500, 11, tie_p=0.2, clock_pin_share=0.4)
+    bin_ps = 30
+    dLdP = np.random.default_rng(4).normal(size=1500 // bin_ps)
+    got = opat.adjoint(plib, pnet, ptr, bin_ps, dLdP, glitch_clock_ps=clock)
+    for g in range(4):
+        h = 1e-3 * float(pnet.load_ff[g])
+        loss = []
+        for sgn in (1.0, -1.0):
+            lf = pnet.load_ff.astype(np.float64).copy()
+            lf[g] += sgn * h
+            bins = opat.walk(plib, dataclasses.replace(pnet, load_ff=lf), ptr, bin_ps, glitch_clock_ps=clock)["bins"]
+            loss.append(float(np.dot(dLdP, bins * 1e-3 / bin_ps)))
+        fd = (loss[0] - loss[1]) / (2 * h)
+        assert got[g] == pytest.approx(fd, rel=1e-7, abs=1e-9 * max(1.0, abs(fd)))
+    assert np.count_nonzero(got) >= 3
