@@ -748,7 +748,10 @@ def measure_patterns(eng, dev, cfg, wave, n_ev, steps):
     for _ in range(3):
         run()
     torch.cuda.synchronize(dev)
-    plain_run_ms = _events_per_s(run, steps, dev)
+    # the plain run with the same phase events as the rows below; the median of three trials
+    eng.set_param("timing", 1)
+    plain_run_ms = statistics.median(_events_per_s(run, steps, dev) for _ in range(3))
+    eng.set_param("timing", 0)
     eng.load_pattern_cells(plib)
     eng.load_pattern_netlist(pnet)
     eng.load_pattern_events(0, ptr)
