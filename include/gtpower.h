@@ -587,7 +587,10 @@ int gtp_measure_replay(gtp_ctx* ctx, int32_t window, int32_t bin_ps, double* ms)
  * "t_merge_ns", "t_pattern_ns" (the pattern gates' walk, also inside
  * "t_walk_ns"), "t_prep_ns" (the pass that rebuilds the event descriptors
  * and per-gate energy tables after a netlist, load or scale change, at the
- * start of the next run), "n_timed", and "launches" = kernels launched since timing
+ * start of the next run), "t_stream_setup_ns", "t_stream_copy_ns",
+ * "t_stream_tail_ns" (a streamed run's time before its first copy, from the
+ * first copy's start to the last copy's end, and after that), "n_timed",
+ * and "launches" = kernels launched since timing
  * was last set; 2 = "t_walk_ns" only, two events a run instead of twelve,
  * so that timing a step barely lengthens it; 0 = off). */
 int gtp_set_param(gtp_ctx* ctx, const char* key, int64_t value);

@@ -195,6 +195,9 @@ struct gtp_ctx {
   // gate pass, plan, walk (all walks), merge; the tiled and pattern walks; the descriptor and gate-table pass
   int64_t t_ns[7] = {0, 0, 0, 0, 0, 0, 0};
   bool prep_marked = false;  // the run rebuilt descriptors and gate tables under timing level 1
+  // streamed runs under timing level 1: start, first copy, last copy done, end
+  cudaEvent_t ev_sx[4] = {};
+  int64_t t_sx[3] = {0, 0, 0};  // setup (to the first copy), copies, tail (last copy to the end)
   int64_t n_timed = 0;
   int64_t launches = 0;
 };
@@ -991,6 +994,8 @@ void gtp_destroy(gtp_ctx* ctx) {
   if (ctx->h_plan) cudaFreeHost(ctx->h_plan);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& e : ctx->ev_sx)
+    if (e) cudaEventDestroy(e);
   delete ctx;
 }
 
@@ -1525,6 +1530,7 @@ int gtp_run_power_streamed(gtp_ctx* ctx, int32_t window, int64_t window_ps, int6
       CU(ctx->pk_buf[i].reserve(sizeof(uint32_t) * (size_t)(pk_words + max_chunk / 32 + 2)), "alloc packed buffer");
   // the window: offsets and initial states on the device, records only chunk by chunk
   CU(cudaStreamSynchronize(st), "run_power_streamed");
+  if (ctx->timing == 1 && ctx->ev_sx[0]) cudaEventRecord(ctx->ev_sx[0], st);
   Window& W = ctx->windows[window];
   W.loaded = false;
   W.has_result = false;
@@ -1571,6 +1577,7 @@ int gtp_run_power_streamed(gtp_ctx* ctx, int32_t window, int64_t window_ps, int6
   // the copy stream starts after the uploads above
   CU(cudaEventRecord(ctx->ev_walked[0], st), "event");
   CU(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_walked[0], 0), "wait");
+  const bool sx = ctx->timing == 1 && ctx->ev_sx[0];
   const uint2* host_rec = reinterpret_cast<const uint2*>(events);
   const uint32_t* host_anchor = reinterpret_cast<const uint32_t*>(events);
   const uint32_t* host_word = host_anchor + (n_events + 31) / 32;
@@ -1587,6 +1594,7 @@ int gtp_run_power_streamed(gtp_ctx* ctx, int32_t window, int64_t window_ps, int6
     }
     const int64_t r0 = gate_offsets[gb[c]], nr = gate_offsets[gb[c + 1]] - r0;
     if (c >= 2) CU(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_walked[b], 0), "wait walk");
+    if (sx && c == 0) cudaEventRecord(ctx->ev_sx[1], ctx->copy_stream);
     uint32_t* pk_word = ctx->pk_buf[b].as<uint32_t>();
     uint32_t* pk_anchor = pk_word + pk_words;
     if (nr > 0 && !packed)
@@ -1599,6 +1607,7 @@ int gtp_run_power_streamed(gtp_ctx* ctx, int32_t window, int64_t window_ps, int6
       CU(cudaMemcpyAsync(pk_anchor, host_anchor + a0, sizeof(uint32_t) * (size_t)(a1 - a0 + 1),
                          cudaMemcpyHostToDevice, ctx->copy_stream), "copy chunk anchors");
     }
+    if (sx && c == n_chunks - 1) cudaEventRecord(ctx->ev_sx[2], ctx->copy_stream);
     CU(cudaEventRecord(ctx->ev_copied[b], ctx->copy_stream), "event");
     CU(cudaStreamWaitEvent(st, ctx->ev_copied[b], 0), "wait copy");
     if (nr > 0 && packed) {
@@ -1630,7 +1639,15 @@ int gtp_run_power_streamed(gtp_ctx* ctx, int32_t window, int64_t window_ps, int6
   CU(cudaMemcpyAsync(ctx->h_err, ctx->d_err.p, sizeof(DevError), cudaMemcpyDeviceToHost, st), "read status");
   unsigned long long key = ~0ull;
   CU(cudaMemcpyAsync(&key, ctx->first_bad.p, sizeof key, cudaMemcpyDeviceToHost, st), "read trace check");
+  if (sx) cudaEventRecord(ctx->ev_sx[3], st);
   CU(cudaStreamSynchronize(st), "run_power_streamed");
+  if (sx) {
+    for (int k = 0; k < 3; ++k) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ctx->ev_sx[k], ctx->ev_sx[k + 1]) == cudaSuccess) ctx->t_sx[k] += (int64_t)(ms * 1e6);
+    }
+    ctx->n_timed += 1;
+  }
   int rc = GTP_OK;
   if (ctx->h_err->code != 0) {
     if (key != ~0ull) {
@@ -2209,11 +2226,14 @@ int gtp_set_param(gtp_ctx* ctx, const char* key, int64_t value) {
     // 1: time the phases of every following run with CUDA events; 2: the walk only (two events a run, so
     // the timing barely adds to a step); any value resets the totals
     DeviceGuard dg(ctx->device);
-    if (value > 0 && !ctx->ev[0])
+    if (value > 0 && !ctx->ev[0]) {
       for (auto& e : ctx->ev) CU(cudaEventCreate(&e), "event create");
+      for (auto& e : ctx->ev_sx) CU(cudaEventCreate(&e), "event create");
+    }
     if (value > 2) return fail(ctx, GTP_ERANGE, "timing must be 0, 1 or 2");
     ctx->timing = value > 0 ? (int)value : 0;
     for (auto& t : ctx->t_ns) t = 0;
+    for (auto& t : ctx->t_sx) t = 0;
     ctx->prep_marked = false;
     ctx->n_timed = 0;
     ctx->launches = 0;
@@ -2242,6 +2262,9 @@ int64_t gtp_get_param(const gtp_ctx* ctx, const char* key) {
   if (k == "t_tiled_ns") return ctx->t_ns[4];
   if (k == "t_pattern_ns") return ctx->t_ns[5];
   if (k == "t_prep_ns") return ctx->t_ns[6];
+  if (k == "t_stream_setup_ns") return ctx->t_sx[0];
+  if (k == "t_stream_copy_ns") return ctx->t_sx[1];
+  if (k == "t_stream_tail_ns") return ctx->t_sx[2];
   if (k == "scheme_evt_tgt") return ctx->p_evt_tgt;
   if (k == "scheme_thr_floor") return ctx->p_thr_floor;
   if (k == "scheme_ncyc_fix") return ctx->p_ncyc_fix;
