@@ -113,7 +113,8 @@ struct DenseSmem {
   uint2* halo;     // [2][2] per staging buffer: the records just before and just after the segment
   float* ginv;     // glitch detection: [8] per pin 2 / (rise + fall transition time), -1 for none
   uint32_t* gprev; // glitch detection: [8][32] per pin and lane, the pin's previous event time + 1 (0: none)
-  uint32_t* gtot;  // glitch detection: [8] per pin, the segment's last event time + 1 (medium gates)
+  uint32_t* gown;  // glitch detection: [8][32] per pin and lane, the lane's last time + 1 on the pin in the segment
+  uint32_t* gtot;  // glitch detection: [8] per pin, the last time + 1 before the warp's segment (big gates)
   uint32_t* gcarry;// glitch detection: [8] per pin, the gate's last event time + 1 before the segment
   double* wacc;    // adjoint: [2 * n_cells] per-warp cell sums
 };
@@ -353,34 +354,38 @@ struct SegSums {
 };
 
 // Glitch detection, per staged segment: each pin's previous event time (+1;
-// 0: none) as the lane's first event sees it within the segment.  The lane
-// writes its records' times into its column of gprev (by pin), and a warp
-// max-scan per pin turns the columns into the last time on that pin in the
-// lanes before (times do not decrease along the segment).  The segment's
-// last time per pin goes to tot[pin].  The callers then fold in the gate's
-// earlier segments.
+// 0: none) as the lane's first event on that pin sees it (times do not
+// decrease along a gate).  Each lane writes its records' times into its
+// column of gown (by pin; its last one stays) and notes which pins its
+// records hold; per pin, one ballot gives the nearest earlier lane with an
+// event on the pin, whose time the lane takes, else before[pin] (the gate's
+// last time on the pin before the segment; 0 with before == nullptr, when the
+// caller folds it in afterwards).  Returns, in lane p <= n_in, the segment's
+// last time on pin p, else before[p] (0).
 template <int K, bool FULL>
-__device__ __forceinline__ void gl_segment_scan(const DGate& d, const uint2* buf, const Seg& q, uint32_t* gprev,
-                                                uint32_t* tot, int lane) {
-  for (uint32_t p = 0; p <= d.n_in; ++p) gprev[p * 32 + lane] = 0u;
+__device__ __forceinline__ uint32_t gl_segment_prev(const DGate& d, const uint2* buf, const Seg& q, uint32_t* gprev,
+                                                    uint32_t* gown, const uint32_t* before, int lane) {
   const uint32_t rb = row_base<K>(lane);
+  uint32_t pm = 0u;
 #pragma unroll
   for (int k = 0; k < K; ++k)
     if (FULL || k < q.nk) {
       const uint2 r = buf[rb ^ (uint32_t)k];
-      gprev[min(r.y & 0xFu, 7u) * 32 + lane] = r.x + 1u;  // a bad pin is screened out before the replay
+      const uint32_t pin = min(r.y & 0xFu, 7u);  // a bad pin is screened out before the replay
+      gown[pin * 32 + lane] = r.x + 1u;
+      pm |= 1u << pin;
     }
+  __syncwarp();
+  const unsigned lt = (1u << lane) - 1u;
+  uint32_t tot = 0u;
   for (uint32_t p = 0; p <= d.n_in; ++p) {
-    uint32_t inc = gprev[p * 32 + lane];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(kFull, inc, o);
-      if (lane >= o) inc = max(inc, y);
-    }
-    const uint32_t ex = __shfl_up_sync(kFull, inc, 1);
-    gprev[p * 32 + lane] = lane == 0 ? 0u : ex;
-    if (lane == 31) tot[p] = inc;
+    const unsigned m = __ballot_sync(kFull, (pm >> p) & 1u);
+    const unsigned lo = m & lt;
+    const uint32_t b = before ? before[p] : 0u;
+    gprev[p * 32 + lane] = lo ? gown[p * 32 + 31 - __clz(lo)] : b;
+    if (lane == (int)p) tot = m ? gown[p * 32 + 31 - __clz(m)] : b;
   }
+  return tot;
 }
 
 template <int K, bool BWD, bool TAB, bool FULL, bool GL, bool CMP>
@@ -657,13 +662,11 @@ __device__ __forceinline__ void medium_gate(const LibView& L, const NetView& N, 
     const uint2* halo = sm.halo + (s & 1) * 2;
     const bool full = (s + 1) * SEG <= d.n;
     const uint32_t tx = full ? seg_front<K, true>(d, s, cur, halo, q, lane) : seg_front<K, false>(d, s, cur, halo, q, lane);
-    if (GL) {  // previous event times per pin: this segment's earlier lanes, then the gate's earlier segments
-      if (full) gl_segment_scan<K, true>(d, cur, q, sm.gprev, sm.gtot, lane);
-      else gl_segment_scan<K, false>(d, cur, q, sm.gprev, sm.gtot, lane);
+    if (GL) {  // previous event times per pin: this segment's earlier lanes, else the gate's earlier segments
+      const uint32_t tot = full ? gl_segment_prev<K, true>(d, cur, q, sm.gprev, sm.gown, sm.gcarry, lane)
+                                : gl_segment_prev<K, false>(d, cur, q, sm.gprev, sm.gown, sm.gcarry, lane);
       __syncwarp();
-      for (uint32_t p = 0; p <= d.n_in; ++p) sm.gprev[p * 32 + lane] = max(sm.gprev[p * 32 + lane], sm.gcarry[p]);
-      __syncwarp();
-      if (lane <= (int)d.n_in) sm.gcarry[lane] = max(sm.gcarry[lane], sm.gtot[lane]);
+      if (lane <= (int)d.n_in) sm.gcarry[lane] = tot;
     }
     if (full) {
       acc.add(seg_back<K, BWD, TAB, true, GL, CMP>(L, N, d, sm, cur, q, carry, err, lane), GL);
@@ -707,25 +710,27 @@ __device__ __forceinline__ void big_gate(const LibView& L, const NetView& N, con
     const uint2* halo = sm.halo + (c & 1) * 2;
     const bool full = (s + 1) * SEG <= d.n;
     const uint32_t tx = full ? seg_front<K, true>(d, s, cur, halo, q, lane) : seg_front<K, false>(d, s, cur, halo, q, lane);
-    if (GL) {
-      if (full) gl_segment_scan<K, true>(d, cur, q, sm.gprev, gx[c & 1][wib], lane);
-      else gl_segment_scan<K, false>(d, cur, q, sm.gprev, gx[c & 1][wib], lane);
+    if (GL) {  // this segment's own earlier lanes; the segment's last time per pin for the other warps
+      const uint32_t tot = full ? gl_segment_prev<K, true>(d, cur, q, sm.gprev, sm.gown, nullptr, lane)
+                                : gl_segment_prev<K, false>(d, cur, q, sm.gprev, sm.gown, nullptr, lane);
+      if (lane <= (int)d.n_in) gx[c & 1][wib][lane] = tot;
     }
     if (lane == 0) xfer[c & 1][wib] = tx;
     __syncthreads();
-    if (GL) {  // fold in the chunk's earlier segments (other warps) and the earlier chunks
-      for (uint32_t p = 0; p <= d.n_in; ++p) {
-        uint32_t before = sm.gcarry[p], all = before;
+    if (GL) {  // fold in the chunk's earlier segments (other warps) and the earlier chunks: lane p for pin p
+      if (lane <= (int)d.n_in) {
+        uint32_t before = sm.gcarry[lane], all = before;
+#pragma unroll
         for (int v = 0; v < kWarps; ++v) {
-          const uint32_t m = gx[c & 1][v][p];
+          const uint32_t m = gx[c & 1][v][lane];
           if (v < wib) before = max(before, m);
           all = max(all, m);
         }
-        sm.gprev[p * 32 + lane] = max(sm.gprev[p * 32 + lane], before);
-        __syncwarp();
-        if (lane == 0) sm.gcarry[p] = all;
-        __syncwarp();
+        sm.gtot[lane] = before;
+        sm.gcarry[lane] = all;
       }
+      __syncwarp();
+      for (uint32_t p = 0; p <= d.n_in; ++p) sm.gprev[p * 32 + lane] = max(sm.gprev[p * 32 + lane], sm.gtot[p]);
     }
     uint32_t seg_in = carry;
 #pragma unroll
@@ -1041,7 +1046,7 @@ __device__ __forceinline__ void stage_gate_table(const float* __restrict__ gt, i
 __host__ __device__ inline size_t dense_area(int K, bool bwd, bool gl) {
   return (size_t)kWarps * (2 * 32 * K * sizeof(uint2) + (bwd ? 2 : 1) * kTabEntries * sizeof(float) +
                            kLeakEntries * sizeof(float) + 4 * sizeof(uint2) +
-                           (gl ? 8 * sizeof(float) + (8 * 32 + 16) * sizeof(uint32_t) : 0));
+                           (gl ? 8 * sizeof(float) + (2 * 8 * 32 + 16) * sizeof(uint32_t) : 0));
 }
 __host__ __device__ inline size_t sparse_area(int n_leak, bool bwd, bool gl) {
   return (size_t)(bwd ? (kBwdTabL1 ? 0 : 2) : (kFwdTabL1 ? 0 : 1)) * kGateTab * kWalkThreads * sizeof(float) +
@@ -1101,8 +1106,9 @@ __global__ void __launch_bounds__(kWalkThreads,
   sp += (size_t)kWarps * 4 * sizeof(uint2);
   sm.ginv = reinterpret_cast<float*>(sp) + (size_t)wib * 8;
   sp += (size_t)kWarps * 8 * sizeof(float);
-  sm.gprev = reinterpret_cast<uint32_t*>(sp) + (size_t)wib * (8 * 32 + 16);
-  sm.gtot = sm.gprev + 8 * 32;
+  sm.gprev = reinterpret_cast<uint32_t*>(sp) + (size_t)wib * (2 * 8 * 32 + 16);
+  sm.gown = sm.gprev + 8 * 32;
+  sm.gtot = sm.gown + 8 * 32;
   sm.gcarry = sm.gtot + 8;
   // sparse view of the union area
   float* stab = reinterpret_cast<float*>(smem);
