@@ -378,7 +378,9 @@ __device__ __forceinline__ uint32_t gl_segment_prev(const DGate& d, const uint2*
   __syncwarp();
   const unsigned lt = (1u << lane) - 1u;
   uint32_t tot = 0u;
-  for (uint32_t p = 0; p <= d.n_in; ++p) {
+#pragma unroll
+  for (uint32_t p = 0; p < 8u; ++p) {  // unrolled so that the pins' ballots and loads overlap
+    if (p > d.n_in) break;
     const unsigned m = __ballot_sync(kFull, (pm >> p) & 1u);
     const unsigned lo = m & lt;
     const uint32_t b = before ? before[p] : 0u;
@@ -730,7 +732,11 @@ __device__ __forceinline__ void big_gate(const LibView& L, const NetView& N, con
         sm.gcarry[lane] = all;
       }
       __syncwarp();
-      for (uint32_t p = 0; p <= d.n_in; ++p) sm.gprev[p * 32 + lane] = max(sm.gprev[p * 32 + lane], sm.gtot[p]);
+#pragma unroll
+      for (uint32_t p = 0; p < 8u; ++p) {
+        if (p > d.n_in) break;
+        sm.gprev[p * 32 + lane] = max(sm.gprev[p * 32 + lane], sm.gtot[p]);
+      }
     }
     uint32_t seg_in = carry;
 #pragma unroll
