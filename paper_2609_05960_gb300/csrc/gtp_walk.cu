@@ -130,31 +130,49 @@ __global__ void __launch_bounds__(256) k_prepare(LibView L, NetView N, const Win
       for (int64_t i = tid; i < W.n_bins; i += stride) W.tbins[i] = make_double2(0.0, 0.0);
   }
   double p0 = 0.0;
-  for (int64_t g = W.g0 + tid; g < W.g1; g += stride) {
-    const int64_t c = W.offsets[g + 1] - W.offsets[g];
-    const bool tiled = PLAN && is_tiled(c, tmin, (uint32_t)L.cells[N.cell[g]].n_in);
-    if (GATE) {
-      const int32_t cell = N.cell[g];
-      const CellInfo ci = L.cells[cell];
-      uint32_t s0 = W.init[g];
-      if (s0 >> (ci.n_in + 1)) {
-        report_error(err, GTP_ERANGE, -1 - g);
-        s0 &= (2u << ci.n_in) - 1u;
-      }
-      const float Pl = L.leak[ci.leak_base + s0] * L.lscale[cell];
-      p0 += (double)Pl;
-      const bool split = PLAN && !tiled && gate_items(c, piece_len) > 1;
-      if (!PLAN || c == 0 || tiled || split) {  // the tiled walk and the pieces of a split gate add into its sums
-        W.e_leak[g] = c == 0 ? (double)Pl * (double)W.window_ps * 1e-6 : 0.0;
-        W.e_int[g] = 0.0;
-        W.e_sw[g] = 0.0;
-        if (W.e_gl) W.e_gl[g] = 0.0;
-        W.final_state[g] = (uint8_t)s0;
-      }
+  // kP gates a thread per round, their loads issued together (a window of a batched run has a few blocks
+  // for many gates, so one gate at a time left each thread waiting on one load chain after another)
+  constexpr int kP = 4;
+  for (int64_t g0 = W.g0 + tid; g0 < W.g1; g0 += (int64_t)kP * stride) {
+    int64_t c[kP];
+    int32_t cl[kP];
+    uint32_t s0[kP];
+#pragma unroll
+    for (int j = 0; j < kP; ++j) {
+      const int64_t g = g0 + (int64_t)j * stride;
+      const bool ok = g < W.g1;
+      c[j] = ok ? W.offsets[g + 1] - W.offsets[g] : 0;
+      cl[j] = ok && (GATE || tmin > 0) ? N.cell[g] : 0;
+      s0[j] = ok && GATE ? (uint32_t)W.init[g] : 0u;
     }
-    if (PLAN && c > 0) {
-      const int64_t items = tiled ? 1 : gate_items(c, piece_len);
-      atomicAdd(&sh[work_bucket(items > 1 ? piece_len : c, dmin, seg_len, tiled, items > 1)], (unsigned int)items);
+#pragma unroll
+    for (int j = 0; j < kP; ++j) {
+      const int64_t g = g0 + (int64_t)j * stride;
+      if (g >= W.g1) break;
+      const bool tiled = PLAN && tmin > 0 && is_tiled(c[j], tmin, (uint32_t)L.cells[cl[j]].n_in);
+      if (GATE) {
+        const CellInfo ci = L.cells[cl[j]];
+        uint32_t s = s0[j];
+        if (s >> (ci.n_in + 1)) {
+          report_error(err, GTP_ERANGE, -1 - g);
+          s &= (2u << ci.n_in) - 1u;
+        }
+        const float Pl = L.leak[ci.leak_base + s] * L.lscale[cl[j]];
+        p0 += (double)Pl;
+        const bool split = PLAN && !tiled && gate_items(c[j], piece_len) > 1;
+        if (!PLAN || c[j] == 0 || tiled || split) {  // the tiled walk and the pieces of a split gate add into its sums
+          W.e_leak[g] = c[j] == 0 ? (double)Pl * (double)W.window_ps * 1e-6 : 0.0;
+          W.e_int[g] = 0.0;
+          W.e_sw[g] = 0.0;
+          if (W.e_gl) W.e_gl[g] = 0.0;
+          W.final_state[g] = (uint8_t)s;
+        }
+      }
+      if (PLAN && c[j] > 0) {
+        const int64_t items = tiled ? 1 : gate_items(c[j], piece_len);
+        atomicAdd(&sh[work_bucket(items > 1 ? piece_len : c[j], dmin, seg_len, tiled, items > 1)],
+                  (unsigned int)items);
+      }
     }
   }
   if (GATE) {
@@ -186,7 +204,10 @@ __global__ void __launch_bounds__(256) k_prepare(LibView L, NetView N, const Win
 
 // Each block round places kScatterPer gates per thread, so the bucket
 // cursors see one atomic per bucket per 256 * kScatterPer gates.
-constexpr int kScatterPer = 8;
+#ifndef GTP_SCATTER_PER
+#define GTP_SCATTER_PER 8
+#endif
+constexpr int kScatterPer = GTP_SCATTER_PER;
 
 __global__ void k_plan_scatter(const WinDesc* __restrict__ wins, int64_t seg_len, int dmin, PlanBufs P,
                                const int32_t* __restrict__ gcell, const CellInfo* __restrict__ cells, int64_t tmin,
@@ -207,7 +228,7 @@ __global__ void k_plan_scatter(const WinDesc* __restrict__ wins, int64_t seg_len
     for (int j = 0; j < kScatterPer; ++j) {
       const int64_t g = base + (int64_t)j * blockDim.x + threadIdx.x;
       const int64_t c = g < W.g1 ? W.offsets[g + 1] - W.offsets[g] : 0;
-      const bool tiled = c > 0 && is_tiled(c, tmin, (uint32_t)cells[gcell[g]].n_in);
+      const bool tiled = c > 0 && tmin > 0 && is_tiled(c, tmin, (uint32_t)cells[gcell[g]].n_in);
       items[j] = (unsigned int)(tiled ? 1 : gate_items(c, piece_len));
       bk[j] = c > 0 ? work_bucket(items[j] > 1 ? piece_len : c, dmin, seg_len, tiled, items[j] > 1) : -1;
       local[j] = bk[j] >= 0 ? atomicAdd(&sh[bk[j]], items[j]) : 0u;
