@@ -145,6 +145,7 @@ __global__ void __launch_bounds__(256) k_prepare(LibView L, NetView N, const Win
       cl[j] = ok && (GATE || tmin > 0) ? N.cell[g] : 0;
       s0[j] = ok && GATE ? (uint32_t)W.init[g] : 0u;
     }
+    float p4 = 0.f;  // the round's initial leakage powers (FP32 for at most kP terms, then one FP64 add)
 #pragma unroll
     for (int j = 0; j < kP; ++j) {
       const int64_t g = g0 + (int64_t)j * stride;
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(256) k_prepare(LibView L, NetView N, const Win
           s &= (2u << ci.n_in) - 1u;
         }
         const float Pl = L.leak[ci.leak_base + s] * L.lscale[cl[j]];
-        p0 += (double)Pl;
+        p4 += Pl;
         const bool split = PLAN && !tiled && gate_items(c[j], piece_len) > 1;
         if (!PLAN || c[j] == 0 || tiled || split) {  // the tiled walk and the pieces of a split gate add into its sums
           W.e_leak[g] = c[j] == 0 ? (double)Pl * (double)W.window_ps * 1e-6 : 0.0;
@@ -174,6 +175,7 @@ __global__ void __launch_bounds__(256) k_prepare(LibView L, NetView N, const Win
                   (unsigned int)items);
       }
     }
+    if (GATE) p0 += (double)p4;
   }
   if (GATE) {
     for (int o = 16; o > 0; o >>= 1) p0 += __shfl_down_sync(0xffffffffu, p0, o);
