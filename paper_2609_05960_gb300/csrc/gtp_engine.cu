@@ -170,7 +170,7 @@ struct gtp_ctx {
   int64_t p_kernel = 0;
   int64_t p_rpt = 8;
   int64_t p_ctas_per_sm = 0;
-  int64_t p_dense_min = 256;
+  int64_t p_dense_min = -1;  // -1: kDenseMinFwd for forward runs, kDenseMinBwd for the adjoint
   int64_t p_tile_min = 0;  // gates with this many events or more take the time-sliced walk (0: none)
   int64_t p_piece_len = -1;   // gates with more events are split into pieces (0: never, -1: chosen per run)
   int64_t run_piece_len = 0;  // the piece length of the run being planned
@@ -462,12 +462,25 @@ int upload_plan(gtp_ctx* ctx, int n, cudaStream_t st) {
   return GTP_OK;
 }
 
-WalkArgs walk_args(gtp_ctx* ctx, int n) {
+// Gates with more events than dense_min are walked by warps, the others one
+// per thread.  Measured on the large, adjoint and stress workloads (walk ms,
+// dense_min 256 / 512 / 768 / 1024): forward 1.204 / 1.181 / 1.178 / 1.180,
+// 0.611 / 0.602 / 0.600 / 0.606, 13.37 / 13.35 / 13.32 / 13.33; the adjoint,
+// whose sparse threads wait on their gradient loads, 1.408 at 256 and 1.449
+// at 512 (large).
+constexpr int kDenseMinFwd = 768;
+constexpr int kDenseMinBwd = 256;
+
+int dense_min_of(const gtp_ctx* ctx, bool backward) {
+  return ctx->p_dense_min > 0 ? (int)ctx->p_dense_min : (backward ? kDenseMinBwd : kDenseMinFwd);
+}
+
+WalkArgs walk_args(gtp_ctx* ctx, int n, bool backward = false) {
   WalkArgs A{};
   A.wins = plan_wins(ctx->plan.p);
   A.n_win = n;
   A.rpt = (int)ctx->p_rpt;
-  A.dense_min = (int)ctx->p_dense_min;
+  A.dense_min = dense_min_of(ctx, backward);
   A.grid = ctx->p_ctas_per_sm > 0 ? (int)(ctx->p_ctas_per_sm * ctx->n_sm) : 0;
   A.n_sm = ctx->n_sm;
   A.err = ctx->d_err.as<DevError>();
@@ -1746,7 +1759,7 @@ int gtp_run_power_backward(gtp_ctx* ctx, int32_t window, int32_t bin_ps, const f
   mark(ctx, 1, st);
   ctx->launches += 4;
   mark(ctx, 2, st);
-  WalkArgs A = walk_args(ctx, 1);
+  WalkArgs A = walk_args(ctx, 1, true);
   A.whole = ctx->run_whole;
   if (W->n_events > 0) CU(launch_plan(ctx->N, ctx->L, A, st), "plan");
   mark(ctx, 3, st);
@@ -1796,7 +1809,7 @@ int gtp_autotune(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_
   int64_t br = ctx->p_rpt, bc = ctx->p_dense_min;
   std::vector<double*> none(n_windows, nullptr);
   const int rpts[] = {4, 8, 16};
-  const int dmins[] = {64, 256, 1024};
+  const int dmins[] = {64, 256, 768, 2048};
   int rc = GTP_OK;
   ctx->p_ctas_per_sm = 0;
   for (int r : rpts) {
@@ -2200,7 +2213,7 @@ int gtp_set_param(gtp_ctx* ctx, const char* key, int64_t value) {
     ctx->p_ctas_per_sm = value < 0 ? 0 : value;
   } else if (k == "dense_min") {
     if (value == 0 || value > 4096) return fail(ctx, GTP_ERANGE, "dense_min must be 1..4096");
-    ctx->p_dense_min = value < 0 ? 256 : value;
+    ctx->p_dense_min = value < 0 ? -1 : value;
   } else if (k == "piece_len") {
     ctx->p_piece_len = value < 0 ? -1 : value;
   } else if (k == "sipl_max_pins") {
@@ -2249,7 +2262,8 @@ int64_t gtp_get_param(const gtp_ctx* ctx, const char* key) {
   if (k == "kernel") return ctx->p_kernel;
   if (k == "records_per_thread") return ctx->p_rpt;
   if (k == "ctas_per_sm") return ctx->p_ctas_per_sm;
-  if (k == "dense_min") return ctx->p_dense_min;
+  if (k == "dense_min") return dense_min_of(ctx, false);
+  if (k == "dense_min_backward") return dense_min_of(ctx, true);
   if (k == "tile_min") return ctx->p_tile_min;
   if (k == "piece_len") return ctx->p_piece_len;
   if (k == "run_piece_len") return ctx->run_piece_len;
