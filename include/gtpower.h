@@ -524,7 +524,7 @@ int gtp_run_power_backward(gtp_ctx* ctx, int32_t window, int32_t bin_ps, const f
  * parallelism floor; Sec. 6.4) for this engine's partitioning parameters.
  * Autotuner: time the walk of the given windows for every candidate
  * (records per lane 4/8/16 = segment length 128/256/512 events, dense_min
- * 64/256/768/2048), `iters` timed runs each, keep the fastest as the context's
+ * 64/256/512/1024), `iters` timed runs each, keep the fastest as the context's
  * parameters and report its time per run (ms) in *best_ms.  Runs the windows
  * repeatedly; their per-gate results are those of the last run.
  */
@@ -556,9 +556,11 @@ int gtp_measure_replay(gtp_ctx* ctx, int32_t window, int32_t bin_ps, double* ms)
 /* Engine tuning knobs; value < 0 restores the default.  Keys:
  * "records_per_thread" (4, 8, 16; events per lane of a dense segment),
  * "ctas_per_sm" (0 = full occupancy), "dense_min" (gates with more events are cut into segments and
- * walked by warps, the others one per thread; 1..4096; by default 768 in
- * forward runs and 256 in the adjoint; gtp_get_param "dense_min" and
- * "dense_min_backward" report the values in use),
+ * walked by warps, the others one per thread; 1..4096; by default chosen
+ * per run: 256 in the adjoint and in forward runs of fewer than 260,000
+ * events per SM (in the busiest window group, or streamed chunk), 384 up to
+ * 600,000, 512 above; gtp_get_param "dense_min" reports the value set, else
+ * the last run's),
  * "piece_len" (a gate with more events than this is walked as several
  * work items of piece_len events, each starting from the state its earlier
  * records leave, so that one very busy gate cannot hold up a run; -1 = chosen

@@ -170,7 +170,8 @@ struct gtp_ctx {
   int64_t p_kernel = 0;
   int64_t p_rpt = 8;
   int64_t p_ctas_per_sm = 0;
-  int64_t p_dense_min = -1;  // -1: kDenseMinFwd for forward runs, kDenseMinBwd for the adjoint
+  int64_t p_dense_min = -1;  // -1: chosen per run (see dense_min_auto)
+  int64_t run_dense_min = 0; // the run being planned (0 before the first)
   int64_t p_tile_min = 0;  // gates with this many events or more take the time-sliced walk (0: none)
   int64_t p_piece_len = -1;   // gates with more events are split into pieces (0: never, -1: chosen per run)
   int64_t run_piece_len = 0;  // the piece length of the run being planned
@@ -312,6 +313,22 @@ Window* get_window(gtp_ctx* ctx, int32_t w) {
 
 int64_t seg_len_of(const gtp_ctx* ctx) { return 32 * ctx->p_rpt; }
 
+// Gates with more events than dense_min are walked by warps, the others one
+// per thread.  A thread walks its gate's events one after another, so a
+// sparse item (256 gates of similar count) lasts about dense_min event
+// latencies: a large dense_min pays off only when there is enough work to
+// hide the longest items.  Forward walk ms on the large recipe scaled from
+// 10M to 200M events (dense_min 256 / 384 / 512 / 768): 10M 0.164 / 0.227 /
+// 0.276 / 0.371, 20M 0.182 / 0.244 / 0.310 / 0.421, 40M 0.300 / 0.296 /
+// 0.309 / 0.449, 70M 0.475 / 0.468 / 0.469 / 0.477, 100M 0.638 / 0.628 /
+// 0.628 / 0.629, 200M 1.204 / 1.185 / 1.181 / 1.178.  The adjoint, whose
+// sparse threads wait on a gradient load per event, stays at 256 (large:
+// 1.408 ms at 256, 1.449 at 512).
+int dense_min_auto(int64_t events_per_sm, bool backward) {
+  if (backward || events_per_sm < 260000) return 256;
+  return events_per_sm < 600000 ? 384 : 512;
+}
+
 // Fill the descriptor table of a run in the pinned staging buffer, reserving
 // the windows' device buffers.  The upload is enqueued by upload_plan().
 int build_plan(gtp_ctx* ctx, const std::vector<Window*>& ws, int32_t bin_ps, const std::vector<double*>& waves,
@@ -437,6 +454,8 @@ int build_plan(gtp_ctx* ctx, const std::vector<Window*>& ws, int32_t bin_ps, con
   for (Window* w : ws) e_all += w->n_events;
   if (pl > 0 && e_all / pl >= (int64_t)1 << 20) pl = (e_all >> 20) / kPieceUnit * kPieceUnit + kPieceUnit;
   ctx->run_piece_len = pl;
+  ctx->run_dense_min = ctx->p_dense_min > 0 ? ctx->p_dense_min
+                                            : dense_min_auto(e_total / std::max(ctx->n_sm, 1), backward);
   ctx->run_whole = true;
   for (Window* w : ws)
     if (pl > 0 && (w->streamed || (int64_t)w->max_count > pl)) ctx->run_whole = false;
@@ -462,25 +481,12 @@ int upload_plan(gtp_ctx* ctx, int n, cudaStream_t st) {
   return GTP_OK;
 }
 
-// Gates with more events than dense_min are walked by warps, the others one
-// per thread.  Measured on the large, adjoint and stress workloads (walk ms,
-// dense_min 256 / 512 / 768 / 1024): forward 1.204 / 1.181 / 1.178 / 1.180,
-// 0.611 / 0.602 / 0.600 / 0.606, 13.37 / 13.35 / 13.32 / 13.33; the adjoint,
-// whose sparse threads wait on their gradient loads, 1.408 at 256 and 1.449
-// at 512 (large).
-constexpr int kDenseMinFwd = 768;
-constexpr int kDenseMinBwd = 256;
-
-int dense_min_of(const gtp_ctx* ctx, bool backward) {
-  return ctx->p_dense_min > 0 ? (int)ctx->p_dense_min : (backward ? kDenseMinBwd : kDenseMinFwd);
-}
-
-WalkArgs walk_args(gtp_ctx* ctx, int n, bool backward = false) {
+WalkArgs walk_args(gtp_ctx* ctx, int n) {
   WalkArgs A{};
   A.wins = plan_wins(ctx->plan.p);
   A.n_win = n;
   A.rpt = (int)ctx->p_rpt;
-  A.dense_min = dense_min_of(ctx, backward);
+  A.dense_min = (int)ctx->run_dense_min;  // set by build_plan
   A.grid = ctx->p_ctas_per_sm > 0 ? (int)(ctx->p_ctas_per_sm * ctx->n_sm) : 0;
   A.n_sm = ctx->n_sm;
   A.err = ctx->d_err.as<DevError>();
@@ -820,7 +826,7 @@ int run_forward(gtp_ctx* ctx, const int32_t* windows, int n, int32_t bin_ps, dou
   CU(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(DevError), ctx->stream), "zero status");
   if (use_graph) {
     GraphKey key{std::vector<int32_t>(windows, windows + n), bin_ps, ctx->p_rpt,
-                       ctx->p_ctas_per_sm, ctx->p_kernel, ctx->p_dense_min, ctx->p_tile_min, ctx->run_piece_len,
+                       ctx->p_ctas_per_sm, ctx->p_kernel, ctx->run_dense_min, ctx->p_tile_min, ctx->run_piece_len,
                        ctx->plan_gen,
                        n_tiles_total, any_events, ctx->timing, {}, ctx->run_pat_items, ctx->run_whole};
     for (const auto& gr : ctx->run_groups) key.groups.push_back(gr.first);
@@ -1572,6 +1578,8 @@ int gtp_run_power_streamed(gtp_ctx* ctx, int32_t window, int64_t window_ps, int6
   int64_t n_seg_total = 0, n_tiles_total = 0;
   std::vector<Window*> ws{&W};
   RC(build_plan(ctx, ws, bin_ps, std::vector<double*>{wave}, false, &n_seg_total, &n_tiles_total));
+  // each chunk is walked by its own launch: the split between warps and threads follows the chunk's size
+  if (ctx->p_dense_min <= 0) ctx->run_dense_min = dense_min_auto(max_chunk / std::max(ctx->n_sm, 1), false);
   // one descriptor per chunk: the window's, with the chunk's gates and a record base that puts the
   // chunk buffer at the chunk's first record index (only that chunk's records are ever read)
   WinDesc* hw = plan_wins(ctx->h_plan);
@@ -1759,7 +1767,7 @@ int gtp_run_power_backward(gtp_ctx* ctx, int32_t window, int32_t bin_ps, const f
   mark(ctx, 1, st);
   ctx->launches += 4;
   mark(ctx, 2, st);
-  WalkArgs A = walk_args(ctx, 1, true);
+  WalkArgs A = walk_args(ctx, 1);
   A.whole = ctx->run_whole;
   if (W->n_events > 0) CU(launch_plan(ctx->N, ctx->L, A, st), "plan");
   mark(ctx, 3, st);
@@ -1809,7 +1817,7 @@ int gtp_autotune(gtp_ctx* ctx, int32_t n_windows, const int32_t* windows, int32_
   int64_t br = ctx->p_rpt, bc = ctx->p_dense_min;
   std::vector<double*> none(n_windows, nullptr);
   const int rpts[] = {4, 8, 16};
-  const int dmins[] = {64, 256, 768, 2048};
+  const int dmins[] = {64, 256, 512, 1024};
   int rc = GTP_OK;
   ctx->p_ctas_per_sm = 0;
   for (int r : rpts) {
@@ -2262,8 +2270,7 @@ int64_t gtp_get_param(const gtp_ctx* ctx, const char* key) {
   if (k == "kernel") return ctx->p_kernel;
   if (k == "records_per_thread") return ctx->p_rpt;
   if (k == "ctas_per_sm") return ctx->p_ctas_per_sm;
-  if (k == "dense_min") return dense_min_of(ctx, false);
-  if (k == "dense_min_backward") return dense_min_of(ctx, true);
+  if (k == "dense_min") return ctx->p_dense_min > 0 ? ctx->p_dense_min : (ctx->run_dense_min > 0 ? ctx->run_dense_min : 256);
   if (k == "tile_min") return ctx->p_tile_min;
   if (k == "piece_len") return ctx->p_piece_len;
   if (k == "run_piece_len") return ctx->run_piece_len;

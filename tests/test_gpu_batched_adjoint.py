@@ -217,7 +217,7 @@ def test_autotune_picks_a_valid_plan(engine):
     ms = engine.autotune([0], 100, iters=2)
     assert ms > 0
     assert engine.get_param("records_per_thread") in (4, 8, 16)
-    assert engine.get_param("dense_min") in (64, 256, 768, 2048)
+    assert engine.get_param("dense_min") in (64, 256, 512, 1024)
     w = engine.run_power(0, 100).cpu().numpy()
     ref = oracle.waveform_w(oracle.walk(lib, net, tr, 100)["bins"], 100)
     assert (np.abs(w - ref) / ref).max() <= TOL
