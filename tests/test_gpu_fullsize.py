@@ -116,6 +116,7 @@ def test_large_full_size(engine, opool):
     engine.load_events(0, window_ps=cfg.window_ps, offsets=off, records=rec, init_state=init, borrow=True)
     wave = engine.run_power(0, cfg.bin_ps, graph=False)
     ge = engine.gate_energy(0, device=True)
+    assert engine.get_param("dense_min") == 512  # chosen for 200M events (1.3M an SM): the run above walks it
     # the GPU generator writes the host generator's bits
     host = synth.gate_records(net, tr, np.arange(4))[1]
     assert np.array_equal(host, rec[:len(host)].cpu().numpy().view(np.uint32))

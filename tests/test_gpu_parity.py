@@ -442,3 +442,25 @@ def test_load_and_scale_changes_rebuild_lookups(engine, params):
             got = got.cpu().numpy()
             assert np.all(np.abs(got - ref) <= 1e-4 * np.abs(ref) + 1e-5 * np.abs(ref).max())
     engine.set_scales(None, None)
+
+
+def test_dense_min_chosen_per_run(engine):
+    """Unless set, dense_min follows the run: 256 for a small window and for
+    the adjoint; a value set applies to both directions."""
+    import torch
+    lib, net, tr = small_random(n_gates=300, n_events=40_000, window_ps=400_000, seed=57)
+    engine.load_library(lib)
+    engine.load_netlist(net)
+    engine.set_param("dense_min", -1)
+    engine.load_events(0, tr)
+    engine.run_power(0, 100)
+    assert engine.get_param("dense_min") == 256
+    engine.set_param("dense_min", 48)
+    w = engine.run_power(0, 100).cpu().numpy()
+    assert engine.get_param("dense_min") == 48
+    assert_matches(w, engine.gate_energy(0, device=False), oracle.walk(lib, net, tr, 100), 100)
+    engine.run_power_backward(0, 100, torch.ones(4000, dtype=torch.float32, device=engine.device))
+    assert engine.get_param("dense_min") == 48
+    engine.set_param("dense_min", -1)
+    engine.run_power_backward(0, 100, torch.ones(4000, dtype=torch.float32, device=engine.device))
+    assert engine.get_param("dense_min") == 256
