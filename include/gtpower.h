@@ -559,8 +559,9 @@ int gtp_measure_replay(gtp_ctx* ctx, int32_t window, int32_t bin_ps, double* ms)
  * walked by warps, the others one per thread; 1..4096; by default chosen
  * per run: 256 in the adjoint and in forward runs of fewer than 260,000
  * events per SM (in the busiest window group, or streamed chunk), 384 up to
- * 600,000, 512 above; gtp_get_param "dense_min" reports the value set, else
- * the last run's),
+ * 600,000, 512 above; with glitch detection 384 below 200,000 and 1024
+ * above; gtp_get_param "dense_min" reports the value set, else the last
+ * run's),
  * "piece_len" (a gate with more events than this is walked as several
  * work items of piece_len events, each starting from the state its earlier
  * records leave, so that one very busy gate cannot hold up a run; -1 = chosen

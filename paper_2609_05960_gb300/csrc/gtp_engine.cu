@@ -323,9 +323,15 @@ int64_t seg_len_of(const gtp_ctx* ctx) { return 32 * ctx->p_rpt; }
 // 0.309 / 0.449, 70M 0.475 / 0.468 / 0.469 / 0.477, 100M 0.638 / 0.628 /
 // 0.628 / 0.629, 200M 1.204 / 1.185 / 1.181 / 1.178.  The adjoint, whose
 // sparse threads wait on a gradient load per event, stays at 256 (large:
-// 1.408 ms at 256, 1.449 at 512).
-int dense_min_auto(int64_t events_per_sm, bool backward) {
-  if (backward || events_per_sm < 260000) return 256;
+// 1.408 ms at 256, 1.449 at 512).  With glitch detection the dense segments
+// cost more (per-pin prefixes), so more gates go to threads: glitch walk ms
+// (dense_min 256 / 384 / 512 / 768 / 1024) 20M 0.298 / 0.294 / 0.294 /
+// 0.337 / 0.430, 40M 0.499 / 0.488 / 0.486 / 0.483 / 0.479, 100M 1.036 /
+// 1.010 / 0.999 / 0.987 / 0.980, 200M 1.959 / 1.903 / 1.878 / 1.850 / 1.833.
+int dense_min_auto(int64_t events_per_sm, bool backward, bool glitch) {
+  if (backward) return 256;
+  if (glitch) return events_per_sm < 200000 ? 384 : 1024;
+  if (events_per_sm < 260000) return 256;
   return events_per_sm < 600000 ? 384 : 512;
 }
 
@@ -455,7 +461,8 @@ int build_plan(gtp_ctx* ctx, const std::vector<Window*>& ws, int32_t bin_ps, con
   if (pl > 0 && e_all / pl >= (int64_t)1 << 20) pl = (e_all >> 20) / kPieceUnit * kPieceUnit + kPieceUnit;
   ctx->run_piece_len = pl;
   ctx->run_dense_min = ctx->p_dense_min > 0 ? ctx->p_dense_min
-                                            : dense_min_auto(e_total / std::max(ctx->n_sm, 1), backward);
+                                            : dense_min_auto(e_total / std::max(ctx->n_sm, 1), backward,
+                                                             ctx->N.clock_ps > 0);
   ctx->run_whole = true;
   for (Window* w : ws)
     if (pl > 0 && (w->streamed || (int64_t)w->max_count > pl)) ctx->run_whole = false;
@@ -1579,7 +1586,8 @@ int gtp_run_power_streamed(gtp_ctx* ctx, int32_t window, int64_t window_ps, int6
   std::vector<Window*> ws{&W};
   RC(build_plan(ctx, ws, bin_ps, std::vector<double*>{wave}, false, &n_seg_total, &n_tiles_total));
   // each chunk is walked by its own launch: the split between warps and threads follows the chunk's size
-  if (ctx->p_dense_min <= 0) ctx->run_dense_min = dense_min_auto(max_chunk / std::max(ctx->n_sm, 1), false);
+  if (ctx->p_dense_min <= 0)
+    ctx->run_dense_min = dense_min_auto(max_chunk / std::max(ctx->n_sm, 1), false, ctx->N.clock_ps > 0);
   // one descriptor per chunk: the window's, with the chunk's gates and a record base that puts the
   // chunk buffer at the chunk's first record index (only that chunk's records are ever read)
   WinDesc* hw = plan_wins(ctx->h_plan);
