@@ -555,7 +555,10 @@ int gtp_measure_replay(gtp_ctx* ctx, int32_t window, int32_t bin_ps, double* ms)
 
 /* Engine tuning knobs; value < 0 restores the default.  Keys:
  * "records_per_thread" (4, 8, 16; events per lane of a dense segment),
- * "ctas_per_sm" (0 = full occupancy), "dense_min" (gates with more events are cut into segments and
+ * "ctas_per_sm" (0 = full occupancy), "bwd_staged" (the adjoint's sparse
+ * threads stage their gate tables in shared memory: 1 always, 0 never, -1 =
+ * below 200,000 events per SM, the default; runs without glitch detection),
+ * "dense_min" (gates with more events are cut into segments and
  * walked by warps, the others one per thread; 1..4096; by default chosen
  * per run: 256 in the adjoint and in forward runs of fewer than 260,000
  * events per SM (in the busiest window group, or streamed chunk), 384 up to

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 
 SOURCES = ["gtp_engine.cu", "gtp_kernels.cu", "gtp_walk.cu", "gtp_walk_glitch.cu", "gtp_walk_comp.cu", "gtp_scheme.cu",
            "gtp_sipl.cu", "gtp_noalloc.cu", "gtp_tiled.cu", "gtp_pattern.cu", "gtp_walk_whole.cu",
-           "gtp_walk_glitch_whole.cu", "gtp_walk_adjoint_whole.cu"]
+           "gtp_walk_glitch_whole.cu", "gtp_walk_adjoint_whole.cu", "gtp_walk_adjoint_staged.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr"]

@@ -172,6 +172,7 @@ struct gtp_ctx {
   int64_t p_ctas_per_sm = 0;
   int64_t p_dense_min = -1;  // -1: chosen per run (see dense_min_auto)
   int64_t run_dense_min = 0; // the run being planned (0 before the first)
+  int64_t p_bwd_staged = -1; // adjoint gate tables: 1 staged, 0 in place, -1 by the window's events per SM
   int64_t p_tile_min = 0;  // gates with this many events or more take the time-sliced walk (0: none)
   int64_t p_piece_len = -1;   // gates with more events are split into pieces (0: never, -1: chosen per run)
   int64_t run_piece_len = 0;  // the piece length of the run being planned
@@ -328,6 +329,10 @@ int64_t seg_len_of(const gtp_ctx* ctx) { return 32 * ctx->p_rpt; }
 // (dense_min 256 / 384 / 512 / 768 / 1024) 20M 0.298 / 0.294 / 0.294 /
 // 0.337 / 0.430, 40M 0.499 / 0.488 / 0.486 / 0.483 / 0.479, 100M 1.036 /
 // 1.010 / 0.999 / 0.987 / 0.980, 200M 1.959 / 1.903 / 1.878 / 1.850 / 1.833.
+// The adjoint (without glitch detection) stages its sparse threads' gate
+// tables below this many events per SM.
+constexpr int64_t kBwdStagedBelow = 200000;
+
 int dense_min_auto(int64_t events_per_sm, bool backward, bool glitch) {
   if (backward) return 256;
   if (glitch) return events_per_sm < 200000 ? 384 : 1024;
@@ -1777,6 +1782,9 @@ int gtp_run_power_backward(gtp_ctx* ctx, int32_t window, int32_t bin_ps, const f
   mark(ctx, 2, st);
   WalkArgs A = walk_args(ctx, 1);
   A.whole = ctx->run_whole;
+  // small windows: the build with staged gate tables (see gtp_walk_adjoint_staged.cu)
+  A.staged = ctx->p_bwd_staged != 0 &&
+             (ctx->p_bwd_staged > 0 || W->n_events / std::max(ctx->n_sm, 1) < kBwdStagedBelow);
   if (W->n_events > 0) CU(launch_plan(ctx->N, ctx->L, A, st), "plan");
   mark(ctx, 3, st);
   mark(ctx, 4, st);
@@ -2227,6 +2235,9 @@ int gtp_set_param(gtp_ctx* ctx, const char* key, int64_t value) {
   } else if (k == "ctas_per_sm") {
     if (value > 32) return fail(ctx, GTP_ERANGE, "ctas_per_sm must be <= 32");
     ctx->p_ctas_per_sm = value < 0 ? 0 : value;
+  } else if (k == "bwd_staged") {
+    if (value > 1) return fail(ctx, GTP_ERANGE, "bwd_staged must be -1, 0 or 1");
+    ctx->p_bwd_staged = value < 0 ? -1 : value;
   } else if (k == "dense_min") {
     if (value == 0 || value > 4096) return fail(ctx, GTP_ERANGE, "dense_min must be 1..4096");
     ctx->p_dense_min = value < 0 ? -1 : value;
@@ -2278,6 +2289,7 @@ int64_t gtp_get_param(const gtp_ctx* ctx, const char* key) {
   if (k == "kernel") return ctx->p_kernel;
   if (k == "records_per_thread") return ctx->p_rpt;
   if (k == "ctas_per_sm") return ctx->p_ctas_per_sm;
+  if (k == "bwd_staged") return ctx->p_bwd_staged;
   if (k == "dense_min") return ctx->p_dense_min > 0 ? ctx->p_dense_min : (ctx->run_dense_min > 0 ? ctx->run_dense_min : 256);
   if (k == "tile_min") return ctx->p_tile_min;
   if (k == "piece_len") return ctx->p_piece_len;

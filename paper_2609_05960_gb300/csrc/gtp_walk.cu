@@ -317,6 +317,7 @@ cudaError_t launch_walk(const LibView& L, const NetView& N, const WalkArgs& A, b
     if (!backward && A.whole) return launch_walk_glitch_whole(L, N, A, st);
     return launch_walk_glitch(L, N, A, backward, st);
   }
+  if (backward && A.staged) return launch_walk_adjoint_staged(L, N, A, st);
   if (A.whole) return backward ? launch_walk_adjoint_whole(L, N, A, st) : launch_walk_plain_whole(L, N, A, st);
   return launch_walk_gl<false>(L, N, A, backward, st);
 }

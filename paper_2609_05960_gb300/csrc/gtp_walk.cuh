@@ -66,6 +66,8 @@ struct WalkArgs {
                             // multiple of kPieceUnit
   bool whole;               // no gate of the run has more than piece_len events, so the walk compiled without
                             // pieces is launched (forward and adjoint runs)
+  bool staged;              // adjoint without glitch detection: the build with the sparse threads' gate tables
+                            // staged in shared memory (small windows)
 };
 
 // Work-list entries are {window | piece << kPieceShift, gate}.
@@ -109,6 +111,7 @@ cudaError_t launch_walk_components(const LibView& L, const NetView& N, const Wal
 cudaError_t launch_walk_plain_whole(const LibView& L, const NetView& N, const WalkArgs& A, cudaStream_t st);
 cudaError_t launch_walk_glitch_whole(const LibView& L, const NetView& N, const WalkArgs& A, cudaStream_t st);
 cudaError_t launch_walk_adjoint_whole(const LibView& L, const NetView& N, const WalkArgs& A, cudaStream_t st);
+cudaError_t launch_walk_adjoint_staged(const LibView& L, const NetView& N, const WalkArgs& A, cudaStream_t st);
 // The gates' event descriptors and energy tables in one pass (null outputs
 // are skipped).
 cudaError_t launch_gate_prep(const LibView& L, const NetView& N, uint4* desc, float* gtab, float* gtab_bwd,

@@ -253,3 +253,35 @@ def test_single_window_graph_follows_reloads_and_times_phases(engine):
     assert (np.abs(got - ref) / ref).max() <= TOL
     assert engine.get_param("n_timed") == 1 and engine.get_param("t_walk_ns") > 0
     engine.set_param("timing", 0)
+
+
+@pytest.mark.parametrize("staged", [0, 1])
+@pytest.mark.parametrize("rpt", [4, 8, 16])
+def test_adjoint_gate_table_placements_match_oracle(engine, staged, rpt):
+    """Both adjoint builds (sparse threads' gate tables in place or staged in
+    shared memory) against the FP64 oracle adjoint, with whole and split gates."""
+    import torch
+    lib, net, tr = small_random(n_gates=300, n_events=80_000, window_ps=400_000, seed=63, tie_p=0.05, zipf_s=1.4)
+    bin_ps = 50
+    engine.load_library(lib)
+    engine.load_netlist(net)
+    _reset(engine)
+    engine.set_param("records_per_thread", rpt)
+    engine.set_param("bwd_staged", staged)
+    rng = np.random.default_rng(2)
+    es = rng.uniform(0.5, 2.0, lib.n_cells).astype(np.float32)
+    ls = rng.uniform(0.5, 2.0, lib.n_cells).astype(np.float32)
+    engine.set_scales(es, ls)
+    engine.load_events(0, tr)
+    w = rng.normal(size=tr.window_ps // bin_ps).astype(np.float32) * 1e3
+    rC, rde, rdl = oracle.adjoint(lib, net, tr, bin_ps, w.astype(np.float64), escale=es.astype(np.float64),
+                                  lscale=ls.astype(np.float64))
+    for piece_len in (-1, 4096):  # -1: no gate split; 4096: the busiest gates in pieces
+        engine.set_param("piece_len", piece_len)
+        dC, de, dl = engine.run_power_backward(0, bin_ps, torch.from_numpy(w).to(engine.device))
+        _grad_close(dC.cpu().numpy(), rC)
+        _grad_close(de.cpu().numpy(), rde)
+        _grad_close(dl.cpu().numpy(), rdl)
+    engine.set_param("bwd_staged", -1)
+    engine.set_param("piece_len", -1)
+    engine.set_scales(None, None)
